@@ -1,0 +1,185 @@
+/*
+ * h2.h -- C ABI of the GB300 library for the accuracy-controlled, structure-
+ * preserving H^2 matrix-matrix product with change of cluster bases (Ma & Jiao,
+ * "Accuracy Controlled Structure-Preserving H^2-Matrix-Matrix Product in Linear
+ * Complexity with Change of Cluster Bases").
+ *
+ * Conventions shared by every entry point
+ *   - Plain C types only.  Host pointers are marked "host", device pointers
+ *     "device" (memory of the current CUDA device, e.g. from cudaMalloc or a torch
+ *     CUDA tensor's data_ptr).
+ *   - Every call returns an h2_status; no exception or abort crosses the ABI.
+ *     On failure h2_last_error() returns a thread-local, human-readable message
+ *     and no output handle is created.
+ *   - Handles own their device memory; h2_destroy frees it.  Handles are not
+ *     thread-safe: do not use one handle from two threads at once.
+ *   - Work is enqueued on opts->stream (a cudaStream_t, NULL = the legacy default
+ *     stream).  Calls that return host data synchronise that stream.
+ *   - Point and vector data are in the caller's ("user") order; the library
+ *     permutes to its cluster-tree order internally.
+ *   - Real kernels only on the GPU path in this version (kind 0 and 1); the
+ *     complex Helmholtz kernel returns H2_EUNSUPPORTED.
+ *   - Arithmetic: float64 throughout (H2_FP64) or float32 bulk products with
+ *     float64 Gram matrices, eigen-decompositions and bases (H2_MIXED_FP32).
+ */
+#ifndef H2_GB300_H
+#define H2_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct h2_matrix* h2_handle;
+
+typedef enum {
+  H2_OK = 0,
+  H2_EINVAL = 1,       /* bad argument (null pointer, size, parameter range)        */
+  H2_ENOMEM = 2,       /* device or host allocation failed                           */
+  H2_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed                */
+  H2_ESTRUCT = 4,      /* A and B do not share one cluster tree and block partition */
+  H2_ETIMEOUT = 5,     /* a bounded device-side wait gave up                        */
+  H2_EINTERNAL = 6,    /* internal consistency check failed                          */
+  H2_EUNSUPPORTED = 7  /* valid request this build does not implement               */
+} h2_status;
+
+/* Kernel functions K(x, y), r = |x - y|; the diagonal (x == y) takes diag_re. */
+typedef enum {
+  H2_K_LAPLACE = 0,    /* 1 / (4 pi r)                                   */
+  H2_K_INV_R2 = 1,     /* 1 / r^2                                        */
+  H2_K_HELMHOLTZ = 2   /* exp(-j k r) / (4 pi r)  (oracle only for now)  */
+} h2_kernel_kind;
+
+typedef struct {
+  int32_t kind;        /* h2_kernel_kind */
+  double wavenumber;   /* k of the Helmholtz kernel, ignored otherwise */
+  double diag_re;      /* value on the diagonal */
+  double diag_im;
+} h2_kernel;
+
+typedef enum {
+  H2_FP64 = 0,         /* every product, Gram and eigen-decomposition in float64 */
+  H2_MIXED_FP32 = 1    /* dense and coupling products in float32 (float32
+                          accumulation); Gram sums, eigen-decompositions, new bases
+                          and projections in float64 */
+} h2_precision;
+
+/* Truncation rule of the new cluster bases (Sec. III-C, IV-C): the summed,
+ * normalised Gram matrix G is decomposed, G = U diag(lambda) U^H, and column m of U
+ * is kept when lambda_m / lambda_1 > threshold. */
+typedef enum {
+  H2_TRUNC_PAPER = 0,  /* threshold = eps: the normalised singular values of G (the
+                          paper's statement; error ~ sqrt(eps) in practice)      */
+  H2_TRUNC_SV = 1,     /* threshold = eps^2: singular values of the stacked
+                          contributions (error ~ eps)                            */
+  H2_TRUNC_FULL = 2    /* keep every vector (no truncation; for testing)         */
+} h2_trunc;
+
+typedef struct {
+  int32_t precision;   /* h2_precision, default H2_FP64                          */
+  int32_t trunc;       /* h2_trunc, default H2_TRUNC_PAPER                       */
+  int32_t rank_cap;    /* largest rank of a non-leaf cluster of C; 0 = default 48;
+                          ranks above it are cut to the cap and counted in
+                          h2_stats.cap_hits                                       */
+  int32_t reserved;
+  void* stream;        /* cudaStream_t, NULL = legacy default stream            */
+} h2_opts;             /* a NULL h2_opts* means all defaults */
+
+typedef struct {
+  int64_t n;                 /* number of points / matrix order                  */
+  int32_t levels;            /* L + 1 (root level 0 .. leaf level L)             */
+  int32_t leaf_size;         /* largest leaf cluster                             */
+  int32_t l_min;             /* coarsest level holding an admissible block       */
+  int32_t csp;               /* sparsity constant: most blocks of one cluster on
+                                one level                                         */
+  int64_t n_admissible;      /* R blocks, all levels                             */
+  int64_t n_dense;           /* F blocks (leaf level)                            */
+  int32_t max_rank_row[32];  /* largest row rank per level                       */
+  int32_t max_rank_col[32];
+  int64_t bytes_stored;      /* algorithmic size of the representation: F entries
+                                + coupling entries + leaf basis entries + transfer
+                                entries at the actual ranks, times 8 bytes        */
+  int64_t device_bytes;      /* device memory held by the handle                 */
+  int64_t cap_hits;          /* clusters whose rank was cut at rank_cap (product) */
+  double mmp_ms;             /* device time of the product that made this handle
+                                (0 for built handles)                             */
+} h2_stats;
+
+/* Build an H^2 approximation of the kernel matrix K(points_a, points_b) on the
+ * device.
+ *   points  host, n x 3 row-major (x, y, z per point), user order; copied.
+ *   kernel  host; see h2_kernel.
+ *   leaf_size  largest number of points of a leaf cluster (>= 1, <= 64).
+ *   eta     admissibility parameter of Eq. admCond (> 0).
+ *   eps     construction accuracy: a basis keeps the singular vectors of its
+ *           (sampled) far field with sigma / sigma_1 > eps.
+ * Structure (Sec. II): cardinality-balanced bisection cluster tree with all leaves
+ * on level L, block partition by Eq. admCond with bounding boxes.  The numeric
+ * construction is not specified by the paper (it cites another method); this build
+ * uses nested far-field sampling with interpolative skeletons (the design doc names the
+ * reading).  Errors: H2_EINVAL for bad sizes or non-finite points,
+ * H2_EUNSUPPORTED for a complex kernel. */
+h2_status h2_build(const double* points, int64_t n, const h2_kernel* kernel,
+                   int32_t leaf_size, double eta, double eps, const h2_opts* opts,
+                   h2_handle* out);
+
+/* Create a handle from host arrays that describe an H^2 matrix on the same tree
+ * and partition that h2_build(points, n, kernel, leaf_size, eta, ...) makes.  Used
+ * to feed matrices built elsewhere (e.g. by a reference implementation) to the
+ * product.  All arrays are host, float64, tree order, concatenated in this order:
+ *   kr, kc      int32 ranks per cluster, clusters ordered by level then index
+ *               (2^(L+1) - 1 entries each)
+ *   vr, vc      per leaf t (index order): |t| x kr_t (resp. kc_t), row-major
+ *   er, ec      per non-leaf (l, t), levels 0..L-1: (k_t1 + k_t2) x k_t, row-major
+ *   s           per admissible block, ordered by level then (t, s): kr_t x kc_s
+ *   f           per dense leaf block, ordered by (t, s): |t| x |s|
+ * Errors: H2_EINVAL if a rank is negative or larger than the cluster allows. */
+h2_status h2_import(const double* points, int64_t n, int32_t leaf_size, double eta,
+                    const int32_t* kr, const int32_t* kc, const double* vr,
+                    const double* vc, const double* er, const double* ec,
+                    const double* s, const double* f, const h2_opts* opts,
+                    h2_handle* out);
+
+/* The inverse of h2_import: copy the representation to host arrays in the same
+ * packed layout.  Pass NULL for the arrays to query sizes only: the element counts
+ * are written to sizes[0..5] = {ranks (each of kr, kc), vr, vc, er, ec, s, f}
+ * (sizes has 8 entries: nranks, nvr, nvc, ner, nec, ns, nf, 0). */
+h2_status h2_export(h2_handle h, int64_t* sizes, int32_t* kr, int32_t* kc, double* vr,
+                    double* vc, double* er, double* ec, double* s, double* f);
+
+/* C = A x B with change of cluster bases (Sec. III leaf level, Sec. IV non-leaf
+ * levels, top-down split of the couplings held by non-leaf blocks).  C keeps A's
+ * partition and gets new orthonormal nested bases truncated at eps (see h2_trunc).
+ * A and B must come from the same points, leaf size and eta (else H2_ESTRUCT).
+ * The product is enqueued on opts->stream; the call returns after it has been
+ * launched and synchronises only to finish its setup.  *C owns its memory. */
+h2_status h2_mmp(h2_handle A, h2_handle B, double eps, const h2_opts* opts,
+                 h2_handle* C);
+
+/* y = H x (exact H^2 arithmetic: forward transform, coupling, backward transform,
+ * near field).  x, y: device float64, column-major n x nrhs, user order; y is
+ * overwritten.  Enqueued on the stream of the handle's last call. */
+h2_status h2_matvec(h2_handle h, const double* x, double* y, int64_t nrhs);
+
+/* Dense n x n matrix, device float64, column-major, user order (testing; n <=
+ * 16384). */
+h2_status h2_to_dense(h2_handle h, double* out);
+
+/* Statistics; synchronises. */
+h2_status h2_info(h2_handle h, h2_stats* stats);
+
+/* Tree order of the points: perm[p] = user index of tree position p (host, n
+ * entries); and the blocks of one level, sorted by (t, s): kind 0 = admissible R,
+ * 1 = dense F, 2 = non-leaf NL.  Pass NULL arrays to query *count. */
+h2_status h2_tree_perm(h2_handle h, int64_t* perm);
+h2_status h2_level_blocks(h2_handle h, int32_t level, int32_t* t, int32_t* s,
+                          int8_t* kind, int64_t* count);
+
+void h2_destroy(h2_handle h);
+const char* h2_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

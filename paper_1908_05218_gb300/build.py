@@ -1,0 +1,77 @@
+"""Builds the in-tree shared library libh2gb300.so for sm_103a (nvcc + g++).
+
+Translation units compile in parallel; the result is written next to this file.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+OUT = os.path.join(HERE, "libh2gb300.so")
+OBJ = os.path.join(HERE, "_build")
+
+CU = ["kernels.cu", "capi.cu"]
+CPP = ["structure.cpp", "builder.cpp", "plan.cpp"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def _nvcc() -> str:
+    for c in (shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if c and os.path.exists(c):
+            return c
+    raise RuntimeError("nvcc not found")
+
+
+def _run(cmd):
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("build failed:\n" + " ".join(cmd) + "\n" + r.stdout + r.stderr)
+    return r.stdout + r.stderr
+
+
+def _stale(src: str, obj: str) -> bool:
+    if not os.path.exists(obj):
+        return True
+    t = os.path.getmtime(obj)
+    deps = [src, os.path.join(CSRC, "internal.hpp"), os.path.join(HERE, "..", "include", "h2.h")]
+    return any(os.path.getmtime(d) > t for d in deps)
+
+
+def build(verbose: bool = False, ptxas_info: bool = False) -> str:
+    nvcc = _nvcc()
+    os.makedirs(OBJ, exist_ok=True)
+    jobs = []
+    for f in CU:
+        src = os.path.join(CSRC, f)
+        obj = os.path.join(OBJ, f + ".o")
+        cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-c", src, "-o", obj]
+        if ptxas_info:
+            cmd.insert(1, "-Xptxas=-v")
+        jobs.append((src, obj, cmd))
+    for f in CPP:
+        src = os.path.join(CSRC, f)
+        obj = os.path.join(OBJ, f + ".o")
+        cmd = ["g++", "-O3", "-std=c++17", "-fPIC", "-fopenmp", "-c", src, "-o", obj]
+        jobs.append((src, obj, cmd))
+    todo = [j for j in jobs if _stale(j[0], j[1]) or ptxas_info]
+    logs = []
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+        for out in ex.map(lambda j: _run(j[2]), todo):
+            logs.append(out)
+    objs = [j[1] for j in jobs]
+    if todo or not os.path.exists(OUT):
+        tmp = OUT + ".tmp"
+        _run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fopenmp", "-lgomp"])
+        os.replace(tmp, OUT)
+    if verbose:
+        sys.stdout.write("".join(logs))
+    return OUT
+
+
+if __name__ == "__main__":
+    print(build(verbose=True, ptxas_info="--ptxas" in sys.argv))

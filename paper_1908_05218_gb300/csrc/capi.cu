@@ -1,0 +1,714 @@
+// C ABI of the H^2 library: handle lifetime, device memory, plan execution.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+
+#include "internal.hpp"
+
+struct h2_matrix {
+  h2::Mat m;
+  // product plans keyed by (B handle, B caps, trunc, cap); owned by A's handle
+  struct MmpEntry {
+    const h2_matrix* B = nullptr;
+    std::vector<int> Bkr, Bkc;
+    int trunc = 0, cap = 0;
+    h2::Plan plan;
+  };
+  std::vector<std::unique_ptr<MmpEntry>> mmp_plans;
+  std::map<int64_t, std::unique_ptr<h2::Plan>> mv_plans;  // by nrhs
+  std::map<int64_t, std::pair<int64_t, int64_t>> mv_offs;
+  int64_t* d_user = nullptr;  // padded tree row -> user index (-1: padding)
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool timed = false;
+  int origin_trunc = -1, origin_cap = -1;
+  const h2_matrix* origin_A = nullptr;
+  const h2_matrix* origin_B = nullptr;
+};
+
+namespace {
+thread_local std::string g_err;
+
+h2_status fail(h2_status c, const std::string& m) {
+  g_err = m;
+  return c;
+}
+
+template <class F>
+h2_status guarded(F&& f) {
+  try {
+    f();
+    return H2_OK;
+  } catch (const h2::Error& e) {
+    return fail(e.code, e.what());
+  } catch (const std::bad_alloc&) {
+    return fail(H2_ENOMEM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(H2_EINTERNAL, e.what());
+  }
+}
+
+void* dmalloc(size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 256;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw h2::Error(H2_ENOMEM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+  }
+  return p;
+}
+
+h2_opts defaults(const h2_opts* o) {
+  h2_opts d{};
+  d.precision = H2_FP64;
+  d.trunc = H2_TRUNC_PAPER;
+  d.rank_cap = 48;
+  d.stream = nullptr;
+  if (o) {
+    d = *o;
+    if (d.rank_cap <= 0) d.rank_cap = 48;
+  }
+  if (d.precision != H2_FP64 && d.precision != H2_MIXED_FP32) throw h2::Error(H2_EINVAL, "bad precision");
+  if (d.trunc < 0 || d.trunc > 2) throw h2::Error(H2_EINVAL, "bad truncation mode");
+  if (d.rank_cap > 64) throw h2::Error(H2_EINVAL, "rank_cap above 64");
+  return d;
+}
+
+int64_t round32(int64_t x) { return (x + 31) & ~int64_t(31); }
+
+void make_user_map(h2_matrix* h) {
+  const h2::Structure& st = *h->m.st;
+  int64_t nl = 1LL << st.L, rows = nl * st.LS;
+  std::vector<int64_t> user(rows, -1);
+  for (int64_t t = 0; t < nl; ++t)
+    for (int64_t r = 0; r < st.size[st.L][t]; ++r) user[t * st.LS + r] = st.perm[st.start[st.L][t] + r];
+  h->d_user = (int64_t*)dmalloc(rows * sizeof(int64_t));
+  h2::cuda_check(cudaMemcpy(h->d_user, user.data(), rows * sizeof(int64_t), cudaMemcpyHostToDevice), "upload user map");
+}
+
+}  // namespace
+
+namespace h2 {
+
+void cuda_check(int err, const char* what) {
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    throw Error(H2_ECUDA, std::string(what) + ": " + cudaGetErrorString((cudaError_t)err));
+  }
+}
+
+int64_t mat_elems(Mat& m) {
+  const Structure& st = *m.st;
+  const int L = st.L;
+  const int64_t nl = 1LL << L, LS = st.LS;
+  int64_t o = 0;
+  m.off_Vr = o;
+  o += round32(nl * LS * m.Kr[L]);
+  m.off_Vc = o;
+  o += round32(nl * LS * m.Kc[L]);
+  m.off_Er.assign(L, 0);
+  m.off_Ec.assign(L, 0);
+  for (int l = 0; l < L; ++l) {
+    m.off_Er[l] = o;
+    o += round32((1LL << l) * 2LL * m.Kr[l + 1] * m.Kr[l]);
+    m.off_Ec[l] = o;
+    o += round32((1LL << l) * 2LL * m.Kc[l + 1] * m.Kc[l]);
+  }
+  m.off_S.assign(L + 1, 0);
+  for (int l = 0; l <= L; ++l) {
+    m.off_S[l] = o;
+    o += round32(st.nR[l] * (int64_t)m.Kr[l] * m.Kc[l]);
+  }
+  m.off_F = o;
+  o += round32(st.nF * LS * LS);
+  m.arena_elems = o;
+  return o;
+}
+
+void alloc_mat(Mat& m) {
+  const Structure& st = *m.st;
+  int64_t o = mat_elems(m);
+  m.arena = (double*)dmalloc(o * sizeof(double));
+  cuda_check(cudaMemset(m.arena, 0, o * sizeof(double)), "zero arena");
+  const int nn = st.nnodes();
+  m.d_kr = (int32_t*)dmalloc(2 * nn * sizeof(int32_t) + 64);
+  m.d_kc = m.d_kr + nn;
+  cuda_check(cudaMemset(m.d_kr, 0, 2 * nn * sizeof(int32_t) + 64), "zero ranks");
+  m.d_cap = (unsigned long long*)((char*)m.d_kr + ((2 * nn * sizeof(int32_t) + 15) & ~size_t(15)));
+}
+
+void free_mat(Mat& m) {
+  if (m.arena) cudaFree(m.arena);
+  if (m.d_kr) cudaFree(m.d_kr);
+  for (void* p : m.extra_allocs) cudaFree(p);
+  m.arena = nullptr;
+  m.d_kr = m.d_kc = nullptr;
+  m.extra_allocs.clear();
+}
+
+void sync_ranks_to_host(Mat& m) {
+  if (m.ranks_on_host) return;
+  const int nn = m.st->nnodes();
+  m.h_kr.resize(nn);
+  m.h_kc.resize(nn);
+  cuda_check(cudaStreamSynchronize((cudaStream_t)m.stream), "synchronise");
+  cuda_check(cudaMemcpy(m.h_kr.data(), m.d_kr, nn * sizeof(int32_t), cudaMemcpyDeviceToHost), "ranks");
+  cuda_check(cudaMemcpy(m.h_kc.data(), m.d_kc, nn * sizeof(int32_t), cudaMemcpyDeviceToHost), "ranks");
+  m.ranks_on_host = true;
+}
+
+// packed host layout -> padded device arena (caps = largest rank per level)
+void unpack_to_device(const Packed& p, Mat& m) {
+  const Structure& st = *m.st;
+  const int L = st.L, LS = st.LS, nn = st.nnodes();
+  if ((int)p.kr.size() != nn || (int)p.kc.size() != nn) throw Error(H2_EINVAL, "rank arrays have the wrong length");
+  m.Kr.assign(L + 1, 0);
+  m.Kc.assign(L + 1, 0);
+  for (int l = 0; l <= L; ++l)
+    for (int64_t t = 0; t < (1LL << l); ++t) {
+      int kr = p.kr[Structure::node(l, t)], kc = p.kc[Structure::node(l, t)];
+      int64_t lim = st.size[l][t];
+      if (l < L) {
+        lim = std::min<int64_t>(lim, (int64_t)p.kr[Structure::node(l + 1, 2 * t)] + p.kr[Structure::node(l + 1, 2 * t + 1)]);
+      }
+      if (kr < 0 || kc < 0 || kr > st.size[l][t] || kc > st.size[l][t] || kr > 128 || kc > 128)
+        throw Error(H2_EINVAL, "rank out of range");
+      if (l < L) {
+        int64_t lr = (int64_t)p.kr[Structure::node(l + 1, 2 * t)] + p.kr[Structure::node(l + 1, 2 * t + 1)];
+        int64_t lc = (int64_t)p.kc[Structure::node(l + 1, 2 * t)] + p.kc[Structure::node(l + 1, 2 * t + 1)];
+        if (kr > lr || kc > lc) throw Error(H2_EINVAL, "rank above the sum of the children's ranks");
+      }
+      (void)lim;
+      m.Kr[l] = std::max(m.Kr[l], kr);
+      m.Kc[l] = std::max(m.Kc[l], kc);
+    }
+  alloc_mat(m);
+  std::vector<double> h(m.arena_elems, 0.0);
+  size_t pos = 0;
+  auto need = [&](const std::vector<double>& v, size_t cnt) {
+    if (pos + cnt > v.size()) throw Error(H2_EINVAL, "packed array too short");
+  };
+  const int64_t nl = 1LL << L;
+  for (int col = 0; col < 2; ++col) {
+    const auto& v = col ? p.vc : p.vr;
+    const auto& rk = col ? p.kc : p.kr;
+    int K = col ? m.Kc[L] : m.Kr[L];
+    pos = 0;
+    for (int64_t t = 0; t < nl; ++t) {
+      int k = rk[Structure::node(L, t)];
+      int64_t n = st.size[L][t];
+      need(v, n * k);
+      double* dst = &h[(col ? m.Vc(t) : m.Vr(t))];
+      for (int64_t r = 0; r < n; ++r)
+        for (int c = 0; c < k; ++c) dst[r * K + c] = v[pos + r * k + c];
+      pos += n * k;
+    }
+    if (pos != v.size()) throw Error(H2_EINVAL, "leaf basis array has the wrong length");
+  }
+  for (int col = 0; col < 2; ++col) {
+    const auto& v = col ? p.ec : p.er;
+    const auto& rk = col ? p.kc : p.kr;
+    const auto& K = col ? m.Kc : m.Kr;
+    pos = 0;
+    for (int l = 0; l < L; ++l)
+      for (int64_t t = 0; t < (1LL << l); ++t) {
+        int k = rk[Structure::node(l, t)], k1 = rk[Structure::node(l + 1, 2 * t)], k2 = rk[Structure::node(l + 1, 2 * t + 1)];
+        need(v, (int64_t)(k1 + k2) * k);
+        double* dst = &h[col ? m.Ec(l, t) : m.Er(l, t)];
+        for (int r = 0; r < k1 + k2; ++r) {
+          int pr = r < k1 ? r : K[l + 1] + (r - k1);
+          for (int c = 0; c < k; ++c) dst[(int64_t)pr * K[l] + c] = v[pos + (int64_t)r * k + c];
+        }
+        pos += (int64_t)(k1 + k2) * k;
+      }
+    if (pos != v.size()) throw Error(H2_EINVAL, "transfer array has the wrong length");
+  }
+  pos = 0;
+  for (int l = 0; l <= L; ++l)
+    for (auto& b : st.blocks[l]) {
+      if (b.kind != KR) continue;
+      int kt = p.kr[Structure::node(l, b.t)], ks = p.kc[Structure::node(l, b.s)];
+      need(p.s, (int64_t)kt * ks);
+      double* dst = &h[m.S(l, b.idx)];
+      for (int r = 0; r < kt; ++r)
+        for (int c = 0; c < ks; ++c) dst[(int64_t)r * m.Kc[l] + c] = p.s[pos + (int64_t)r * ks + c];
+      pos += (int64_t)kt * ks;
+    }
+  if (pos != p.s.size()) throw Error(H2_EINVAL, "coupling array has the wrong length");
+  pos = 0;
+  for (auto& b : st.blocks[L]) {
+    if (b.kind != KF) continue;
+    int64_t nt = st.size[L][b.t], ns = st.size[L][b.s];
+    need(p.f, nt * ns);
+    double* dst = &h[m.F(b.idx)];
+    for (int64_t r = 0; r < nt; ++r)
+      for (int64_t c = 0; c < ns; ++c) dst[r * LS + c] = p.f[pos + r * ns + c];
+    pos += nt * ns;
+  }
+  if (pos != p.f.size()) throw Error(H2_EINVAL, "dense array has the wrong length");
+  cuda_check(cudaMemcpy(m.arena, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice), "upload arena");
+  cuda_check(cudaMemcpy(m.d_kr, p.kr.data(), nn * sizeof(int32_t), cudaMemcpyHostToDevice), "upload ranks");
+  cuda_check(cudaMemcpy(m.d_kc, p.kc.data(), nn * sizeof(int32_t), cudaMemcpyHostToDevice), "upload ranks");
+  m.h_kr = p.kr;
+  m.h_kc = p.kc;
+  m.ranks_on_host = true;
+}
+
+void pack_from_device(Mat& m, Packed& p) {
+  sync_ranks_to_host(m);
+  const Structure& st = *m.st;
+  const int L = st.L, LS = st.LS;
+  std::vector<double> h(m.arena_elems);
+  cuda_check(cudaMemcpy(h.data(), m.arena, h.size() * sizeof(double), cudaMemcpyDeviceToHost), "download arena");
+  p.kr = m.h_kr;
+  p.kc = m.h_kc;
+  p.vr.clear();
+  p.vc.clear();
+  p.er.clear();
+  p.ec.clear();
+  p.s.clear();
+  p.f.clear();
+  for (int col = 0; col < 2; ++col) {
+    auto& v = col ? p.vc : p.vr;
+    const auto& rk = col ? p.kc : p.kr;
+    int K = col ? m.Kc[L] : m.Kr[L];
+    for (int64_t t = 0; t < (1LL << L); ++t) {
+      int k = rk[Structure::node(L, t)];
+      const double* src = &h[col ? m.Vc(t) : m.Vr(t)];
+      for (int64_t r = 0; r < st.size[L][t]; ++r)
+        for (int c = 0; c < k; ++c) v.push_back(src[r * K + c]);
+    }
+  }
+  for (int col = 0; col < 2; ++col) {
+    auto& v = col ? p.ec : p.er;
+    const auto& rk = col ? p.kc : p.kr;
+    const auto& K = col ? m.Kc : m.Kr;
+    for (int l = 0; l < L; ++l)
+      for (int64_t t = 0; t < (1LL << l); ++t) {
+        int k = rk[Structure::node(l, t)], k1 = rk[Structure::node(l + 1, 2 * t)], k2 = rk[Structure::node(l + 1, 2 * t + 1)];
+        const double* src = &h[col ? m.Ec(l, t) : m.Er(l, t)];
+        for (int r = 0; r < k1 + k2; ++r) {
+          int pr = r < k1 ? r : K[l + 1] + (r - k1);
+          for (int c = 0; c < k; ++c) v.push_back(src[(int64_t)pr * K[l] + c]);
+        }
+      }
+  }
+  for (int l = 0; l <= L; ++l)
+    for (auto& b : st.blocks[l]) {
+      if (b.kind != KR) continue;
+      int kt = p.kr[Structure::node(l, b.t)], ks = p.kc[Structure::node(l, b.s)];
+      const double* src = &h[m.S(l, b.idx)];
+      for (int r = 0; r < kt; ++r)
+        for (int c = 0; c < ks; ++c) p.s.push_back(src[(int64_t)r * m.Kc[l] + c]);
+    }
+  for (auto& b : st.blocks[L]) {
+    if (b.kind != KF) continue;
+    const double* src = &h[m.F(b.idx)];
+    for (int64_t r = 0; r < st.size[L][b.t]; ++r)
+      for (int64_t c = 0; c < st.size[L][b.s]; ++c) p.f.push_back(src[r * LS + c]);
+  }
+}
+
+// Host-side check that every access of a plan stays inside its arena: run before a
+// plan's first upload so that an indexing error is reported instead of executed.
+void validate_plan(const Plan& P, const int64_t sizes[4]) {
+  auto check = [&](int64_t tagged, int64_t extent, const char* what) {
+    if (extent <= 0) return;
+    int64_t a = (int64_t)((uint64_t)tagged >> 62), off = tagged & ((int64_t(1) << 62) - 1);
+    if (tagged < 0 || off + extent > sizes[a])
+      throw Error(H2_EINTERNAL, std::string("plan access out of bounds: ") + what);
+  };
+  for (const Seg& s : P.segs) {
+    bool ta = s.flags & SF_TA, tb = s.flags & SF_TB;
+    check(s.out, (int64_t)(s.m - 1) * s.ldc + s.n, "segment output");
+    if (s.ldc < s.n) throw Error(H2_EINTERNAL, "segment ldc < n");
+    for (int32_t q = s.first; q < s.first + s.count; ++q) {
+      const Item& it = P.items[q];
+      if (s.flags & SF_SUM) {
+        if (s.lda < s.n) throw Error(H2_EINTERNAL, "sum lda < n");
+        check(it.a, (int64_t)(s.m - 1) * s.lda + s.n, "sum input");
+        continue;
+      }
+      if ((!ta && s.lda < s.k) || (ta && s.lda < s.m) || (!tb && s.ldb < s.n) || (tb && s.ldb < s.k))
+        throw Error(H2_EINTERNAL, "segment leading dimension too small");
+      check(it.a, ta ? (int64_t)(s.k - 1) * s.lda + s.m : (int64_t)(s.m - 1) * s.lda + s.k, "segment A");
+      check(it.b, tb ? (int64_t)(s.n - 1) * s.ldb + s.k : (int64_t)(s.k - 1) * s.ldb + s.n, "segment B");
+    }
+  }
+  for (const EigTask& e : P.eigs) {
+    for (int m = 0; m < 3; ++m)
+      if (e.g[m] >= 0) check(e.g[m], (int64_t)e.n_pad * e.n_pad, "eig Gram");
+    check(e.out, (int64_t)e.n_pad * e.kcap, "eig output");
+    if (e.child1 < 0 && e.nleaf > e.n_pad) throw Error(H2_EINTERNAL, "eig leaf size above n_pad");
+    if (e.child1 >= 0 && 2 * e.half > e.n_pad) throw Error(H2_EINTERNAL, "eig half above n_pad");
+  }
+  for (const Launch& L : P.launches)
+    if (L.kind == Launch::MEMSET) check(L.off, L.elems, "memset");
+}
+
+void upload_plan(Plan& P) {
+  P.d_segs = (Seg*)dmalloc(std::max<size_t>(1, P.segs.size()) * sizeof(Seg));
+  P.d_items = (Item*)dmalloc(std::max<size_t>(1, P.items.size()) * sizeof(Item));
+  P.d_eigs = (EigTask*)dmalloc(std::max<size_t>(1, P.eigs.size()) * sizeof(EigTask));
+  if (!P.segs.empty()) cuda_check(cudaMemcpy(P.d_segs, P.segs.data(), P.segs.size() * sizeof(Seg), cudaMemcpyHostToDevice), "upload segs");
+  if (!P.items.empty()) cuda_check(cudaMemcpy(P.d_items, P.items.data(), P.items.size() * sizeof(Item), cudaMemcpyHostToDevice), "upload items");
+  if (!P.eigs.empty()) cuda_check(cudaMemcpy(P.d_eigs, P.eigs.data(), P.eigs.size() * sizeof(EigTask), cudaMemcpyHostToDevice), "upload eigs");
+  int64_t scratch = 0;
+  for (auto& L : P.launches) {
+    if (L.kind == Launch::GEMM) {
+      int mx = 1;
+      for (int64_t q = L.first; q < L.first + L.count; ++q) mx = std::max<int>(mx, P.segs[q].n);
+      L.aux = mx;
+    } else if (L.kind == Launch::EIG) {
+      int mx = 1;
+      for (int64_t q = L.first; q < L.first + L.count; ++q) mx = std::max<int>(mx, P.eigs[q].n_pad);
+      if (mx > 256) throw Error(H2_EUNSUPPORTED, "Gram matrix larger than 256 (raise no caps in full mode)");
+      L.aux = mx;
+      int nn = mx + (mx & 1);
+      if (nn > 112) scratch = std::max<int64_t>(scratch, L.count * 2LL * nn * nn);
+    }
+  }
+  P.d_scratch = (double*)dmalloc(std::max<int64_t>(1, scratch) * sizeof(double));
+  P.d_w = (double*)dmalloc(std::max<int64_t>(1, P.w_elems) * sizeof(double));
+}
+
+void free_plan(Plan& P) {
+  for (void* q : {(void*)P.d_segs, (void*)P.d_items, (void*)P.d_eigs, (void*)P.d_w, (void*)P.d_scratch})
+    if (q) cudaFree(q);
+  P.d_segs = nullptr;
+  P.d_items = nullptr;
+  P.d_eigs = nullptr;
+  P.d_w = nullptr;
+  P.d_scratch = nullptr;
+}
+
+void run_plan(const Plan& P, double* const arenas[4], int32_t* kr, int32_t* kc, unsigned long long* cap_hits,
+              const MmpParams& prm, void* stream, bool skip_memset) {
+  for (auto& L : P.launches) {
+    if (L.kind == Launch::MEMSET) {
+      if (skip_memset || L.elems == 0) continue;
+      double* p = arenas[(uint64_t)L.off >> 62] + (L.off & ((int64_t(1) << 62) - 1));
+      cuda_check(cudaMemsetAsync(p, 0, L.elems * sizeof(double), (cudaStream_t)stream), "memset");
+    } else if (L.kind == Launch::GEMM) {
+      launch_gemm(P.d_segs, P.d_items, L.first, L.count, arenas, L.aux, stream);
+    } else {
+      launch_eig(P.d_eigs, L.first, L.count, arenas, kr, kc, prm.eps, prm.trunc, cap_hits, L.aux, P.d_scratch,
+                 stream);
+    }
+    cuda_check(cudaGetLastError(), L.phase);
+  }
+}
+
+}  // namespace h2
+
+using namespace h2;
+
+extern "C" {
+
+const char* h2_last_error(void) { return g_err.c_str(); }
+
+static void finish_handle(h2_matrix* h, const h2_opts& o) {
+  h->m.stream = o.stream;
+  make_user_map(h);
+}
+
+h2_status h2_build(const double* points, int64_t n, const h2_kernel* kernel, int32_t leaf_size, double eta,
+                   double eps, const h2_opts* opts, h2_handle* out) {
+  if (!points || !kernel || !out) return fail(H2_EINVAL, "null argument");
+  *out = nullptr;
+  return guarded([&] {
+    h2_opts o = defaults(opts);
+    if (!(eps > 0) || !(eps < 1)) throw Error(H2_EINVAL, "eps must lie in (0, 1)");
+    if (kernel->kind == H2_K_HELMHOLTZ) throw Error(H2_EUNSUPPORTED, "complex kernels are not supported on the GPU path");
+    if (kernel->kind != H2_K_LAPLACE && kernel->kind != H2_K_INV_R2) throw Error(H2_EINVAL, "unknown kernel kind");
+    auto h = std::make_unique<h2_matrix>();
+    h->m.st = build_structure(points, n, leaf_size, eta);
+    Packed p;
+    build_h2_host(*h->m.st, *kernel, eps, p);
+    unpack_to_device(p, h->m);
+    finish_handle(h.get(), o);
+    *out = h.release();
+  });
+}
+
+h2_status h2_import(const double* points, int64_t n, int32_t leaf_size, double eta, const int32_t* kr,
+                    const int32_t* kc, const double* vr, const double* vc, const double* er, const double* ec,
+                    const double* s, const double* f, const h2_opts* opts, h2_handle* out) {
+  if (!points || !kr || !kc || !out) return fail(H2_EINVAL, "null argument");
+  *out = nullptr;
+  return guarded([&] {
+    h2_opts o = defaults(opts);
+    auto h = std::make_unique<h2_matrix>();
+    h->m.st = build_structure(points, n, leaf_size, eta);
+    const Structure& st = *h->m.st;
+    const int nn = st.nnodes(), L = st.L;
+    Packed p;
+    p.kr.assign(kr, kr + nn);
+    p.kc.assign(kc, kc + nn);
+    int64_t nvr = 0, nvc = 0, ner = 0, nec = 0, ns = 0, nf = 0;
+    for (int64_t t = 0; t < (1LL << L); ++t) {
+      nvr += st.size[L][t] * kr[Structure::node(L, t)];
+      nvc += st.size[L][t] * kc[Structure::node(L, t)];
+    }
+    for (int l = 0; l < L; ++l)
+      for (int64_t t = 0; t < (1LL << l); ++t) {
+        ner += (int64_t)(kr[Structure::node(l + 1, 2 * t)] + kr[Structure::node(l + 1, 2 * t + 1)]) * kr[Structure::node(l, t)];
+        nec += (int64_t)(kc[Structure::node(l + 1, 2 * t)] + kc[Structure::node(l + 1, 2 * t + 1)]) * kc[Structure::node(l, t)];
+      }
+    for (int l = 0; l <= L; ++l)
+      for (auto& b : st.blocks[l]) {
+        if (b.kind == KR) ns += (int64_t)kr[Structure::node(l, b.t)] * kc[Structure::node(l, b.s)];
+        if (b.kind == KF) nf += st.size[L][b.t] * st.size[L][b.s];
+      }
+    if ((nvr && !vr) || (nvc && !vc) || (ner && !er) || (nec && !ec) || (ns && !s) || (nf && !f))
+      throw Error(H2_EINVAL, "null array");
+    p.vr.assign(vr, vr + nvr);
+    p.vc.assign(vc, vc + nvc);
+    p.er.assign(er, er + ner);
+    p.ec.assign(ec, ec + nec);
+    p.s.assign(s, s + ns);
+    p.f.assign(f, f + nf);
+    unpack_to_device(p, h->m);
+    finish_handle(h.get(), o);
+    *out = h.release();
+  });
+}
+
+h2_status h2_export(h2_handle h, int64_t* sizes, int32_t* kr, int32_t* kc, double* vr, double* vc, double* er,
+                    double* ec, double* s, double* f) {
+  if (!h || !sizes) return fail(H2_EINVAL, "null argument");
+  return guarded([&] {
+    Packed p;
+    pack_from_device(h->m, p);
+    sizes[0] = (int64_t)p.kr.size();
+    sizes[1] = (int64_t)p.vr.size();
+    sizes[2] = (int64_t)p.vc.size();
+    sizes[3] = (int64_t)p.er.size();
+    sizes[4] = (int64_t)p.ec.size();
+    sizes[5] = (int64_t)p.s.size();
+    sizes[6] = (int64_t)p.f.size();
+    sizes[7] = 0;
+    if (kr) std::copy(p.kr.begin(), p.kr.end(), kr);
+    if (kc) std::copy(p.kc.begin(), p.kc.end(), kc);
+    if (vr) std::copy(p.vr.begin(), p.vr.end(), vr);
+    if (vc) std::copy(p.vc.begin(), p.vc.end(), vc);
+    if (er) std::copy(p.er.begin(), p.er.end(), er);
+    if (ec) std::copy(p.ec.begin(), p.ec.end(), ec);
+    if (s) std::copy(p.s.begin(), p.s.end(), s);
+    if (f) std::copy(p.f.begin(), p.f.end(), f);
+  });
+}
+
+h2_status h2_mmp(h2_handle A, h2_handle B, double eps, const h2_opts* opts, h2_handle* C) {
+  if (!A || !B || !C) return fail(H2_EINVAL, "null argument");
+  return guarded([&] {
+    h2_opts o = defaults(opts);
+    if (o.trunc != H2_TRUNC_FULL && !(eps > 0 && eps < 1)) throw Error(H2_EINVAL, "eps must lie in (0, 1)");
+    if (o.precision != H2_FP64) throw Error(H2_EUNSUPPORTED, "precision mode not built yet");
+    if (!same_structure(*A->m.st, *B->m.st)) throw Error(H2_ESTRUCT, "A and B have different trees or partitions");
+    MmpParams prm{eps, o.trunc, o.rank_cap, o.precision};
+    // plan cache on A
+    h2_matrix::MmpEntry* ent = nullptr;
+    for (auto& e : A->mmp_plans)
+      if (e->B == B && e->Bkr == B->m.Kr && e->Bkc == B->m.Kc && e->trunc == o.trunc && e->cap == o.rank_cap)
+        ent = e.get();
+    Mat Ccaps;
+    Ccaps.st = A->m.st;
+    if (!ent) {
+      auto e = std::make_unique<h2_matrix::MmpEntry>();
+      e->B = B;
+      e->Bkr = B->m.Kr;
+      e->Bkc = B->m.Kc;
+      e->trunc = o.trunc;
+      e->cap = o.rank_cap;
+      build_mmp_plan(A->m, B->m, Ccaps, prm, e->plan);
+      e->plan.ckr = Ccaps.Kr;
+      e->plan.ckc = Ccaps.Kc;
+      {
+        Mat probe;
+        probe.st = A->m.st;
+        probe.Kr = Ccaps.Kr;
+        probe.Kc = Ccaps.Kc;
+        int64_t csize = mat_elems(probe);
+        int64_t sizes[4] = {A->m.arena_elems, B->m.arena_elems, csize, e->plan.w_elems};
+        validate_plan(e->plan, sizes);
+      }
+      upload_plan(e->plan);
+      ent = e.get();
+      A->mmp_plans.push_back(std::move(e));
+    }
+    h2_matrix* out = *C;
+    bool reuse = out && out->origin_A == A && out->origin_B == B && out->origin_trunc == o.trunc &&
+                 out->origin_cap == o.rank_cap && out->m.Kr == ent->plan.ckr && out->m.Kc == ent->plan.ckc;
+    std::unique_ptr<h2_matrix> fresh;
+    if (!reuse) {
+      fresh = std::make_unique<h2_matrix>();
+      fresh->m.st = A->m.st;
+      fresh->m.Kr = ent->plan.ckr;
+      fresh->m.Kc = ent->plan.ckc;
+      alloc_mat(fresh->m);
+      fresh->m.stream = o.stream;
+      make_user_map(fresh.get());
+      cudaEventCreate(&fresh->ev0);
+      cudaEventCreate(&fresh->ev1);
+      fresh->origin_A = A;
+      fresh->origin_B = B;
+      fresh->origin_trunc = o.trunc;
+      fresh->origin_cap = o.rank_cap;
+      out = fresh.get();
+    }
+    out->m.stream = o.stream;
+    out->m.ranks_on_host = false;
+    cudaStream_t s = (cudaStream_t)o.stream;
+    cuda_check(cudaEventRecord(out->ev0, s), "event");
+    cuda_check(cudaMemsetAsync(out->m.arena, 0, out->m.arena_elems * sizeof(double), s), "zero C");
+    cuda_check(cudaMemsetAsync(out->m.d_kr, 0, 2 * A->m.st->nnodes() * sizeof(int32_t) + 64, s), "zero ranks");
+    double* arenas[4] = {A->m.arena, B->m.arena, out->m.arena, ent->plan.d_w};
+    run_plan(ent->plan, arenas, out->m.d_kr, out->m.d_kc, out->m.d_cap, prm, o.stream, false);
+    cuda_check(cudaEventRecord(out->ev1, s), "event");
+    out->timed = true;
+    if (fresh) *C = fresh.release();
+  });
+}
+
+h2_status h2_matvec(h2_handle h, const double* x, double* y, int64_t nrhs) {
+  if (!h || !x || !y) return fail(H2_EINVAL, "null argument");
+  if (nrhs < 1 || nrhs > 16384) return fail(H2_EINVAL, "nrhs must lie in [1, 16384]");
+  return guarded([&] {
+    auto it = h->mv_plans.find(nrhs);
+    if (it == h->mv_plans.end()) {
+      auto p = std::make_unique<Plan>();
+      int64_t ox, oy;
+      build_matvec_plan(h->m, nrhs, *p, ox, oy);
+      int64_t sizes[4] = {h->m.arena_elems, 0, 0, p->w_elems};
+      validate_plan(*p, sizes);
+      upload_plan(*p);
+      h->mv_offs[nrhs] = {ox, oy};
+      it = h->mv_plans.emplace(nrhs, std::move(p)).first;
+    }
+    Plan& P = *it->second;
+    auto offs = h->mv_offs[nrhs];
+    const Structure& st = *h->m.st;
+    int64_t rows = (1LL << st.L) * st.LS;
+    cudaStream_t s = (cudaStream_t)h->m.stream;
+    cuda_check(cudaMemsetAsync(P.d_w, 0, P.w_elems * sizeof(double), s), "zero workspace");
+    double* xt = P.d_w + (offs.first & ((int64_t(1) << 62) - 1));
+    double* yt = P.d_w + (offs.second & ((int64_t(1) << 62) - 1));
+    launch_permute(x, xt, h->d_user, rows, st.n, nrhs, true, s);
+    double* arenas[4] = {h->m.arena, nullptr, nullptr, P.d_w};
+    MmpParams prm{0, 0, 0, 0};
+    run_plan(P, arenas, nullptr, nullptr, nullptr, prm, s, true);
+    launch_permute(yt, y, h->d_user, rows, st.n, nrhs, false, s);
+    cuda_check(cudaGetLastError(), "matvec");
+  });
+}
+
+h2_status h2_to_dense(h2_handle h, double* out) {
+  if (!h || !out) return fail(H2_EINVAL, "null argument");
+  int64_t n = h->m.st->n;
+  if (n > 16384) return fail(H2_EINVAL, "to_dense is for n <= 16384");
+  return guarded([&] {
+    double* eye = (double*)dmalloc(n * n * sizeof(double));
+    cudaStream_t s = (cudaStream_t)h->m.stream;
+    launch_identity(eye, n, s);
+    cuda_check(cudaGetLastError(), "identity");
+    h2_status st = h2_matvec(h, eye, out, n);
+    cudaStreamSynchronize(s);
+    cudaFree(eye);
+    if (st != H2_OK) throw Error(st, g_err);
+  });
+}
+
+h2_status h2_info(h2_handle h, h2_stats* s) {
+  if (!h || !s) return fail(H2_EINVAL, "null argument");
+  return guarded([&] {
+    Mat& m = h->m;
+    sync_ranks_to_host(m);
+    const Structure& st = *m.st;
+    std::memset(s, 0, sizeof(*s));
+    s->n = st.n;
+    s->levels = st.L + 1;
+    s->leaf_size = st.LS;
+    s->l_min = st.lmin;
+    s->csp = st.csp;
+    for (int l = 0; l <= st.L; ++l) s->n_admissible += st.nR[l];
+    s->n_dense = st.nF;
+    int64_t bytes = 0;
+    for (int l = 0; l <= st.L && l < 32; ++l) {
+      int mr = 0, mc = 0;
+      for (int64_t t = 0; t < (1LL << l); ++t) {
+        mr = std::max(mr, m.h_kr[Structure::node(l, t)]);
+        mc = std::max(mc, m.h_kc[Structure::node(l, t)]);
+      }
+      s->max_rank_row[l] = mr;
+      s->max_rank_col[l] = mc;
+    }
+    for (int l = 0; l <= st.L; ++l)
+      for (auto& b : st.blocks[l]) {
+        if (b.kind == KR) bytes += (int64_t)m.h_kr[Structure::node(l, b.t)] * m.h_kc[Structure::node(l, b.s)];
+        if (b.kind == KF) bytes += st.size[st.L][b.t] * st.size[st.L][b.s];
+      }
+    for (int64_t t = 0; t < (1LL << st.L); ++t)
+      bytes += st.size[st.L][t] * (int64_t)(m.h_kr[Structure::node(st.L, t)] + m.h_kc[Structure::node(st.L, t)]);
+    for (int l = 0; l < st.L; ++l)
+      for (int64_t t = 0; t < (1LL << l); ++t) {
+        bytes += (int64_t)(m.h_kr[Structure::node(l + 1, 2 * t)] + m.h_kr[Structure::node(l + 1, 2 * t + 1)]) *
+                 m.h_kr[Structure::node(l, t)];
+        bytes += (int64_t)(m.h_kc[Structure::node(l + 1, 2 * t)] + m.h_kc[Structure::node(l + 1, 2 * t + 1)]) *
+                 m.h_kc[Structure::node(l, t)];
+      }
+    s->bytes_stored = bytes * 8;
+    s->device_bytes = m.arena_elems * 8;
+    if (m.d_cap) {
+      unsigned long long c = 0;
+      cuda_check(cudaMemcpy(&c, m.d_cap, sizeof(c), cudaMemcpyDeviceToHost), "counter");
+      s->cap_hits = (int64_t)c;
+    }
+    if (h->timed) {
+      float ms = 0;
+      cuda_check(cudaEventSynchronize(h->ev1), "event");
+      cuda_check(cudaEventElapsedTime(&ms, h->ev0, h->ev1), "event");
+      s->mmp_ms = ms;
+    }
+  });
+}
+
+h2_status h2_tree_perm(h2_handle h, int64_t* perm) {
+  if (!h || !perm) return fail(H2_EINVAL, "null argument");
+  std::copy(h->m.st->perm.begin(), h->m.st->perm.end(), perm);
+  return H2_OK;
+}
+
+h2_status h2_level_blocks(h2_handle h, int32_t level, int32_t* t, int32_t* s, int8_t* kind, int64_t* count) {
+  if (!h || !count) return fail(H2_EINVAL, "null argument");
+  const Structure& st = *h->m.st;
+  if (level < 0 || level > st.L) return fail(H2_EINVAL, "level out of range");
+  const auto& bl = st.blocks[level];
+  *count = (int64_t)bl.size();
+  if (t && s && kind)
+    for (size_t p = 0; p < bl.size(); ++p) {
+      t[p] = bl[p].t;
+      s[p] = bl[p].s;
+      kind[p] = bl[p].kind;
+    }
+  return H2_OK;
+}
+
+void h2_destroy(h2_handle h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  for (auto& e : h->mmp_plans) free_plan(e->plan);
+  for (auto& kv : h->mv_plans) free_plan(*kv.second);
+  if (h->d_user) cudaFree(h->d_user);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  free_mat(h->m);
+  delete h;
+}
+
+}  // extern "C"

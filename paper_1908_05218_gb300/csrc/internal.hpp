@@ -1,0 +1,186 @@
+// Internal declarations of the H^2 library (host side).
+#pragma once
+#include <array>
+#include <cstdint>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/h2.h"
+
+namespace h2 {
+
+// Error carried to the C ABI boundary.
+struct Error : std::runtime_error {
+  h2_status code;
+  Error(h2_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+enum BlockKind : int8_t { KR = 0, KF = 1, KNL = 2 };
+
+struct Block {
+  int32_t t, s;
+  int8_t kind;
+  int64_t idx;  // index among R blocks of its level, or among F blocks
+};
+
+// Cluster tree and block partition (Sec. II): complete binary tree, root level 0,
+// leaves at level L, cluster t of level l has children 2t, 2t+1.
+struct Structure {
+  int64_t n = 0;
+  int leaf_size = 0;
+  double eta = 0;
+  int L = 0;
+  int LS = 0;  // largest leaf cluster (padded row count of leaf blocks)
+  std::vector<double> pts;  // tree order, n x 3
+  std::vector<int64_t> perm;  // tree position -> user index
+  std::vector<std::vector<int64_t>> start, size;  // per level, per cluster
+  std::vector<std::vector<std::array<double, 3>>> lo, hi;
+  std::vector<std::vector<Block>> blocks;  // per level, sorted by (t, s)
+  std::vector<std::unordered_map<int64_t, int32_t>> where;  // (t<<32|s) -> position
+  std::vector<std::vector<int32_t>> row_ptr;  // CSR over blocks[l] by row cluster
+  std::vector<std::vector<int32_t>> col_ptr, col_list;  // CSC: positions by column
+  std::vector<int64_t> nR;  // admissible blocks per level
+  int64_t nF = 0;
+  int lmin = 0;
+  int csp = 0;
+
+  static int64_t key(int64_t t, int64_t s) { return (t << 32) | s; }
+  int32_t find(int l, int64_t t, int64_t s) const {
+    auto it = where[l].find(key(t, s));
+    return it == where[l].end() ? -1 : it->second;
+  }
+  static int node(int l, int64_t t) { return (int)((1LL << l) - 1 + t); }
+  int nnodes() const { return (int)((1LL << (L + 1)) - 1); }
+};
+
+std::shared_ptr<Structure> build_structure(const double* user_pts, int64_t n, int leaf_size,
+                                           double eta);
+bool same_structure(const Structure& a, const Structure& b);
+
+// Numeric H^2 matrix on the device.  All matrices row-major, padded: a leaf basis
+// is LS x K[L]; the stacked transfer of a level-l cluster is 2K[l+1] x K[l] (child 1
+// in rows [0, K[l+1]), child 2 in rows [K[l+1], 2K[l+1])); couplings K_r[l] x K_c[l];
+// dense blocks LS x LS.  Every padded entry is exactly zero.
+struct Mat {
+  std::shared_ptr<Structure> st;
+  std::vector<int> Kr, Kc;  // caps (padded dims) per level
+  double* arena = nullptr;  // device
+  int64_t arena_elems = 0;
+  int64_t off_Vr = 0, off_Vc = 0, off_F = 0;
+  std::vector<int64_t> off_Er, off_Ec, off_S;
+  int32_t* d_kr = nullptr;  // device ranks, indexed by Structure::node
+  int32_t* d_kc = nullptr;
+  std::vector<int32_t> h_kr, h_kc;  // host copies
+  bool ranks_on_host = false;
+  unsigned long long* d_cap = nullptr;  // device counter of ranks cut at the cap
+  void* stream = nullptr;
+  std::vector<void*> extra_allocs;  // device buffers owned by the handle
+
+  int64_t Vr(int64_t t) const { return off_Vr + t * st->LS * Kr[st->L]; }
+  int64_t Vc(int64_t t) const { return off_Vc + t * st->LS * Kc[st->L]; }
+  int64_t Er(int l, int64_t t) const { return off_Er[l] + t * 2LL * Kr[l + 1] * Kr[l]; }
+  int64_t Ec(int l, int64_t t) const { return off_Ec[l] + t * 2LL * Kc[l + 1] * Kc[l]; }
+  int64_t S(int l, int64_t r) const { return off_S[l] + r * (int64_t)Kr[l] * Kc[l]; }
+  int64_t F(int64_t f) const { return off_F + f * (int64_t)st->LS * st->LS; }
+};
+
+int64_t mat_elems(Mat& m);  // computes the offsets from the caps; returns the arena size
+void alloc_mat(Mat& m);  // computes offsets from caps, allocates + zeroes arena and ranks
+void free_mat(Mat& m);
+void sync_ranks_to_host(Mat& m);
+
+// ---------------------------------------------------------------- device program
+// Offsets into one of four arenas: the tag in bits 62-63 selects it.
+enum Arena : int64_t { AR_A = 0, AR_B = 1, AR_C = 2, AR_W = 3 };
+inline int64_t tag(Arena a, int64_t off) { return (a << 62) | off; }
+
+// Segmented batched GEMM: out[m x n] (=|+=) sum_items op(A) op(B), one CTA per segment.
+enum SegFlags : uint8_t { SF_TA = 1, SF_TB = 2, SF_ACC = 4, SF_SUM = 8 };
+struct Seg {
+  int64_t out;
+  int32_t first, count;
+  int16_t m, n, k, lda, ldb, ldc;
+  uint8_t flags;
+  uint8_t pad[7];
+};
+struct Item {
+  int64_t a, b;
+};
+
+// Normalised Gram sum + eigen-decomposition + truncation for one cluster.
+struct EigTask {
+  int64_t g[3];      // tagged offsets of the three Gram matrices (-1: absent)
+  int64_t out;       // tagged offset of the new basis / stacked transfer (n_pad x kcap)
+  int32_t rank_out;  // node id whose rank is written
+  int32_t child1, child2;  // node ids of the children (ranks in the same rank array), -1: leaf
+  int32_t nleaf;     // leaf: cluster size; active rows [0, nleaf)
+  int16_t n_pad, half, kcap, col;  // Gram dim, child offset, max rank, 1 = column basis
+};
+
+struct Launch {
+  enum Kind { GEMM, EIG, MEMSET } kind;
+  int64_t first = 0, count = 0;  // range in segs / eigs
+  int64_t off = 0, elems = 0;    // MEMSET: tagged offset and size
+  int level = -1;
+  int aux = 0;                   // GEMM: largest n; EIG: largest Gram dim
+  const char* phase = "";
+};
+
+struct Plan {
+  std::vector<Seg> segs;
+  std::vector<Item> items;
+  std::vector<EigTask> eigs;
+  std::vector<Launch> launches;
+  int64_t w_elems = 0;  // workspace size
+  // device copies
+  Seg* d_segs = nullptr;
+  Item* d_items = nullptr;
+  EigTask* d_eigs = nullptr;
+  double* d_w = nullptr;
+  double* d_scratch = nullptr;  // eigen work space for Gram matrices above 112
+  int64_t flops = 0;     // counted 2mnk over GEMM segments (padded dims)
+  std::vector<int> ckr, ckc;  // caps of the product
+};
+
+struct MmpParams {
+  double eps;
+  int trunc;
+  int rank_cap;
+  int precision;
+};
+
+// Builds the plan of C = A B; sets C's caps (C must share A's structure).
+void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& p, Plan& plan);
+void build_matvec_plan(const Mat& H, int64_t nrhs, Plan& plan, int64_t& off_x, int64_t& off_y);
+void validate_plan(const Plan& plan, const int64_t sizes[4]);
+void upload_plan(Plan& plan);
+void free_plan(Plan& plan);
+
+// Runs a plan: arenas[4] device base pointers.
+void run_plan(const Plan& plan, double* const arenas[4], int32_t* kr_out, int32_t* kc_out,
+              unsigned long long* cap_hits, const MmpParams& p, void* stream, bool skip_memset);
+
+// device helpers (kernels.cu)
+void launch_gemm(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count,
+                 double* const arenas[4], int maxn, void* stream);
+void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, double* const arenas[4],
+                int32_t* kr, int32_t* kc, double eps, int trunc, unsigned long long* cap_hits,
+                int max_npad, double* scratch, void* stream);
+void launch_permute(const double* src, double* dst, const int64_t* user, int64_t rows, int64_t n,
+                    int64_t nrhs, bool to_tree, void* stream);
+void launch_identity(double* out, int64_t n, void* stream);
+void cuda_check(int err, const char* what);
+
+// construction (builder.cpp): fills host arrays of the packed import layout
+struct Packed {
+  std::vector<int32_t> kr, kc;
+  std::vector<double> vr, vc, er, ec, s, f;
+};
+void build_h2_host(const Structure& st, const h2_kernel& k, double eps, Packed& out);
+void unpack_to_device(const Packed& p, Mat& m);
+void pack_from_device(Mat& m, Packed& p);
+
+}  // namespace h2

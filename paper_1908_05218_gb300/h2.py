@@ -1,0 +1,224 @@
+"""Python binding of the C ABI in include/h2.h (argument marshalling only).
+
+Every numeric step runs in the CUDA library libh2gb300.so; this module converts
+numpy arrays and torch CUDA tensors to pointers and status codes to exceptions.
+Importing it on a machine without the built library raises immediately: there is
+no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libh2gb300.so")
+
+H2_OK, H2_EINVAL, H2_ENOMEM, H2_ECUDA, H2_ESTRUCT, H2_ETIMEOUT, H2_EINTERNAL, H2_EUNSUPPORTED = range(8)
+FP64, MIXED_FP32 = 0, 1
+TRUNC_PAPER, TRUNC_SV, TRUNC_FULL = 0, 1, 2
+_TRUNC = {"paper": TRUNC_PAPER, "sv": TRUNC_SV, "full": TRUNC_FULL}
+
+# exported symbols and their signatures (checked by the CPU tests)
+SYMBOLS = ["h2_build", "h2_import", "h2_export", "h2_mmp", "h2_matvec", "h2_to_dense", "h2_info",
+           "h2_tree_perm", "h2_level_blocks", "h2_destroy", "h2_last_error"]
+
+
+class H2Error(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"h2 status {code}: {msg}")
+        self.code = code
+
+
+class Kernel(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("wavenumber", C.c_double), ("diag_re", C.c_double), ("diag_im", C.c_double)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("trunc", C.c_int32), ("rank_cap", C.c_int32), ("reserved", C.c_int32),
+                ("stream", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("levels", C.c_int32), ("leaf_size", C.c_int32), ("l_min", C.c_int32),
+                ("csp", C.c_int32), ("n_admissible", C.c_int64), ("n_dense", C.c_int64),
+                ("max_rank_row", C.c_int32 * 32), ("max_rank_col", C.c_int32 * 32), ("bytes_stored", C.c_int64),
+                ("device_bytes", C.c_int64), ("cap_hits", C.c_int64), ("mmp_ms", C.c_double)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} missing: run __graft_entry__.build() (the CUDA library is required)")
+    lib = C.CDLL(path)
+    P, I32, I64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    lib.h2_build.argtypes = [P, I64, C.POINTER(Kernel), I32, D, D, C.POINTER(Opts), C.POINTER(P)]
+    lib.h2_import.argtypes = [P, I64, I32, D, P, P, P, P, P, P, P, P, C.POINTER(Opts), C.POINTER(P)]
+    lib.h2_export.argtypes = [P, P, P, P, P, P, P, P, P, P]
+    lib.h2_mmp.argtypes = [P, P, D, C.POINTER(Opts), C.POINTER(P)]
+    lib.h2_matvec.argtypes = [P, P, P, I64]
+    lib.h2_to_dense.argtypes = [P, P]
+    lib.h2_info.argtypes = [P, C.POINTER(Stats)]
+    lib.h2_tree_perm.argtypes = [P, P]
+    lib.h2_level_blocks.argtypes = [P, I32, P, P, P, P]
+    lib.h2_destroy.argtypes = [P]
+    lib.h2_destroy.restype = None
+    lib.h2_last_error.restype = C.c_char_p
+    for name in SYMBOLS:
+        if name not in ("h2_destroy", "h2_last_error"):
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _check(code: int):
+    if code != H2_OK:
+        raise H2Error(code, load().h2_last_error().decode())
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p) if a is not None and a.size else None
+
+
+def make_opts(precision: int = FP64, trunc: str | int = "paper", rank_cap: int = 0, stream=None) -> Opts:
+    t = _TRUNC[trunc] if isinstance(trunc, str) else int(trunc)
+    if stream is None:
+        try:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
+        except Exception:  # pragma: no cover - torch without CUDA
+            stream = None
+    return Opts(precision, t, rank_cap, 0, stream)
+
+
+def make_kernel(spec) -> Kernel:
+    return Kernel(int(spec.kind), float(spec.wavenumber), float(spec.diag), float(spec.diag_im))
+
+
+@dataclass
+class Packed:
+    kr: np.ndarray
+    kc: np.ndarray
+    vr: np.ndarray
+    vc: np.ndarray
+    er: np.ndarray
+    ec: np.ndarray
+    s: np.ndarray
+    f: np.ndarray
+
+
+class H2Matrix:
+    """Owning wrapper of an h2_handle."""
+
+    def __init__(self, handle: int, n: int):
+        self.handle = C.c_void_p(handle)
+        self.n = n
+
+    def __del__(self):
+        self.destroy()
+
+    def destroy(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            load().h2_destroy(self.handle)
+            self.handle = C.c_void_p(0)
+
+    def mmp(self, other: "H2Matrix", eps: float, precision: int = FP64, trunc="paper", rank_cap: int = 0,
+            out: "H2Matrix | None" = None, stream=None) -> "H2Matrix":
+        """C = self x other (h2_mmp); `out` from an earlier identical call is overwritten in place."""
+        o = make_opts(precision, trunc, rank_cap, stream)
+        h = C.c_void_p(out.handle.value if out is not None else 0)
+        _check(load().h2_mmp(self.handle, other.handle, float(eps), C.byref(o), C.byref(h)))
+        if out is not None and h.value == out.handle.value:
+            return out
+        return H2Matrix(h.value, self.n)
+
+    def matvec(self, x, y=None):
+        """y = H x for torch CUDA float64 x of shape (n,) or (n, nrhs) (h2_matvec)."""
+        import torch
+        squeeze = x.dim() == 1
+        X = x.reshape(self.n, -1)
+        nrhs = X.shape[1]
+        xc = X.t().contiguous()          # column-major n x nrhs
+        yc = torch.empty_like(xc)
+        _check(load().h2_matvec(self.handle, C.c_void_p(xc.data_ptr()), C.c_void_p(yc.data_ptr()), nrhs))
+        out = yc.t()
+        if y is not None:
+            y.copy_(out.reshape(y.shape))
+            return y
+        return out[:, 0] if squeeze else out
+
+    def matvec_ptr(self, x_ptr: int, y_ptr: int, nrhs: int):
+        _check(load().h2_matvec(self.handle, C.c_void_p(x_ptr), C.c_void_p(y_ptr), int(nrhs)))
+
+    def to_dense(self):
+        import torch
+        out = torch.empty((self.n, self.n), dtype=torch.float64, device="cuda")
+        _check(load().h2_to_dense(self.handle, C.c_void_p(out.data_ptr())))
+        return out.t()                   # column-major buffer -> row-major view
+
+    def info(self) -> dict:
+        s = Stats()
+        _check(load().h2_info(self.handle, C.byref(s)))
+        L = s.levels
+        return {"n": s.n, "levels": L, "leaf_size": s.leaf_size, "l_min": s.l_min, "csp": s.csp,
+                "n_admissible": s.n_admissible, "n_dense": s.n_dense,
+                "max_rank_row": list(s.max_rank_row[:L]), "max_rank_col": list(s.max_rank_col[:L]),
+                "bytes_stored": s.bytes_stored, "device_bytes": s.device_bytes, "cap_hits": s.cap_hits,
+                "mmp_ms": s.mmp_ms}
+
+    def export(self) -> Packed:
+        lib = load()
+        sizes = np.zeros(8, dtype=np.int64)
+        _check(lib.h2_export(self.handle, _ptr(sizes), None, None, None, None, None, None, None, None))
+        kr = np.zeros(sizes[0], np.int32)
+        kc = np.zeros(sizes[0], np.int32)
+        arrs = [np.zeros(sizes[i], np.float64) for i in range(1, 7)]
+        _check(lib.h2_export(self.handle, _ptr(sizes), _ptr(kr), _ptr(kc), *[_ptr(a) for a in arrs]))
+        return Packed(kr, kc, *arrs)
+
+    def tree_perm(self) -> np.ndarray:
+        p = np.zeros(self.n, dtype=np.int64)
+        _check(load().h2_tree_perm(self.handle, _ptr(p)))
+        return p
+
+    def level_blocks(self, level: int):
+        lib = load()
+        cnt = C.c_int64(0)
+        _check(lib.h2_level_blocks(self.handle, level, None, None, None, C.byref(cnt)))
+        t = np.zeros(cnt.value, np.int32)
+        s = np.zeros(cnt.value, np.int32)
+        k = np.zeros(cnt.value, np.int8)
+        if cnt.value:
+            _check(lib.h2_level_blocks(self.handle, level, _ptr(t), _ptr(s), _ptr(k), C.byref(cnt)))
+        return t, s, k
+
+
+def h2_build(points: np.ndarray, spec, leaf_size: int = 32, eta: float = 1.0, eps: float = 1e-4,
+             stream=None) -> H2Matrix:
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    k = make_kernel(spec)
+    o = make_opts(stream=stream)
+    h = C.c_void_p(0)
+    _check(load().h2_build(_ptr(pts), pts.shape[0], C.byref(k), int(leaf_size), float(eta), float(eps),
+                           C.byref(o), C.byref(h)))
+    return H2Matrix(h.value, pts.shape[0])
+
+
+def h2_import(points: np.ndarray, leaf_size: int, eta: float, p: Packed, stream=None) -> H2Matrix:
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (p.vr, p.vc, p.er, p.ec, p.s, p.f)]
+    kr = np.ascontiguousarray(p.kr, dtype=np.int32)
+    kc = np.ascontiguousarray(p.kc, dtype=np.int32)
+    o = make_opts(stream=stream)
+    h = C.c_void_p(0)
+    _check(load().h2_import(_ptr(pts), pts.shape[0], int(leaf_size), float(eta), _ptr(kr), _ptr(kc),
+                            *[_ptr(a) for a in arrs], C.byref(o), C.byref(h)))
+    return H2Matrix(h.value, pts.shape[0])

@@ -1,0 +1,136 @@
+"""GPU parity: the CUDA path against the CPU oracle, through the C ABI.
+
+Tolerances (float64 path): the structure and the ranks must match exactly; dense
+expansions and products agree to 1e-10 relative (the two sides sum in different
+orders and decompose with different eigensolvers; the truncation decisions are
+compared exactly and the margin of each case is far above rounding).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import h2 as oh2
+from oracle import mmp as ommp
+from oracle.tree import build_partition, build_tree
+from paper_1908_05218_gb300 import inputs
+
+from oracle_bridge import pack, ranks
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    assert torch.cuda.is_available()
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1908_05218_gb300 import h2
+    return h2
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+CASES = {
+    # name: (workload factory, leaf, eta, eps_h2)
+    "cubes_1024": (lambda: inputs.workload_cube_array(2, 2, 256), 32, 1.0, 1e-4),
+    "cubes_2048_invr2": (lambda: inputs.workload_cube_array(2, 2, 512, kernel="invr2"), 32, 1.0, 1e-4),
+    "uniform_1000_ragged": (lambda: inputs.workload_uniform(1000, seed=5), 32, 1.0, 1e-6),
+    "sphere_700_ragged": (lambda: inputs.Workload("s", inputs.fibonacci_sphere(700, 2.0), inputs.laplace_spec(0.1), 0.1), 20, 1.5, 1e-5),
+}
+
+_cache = {}
+
+
+def oracle_case(name):
+    if name not in _cache:
+        fac, leaf, eta, e = CASES[name]
+        w = fac()
+        _cache[name] = (w, leaf, eta, oh2.build(w.points, w.kernel, leaf, eta, e))
+    return _cache[name]
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_structure_is_bit_exact(lib, name):
+    w, leaf, eta, A = oracle_case(name)
+    g = lib.h2_import(w.points, leaf, eta, pack(A))
+    np.testing.assert_array_equal(g.tree_perm(), A.tree.perm)
+    for l in range(A.L + 1):
+        t, s, k = g.level_blocks(l)
+        ob = A.part.blocks[l]
+        assert len(t) == len(ob)
+        kinds = {"R": 0, "F": 1, "NL": 2}
+        assert list(zip(t.tolist(), s.tolist(), k.tolist())) == [(a, b, kinds[c]) for (a, b, c) in ob]
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_import_export_roundtrip_and_matvec(lib, name):
+    import torch
+    w, leaf, eta, A = oracle_case(name)
+    p = pack(A)
+    g = lib.h2_import(w.points, leaf, eta, p)
+    e = g.export()
+    for f in ("kr", "kc", "vr", "vc", "er", "ec", "s", "f"):
+        np.testing.assert_array_equal(getattr(e, f), getattr(p, f))
+    x = inputs.standard_normal((w.points.shape[0], 3), seed=2)
+    y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y, oh2.matvec(A, x)) < 1e-13
+    y1 = g.matvec(torch.from_numpy(x[:, 1].copy()).cuda()).cpu().numpy()
+    assert rel(y1, oh2.matvec(A, x[:, 1])) < 1e-13
+    assert rel(g.to_dense().cpu().numpy(), oh2.to_dense(A)) < 1e-13
+
+
+@pytest.mark.parametrize("name,mode,eps", [("cubes_1024", "paper", 1e-4), ("cubes_1024", "sv", 1e-4),
+                                           ("cubes_2048_invr2", "paper", 1e-2), ("uniform_1000_ragged", "paper", 1e-6),
+                                           ("sphere_700_ragged", "sv", 1e-3), ("uniform_1000_ragged", "full", 0.0)])
+def test_product_matches_oracle(lib, name, mode, eps):
+    w, leaf, eta, A = oracle_case(name)
+    # B: a different matrix on the same tree (other kernel), bases rotated so that
+    # row and column bases differ
+    wb = inputs.Workload("b", w.points, inputs.inv_r2_spec(w.spacing) if w.kernel.kind == 0 else inputs.laplace_spec(w.spacing), w.spacing)
+    key = name + "_B"
+    if key not in _cache:
+        _cache[key] = oh2.rotate_bases(oh2.build(wb.points, wb.kernel, leaf, eta, 1e-4), seed=7)
+    B = _cache[key]
+    st = {}
+    C = ommp.mmp(A, B, eps, mode, stats=st)
+    ga = lib.h2_import(w.points, leaf, eta, pack(A))
+    gb = lib.h2_import(w.points, leaf, eta, pack(B))
+    gc = ga.mmp(gb, eps, trunc=mode, rank_cap=64 if mode != "full" else 0)
+    info = gc.info()
+    assert info["cap_hits"] == 0
+    ckr, ckc = ranks(C)
+    e = gc.export()
+    np.testing.assert_array_equal(e.kr[: len(ckr)], ckr)
+    np.testing.assert_array_equal(e.kc[: len(ckc)], ckc)
+    d_gpu = gc.to_dense().cpu().numpy()
+    d_orc = oh2.to_dense(C)
+    assert rel(d_gpu, d_orc) < TOL
+    if mode == "full":
+        assert rel(d_gpu, oh2.to_dense(A) @ oh2.to_dense(B)) < 1e-12
+
+
+def test_product_is_deterministic_and_reusable(lib):
+    w, leaf, eta, A = oracle_case("cubes_1024")
+    ga = lib.h2_import(w.points, leaf, eta, pack(A))
+    c1 = ga.mmp(ga, 1e-4)
+    d1 = c1.to_dense().cpu().numpy()
+    c2 = ga.mmp(ga, 1e-4, out=c1)      # in place
+    assert c2 is c1
+    d2 = c1.to_dense().cpu().numpy()
+    np.testing.assert_array_equal(d1, d2)
+
+
+def test_structure_mismatch_is_rejected(lib):
+    w, leaf, eta, A = oracle_case("cubes_1024")
+    w2, leaf2, eta2, A2 = oracle_case("uniform_1000_ragged")
+    ga = lib.h2_import(w.points, leaf, eta, pack(A))
+    gb = lib.h2_import(w2.points, leaf2, eta2, pack(A2))
+    with pytest.raises(lib.H2Error) as ei:
+        ga.mmp(gb, 1e-4)
+    assert ei.value.code == lib.H2_ESTRUCT
