@@ -319,7 +319,7 @@ void pack_from_device(Mat& m, Packed& p) {
 void validate_plan(const Plan& P, const int64_t sizes[4]) {
   auto check = [&](int64_t tagged, int64_t extent, const char* what) {
     if (extent <= 0) return;
-    int64_t a = (int64_t)((uint64_t)tagged >> 62), off = tagged & ((int64_t(1) << 62) - 1);
+    int64_t a = arena_of(tagged), off = offset_of(tagged);
     if (tagged < 0 || off + extent > sizes[a])
       throw Error(H2_EINTERNAL, std::string("plan access out of bounds: ") + what);
   };
@@ -392,7 +392,7 @@ void run_plan(const Plan& P, double* const arenas[4], int32_t* kr, int32_t* kc, 
   for (auto& L : P.launches) {
     if (L.kind == Launch::MEMSET) {
       if (skip_memset || L.elems == 0) continue;
-      double* p = arenas[(uint64_t)L.off >> 62] + (L.off & ((int64_t(1) << 62) - 1));
+      double* p = arenas[arena_of(L.off)] + offset_of(L.off);
       cuda_check(cudaMemsetAsync(p, 0, L.elems * sizeof(double), (cudaStream_t)stream), "memset");
     } else if (L.kind == Launch::GEMM) {
       launch_gemm(P.d_segs, P.d_items, L.first, L.count, arenas, L.aux, stream);
@@ -597,8 +597,8 @@ h2_status h2_matvec(h2_handle h, const double* x, double* y, int64_t nrhs) {
     int64_t rows = (1LL << st.L) * st.LS;
     cudaStream_t s = (cudaStream_t)h->m.stream;
     cuda_check(cudaMemsetAsync(P.d_w, 0, P.w_elems * sizeof(double), s), "zero workspace");
-    double* xt = P.d_w + (offs.first & ((int64_t(1) << 62) - 1));
-    double* yt = P.d_w + (offs.second & ((int64_t(1) << 62) - 1));
+    double* xt = P.d_w + offset_of(offs.first);
+    double* yt = P.d_w + offset_of(offs.second);
     launch_permute(x, xt, h->d_user, rows, st.n, nrhs, true, s);
     double* arenas[4] = {h->m.arena, nullptr, nullptr, P.d_w};
     MmpParams prm{0, 0, 0, 0};

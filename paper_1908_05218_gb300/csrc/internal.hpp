@@ -93,9 +93,14 @@ void free_mat(Mat& m);
 void sync_ranks_to_host(Mat& m);
 
 // ---------------------------------------------------------------- device program
-// Offsets into one of four arenas: the tag in bits 62-63 selects it.
+// Offsets into one of four arenas: the tag in bits 60-61 selects it, so a tagged
+// offset is never negative and -1 can mark "absent".
 enum Arena : int64_t { AR_A = 0, AR_B = 1, AR_C = 2, AR_W = 3 };
-inline int64_t tag(Arena a, int64_t off) { return (a << 62) | off; }
+constexpr int kTagShift = 60;
+constexpr int64_t kOffMask = (int64_t(1) << kTagShift) - 1;
+inline int64_t tag(Arena a, int64_t off) { return (a << kTagShift) | off; }
+inline int arena_of(int64_t t) { return (int)((t >> kTagShift) & 3); }
+inline int64_t offset_of(int64_t t) { return t & kOffMask; }
 
 // Segmented batched GEMM: out[m x n] (=|+=) sum_items op(A) op(B), one CTA per segment.
 enum SegFlags : uint8_t { SF_TA = 1, SF_TB = 2, SF_ACC = 4, SF_SUM = 8 };

@@ -15,7 +15,7 @@ struct Arenas {
 };
 
 __device__ __forceinline__ double* resolve(const Arenas& a, int64_t t) {
-  return a.p[(uint64_t)t >> 62] + (t & ((int64_t(1) << 62) - 1));
+  return a.p[(t >> kTagShift) & 3] + (t & kOffMask);
 }
 
 // ------------------------------------------------------------ segmented GEMM

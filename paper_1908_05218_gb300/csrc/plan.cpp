@@ -189,6 +189,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
     C.Kr[l] = std::min(2 * C.Kr[l + 1], cap);
     C.Kc[l] = std::min(2 * C.Kc[l + 1], cap);
   }
+  mat_elems(C);  // offsets of C's arrays
   // zero the workspace first (outputs accumulate)
   {
     Launch z;
