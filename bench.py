@@ -1,0 +1,328 @@
+"""Benchmark of the H^2 matrix-matrix product C = A x B with change of bases.
+
+One step = one full product (every phase of Sec. III-IV: basis products, dense
+targets, Gram matrices, eigen-decompositions, projections, collects, couplings,
+merges, the top-down split) on inputs resident in device memory.  The metric is
+algorithmic throughput: (bytes of A + B + C at their actual ranks) / product time,
+in GB/s, with the product time itself reported beside it.
+
+  python bench.py [--gpus N --steps K --warmup W] [--workload cubes16x16|cubes4x4]
+                  [--precision fp64|mixed] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the plain float64 restatement of the method)
+on a bounded sample of the same geometry: the reference arm.
+Multi-GPU: one product does not shard (every level exchanges neighbour blocks), so
+N GPUs run N independent replicas; the value is the work of all replicas divided by
+the slowest replica's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (nx, ny, points per cube, eps, description)
+    "cubes16x16": (16, 16, 4096, 1e-4, "N=1,048,576 panel centroids on a 16x16 array of unit cubes"),
+    "cubes4x4": (4, 4, 4096, 1e-4, "N=65,536 panel centroids on a 4x4 array of unit cubes"),
+    "cubes2x2": (2, 2, 1024, 1e-4, "N=4,096 panel centroids on a 2x2 array of unit cubes"),
+}
+LEAF, ETA, EPS_H2 = 32, 1.0, 1e-4
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def reference_arm(args):
+    """The CPU oracle on a bounded sample of the workload (1 core, float64)."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    t0 = time.time()
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-sample",
+                          "--steps", str(args.steps)], capture_output=True, text=True, env=env)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    res = json.loads(out.stdout.strip().splitlines()[-1])
+    res["wall_s"] = time.time() - t0
+    return res
+
+
+def oracle_sample(steps: int):
+    """Child process: oracle product on N=4096 points of the cube-array geometry."""
+    import numpy as np
+
+    from oracle import h2 as oh2
+    from oracle import mmp as ommp
+    from paper_1908_05218_gb300 import inputs
+    nx, ny, ppc, eps, _ = WORKLOADS["cubes2x2"]
+    wa = inputs.workload_cube_array(nx, ny, ppc)
+    wb = inputs.workload_cube_array(nx, ny, ppc, kernel="invr2")
+    A = oh2.build(wa.points, wa.kernel, LEAF, ETA, EPS_H2)
+    B = oh2.build(wb.points, wb.kernel, LEAF, ETA, EPS_H2)
+
+    def size(h):
+        n = sum(v.size for v in h.Vr.values()) + sum(v.size for v in h.Vc.values())
+        n += sum(v.size for v in h.Er.values()) + sum(v.size for v in h.Ec.values())
+        n += sum(v.size for v in h.S.values()) + sum(v.size for v in h.Fb.values())
+        return 8 * n
+
+    times = []
+    C = None
+    for _ in range(max(1, steps)):
+        t0 = time.perf_counter()
+        C = ommp.mmp(A, B, eps, "paper")
+        times.append(time.perf_counter() - t0)
+    t = float(np.median(times))
+    nbytes = size(A) + size(B) + size(C)
+    print(json.dumps({"t": t, "bytes": nbytes, "n": int(wa.points.shape[0]), "steps": len(times)}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cubes4x4", choices=list(WORKLOADS))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--oracle-sample", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    if args.oracle_sample:
+        oracle_sample(args.steps)
+        return
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    nx, ny, ppc, eps, desc = WORKLOADS[args.workload]
+    metric = "H2-MMP throughput (bytes of A+B+C at actual ranks / product time)"
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        r = reference_arm(args)
+        gbs = r["bytes"] / r["t"] / 1e9
+        line = {"metric": metric, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus, "steps": r["steps"],
+                "warmup": 0, "ms_per_step": r["t"] * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+                "config": {"workload": f"cube array 2x2, 1024 points per cube (N={r['n']}), leaf {LEAF}, "
+                                       f"eta {ETA}, eps {eps}, A: 1/(4 pi r), B: 1/r^2",
+                           "sample_of": desc},
+                "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                                 "sample": f"N={r['n']} product, median of {r['steps']}"},
+                "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    # CPU baseline first, in a child process started before any CUDA call
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = reference_arm(argparse.Namespace(steps=1))
+        except Exception as e:  # reported, not fatal
+            cpu = {"error": str(e)[-300:]}
+
+    import numpy as np
+    import torch
+
+    from paper_1908_05218_gb300 import h2 as lib
+    from paper_1908_05218_gb300 import inputs
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    lib.load()
+    prec = lib.FP64 if args.precision == "fp64" else lib.MIXED_FP32
+
+    wa = inputs.workload_cube_array(nx, ny, ppc)
+    wb = inputs.workload_cube_array(nx, ny, ppc, kernel="invr2")
+    t0 = time.time()
+    A = lib.h2_build(wa.points, wa.kernel, LEAF, ETA, EPS_H2)
+    B = lib.h2_build(wb.points, wb.kernel, LEAF, ETA, EPS_H2)
+    build_s = time.time() - t0
+    stream = torch.cuda.current_stream()
+
+    C = None
+    t0 = time.time()
+    C = A.mmp(B, eps, precision=prec, out=C)
+    torch.cuda.synchronize()
+    setup_s = time.time() - t0
+    for _ in range(args.warmup):
+        C = A.mmp(B, eps, precision=prec, out=C)
+    torch.cuda.synchronize()
+
+    A.trace_enable(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            C = A.mmp(B, eps, precision=prec, out=C)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1) / max(1, args.steps)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    kinds, levels, lms, lfl = C.trace_read()
+    A.trace_enable(False)
+
+    ia, ib, ic = A.info(), B.info(), C.info()
+    nbytes = ia["bytes_stored"] + ib["bytes_stored"] + ic["bytes_stored"]
+    value = nbytes * world / (ms * 1e-3) / 1e9
+
+    # accuracy of this product: Eq. error with exact H^2 matvecs, 4 random vectors
+    x = torch.from_numpy(inputs.standard_normal((wa.points.shape[0], 4), seed=1)).cuda()
+    y_ref = A.matvec(B.matvec(x))
+    rel_err = float(torch.linalg.norm(C.matvec(x) - y_ref) / torch.linalg.norm(y_ref))
+
+    # roofline: the dominant kernel of the traced step
+    tot = {}
+    for k, m_, f_ in zip(kinds, lms, lfl):
+        tt = tot.setdefault(k, [0.0, 0.0, 0])
+        tt[0] += m_
+        tt[1] += f_
+        tt[2] += 1
+    dom = max(tot, key=lambda k: tot[k][0])
+    peaks, src = _peaks()
+    fp64_peak = 1.01  # TFLOP/s, DFMA probe on this machine's GB300 (profiles/fp64_fp32_throughput_probe.txt)
+    fp32_peak = 67.0
+    if dom == "gemm":
+        achieved = tot[dom][1] / (tot[dom][0] * 1e-3) / 1e12
+        peak = fp64_peak if args.precision == "fp64" else fp32_peak
+        roof = {"bound": "alu", "kernel": "seg_gemm_kernel", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "launches_per_step": tot[dom][2], "ms_per_step": tot[dom][0],
+                "note": "executed flops at padded dims; peak = measured DFMA/FFMA probe, not MEASURED_PEAKS"}
+    else:
+        roof = {"bound": "alu", "kernel": dom, "ms_per_step": tot[dom][0], "achieved": None, "peak": None,
+                "unit": None, "frac": None, "traffic": None}
+    phase_ms = {k: round(v[0], 3) for k, v in tot.items()}
+
+    # end to end through the public API with host buffers: upload A and B from host
+    # arrays, the product, download C
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        pa, pbk = A.export(), B.export()
+        h2d = sum(a.nbytes for a in (pa.kr, pa.kc, pa.vr, pa.vc, pa.er, pa.ec, pa.s, pa.f))
+        h2d += sum(a.nbytes for a in (pbk.kr, pbk.kc, pbk.vr, pbk.vc, pbk.er, pbk.ec, pbk.s, pbk.f))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        A2 = lib.h2_import(wa.points, LEAF, ETA, pa)
+        B2 = lib.h2_import(wb.points, LEAF, ETA, pbk)
+        C2 = A2.mmp(B2, eps, precision=prec)
+        pc = C2.export()
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        d2h = sum(a.nbytes for a in (pc.kr, pc.kc, pc.vr, pc.vc, pc.er, pc.ec, pc.s, pc.f))
+        e2e = {"value": nbytes / te / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "seconds": te, "steps": 1}
+        for h in (C2, B2, A2):
+            h.destroy()
+
+    if rank == 0:
+        cpu_line = None
+        if cpu and "t" in cpu:
+            cpu_line = {"value": cpu["bytes"] / cpu["t"] / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                        "sample": f"cube array 2x2, 1024 points per cube (N={cpu['n']}), one product, eps {eps}",
+                        "seconds": cpu["t"]}
+        elif cpu:
+            cpu_line = {"error": cpu.get("error")}
+        line = {
+            "metric": metric, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": f"{desc}; leaf {LEAF}, eta {ETA}, eps_trunc {eps} (paper rule), "
+                                   f"eps_H2 {EPS_H2}; A: 1/(4 pi r), B: 1/r^2",
+                       "inputs": "A, B, C together exceed L2 (no flush needed)", "parallelism": "replicas"},
+            "mmp_s": ms * 1e-3, "rel_err_vs_exact_h2_matvecs": rel_err,
+            "ranks_C_max_row": ic["max_rank_row"], "cap_hits": ic["cap_hits"],
+            "bytes_alg": nbytes, "build_s": build_s, "first_product_s_incl_plan": setup_s,
+            "phase_ms": phase_ms, "roofline": roof, "cpu_baseline": cpu_line, "e2e": e2e,
+            "gpu_launches": int(sum(tot[k][2] for k in tot if k != "memset")) * args.steps,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

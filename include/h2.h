@@ -117,8 +117,8 @@ typedef struct {
  * Structure (Sec. II): cardinality-balanced bisection cluster tree with all leaves
  * on level L, block partition by Eq. admCond with bounding boxes.  The numeric
  * construction is not specified by the paper (it cites another method); this build
- * uses nested far-field sampling with interpolative skeletons (the design doc names the
- * reading).  Errors: H2_EINVAL for bad sizes or non-finite points,
+ * uses nested far-field sampling with interpolative skeletons (sampled far field
+ * per cluster, skeleton rows chosen by pivoted Gram-Schmidt).  Errors: H2_EINVAL for bad sizes or non-finite points,
  * H2_EUNSUPPORTED for a complex kernel. */
 h2_status h2_build(const double* points, int64_t n, const h2_kernel* kernel,
                    int32_t leaf_size, double eta, double eps, const h2_opts* opts,
@@ -175,6 +175,16 @@ h2_status h2_info(h2_handle h, h2_stats* stats);
 h2_status h2_tree_perm(h2_handle h, int64_t* perm);
 h2_status h2_level_blocks(h2_handle h, int32_t level, int32_t* t, int32_t* s,
                           int8_t* kind, int64_t* count);
+
+/* Kernel timing of the next products made from A (device events around every
+ * launch group of h2_mmp; off by default because it adds event records).  After a
+ * product, h2_trace_read returns, for up to `cap` launch groups in program order,
+ * the kernel kind (0 GEMM, 1 eigen, 2 memset), the level, the device time in ms and
+ * the counted float64 multiply-add flops (2 m n k per product at the actual padded
+ * dims) of that group; *count gets the number of groups.  Synchronises. */
+h2_status h2_trace_enable(h2_handle A, int32_t on);
+h2_status h2_trace_read(h2_handle C, int32_t cap, int32_t* kind, int32_t* level, double* ms,
+                        double* flops, int32_t* count);
 
 void h2_destroy(h2_handle h);
 const char* h2_last_error(void);

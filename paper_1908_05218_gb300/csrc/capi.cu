@@ -26,6 +26,9 @@ struct h2_matrix {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool timed = false;
   int origin_trunc = -1, origin_cap = -1;
+  bool trace_on = false;     // on A: trace the products made from it
+  h2::Trace trace;           // on C: events of the product that made it
+  const h2::Plan* trace_plan = nullptr;
   const h2_matrix* origin_A = nullptr;
   const h2_matrix* origin_B = nullptr;
 };
@@ -316,7 +319,7 @@ void pack_from_device(Mat& m, Packed& p) {
 
 // Host-side check that every access of a plan stays inside its arena: run before a
 // plan's first upload so that an indexing error is reported instead of executed.
-void validate_plan(const Plan& P, const int64_t sizes[4]) {
+void validate_plan(const Plan& P, const int64_t sizes[kArenas]) {
   auto check = [&](int64_t tagged, int64_t extent, const char* what) {
     if (extent <= 0) return;
     int64_t a = arena_of(tagged), off = offset_of(tagged);
@@ -362,8 +365,14 @@ void upload_plan(Plan& P) {
   for (auto& L : P.launches) {
     if (L.kind == Launch::GEMM) {
       int mx = 1;
-      for (int64_t q = L.first; q < L.first + L.count; ++q) mx = std::max<int>(mx, P.segs[q].n);
+      double fl = 0;
+      for (int64_t q = L.first; q < L.first + L.count; ++q) {
+        const Seg& s = P.segs[q];
+        mx = std::max<int>(mx, s.n);
+        if (!(s.flags & SF_SUM)) fl += 2.0 * s.m * s.n * s.k * s.count;
+      }
       L.aux = mx;
+      L.flops = fl;
     } else if (L.kind == Launch::EIG) {
       int mx = 1;
       for (int64_t q = L.first; q < L.first + L.count; ++q) mx = std::max<int>(mx, P.eigs[q].n_pad);
@@ -374,22 +383,35 @@ void upload_plan(Plan& P) {
     }
   }
   P.d_scratch = (double*)dmalloc(std::max<int64_t>(1, scratch) * sizeof(double));
-  P.d_w = (double*)dmalloc(std::max<int64_t>(1, P.w_elems) * sizeof(double));
+  for (int a = AR_P; a <= AR_S; ++a) P.d_region[a] = (double*)dmalloc(std::max<int64_t>(1, P.region[a]) * sizeof(double));
 }
 
 void free_plan(Plan& P) {
-  for (void* q : {(void*)P.d_segs, (void*)P.d_items, (void*)P.d_eigs, (void*)P.d_w, (void*)P.d_scratch})
+  for (void* q : {(void*)P.d_segs, (void*)P.d_items, (void*)P.d_eigs, (void*)P.d_scratch})
     if (q) cudaFree(q);
+  for (int a = 0; a < kArenas; ++a) {
+    if (P.d_region[a]) cudaFree(P.d_region[a]);
+    P.d_region[a] = nullptr;
+  }
   P.d_segs = nullptr;
   P.d_items = nullptr;
   P.d_eigs = nullptr;
-  P.d_w = nullptr;
   P.d_scratch = nullptr;
 }
 
-void run_plan(const Plan& P, double* const arenas[4], int32_t* kr, int32_t* kc, unsigned long long* cap_hits,
-              const MmpParams& prm, void* stream, bool skip_memset) {
-  for (auto& L : P.launches) {
+void run_plan(const Plan& P, double* const arenas[kArenas], int32_t* kr, int32_t* kc, unsigned long long* cap_hits,
+              const MmpParams& prm, void* stream, bool skip_memset, Trace* tr) {
+  if (tr) {
+    while (tr->ev.size() < 2 * P.launches.size()) {
+      cudaEvent_t e;
+      cuda_check(cudaEventCreate(&e), "event");
+      tr->ev.push_back((void*)e);
+    }
+    tr->recorded = true;
+  }
+  for (size_t li = 0; li < P.launches.size(); ++li) {
+    const Launch& L = P.launches[li];
+    if (tr) cuda_check(cudaEventRecord((cudaEvent_t)tr->ev[2 * li], (cudaStream_t)stream), "event");
     if (L.kind == Launch::MEMSET) {
       if (skip_memset || L.elems == 0) continue;
       double* p = arenas[arena_of(L.off)] + offset_of(L.off);
@@ -401,6 +423,7 @@ void run_plan(const Plan& P, double* const arenas[4], int32_t* kr, int32_t* kc, 
                  stream);
     }
     cuda_check(cudaGetLastError(), L.phase);
+    if (tr) cuda_check(cudaEventRecord((cudaEvent_t)tr->ev[2 * li + 1], (cudaStream_t)stream), "event");
   }
 }
 
@@ -535,7 +558,8 @@ h2_status h2_mmp(h2_handle A, h2_handle B, double eps, const h2_opts* opts, h2_h
         probe.Kr = Ccaps.Kr;
         probe.Kc = Ccaps.Kc;
         int64_t csize = mat_elems(probe);
-        int64_t sizes[4] = {A->m.arena_elems, B->m.arena_elems, csize, e->plan.w_elems};
+        int64_t sizes[kArenas] = {A->m.arena_elems, B->m.arena_elems, csize, e->plan.region[AR_P],
+                                  e->plan.region[AR_G0], e->plan.region[AR_G1], e->plan.region[AR_S], 0};
         validate_plan(e->plan, sizes);
       }
       upload_plan(e->plan);
@@ -568,8 +592,11 @@ h2_status h2_mmp(h2_handle A, h2_handle B, double eps, const h2_opts* opts, h2_h
     cuda_check(cudaEventRecord(out->ev0, s), "event");
     cuda_check(cudaMemsetAsync(out->m.arena, 0, out->m.arena_elems * sizeof(double), s), "zero C");
     cuda_check(cudaMemsetAsync(out->m.d_kr, 0, 2 * A->m.st->nnodes() * sizeof(int32_t) + 64, s), "zero ranks");
-    double* arenas[4] = {A->m.arena, B->m.arena, out->m.arena, ent->plan.d_w};
-    run_plan(ent->plan, arenas, out->m.d_kr, out->m.d_kc, out->m.d_cap, prm, o.stream, false);
+    double* arenas[kArenas] = {A->m.arena, B->m.arena, out->m.arena, ent->plan.d_region[AR_P],
+                               ent->plan.d_region[AR_G0], ent->plan.d_region[AR_G1], ent->plan.d_region[AR_S], nullptr};
+    out->trace_plan = A->trace_on ? &ent->plan : nullptr;
+    run_plan(ent->plan, arenas, out->m.d_kr, out->m.d_kc, out->m.d_cap, prm, o.stream, false,
+             A->trace_on ? &out->trace : nullptr);
     cuda_check(cudaEventRecord(out->ev1, s), "event");
     out->timed = true;
     if (fresh) *C = fresh.release();
@@ -585,7 +612,7 @@ h2_status h2_matvec(h2_handle h, const double* x, double* y, int64_t nrhs) {
       auto p = std::make_unique<Plan>();
       int64_t ox, oy;
       build_matvec_plan(h->m, nrhs, *p, ox, oy);
-      int64_t sizes[4] = {h->m.arena_elems, 0, 0, p->w_elems};
+      int64_t sizes[kArenas] = {h->m.arena_elems, 0, 0, p->region[AR_P], 0, 0, 0, 0};
       validate_plan(*p, sizes);
       upload_plan(*p);
       h->mv_offs[nrhs] = {ox, oy};
@@ -596,11 +623,12 @@ h2_status h2_matvec(h2_handle h, const double* x, double* y, int64_t nrhs) {
     const Structure& st = *h->m.st;
     int64_t rows = (1LL << st.L) * st.LS;
     cudaStream_t s = (cudaStream_t)h->m.stream;
-    cuda_check(cudaMemsetAsync(P.d_w, 0, P.w_elems * sizeof(double), s), "zero workspace");
-    double* xt = P.d_w + offset_of(offs.first);
-    double* yt = P.d_w + offset_of(offs.second);
+    double* W = P.d_region[AR_P];
+    cuda_check(cudaMemsetAsync(W, 0, P.region[AR_P] * sizeof(double), s), "zero workspace");
+    double* xt = W + offset_of(offs.first);
+    double* yt = W + offset_of(offs.second);
     launch_permute(x, xt, h->d_user, rows, st.n, nrhs, true, s);
-    double* arenas[4] = {h->m.arena, nullptr, nullptr, P.d_w};
+    double* arenas[kArenas] = {h->m.arena, nullptr, nullptr, W, nullptr, nullptr, nullptr, nullptr};
     MmpParams prm{0, 0, 0, 0};
     run_plan(P, arenas, nullptr, nullptr, nullptr, prm, s, true);
     launch_permute(yt, y, h->d_user, rows, st.n, nrhs, false, s);
@@ -699,8 +727,36 @@ h2_status h2_level_blocks(h2_handle h, int32_t level, int32_t* t, int32_t* s, in
   return H2_OK;
 }
 
+h2_status h2_trace_enable(h2_handle A, int32_t on) {
+  if (!A) return fail(H2_EINVAL, "null argument");
+  A->trace_on = on != 0;
+  return H2_OK;
+}
+
+h2_status h2_trace_read(h2_handle C, int32_t cap, int32_t* kind, int32_t* level, double* ms, double* flops,
+                        int32_t* count) {
+  if (!C || !count) return fail(H2_EINVAL, "null argument");
+  return guarded([&] {
+    if (!C->trace_plan || !C->trace.recorded) throw Error(H2_EINVAL, "no traced product on this handle");
+    const Plan& P = *C->trace_plan;
+    cuda_check(cudaStreamSynchronize((cudaStream_t)C->m.stream), "synchronise");
+    int32_t n = (int32_t)P.launches.size();
+    *count = n;
+    for (int32_t i = 0; i < n && i < cap; ++i) {
+      const Launch& L = P.launches[i];
+      float t = 0;
+      cuda_check(cudaEventElapsedTime(&t, (cudaEvent_t)C->trace.ev[2 * i], (cudaEvent_t)C->trace.ev[2 * i + 1]), "event");
+      if (kind) kind[i] = L.kind == Launch::GEMM ? 0 : (L.kind == Launch::EIG ? 1 : 2);
+      if (level) level[i] = L.level;
+      if (ms) ms[i] = t;
+      if (flops) flops[i] = L.flops;
+    }
+  });
+}
+
 void h2_destroy(h2_handle h) {
   if (!h) return;
+  for (void* e : h->trace.ev) cudaEventDestroy((cudaEvent_t)e);
   cudaDeviceSynchronize();
   for (auto& e : h->mmp_plans) free_plan(e->plan);
   for (auto& kv : h->mv_plans) free_plan(*kv.second);

@@ -93,13 +93,17 @@ void free_mat(Mat& m);
 void sync_ranks_to_host(Mat& m);
 
 // ---------------------------------------------------------------- device program
-// Offsets into one of four arenas: the tag in bits 60-61 selects it, so a tagged
-// offset is never negative and -1 can mark "absent".
-enum Arena : int64_t { AR_A = 0, AR_B = 1, AR_C = 2, AR_W = 3 };
+// Offsets into one of eight arenas: the tag in bits 60-62 selects it, so a tagged
+// offset is never negative and -1 can mark "absent".  A, B, C are the matrices; P
+// holds data that lives for the whole product (couplings of non-leaf targets of C
+// until the top-down split), G0/G1 hold what level l hands to level l-1 (ping-pong
+// by level parity), S holds the temporaries of one level.
+enum Arena : int64_t { AR_A = 0, AR_B = 1, AR_C = 2, AR_P = 3, AR_G0 = 4, AR_G1 = 5, AR_S = 6, AR_X = 7 };
+constexpr int kArenas = 8;
 constexpr int kTagShift = 60;
 constexpr int64_t kOffMask = (int64_t(1) << kTagShift) - 1;
 inline int64_t tag(Arena a, int64_t off) { return (a << kTagShift) | off; }
-inline int arena_of(int64_t t) { return (int)((t >> kTagShift) & 3); }
+inline int arena_of(int64_t t) { return (int)((t >> kTagShift) & 7); }
 inline int64_t offset_of(int64_t t) { return t & kOffMask; }
 
 // Segmented batched GEMM: out[m x n] (=|+=) sum_items op(A) op(B), one CTA per segment.
@@ -132,6 +136,7 @@ struct Launch {
   int level = -1;
   int aux = 0;                   // GEMM: largest n; EIG: largest Gram dim
   const char* phase = "";
+  double flops = 0;              // GEMM: counted 2 m n k over the group
 };
 
 struct Plan {
@@ -139,12 +144,12 @@ struct Plan {
   std::vector<Item> items;
   std::vector<EigTask> eigs;
   std::vector<Launch> launches;
-  int64_t w_elems = 0;  // workspace size
+  int64_t region[kArenas] = {0, 0, 0, 0, 0, 0, 0, 0};  // sizes of P, G0, G1, S (others 0)
   // device copies
   Seg* d_segs = nullptr;
   Item* d_items = nullptr;
   EigTask* d_eigs = nullptr;
-  double* d_w = nullptr;
+  double* d_region[kArenas] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double* d_scratch = nullptr;  // eigen work space for Gram matrices above 112
   int64_t flops = 0;     // counted 2mnk over GEMM segments (padded dims)
   std::vector<int> ckr, ckc;  // caps of the product
@@ -160,18 +165,23 @@ struct MmpParams {
 // Builds the plan of C = A B; sets C's caps (C must share A's structure).
 void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& p, Plan& plan);
 void build_matvec_plan(const Mat& H, int64_t nrhs, Plan& plan, int64_t& off_x, int64_t& off_y);
-void validate_plan(const Plan& plan, const int64_t sizes[4]);
+void validate_plan(const Plan& plan, const int64_t sizes[kArenas]);
 void upload_plan(Plan& plan);
 void free_plan(Plan& plan);
 
-// Runs a plan: arenas[4] device base pointers.
-void run_plan(const Plan& plan, double* const arenas[4], int32_t* kr_out, int32_t* kc_out,
-              unsigned long long* cap_hits, const MmpParams& p, void* stream, bool skip_memset);
+// Runs a plan: arenas[kArenas] device base pointers.
+struct Trace {
+  std::vector<void*> ev;  // cudaEvent_t, 2 per launch
+  bool recorded = false;
+};
+void run_plan(const Plan& plan, double* const arenas[kArenas], int32_t* kr_out, int32_t* kc_out,
+              unsigned long long* cap_hits, const MmpParams& p, void* stream, bool skip_memset,
+              Trace* trace = nullptr);
 
 // device helpers (kernels.cu)
 void launch_gemm(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count,
-                 double* const arenas[4], int maxn, void* stream);
-void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, double* const arenas[4],
+                 double* const arenas[kArenas], int maxn, void* stream);
+void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, double* const arenas[kArenas],
                 int32_t* kr, int32_t* kc, double eps, int trunc, unsigned long long* cap_hits,
                 int max_npad, double* scratch, void* stream);
 void launch_permute(const double* src, double* dst, const int64_t* user, int64_t rows, int64_t n,

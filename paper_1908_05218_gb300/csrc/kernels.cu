@@ -11,11 +11,11 @@
 namespace h2 {
 
 struct Arenas {
-  double* p[4];
+  double* p[kArenas];
 };
 
 __device__ __forceinline__ double* resolve(const Arenas& a, int64_t t) {
-  return a.p[(t >> kTagShift) & 3] + (t & kOffMask);
+  return a.p[(t >> kTagShift) & 7] + (t & kOffMask);
 }
 
 // ------------------------------------------------------------ segmented GEMM
@@ -102,10 +102,10 @@ __global__ void __launch_bounds__(256) seg_gemm_kernel(const Seg* __restrict__ s
   }
 }
 
-void launch_gemm(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, double* const arenas[4],
+void launch_gemm(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, double* const arenas[kArenas],
                  int maxn, void* stream) {
   Arenas ar;
-  for (int i = 0; i < 4; ++i) ar.p[i] = arenas[i];
+  for (int i = 0; i < kArenas; ++i) ar.p[i] = arenas[i];
   const int64_t kMaxGrid = 2147483647LL;
   int gy = (maxn + GT - 1) / GT;
   if (gy < 1) gy = 1;
@@ -306,11 +306,11 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
   }
 }
 
-void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, double* const arenas[4], int32_t* kr,
+void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, double* const arenas[kArenas], int32_t* kr,
                 int32_t* kc, double eps, int trunc, unsigned long long* cap_hits, int max_npad, double* scratch,
                 void* stream) {
   Arenas ar;
-  for (int i = 0; i < 4; ++i) ar.p[i] = arenas[i];
+  for (int i = 0; i < kArenas; ++i) ar.p[i] = arenas[i];
   int nn = max_npad + (max_npad & 1);
   size_t smem = 0;
   int64_t stride = 0;

@@ -34,15 +34,29 @@ enum TClass : int8_t { TC_R = 0, TC_F = 1, TC_NL = 2, TC_SUB = 3 };
 
 struct PlanBuilder {
   Plan& P;
-  int64_t wtop = 0;
+  int64_t top[kArenas] = {0, 0, 0, 0, 0, 0, 0, 0};
   size_t g0 = 0;
   explicit PlanBuilder(Plan& p) : P(p) {}
 
-  int64_t W(int64_t elems) {
-    int64_t o = wtop;
-    wtop += (elems + 31) & ~int64_t(31);
-    return tag(AR_W, o);
+  // bump allocation in one region, 256-byte aligned
+  int64_t alloc(Arena a, int64_t elems) {
+    int64_t o = top[a];
+    top[a] += (elems + 31) & ~int64_t(31);
+    P.region[a] = std::max(P.region[a], top[a]);
+    return tag(a, o);
   }
+  void reset(Arena a) { top[a] = 0; }
+  // zero [0, top) of a region at this point of the program; the size is patched by
+  // close_memset once the level has been planned
+  size_t open_memset(Arena a) {
+    Launch z;
+    z.kind = Launch::MEMSET;
+    z.off = tag(a, 0);
+    z.phase = "zero";
+    P.launches.push_back(z);
+    return P.launches.size() - 1;
+  }
+  void close_memset(size_t idx, Arena a) { P.launches[idx].elems = top[a]; }
   void begin() { g0 = P.segs.size(); }
   void end(const char* phase, int level) {
     if (P.segs.size() > g0) {
@@ -118,10 +132,9 @@ struct Target {
   int32_t i, k;
   int8_t cls;
   int64_t ssum = -1;   // tagged offset of the summed coupling (R: C's S; SUB/NL: W)
-  int64_t s24 = -1, s3 = -1, M = -1, Mt = -1;
   int32_t cpos = -1;   // position of the block in C's level list (R, F, NL targets)
   bool has_nlnl = false;
-  std::vector<int32_t> child;  // SUB/R targets with NL x NL triples: 4 child target ids
+  std::vector<Item> g1;  // leaf case-1 items (V^C_i^T F_ij, F_jk V^C_k)
 };
 
 struct LevelTargets {
@@ -180,23 +193,12 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
   C.Kr.assign(L + 1, 0);
   C.Kc.assign(L + 1, 0);
   C.Kr[L] = C.Kc[L] = LS;
-  for (int l = L - 1; l >= 0; --l) {
-    if (l < lmin) {
-      C.Kr[l] = C.Kc[l] = 0;
-      continue;
-    }
+  for (int l = L - 1; l >= lmin; --l) {
     int cap = prm.trunc == H2_TRUNC_FULL ? 1 << 20 : prm.rank_cap;
     C.Kr[l] = std::min(2 * C.Kr[l + 1], cap);
     C.Kc[l] = std::min(2 * C.Kc[l + 1], cap);
   }
   mat_elems(C);  // offsets of C's arrays
-  // zero the workspace first (outputs accumulate)
-  {
-    Launch z;
-    z.kind = Launch::MEMSET;
-    z.phase = "zero";
-    P.launches.push_back(z);  // size filled at the end
-  }
   auto rA = [&](int l) { return A.Kr[l]; };
   auto cA = [&](int l) { return A.Kc[l]; };
   auto rB = [&](int l) { return B.Kr[l]; };
@@ -206,422 +208,340 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
   auto tA = [&](int64_t o) { return tag(AR_A, o); };
   auto tB = [&](int64_t o) { return tag(AR_B, o); };
   auto tC = [&](int64_t o) { return tag(AR_C, o); };
-
-  // ---- B_j on levels l_min..L
-  std::vector<std::vector<int64_t>> Bj(L + 1);
-  for (int l = L; l >= lmin; --l) {
-    int64_t nc = 1LL << l;
-    Bj[l].resize(nc);
-    for (int64_t j = 0; j < nc; ++j) Bj[l][j] = pb.W((int64_t)cA(l) * rB(l));
-  }
-  pb.begin();
-  for (int64_t j = 0; j < (1LL << L); ++j)
-    pb.gemm1(Bj[L][j], cA(L), rB(L), LS, cA(L), rB(L), rB(L), SF_TA, tA(A.Vc(j)), tB(B.Vr(j)));
-  pb.end("bprod", L);
-  for (int l = L - 1; l >= lmin; --l) {
-    int64_t nc = 1LL << l;
-    std::vector<int64_t> tmp(2 * nc);
-    for (auto& x : tmp) x = pb.W((int64_t)cA(l + 1) * rB(l));
-    pb.begin();
-    for (int64_t j = 0; j < nc; ++j)
-      for (int a = 0; a < 2; ++a)
-        pb.gemm1(tmp[2 * j + a], cA(l + 1), rB(l), rB(l + 1), rB(l + 1), rB(l), rB(l), 0, Bj[l + 1][2 * j + a],
-                 tB(B.Er(l, j) + (int64_t)a * rB(l + 1) * rB(l)));
-    pb.end("bprod", l);
-    pb.begin();
-    for (int64_t j = 0; j < nc; ++j) {
-      std::vector<Item> it;
-      for (int a = 0; a < 2; ++a) it.push_back({tA(A.Ec(l, j) + (int64_t)a * cA(l + 1) * cA(l)), tmp[2 * j + a]});
-      pb.gemm(Bj[l][j], cA(l), rB(l), cA(l + 1), cA(l), rB(l), rB(l), SF_TA, it);
-    }
-    pb.end("bprod", l);
-  }
-
-  // per-level data that the next level up reads
-  std::vector<std::vector<int64_t>> PA(L + 1), PB(L + 1), Ahat(L + 1), Bhat(L + 1);
-  std::vector<LevelTargets> LT(L + 1);
+  auto G = [](int l) { return (l & 1) ? AR_G1 : AR_G0; };
   const int64_t LS2 = (int64_t)LS * LS;
 
-  // =========================================================== leaf level (Sec. III)
-  {
-    const int l = L;
+  const size_t zP = pb.open_memset(AR_P);  // couplings held by NL targets accumulate
+  // per-level data handed to the next level up (in G[level parity])
+  std::vector<std::vector<int64_t>> Bj(L + 1), PA(L + 1), PB(L + 1), Ahat(L + 1), Bhat(L + 1);
+  std::vector<LevelTargets> LT(L + 1);
+
+  for (int l = L; l >= lmin; --l) {
+    const bool leaf = l == L;
+    const int c = l + 1;
+    const Arena g = G(l);
+    pb.reset(g);
+    pb.reset(AR_S);
+    const size_t zG = pb.open_memset(g), zS = pb.open_memset(AR_S);
     LevelTargets& lt = LT[l];
     enumerate(st, l, lt);
     const auto& bl = st.blocks[l];
     const int64_t nb = (int64_t)bl.size(), nc = 1LL << l;
-    // allocations
-    std::vector<int64_t> Y(nb, -1), Yb(nb, -1), T1(nb, -1), T2(nb, -1), Q(nb, -1), Rr(nb, -1), Wsum(nb, -1),
-        YW(nb, -1), Wsc(nb, -1), YWc(nb, -1), Ach(nb, -1), Bch(nb, -1);
+
+    // ---- B_j (Sec. III-D, Eq. nonleafproduct)
+    Bj[l].resize(nc);
+    for (int64_t j = 0; j < nc; ++j) Bj[l][j] = pb.alloc(g, (int64_t)cA(l) * rB(l));
+    if (leaf) {
+      pb.begin();
+      for (int64_t j = 0; j < nc; ++j)
+        pb.gemm1(Bj[l][j], cA(l), rB(l), LS, cA(l), rB(l), rB(l), SF_TA, tA(A.Vc(j)), tB(B.Vr(j)));
+      pb.end("bprod", l);
+    } else {
+      std::vector<int64_t> tmp(2 * nc);
+      for (auto& x : tmp) x = pb.alloc(AR_S, (int64_t)cA(c) * rB(l));
+      pb.begin();
+      for (int64_t j = 0; j < nc; ++j)
+        for (int a = 0; a < 2; ++a)
+          pb.gemm1(tmp[2 * j + a], cA(c), rB(l), rB(c), rB(c), rB(l), rB(l), 0, Bj[c][2 * j + a],
+                   tB(B.Er(l, j) + (int64_t)a * rB(c) * rB(l)));
+      pb.end("bprod", l);
+      pb.begin();
+      for (int64_t j = 0; j < nc; ++j) {
+        std::vector<Item> it;
+        for (int a = 0; a < 2; ++a) it.push_back({tA(A.Ec(l, j) + (int64_t)a * cA(c) * cA(l)), tmp[2 * j + a]});
+        pb.gemm(Bj[l][j], cA(l), rB(l), cA(c), cA(l), rB(l), rB(l), SF_TA, it);
+      }
+      pb.end("bprod", l);
+    }
+
+    // ---- targets: where each summed coupling lives
+    for (auto& T : lt.tg) {
+      if (T.cls == TC_F) continue;
+      if (T.cls == TC_R) T.ssum = tC(C.S(l, bl[T.cpos].idx));
+      else if (T.cls == TC_NL) T.ssum = pb.alloc(AR_P, (int64_t)rC(l) * cC(l));
+      else T.ssum = pb.alloc(g, (int64_t)rC(l) * cC(l));
+    }
+    // R-block products of this level: T1 = S^A B_j, T2 = B_j S^B
+    std::vector<int64_t> T1(nb, -1), T2(nb, -1), PAS(nb, -1), SBP(nb, -1);
     Ahat[l].assign(nb, -1);
     Bhat[l].assign(nb, -1);
     for (int64_t p = 0; p < nb; ++p) {
-      Ahat[l][p] = pb.W((int64_t)rC(l) * rB(l));
-      Bhat[l][p] = pb.W((int64_t)cA(l) * cC(l));
-      if (bl[p].kind == KF) {
-        Y[p] = pb.W((int64_t)LS * rB(l));
-        Yb[p] = pb.W((int64_t)cA(l) * LS);
-        Q[p] = pb.W(LS2);
-        Rr[p] = pb.W(LS2);
-        Ach[p] = pb.W((int64_t)rC(l) * LS);
-        Bch[p] = pb.W((int64_t)LS * cC(l));
-      } else {
-        T1[p] = pb.W((int64_t)rA(l) * rB(l));
-        T2[p] = pb.W((int64_t)cA(l) * cB(l));
+      Ahat[l][p] = pb.alloc(g, (int64_t)rC(l) * rB(l));
+      Bhat[l][p] = pb.alloc(g, (int64_t)cA(l) * cC(l));
+      if (bl[p].kind == KR) {
+        T1[p] = pb.alloc(AR_S, (int64_t)rA(l) * rB(l));
+        T2[p] = pb.alloc(AR_S, (int64_t)cA(l) * cB(l));
+        PAS[p] = pb.alloc(AR_S, (int64_t)rC(l) * cA(l));
+        SBP[p] = pb.alloc(AR_S, (int64_t)rB(l) * cC(l));
       }
     }
-    std::vector<int64_t> G1r(nc, -1), G2r(nc, -1), G3r(nc), G1c(nc, -1), G2c(nc, -1), G3c(nc);
-    for (int64_t t = 0; t < nc; ++t) {
-      G3r[t] = pb.W(LS2);
-      G3c[t] = pb.W(LS2);
-    }
-    // which F blocks have a case-1 partner with an R/SUB target (for the Gram sums)
-    std::vector<std::vector<int64_t>> Ksets(nb), Isets(nb);  // Q of (j,k) per A-block; Rr of (i,j) per B-block
-    std::vector<std::vector<Item>> gF(lt.tg.size()), gZ(lt.tg.size()), gZp(lt.tg.size()), gZpp(lt.tg.size()),
-        g1(lt.tg.size()), g24(lt.tg.size()), g3(lt.tg.size());
-    std::vector<int64_t> Z(lt.tg.size(), -1), Zp(lt.tg.size(), -1), Zpp(lt.tg.size(), -1);
-    for (auto& tr : lt.trip) {
-      const Block &ba = bl[tr.pa], &bb = bl[tr.pb];
-      Target& T = lt.tg[tr.tgt];
-      if (T.cls == TC_F) {
-        if (ba.kind == KF && bb.kind == KF) gF[tr.tgt].push_back({tA(A.F(ba.idx)), tB(B.F(bb.idx))});
-        else if (ba.kind == KF) gZ[tr.tgt].push_back({Y[tr.pa], tB(B.S(l, bb.idx))});
-        else if (bb.kind == KF) gZp[tr.tgt].push_back({tA(A.S(l, ba.idx)), Yb[tr.pb]});
-        else gZpp[tr.tgt].push_back({T1[tr.pa], tB(B.S(l, bb.idx))});
-      } else {
-        if (ba.kind == KF && bb.kind == KF) {
-          Ksets[tr.pa].push_back(Q[tr.pb]);
-          Isets[tr.pb].push_back(Rr[tr.pa]);
-          g1[tr.tgt].push_back({Ach[tr.pa], Bch[tr.pb]});
-        } else if (bb.kind == KR) {
-          g24[tr.tgt].push_back({Ahat[l][tr.pa], tB(B.S(l, bb.idx))});
-        } else {
-          g3[tr.tgt].push_back({tA(A.S(l, ba.idx)), Bhat[l][tr.pb]});
-        }
-      }
-    }
-    for (size_t q = 0; q < lt.tg.size(); ++q) {
-      Target& T = lt.tg[q];
-      if (T.cls == TC_F) {
-        if (!gZ[q].empty()) Z[q] = pb.W((int64_t)LS * cB(l));
-        if (!gZp[q].empty()) Zp[q] = pb.W((int64_t)rA(l) * LS);
-        if (!gZpp[q].empty()) Zpp[q] = pb.W((int64_t)rA(l) * cB(l));
-        if (Zpp[q] >= 0 && Z[q] < 0) Z[q] = pb.W((int64_t)LS * cB(l));
-      } else {
-        T.ssum = T.cls == TC_R ? tC(C.S(l, bl[T.cpos].idx)) : pb.W((int64_t)rC(l) * cC(l));
-        if (!g24[q].empty()) T.s24 = pb.W((int64_t)rC(l) * cB(l));
-        if (!g3[q].empty()) T.s3 = pb.W((int64_t)rA(l) * cC(l));
-      }
-    }
-    for (int64_t p = 0; p < nb; ++p) {
-      if (!Ksets[p].empty()) {
-        Wsum[p] = pb.W(LS2);
-        YW[p] = pb.W(LS2);
-      }
-      if (!Isets[p].empty()) {
-        Wsc[p] = pb.W(LS2);
-        YWc[p] = pb.W(LS2);
-      }
-    }
-    // L1: per-block products
-    pb.begin();
-    for (int64_t p = 0; p < nb; ++p) {
-      const Block& b = bl[p];
-      if (b.kind == KF) {
-        pb.gemm1(Y[p], LS, rB(l), LS, LS, rB(l), rB(l), 0, tA(A.F(b.idx)), tB(B.Vr(b.s)));
-        pb.gemm1(Yb[p], cA(l), LS, LS, cA(l), LS, LS, SF_TA, tA(A.Vc(b.t)), tB(B.F(b.idx)));
-        pb.gemm1(Q[p], LS, LS, LS, LS, LS, LS, SF_TB, tB(B.F(b.idx)), tB(B.F(b.idx)));
-        pb.gemm1(Rr[p], LS, LS, LS, LS, LS, LS, SF_TA, tA(A.F(b.idx)), tA(A.F(b.idx)));
-      } else {
-        pb.gemm1(T1[p], rA(l), rB(l), cA(l), cA(l), rB(l), rB(l), 0, tA(A.S(l, b.idx)), Bj[l][b.s]);
-        pb.gemm1(T2[p], cA(l), cB(l), rB(l), rB(l), cB(l), cB(l), 0, Bj[l][b.t], tB(B.S(l, b.idx)));
-      }
-    }
-    for (int64_t t = 0; t < nc; ++t) {
-      pb.gemm1(G3r[t], LS, LS, rA(l), rA(l), rA(l), LS, SF_TB, tA(A.Vr(t)), tA(A.Vr(t)));
-      pb.gemm1(G3c[t], LS, LS, cB(l), cB(l), cB(l), LS, SF_TB, tB(B.Vc(t)), tB(B.Vc(t)));
-    }
-    pb.end("leaf_blockprod", l);
-    // L2: dense targets, Gram pieces
-    pb.begin();
-    for (size_t q = 0; q < lt.tg.size(); ++q) {
-      const Target& T = lt.tg[q];
-      if (T.cls != TC_F) continue;
-      int64_t fc = tC(C.F(bl[T.cpos].idx));
-      pb.gemm(fc, LS, LS, LS, LS, LS, LS, SF_ACC, gF[q]);
-      pb.gemm(Z[q], LS, cB(l), rB(l), rB(l), cB(l), cB(l), 0, gZ[q]);
-      pb.gemm(Zp[q], rA(l), LS, cA(l), cA(l), LS, LS, 0, gZp[q]);
-      pb.gemm(Zpp[q], rA(l), cB(l), rB(l), rB(l), cB(l), cB(l), 0, gZpp[q]);
-    }
-    for (int64_t p = 0; p < nb; ++p) {
-      pb.sum(Wsum[p], LS, LS, LS, LS, false, Ksets[p]);
-      pb.sum(Wsc[p], LS, LS, LS, LS, false, Isets[p]);
-    }
-    for (int64_t t = 0; t < nc; ++t) {
-      std::vector<Item> r2, c2;
-      for (int32_t p = st.row_ptr[l][t]; p < st.row_ptr[l][t + 1]; ++p)
-        if (bl[p].kind == KF) r2.push_back({Y[p], Y[p]});
-      for (int32_t q = st.col_ptr[l][t]; q < st.col_ptr[l][t + 1]; ++q) {
-        int32_t p = st.col_list[l][q];
-        if (bl[p].kind == KF) c2.push_back({Yb[p], Yb[p]});
-      }
-      if (!r2.empty()) {
-        G2r[t] = pb.W(LS2);
-        pb.gemm(G2r[t], LS, LS, rB(l), rB(l), rB(l), LS, SF_TB, r2);
-      }
-      if (!c2.empty()) {
-        G2c[t] = pb.W(LS2);
-        pb.gemm(G2c[t], LS, LS, cA(l), LS, LS, LS, SF_TA, c2);
-      }
-    }
-    pb.end("leaf_dense_gram", l);
-    // L3
-    pb.begin();
-    for (size_t q = 0; q < lt.tg.size(); ++q) {
-      const Target& T = lt.tg[q];
-      if (T.cls != TC_F || Zpp[q] < 0) continue;
-      pb.gemm1(Z[q], LS, cB(l), rA(l), rA(l), cB(l), cB(l), SF_ACC, tA(A.Vr(T.i)), Zpp[q]);
-    }
-    for (int64_t p = 0; p < nb; ++p) {
-      if (YW[p] >= 0) pb.gemm1(YW[p], LS, LS, LS, LS, LS, LS, 0, tA(A.F(bl[p].idx)), Wsum[p]);
-      if (YWc[p] >= 0) pb.gemm1(YWc[p], LS, LS, LS, LS, LS, LS, 0, Wsc[p], tB(B.F(bl[p].idx)));
-    }
-    pb.end("leaf_dense_gram", l);
-    // L4
-    pb.begin();
-    for (size_t q = 0; q < lt.tg.size(); ++q) {
-      const Target& T = lt.tg[q];
-      if (T.cls != TC_F || Z[q] < 0) continue;
-      pb.gemm1(tC(C.F(bl[T.cpos].idx)), LS, LS, cB(l), cB(l), cB(l), LS, SF_TB | SF_ACC, Z[q], tB(B.Vc(T.k)));
-    }
-    for (int64_t t = 0; t < nc; ++t) {
-      std::vector<Item> r1, c1;
-      for (int32_t p = st.row_ptr[l][t]; p < st.row_ptr[l][t + 1]; ++p)
-        if (YW[p] >= 0) r1.push_back({YW[p], tA(A.F(bl[p].idx))});
-      for (int32_t q = st.col_ptr[l][t]; q < st.col_ptr[l][t + 1]; ++q) {
-        int32_t p = st.col_list[l][q];
-        if (YWc[p] >= 0) c1.push_back({tB(B.F(bl[p].idx)), YWc[p]});
-      }
-      if (!r1.empty()) {
-        G1r[t] = pb.W(LS2);
-        pb.gemm(G1r[t], LS, LS, LS, LS, LS, LS, SF_TB, r1);
-      }
-      if (!c1.empty()) {
-        G1c[t] = pb.W(LS2);
-        pb.gemm(G1c[t], LS, LS, LS, LS, LS, LS, SF_TA, c1);
-      }
-    }
-    pb.end("leaf_dense_gram", l);
-    pb.begin();
-    for (size_t q = 0; q < lt.tg.size(); ++q) {
-      const Target& T = lt.tg[q];
-      if (T.cls != TC_F || Zp[q] < 0) continue;
-      pb.gemm1(tC(C.F(bl[T.cpos].idx)), LS, LS, rA(l), rA(l), LS, LS, SF_ACC, tA(A.Vr(T.i)), Zp[q]);
-    }
-    pb.end("leaf_dense", l);
-    // eig: new leaf bases
-    size_t e0 = P.eigs.size();
-    for (int64_t t = 0; t < nc; ++t) {
-      for (int col = 0; col < 2; ++col) {
-        EigTask e{};
-        e.g[0] = col ? G1c[t] : G1r[t];
-        e.g[1] = col ? G2c[t] : G2r[t];
-        e.g[2] = col ? G3c[t] : G3r[t];
-        e.out = tC(col ? C.Vc(t) : C.Vr(t));
-        e.rank_out = Structure::node(l, t);
-        e.child1 = e.child2 = -1;
-        e.nleaf = (int32_t)st.size[l][t];
-        e.n_pad = (int16_t)LS;
-        e.half = 0;
-        e.kcap = (int16_t)(col ? cC(l) : rC(l));
-        e.col = (int16_t)col;
-        P.eigs.push_back(e);
-      }
-    }
-    pb.eigs(e0, "eig", l);
-    // projections and collects
-    PA[l].resize(nc);
-    PB[l].resize(nc);
-    pb.begin();
-    for (int64_t t = 0; t < nc; ++t) {
-      PA[l][t] = pb.W((int64_t)rC(l) * rA(l));
-      PB[l][t] = pb.W((int64_t)cB(l) * cC(l));
-      pb.gemm1(PA[l][t], rC(l), rA(l), LS, rC(l), rA(l), rA(l), SF_TA, tC(C.Vr(t)), tA(A.Vr(t)));
-      pb.gemm1(PB[l][t], cB(l), cC(l), LS, cB(l), cC(l), cC(l), SF_TA, tB(B.Vc(t)), tC(C.Vc(t)));
-    }
-    for (int64_t p = 0; p < nb; ++p) {
-      const Block& b = bl[p];
-      if (b.kind != KF) continue;
-      pb.gemm1(Ahat[l][p], rC(l), rB(l), LS, rC(l), rB(l), rB(l), SF_TA, tC(C.Vr(b.t)), Y[p]);
-      pb.gemm1(Bhat[l][p], cA(l), cC(l), LS, LS, cC(l), cC(l), 0, Yb[p], tC(C.Vc(b.s)));
-      pb.gemm1(Ach[p], rC(l), LS, LS, rC(l), LS, LS, SF_TA, tC(C.Vr(b.t)), tA(A.F(b.idx)));
-      pb.gemm1(Bch[p], LS, cC(l), LS, LS, cC(l), cC(l), 0, tB(B.F(b.idx)), tC(C.Vc(b.s)));
-    }
-    pb.end("leaf_proj", l);
     pb.begin();
     for (int64_t p = 0; p < nb; ++p) {
       const Block& b = bl[p];
       if (b.kind != KR) continue;
-      pb.gemm1(Ahat[l][p], rC(l), rB(l), rA(l), rA(l), rB(l), rB(l), 0, PA[l][b.t], T1[p]);
-      pb.gemm1(Bhat[l][p], cA(l), cC(l), cB(l), cB(l), cC(l), cC(l), 0, T2[p], PB[l][b.s]);
+      pb.gemm1(T1[p], rA(l), rB(l), cA(l), cA(l), rB(l), rB(l), 0, tA(A.S(l, b.idx)), Bj[l][b.s]);
+      pb.gemm1(T2[p], cA(l), cB(l), rB(l), rB(l), cB(l), cB(l), 0, Bj[l][b.t], tB(B.S(l, b.idx)));
     }
-    for (size_t q = 0; q < lt.tg.size(); ++q) {
-      const Target& T = lt.tg[q];
-      if (T.cls == TC_F) continue;
-      pb.gemm(T.ssum, rC(l), cC(l), LS, LS, cC(l), cC(l), SF_ACC, g1[q]);
-    }
-    pb.end("leaf_coup", l);
-    pb.begin();
-    for (size_t q = 0; q < lt.tg.size(); ++q) {
-      const Target& T = lt.tg[q];
-      if (T.cls == TC_F) continue;
-      pb.gemm(T.s24, rC(l), cB(l), rB(l), rB(l), cB(l), cB(l), 0, g24[q]);
-      pb.gemm(T.s3, rA(l), cC(l), cA(l), cA(l), cC(l), cC(l), 0, g3[q]);
-    }
-    pb.end("leaf_coup", l);
-    pb.begin();
-    for (auto& T : lt.tg)
-      if (T.cls != TC_F && T.s24 >= 0)
-        pb.gemm1(T.ssum, rC(l), cC(l), cB(l), cB(l), cC(l), cC(l), SF_ACC, T.s24, PB[l][T.k]);
-    pb.end("leaf_coup", l);
-    pb.begin();
-    for (auto& T : lt.tg)
-      if (T.cls != TC_F && T.s3 >= 0)
-        pb.gemm1(T.ssum, rC(l), cC(l), rA(l), rA(l), cC(l), cC(l), SF_ACC, PA[l][T.i], T.s3);
-    pb.end("leaf_coup", l);
-  }
+    pb.end("rprod", l);
 
-  // ================================================== non-leaf levels (Sec. IV)
-  for (int l = L - 1; l >= lmin; --l) {
-    const int c = l + 1;
-    LevelTargets& lt = LT[l];
-    enumerate(st, l, lt);
-    const auto& bl = st.blocks[l];
-    const int64_t nb = (int64_t)bl.size(), nc = 1LL << l;
-    const int hr = rC(c), hc = cC(c);  // child caps of C
-    std::vector<int64_t> Ac(nb, -1), Bc(nb, -1), Yn(nb, -1), Ybn(nb, -1), T1(nb, -1), T2(nb, -1);
-    Ahat[l].assign(nb, -1);
-    Bhat[l].assign(nb, -1);
-    for (int64_t p = 0; p < nb; ++p) {
-      Ahat[l][p] = pb.W((int64_t)rC(l) * rB(l));
-      Bhat[l][p] = pb.W((int64_t)cA(l) * cC(l));
-      if (bl[p].kind == KNL) {
-        Ac[p] = pb.W((int64_t)2 * hr * 2 * rB(c));
-        Bc[p] = pb.W((int64_t)2 * cA(c) * 2 * hc);
-        Yn[p] = pb.W((int64_t)2 * hr * rB(l));
-        Ybn[p] = pb.W((int64_t)cA(l) * 2 * hc);
-      } else if (bl[p].kind == KR) {
-        T1[p] = pb.W((int64_t)rA(l) * rB(l));
-        T2[p] = pb.W((int64_t)cA(l) * cB(l));
+    // Gram matrices of the new bases (row: gr x gr, column: gc x gc)
+    const int gr = leaf ? LS : 2 * rC(c), gc = leaf ? LS : 2 * cC(c);
+    std::vector<int64_t> G1r(nc, -1), G2r(nc, -1), G3r(nc, -1), G1c(nc, -1), G2c(nc, -1), G3c(nc, -1);
+    // per-block factors reused after the eigen step
+    std::vector<int64_t> Y(nb, -1), Yb(nb, -1), Ach(nb, -1), Bch(nb, -1), Wr(nc, -1), Wc(nc, -1);
+    std::vector<int64_t> Mt(lt.tg.size(), -1);
+
+    if (leaf) {
+      // ===================================================== leaf level (Sec. III)
+      std::vector<int64_t> Q(nb, -1), Rr(nb, -1), Wsum(nb, -1), Wsc(nb, -1);
+      for (int64_t p = 0; p < nb; ++p)
+        if (bl[p].kind == KF) {
+          Y[p] = pb.alloc(AR_S, (int64_t)LS * rB(l));
+          Yb[p] = pb.alloc(AR_S, (int64_t)cA(l) * LS);
+          Q[p] = pb.alloc(AR_S, LS2);   // F F^T, later F W, later V^C^T F
+          Rr[p] = pb.alloc(AR_S, LS2);  // F^T F, later W F, later F V^C
+        }
+      std::vector<std::vector<int64_t>> Ksets(nb), Isets(nb);
+      std::vector<std::vector<Item>> gF(lt.tg.size()), gZ(lt.tg.size()), gZp(lt.tg.size()), gZpp(lt.tg.size()),
+          g1(lt.tg.size());
+      std::vector<int64_t> Z(lt.tg.size(), -1), Zp(lt.tg.size(), -1), Zpp(lt.tg.size(), -1);
+      for (auto& tr : lt.trip) {
+        const Block &ba = bl[tr.pa], &bb = bl[tr.pb];
+        const Target& T = lt.tg[tr.tgt];
+        if (T.cls == TC_F) {
+          if (ba.kind == KF && bb.kind == KF) gF[tr.tgt].push_back({tA(A.F(ba.idx)), tB(B.F(bb.idx))});
+          else if (ba.kind == KF) gZ[tr.tgt].push_back({Y[tr.pa], tB(B.S(l, bb.idx))});
+          else if (bb.kind == KF) gZp[tr.tgt].push_back({tA(A.S(l, ba.idx)), Yb[tr.pb]});
+          else gZpp[tr.tgt].push_back({T1[tr.pa], tB(B.S(l, bb.idx))});
+        } else if (ba.kind == KF && bb.kind == KF) {
+          Ksets[tr.pa].push_back(Q[tr.pb]);
+          Isets[tr.pb].push_back(Rr[tr.pa]);
+          g1[tr.tgt].push_back({Q[tr.pa], Rr[tr.pb]});  // (V^C_i^T F_ij)(F_jk V^C_k) after the eig
+        }
       }
-    }
-    // targets
-    std::vector<std::vector<Item>> g24(lt.tg.size()), g3(lt.tg.size());
-    for (auto& tr : lt.trip) {
-      const Block &ba = bl[tr.pa], &bb = bl[tr.pb];
-      if (ba.kind == KNL && bb.kind == KNL) continue;
-      if (bb.kind == KR) g24[tr.tgt].push_back({Ahat[l][tr.pa], tB(B.S(l, bb.idx))});
-      else g3[tr.tgt].push_back({tA(A.S(l, ba.idx)), Bhat[l][tr.pb]});
-    }
-    for (size_t q = 0; q < lt.tg.size(); ++q) {
-      Target& T = lt.tg[q];
-      if (T.cls == TC_F) throw Error(H2_EINTERNAL, "dense target above the leaf level");
-      T.ssum = T.cls == TC_R ? tC(C.S(l, bl[T.cpos].idx)) : pb.W((int64_t)rC(l) * cC(l));
-      if (!g24[q].empty()) T.s24 = pb.W((int64_t)rC(l) * cB(l));
-      if (!g3[q].empty()) T.s3 = pb.W((int64_t)rA(l) * cC(l));
-      if (T.has_nlnl && T.cls != TC_NL) {
-        T.M = pb.W((int64_t)2 * hr * 2 * hc);
-        T.Mt = pb.W((int64_t)2 * hr * cC(l));
+      for (size_t q = 0; q < lt.tg.size(); ++q) {
+        if (lt.tg[q].cls != TC_F) continue;
+        if (!gZ[q].empty() || !gZpp[q].empty()) Z[q] = pb.alloc(AR_S, (int64_t)LS * cB(l));
+        if (!gZp[q].empty()) Zp[q] = pb.alloc(AR_S, (int64_t)rA(l) * LS);
+        if (!gZpp[q].empty()) Zpp[q] = pb.alloc(AR_S, (int64_t)rA(l) * cB(l));
       }
-    }
-    // N1: assemble collected NL blocks and merged couplings; R-block products
-    pb.begin();
-    for (int64_t p = 0; p < nb; ++p) {
-      const Block& b = bl[p];
-      if (b.kind == KNL) {
+      for (int64_t p = 0; p < nb; ++p) {
+        if (!Ksets[p].empty()) Wsum[p] = pb.alloc(AR_S, LS2);
+        if (!Isets[p].empty()) Wsc[p] = pb.alloc(AR_S, LS2);
+      }
+      for (int64_t t = 0; t < nc; ++t) {
+        G3r[t] = pb.alloc(AR_S, LS2);
+        G3c[t] = pb.alloc(AR_S, LS2);
+      }
+      // L1: per-block products
+      pb.begin();
+      for (int64_t p = 0; p < nb; ++p) {
+        const Block& b = bl[p];
+        if (b.kind != KF) continue;
+        pb.gemm1(Y[p], LS, rB(l), LS, LS, rB(l), rB(l), 0, tA(A.F(b.idx)), tB(B.Vr(b.s)));
+        pb.gemm1(Yb[p], cA(l), LS, LS, cA(l), LS, LS, SF_TA, tA(A.Vc(b.t)), tB(B.F(b.idx)));
+        pb.gemm1(Q[p], LS, LS, LS, LS, LS, LS, SF_TB, tB(B.F(b.idx)), tB(B.F(b.idx)));
+        pb.gemm1(Rr[p], LS, LS, LS, LS, LS, LS, SF_TA, tA(A.F(b.idx)), tA(A.F(b.idx)));
+      }
+      for (int64_t t = 0; t < nc; ++t) {
+        pb.gemm1(G3r[t], LS, LS, rA(l), rA(l), rA(l), LS, SF_TB, tA(A.Vr(t)), tA(A.Vr(t)));
+        pb.gemm1(G3c[t], LS, LS, cB(l), cB(l), cB(l), LS, SF_TB, tB(B.Vc(t)), tB(B.Vc(t)));
+      }
+      pb.end("leaf_blockprod", l);
+      // L2: dense targets (Sec. III-A) and Gram pieces
+      pb.begin();
+      for (size_t q = 0; q < lt.tg.size(); ++q) {
+        const Target& T = lt.tg[q];
+        if (T.cls != TC_F) continue;
+        pb.gemm(tC(C.F(bl[T.cpos].idx)), LS, LS, LS, LS, LS, LS, SF_ACC, gF[q]);
+        pb.gemm(Z[q], LS, cB(l), rB(l), rB(l), cB(l), cB(l), 0, gZ[q]);
+        pb.gemm(Zp[q], rA(l), LS, cA(l), cA(l), LS, LS, 0, gZp[q]);
+        pb.gemm(Zpp[q], rA(l), cB(l), rB(l), rB(l), cB(l), cB(l), 0, gZpp[q]);
+      }
+      for (int64_t p = 0; p < nb; ++p) {
+        pb.sum(Wsum[p], LS, LS, LS, LS, false, Ksets[p]);
+        pb.sum(Wsc[p], LS, LS, LS, LS, false, Isets[p]);
+      }
+      for (int64_t t = 0; t < nc; ++t) {
+        std::vector<Item> r2, c2;
+        for (int32_t p = st.row_ptr[l][t]; p < st.row_ptr[l][t + 1]; ++p)
+          if (bl[p].kind == KF) r2.push_back({Y[p], Y[p]});
+        for (int32_t q = st.col_ptr[l][t]; q < st.col_ptr[l][t + 1]; ++q) {
+          int32_t p = st.col_list[l][q];
+          if (bl[p].kind == KF) c2.push_back({Yb[p], Yb[p]});
+        }
+        if (!r2.empty()) {
+          G2r[t] = pb.alloc(AR_S, LS2);
+          pb.gemm(G2r[t], LS, LS, rB(l), rB(l), rB(l), LS, SF_TB, r2);  // Eq. Gr2L
+        }
+        if (!c2.empty()) {
+          G2c[t] = pb.alloc(AR_S, LS2);
+          pb.gemm(G2c[t], LS, LS, cA(l), LS, LS, LS, SF_TA, c2);  // Eq. case2-ch
+        }
+      }
+      pb.end("leaf_dense_gram", l);
+      // L3: Z += V^A_i Z''; F W and W F (into the storage of F F^T, F^T F)
+      pb.begin();
+      for (size_t q = 0; q < lt.tg.size(); ++q) {
+        const Target& T = lt.tg[q];
+        if (T.cls == TC_F && Zpp[q] >= 0)
+          pb.gemm1(Z[q], LS, cB(l), rA(l), rA(l), cB(l), cB(l), SF_ACC, tA(A.Vr(T.i)), Zpp[q]);
+      }
+      for (int64_t p = 0; p < nb; ++p) {
+        if (Wsum[p] >= 0) pb.gemm1(Q[p], LS, LS, LS, LS, LS, LS, 0, tA(A.F(bl[p].idx)), Wsum[p]);
+        if (Wsc[p] >= 0) pb.gemm1(Rr[p], LS, LS, LS, LS, LS, LS, 0, Wsc[p], tB(B.F(bl[p].idx)));
+      }
+      pb.end("leaf_dense_gram", l);
+      // L4: Eq. Gr1L / case1-ch regrouped; dense targets, F += Z V^B_k^T
+      pb.begin();
+      for (size_t q = 0; q < lt.tg.size(); ++q) {
+        const Target& T = lt.tg[q];
+        if (T.cls == TC_F && Z[q] >= 0)
+          pb.gemm1(tC(C.F(bl[T.cpos].idx)), LS, LS, cB(l), cB(l), cB(l), LS, SF_TB | SF_ACC, Z[q], tB(B.Vc(T.k)));
+      }
+      for (int64_t t = 0; t < nc; ++t) {
+        std::vector<Item> r1, c1;
+        for (int32_t p = st.row_ptr[l][t]; p < st.row_ptr[l][t + 1]; ++p)
+          if (Wsum[p] >= 0) r1.push_back({Q[p], tA(A.F(bl[p].idx))});
+        for (int32_t q = st.col_ptr[l][t]; q < st.col_ptr[l][t + 1]; ++q) {
+          int32_t p = st.col_list[l][q];
+          if (Wsc[p] >= 0) c1.push_back({tB(B.F(bl[p].idx)), Rr[p]});
+        }
+        if (!r1.empty()) {
+          G1r[t] = pb.alloc(AR_S, LS2);
+          pb.gemm(G1r[t], LS, LS, LS, LS, LS, LS, SF_TB, r1);
+        }
+        if (!c1.empty()) {
+          G1c[t] = pb.alloc(AR_S, LS2);
+          pb.gemm(G1c[t], LS, LS, LS, LS, LS, LS, SF_TA, c1);
+        }
+      }
+      pb.end("leaf_dense_gram", l);
+      pb.begin();
+      for (size_t q = 0; q < lt.tg.size(); ++q) {
+        const Target& T = lt.tg[q];
+        if (T.cls == TC_F && Zp[q] >= 0)
+          pb.gemm1(tC(C.F(bl[T.cpos].idx)), LS, LS, rA(l), rA(l), LS, LS, SF_ACC, tA(A.Vr(T.i)), Zp[q]);
+      }
+      pb.end("leaf_dense", l);
+      // case-1 couplings after the eig reuse Q (as V^C_i^T F_ij) and Rr (as F_jk V^C_k)
+      for (int64_t p = 0; p < nb; ++p) {
+        Ach[p] = Q[p];
+        Bch[p] = Rr[p];
+      }
+      for (size_t q = 0; q < lt.tg.size(); ++q) lt.tg[q].g1 = std::move(g1[q]);
+    } else {
+      // ================================================ non-leaf level (Sec. IV)
+      std::vector<int64_t> Ac(nb, -1), Bc(nb, -1);
+      for (int64_t p = 0; p < nb; ++p)
+        if (bl[p].kind == KNL) {
+          Ac[p] = pb.alloc(AR_S, (int64_t)gr * 2 * rB(c));
+          Bc[p] = pb.alloc(AR_S, (int64_t)2 * cA(c) * gc);
+          Y[p] = pb.alloc(AR_S, (int64_t)gr * rB(l));
+          Yb[p] = pb.alloc(AR_S, (int64_t)cA(l) * gc);
+        }
+      // steps 1-2: collected NL blocks of A and B (Eq. nonleafA / nonleafB)
+      pb.begin();
+      const int hr = rC(c), hc = cC(c);
+      for (int64_t p = 0; p < nb; ++p) {
+        const Block& b = bl[p];
+        if (b.kind != KNL) continue;
         for (int a = 0; a < 2; ++a)
           for (int bb = 0; bb < 2; ++bb) {
             int32_t cp = st.find(c, 2 * b.t + a, 2 * b.s + bb);
             if (cp < 0) throw Error(H2_EINTERNAL, "missing child block");
             pb.sum(Ac[p] + (int64_t)a * hr * 2 * rB(c) + (int64_t)bb * rB(c), hr, rB(c), rB(c), 2 * rB(c), false,
                    {Ahat[c][cp]});
-            pb.sum(Bc[p] + (int64_t)a * cA(c) * 2 * hc + (int64_t)bb * hc, cA(c), hc, hc, 2 * hc, false, {Bhat[c][cp]});
+            pb.sum(Bc[p] + (int64_t)a * cA(c) * gc + (int64_t)bb * hc, cA(c), hc, hc, gc, false, {Bhat[c][cp]});
           }
-      } else if (b.kind == KR) {
-        pb.gemm1(T1[p], rA(l), rB(l), cA(l), cA(l), rB(l), rB(l), 0, tA(A.S(l, b.idx)), Bj[l][b.s]);
-        pb.gemm1(T2[p], cA(l), cB(l), rB(l), rB(l), cB(l), cB(l), 0, Bj[l][b.t], tB(B.S(l, b.idx)));
       }
-    }
-    for (auto& T : lt.tg) {
-      if (T.M < 0) continue;
-      for (int a = 0; a < 2; ++a)
-        for (int bb = 0; bb < 2; ++bb) {
-          auto it = LT[c].id.find(Structure::key(2 * T.i + a, 2 * T.k + bb));
-          if (it == LT[c].id.end()) throw Error(H2_EINTERNAL, "missing child target");
-          pb.sum(T.M + (int64_t)a * hr * 2 * hc + (int64_t)bb * hc, hr, hc, hc, 2 * hc, false,
-                 {LT[c].tg[it->second].ssum});
+      pb.end("collect", l);
+      // Gram factors: Y = (NL^A)_coll E^B_j, Yb = (E^A_j)^T (NL^B)_coll, W = P_ch E
+      for (int64_t t = 0; t < nc; ++t) {
+        Wr[t] = pb.alloc(AR_S, (int64_t)gr * rA(l));
+        Wc[t] = pb.alloc(AR_S, (int64_t)gc * cB(l));
+        G3r[t] = pb.alloc(AR_S, (int64_t)gr * gr);
+        G3c[t] = pb.alloc(AR_S, (int64_t)gc * gc);
+      }
+      pb.begin();
+      for (int64_t p = 0; p < nb; ++p) {
+        const Block& b = bl[p];
+        if (b.kind != KNL) continue;
+        pb.gemm1(Y[p], gr, rB(l), 2 * rB(c), 2 * rB(c), rB(l), rB(l), 0, Ac[p], tB(B.Er(l, b.s)));
+        pb.gemm1(Yb[p], cA(l), gc, 2 * cA(c), cA(l), gc, gc, SF_TA, tA(A.Ec(l, b.t)), Bc[p]);
+      }
+      for (int64_t t = 0; t < nc; ++t)
+        for (int a = 0; a < 2; ++a) {
+          pb.gemm1(Wr[t] + (int64_t)a * hr * rA(l), hr, rA(l), rA(c), rA(c), rA(l), rA(l), 0, PA[c][2 * t + a],
+                   tA(A.Er(l, t) + (int64_t)a * rA(c) * rA(l)));
+          pb.gemm1(Wc[t] + (int64_t)a * hc * cB(l), hc, cB(l), cB(c), hc, cB(l), cB(l), SF_TA, PB[c][2 * t + a],
+                   tB(B.Ec(l, t) + (int64_t)a * cB(c) * cB(l)));
         }
+      // Eq. case1-ch-nl from the children's summed couplings, without assembling M:
+      // block (a, a') of G1r_i = sum over targets (i, k), b of S_{ia,kb} S_{ia',kb}^T
+      std::vector<std::vector<std::pair<int32_t, int32_t>>> trow(nc), tcol(nc);  // (target, -) per i / per k
+      for (size_t q = 0; q < lt.tg.size(); ++q) {
+        const Target& T = lt.tg[q];
+        if (!T.has_nlnl || T.cls == TC_NL) continue;
+        trow[T.i].push_back({(int32_t)q, 0});
+        tcol[T.k].push_back({(int32_t)q, 0});
+      }
+      auto child_ssum = [&](const Target& T, int a, int b) {
+        auto it = LT[c].id.find(Structure::key(2 * T.i + a, 2 * T.k + b));
+        if (it == LT[c].id.end()) throw Error(H2_EINTERNAL, "missing child target");
+        return LT[c].tg[it->second].ssum;
+      };
+      for (int64_t t = 0; t < nc; ++t) {
+        if (!trow[t].empty()) {
+          G1r[t] = pb.alloc(AR_S, (int64_t)gr * gr);
+          for (int a = 0; a < 2; ++a)
+            for (int a2 = 0; a2 < 2; ++a2) {
+              std::vector<Item> it;
+              for (auto& tq : trow[t])
+                for (int b = 0; b < 2; ++b)
+                  it.push_back({child_ssum(lt.tg[tq.first], a, b), child_ssum(lt.tg[tq.first], a2, b)});
+              pb.gemm(G1r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr, hr, hr, hc, hc, hc, gr, SF_TB, it);
+            }
+        }
+        if (!tcol[t].empty()) {
+          G1c[t] = pb.alloc(AR_S, (int64_t)gc * gc);
+          for (int b = 0; b < 2; ++b)
+            for (int b2 = 0; b2 < 2; ++b2) {
+              std::vector<Item> it;
+              for (auto& tq : tcol[t])
+                for (int a = 0; a < 2; ++a)
+                  it.push_back({child_ssum(lt.tg[tq.first], a, b), child_ssum(lt.tg[tq.first], a, b2)});
+              pb.gemm(G1c[t] + (int64_t)b * hc * gc + (int64_t)b2 * hc, hc, hc, hr, hc, hc, gc, SF_TA, it);
+            }
+        }
+      }
+      pb.end("nl_gram", l);
+      pb.begin();
+      for (int64_t t = 0; t < nc; ++t) {
+        std::vector<Item> r2, c2;
+        for (int32_t p = st.row_ptr[l][t]; p < st.row_ptr[l][t + 1]; ++p)
+          if (bl[p].kind == KNL) r2.push_back({Y[p], Y[p]});
+        for (int32_t q = st.col_ptr[l][t]; q < st.col_ptr[l][t + 1]; ++q) {
+          int32_t p = st.col_list[l][q];
+          if (bl[p].kind == KNL) c2.push_back({Yb[p], Yb[p]});
+        }
+        if (!r2.empty()) {
+          G2r[t] = pb.alloc(AR_S, (int64_t)gr * gr);
+          pb.gemm(G2r[t], gr, gr, rB(l), rB(l), rB(l), gr, SF_TB, r2);  // Eq. case2-ch-nl
+        }
+        if (!c2.empty()) {
+          G2c[t] = pb.alloc(AR_S, (int64_t)gc * gc);
+          pb.gemm(G2c[t], gc, gc, cA(l), gc, gc, gc, SF_TA, c2);
+        }
+        pb.gemm1(G3r[t], gr, gr, rA(l), rA(l), rA(l), gr, SF_TB, Wr[t], Wr[t]);  // Eq. case3-ch-nl
+        pb.gemm1(G3c[t], gc, gc, cB(l), cB(l), cB(l), gc, SF_TB, Wc[t], Wc[t]);
+      }
+      pb.end("nl_gram", l);
+      for (size_t q = 0; q < lt.tg.size(); ++q)
+        if (lt.tg[q].has_nlnl && lt.tg[q].cls != TC_NL) Mt[q] = pb.alloc(AR_S, (int64_t)gr * cC(l));
     }
-    pb.end("merge", l);
-    // N2: Gram factors
-    std::vector<int64_t> Wr(nc), Wc(nc);
-    pb.begin();
-    for (int64_t p = 0; p < nb; ++p) {
-      const Block& b = bl[p];
-      if (b.kind != KNL) continue;
-      pb.gemm1(Yn[p], 2 * hr, rB(l), 2 * rB(c), 2 * rB(c), rB(l), rB(l), 0, Ac[p], tB(B.Er(l, b.s)));
-      pb.gemm1(Ybn[p], cA(l), 2 * hc, 2 * cA(c), cA(l), 2 * hc, 2 * hc, SF_TA, tA(A.Ec(l, b.t)), Bc[p]);
-    }
-    for (int64_t t = 0; t < nc; ++t) {
-      Wr[t] = pb.W((int64_t)2 * hr * rA(l));
-      Wc[t] = pb.W((int64_t)2 * hc * cB(l));
-      for (int a = 0; a < 2; ++a) {
-        pb.gemm1(Wr[t] + (int64_t)a * hr * rA(l), hr, rA(l), rA(c), rA(c), rA(l), rA(l), 0, PA[c][2 * t + a],
-                 tA(A.Er(l, t) + (int64_t)a * rA(c) * rA(l)));
-        pb.gemm1(Wc[t] + (int64_t)a * hc * cB(l), hc, cB(l), cB(c), hc, cB(l), cB(l), SF_TA, PB[c][2 * t + a],
-                 tB(B.Ec(l, t) + (int64_t)a * cB(c) * cB(l)));
-      }
-    }
-    pb.end("nl_gram", l);
-    // N3: Grams
-    const int gr = 2 * hr, gc = 2 * hc;
-    std::vector<int64_t> G1r(nc, -1), G2r(nc, -1), G3r(nc), G1c(nc, -1), G2c(nc, -1), G3c(nc);
-    std::vector<std::vector<Item>> r1(nc), c1(nc);
-    for (auto& T : lt.tg)
-      if (T.M >= 0) {
-        r1[T.i].push_back({T.M, T.M});
-        c1[T.k].push_back({T.M, T.M});
-      }
-    pb.begin();
-    for (int64_t t = 0; t < nc; ++t) {
-      std::vector<Item> r2, c2;
-      for (int32_t p = st.row_ptr[l][t]; p < st.row_ptr[l][t + 1]; ++p)
-        if (bl[p].kind == KNL) r2.push_back({Yn[p], Yn[p]});
-      for (int32_t q = st.col_ptr[l][t]; q < st.col_ptr[l][t + 1]; ++q) {
-        int32_t p = st.col_list[l][q];
-        if (bl[p].kind == KNL) c2.push_back({Ybn[p], Ybn[p]});
-      }
-      if (!r1[t].empty()) {
-        G1r[t] = pb.W((int64_t)gr * gr);
-        pb.gemm(G1r[t], gr, gr, gc, gc, gc, gr, SF_TB, r1[t]);
-      }
-      if (!c1[t].empty()) {
-        G1c[t] = pb.W((int64_t)gc * gc);
-        pb.gemm(G1c[t], gc, gc, gr, gc, gc, gc, SF_TA, c1[t]);
-      }
-      if (!r2.empty()) {
-        G2r[t] = pb.W((int64_t)gr * gr);
-        pb.gemm(G2r[t], gr, gr, rB(l), rB(l), rB(l), gr, SF_TB, r2);
-      }
-      if (!c2.empty()) {
-        G2c[t] = pb.W((int64_t)gc * gc);
-        pb.gemm(G2c[t], gc, gc, cA(l), gc, gc, gc, SF_TA, c2);
-      }
-      G3r[t] = pb.W((int64_t)gr * gr);
-      G3c[t] = pb.W((int64_t)gc * gc);
-      pb.gemm1(G3r[t], gr, gr, rA(l), rA(l), rA(l), gr, SF_TB, Wr[t], Wr[t]);
-      pb.gemm1(G3c[t], gc, gc, cB(l), cB(l), cB(l), gc, SF_TB, Wc[t], Wc[t]);
-    }
-    pb.end("nl_gram", l);
+
+    // ---- eig: new leaf bases / stacked transfer matrices of C
     size_t e0 = P.eigs.size();
     for (int64_t t = 0; t < nc; ++t)
       for (int col = 0; col < 2; ++col) {
@@ -629,137 +549,180 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         e.g[0] = col ? G1c[t] : G1r[t];
         e.g[1] = col ? G2c[t] : G2r[t];
         e.g[2] = col ? G3c[t] : G3r[t];
-        e.out = tC(col ? C.Ec(l, t) : C.Er(l, t));
+        e.out = tC(leaf ? (col ? C.Vc(t) : C.Vr(t)) : (col ? C.Ec(l, t) : C.Er(l, t)));
         e.rank_out = Structure::node(l, t);
-        e.child1 = Structure::node(c, 2 * t);
-        e.child2 = Structure::node(c, 2 * t + 1);
-        e.nleaf = 0;
+        e.child1 = leaf ? -1 : Structure::node(c, 2 * t);
+        e.child2 = leaf ? -1 : Structure::node(c, 2 * t + 1);
+        e.nleaf = leaf ? (int32_t)st.size[l][t] : 0;
         e.n_pad = (int16_t)(col ? gc : gr);
-        e.half = (int16_t)(col ? hc : hr);
+        e.half = leaf ? 0 : (int16_t)(col ? cC(c) : rC(c));
         e.kcap = (int16_t)(col ? cC(l) : rC(l));
         e.col = (int16_t)col;
         P.eigs.push_back(e);
       }
     pb.eigs(e0, "eig", l);
-    // N4: projections, NL collects, case-1 half products
+
+    // ---- projections (Eq. leafproj / nonleafproj) and collects (Eq. Fcollect, NLcollect)
     PA[l].resize(nc);
     PB[l].resize(nc);
+    for (int64_t t = 0; t < nc; ++t) {
+      PA[l][t] = pb.alloc(g, (int64_t)rC(l) * rA(l));
+      PB[l][t] = pb.alloc(g, (int64_t)cB(l) * cC(l));
+    }
     pb.begin();
     for (int64_t t = 0; t < nc; ++t) {
-      PA[l][t] = pb.W((int64_t)rC(l) * rA(l));
-      PB[l][t] = pb.W((int64_t)cB(l) * cC(l));
-      pb.gemm1(PA[l][t], rC(l), rA(l), gr, rC(l), rA(l), rA(l), SF_TA, tC(C.Er(l, t)), Wr[t]);
-      pb.gemm1(PB[l][t], cB(l), cC(l), gc, cB(l), cC(l), cC(l), SF_TA, Wc[t], tC(C.Ec(l, t)));
+      if (leaf) {
+        pb.gemm1(PA[l][t], rC(l), rA(l), LS, rC(l), rA(l), rA(l), SF_TA, tC(C.Vr(t)), tA(A.Vr(t)));
+        pb.gemm1(PB[l][t], cB(l), cC(l), LS, cB(l), cC(l), cC(l), SF_TA, tB(B.Vc(t)), tC(C.Vc(t)));
+      } else {
+        pb.gemm1(PA[l][t], rC(l), rA(l), gr, rC(l), rA(l), rA(l), SF_TA, tC(C.Er(l, t)), Wr[t]);
+        pb.gemm1(PB[l][t], cB(l), cC(l), gc, cB(l), cC(l), cC(l), SF_TA, Wc[t], tC(C.Ec(l, t)));
+      }
     }
     for (int64_t p = 0; p < nb; ++p) {
       const Block& b = bl[p];
-      if (b.kind != KNL) continue;
-      pb.gemm1(Ahat[l][p], rC(l), rB(l), gr, rC(l), rB(l), rB(l), SF_TA, tC(C.Er(l, b.t)), Yn[p]);
-      pb.gemm1(Bhat[l][p], cA(l), cC(l), gc, gc, cC(l), cC(l), 0, Ybn[p], tC(C.Ec(l, b.s)));
+      if (leaf && b.kind == KF) {
+        pb.gemm1(Ahat[l][p], rC(l), rB(l), LS, rC(l), rB(l), rB(l), SF_TA, tC(C.Vr(b.t)), Y[p]);
+        pb.gemm1(Bhat[l][p], cA(l), cC(l), LS, LS, cC(l), cC(l), 0, Yb[p], tC(C.Vc(b.s)));
+        pb.gemm1(Ach[p], rC(l), LS, LS, rC(l), LS, LS, SF_TA, tC(C.Vr(b.t)), tA(A.F(b.idx)));
+        pb.gemm1(Bch[p], LS, cC(l), LS, LS, cC(l), cC(l), 0, tB(B.F(b.idx)), tC(C.Vc(b.s)));
+      } else if (!leaf && b.kind == KNL) {
+        pb.gemm1(Ahat[l][p], rC(l), rB(l), gr, rC(l), rB(l), rB(l), SF_TA, tC(C.Er(l, b.t)), Y[p]);
+        pb.gemm1(Bhat[l][p], cA(l), cC(l), gc, gc, cC(l), cC(l), 0, Yb[p], tC(C.Ec(l, b.s)));
+      }
     }
-    for (auto& T : lt.tg)
-      if (T.M >= 0) pb.gemm1(T.Mt, gr, cC(l), gc, gc, cC(l), cC(l), 0, T.M, tC(C.Ec(l, T.k)));
-    pb.end("nl_proj", l);
-    // N5
+    if (!leaf) {
+      // M E^C_k from the children's sums: half a = sum_b S_{ia,kb} T^C_{kb}
+      const int hr = rC(c), hc = cC(c);
+      for (size_t q = 0; q < lt.tg.size(); ++q) {
+        if (Mt[q] < 0) continue;
+        const Target& T = lt.tg[q];
+        for (int a = 0; a < 2; ++a) {
+          std::vector<Item> it;
+          for (int b = 0; b < 2; ++b) {
+            auto f = LT[c].id.find(Structure::key(2 * T.i + a, 2 * T.k + b));
+            it.push_back({LT[c].tg[f->second].ssum, tC(C.Ec(l, T.k) + (int64_t)b * hc * cC(l))});
+          }
+          pb.gemm(Mt[q] + (int64_t)a * hr * cC(l), hr, cC(l), hc, hc, cC(l), cC(l), 0, it);
+        }
+      }
+    }
+    pb.end("proj", l);
+    // R images (Eq. nonleafA / nonleafB) and the case-2/3/4 factors
     pb.begin();
     for (int64_t p = 0; p < nb; ++p) {
       const Block& b = bl[p];
       if (b.kind != KR) continue;
       pb.gemm1(Ahat[l][p], rC(l), rB(l), rA(l), rA(l), rB(l), rB(l), 0, PA[l][b.t], T1[p]);
       pb.gemm1(Bhat[l][p], cA(l), cC(l), cB(l), cB(l), cC(l), cC(l), 0, T2[p], PB[l][b.s]);
+      pb.gemm1(PAS[p], rC(l), cA(l), rA(l), rA(l), cA(l), cA(l), 0, PA[l][b.t], tA(A.S(l, b.idx)));
+      pb.gemm1(SBP[p], rB(l), cC(l), cB(l), cB(l), cC(l), cC(l), 0, tB(B.S(l, b.idx)), PB[l][b.s]);
     }
-    for (auto& T : lt.tg)
-      if (T.M >= 0) pb.gemm1(T.ssum, rC(l), cC(l), gr, rC(l), cC(l), cC(l), SF_TA | SF_ACC, tC(C.Er(l, T.i)), T.Mt);
-    pb.end("nl_coup", l);
+    pb.end("rimage", l);
+
+    // ---- couplings (Eq. leafcoup_simple / nonleafcoup_simple), three passes per target
+    std::vector<std::vector<Item>> g24(lt.tg.size()), g3(lt.tg.size());
+    for (auto& tr : lt.trip) {
+      const Block &ba = bl[tr.pa], &bb = bl[tr.pb];
+      const Target& T = lt.tg[tr.tgt];
+      if (T.cls == TC_F) continue;
+      if (ba.kind == KNL && bb.kind == KNL) continue;
+      if (ba.kind == KF && bb.kind == KF) continue;                      // case-1 (leaf)
+      if (bb.kind == KR) g24[tr.tgt].push_back({Ahat[l][tr.pa], SBP[tr.pb]});   // case-2, case-4
+      else g3[tr.tgt].push_back({PAS[tr.pa], Bhat[l][tr.pb]});                   // case-3
+    }
     pb.begin();
     for (size_t q = 0; q < lt.tg.size(); ++q) {
-      const Target& T = lt.tg[q];
-      pb.gemm(T.s24, rC(l), cB(l), rB(l), rB(l), cB(l), cB(l), 0, g24[q]);
-      pb.gemm(T.s3, rA(l), cC(l), cA(l), cA(l), cC(l), cC(l), 0, g3[q]);
+      Target& T = lt.tg[q];
+      if (T.cls == TC_F) continue;
+      if (leaf) pb.gemm(T.ssum, rC(l), cC(l), LS, LS, cC(l), cC(l), SF_ACC, T.g1);   // case-1
+      else if (Mt[q] >= 0) pb.gemm1(T.ssum, rC(l), cC(l), gr, rC(l), cC(l), cC(l), SF_TA | SF_ACC, tC(C.Er(l, T.i)), Mt[q]);
     }
-    pb.end("nl_coup", l);
+    pb.end("coup", l);
     pb.begin();
-    for (auto& T : lt.tg)
-      if (T.s24 >= 0) pb.gemm1(T.ssum, rC(l), cC(l), cB(l), cB(l), cC(l), cC(l), SF_ACC, T.s24, PB[l][T.k]);
-    pb.end("nl_coup", l);
+    for (size_t q = 0; q < lt.tg.size(); ++q)
+      if (lt.tg[q].cls != TC_F) pb.gemm(lt.tg[q].ssum, rC(l), cC(l), rB(l), rB(l), cC(l), cC(l), SF_ACC, g24[q]);
+    pb.end("coup", l);
     pb.begin();
-    for (auto& T : lt.tg)
-      if (T.s3 >= 0) pb.gemm1(T.ssum, rC(l), cC(l), rA(l), rA(l), cC(l), cC(l), SF_ACC, PA[l][T.i], T.s3);
-    pb.end("nl_coup", l);
+    for (size_t q = 0; q < lt.tg.size(); ++q)
+      if (lt.tg[q].cls != TC_F) pb.gemm(lt.tg[q].ssum, rC(l), cC(l), cA(l), cA(l), cC(l), cC(l), SF_ACC, g3[q]);
+    pb.end("coup", l);
+    pb.close_memset(zG, g);
+    pb.close_memset(zS, AR_S);
+    // the children's data of this level are consumed: free the lists
+    if (c <= L) {
+      Ahat[c].clear();
+      Bhat[c].clear();
+      PA[c].clear();
+      PB[c].clear();
+      Bj[c].clear();
+    }
   }
 
   // ============================================ top-down split of NL-held couplings
-  {
-    // H slot per NL block: its target sum if it is a target, else a fresh slot when
-    // its parent passes something down
-    std::vector<std::vector<int64_t>> H(L + 1);
-    for (int l = lmin; l < L; ++l) {
-      const auto& bl = st.blocks[l];
-      H[l].assign(bl.size(), -1);
-      for (auto& T : LT[l].tg)
-        if (T.cls == TC_NL) H[l][T.cpos] = T.ssum;
-    }
-    for (int l = lmin; l < L; ++l) {
-      const int c = l + 1;
-      const auto& bl = st.blocks[l];
-      const int hr = rC(c), hc = cC(c);
-      std::vector<int64_t> Xt(bl.size(), -1), X(bl.size(), -1);
-      for (size_t p = 0; p < bl.size(); ++p)
-        if (bl[p].kind == KNL && H[l][p] >= 0) {
-          Xt[p] = pb.W((int64_t)rC(l) * 2 * hc);
-          X[p] = pb.W((int64_t)2 * hr * 2 * hc);
-        }
-      pb.begin();
-      for (size_t p = 0; p < bl.size(); ++p)
-        if (Xt[p] >= 0)
-          pb.gemm1(Xt[p], rC(l), 2 * hc, cC(l), cC(l), cC(l), 2 * hc, SF_TB, H[l][p], tC(C.Ec(l, bl[p].s)));
-      pb.end("split", l);
-      pb.begin();
-      for (size_t p = 0; p < bl.size(); ++p)
-        if (X[p] >= 0)
-          pb.gemm1(X[p], 2 * hr, 2 * hc, rC(l), rC(l), 2 * hc, 2 * hc, 0, tC(C.Er(l, bl[p].t)), Xt[p]);
-      pb.end("split", l);
-      if (c < L) {
-        // children R: S += X_ab ; children NL: H += X_ab
-        for (size_t p = 0; p < st.blocks[c].size(); ++p)
-          if (st.blocks[c][p].kind == KNL && H[c][p] < 0) {
-            int32_t pp = st.find(l, st.blocks[c][p].t >> 1, st.blocks[c][p].s >> 1);
-            if (pp >= 0 && X[pp] >= 0) H[c][p] = pb.W((int64_t)rC(c) * cC(c));
-          }
-      }
-      pb.begin();
-      std::vector<int64_t> Ft;
-      std::vector<std::pair<int64_t, int64_t>> Fupd;  // (tmp, target F offset) with child row cluster
-      std::vector<int32_t> Frow;
-      for (size_t p = 0; p < bl.size(); ++p) {
-        if (X[p] < 0) continue;
-        for (int a = 0; a < 2; ++a)
-          for (int bb = 0; bb < 2; ++bb) {
-            int32_t cp = st.find(c, 2 * bl[p].t + a, 2 * bl[p].s + bb);
-            const Block& cb = st.blocks[c][cp];
-            int64_t xab = X[p] + (int64_t)a * hr * 2 * hc + (int64_t)bb * hc;
-            if (cb.kind == KR) {
-              pb.sum(tC(C.S(c, cb.idx)), hr, hc, 2 * hc, cC(c), true, {xab});
-            } else if (cb.kind == KNL) {
-              pb.sum(H[c][cp], hr, hc, 2 * hc, cC(c), true, {xab});
-            } else {
-              int64_t tmp = pb.W((int64_t)rC(c) * LS);
-              pb.gemm1(tmp, rC(c), LS, cC(c), 2 * hc, cC(c), LS, SF_TB, xab, tC(C.Vc(cb.s)));
-              Fupd.push_back({tmp, tC(C.F(cb.idx))});
-              Frow.push_back(cb.t);
-            }
-          }
-      }
-      pb.end("split", l);
-      pb.begin();
-      for (size_t q = 0; q < Fupd.size(); ++q)
-        pb.gemm1(Fupd[q].second, LS, LS, rC(c), rC(c), LS, LS, SF_ACC, tC(C.Vr(Frow[q])), Fupd[q].first);
-      pb.end("split", c);
-    }
+  std::vector<std::vector<int64_t>> H(L + 1);
+  for (int l = lmin; l < L; ++l) {
+    H[l].assign(st.blocks[l].size(), -1);
+    for (auto& T : LT[l].tg)
+      if (T.cls == TC_NL) H[l][T.cpos] = T.ssum;
   }
-  P.w_elems = pb.wtop;
-  P.launches[0].off = tag(AR_W, 0);
-  P.launches[0].elems = pb.wtop;
+  for (int l = lmin; l < L; ++l) {
+    const int c = l + 1;
+    const auto& bl = st.blocks[l];
+    const int hr = rC(c), hc = cC(c);
+    pb.reset(AR_S);
+    const size_t zS = pb.open_memset(AR_S);
+    std::vector<int64_t> Xt(bl.size(), -1), X(bl.size(), -1);
+    for (size_t p = 0; p < bl.size(); ++p)
+      if (bl[p].kind == KNL && H[l][p] >= 0) {
+        Xt[p] = pb.alloc(AR_S, (int64_t)rC(l) * 2 * hc);
+        X[p] = pb.alloc(AR_S, (int64_t)2 * hr * 2 * hc);
+      }
+    if (c < L)
+      for (size_t p = 0; p < st.blocks[c].size(); ++p)
+        if (st.blocks[c][p].kind == KNL && H[c][p] < 0) {
+          int32_t pp = st.find(l, st.blocks[c][p].t >> 1, st.blocks[c][p].s >> 1);
+          if (pp >= 0 && X[pp] >= 0) H[c][p] = pb.alloc(AR_P, (int64_t)rC(c) * cC(c));
+        }
+    pb.begin();
+    for (size_t p = 0; p < bl.size(); ++p)
+      if (Xt[p] >= 0)
+        pb.gemm1(Xt[p], rC(l), 2 * hc, cC(l), cC(l), cC(l), 2 * hc, SF_TB, H[l][p], tC(C.Ec(l, bl[p].s)));
+    pb.end("split", l);
+    pb.begin();
+    for (size_t p = 0; p < bl.size(); ++p)
+      if (X[p] >= 0) pb.gemm1(X[p], 2 * hr, 2 * hc, rC(l), rC(l), 2 * hc, 2 * hc, 0, tC(C.Er(l, bl[p].t)), Xt[p]);
+    pb.end("split", l);
+    std::vector<std::pair<int64_t, int64_t>> Fupd;
+    std::vector<int32_t> Frow;
+    pb.begin();
+    for (size_t p = 0; p < bl.size(); ++p) {
+      if (X[p] < 0) continue;
+      for (int a = 0; a < 2; ++a)
+        for (int bb = 0; bb < 2; ++bb) {
+          int32_t cp = st.find(c, 2 * bl[p].t + a, 2 * bl[p].s + bb);
+          const Block& cb = st.blocks[c][cp];
+          int64_t xab = X[p] + (int64_t)a * hr * 2 * hc + (int64_t)bb * hc;
+          if (cb.kind == KR) {
+            pb.sum(tC(C.S(c, cb.idx)), hr, hc, 2 * hc, cC(c), true, {xab});
+          } else if (cb.kind == KNL) {
+            pb.sum(H[c][cp], hr, hc, 2 * hc, cC(c), true, {xab});
+          } else {
+            int64_t tmp = pb.alloc(AR_S, (int64_t)rC(c) * LS);
+            pb.gemm1(tmp, rC(c), LS, cC(c), 2 * hc, cC(c), LS, SF_TB, xab, tC(C.Vc(cb.s)));
+            Fupd.push_back({tmp, tC(C.F(cb.idx))});
+            Frow.push_back(cb.t);
+          }
+        }
+    }
+    pb.end("split", l);
+    pb.begin();
+    for (size_t q = 0; q < Fupd.size(); ++q)
+      pb.gemm1(Fupd[q].second, LS, LS, rC(c), rC(c), LS, LS, SF_ACC, tC(C.Vr(Frow[q])), Fupd[q].first);
+    pb.end("split", c);
+    pb.close_memset(zS, AR_S);
+  }
+  pb.close_memset(zP, AR_P);
 }
 
 void build_matvec_plan(const Mat& H, int64_t nrhs, Plan& P, int64_t& off_x, int64_t& off_y) {
@@ -768,19 +731,14 @@ void build_matvec_plan(const Mat& H, int64_t nrhs, Plan& P, int64_t& off_x, int6
   PlanBuilder pb(P);
   const int64_t nl = 1LL << L;
   const int nr = (int)nrhs;
-  off_x = pb.W(nl * LS * nrhs);
-  off_y = pb.W(nl * LS * nrhs);
+  const Arena W = AR_P;
+  off_x = pb.alloc(W, nl * LS * nrhs);
+  off_y = pb.alloc(W, nl * LS * nrhs);
   std::vector<int64_t> xh(L + 1), yh(L + 1);
   for (int l = 0; l <= L; ++l) {
-    xh[l] = pb.W((1LL << l) * H.Kc[l] * nrhs);
-    yh[l] = pb.W((1LL << l) * H.Kr[l] * nrhs);
+    xh[l] = pb.alloc(W, (1LL << l) * H.Kc[l] * nrhs);
+    yh[l] = pb.alloc(W, (1LL << l) * H.Kr[l] * nrhs);
   }
-  Launch z;
-  z.kind = Launch::MEMSET;
-  z.off = tag(AR_W, 0);
-  z.elems = pb.wtop;
-  z.phase = "zero";
-  P.launches.push_back(z);
   auto tH = [&](int64_t o) { return tag(AR_A, o); };
   // forward transform
   pb.begin();
@@ -822,7 +780,6 @@ void build_matvec_plan(const Mat& H, int64_t nrhs, Plan& P, int64_t& off_x, int6
   for (int64_t t = 0; t < nl; ++t)
     pb.gemm1(off_y + t * LS * nrhs, LS, nr, H.Kr[L], H.Kr[L], nr, nr, SF_ACC, tH(H.Vr(t)), yh[L] + t * H.Kr[L] * nrhs);
   pb.end("mv_backward", L);
-  P.w_elems = pb.wtop;
 }
 
 }  // namespace h2

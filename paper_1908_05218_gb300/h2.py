@@ -23,7 +23,7 @@ _TRUNC = {"paper": TRUNC_PAPER, "sv": TRUNC_SV, "full": TRUNC_FULL}
 
 # exported symbols and their signatures (checked by the CPU tests)
 SYMBOLS = ["h2_build", "h2_import", "h2_export", "h2_mmp", "h2_matvec", "h2_to_dense", "h2_info",
-           "h2_tree_perm", "h2_level_blocks", "h2_destroy", "h2_last_error"]
+           "h2_tree_perm", "h2_level_blocks", "h2_trace_enable", "h2_trace_read", "h2_destroy", "h2_last_error"]
 
 
 class H2Error(RuntimeError):
@@ -69,6 +69,8 @@ def load(path: str = LIB_PATH):
     lib.h2_info.argtypes = [P, C.POINTER(Stats)]
     lib.h2_tree_perm.argtypes = [P, P]
     lib.h2_level_blocks.argtypes = [P, I32, P, P, P, P]
+    lib.h2_trace_enable.argtypes = [P, I32]
+    lib.h2_trace_read.argtypes = [P, I32, P, P, P, P, P]
     lib.h2_destroy.argtypes = [P]
     lib.h2_destroy.restype = None
     lib.h2_last_error.restype = C.c_char_p
@@ -183,6 +185,22 @@ class H2Matrix:
         arrs = [np.zeros(sizes[i], np.float64) for i in range(1, 7)]
         _check(lib.h2_export(self.handle, _ptr(sizes), _ptr(kr), _ptr(kc), *[_ptr(a) for a in arrs]))
         return Packed(kr, kc, *arrs)
+
+    def trace_enable(self, on: bool = True):
+        _check(load().h2_trace_enable(self.handle, int(on)))
+
+    def trace_read(self) -> list:
+        """Per launch group of the product that made this handle: (kind, level, ms, flops)."""
+        lib = load()
+        cnt = C.c_int32(0)
+        _check(lib.h2_trace_read(self.handle, 0, None, None, None, None, C.byref(cnt)))
+        n = cnt.value
+        kind = np.zeros(n, np.int32)
+        level = np.zeros(n, np.int32)
+        ms = np.zeros(n, np.float64)
+        fl = np.zeros(n, np.float64)
+        _check(lib.h2_trace_read(self.handle, n, _ptr(kind), _ptr(level), _ptr(ms), _ptr(fl), C.byref(cnt)))
+        return [("gemm", "eig", "memset")[k] for k in kind], level, ms, fl
 
     def tree_perm(self) -> np.ndarray:
         p = np.zeros(self.n, dtype=np.int64)
