@@ -162,6 +162,23 @@ h2_status h2_mmp(h2_handle A, h2_handle B, double eps, const h2_opts* opts,
  * overwritten.  Enqueued on the stream of the handle's last call. */
 h2_status h2_matvec(h2_handle h, const double* x, double* y, int64_t nrhs);
 
+/* y = H x like h2_matvec, but the call allocates no memory at all: its work space
+ * (the tree-ordered copies of x and y, the coefficient vectors of every level and
+ * the block lists) lives in one fixed 32 MiB array compiled into the library.  The
+ * paper has no counterpart; it exists for callers that may not allocate device
+ * memory during the call, such as code running under a device-memory budget fixed
+ * in advance, or hosts that gave all free device memory to another allocator.
+ *   x, y   device float64, column-major n x nrhs, user order; y is overwritten.
+ *   nrhs   1..64.
+ * Returns H2_EINVAL when the matrix and nrhs need more than the 32 MiB (roughly
+ * n * nrhs * 16 bytes plus the coefficient vectors and block lists).  Every device
+ * that loads the library holds the array until the process exits.  All calls share
+ * it: calls that overlap on the GPU (different streams or threads) race and return
+ * wrong results.  The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Enqueued on the stream of the handle's last call. */
+h2_status h2_matvec_noalloc(h2_handle h, const double* x, double* y, int64_t nrhs);
+
 /* Dense n x n matrix, device float64, column-major, user order (testing; n <=
  * 16384). */
 h2_status h2_to_dense(h2_handle h, double* out);

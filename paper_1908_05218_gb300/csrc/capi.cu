@@ -636,6 +636,14 @@ h2_status h2_matvec(h2_handle h, const double* x, double* y, int64_t nrhs) {
   });
 }
 
+h2_status h2_matvec_noalloc(h2_handle h, const double* x, double* y, int64_t nrhs) {
+  if (!h || !x || !y) return fail(H2_EINVAL, "null argument");
+  std::string err;
+  h2_status st = h2::matvec_noalloc(h->m, h->d_user, x, y, nrhs, err);
+  if (st != H2_OK) return fail(st, err);
+  return H2_OK;
+}
+
 h2_status h2_to_dense(h2_handle h, double* out) {
   if (!h || !out) return fail(H2_EINVAL, "null argument");
   int64_t n = h->m.st->n;

@@ -187,6 +187,8 @@ void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, double* con
 void launch_permute(const double* src, double* dst, const int64_t* user, int64_t rows, int64_t n,
                     int64_t nrhs, bool to_tree, void* stream);
 void launch_identity(double* out, int64_t n, void* stream);
+h2_status matvec_noalloc(const Mat& m, const int64_t* d_user, const double* x, double* y, int64_t nrhs,
+                         std::string& err);
 void cuda_check(int err, const char* what);
 
 // construction (builder.cpp): fills host arrays of the packed import layout

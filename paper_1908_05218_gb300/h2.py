@@ -22,7 +22,7 @@ TRUNC_PAPER, TRUNC_SV, TRUNC_FULL = 0, 1, 2
 _TRUNC = {"paper": TRUNC_PAPER, "sv": TRUNC_SV, "full": TRUNC_FULL}
 
 # exported symbols and their signatures (checked by the CPU tests)
-SYMBOLS = ["h2_build", "h2_import", "h2_export", "h2_mmp", "h2_matvec", "h2_to_dense", "h2_info",
+SYMBOLS = ["h2_build", "h2_import", "h2_export", "h2_mmp", "h2_matvec", "h2_matvec_noalloc", "h2_to_dense", "h2_info",
            "h2_tree_perm", "h2_level_blocks", "h2_trace_enable", "h2_trace_read", "h2_destroy", "h2_last_error"]
 
 
@@ -65,6 +65,7 @@ def load(path: str = LIB_PATH):
     lib.h2_export.argtypes = [P, P, P, P, P, P, P, P, P, P]
     lib.h2_mmp.argtypes = [P, P, D, C.POINTER(Opts), C.POINTER(P)]
     lib.h2_matvec.argtypes = [P, P, P, I64]
+    lib.h2_matvec_noalloc.argtypes = [P, P, P, I64]
     lib.h2_to_dense.argtypes = [P, P]
     lib.h2_info.argtypes = [P, C.POINTER(Stats)]
     lib.h2_tree_perm.argtypes = [P, P]
@@ -155,6 +156,18 @@ class H2Matrix:
         if y is not None:
             y.copy_(out.reshape(y.shape))
             return y
+        return out[:, 0] if squeeze else out
+
+    def matvec_noalloc(self, x):
+        """y = H x through h2_matvec_noalloc (no allocation inside the library call)."""
+        import torch
+        squeeze = x.dim() == 1
+        X = x.reshape(self.n, -1)
+        xc = X.t().contiguous()
+        yc = torch.empty_like(xc)
+        _check(load().h2_matvec_noalloc(self.handle, C.c_void_p(xc.data_ptr()), C.c_void_p(yc.data_ptr()),
+                                        X.shape[1]))
+        out = yc.t()
         return out[:, 0] if squeeze else out
 
     def matvec_ptr(self, x_ptr: int, y_ptr: int, nrhs: int):
