@@ -240,7 +240,7 @@ def main():
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    kinds, levels, lms, lfl = C.trace_read()
+    kinds, levels, lms, lfl, lnames = C.trace_read()
     A.trace_enable(False)
 
     ia, ib, ic = A.info(), B.info(), C.info()
@@ -274,6 +274,12 @@ def main():
         roof = {"bound": "alu", "kernel": dom, "ms_per_step": tot[dom][0], "achieved": None, "peak": None,
                 "unit": None, "frac": None, "traffic": None}
     phase_ms = {k: round(v[0], 3) for k, v in tot.items()}
+    by_phase = {}
+    for nm, m_ in zip(lnames, lms):
+        by_phase[nm] = by_phase.get(nm, 0.0) + m_
+    by_level = {}
+    for lv, m_ in zip(levels, lms):
+        by_level[int(lv)] = by_level.get(int(lv), 0.0) + m_
 
     # end to end through the public API with host buffers: upload A and B from host
     # arrays, the product, download C
@@ -315,7 +321,8 @@ def main():
             "mmp_s": ms * 1e-3, "rel_err_vs_exact_h2_matvecs": rel_err,
             "ranks_C_max_row": ic["max_rank_row"], "cap_hits": ic["cap_hits"],
             "bytes_alg": nbytes, "build_s": build_s, "first_product_s_incl_plan": setup_s,
-            "phase_ms": phase_ms, "roofline": roof, "cpu_baseline": cpu_line, "e2e": e2e,
+            "phase_ms": phase_ms, "phase_ms_by_name": {k: round(v, 3) for k, v in by_phase.items()},
+            "ms_by_level": {k: round(v, 3) for k, v in sorted(by_level.items())}, "roofline": roof, "cpu_baseline": cpu_line, "e2e": e2e,
             "gpu_launches": int(sum(tot[k][2] for k in tot if k != "memset")) * args.steps,
             "clocks": clk.summary(),
         }

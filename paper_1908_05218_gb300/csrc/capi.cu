@@ -16,7 +16,7 @@ struct h2_matrix {
   struct MmpEntry {
     const h2_matrix* B = nullptr;
     std::vector<int> Bkr, Bkc;
-    int trunc = 0, cap = 0;
+    int trunc = 0, cap = 0, precision = 0;
     h2::Plan plan;
   };
   std::vector<std::unique_ptr<MmpEntry>> mmp_plans;
@@ -25,7 +25,7 @@ struct h2_matrix {
   int64_t* d_user = nullptr;  // padded tree row -> user index (-1: padding)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool timed = false;
-  int origin_trunc = -1, origin_cap = -1;
+  int origin_trunc = -1, origin_cap = -1, origin_prec = -1;
   bool trace_on = false;     // on A: trace the products made from it
   h2::Trace trace;           // on C: events of the product that made it
   const h2::Plan* trace_plan = nullptr;
@@ -147,6 +147,8 @@ void alloc_mat(Mat& m) {
 
 void free_mat(Mat& m) {
   if (m.arena) cudaFree(m.arena);
+  if (m.arena32) cudaFree(m.arena32);
+  m.arena32 = nullptr;
   if (m.d_kr) cudaFree(m.d_kr);
   for (void* p : m.extra_allocs) cudaFree(p);
   m.arena = nullptr;
@@ -354,7 +356,7 @@ void validate_plan(const Plan& P, const int64_t sizes[kArenas]) {
     if (L.kind == Launch::MEMSET) check(L.off, L.elems, "memset");
 }
 
-void upload_plan(Plan& P) {
+void upload_plan(Plan& P, size_t region_esize) {
   P.d_segs = (Seg*)dmalloc(std::max<size_t>(1, P.segs.size()) * sizeof(Seg));
   P.d_items = (Item*)dmalloc(std::max<size_t>(1, P.items.size()) * sizeof(Item));
   P.d_eigs = (EigTask*)dmalloc(std::max<size_t>(1, P.eigs.size()) * sizeof(EigTask));
@@ -364,14 +366,16 @@ void upload_plan(Plan& P) {
   int64_t scratch = 0;
   for (auto& L : P.launches) {
     if (L.kind == Launch::GEMM) {
-      int mx = 1;
+      int mx = 1, md = 1;
       double fl = 0;
       for (int64_t q = L.first; q < L.first + L.count; ++q) {
         const Seg& s = P.segs[q];
         mx = std::max<int>(mx, s.n);
+        md = std::max<int>(md, std::max<int>(s.m, s.n));
         if (!(s.flags & SF_SUM)) fl += 2.0 * s.m * s.n * s.k * s.count;
       }
       L.aux = mx;
+      L.aux2 = md;
       L.flops = fl;
     } else if (L.kind == Launch::EIG) {
       int mx = 1;
@@ -383,7 +387,7 @@ void upload_plan(Plan& P) {
     }
   }
   P.d_scratch = (double*)dmalloc(std::max<int64_t>(1, scratch) * sizeof(double));
-  for (int a = AR_P; a <= AR_S; ++a) P.d_region[a] = (double*)dmalloc(std::max<int64_t>(1, P.region[a]) * sizeof(double));
+  for (int a = AR_P; a <= AR_S; ++a) P.d_region[a] = (double*)dmalloc(std::max<int64_t>(1, P.region[a]) * region_esize);
 }
 
 void free_plan(Plan& P) {
@@ -399,7 +403,7 @@ void free_plan(Plan& P) {
   P.d_scratch = nullptr;
 }
 
-void run_plan(const Plan& P, double* const arenas[kArenas], int32_t* kr, int32_t* kc, unsigned long long* cap_hits,
+void run_plan(const Plan& P, const ArenaSet& ar, int32_t* kr, int32_t* kc, unsigned long long* cap_hits,
               const MmpParams& prm, void* stream, bool skip_memset, Trace* tr) {
   if (tr) {
     while (tr->ev.size() < 2 * P.launches.size()) {
@@ -414,13 +418,13 @@ void run_plan(const Plan& P, double* const arenas[kArenas], int32_t* kr, int32_t
     if (tr) cuda_check(cudaEventRecord((cudaEvent_t)tr->ev[2 * li], (cudaStream_t)stream), "event");
     if (L.kind == Launch::MEMSET) {
       if (skip_memset || L.elems == 0) continue;
-      double* p = arenas[arena_of(L.off)] + offset_of(L.off);
-      cuda_check(cudaMemsetAsync(p, 0, L.elems * sizeof(double), (cudaStream_t)stream), "memset");
+      int a = arena_of(L.off);
+      char* p = (char*)ar.p[a] + offset_of(L.off) * ar.esize(a);
+      cuda_check(cudaMemsetAsync(p, 0, L.elems * ar.esize(a), (cudaStream_t)stream), "memset");
     } else if (L.kind == Launch::GEMM) {
-      launch_gemm(P.d_segs, P.d_items, L.first, L.count, arenas, L.aux, stream);
+      launch_gemm(P.d_segs, P.d_items, L.first, L.count, ar, L.aux, L.aux2, prm.precision == H2_MIXED_FP32, stream);
     } else {
-      launch_eig(P.d_eigs, L.first, L.count, arenas, kr, kc, prm.eps, prm.trunc, cap_hits, L.aux, P.d_scratch,
-                 stream);
+      launch_eig(P.d_eigs, L.first, L.count, ar, kr, kc, prm.eps, prm.trunc, cap_hits, L.aux, P.d_scratch, stream);
     }
     cuda_check(cudaGetLastError(), L.phase);
     if (tr) cuda_check(cudaEventRecord((cudaEvent_t)tr->ev[2 * li + 1], (cudaStream_t)stream), "event");
@@ -532,13 +536,13 @@ h2_status h2_mmp(h2_handle A, h2_handle B, double eps, const h2_opts* opts, h2_h
   return guarded([&] {
     h2_opts o = defaults(opts);
     if (o.trunc != H2_TRUNC_FULL && !(eps > 0 && eps < 1)) throw Error(H2_EINVAL, "eps must lie in (0, 1)");
-    if (o.precision != H2_FP64) throw Error(H2_EUNSUPPORTED, "precision mode not built yet");
     if (!same_structure(*A->m.st, *B->m.st)) throw Error(H2_ESTRUCT, "A and B have different trees or partitions");
     MmpParams prm{eps, o.trunc, o.rank_cap, o.precision};
     // plan cache on A
     h2_matrix::MmpEntry* ent = nullptr;
     for (auto& e : A->mmp_plans)
-      if (e->B == B && e->Bkr == B->m.Kr && e->Bkc == B->m.Kc && e->trunc == o.trunc && e->cap == o.rank_cap)
+      if (e->B == B && e->Bkr == B->m.Kr && e->Bkc == B->m.Kc && e->trunc == o.trunc && e->cap == o.rank_cap &&
+          e->precision == o.precision)
         ent = e.get();
     Mat Ccaps;
     Ccaps.st = A->m.st;
@@ -549,6 +553,7 @@ h2_status h2_mmp(h2_handle A, h2_handle B, double eps, const h2_opts* opts, h2_h
       e->Bkc = B->m.Kc;
       e->trunc = o.trunc;
       e->cap = o.rank_cap;
+      e->precision = o.precision;
       build_mmp_plan(A->m, B->m, Ccaps, prm, e->plan);
       e->plan.ckr = Ccaps.Kr;
       e->plan.ckc = Ccaps.Kc;
@@ -562,13 +567,14 @@ h2_status h2_mmp(h2_handle A, h2_handle B, double eps, const h2_opts* opts, h2_h
                                   e->plan.region[AR_G0], e->plan.region[AR_G1], e->plan.region[AR_S], 0};
         validate_plan(e->plan, sizes);
       }
-      upload_plan(e->plan);
+      upload_plan(e->plan, o.precision == H2_MIXED_FP32 ? sizeof(float) : sizeof(double));
       ent = e.get();
       A->mmp_plans.push_back(std::move(e));
     }
     h2_matrix* out = *C;
     bool reuse = out && out->origin_A == A && out->origin_B == B && out->origin_trunc == o.trunc &&
-                 out->origin_cap == o.rank_cap && out->m.Kr == ent->plan.ckr && out->m.Kc == ent->plan.ckc;
+                 out->origin_cap == o.rank_cap && out->origin_prec == o.precision && out->m.Kr == ent->plan.ckr &&
+                 out->m.Kc == ent->plan.ckc;
     std::unique_ptr<h2_matrix> fresh;
     if (!reuse) {
       fresh = std::make_unique<h2_matrix>();
@@ -584,6 +590,7 @@ h2_status h2_mmp(h2_handle A, h2_handle B, double eps, const h2_opts* opts, h2_h
       fresh->origin_B = B;
       fresh->origin_trunc = o.trunc;
       fresh->origin_cap = o.rank_cap;
+      fresh->origin_prec = o.precision;
       out = fresh.get();
     }
     out->m.stream = o.stream;
@@ -592,10 +599,33 @@ h2_status h2_mmp(h2_handle A, h2_handle B, double eps, const h2_opts* opts, h2_h
     cuda_check(cudaEventRecord(out->ev0, s), "event");
     cuda_check(cudaMemsetAsync(out->m.arena, 0, out->m.arena_elems * sizeof(double), s), "zero C");
     cuda_check(cudaMemsetAsync(out->m.d_kr, 0, 2 * A->m.st->nnodes() * sizeof(int32_t) + 64, s), "zero ranks");
-    double* arenas[kArenas] = {A->m.arena, B->m.arena, out->m.arena, ent->plan.d_region[AR_P],
-                               ent->plan.d_region[AR_G0], ent->plan.d_region[AR_G1], ent->plan.d_region[AR_S], nullptr};
+    ArenaSet ar;
+    const bool mixed = o.precision == H2_MIXED_FP32;
+    if (mixed) {
+      for (h2_matrix* h : {A, B}) {
+        if (!h->m.arena32) {
+          h->m.arena32 = (float*)dmalloc(h->m.arena_elems * sizeof(float));
+          launch_to_f32(h->m.arena, h->m.arena32, h->m.arena_elems, o.stream);
+          cuda_check(cudaGetLastError(), "convert to float");
+        }
+      }
+      ar.p[AR_A] = A->m.arena32;
+      ar.p[AR_B] = B->m.arena32;
+      ar.f32 = (1u << AR_A) | (1u << AR_B) | (1u << AR_P) | (1u << AR_G0) | (1u << AR_G1) | (1u << AR_S);
+    } else {
+      ar.p[AR_A] = A->m.arena;
+      ar.p[AR_B] = B->m.arena;
+    }
+    ar.p[AR_C] = out->m.arena;
+    for (int a = AR_P; a <= AR_S; ++a) ar.p[a] = ent->plan.d_region[a];
+    ar.rk[RK_AR] = A->m.d_kr;
+    ar.rk[RK_AC] = A->m.d_kc;
+    ar.rk[RK_BR] = B->m.d_kr;
+    ar.rk[RK_BC] = B->m.d_kc;
+    ar.rk[RK_CR] = out->m.d_kr;
+    ar.rk[RK_CC] = out->m.d_kc;
     out->trace_plan = A->trace_on ? &ent->plan : nullptr;
-    run_plan(ent->plan, arenas, out->m.d_kr, out->m.d_kc, out->m.d_cap, prm, o.stream, false,
+    run_plan(ent->plan, ar, out->m.d_kr, out->m.d_kc, out->m.d_cap, prm, o.stream, false,
              A->trace_on ? &out->trace : nullptr);
     cuda_check(cudaEventRecord(out->ev1, s), "event");
     out->timed = true;
@@ -614,7 +644,7 @@ h2_status h2_matvec(h2_handle h, const double* x, double* y, int64_t nrhs) {
       build_matvec_plan(h->m, nrhs, *p, ox, oy);
       int64_t sizes[kArenas] = {h->m.arena_elems, 0, 0, p->region[AR_P], 0, 0, 0, 0};
       validate_plan(*p, sizes);
-      upload_plan(*p);
+      upload_plan(*p, sizeof(double));
       h->mv_offs[nrhs] = {ox, oy};
       it = h->mv_plans.emplace(nrhs, std::move(p)).first;
     }
@@ -628,9 +658,11 @@ h2_status h2_matvec(h2_handle h, const double* x, double* y, int64_t nrhs) {
     double* xt = W + offset_of(offs.first);
     double* yt = W + offset_of(offs.second);
     launch_permute(x, xt, h->d_user, rows, st.n, nrhs, true, s);
-    double* arenas[kArenas] = {h->m.arena, nullptr, nullptr, W, nullptr, nullptr, nullptr, nullptr};
+    ArenaSet ar;
+    ar.p[AR_A] = h->m.arena;
+    ar.p[AR_P] = W;
     MmpParams prm{0, 0, 0, 0};
-    run_plan(P, arenas, nullptr, nullptr, nullptr, prm, s, true);
+    run_plan(P, ar, nullptr, nullptr, nullptr, prm, s, true);
     launch_permute(yt, y, h->d_user, rows, st.n, nrhs, false, s);
     cuda_check(cudaGetLastError(), "matvec");
   });
@@ -760,6 +792,11 @@ h2_status h2_trace_read(h2_handle C, int32_t cap, int32_t* kind, int32_t* level,
       if (flops) flops[i] = L.flops;
     }
   });
+}
+
+const char* h2_trace_phase(h2_handle C, int32_t i) {
+  if (!C || !C->trace_plan || i < 0 || i >= (int32_t)C->trace_plan->launches.size()) return nullptr;
+  return C->trace_plan->launches[i].phase;
 }
 
 void h2_destroy(h2_handle h) {

@@ -73,6 +73,7 @@ struct Mat {
   std::vector<int64_t> off_Er, off_Ec, off_S;
   int32_t* d_kr = nullptr;  // device ranks, indexed by Structure::node
   int32_t* d_kc = nullptr;
+  float* arena32 = nullptr;  // float copy of the arena (mixed precision), made on first use
   std::vector<int32_t> h_kr, h_kc;  // host copies
   bool ranks_on_host = false;
   unsigned long long* d_cap = nullptr;  // device counter of ranks cut at the cap
@@ -107,16 +108,27 @@ inline int arena_of(int64_t t) { return (int)((t >> kTagShift) & 7); }
 inline int64_t offset_of(int64_t t) { return t & kOffMask; }
 
 // Segmented batched GEMM: out[m x n] (=|+=) sum_items op(A) op(B), one CTA per segment.
+// m, n, k are the padded dims; a dim reference (rank array << kRefShift | cluster node,
+// -1 = none) bounds the loop by the actual rank read on the device, so padded zeros
+// are skipped.  Rank arrays: 0 A.kr, 1 A.kc, 2 B.kr, 3 B.kc, 4 C.kr, 5 C.kc.
 enum SegFlags : uint8_t { SF_TA = 1, SF_TB = 2, SF_ACC = 4, SF_SUM = 8 };
+enum RankSrc : int32_t { RK_AR = 0, RK_AC = 1, RK_BR = 2, RK_BC = 3, RK_CR = 4, RK_CC = 5 };
+constexpr int kRefShift = 26;
+inline int32_t rref(RankSrc s, int node) { return (int32_t)((s << kRefShift) | node); }
 struct Seg {
   int64_t out;
   int32_t first, count;
   int16_t m, n, k, lda, ldb, ldc;
+  int32_t mref, nref;
   uint8_t flags;
   uint8_t pad[7];
 };
 struct Item {
-  int64_t a, b;
+  int64_t a = 0, b = 0;
+  int32_t kref = -1;  // bound of this item's k (see Seg), -1 = none
+  int32_t pad = 0;
+  Item() = default;
+  Item(int64_t a_, int64_t b_, int32_t k_ = -1) : a(a_), b(b_), kref(k_), pad(0) {}
 };
 
 // Normalised Gram sum + eigen-decomposition + truncation for one cluster.
@@ -135,6 +147,7 @@ struct Launch {
   int64_t off = 0, elems = 0;    // MEMSET: tagged offset and size
   int level = -1;
   int aux = 0;                   // GEMM: largest n; EIG: largest Gram dim
+  int aux2 = 0;                  // GEMM: largest max(m, n)
   const char* phase = "";
   double flops = 0;              // GEMM: counted 2 m n k over the group
 };
@@ -166,7 +179,7 @@ struct MmpParams {
 void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& p, Plan& plan);
 void build_matvec_plan(const Mat& H, int64_t nrhs, Plan& plan, int64_t& off_x, int64_t& off_y);
 void validate_plan(const Plan& plan, const int64_t sizes[kArenas]);
-void upload_plan(Plan& plan);
+void upload_plan(Plan& plan, size_t region_esize);
 void free_plan(Plan& plan);
 
 // Runs a plan: arenas[kArenas] device base pointers.
@@ -174,16 +187,25 @@ struct Trace {
   std::vector<void*> ev;  // cudaEvent_t, 2 per launch
   bool recorded = false;
 };
-void run_plan(const Plan& plan, double* const arenas[kArenas], int32_t* kr_out, int32_t* kc_out,
+// Arena base pointers, which of them hold float (bit per arena), and the six rank
+// arrays that dim references read.
+struct ArenaSet {
+  void* p[kArenas] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  uint32_t f32 = 0;
+  const int32_t* rk[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  size_t esize(int a) const { return ((f32 >> a) & 1) ? 4 : 8; }
+};
+void run_plan(const Plan& plan, const ArenaSet& ar, int32_t* kr_out, int32_t* kc_out,
               unsigned long long* cap_hits, const MmpParams& p, void* stream, bool skip_memset,
               Trace* trace = nullptr);
 
 // device helpers (kernels.cu)
-void launch_gemm(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count,
-                 double* const arenas[kArenas], int maxn, void* stream);
-void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, double* const arenas[kArenas],
+void launch_gemm(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const ArenaSet& ar,
+                 int maxn, int maxdim, bool fp32, void* stream);
+void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, const ArenaSet& ar,
                 int32_t* kr, int32_t* kc, double eps, int trunc, unsigned long long* cap_hits,
                 int max_npad, double* scratch, void* stream);
+void launch_to_f32(const double* src, float* dst, int64_t n, void* stream);
 void launch_permute(const double* src, double* dst, const int64_t* user, int64_t rows, int64_t n,
                     int64_t nrhs, bool to_tree, void* stream);
 void launch_identity(double* out, int64_t n, void* stream);

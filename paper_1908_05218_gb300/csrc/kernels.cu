@@ -11,74 +11,115 @@
 namespace h2 {
 
 struct Arenas {
-  double* p[kArenas];
+  char* p[kArenas];
+  uint32_t f32;
+  const int32_t* rk[6];
 };
 
-__device__ __forceinline__ double* resolve(const Arenas& a, int64_t t) {
-  return a.p[(t >> kTagShift) & 7] + (t & kOffMask);
+__device__ __forceinline__ int arena_idx(int64_t t) { return (int)((t >> kTagShift) & 7); }
+
+// typed view of one tagged matrix: float or double storage, read/written as Acc
+struct View {
+  char* base;
+  bool f32;
+};
+
+__device__ __forceinline__ View view(const Arenas& a, int64_t t) {
+  int ai = arena_idx(t);
+  bool f = (a.f32 >> ai) & 1;
+  return View{a.p[ai] + (t & kOffMask) * (f ? 4 : 8), f};
+}
+
+template <typename Acc>
+__device__ __forceinline__ Acc ld(const View& v, int64_t i) {
+  return v.f32 ? (Acc)((const float*)v.base)[i] : (Acc)((const double*)v.base)[i];
+}
+
+template <typename Acc>
+__device__ __forceinline__ void st(const View& v, int64_t i, Acc x, bool acc) {
+  if (v.f32) {
+    float* p = (float*)v.base + i;
+    *p = acc ? (float)(*p + x) : (float)x;
+  } else {
+    double* p = (double*)v.base + i;
+    *p = acc ? *p + (double)x : (double)x;
+  }
+}
+
+__device__ __forceinline__ int bound(const Arenas& a, int32_t ref, int padded) {
+  if (ref < 0) return padded;
+  int r = a.rk[ref >> kRefShift][ref & ((1 << kRefShift) - 1)];
+  return r < padded ? r : padded;
 }
 
 // ------------------------------------------------------------ segmented GEMM
-// One CTA per segment (blockIdx.x) and 64-column slice (blockIdx.y); the CTA
-// walks 64 x 64 output tiles, each thread owning rows ty + 16 i, cols tx + 16 j.
-constexpr int GT = 64, GK = 32, GPAD = 65;
+// One CTA per segment (blockIdx.x) and TILE-column slice (blockIdx.y); the CTA walks
+// TILE x TILE output tiles, thread (tx, ty) owning rows ty + P i, cols tx + P j
+// (P = TILE/4, 4 x 4 outputs per thread).  Operands are staged through shared
+// memory in k-slices of GK; loop bounds are the actual ranks where the segment
+// refers to them.
+constexpr int GK = 32;
 
-__global__ void __launch_bounds__(256) seg_gemm_kernel(const Seg* __restrict__ segs,
-                                                       const Item* __restrict__ items, int64_t first,
-                                                       Arenas ar) {
-  __shared__ double sA[GK * GPAD];
-  __shared__ double sB[GK * GPAD];
+template <int TILE, typename Acc>
+__global__ void __launch_bounds__((TILE / 4) * (TILE / 4)) seg_gemm_kernel(const Seg* __restrict__ segs,
+                                                                           const Item* __restrict__ items,
+                                                                           int64_t first, Arenas ar) {
+  constexpr int P = TILE / 4, NT = P * P, PAD = TILE + 1;
+  __shared__ Acc sA[GK * PAD];
+  __shared__ Acc sB[GK * PAD];
   const Seg s = segs[first + blockIdx.x];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int tid = threadIdx.x, tx = tid % P, ty = tid / P;
   const bool ta = s.flags & SF_TA, tb = s.flags & SF_TB, accum = s.flags & SF_ACC;
-  double* out = resolve(ar, s.out);
+  const int M = bound(ar, s.mref, s.m), N = bound(ar, s.nref, s.n);
+  const View out = view(ar, s.out);
   const Item* it = items + s.first;
-  for (int n0 = blockIdx.y * GT; n0 < s.n; n0 += gridDim.y * GT) {
-    for (int m0 = 0; m0 < s.m; m0 += GT) {
-      double acc[4][4];
+  for (int n0 = blockIdx.y * TILE; n0 < N; n0 += gridDim.y * TILE) {
+    for (int m0 = 0; m0 < M; m0 += TILE) {
+      Acc acc[4][4];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+        for (int j = 0; j < 4; ++j) acc[i][j] = Acc(0);
       if (s.flags & SF_SUM) {
         for (int q = 0; q < s.count; ++q) {
-          const double* A = resolve(ar, it[q].a);
+          const View A = view(ar, it[q].a);
 #pragma unroll
           for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-              int r = m0 + ty + 16 * i, c = n0 + tx + 16 * j;
-              if (r < s.m && c < s.n) acc[i][j] += A[(int64_t)r * s.lda + c];
+              int r = m0 + ty + P * i, c = n0 + tx + P * j;
+              if (r < M && c < N) acc[i][j] += ld<Acc>(A, (int64_t)r * s.lda + c);
             }
         }
       } else {
         for (int q = 0; q < s.count; ++q) {
-          const double* A = resolve(ar, it[q].a);
-          const double* B = resolve(ar, it[q].b);
-          for (int k0 = 0; k0 < s.k; k0 += GK) {
-            for (int e = tid; e < GT * GK; e += 256) {
+          const Item itq = it[q];
+          const int K = bound(ar, itq.kref, s.k);
+          const View A = view(ar, itq.a), B = view(ar, itq.b);
+          for (int k0 = 0; k0 < K; k0 += GK) {
+            for (int e = tid; e < TILE * GK; e += NT) {
               int r, kk;
-              if (ta) { r = e % GT; kk = e / GT; } else { kk = e % GK; r = e / GK; }
+              if (ta) { r = e % TILE; kk = e / TILE; } else { kk = e % GK; r = e / GK; }
               int gr = m0 + r, gk = k0 + kk;
-              double v = 0.0;
-              if (gr < s.m && gk < s.k) v = ta ? A[(int64_t)gk * s.lda + gr] : A[(int64_t)gr * s.lda + gk];
-              sA[kk * GPAD + r] = v;
+              Acc v = Acc(0);
+              if (gr < M && gk < K) v = ld<Acc>(A, ta ? (int64_t)gk * s.lda + gr : (int64_t)gr * s.lda + gk);
+              sA[kk * PAD + r] = v;
               int c;
-              if (tb) { kk = e % GK; c = e / GK; } else { c = e % GT; kk = e / GT; }
+              if (tb) { kk = e % GK; c = e / GK; } else { c = e % TILE; kk = e / TILE; }
               int gc = n0 + c;
               gk = k0 + kk;
-              double w = 0.0;
-              if (gc < s.n && gk < s.k) w = tb ? B[(int64_t)gc * s.ldb + gk] : B[(int64_t)gk * s.ldb + gc];
-              sB[kk * GPAD + c] = w;
+              Acc w = Acc(0);
+              if (gc < N && gk < K) w = ld<Acc>(B, tb ? (int64_t)gc * s.ldb + gk : (int64_t)gk * s.ldb + gc);
+              sB[kk * PAD + c] = w;
             }
             __syncthreads();
-            const int kl = min(GK, s.k - k0);
+            const int kl = min(GK, K - k0);
             for (int kk = 0; kk < kl; ++kk) {
-              double a[4], b[4];
+              Acc a[4], b[4];
 #pragma unroll
-              for (int i = 0; i < 4; ++i) a[i] = sA[kk * GPAD + ty + 16 * i];
+              for (int i = 0; i < 4; ++i) a[i] = sA[kk * PAD + ty + P * i];
 #pragma unroll
-              for (int j = 0; j < 4; ++j) b[j] = sB[kk * GPAD + tx + 16 * j];
+              for (int j = 0; j < 4; ++j) b[j] = sB[kk * PAD + tx + P * j];
 #pragma unroll
               for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -92,29 +133,55 @@ __global__ void __launch_bounds__(256) seg_gemm_kernel(const Seg* __restrict__ s
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          int r = m0 + ty + 16 * i, c = n0 + tx + 16 * j;
-          if (r < s.m && c < s.n) {
-            double* o = out + (int64_t)r * s.ldc + c;
-            *o = accum ? *o + acc[i][j] : acc[i][j];
-          }
+          int r = m0 + ty + P * i, c = n0 + tx + P * j;
+          if (r < M && c < N) st<Acc>(out, (int64_t)r * s.ldc + c, acc[i][j], accum);
         }
     }
   }
 }
 
-void launch_gemm(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, double* const arenas[kArenas],
-                 int maxn, void* stream) {
-  Arenas ar;
-  for (int i = 0; i < kArenas; ++i) ar.p[i] = arenas[i];
+static Arenas to_dev(const ArenaSet& a) {
+  Arenas d;
+  for (int i = 0; i < kArenas; ++i) d.p[i] = (char*)a.p[i];
+  d.f32 = a.f32;
+  for (int i = 0; i < 6; ++i) d.rk[i] = a.rk[i];
+  return d;
+}
+
+template <int TILE, typename Acc>
+static void gemm_launch(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const Arenas& ar,
+                        int maxn, void* stream) {
   const int64_t kMaxGrid = 2147483647LL;
-  int gy = (maxn + GT - 1) / GT;
+  int gy = (maxn + TILE - 1) / TILE;
   if (gy < 1) gy = 1;
   if (gy > 256) gy = 256;
   for (int64_t off = 0; off < count; off += kMaxGrid) {
     int64_t c = count - off < kMaxGrid ? count - off : kMaxGrid;
     dim3 grid((unsigned)c, (unsigned)gy);
-    seg_gemm_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(d_segs, d_items, first + off, ar);
+    seg_gemm_kernel<TILE, Acc><<<grid, (TILE / 4) * (TILE / 4), 0, (cudaStream_t)stream>>>(d_segs, d_items,
+                                                                                        first + off, ar);
   }
+}
+
+void launch_gemm(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const ArenaSet& a, int maxn,
+                 int maxdim, bool fp32, void* stream) {
+  Arenas ar = to_dev(a);
+  if (fp32) {
+    if (maxdim <= 32) gemm_launch<32, float>(d_segs, d_items, first, count, ar, maxn, stream);
+    else gemm_launch<64, float>(d_segs, d_items, first, count, ar, maxn, stream);
+  } else {
+    if (maxdim <= 32) gemm_launch<32, double>(d_segs, d_items, first, count, ar, maxn, stream);
+    else gemm_launch<64, double>(d_segs, d_items, first, count, ar, maxn, stream);
+  }
+}
+
+__global__ void to_f32_kernel(const double* __restrict__ s, float* __restrict__ d, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i < n; i += (int64_t)gridDim.x * blockDim.x) d[i] = (float)s[i];
+}
+
+void launch_to_f32(const double* src, float* dst, int64_t n, void* stream) {
+  to_f32_kernel<<<4 * 152, 256, 0, (cudaStream_t)stream>>>(src, dst, n);
 }
 
 // ------------------------------------------------------------ eigen + truncation
@@ -177,16 +244,17 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
   __syncthreads();
   for (int m = 0; m < 3; ++m) {
     if (t.g[m] < 0) continue;
-    const double* G = resolve(ar, t.g[m]);
+    const View G = view(ar, t.g[m]);
     double loc = 0.0;
     for (int e = tid; e < n * n; e += nt) {
-      double v = G[(int64_t)act[e / n] * t.n_pad + act[e % n]];
+      double v = ld<double>(G, (int64_t)act[e / n] * t.n_pad + act[e % n]);
       loc += v * v;
     }
     double nrm2 = block_sum(loc, red);
     if (nrm2 > 0.0) {
       double inv = 1.0 / sqrt(nrm2);
-      for (int e = tid; e < n * n; e += nt) A[(e / n) * nn + (e % n)] += G[(int64_t)act[e / n] * t.n_pad + act[e % n]] * inv;
+      for (int e = tid; e < n * n; e += nt)
+        A[(e / n) * nn + (e % n)] += ld<double>(G, (int64_t)act[e / n] * t.n_pad + act[e % n]) * inv;
     }
     __syncthreads();
   }
@@ -289,7 +357,7 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
   }
   __syncthreads();
   const int rank = s_rank;
-  double* out = resolve(ar, t.out);
+  double* out = (double*)view(ar, t.out).base;  // the new bases are float64 (arena C)
   for (int e = tid; e < t.n_pad * t.kcap; e += nt) out[e] = 0.0;
   __syncthreads();
   // sign: the entry of largest magnitude (first such) is positive
@@ -306,11 +374,10 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
   }
 }
 
-void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, double* const arenas[kArenas], int32_t* kr,
+void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, const ArenaSet& a, int32_t* kr,
                 int32_t* kc, double eps, int trunc, unsigned long long* cap_hits, int max_npad, double* scratch,
                 void* stream) {
-  Arenas ar;
-  for (int i = 0; i < kArenas; ++i) ar.p[i] = arenas[i];
+  Arenas ar = to_dev(a);
   int nn = max_npad + (max_npad & 1);
   size_t smem = 0;
   int64_t stride = 0;

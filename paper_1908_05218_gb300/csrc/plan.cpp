@@ -81,7 +81,7 @@ struct PlanBuilder {
     }
   }
   void gemm(int64_t out, int m, int n, int k, int lda, int ldb, int ldc, uint8_t fl,
-            const std::vector<Item>& it) {
+            const std::vector<Item>& it, int32_t mref = -1, int32_t nref = -1) {
     if (m <= 0 || n <= 0 || it.empty()) return;
     if (k <= 0) return;  // zero contribution; outputs start at zero
     Seg s{};
@@ -94,14 +94,17 @@ struct PlanBuilder {
     s.lda = (int16_t)lda;
     s.ldb = (int16_t)ldb;
     s.ldc = (int16_t)ldc;
+    s.mref = mref;
+    s.nref = nref;
     s.flags = fl;
     if ((int64_t)P.items.size() + (int64_t)it.size() > INT32_MAX) throw Error(H2_ENOMEM, "plan too large");
     P.items.insert(P.items.end(), it.begin(), it.end());
     P.segs.push_back(s);
     P.flops += 2LL * m * n * k * (int64_t)it.size();
   }
-  void gemm1(int64_t out, int m, int n, int k, int lda, int ldb, int ldc, uint8_t fl, int64_t a, int64_t b) {
-    gemm(out, m, n, k, lda, ldb, ldc, fl, {Item{a, b}});
+  void gemm1(int64_t out, int m, int n, int k, int lda, int ldb, int ldc, uint8_t fl, int64_t a, int64_t b,
+             int32_t mref = -1, int32_t nref = -1, int32_t kref = -1) {
+    gemm(out, m, n, k, lda, ldb, ldc, fl, {Item{a, b, kref}}, mref, nref);
   }
   void sum(int64_t out, int m, int n, int lda, int ldc, bool acc, const std::vector<int64_t>& mats) {
     if (m <= 0 || n <= 0 || mats.empty()) return;
@@ -117,6 +120,8 @@ struct PlanBuilder {
     s.lda = (int16_t)lda;
     s.ldb = 0;
     s.ldc = (int16_t)ldc;
+    s.mref = -1;
+    s.nref = -1;
     s.flags = SF_SUM | (acc ? SF_ACC : 0);
     P.items.insert(P.items.end(), it.begin(), it.end());
     P.segs.push_back(s);
@@ -209,6 +214,13 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
   auto tB = [&](int64_t o) { return tag(AR_B, o); };
   auto tC = [&](int64_t o) { return tag(AR_C, o); };
   auto G = [](int l) { return (l & 1) ? AR_G1 : AR_G0; };
+  // rank references of cluster t of level l (loop bounds read on the device)
+  auto AR = [](int l, int64_t t) { return rref(RK_AR, Structure::node(l, t)); };
+  auto AC = [](int l, int64_t t) { return rref(RK_AC, Structure::node(l, t)); };
+  auto BR = [](int l, int64_t t) { return rref(RK_BR, Structure::node(l, t)); };
+  auto BC = [](int l, int64_t t) { return rref(RK_BC, Structure::node(l, t)); };
+  auto CR = [](int l, int64_t t) { return rref(RK_CR, Structure::node(l, t)); };
+  auto CC = [](int l, int64_t t) { return rref(RK_CC, Structure::node(l, t)); };
   const int64_t LS2 = (int64_t)LS * LS;
 
   const size_t zP = pb.open_memset(AR_P);  // couplings held by NL targets accumulate
@@ -234,7 +246,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
     if (leaf) {
       pb.begin();
       for (int64_t j = 0; j < nc; ++j)
-        pb.gemm1(Bj[l][j], cA(l), rB(l), LS, cA(l), rB(l), rB(l), SF_TA, tA(A.Vc(j)), tB(B.Vr(j)));
+        pb.gemm1(Bj[l][j], cA(l), rB(l), LS, cA(l), rB(l), rB(l), SF_TA, tA(A.Vc(j)), tB(B.Vr(j)), AC(l, j), BR(l, j));
       pb.end("bprod", l);
     } else {
       std::vector<int64_t> tmp(2 * nc);
@@ -243,13 +255,14 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       for (int64_t j = 0; j < nc; ++j)
         for (int a = 0; a < 2; ++a)
           pb.gemm1(tmp[2 * j + a], cA(c), rB(l), rB(c), rB(c), rB(l), rB(l), 0, Bj[c][2 * j + a],
-                   tB(B.Er(l, j) + (int64_t)a * rB(c) * rB(l)));
+                   tB(B.Er(l, j) + (int64_t)a * rB(c) * rB(l)), AC(c, 2 * j + a), BR(l, j), BR(c, 2 * j + a));
       pb.end("bprod", l);
       pb.begin();
       for (int64_t j = 0; j < nc; ++j) {
         std::vector<Item> it;
-        for (int a = 0; a < 2; ++a) it.push_back({tA(A.Ec(l, j) + (int64_t)a * cA(c) * cA(l)), tmp[2 * j + a]});
-        pb.gemm(Bj[l][j], cA(l), rB(l), cA(c), cA(l), rB(l), rB(l), SF_TA, it);
+        for (int a = 0; a < 2; ++a)
+          it.push_back({tA(A.Ec(l, j) + (int64_t)a * cA(c) * cA(l)), tmp[2 * j + a], AC(c, 2 * j + a)});
+        pb.gemm(Bj[l][j], cA(l), rB(l), cA(c), cA(l), rB(l), rB(l), SF_TA, it, AC(l, j), BR(l, j));
       }
       pb.end("bprod", l);
     }
@@ -279,8 +292,10 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
     for (int64_t p = 0; p < nb; ++p) {
       const Block& b = bl[p];
       if (b.kind != KR) continue;
-      pb.gemm1(T1[p], rA(l), rB(l), cA(l), cA(l), rB(l), rB(l), 0, tA(A.S(l, b.idx)), Bj[l][b.s]);
-      pb.gemm1(T2[p], cA(l), cB(l), rB(l), rB(l), cB(l), cB(l), 0, Bj[l][b.t], tB(B.S(l, b.idx)));
+      pb.gemm1(T1[p], rA(l), rB(l), cA(l), cA(l), rB(l), rB(l), 0, tA(A.S(l, b.idx)), Bj[l][b.s], AR(l, b.t),
+               BR(l, b.s), AC(l, b.s));
+      pb.gemm1(T2[p], cA(l), cB(l), rB(l), rB(l), cB(l), cB(l), 0, Bj[l][b.t], tB(B.S(l, b.idx)), AC(l, b.t),
+               BC(l, b.s), BR(l, b.t));
     }
     pb.end("rprod", l);
 
@@ -310,9 +325,9 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         const Target& T = lt.tg[tr.tgt];
         if (T.cls == TC_F) {
           if (ba.kind == KF && bb.kind == KF) gF[tr.tgt].push_back({tA(A.F(ba.idx)), tB(B.F(bb.idx))});
-          else if (ba.kind == KF) gZ[tr.tgt].push_back({Y[tr.pa], tB(B.S(l, bb.idx))});
-          else if (bb.kind == KF) gZp[tr.tgt].push_back({tA(A.S(l, ba.idx)), Yb[tr.pb]});
-          else gZpp[tr.tgt].push_back({T1[tr.pa], tB(B.S(l, bb.idx))});
+          else if (ba.kind == KF) gZ[tr.tgt].push_back({Y[tr.pa], tB(B.S(l, bb.idx)), BR(l, ba.s)});
+          else if (bb.kind == KF) gZp[tr.tgt].push_back({tA(A.S(l, ba.idx)), Yb[tr.pb], AC(l, ba.s)});
+          else gZpp[tr.tgt].push_back({T1[tr.pa], tB(B.S(l, bb.idx)), BR(l, ba.s)});
         } else if (ba.kind == KF && bb.kind == KF) {
           Ksets[tr.pa].push_back(Q[tr.pb]);
           Isets[tr.pb].push_back(Rr[tr.pa]);
@@ -338,14 +353,14 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       for (int64_t p = 0; p < nb; ++p) {
         const Block& b = bl[p];
         if (b.kind != KF) continue;
-        pb.gemm1(Y[p], LS, rB(l), LS, LS, rB(l), rB(l), 0, tA(A.F(b.idx)), tB(B.Vr(b.s)));
-        pb.gemm1(Yb[p], cA(l), LS, LS, cA(l), LS, LS, SF_TA, tA(A.Vc(b.t)), tB(B.F(b.idx)));
+        pb.gemm1(Y[p], LS, rB(l), LS, LS, rB(l), rB(l), 0, tA(A.F(b.idx)), tB(B.Vr(b.s)), -1, BR(l, b.s));
+        pb.gemm1(Yb[p], cA(l), LS, LS, cA(l), LS, LS, SF_TA, tA(A.Vc(b.t)), tB(B.F(b.idx)), AC(l, b.t));
         pb.gemm1(Q[p], LS, LS, LS, LS, LS, LS, SF_TB, tB(B.F(b.idx)), tB(B.F(b.idx)));
         pb.gemm1(Rr[p], LS, LS, LS, LS, LS, LS, SF_TA, tA(A.F(b.idx)), tA(A.F(b.idx)));
       }
       for (int64_t t = 0; t < nc; ++t) {
-        pb.gemm1(G3r[t], LS, LS, rA(l), rA(l), rA(l), LS, SF_TB, tA(A.Vr(t)), tA(A.Vr(t)));
-        pb.gemm1(G3c[t], LS, LS, cB(l), cB(l), cB(l), LS, SF_TB, tB(B.Vc(t)), tB(B.Vc(t)));
+        pb.gemm1(G3r[t], LS, LS, rA(l), rA(l), rA(l), LS, SF_TB, tA(A.Vr(t)), tA(A.Vr(t)), -1, -1, AR(l, t));
+        pb.gemm1(G3c[t], LS, LS, cB(l), cB(l), cB(l), LS, SF_TB, tB(B.Vc(t)), tB(B.Vc(t)), -1, -1, BC(l, t));
       }
       pb.end("leaf_blockprod", l);
       // L2: dense targets (Sec. III-A) and Gram pieces
@@ -354,9 +369,9 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         const Target& T = lt.tg[q];
         if (T.cls != TC_F) continue;
         pb.gemm(tC(C.F(bl[T.cpos].idx)), LS, LS, LS, LS, LS, LS, SF_ACC, gF[q]);
-        pb.gemm(Z[q], LS, cB(l), rB(l), rB(l), cB(l), cB(l), 0, gZ[q]);
-        pb.gemm(Zp[q], rA(l), LS, cA(l), cA(l), LS, LS, 0, gZp[q]);
-        pb.gemm(Zpp[q], rA(l), cB(l), rB(l), rB(l), cB(l), cB(l), 0, gZpp[q]);
+        pb.gemm(Z[q], LS, cB(l), rB(l), rB(l), cB(l), cB(l), 0, gZ[q], -1, BC(l, T.k));
+        pb.gemm(Zp[q], rA(l), LS, cA(l), cA(l), LS, LS, 0, gZp[q], AR(l, T.i));
+        pb.gemm(Zpp[q], rA(l), cB(l), rB(l), rB(l), cB(l), cB(l), 0, gZpp[q], AR(l, T.i), BC(l, T.k));
       }
       for (int64_t p = 0; p < nb; ++p) {
         pb.sum(Wsum[p], LS, LS, LS, LS, false, Ksets[p]);
@@ -365,10 +380,10 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       for (int64_t t = 0; t < nc; ++t) {
         std::vector<Item> r2, c2;
         for (int32_t p = st.row_ptr[l][t]; p < st.row_ptr[l][t + 1]; ++p)
-          if (bl[p].kind == KF) r2.push_back({Y[p], Y[p]});
+          if (bl[p].kind == KF) r2.push_back({Y[p], Y[p], BR(l, bl[p].s)});
         for (int32_t q = st.col_ptr[l][t]; q < st.col_ptr[l][t + 1]; ++q) {
           int32_t p = st.col_list[l][q];
-          if (bl[p].kind == KF) c2.push_back({Yb[p], Yb[p]});
+          if (bl[p].kind == KF) c2.push_back({Yb[p], Yb[p], AC(l, bl[p].t)});
         }
         if (!r2.empty()) {
           G2r[t] = pb.alloc(AR_S, LS2);
@@ -385,7 +400,8 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       for (size_t q = 0; q < lt.tg.size(); ++q) {
         const Target& T = lt.tg[q];
         if (T.cls == TC_F && Zpp[q] >= 0)
-          pb.gemm1(Z[q], LS, cB(l), rA(l), rA(l), cB(l), cB(l), SF_ACC, tA(A.Vr(T.i)), Zpp[q]);
+          pb.gemm1(Z[q], LS, cB(l), rA(l), rA(l), cB(l), cB(l), SF_ACC, tA(A.Vr(T.i)), Zpp[q], -1, BC(l, T.k),
+                   AR(l, T.i));
       }
       for (int64_t p = 0; p < nb; ++p) {
         if (Wsum[p] >= 0) pb.gemm1(Q[p], LS, LS, LS, LS, LS, LS, 0, tA(A.F(bl[p].idx)), Wsum[p]);
@@ -397,7 +413,8 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       for (size_t q = 0; q < lt.tg.size(); ++q) {
         const Target& T = lt.tg[q];
         if (T.cls == TC_F && Z[q] >= 0)
-          pb.gemm1(tC(C.F(bl[T.cpos].idx)), LS, LS, cB(l), cB(l), cB(l), LS, SF_TB | SF_ACC, Z[q], tB(B.Vc(T.k)));
+          pb.gemm1(tC(C.F(bl[T.cpos].idx)), LS, LS, cB(l), cB(l), cB(l), LS, SF_TB | SF_ACC, Z[q], tB(B.Vc(T.k)), -1,
+                   -1, BC(l, T.k));
       }
       for (int64_t t = 0; t < nc; ++t) {
         std::vector<Item> r1, c1;
@@ -421,7 +438,8 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       for (size_t q = 0; q < lt.tg.size(); ++q) {
         const Target& T = lt.tg[q];
         if (T.cls == TC_F && Zp[q] >= 0)
-          pb.gemm1(tC(C.F(bl[T.cpos].idx)), LS, LS, rA(l), rA(l), LS, LS, SF_ACC, tA(A.Vr(T.i)), Zp[q]);
+          pb.gemm1(tC(C.F(bl[T.cpos].idx)), LS, LS, rA(l), rA(l), LS, LS, SF_ACC, tA(A.Vr(T.i)), Zp[q], -1, -1,
+                   AR(l, T.i));
       }
       pb.end("leaf_dense", l);
       // case-1 couplings after the eig reuse Q (as V^C_i^T F_ij) and Rr (as F_jk V^C_k)
@@ -467,15 +485,15 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       for (int64_t p = 0; p < nb; ++p) {
         const Block& b = bl[p];
         if (b.kind != KNL) continue;
-        pb.gemm1(Y[p], gr, rB(l), 2 * rB(c), 2 * rB(c), rB(l), rB(l), 0, Ac[p], tB(B.Er(l, b.s)));
-        pb.gemm1(Yb[p], cA(l), gc, 2 * cA(c), cA(l), gc, gc, SF_TA, tA(A.Ec(l, b.t)), Bc[p]);
+        pb.gemm1(Y[p], gr, rB(l), 2 * rB(c), 2 * rB(c), rB(l), rB(l), 0, Ac[p], tB(B.Er(l, b.s)), -1, BR(l, b.s));
+        pb.gemm1(Yb[p], cA(l), gc, 2 * cA(c), cA(l), gc, gc, SF_TA, tA(A.Ec(l, b.t)), Bc[p], AC(l, b.t));
       }
       for (int64_t t = 0; t < nc; ++t)
         for (int a = 0; a < 2; ++a) {
           pb.gemm1(Wr[t] + (int64_t)a * hr * rA(l), hr, rA(l), rA(c), rA(c), rA(l), rA(l), 0, PA[c][2 * t + a],
-                   tA(A.Er(l, t) + (int64_t)a * rA(c) * rA(l)));
+                   tA(A.Er(l, t) + (int64_t)a * rA(c) * rA(l)), CR(c, 2 * t + a), AR(l, t), AR(c, 2 * t + a));
           pb.gemm1(Wc[t] + (int64_t)a * hc * cB(l), hc, cB(l), cB(c), hc, cB(l), cB(l), SF_TA, PB[c][2 * t + a],
-                   tB(B.Ec(l, t) + (int64_t)a * cB(c) * cB(l)));
+                   tB(B.Ec(l, t) + (int64_t)a * cB(c) * cB(l)), CC(c, 2 * t + a), BC(l, t), BC(c, 2 * t + a));
         }
       // Eq. case1-ch-nl from the children's summed couplings, without assembling M:
       // block (a, a') of G1r_i = sum over targets (i, k), b of S_{ia,kb} S_{ia',kb}^T
@@ -499,8 +517,10 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
               std::vector<Item> it;
               for (auto& tq : trow[t])
                 for (int b = 0; b < 2; ++b)
-                  it.push_back({child_ssum(lt.tg[tq.first], a, b), child_ssum(lt.tg[tq.first], a2, b)});
-              pb.gemm(G1r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr, hr, hr, hc, hc, hc, gr, SF_TB, it);
+                  it.push_back({child_ssum(lt.tg[tq.first], a, b), child_ssum(lt.tg[tq.first], a2, b),
+                                CC(c, 2 * lt.tg[tq.first].k + b)});
+              pb.gemm(G1r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr, hr, hr, hc, hc, hc, gr, SF_TB, it,
+                      CR(c, 2 * t + a), CR(c, 2 * t + a2));
             }
         }
         if (!tcol[t].empty()) {
@@ -510,8 +530,10 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
               std::vector<Item> it;
               for (auto& tq : tcol[t])
                 for (int a = 0; a < 2; ++a)
-                  it.push_back({child_ssum(lt.tg[tq.first], a, b), child_ssum(lt.tg[tq.first], a, b2)});
-              pb.gemm(G1c[t] + (int64_t)b * hc * gc + (int64_t)b2 * hc, hc, hc, hr, hc, hc, gc, SF_TA, it);
+                  it.push_back({child_ssum(lt.tg[tq.first], a, b), child_ssum(lt.tg[tq.first], a, b2),
+                                CR(c, 2 * lt.tg[tq.first].i + a)});
+              pb.gemm(G1c[t] + (int64_t)b * hc * gc + (int64_t)b2 * hc, hc, hc, hr, hc, hc, gc, SF_TA, it,
+                      CC(c, 2 * t + b), CC(c, 2 * t + b2));
             }
         }
       }
@@ -520,10 +542,10 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       for (int64_t t = 0; t < nc; ++t) {
         std::vector<Item> r2, c2;
         for (int32_t p = st.row_ptr[l][t]; p < st.row_ptr[l][t + 1]; ++p)
-          if (bl[p].kind == KNL) r2.push_back({Y[p], Y[p]});
+          if (bl[p].kind == KNL) r2.push_back({Y[p], Y[p], BR(l, bl[p].s)});
         for (int32_t q = st.col_ptr[l][t]; q < st.col_ptr[l][t + 1]; ++q) {
           int32_t p = st.col_list[l][q];
-          if (bl[p].kind == KNL) c2.push_back({Yb[p], Yb[p]});
+          if (bl[p].kind == KNL) c2.push_back({Yb[p], Yb[p], AC(l, bl[p].t)});
         }
         if (!r2.empty()) {
           G2r[t] = pb.alloc(AR_S, (int64_t)gr * gr);
@@ -533,8 +555,8 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
           G2c[t] = pb.alloc(AR_S, (int64_t)gc * gc);
           pb.gemm(G2c[t], gc, gc, cA(l), gc, gc, gc, SF_TA, c2);
         }
-        pb.gemm1(G3r[t], gr, gr, rA(l), rA(l), rA(l), gr, SF_TB, Wr[t], Wr[t]);  // Eq. case3-ch-nl
-        pb.gemm1(G3c[t], gc, gc, cB(l), cB(l), cB(l), gc, SF_TB, Wc[t], Wc[t]);
+        pb.gemm1(G3r[t], gr, gr, rA(l), rA(l), rA(l), gr, SF_TB, Wr[t], Wr[t], -1, -1, AR(l, t));  // Eq. case3-ch-nl
+        pb.gemm1(G3c[t], gc, gc, cB(l), cB(l), cB(l), gc, SF_TB, Wc[t], Wc[t], -1, -1, BC(l, t));
       }
       pb.end("nl_gram", l);
       for (size_t q = 0; q < lt.tg.size(); ++q)
@@ -572,23 +594,23 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
     pb.begin();
     for (int64_t t = 0; t < nc; ++t) {
       if (leaf) {
-        pb.gemm1(PA[l][t], rC(l), rA(l), LS, rC(l), rA(l), rA(l), SF_TA, tC(C.Vr(t)), tA(A.Vr(t)));
-        pb.gemm1(PB[l][t], cB(l), cC(l), LS, cB(l), cC(l), cC(l), SF_TA, tB(B.Vc(t)), tC(C.Vc(t)));
+        pb.gemm1(PA[l][t], rC(l), rA(l), LS, rC(l), rA(l), rA(l), SF_TA, tC(C.Vr(t)), tA(A.Vr(t)), CR(l, t), AR(l, t));
+        pb.gemm1(PB[l][t], cB(l), cC(l), LS, cB(l), cC(l), cC(l), SF_TA, tB(B.Vc(t)), tC(C.Vc(t)), BC(l, t), CC(l, t));
       } else {
-        pb.gemm1(PA[l][t], rC(l), rA(l), gr, rC(l), rA(l), rA(l), SF_TA, tC(C.Er(l, t)), Wr[t]);
-        pb.gemm1(PB[l][t], cB(l), cC(l), gc, cB(l), cC(l), cC(l), SF_TA, Wc[t], tC(C.Ec(l, t)));
+        pb.gemm1(PA[l][t], rC(l), rA(l), gr, rC(l), rA(l), rA(l), SF_TA, tC(C.Er(l, t)), Wr[t], CR(l, t), AR(l, t));
+        pb.gemm1(PB[l][t], cB(l), cC(l), gc, cB(l), cC(l), cC(l), SF_TA, Wc[t], tC(C.Ec(l, t)), BC(l, t), CC(l, t));
       }
     }
     for (int64_t p = 0; p < nb; ++p) {
       const Block& b = bl[p];
       if (leaf && b.kind == KF) {
-        pb.gemm1(Ahat[l][p], rC(l), rB(l), LS, rC(l), rB(l), rB(l), SF_TA, tC(C.Vr(b.t)), Y[p]);
-        pb.gemm1(Bhat[l][p], cA(l), cC(l), LS, LS, cC(l), cC(l), 0, Yb[p], tC(C.Vc(b.s)));
-        pb.gemm1(Ach[p], rC(l), LS, LS, rC(l), LS, LS, SF_TA, tC(C.Vr(b.t)), tA(A.F(b.idx)));
-        pb.gemm1(Bch[p], LS, cC(l), LS, LS, cC(l), cC(l), 0, tB(B.F(b.idx)), tC(C.Vc(b.s)));
+        pb.gemm1(Ahat[l][p], rC(l), rB(l), LS, rC(l), rB(l), rB(l), SF_TA, tC(C.Vr(b.t)), Y[p], CR(l, b.t), BR(l, b.s));
+        pb.gemm1(Bhat[l][p], cA(l), cC(l), LS, LS, cC(l), cC(l), 0, Yb[p], tC(C.Vc(b.s)), AC(l, b.t), CC(l, b.s));
+        pb.gemm1(Ach[p], rC(l), LS, LS, rC(l), LS, LS, SF_TA, tC(C.Vr(b.t)), tA(A.F(b.idx)), CR(l, b.t));
+        pb.gemm1(Bch[p], LS, cC(l), LS, LS, cC(l), cC(l), 0, tB(B.F(b.idx)), tC(C.Vc(b.s)), -1, CC(l, b.s));
       } else if (!leaf && b.kind == KNL) {
-        pb.gemm1(Ahat[l][p], rC(l), rB(l), gr, rC(l), rB(l), rB(l), SF_TA, tC(C.Er(l, b.t)), Y[p]);
-        pb.gemm1(Bhat[l][p], cA(l), cC(l), gc, gc, cC(l), cC(l), 0, Yb[p], tC(C.Ec(l, b.s)));
+        pb.gemm1(Ahat[l][p], rC(l), rB(l), gr, rC(l), rB(l), rB(l), SF_TA, tC(C.Er(l, b.t)), Y[p], CR(l, b.t), BR(l, b.s));
+        pb.gemm1(Bhat[l][p], cA(l), cC(l), gc, gc, cC(l), cC(l), 0, Yb[p], tC(C.Ec(l, b.s)), AC(l, b.t), CC(l, b.s));
       }
     }
     if (!leaf) {
@@ -601,9 +623,10 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
           std::vector<Item> it;
           for (int b = 0; b < 2; ++b) {
             auto f = LT[c].id.find(Structure::key(2 * T.i + a, 2 * T.k + b));
-            it.push_back({LT[c].tg[f->second].ssum, tC(C.Ec(l, T.k) + (int64_t)b * hc * cC(l))});
+            it.push_back({LT[c].tg[f->second].ssum, tC(C.Ec(l, T.k) + (int64_t)b * hc * cC(l)), CC(c, 2 * T.k + b)});
           }
-          pb.gemm(Mt[q] + (int64_t)a * hr * cC(l), hr, cC(l), hc, hc, cC(l), cC(l), 0, it);
+          pb.gemm(Mt[q] + (int64_t)a * hr * cC(l), hr, cC(l), hc, hc, cC(l), cC(l), 0, it, CR(c, 2 * T.i + a),
+                  CC(l, T.k));
         }
       }
     }
@@ -613,10 +636,14 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
     for (int64_t p = 0; p < nb; ++p) {
       const Block& b = bl[p];
       if (b.kind != KR) continue;
-      pb.gemm1(Ahat[l][p], rC(l), rB(l), rA(l), rA(l), rB(l), rB(l), 0, PA[l][b.t], T1[p]);
-      pb.gemm1(Bhat[l][p], cA(l), cC(l), cB(l), cB(l), cC(l), cC(l), 0, T2[p], PB[l][b.s]);
-      pb.gemm1(PAS[p], rC(l), cA(l), rA(l), rA(l), cA(l), cA(l), 0, PA[l][b.t], tA(A.S(l, b.idx)));
-      pb.gemm1(SBP[p], rB(l), cC(l), cB(l), cB(l), cC(l), cC(l), 0, tB(B.S(l, b.idx)), PB[l][b.s]);
+      pb.gemm1(Ahat[l][p], rC(l), rB(l), rA(l), rA(l), rB(l), rB(l), 0, PA[l][b.t], T1[p], CR(l, b.t), BR(l, b.s),
+               AR(l, b.t));
+      pb.gemm1(Bhat[l][p], cA(l), cC(l), cB(l), cB(l), cC(l), cC(l), 0, T2[p], PB[l][b.s], AC(l, b.t), CC(l, b.s),
+               BC(l, b.s));
+      pb.gemm1(PAS[p], rC(l), cA(l), rA(l), rA(l), cA(l), cA(l), 0, PA[l][b.t], tA(A.S(l, b.idx)), CR(l, b.t),
+               AC(l, b.s), AR(l, b.t));
+      pb.gemm1(SBP[p], rB(l), cC(l), cB(l), cB(l), cC(l), cC(l), 0, tB(B.S(l, b.idx)), PB[l][b.s], BR(l, b.t),
+               CC(l, b.s), BC(l, b.s));
     }
     pb.end("rimage", l);
 
@@ -628,24 +655,30 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       if (T.cls == TC_F) continue;
       if (ba.kind == KNL && bb.kind == KNL) continue;
       if (ba.kind == KF && bb.kind == KF) continue;                      // case-1 (leaf)
-      if (bb.kind == KR) g24[tr.tgt].push_back({Ahat[l][tr.pa], SBP[tr.pb]});   // case-2, case-4
-      else g3[tr.tgt].push_back({PAS[tr.pa], Bhat[l][tr.pb]});                   // case-3
+      if (bb.kind == KR) g24[tr.tgt].push_back({Ahat[l][tr.pa], SBP[tr.pb], BR(l, ba.s)});  // case-2, case-4
+      else g3[tr.tgt].push_back({PAS[tr.pa], Bhat[l][tr.pb], AC(l, ba.s)});                  // case-3
     }
     pb.begin();
     for (size_t q = 0; q < lt.tg.size(); ++q) {
       Target& T = lt.tg[q];
       if (T.cls == TC_F) continue;
-      if (leaf) pb.gemm(T.ssum, rC(l), cC(l), LS, LS, cC(l), cC(l), SF_ACC, T.g1);   // case-1
-      else if (Mt[q] >= 0) pb.gemm1(T.ssum, rC(l), cC(l), gr, rC(l), cC(l), cC(l), SF_TA | SF_ACC, tC(C.Er(l, T.i)), Mt[q]);
+      if (leaf) pb.gemm(T.ssum, rC(l), cC(l), LS, LS, cC(l), cC(l), SF_ACC, T.g1, CR(l, T.i), CC(l, T.k));  // case-1
+      else if (Mt[q] >= 0)
+        pb.gemm1(T.ssum, rC(l), cC(l), gr, rC(l), cC(l), cC(l), SF_TA | SF_ACC, tC(C.Er(l, T.i)), Mt[q], CR(l, T.i),
+                 CC(l, T.k));
     }
     pb.end("coup", l);
     pb.begin();
     for (size_t q = 0; q < lt.tg.size(); ++q)
-      if (lt.tg[q].cls != TC_F) pb.gemm(lt.tg[q].ssum, rC(l), cC(l), rB(l), rB(l), cC(l), cC(l), SF_ACC, g24[q]);
+      if (lt.tg[q].cls != TC_F)
+        pb.gemm(lt.tg[q].ssum, rC(l), cC(l), rB(l), rB(l), cC(l), cC(l), SF_ACC, g24[q], CR(l, lt.tg[q].i),
+                CC(l, lt.tg[q].k));
     pb.end("coup", l);
     pb.begin();
     for (size_t q = 0; q < lt.tg.size(); ++q)
-      if (lt.tg[q].cls != TC_F) pb.gemm(lt.tg[q].ssum, rC(l), cC(l), cA(l), cA(l), cC(l), cC(l), SF_ACC, g3[q]);
+      if (lt.tg[q].cls != TC_F)
+        pb.gemm(lt.tg[q].ssum, rC(l), cC(l), cA(l), cA(l), cC(l), cC(l), SF_ACC, g3[q], CR(l, lt.tg[q].i),
+                CC(l, lt.tg[q].k));
     pb.end("coup", l);
     pb.close_memset(zG, g);
     pb.close_memset(zS, AR_S);
@@ -687,11 +720,14 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
     pb.begin();
     for (size_t p = 0; p < bl.size(); ++p)
       if (Xt[p] >= 0)
-        pb.gemm1(Xt[p], rC(l), 2 * hc, cC(l), cC(l), cC(l), 2 * hc, SF_TB, H[l][p], tC(C.Ec(l, bl[p].s)));
+        pb.gemm1(Xt[p], rC(l), 2 * hc, cC(l), cC(l), cC(l), 2 * hc, SF_TB, H[l][p], tC(C.Ec(l, bl[p].s)),
+                 CR(l, bl[p].t), -1, CC(l, bl[p].s));
     pb.end("split", l);
     pb.begin();
     for (size_t p = 0; p < bl.size(); ++p)
-      if (X[p] >= 0) pb.gemm1(X[p], 2 * hr, 2 * hc, rC(l), rC(l), 2 * hc, 2 * hc, 0, tC(C.Er(l, bl[p].t)), Xt[p]);
+      if (X[p] >= 0)
+        pb.gemm1(X[p], 2 * hr, 2 * hc, rC(l), rC(l), 2 * hc, 2 * hc, 0, tC(C.Er(l, bl[p].t)), Xt[p], -1, -1,
+                 CR(l, bl[p].t));
     pb.end("split", l);
     std::vector<std::pair<int64_t, int64_t>> Fupd;
     std::vector<int32_t> Frow;
@@ -709,7 +745,8 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
             pb.sum(H[c][cp], hr, hc, 2 * hc, cC(c), true, {xab});
           } else {
             int64_t tmp = pb.alloc(AR_S, (int64_t)rC(c) * LS);
-            pb.gemm1(tmp, rC(c), LS, cC(c), 2 * hc, cC(c), LS, SF_TB, xab, tC(C.Vc(cb.s)));
+            pb.gemm1(tmp, rC(c), LS, cC(c), 2 * hc, cC(c), LS, SF_TB, xab, tC(C.Vc(cb.s)), CR(c, cb.t), -1,
+                     CC(c, cb.s));
             Fupd.push_back({tmp, tC(C.F(cb.idx))});
             Frow.push_back(cb.t);
           }
@@ -718,7 +755,8 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
     pb.end("split", l);
     pb.begin();
     for (size_t q = 0; q < Fupd.size(); ++q)
-      pb.gemm1(Fupd[q].second, LS, LS, rC(c), rC(c), LS, LS, SF_ACC, tC(C.Vr(Frow[q])), Fupd[q].first);
+      pb.gemm1(Fupd[q].second, LS, LS, rC(c), rC(c), LS, LS, SF_ACC, tC(C.Vr(Frow[q])), Fupd[q].first, -1, -1,
+               CR(c, Frow[q]));
     pb.end("split", c);
     pb.close_memset(zS, AR_S);
   }

@@ -134,3 +134,30 @@ def test_structure_mismatch_is_rejected(lib):
     with pytest.raises(lib.H2Error) as ei:
         ga.mmp(gb, 1e-4)
     assert ei.value.code == lib.H2_ESTRUCT
+
+
+@pytest.mark.parametrize("name,mode,eps", [("cubes_1024", "paper", 1e-4), ("cubes_2048_invr2", "paper", 1e-3),
+                                           ("uniform_1000_ragged", "paper", 1e-4)])
+def test_mixed_product_within_2eps_of_oracle(lib, name, mode, eps):
+    # float32 products with float32 accumulation, float64 Grams/eigen/bases: the
+    # result must stay within 2 eps of the float64 oracle and be no less accurate
+    # against the exact product A B
+    w, leaf, eta, A = oracle_case(name)
+    C = ommp.mmp(A, A, eps, mode)
+    ga = lib.h2_import(w.points, leaf, eta, pack(A))
+    gc = ga.mmp(ga, eps, precision=lib.MIXED_FP32, trunc=mode)
+    d_gpu = gc.to_dense().cpu().numpy()
+    d_orc = oh2.to_dense(C)
+    exact = oh2.to_dense(A) @ oh2.to_dense(A)
+    assert rel(d_gpu, d_orc) < 2 * eps
+    assert rel(d_gpu, exact) < 1.2 * rel(d_orc, exact) + 1e-6
+
+
+def test_fp64_rank_bounds_do_not_change_results(lib):
+    # the same product twice, the second time re-using the cached plan and output
+    w, leaf, eta, A = oracle_case("sphere_700_ragged")
+    ga = lib.h2_import(w.points, leaf, eta, pack(A))
+    c1 = ga.mmp(ga, 1e-5, trunc="sv")
+    d1 = c1.to_dense().cpu().numpy()
+    C = ommp.mmp(A, A, 1e-5, "sv")
+    assert rel(d1, oh2.to_dense(C)) < TOL
