@@ -424,7 +424,10 @@ void run_plan(const Plan& P, const ArenaSet& ar, int32_t* kr, int32_t* kc, unsig
     } else if (L.kind == Launch::GEMM) {
       launch_gemm(P.d_segs, P.d_items, L.first, L.count, ar, L.aux, L.aux2, prm.precision == H2_MIXED_FP32, stream);
     } else {
-      launch_eig(P.d_eigs, L.first, L.count, ar, kr, kc, prm.eps, prm.trunc, cap_hits, L.aux, P.d_scratch, stream);
+      if (prm.precision == H2_MIXED_FP32 && L.aux <= 96)
+        launch_eig_mixed(P.d_eigs, L.first, L.count, ar, kr, kc, prm.eps, prm.trunc, cap_hits, L.aux, stream);
+      else
+        launch_eig(P.d_eigs, L.first, L.count, ar, kr, kc, prm.eps, prm.trunc, cap_hits, L.aux, P.d_scratch, stream);
     }
     cuda_check(cudaGetLastError(), L.phase);
     if (tr) cuda_check(cudaEventRecord((cudaEvent_t)tr->ev[2 * li + 1], (cudaStream_t)stream), "event");

@@ -206,6 +206,8 @@ void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, const Arena
                 int32_t* kr, int32_t* kc, double eps, int trunc, unsigned long long* cap_hits,
                 int max_npad, double* scratch, void* stream);
 void launch_to_f32(const double* src, float* dst, int64_t n, void* stream);
+void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const ArenaSet& ar, int32_t* kr,
+                      int32_t* kc, double eps, int trunc, unsigned long long* cap_hits, int max_npad, void* stream);
 void launch_permute(const double* src, double* dst, const int64_t* user, int64_t rows, int64_t n,
                     int64_t nrhs, bool to_tree, void* stream);
 void launch_identity(double* out, int64_t n, void* stream);

@@ -374,6 +374,252 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
   }
 }
 
+// ------------------------------------------------------------ mixed eigen kernel
+// Same task as eig_kernel for the mixed-precision product, with the float64 work
+// cut down: (1) cyclic round-robin Jacobi in float32 on the normalised Gram sum G;
+// (2) the float32 eigenvector matrix is re-orthonormalised in float64 by two
+// Newton-Schulz steps V <- V (3 I - V^T V) / 2 (quadratic: 1e-7 -> 1e-14 -> 1e-16);
+// (3) B = V^T G V in float64 (a similarity transform: same eigenvalues as G, off-
+// diagonal at the float32 level); (4) float64 Jacobi sweeps on B, rotations applied
+// to V, until the off-diagonal norm is below 1e-13 of the total.  Ranks are decided
+// on the float64 eigenvalues of B; the new bases are V's columns (float64,
+// orthonormal).  Shared memory: G, V, T, each n x n float64 (n <= 96).
+constexpr int kMixMax = 96;
+
+template <typename T>
+__device__ void jacobi_sweeps(T* A, T* V, int nn, int max_sweeps, double tol, double* red, T* cs, T* sn, int* pp,
+                              int* qq) {
+  const int tid = threadIdx.x, nt = blockDim.x, np = nn / 2;
+  for (int sweep = 0; sweep < max_sweeps && nn > 1; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int e = tid; e < nn * nn; e += nt) {
+      double v = (double)A[e] * (double)A[e];
+      tot += v;
+      if (e / nn != e % nn) off += v;
+    }
+    off = block_sum(off, red);
+    tot = block_sum(tot, red);
+    if (!(off > tol * tot)) break;
+    for (int step = 0; step < nn - 1; ++step) {
+      for (int k = tid; k < np; k += nt) {
+        int pa = (k == 0) ? 0 : ((k - 1 + step) % (nn - 1)) + 1;
+        int pb = ((nn - 1 - k - 1 + step) % (nn - 1)) + 1;
+        int p = min(pa, pb), q = max(pa, pb);
+        T apq = A[p * nn + q];
+        T c = T(1), s = T(0);
+        if (apq != T(0)) {
+          T tau = (A[q * nn + q] - A[p * nn + p]) / (T(2) * apq);
+          T tt = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+          c = T(1) / sqrt(T(1) + tt * tt);
+          s = tt * c;
+        }
+        pp[k] = p;
+        qq[k] = q;
+        cs[k] = c;
+        sn[k] = s;
+      }
+      __syncthreads();
+      for (int e = tid; e < np * nn; e += nt) {
+        int k = e / nn, j = e % nn;
+        if (sn[k] == T(0)) continue;
+        int p = pp[k], q = qq[k];
+        T x = A[p * nn + j], y = A[q * nn + j];
+        A[p * nn + j] = cs[k] * x - sn[k] * y;
+        A[q * nn + j] = sn[k] * x + cs[k] * y;
+      }
+      __syncthreads();
+      for (int e = tid; e < np * nn; e += nt) {
+        int k = e / nn, i = e % nn;
+        if (sn[k] == T(0)) continue;
+        int p = pp[k], q = qq[k];
+        T x = A[i * nn + p], y = A[i * nn + q];
+        A[i * nn + p] = cs[k] * x - sn[k] * y;
+        A[i * nn + q] = sn[k] * x + cs[k] * y;
+        T vx = V[i * nn + p], vy = V[i * nn + q];
+        V[i * nn + p] = cs[k] * vx - sn[k] * vy;
+        V[i * nn + q] = sn[k] * vx + cs[k] * vy;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// C = op(X) op(Y) for nn x nn float64 matrices in shared memory (C distinct from X, Y)
+__device__ void smem_gemm(const double* X, bool tx, const double* Y, bool ty, double* C, int nn) {
+  for (int e = threadIdx.x; e < nn * nn; e += blockDim.x) {
+    int i = e / nn, j = e % nn;
+    double acc = 0.0;
+    for (int k = 0; k < nn; ++k) acc = fma(tx ? X[k * nn + i] : X[i * nn + k], ty ? Y[j * nn + k] : Y[k * nn + j], acc);
+    C[e] = acc;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) eig_mixed_kernel(const EigTask* __restrict__ tasks, int64_t first, Arenas ar,
+                                                        int32_t* kr, int32_t* kc, double eps, int trunc,
+                                                        unsigned long long* cap_hits) {
+  extern __shared__ double smem[];
+  __shared__ int act[kMixMax + 2];
+  __shared__ double red[8];
+  __shared__ double cs[kMixMax / 2 + 1], sn[kMixMax / 2 + 1];
+  __shared__ float cs32[kMixMax / 2 + 1], sn32[kMixMax / 2 + 1];
+  __shared__ int pp[kMixMax / 2 + 1], qq[kMixMax / 2 + 1];
+  __shared__ int order[kMixMax + 2];
+  __shared__ double lam[kMixMax + 2];
+  __shared__ int s_n, s_rank;
+  const EigTask t = tasks[first + blockIdx.x];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  int32_t* ranks = t.col ? kc : kr;
+  if (tid == 0) {
+    int n = 0;
+    if (t.child1 < 0) {
+      for (int a = 0; a < t.nleaf; ++a) act[n++] = a;
+    } else {
+      int k1 = ranks[t.child1], k2 = ranks[t.child2];
+      for (int a = 0; a < k1; ++a) act[n++] = a;
+      for (int a = 0; a < k2; ++a) act[n++] = t.half + a;
+    }
+    s_n = n;
+  }
+  __syncthreads();
+  const int n = s_n, nn = n + (n & 1);
+  double* G = smem;               // normalised Gram sum, later B = V^T G V
+  double* V = smem + nn * nn;     // eigenvectors (float64)
+  double* T = smem + 2 * nn * nn; // work: float32 A and V during step (1), products later
+  float* A32 = (float*)T;
+  float* V32 = A32 + nn * nn;
+  for (int e = tid; e < nn * nn; e += nt) G[e] = 0.0;
+  __syncthreads();
+  for (int m = 0; m < 3; ++m) {
+    if (t.g[m] < 0) continue;
+    const View Gm = view(ar, t.g[m]);
+    double loc = 0.0;
+    for (int e = tid; e < n * n; e += nt) {
+      double v = ld<double>(Gm, (int64_t)act[e / n] * t.n_pad + act[e % n]);
+      loc += v * v;
+    }
+    double nrm2 = block_sum(loc, red);
+    if (nrm2 > 0.0) {
+      double inv = 1.0 / sqrt(nrm2);
+      for (int e = tid; e < n * n; e += nt)
+        G[(e / n) * nn + (e % n)] += ld<double>(Gm, (int64_t)act[e / n] * t.n_pad + act[e % n]) * inv;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < nn * nn; e += nt) {
+    int a = e / nn, b = e % nn;
+    if (a < b) {
+      double v = 0.5 * (G[a * nn + b] + G[b * nn + a]);
+      G[a * nn + b] = v;
+      G[b * nn + a] = v;
+    }
+  }
+  __syncthreads();
+  // (1) float32 Jacobi
+  for (int e = tid; e < nn * nn; e += nt) {
+    A32[e] = (float)G[e];
+    V32[e] = (e / nn == e % nn) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  jacobi_sweeps<float>(A32, V32, nn, 12, 1e-12, red, cs32, sn32, pp, qq);
+  for (int e = tid; e < nn * nn; e += nt) V[e] = (double)V32[e];
+  __syncthreads();
+  // (2) two Newton-Schulz steps: V <- V (3 I - V^T V) / 2
+  double* W = T;  // nn x nn
+  for (int it = 0; it < 2; ++it) {
+    smem_gemm(V, true, V, false, W, nn);              // W = V^T V
+    for (int e = tid; e < nn * nn; e += nt) {
+      int i = e / nn, j = e % nn;
+      W[e] = ((i == j) ? 1.5 : 0.0) - 0.5 * W[e];
+    }
+    __syncthreads();
+    // V <- V W, row by row through G's spare... use lam as no-alias buffer per row
+    for (int i = 0; i < nn; ++i) {
+      for (int j = tid; j < nn; j += nt) {
+        double acc = 0.0;
+        for (int k = 0; k < nn; ++k) acc = fma(V[i * nn + k], W[k * nn + j], acc);
+        lam[j] = acc;
+      }
+      __syncthreads();
+      for (int j = tid; j < nn; j += nt) V[i * nn + j] = lam[j];
+      __syncthreads();
+    }
+  }
+  // (3) B = V^T G V
+  smem_gemm(G, false, V, false, T, nn);   // T = G V
+  smem_gemm(V, true, T, false, G, nn);    // G <- V^T T
+  for (int e = tid; e < nn * nn; e += nt) {
+    int a = e / nn, b = e % nn;
+    if (a < b) {
+      double v = 0.5 * (G[a * nn + b] + G[b * nn + a]);
+      G[a * nn + b] = v;
+      G[b * nn + a] = v;
+    }
+  }
+  __syncthreads();
+  // (4) float64 Jacobi on B, rotations accumulated into V
+  jacobi_sweeps<double>(G, V, nn, 10, 1e-26, red, cs, sn, pp, qq);
+  for (int a = tid; a < n; a += nt) lam[a] = G[a * nn + a];
+  __syncthreads();
+  for (int a = tid; a < n; a += nt) {
+    int pos = 0;
+    for (int b = 0; b < n; ++b)
+      if (lam[b] > lam[a] || (lam[b] == lam[a] && b < a)) ++pos;
+    order[pos] = a;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int r = 0;
+    if (n > 0) {
+      if (trunc == H2_TRUNC_FULL) {
+        r = n;
+      } else {
+        double l1 = lam[order[0]];
+        double thr = trunc == H2_TRUNC_SV ? eps * eps : eps;
+        if (l1 > 0.0)
+          while (r < n && lam[order[r]] > thr * l1) ++r;
+      }
+    }
+    if (r > t.kcap) {
+      r = t.kcap;
+      atomicAdd(cap_hits, 1ull);
+    }
+    s_rank = r;
+    ranks[t.rank_out] = r;
+  }
+  __syncthreads();
+  const int rank = s_rank;
+  double* out = (double*)view(ar, t.out).base;
+  for (int e = tid; e < t.n_pad * t.kcap; e += nt) out[e] = 0.0;
+  __syncthreads();
+  for (int c = tid; c < rank; c += nt) {
+    int col = order[c];
+    int best = 0;
+    double bv = -1.0;
+    for (int a = 0; a < n; ++a) {
+      double v = fabs(V[a * nn + col]);
+      if (v > bv) { bv = v; best = a; }
+    }
+    double sg = V[best * nn + col] < 0.0 ? -1.0 : 1.0;
+    for (int a = 0; a < n; ++a) out[(int64_t)act[a] * t.kcap + c] = sg * V[a * nn + col];
+  }
+}
+
+void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const ArenaSet& a, int32_t* kr,
+                      int32_t* kc, double eps, int trunc, unsigned long long* cap_hits, int max_npad, void* stream) {
+  Arenas ar = to_dev(a);
+  int nn = max_npad + (max_npad & 1);
+  size_t smem = (size_t)3 * nn * nn * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(eig_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(3 * kMixMax * kMixMax * sizeof(double)));
+    attr = true;
+  }
+  eig_mixed_kernel<<<(unsigned)count, 256, smem, (cudaStream_t)stream>>>(d_eigs, first, ar, kr, kc, eps, trunc,
+                                                                         cap_hits);
+}
+
 void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, const ArenaSet& a, int32_t* kr,
                 int32_t* kc, double eps, int trunc, unsigned long long* cap_hits, int max_npad, double* scratch,
                 void* stream) {
