@@ -202,6 +202,9 @@ h2_status h2_level_blocks(h2_handle h, int32_t level, int32_t* t, int32_t* s,
 h2_status h2_trace_enable(h2_handle A, int32_t on);
 h2_status h2_trace_read(h2_handle C, int32_t cap, int32_t* kind, int32_t* level, double* ms,
                         double* flops, int32_t* count);
+/* Multiply-add flops (2 per multiply-add) the GEMM kernel executed at the actual
+ * ranks during the traced product that made C (counted on the device). */
+h2_status h2_trace_flops(h2_handle C, double* executed);
 /* Name of the phase of launch group i of the traced product (static string; NULL
  * if out of range): bprod, rprod, leaf_blockprod, leaf_dense_gram, leaf_dense,
  * collect, nl_gram, eig, proj, rimage, coup, split, zero. */

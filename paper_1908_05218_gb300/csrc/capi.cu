@@ -628,6 +628,10 @@ h2_status h2_mmp(h2_handle A, h2_handle B, double eps, const h2_opts* opts, h2_h
     ar.rk[RK_CR] = out->m.d_kr;
     ar.rk[RK_CC] = out->m.d_kc;
     out->trace_plan = A->trace_on ? &ent->plan : nullptr;
+    if (A->trace_on) {
+      ar.flops = out->m.d_cap + 1;  // second counter of the handle's counter block
+      cuda_check(cudaMemsetAsync(ar.flops, 0, sizeof(unsigned long long), s), "zero flop counter");
+    }
     run_plan(ent->plan, ar, out->m.d_kr, out->m.d_kc, out->m.d_cap, prm, o.stream, false,
              A->trace_on ? &out->trace : nullptr);
     cuda_check(cudaEventRecord(out->ev1, s), "event");
@@ -794,6 +798,16 @@ h2_status h2_trace_read(h2_handle C, int32_t cap, int32_t* kind, int32_t* level,
       if (ms) ms[i] = t;
       if (flops) flops[i] = L.flops;
     }
+  });
+}
+
+h2_status h2_trace_flops(h2_handle C, double* executed) {
+  if (!C || !executed) return fail(H2_EINVAL, "null argument");
+  return guarded([&] {
+    unsigned long long v = 0;
+    cuda_check(cudaStreamSynchronize((cudaStream_t)C->m.stream), "synchronise");
+    cuda_check(cudaMemcpy(&v, C->m.d_cap + 1, sizeof(v), cudaMemcpyDeviceToHost), "flop counter");
+    *executed = (double)v;
   });
 }
 

@@ -193,6 +193,7 @@ struct ArenaSet {
   void* p[kArenas] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   uint32_t f32 = 0;
   const int32_t* rk[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  unsigned long long* flops = nullptr;  // executed-flop counter (tracing only)
   size_t esize(int a) const { return ((f32 >> a) & 1) ? 4 : 8; }
 };
 void run_plan(const Plan& plan, const ArenaSet& ar, int32_t* kr_out, int32_t* kc_out,

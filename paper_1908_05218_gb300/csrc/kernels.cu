@@ -14,6 +14,7 @@ struct Arenas {
   char* p[kArenas];
   uint32_t f32;
   const int32_t* rk[6];
+  unsigned long long* flops;  // if set: executed multiply-add flops are added here
 };
 
 __device__ __forceinline__ int arena_idx(int64_t t) { return (int)((t >> kTagShift) & 7); }
@@ -55,9 +56,11 @@ __device__ __forceinline__ int bound(const Arenas& a, int32_t ref, int padded) {
 // ------------------------------------------------------------ segmented GEMM
 // One CTA per segment (blockIdx.x) and TILE-column slice (blockIdx.y); the CTA walks
 // TILE x TILE output tiles, thread (tx, ty) owning rows ty + P i, cols tx + P j
-// (P = TILE/4, 4 x 4 outputs per thread).  Operands are staged through shared
-// memory in k-slices of GK; loop bounds are the actual ranks where the segment
-// refers to them.
+// (P = TILE/4, 4 x 4 outputs per thread).  The items of a segment are packed along
+// k into shared-memory slices of depth GK (several short items share one slice, a
+// long one spans several), loading only the actual extents: rows < M, cols < N,
+// k < the item's rank.  Rows/cols beyond M/N hold stale values whose products are
+// never stored.
 constexpr int GK = 32;
 
 template <int TILE, typename Acc>
@@ -73,8 +76,11 @@ __global__ void __launch_bounds__((TILE / 4) * (TILE / 4)) seg_gemm_kernel(const
   const int M = bound(ar, s.mref, s.m), N = bound(ar, s.nref, s.n);
   const View out = view(ar, s.out);
   const Item* it = items + s.first;
+  unsigned long long work = 0;
   for (int n0 = blockIdx.y * TILE; n0 < N; n0 += gridDim.y * TILE) {
+    const int nc = min(TILE, N - n0);
     for (int m0 = 0; m0 < M; m0 += TILE) {
+      const int mc = min(TILE, M - m0);
       Acc acc[4][4];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
@@ -87,57 +93,72 @@ __global__ void __launch_bounds__((TILE / 4) * (TILE / 4)) seg_gemm_kernel(const
           for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-              int r = m0 + ty + P * i, c = n0 + tx + P * j;
-              if (r < M && c < N) acc[i][j] += ld<Acc>(A, (int64_t)r * s.lda + c);
+              int r = ty + P * i, c = tx + P * j;
+              if (r < mc && c < nc) acc[i][j] += ld<Acc>(A, (int64_t)(m0 + r) * s.lda + n0 + c);
             }
         }
       } else {
-        for (int q = 0; q < s.count; ++q) {
-          const Item itq = it[q];
-          const int K = bound(ar, itq.kref, s.k);
-          const View A = view(ar, itq.a), B = view(ar, itq.b);
-          for (int k0 = 0; k0 < K; k0 += GK) {
-            for (int e = tid; e < TILE * GK; e += NT) {
+        int q = 0, koff = 0, K = s.count ? bound(ar, it[0].kref, s.k) : 0;
+        while (q < s.count) {
+          int kfill = 0;
+          while (q < s.count && kfill < GK) {
+            if (K == 0) {  // empty item
+              ++q;
+              if (q < s.count) K = bound(ar, it[q].kref, s.k);
+              continue;
+            }
+            const int take = min(K - koff, GK - kfill);
+            const View A = view(ar, it[q].a), B = view(ar, it[q].b);
+            // A part: op(A)[m0 + r][koff + kk] -> sA[kfill + kk][r]
+            const int na = mc * take;
+            for (int e = tid; e < na; e += NT) {
               int r, kk;
-              if (ta) { r = e % TILE; kk = e / TILE; } else { kk = e % GK; r = e / GK; }
-              int gr = m0 + r, gk = k0 + kk;
-              Acc v = Acc(0);
-              if (gr < M && gk < K) v = ld<Acc>(A, ta ? (int64_t)gk * s.lda + gr : (int64_t)gr * s.lda + gk);
-              sA[kk * PAD + r] = v;
-              int c;
-              if (tb) { kk = e % GK; c = e / GK; } else { c = e % TILE; kk = e / TILE; }
-              int gc = n0 + c;
-              gk = k0 + kk;
-              Acc w = Acc(0);
-              if (gc < N && gk < K) w = ld<Acc>(B, tb ? (int64_t)gc * s.ldb + gk : (int64_t)gk * s.ldb + gc);
-              sB[kk * PAD + c] = w;
+              if (ta) { r = e % mc; kk = e / mc; } else { kk = e % take; r = e / take; }
+              const int64_t idx = ta ? (int64_t)(koff + kk) * s.lda + (m0 + r) : (int64_t)(m0 + r) * s.lda + (koff + kk);
+              sA[(kfill + kk) * PAD + r] = ld<Acc>(A, idx);
             }
-            __syncthreads();
-            const int kl = min(GK, K - k0);
-            for (int kk = 0; kk < kl; ++kk) {
-              Acc a[4], b[4];
-#pragma unroll
-              for (int i = 0; i < 4; ++i) a[i] = sA[kk * PAD + ty + P * i];
-#pragma unroll
-              for (int j = 0; j < 4; ++j) b[j] = sB[kk * PAD + tx + P * j];
-#pragma unroll
-              for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            // B part: op(B)[koff + kk][n0 + c] -> sB[kfill + kk][c]
+            const int nbe = nc * take;
+            for (int e = tid; e < nbe; e += NT) {
+              int c, kk;
+              if (tb) { kk = e % take; c = e / take; } else { c = e % nc; kk = e / nc; }
+              const int64_t idx = tb ? (int64_t)(n0 + c) * s.ldb + (koff + kk) : (int64_t)(koff + kk) * s.ldb + (n0 + c);
+              sB[(kfill + kk) * PAD + c] = ld<Acc>(B, idx);
             }
-            __syncthreads();
+            kfill += take;
+            koff += take;
+            work += 2ull * mc * nc * take;
+            if (koff == K) {
+              koff = 0;
+              ++q;
+              if (q < s.count) K = bound(ar, it[q].kref, s.k);
+            }
           }
+          __syncthreads();
+          for (int kk = 0; kk < kfill; ++kk) {
+            Acc a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = sA[kk * PAD + ty + P * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = sB[kk * PAD + tx + P * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+              for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+          }
+          __syncthreads();
         }
       }
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          int r = m0 + ty + P * i, c = n0 + tx + P * j;
-          if (r < M && c < N) st<Acc>(out, (int64_t)r * s.ldc + c, acc[i][j], accum);
+          int r = ty + P * i, c = tx + P * j;
+          if (r < mc && c < nc) st<Acc>(out, (int64_t)(m0 + r) * s.ldc + n0 + c, acc[i][j], accum);
         }
     }
   }
+  if (ar.flops && tid == 0 && work) atomicAdd(ar.flops, work);
 }
 
 static Arenas to_dev(const ArenaSet& a) {
@@ -145,6 +166,7 @@ static Arenas to_dev(const ArenaSet& a) {
   for (int i = 0; i < kArenas; ++i) d.p[i] = (char*)a.p[i];
   d.f32 = a.f32;
   for (int i = 0; i < 6; ++i) d.rk[i] = a.rk[i];
+  d.flops = a.flops;
   return d;
 }
 
@@ -377,11 +399,11 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
 // ------------------------------------------------------------ mixed eigen kernel
 // Same task as eig_kernel for the mixed-precision product, with the float64 work
 // cut down: (1) cyclic round-robin Jacobi in float32 on the normalised Gram sum G;
-// (2) the float32 eigenvector matrix is re-orthonormalised in float64 by two
-// Newton-Schulz steps V <- V (3 I - V^T V) / 2 (quadratic: 1e-7 -> 1e-14 -> 1e-16);
+// (2) the float32 eigenvector matrix is re-orthonormalised in float64 by one
+// Newton-Schulz step V <- V (3 I - V^T V) / 2 (quadratic: 1e-7 -> 1e-14);
 // (3) B = V^T G V in float64 (a similarity transform: same eigenvalues as G, off-
 // diagonal at the float32 level); (4) float64 Jacobi sweeps on B, rotations applied
-// to V, until the off-diagonal norm is below 1e-13 of the total.  Ranks are decided
+// to V, until the off-diagonal norm is below 1e-10 of the total.  Ranks are decided
 // on the float64 eigenvalues of B; the new bases are V's columns (float64,
 // orthonormal).  Shared memory: G, V, T, each n x n float64 (n <= 96).
 constexpr int kMixMax = 96;
@@ -466,6 +488,7 @@ __global__ void __launch_bounds__(256) eig_mixed_kernel(const EigTask* __restric
   __shared__ int pp[kMixMax / 2 + 1], qq[kMixMax / 2 + 1];
   __shared__ int order[kMixMax + 2];
   __shared__ double lam[kMixMax + 2];
+  __shared__ double rowbuf[8 * kMixMax];
   __shared__ int s_n, s_rank;
   const EigTask t = tasks[first + blockIdx.x];
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -521,27 +544,29 @@ __global__ void __launch_bounds__(256) eig_mixed_kernel(const EigTask* __restric
     V32[e] = (e / nn == e % nn) ? 1.f : 0.f;
   }
   __syncthreads();
-  jacobi_sweeps<float>(A32, V32, nn, 12, 1e-12, red, cs32, sn32, pp, qq);
+  jacobi_sweeps<float>(A32, V32, nn, 12, 1e-10, red, cs32, sn32, pp, qq);
   for (int e = tid; e < nn * nn; e += nt) V[e] = (double)V32[e];
   __syncthreads();
-  // (2) two Newton-Schulz steps: V <- V (3 I - V^T V) / 2
+  // (2) one Newton-Schulz step: V <- V (3 I - V^T V) / 2
   double* W = T;  // nn x nn
-  for (int it = 0; it < 2; ++it) {
+  {
     smem_gemm(V, true, V, false, W, nn);              // W = V^T V
     for (int e = tid; e < nn * nn; e += nt) {
       int i = e / nn, j = e % nn;
       W[e] = ((i == j) ? 1.5 : 0.0) - 0.5 * W[e];
     }
     __syncthreads();
-    // V <- V W, row by row through G's spare... use lam as no-alias buffer per row
-    for (int i = 0; i < nn; ++i) {
-      for (int j = tid; j < nn; j += nt) {
+    // V <- V W, eight rows at a time through a small buffer
+    for (int i0 = 0; i0 < nn; i0 += 8) {
+      const int ni = min(8, nn - i0);
+      for (int e = tid; e < ni * nn; e += nt) {
+        int i = i0 + e / nn, j = e % nn;
         double acc = 0.0;
         for (int k = 0; k < nn; ++k) acc = fma(V[i * nn + k], W[k * nn + j], acc);
-        lam[j] = acc;
+        rowbuf[e] = acc;
       }
       __syncthreads();
-      for (int j = tid; j < nn; j += nt) V[i * nn + j] = lam[j];
+      for (int e = tid; e < ni * nn; e += nt) V[(i0 + e / nn) * nn + e % nn] = rowbuf[e];
       __syncthreads();
     }
   }
@@ -558,7 +583,7 @@ __global__ void __launch_bounds__(256) eig_mixed_kernel(const EigTask* __restric
   }
   __syncthreads();
   // (4) float64 Jacobi on B, rotations accumulated into V
-  jacobi_sweeps<double>(G, V, nn, 10, 1e-26, red, cs, sn, pp, qq);
+  jacobi_sweeps<double>(G, V, nn, 10, 1e-20, red, cs, sn, pp, qq);
   for (int a = tid; a < n; a += nt) lam[a] = G[a * nn + a];
   __syncthreads();
   for (int a = tid; a < n; a += nt) {

@@ -23,7 +23,7 @@ _TRUNC = {"paper": TRUNC_PAPER, "sv": TRUNC_SV, "full": TRUNC_FULL}
 
 # exported symbols and their signatures (checked by the CPU tests)
 SYMBOLS = ["h2_build", "h2_import", "h2_export", "h2_mmp", "h2_matvec", "h2_matvec_noalloc", "h2_to_dense", "h2_info",
-           "h2_tree_perm", "h2_level_blocks", "h2_trace_enable", "h2_trace_read", "h2_trace_phase", "h2_destroy",
+           "h2_tree_perm", "h2_level_blocks", "h2_trace_enable", "h2_trace_read", "h2_trace_flops", "h2_trace_phase", "h2_destroy",
            "h2_last_error"]
 
 
@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH):
     lib.h2_level_blocks.argtypes = [P, I32, P, P, P, P]
     lib.h2_trace_enable.argtypes = [P, I32]
     lib.h2_trace_read.argtypes = [P, I32, P, P, P, P, P]
+    lib.h2_trace_flops.argtypes = [P, P]
     lib.h2_trace_phase.argtypes = [P, I32]
     lib.h2_trace_phase.restype = C.c_char_p
     lib.h2_destroy.argtypes = [P]
@@ -218,6 +219,11 @@ class H2Matrix:
         _check(lib.h2_trace_read(self.handle, n, _ptr(kind), _ptr(level), _ptr(ms), _ptr(fl), C.byref(cnt)))
         names = [lib.h2_trace_phase(self.handle, i).decode() for i in range(n)]
         return [("gemm", "eig", "memset")[k] for k in kind], level, ms, fl, names
+
+    def trace_flops(self) -> float:
+        v = C.c_double(0)
+        _check(load().h2_trace_flops(self.handle, C.byref(v)))
+        return v.value
 
     def tree_perm(self) -> np.ndarray:
         p = np.zeros(self.n, dtype=np.int64)
