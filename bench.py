@@ -278,8 +278,11 @@ def main():
     for nm, m_ in zip(lnames, lms):
         by_phase[nm] = by_phase.get(nm, 0.0) + m_
     by_level = {}
-    for lv, m_ in zip(levels, lms):
+    eig_by_level = {}
+    for lv, m_, kd in zip(levels, lms, kinds):
         by_level[int(lv)] = by_level.get(int(lv), 0.0) + m_
+        if kd == "eig":
+            eig_by_level[int(lv)] = eig_by_level.get(int(lv), 0.0) + m_
 
     # end to end through the public API with host buffers: upload A and B from host
     # arrays, the product, download C
@@ -322,7 +325,8 @@ def main():
             "ranks_C_max_row": ic["max_rank_row"], "cap_hits": ic["cap_hits"],
             "bytes_alg": nbytes, "build_s": build_s, "first_product_s_incl_plan": setup_s,
             "phase_ms": phase_ms, "phase_ms_by_name": {k: round(v, 3) for k, v in by_phase.items()},
-            "ms_by_level": {k: round(v, 3) for k, v in sorted(by_level.items())}, "roofline": roof, "cpu_baseline": cpu_line, "e2e": e2e,
+            "ms_by_level": {k: round(v, 3) for k, v in sorted(by_level.items())},
+            "eig_ms_by_level": {k: round(v, 3) for k, v in sorted(eig_by_level.items())}, "roofline": roof, "cpu_baseline": cpu_line, "e2e": e2e,
             "gpu_launches": int(sum(tot[k][2] for k in tot if k != "memset")) * args.steps,
             "clocks": clk.summary(),
         }

@@ -109,21 +109,30 @@ __global__ void __launch_bounds__((TILE / 4) * (TILE / 4)) seg_gemm_kernel(const
             }
             const int take = min(K - koff, GK - kfill);
             const View A = view(ar, it[q].a), B = view(ar, it[q].b);
-            // A part: op(A)[m0 + r][koff + kk] -> sA[kfill + kk][r]
-            const int na = mc * take;
-            for (int e = tid; e < na; e += NT) {
-              int r, kk;
-              if (ta) { r = e % mc; kk = e / mc; } else { kk = e % take; r = e / take; }
-              const int64_t idx = ta ? (int64_t)(koff + kk) * s.lda + (m0 + r) : (int64_t)(m0 + r) * s.lda + (koff + kk);
-              sA[(kfill + kk) * PAD + r] = ld<Acc>(A, idx);
+            // A part: op(A)[m0 + r][koff + kk] -> sA[kfill + kk][r]; the fast index of a
+            // thread runs along the contiguous dimension (power-of-two strides only)
+            if (ta) {
+              for (int kk = tid / TILE; kk < take; kk += NT / TILE) {
+                const int r = tid % TILE;
+                if (r < mc) sA[(kfill + kk) * PAD + r] = ld<Acc>(A, (int64_t)(koff + kk) * s.lda + (m0 + r));
+              }
+            } else {
+              for (int r = tid / GK; r < mc; r += NT / GK) {
+                const int kk = tid % GK;
+                if (kk < take) sA[(kfill + kk) * PAD + r] = ld<Acc>(A, (int64_t)(m0 + r) * s.lda + (koff + kk));
+              }
             }
             // B part: op(B)[koff + kk][n0 + c] -> sB[kfill + kk][c]
-            const int nbe = nc * take;
-            for (int e = tid; e < nbe; e += NT) {
-              int c, kk;
-              if (tb) { kk = e % take; c = e / take; } else { c = e % nc; kk = e / nc; }
-              const int64_t idx = tb ? (int64_t)(n0 + c) * s.ldb + (koff + kk) : (int64_t)(koff + kk) * s.ldb + (n0 + c);
-              sB[(kfill + kk) * PAD + c] = ld<Acc>(B, idx);
+            if (tb) {
+              for (int c = tid / GK; c < nc; c += NT / GK) {
+                const int kk = tid % GK;
+                if (kk < take) sB[(kfill + kk) * PAD + c] = ld<Acc>(B, (int64_t)(n0 + c) * s.ldb + (koff + kk));
+              }
+            } else {
+              for (int kk = tid / TILE; kk < take; kk += NT / TILE) {
+                const int c = tid % TILE;
+                if (c < nc) sB[(kfill + kk) * PAD + c] = ld<Acc>(B, (int64_t)(koff + kk) * s.ldb + (n0 + c));
+              }
             }
             kfill += take;
             koff += take;
