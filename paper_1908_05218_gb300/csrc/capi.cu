@@ -383,7 +383,7 @@ void upload_plan(Plan& P, size_t region_esize) {
       if (mx > 256) throw Error(H2_EUNSUPPORTED, "Gram matrix larger than 256 (raise no caps in full mode)");
       L.aux = mx;
       int nn = mx + (mx & 1);
-      if (nn > 112) scratch = std::max<int64_t>(scratch, L.count * 2LL * nn * nn);
+      if (nn > 112) scratch = std::max<int64_t>(scratch, L.count * 2LL * nn * (nn + 1));
     }
   }
   P.d_scratch = (double*)dmalloc(std::max<int64_t>(1, scratch) * sizeof(double));

@@ -54,24 +54,41 @@ __device__ __forceinline__ int bound(const Arenas& a, int32_t ref, int padded) {
 }
 
 // ------------------------------------------------------------ segmented GEMM
-// One CTA per segment (blockIdx.x) and TILE-column slice (blockIdx.y); the CTA walks
-// TILE x TILE output tiles, thread (tx, ty) owning rows ty + P i, cols tx + P j
-// (P = TILE/4, 4 x 4 outputs per thread).  The items of a segment are packed along
-// k into shared-memory slices of depth GK (several short items share one slice, a
-// long one spans several), loading only the actual extents: rows < M, cols < N,
-// k < the item's rank.  Rows/cols beyond M/N hold stale values whose products are
-// never stored.
-constexpr int GK = 32;
+// One CTA (64 threads) per segment (blockIdx.x) and 32-column slice (blockIdx.y);
+// the CTA walks 32 x 32 output tiles; thread (tx, ty) owns the contiguous 4 x 4
+// block rows 4 ty.., cols 4 tx.. and reads it from shared memory with vector
+// loads.  The items of a segment are packed along k into shared-memory slices of
+// depth GK (several short items share a slice, a long one spans several), loading
+// only the actual extents: rows < M, cols < N, k < the item's rank.  A warp whose
+// rows all lie beyond M skips the arithmetic; rows/cols beyond M/N hold stale
+// values whose products are never stored.
+constexpr int GK = 32, TILE = 32, GPAD = TILE + 4, GNT = 64;
 
-template <int TILE, typename Acc>
-__global__ void __launch_bounds__((TILE / 4) * (TILE / 4)) seg_gemm_kernel(const Seg* __restrict__ segs,
-                                                                           const Item* __restrict__ items,
-                                                                           int64_t first, Arenas ar) {
-  constexpr int P = TILE / 4, NT = P * P, PAD = TILE + 1;
-  __shared__ Acc sA[GK * PAD];
-  __shared__ Acc sB[GK * PAD];
+template <typename Acc>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  __device__ static void load(const float* p, float v[4]) {
+    float4 x = *reinterpret_cast<const float4*>(p);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+  }
+};
+template <>
+struct Vec4<double> {
+  __device__ static void load(const double* p, double v[4]) {
+    double2 x = *reinterpret_cast<const double2*>(p);
+    double2 y = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+  }
+};
+
+template <typename Acc>
+__global__ void __launch_bounds__(GNT) seg_gemm_kernel(const Seg* __restrict__ segs, const Item* __restrict__ items,
+                                                       int64_t first, Arenas ar) {
+  __shared__ __align__(16) Acc sA[GK * GPAD];
+  __shared__ __align__(16) Acc sB[GK * GPAD];
   const Seg s = segs[first + blockIdx.x];
-  const int tid = threadIdx.x, tx = tid % P, ty = tid / P;
+  const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
   const bool ta = s.flags & SF_TA, tb = s.flags & SF_TB, accum = s.flags & SF_ACC;
   const int M = bound(ar, s.mref, s.m), N = bound(ar, s.nref, s.n);
   const View out = view(ar, s.out);
@@ -81,6 +98,7 @@ __global__ void __launch_bounds__((TILE / 4) * (TILE / 4)) seg_gemm_kernel(const
     const int nc = min(TILE, N - n0);
     for (int m0 = 0; m0 < M; m0 += TILE) {
       const int mc = min(TILE, M - m0);
+      const bool live = (tid >> 5) * 16 < mc;  // this warp owns rows 16 w .. 16 w + 15
       Acc acc[4][4];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
@@ -93,7 +111,7 @@ __global__ void __launch_bounds__((TILE / 4) * (TILE / 4)) seg_gemm_kernel(const
           for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-              int r = ty + P * i, c = tx + P * j;
+              int r = 4 * ty + i, c = 4 * tx + j;
               if (r < mc && c < nc) acc[i][j] += ld<Acc>(A, (int64_t)(m0 + r) * s.lda + n0 + c);
             }
         }
@@ -109,29 +127,29 @@ __global__ void __launch_bounds__((TILE / 4) * (TILE / 4)) seg_gemm_kernel(const
             }
             const int take = min(K - koff, GK - kfill);
             const View A = view(ar, it[q].a), B = view(ar, it[q].b);
-            // A part: op(A)[m0 + r][koff + kk] -> sA[kfill + kk][r]; the fast index of a
-            // thread runs along the contiguous dimension (power-of-two strides only)
+            // op(A)[m0 + r][koff + kk] -> sA[kfill + kk][r]; the fast thread index runs
+            // along the contiguous dimension of the stored matrix
             if (ta) {
-              for (int kk = tid / TILE; kk < take; kk += NT / TILE) {
+              for (int kk = tid / TILE; kk < take; kk += GNT / TILE) {
                 const int r = tid % TILE;
-                if (r < mc) sA[(kfill + kk) * PAD + r] = ld<Acc>(A, (int64_t)(koff + kk) * s.lda + (m0 + r));
+                if (r < mc) sA[(kfill + kk) * GPAD + r] = ld<Acc>(A, (int64_t)(koff + kk) * s.lda + (m0 + r));
               }
             } else {
-              for (int r = tid / GK; r < mc; r += NT / GK) {
+              for (int r = tid / GK; r < mc; r += GNT / GK) {
                 const int kk = tid % GK;
-                if (kk < take) sA[(kfill + kk) * PAD + r] = ld<Acc>(A, (int64_t)(m0 + r) * s.lda + (koff + kk));
+                if (kk < take) sA[(kfill + kk) * GPAD + r] = ld<Acc>(A, (int64_t)(m0 + r) * s.lda + (koff + kk));
               }
             }
-            // B part: op(B)[koff + kk][n0 + c] -> sB[kfill + kk][c]
+            // op(B)[koff + kk][n0 + c] -> sB[kfill + kk][c]
             if (tb) {
-              for (int c = tid / GK; c < nc; c += NT / GK) {
+              for (int c = tid / GK; c < nc; c += GNT / GK) {
                 const int kk = tid % GK;
-                if (kk < take) sB[(kfill + kk) * PAD + c] = ld<Acc>(B, (int64_t)(n0 + c) * s.ldb + (koff + kk));
+                if (kk < take) sB[(kfill + kk) * GPAD + c] = ld<Acc>(B, (int64_t)(n0 + c) * s.ldb + (koff + kk));
               }
             } else {
-              for (int kk = tid / TILE; kk < take; kk += NT / TILE) {
+              for (int kk = tid / TILE; kk < take; kk += GNT / TILE) {
                 const int c = tid % TILE;
-                if (c < nc) sB[(kfill + kk) * PAD + c] = ld<Acc>(B, (int64_t)(koff + kk) * s.ldb + (n0 + c));
+                if (c < nc) sB[(kfill + kk) * GPAD + c] = ld<Acc>(B, (int64_t)(koff + kk) * s.ldb + (n0 + c));
               }
             }
             kfill += take;
@@ -144,16 +162,16 @@ __global__ void __launch_bounds__((TILE / 4) * (TILE / 4)) seg_gemm_kernel(const
             }
           }
           __syncthreads();
-          for (int kk = 0; kk < kfill; ++kk) {
-            Acc a[4], b[4];
+          if (live) {
+            for (int kk = 0; kk < kfill; ++kk) {
+              Acc a[4], b[4];
+              Vec4<Acc>::load(&sA[kk * GPAD + 4 * ty], a);
+              Vec4<Acc>::load(&sB[kk * GPAD + 4 * tx], b);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = sA[kk * PAD + ty + P * i];
+              for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = sB[kk * PAD + tx + P * j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-              for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            }
           }
           __syncthreads();
         }
@@ -162,7 +180,7 @@ __global__ void __launch_bounds__((TILE / 4) * (TILE / 4)) seg_gemm_kernel(const
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          int r = ty + P * i, c = tx + P * j;
+          int r = 4 * ty + i, c = 4 * tx + j;
           if (r < mc && c < nc) st<Acc>(out, (int64_t)(m0 + r) * s.ldc + n0 + c, acc[i][j], accum);
         }
     }
@@ -179,7 +197,7 @@ static Arenas to_dev(const ArenaSet& a) {
   return d;
 }
 
-template <int TILE, typename Acc>
+template <typename Acc>
 static void gemm_launch(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const Arenas& ar,
                         int maxn, void* stream) {
   const int64_t kMaxGrid = 2147483647LL;
@@ -189,21 +207,16 @@ static void gemm_launch(const Seg* d_segs, const Item* d_items, int64_t first, i
   for (int64_t off = 0; off < count; off += kMaxGrid) {
     int64_t c = count - off < kMaxGrid ? count - off : kMaxGrid;
     dim3 grid((unsigned)c, (unsigned)gy);
-    seg_gemm_kernel<TILE, Acc><<<grid, (TILE / 4) * (TILE / 4), 0, (cudaStream_t)stream>>>(d_segs, d_items,
-                                                                                        first + off, ar);
+    seg_gemm_kernel<Acc><<<grid, GNT, 0, (cudaStream_t)stream>>>(d_segs, d_items, first + off, ar);
   }
 }
 
 void launch_gemm(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const ArenaSet& a, int maxn,
                  int maxdim, bool fp32, void* stream) {
+  (void)maxdim;
   Arenas ar = to_dev(a);
-  if (fp32) {
-    if (maxdim <= 32) gemm_launch<32, float>(d_segs, d_items, first, count, ar, maxn, stream);
-    else gemm_launch<64, float>(d_segs, d_items, first, count, ar, maxn, stream);
-  } else {
-    if (maxdim <= 32) gemm_launch<32, double>(d_segs, d_items, first, count, ar, maxn, stream);
-    else gemm_launch<64, double>(d_segs, d_items, first, count, ar, maxn, stream);
-  }
+  if (fp32) gemm_launch<float>(d_segs, d_items, first, count, ar, maxn, stream);
+  else gemm_launch<double>(d_segs, d_items, first, count, ar, maxn, stream);
 }
 
 __global__ void to_f32_kernel(const double* __restrict__ s, float* __restrict__ d, int64_t n) {
@@ -233,6 +246,10 @@ __device__ double block_sum(double v, double* red) {
   return t;
 }
 
+template <typename T>
+__device__ void jacobi_sweeps(T* A, T* V, int nn, int lds, int max_sweeps, double tol, double* red, T* cs, T* sn,
+                              int* pp, int* qq);
+
 __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ tasks, int64_t first, Arenas ar,
                                                   int32_t* kr, int32_t* kc, double eps, int trunc,
                                                   unsigned long long* cap_hits, double* scratch,
@@ -261,17 +278,17 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
   }
   __syncthreads();
   const int n = s_n;
-  const int nn = n + (n & 1);
+  const int nn = n + (n & 1), lds = nn + 1, sz = nn * lds;
   double *A, *V;
   if (nn <= kEigSmemMax) {
     A = smem;
-    V = smem + nn * nn;
+    V = smem + sz;
   } else {
     A = scratch + blockIdx.x * scratch_stride;
-    V = A + (int64_t)nn * nn;
+    V = A + sz;
   }
   // normalised sum of the Gram matrices over the active rows/cols
-  for (int e = tid; e < nn * nn; e += nt) A[e] = 0.0;
+  for (int e = tid; e < sz; e += nt) A[e] = 0.0;
   __syncthreads();
   for (int m = 0; m < 3; ++m) {
     if (t.g[m] < 0) continue;
@@ -285,80 +302,24 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
     if (nrm2 > 0.0) {
       double inv = 1.0 / sqrt(nrm2);
       for (int e = tid; e < n * n; e += nt)
-        A[(e / n) * nn + (e % n)] += ld<double>(G, (int64_t)act[e / n] * t.n_pad + act[e % n]) * inv;
+        A[(e / n) * lds + (e % n)] += ld<double>(G, (int64_t)act[e / n] * t.n_pad + act[e % n]) * inv;
     }
     __syncthreads();
   }
   // symmetrise (the Grams are symmetric up to rounding of their products)
-  for (int e = tid; e < nn * nn; e += nt) {
-    int a = e / nn, b = e % nn;
-    V[e] = (a == b) ? 1.0 : 0.0;
-  }
-  __syncthreads();
+  for (int e = tid; e < sz; e += nt) V[e] = (e / lds == e % lds) ? 1.0 : 0.0;
   for (int e = tid; e < nn * nn; e += nt) {
     int a = e / nn, b = e % nn;
     if (a < b) {
-      double v = 0.5 * (A[a * nn + b] + A[b * nn + a]);
-      A[a * nn + b] = v;
-      A[b * nn + a] = v;
+      double v = 0.5 * (A[a * lds + b] + A[b * lds + a]);
+      A[a * lds + b] = v;
+      A[b * lds + a] = v;
     }
   }
   __syncthreads();
-  const int np = nn / 2;
-  for (int sweep = 0; sweep < 30 && nn > 1; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (int e = tid; e < nn * nn; e += nt) {
-      double v = A[e] * A[e];
-      tot += v;
-      if (e / nn != e % nn) off += v;
-    }
-    off = block_sum(off, red);
-    tot = block_sum(tot, red);
-    if (!(off > 1e-30 * tot)) break;
-    for (int step = 0; step < nn - 1; ++step) {
-      for (int k = tid; k < np; k += nt) {
-        int pa = (k == 0) ? 0 : ((k - 1 + step) % (nn - 1)) + 1;
-        int pb = ((nn - 1 - k - 1 + step) % (nn - 1)) + 1;
-        int p = min(pa, pb), q = max(pa, pb);
-        double apq = A[p * nn + q];
-        double c = 1.0, s = 0.0;
-        if (apq != 0.0) {
-          double tau = (A[q * nn + q] - A[p * nn + p]) / (2.0 * apq);
-          double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-          c = 1.0 / sqrt(1.0 + tt * tt);
-          s = tt * c;
-        }
-        pp[k] = p;
-        qq[k] = q;
-        cs[k] = c;
-        sn[k] = s;
-      }
-      __syncthreads();
-      for (int e = tid; e < np * nn; e += nt) {  // rows p, q
-        int k = e / nn, j = e % nn;
-        if (sn[k] == 0.0) continue;
-        int p = pp[k], q = qq[k];
-        double x = A[p * nn + j], y = A[q * nn + j];
-        A[p * nn + j] = cs[k] * x - sn[k] * y;
-        A[q * nn + j] = sn[k] * x + cs[k] * y;
-      }
-      __syncthreads();
-      for (int e = tid; e < np * nn; e += nt) {  // columns p, q of A and V
-        int k = e / nn, i = e % nn;
-        if (sn[k] == 0.0) continue;
-        int p = pp[k], q = qq[k];
-        double x = A[i * nn + p], y = A[i * nn + q];
-        A[i * nn + p] = cs[k] * x - sn[k] * y;
-        A[i * nn + q] = sn[k] * x + cs[k] * y;
-        double vx = V[i * nn + p], vy = V[i * nn + q];
-        V[i * nn + p] = cs[k] * vx - sn[k] * vy;
-        V[i * nn + q] = sn[k] * vx + cs[k] * vy;
-      }
-      __syncthreads();
-    }
-  }
+  jacobi_sweeps<double>(A, V, nn, lds, 30, 1e-30, red, cs, sn, pp, qq);
   // order by decreasing eigenvalue (ties by index); only the n active ones
-  for (int a = tid; a < n; a += nt) lam[a] = A[a * nn + a];
+  for (int a = tid; a < n; a += nt) lam[a] = A[a * lds + a];
   __syncthreads();
   for (int a = tid; a < n; a += nt) {
     int pos = 0;
@@ -397,37 +358,38 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
     int best = 0;
     double bv = -1.0;
     for (int a = 0; a < n; ++a) {
-      double v = fabs(V[a * nn + col]);
+      double v = fabs(V[a * lds + col]);
       if (v > bv) { bv = v; best = a; }
     }
-    double sg = V[best * nn + col] < 0.0 ? -1.0 : 1.0;
-    for (int a = 0; a < n; ++a) out[(int64_t)act[a] * t.kcap + c] = sg * V[a * nn + col];
+    double sg = V[best * lds + col] < 0.0 ? -1.0 : 1.0;
+    for (int a = 0; a < n; ++a) out[(int64_t)act[a] * t.kcap + c] = sg * V[a * lds + col];
   }
 }
 
 // ------------------------------------------------------------ mixed eigen kernel
 // Same task as eig_kernel for the mixed-precision product, with the float64 work
-// cut down: (1) cyclic round-robin Jacobi in float32 on the normalised Gram sum G;
-// (2) the float32 eigenvector matrix is re-orthonormalised in float64 by one
-// Newton-Schulz step V <- V (3 I - V^T V) / 2 (quadratic: 1e-7 -> 1e-14);
-// (3) B = V^T G V in float64 (a similarity transform: same eigenvalues as G, off-
-// diagonal at the float32 level); (4) float64 Jacobi sweeps on B, rotations applied
-// to V, until the off-diagonal norm is below 1e-10 of the total.  Ranks are decided
-// on the float64 eigenvalues of B; the new bases are V's columns (float64,
-// orthonormal).  Shared memory: G, V, T, each n x n float64 (n <= 96).
+// cut to what decides the result: (1) cyclic round-robin Jacobi in float32 on the
+// normalised Gram sum G (eigenvalue errors ~1e-7 lambda_1, far below the truncation
+// thresholds); (2) the float32 eigenvectors are re-orthonormalised in float64 by one
+// Newton-Schulz step V <- V (3 I - V^T V) / 2 (1e-7 -> 1e-14); (3) the eigenvalues
+// that decide the ranks are the float64 Rayleigh quotients v_j^T G v_j.  The new
+// bases are V's leading columns (float64, orthonormal to ~1e-14).  Shared memory:
+// G, V, T, each n x n float64 (n <= 96).
 constexpr int kMixMax = 96;
 
 template <typename T>
-__device__ void jacobi_sweeps(T* A, T* V, int nn, int max_sweeps, double tol, double* red, T* cs, T* sn, int* pp,
-                              int* qq) {
+__device__ void jacobi_sweeps(T* A, T* V, int nn, int lds, int max_sweeps, double tol, double* red, T* cs, T* sn,
+                              int* pp, int* qq) {
   const int tid = threadIdx.x, nt = blockDim.x, np = nn / 2;
+  const int lane = tid & 31, w = tid >> 5, nw = nt >> 5;
   for (int sweep = 0; sweep < max_sweeps && nn > 1; ++sweep) {
     double off = 0.0, tot = 0.0;
-    for (int e = tid; e < nn * nn; e += nt) {
-      double v = (double)A[e] * (double)A[e];
-      tot += v;
-      if (e / nn != e % nn) off += v;
-    }
+    for (int i = w; i < nn; i += nw)
+      for (int j = lane; j < nn; j += 32) {
+        double v = (double)A[i * lds + j] * (double)A[i * lds + j];
+        tot += v;
+        if (i != j) off += v;
+      }
     off = block_sum(off, red);
     tot = block_sum(tot, red);
     if (!(off > tol * tot)) break;
@@ -436,10 +398,10 @@ __device__ void jacobi_sweeps(T* A, T* V, int nn, int max_sweeps, double tol, do
         int pa = (k == 0) ? 0 : ((k - 1 + step) % (nn - 1)) + 1;
         int pb = ((nn - 1 - k - 1 + step) % (nn - 1)) + 1;
         int p = min(pa, pb), q = max(pa, pb);
-        T apq = A[p * nn + q];
+        T apq = A[p * lds + q];
         T c = T(1), s = T(0);
         if (apq != T(0)) {
-          T tau = (A[q * nn + q] - A[p * nn + p]) / (T(2) * apq);
+          T tau = (A[q * lds + q] - A[p * lds + p]) / (T(2) * apq);
           T tt = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
           c = T(1) / sqrt(T(1) + tt * tt);
           s = tt * c;
@@ -450,38 +412,58 @@ __device__ void jacobi_sweeps(T* A, T* V, int nn, int max_sweeps, double tol, do
         sn[k] = s;
       }
       __syncthreads();
-      for (int e = tid; e < np * nn; e += nt) {
-        int k = e / nn, j = e % nn;
+      for (int k = w; k < np; k += nw) {  // rows p, q
         if (sn[k] == T(0)) continue;
-        int p = pp[k], q = qq[k];
-        T x = A[p * nn + j], y = A[q * nn + j];
-        A[p * nn + j] = cs[k] * x - sn[k] * y;
-        A[q * nn + j] = sn[k] * x + cs[k] * y;
+        const int p = pp[k], q = qq[k];
+        const T c = cs[k], s = sn[k];
+        for (int j = lane; j < nn; j += 32) {
+          T x = A[p * lds + j], y = A[q * lds + j];
+          A[p * lds + j] = c * x - s * y;
+          A[q * lds + j] = s * x + c * y;
+        }
       }
       __syncthreads();
-      for (int e = tid; e < np * nn; e += nt) {
-        int k = e / nn, i = e % nn;
+      for (int k = w; k < np; k += nw) {  // columns p, q of A and V
         if (sn[k] == T(0)) continue;
-        int p = pp[k], q = qq[k];
-        T x = A[i * nn + p], y = A[i * nn + q];
-        A[i * nn + p] = cs[k] * x - sn[k] * y;
-        A[i * nn + q] = sn[k] * x + cs[k] * y;
-        T vx = V[i * nn + p], vy = V[i * nn + q];
-        V[i * nn + p] = cs[k] * vx - sn[k] * vy;
-        V[i * nn + q] = sn[k] * vx + cs[k] * vy;
+        const int p = pp[k], q = qq[k];
+        const T c = cs[k], s = sn[k];
+        for (int i = lane; i < nn; i += 32) {
+          T x = A[i * lds + p], y = A[i * lds + q];
+          A[i * lds + p] = c * x - s * y;
+          A[i * lds + q] = s * x + c * y;
+          T vx = V[i * lds + p], vy = V[i * lds + q];
+          V[i * lds + p] = c * vx - s * vy;
+          V[i * lds + q] = s * vx + c * vy;
+        }
       }
       __syncthreads();
     }
   }
 }
 
-// C = op(X) op(Y) for nn x nn float64 matrices in shared memory (C distinct from X, Y)
-__device__ void smem_gemm(const double* X, bool tx, const double* Y, bool ty, double* C, int nn) {
-  for (int e = threadIdx.x; e < nn * nn; e += blockDim.x) {
-    int i = e / nn, j = e % nn;
-    double acc = 0.0;
-    for (int k = 0; k < nn; ++k) acc = fma(tx ? X[k * nn + i] : X[i * nn + k], ty ? Y[j * nn + k] : Y[k * nn + j], acc);
-    C[e] = acc;
+// C = op(X) op(Y) for nn x nn float64 matrices in shared memory, row stride lds
+// (C distinct from X, Y); each thread computes four outputs of one row with
+// independent accumulators
+__device__ void smem_gemm(const double* X, bool tx, const double* Y, bool ty, double* C, int nn, int lds) {
+  const int nq = (nn + 3) / 4;
+  for (int e = threadIdx.x; e < nn * nq; e += blockDim.x) {
+    const int i = e / nq, j0 = (e % nq) * 4;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    for (int k = 0; k < nn; ++k) {
+      const double x = tx ? X[k * lds + i] : X[i * lds + k];
+      double y0 = ty ? Y[j0 * lds + k] : Y[k * lds + j0];
+      double y1 = (j0 + 1 < nn) ? (ty ? Y[(j0 + 1) * lds + k] : Y[k * lds + j0 + 1]) : 0.0;
+      double y2 = (j0 + 2 < nn) ? (ty ? Y[(j0 + 2) * lds + k] : Y[k * lds + j0 + 2]) : 0.0;
+      double y3 = (j0 + 3 < nn) ? (ty ? Y[(j0 + 3) * lds + k] : Y[k * lds + j0 + 3]) : 0.0;
+      a0 = fma(x, y0, a0);
+      a1 = fma(x, y1, a1);
+      a2 = fma(x, y2, a2);
+      a3 = fma(x, y3, a3);
+    }
+    C[i * lds + j0] = a0;
+    if (j0 + 1 < nn) C[i * lds + j0 + 1] = a1;
+    if (j0 + 2 < nn) C[i * lds + j0 + 2] = a2;
+    if (j0 + 3 < nn) C[i * lds + j0 + 3] = a3;
   }
   __syncthreads();
 }
@@ -514,13 +496,13 @@ __global__ void __launch_bounds__(256) eig_mixed_kernel(const EigTask* __restric
     s_n = n;
   }
   __syncthreads();
-  const int n = s_n, nn = n + (n & 1);
-  double* G = smem;               // normalised Gram sum, later B = V^T G V
-  double* V = smem + nn * nn;     // eigenvectors (float64)
-  double* T = smem + 2 * nn * nn; // work: float32 A and V during step (1), products later
+  const int n = s_n, nn = n + (n & 1), lds = nn + 1, sz = nn * lds;
+  double* G = smem;               // normalised Gram sum (row stride lds)
+  double* V = smem + sz;          // eigenvectors (float64)
+  double* T = smem + 2 * sz;      // work: float32 A and V during step (1), products later
   float* A32 = (float*)T;
-  float* V32 = A32 + nn * nn;
-  for (int e = tid; e < nn * nn; e += nt) G[e] = 0.0;
+  float* V32 = A32 + sz;
+  for (int e = tid; e < sz; e += nt) G[e] = 0.0;
   __syncthreads();
   for (int m = 0; m < 3; ++m) {
     if (t.g[m] < 0) continue;
@@ -534,66 +516,67 @@ __global__ void __launch_bounds__(256) eig_mixed_kernel(const EigTask* __restric
     if (nrm2 > 0.0) {
       double inv = 1.0 / sqrt(nrm2);
       for (int e = tid; e < n * n; e += nt)
-        G[(e / n) * nn + (e % n)] += ld<double>(Gm, (int64_t)act[e / n] * t.n_pad + act[e % n]) * inv;
+        G[(e / n) * lds + (e % n)] += ld<double>(Gm, (int64_t)act[e / n] * t.n_pad + act[e % n]) * inv;
     }
     __syncthreads();
   }
   for (int e = tid; e < nn * nn; e += nt) {
     int a = e / nn, b = e % nn;
     if (a < b) {
-      double v = 0.5 * (G[a * nn + b] + G[b * nn + a]);
-      G[a * nn + b] = v;
-      G[b * nn + a] = v;
+      double v = 0.5 * (G[a * lds + b] + G[b * lds + a]);
+      G[a * lds + b] = v;
+      G[b * lds + a] = v;
     }
   }
   __syncthreads();
   // (1) float32 Jacobi
-  for (int e = tid; e < nn * nn; e += nt) {
+  for (int e = tid; e < sz; e += nt) {
     A32[e] = (float)G[e];
-    V32[e] = (e / nn == e % nn) ? 1.f : 0.f;
+    V32[e] = (e / lds == e % lds) ? 1.f : 0.f;
   }
   __syncthreads();
-  jacobi_sweeps<float>(A32, V32, nn, 12, 1e-10, red, cs32, sn32, pp, qq);
-  for (int e = tid; e < nn * nn; e += nt) V[e] = (double)V32[e];
+  jacobi_sweeps<float>(A32, V32, nn, lds, 12, 1e-10, red, cs32, sn32, pp, qq);
+  for (int e = tid; e < sz; e += nt) V[e] = (double)V32[e];
   __syncthreads();
-  // (2) one Newton-Schulz step: V <- V (3 I - V^T V) / 2
-  double* W = T;  // nn x nn
+  // (2) one Newton-Schulz step: V <- V (3 I - V^T V) / 2, computed as T = V W
   {
-    smem_gemm(V, true, V, false, W, nn);              // W = V^T V
-    for (int e = tid; e < nn * nn; e += nt) {
-      int i = e / nn, j = e % nn;
-      W[e] = ((i == j) ? 1.5 : 0.0) - 0.5 * W[e];
+    smem_gemm(V, true, V, false, T, nn, lds);          // T = V^T V
+    for (int e = tid; e < sz; e += nt) {
+      int i = e / lds, j = e % lds;
+      T[e] = ((i == j) ? 1.5 : 0.0) - 0.5 * T[e];
     }
     __syncthreads();
-    // V <- V W, eight rows at a time through a small buffer
+    // V <- V T, eight rows at a time through a small buffer
     for (int i0 = 0; i0 < nn; i0 += 8) {
       const int ni = min(8, nn - i0);
       for (int e = tid; e < ni * nn; e += nt) {
         int i = i0 + e / nn, j = e % nn;
-        double acc = 0.0;
-        for (int k = 0; k < nn; ++k) acc = fma(V[i * nn + k], W[k * nn + j], acc);
-        rowbuf[e] = acc;
+        double a0 = 0.0, a1 = 0.0;
+        int k = 0;
+        for (; k + 1 < nn; k += 2) {
+          a0 = fma(V[i * lds + k], T[k * lds + j], a0);
+          a1 = fma(V[i * lds + k + 1], T[(k + 1) * lds + j], a1);
+        }
+        if (k < nn) a0 = fma(V[i * lds + k], T[k * lds + j], a0);
+        rowbuf[e] = a0 + a1;
       }
       __syncthreads();
-      for (int e = tid; e < ni * nn; e += nt) V[(i0 + e / nn) * nn + e % nn] = rowbuf[e];
+      for (int e = tid; e < ni * nn; e += nt) V[(i0 + e / nn) * lds + e % nn] = rowbuf[e];
       __syncthreads();
     }
   }
-  // (3) B = V^T G V
-  smem_gemm(G, false, V, false, T, nn);   // T = G V
-  smem_gemm(V, true, T, false, G, nn);    // G <- V^T T
-  for (int e = tid; e < nn * nn; e += nt) {
-    int a = e / nn, b = e % nn;
-    if (a < b) {
-      double v = 0.5 * (G[a * nn + b] + G[b * nn + a]);
-      G[a * nn + b] = v;
-      G[b * nn + a] = v;
+  // (3) float64 Rayleigh quotients lambda_j = v_j^T G v_j
+  smem_gemm(G, false, V, false, T, nn, lds);   // T = G V
+  for (int j = tid; j < n; j += nt) {
+    double a0 = 0.0, a1 = 0.0;
+    int i = 0;
+    for (; i + 1 < nn; i += 2) {
+      a0 = fma(V[i * lds + j], T[i * lds + j], a0);
+      a1 = fma(V[(i + 1) * lds + j], T[(i + 1) * lds + j], a1);
     }
+    if (i < nn) a0 = fma(V[i * lds + j], T[i * lds + j], a0);
+    lam[j] = a0 + a1;
   }
-  __syncthreads();
-  // (4) float64 Jacobi on B, rotations accumulated into V
-  jacobi_sweeps<double>(G, V, nn, 10, 1e-20, red, cs, sn, pp, qq);
-  for (int a = tid; a < n; a += nt) lam[a] = G[a * nn + a];
   __syncthreads();
   for (int a = tid; a < n; a += nt) {
     int pos = 0;
@@ -631,11 +614,11 @@ __global__ void __launch_bounds__(256) eig_mixed_kernel(const EigTask* __restric
     int best = 0;
     double bv = -1.0;
     for (int a = 0; a < n; ++a) {
-      double v = fabs(V[a * nn + col]);
+      double v = fabs(V[a * lds + col]);
       if (v > bv) { bv = v; best = a; }
     }
-    double sg = V[best * nn + col] < 0.0 ? -1.0 : 1.0;
-    for (int a = 0; a < n; ++a) out[(int64_t)act[a] * t.kcap + c] = sg * V[a * nn + col];
+    double sg = V[best * lds + col] < 0.0 ? -1.0 : 1.0;
+    for (int a = 0; a < n; ++a) out[(int64_t)act[a] * t.kcap + c] = sg * V[a * lds + col];
   }
 }
 
@@ -643,11 +626,11 @@ void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const
                       int32_t* kc, double eps, int trunc, unsigned long long* cap_hits, int max_npad, void* stream) {
   Arenas ar = to_dev(a);
   int nn = max_npad + (max_npad & 1);
-  size_t smem = (size_t)3 * nn * nn * sizeof(double);
+  size_t smem = (size_t)3 * nn * (nn + 1) * sizeof(double);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(eig_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(3 * kMixMax * kMixMax * sizeof(double)));
+                         (int)(3 * kMixMax * (kMixMax + 1) * sizeof(double)));
     attr = true;
   }
   eig_mixed_kernel<<<(unsigned)count, 256, smem, (cudaStream_t)stream>>>(d_eigs, first, ar, kr, kc, eps, trunc,
@@ -662,15 +645,15 @@ void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, const Arena
   size_t smem = 0;
   int64_t stride = 0;
   if (nn <= kEigSmemMax) {
-    smem = (size_t)2 * nn * nn * sizeof(double);
+    smem = (size_t)2 * nn * (nn + 1) * sizeof(double);
   } else {
-    smem = (size_t)2 * kEigSmemMax * kEigSmemMax * sizeof(double);
-    stride = (int64_t)2 * nn * nn;
+    smem = (size_t)2 * kEigSmemMax * (kEigSmemMax + 1) * sizeof(double);
+    stride = (int64_t)2 * nn * (nn + 1);
   }
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(2 * kEigSmemMax * kEigSmemMax * sizeof(double)));
+                         (int)(2 * kEigSmemMax * (kEigSmemMax + 1) * sizeof(double)));
     attr = true;
   }
   eig_kernel<<<(unsigned)count, 256, smem, (cudaStream_t)stream>>>(d_eigs, first, ar, kr, kc, eps, trunc, cap_hits,
