@@ -567,7 +567,8 @@ h2_status h2_mmp(h2_handle A, h2_handle B, double eps, const h2_opts* opts, h2_h
         probe.Kc = Ccaps.Kc;
         int64_t csize = mat_elems(probe);
         int64_t sizes[kArenas] = {A->m.arena_elems, B->m.arena_elems, csize, e->plan.region[AR_P],
-                                  e->plan.region[AR_G0], e->plan.region[AR_G1], e->plan.region[AR_S], 0};
+                                  e->plan.region[AR_G0], e->plan.region[AR_G1], e->plan.region[AR_S],
+                                  o.precision == H2_MIXED_FP32 ? probe.off_S[0] : 0};
         validate_plan(e->plan, sizes);
       }
       upload_plan(e->plan, o.precision == H2_MIXED_FP32 ? sizeof(float) : sizeof(double));
@@ -614,7 +615,10 @@ h2_status h2_mmp(h2_handle A, h2_handle B, double eps, const h2_opts* opts, h2_h
       }
       ar.p[AR_A] = A->m.arena32;
       ar.p[AR_B] = B->m.arena32;
-      ar.f32 = (1u << AR_A) | (1u << AR_B) | (1u << AR_P) | (1u << AR_G0) | (1u << AR_G1) | (1u << AR_S);
+      if (!out->m.arena32) out->m.arena32 = (float*)dmalloc(std::max<int64_t>(1, out->m.off_S[0]) * sizeof(float));
+      ar.p[AR_X] = out->m.arena32;  // float copy of C's bases, written by the eigen step
+      ar.f32 = (1u << AR_A) | (1u << AR_B) | (1u << AR_P) | (1u << AR_G0) | (1u << AR_G1) | (1u << AR_S) |
+               (1u << AR_X);
     } else {
       ar.p[AR_A] = A->m.arena;
       ar.p[AR_B] = B->m.arena;

@@ -59,12 +59,14 @@ __device__ __forceinline__ int bound(const Arenas& a, int32_t ref, int padded) {
 // block rows 4 ty.., cols 4 tx.. and reads it from shared memory with vector
 // loads.  The items of a segment are packed along k into shared-memory slices of
 // depth GK (several short items share a slice, a long one spans several), loading
-// only the actual extents: rows < M, cols < N, k < the item's rank.  A warp whose
-// rows all lie beyond M skips the arithmetic; rows/cols beyond M/N hold stale
-// values whose products are never stored.
+// only the actual extents: rows < M, cols < N, k < the item's rank.  Slices are
+// double-buffered: cp.async fills slice s+1 while slice s is multiplied.  All
+// operands of a product have the element type T (the output may be float64); a
+// warp whose rows all lie beyond M skips the arithmetic; rows/cols beyond M/N hold
+// stale values whose products are never stored.
 constexpr int GK = 32, TILE = 32, GPAD = TILE + 4, GNT = 64;
 
-template <typename Acc>
+template <typename T>
 struct Vec4;
 template <>
 struct Vec4<float> {
@@ -82,11 +84,27 @@ struct Vec4<double> {
   }
 };
 
-template <typename Acc>
-__global__ void __launch_bounds__(GNT) seg_gemm_kernel(const Seg* __restrict__ segs, const Item* __restrict__ items,
+template <typename T>
+__device__ __forceinline__ void cp_async(T* dst, const T* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
+template <typename T>
+__device__ __forceinline__ const T* ptr_of(const Arenas& a, int64_t t) {
+  return (const T*)a.p[arena_idx(t)] + (t & kOffMask);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(GNT, 12) seg_gemm_kernel(const Seg* __restrict__ segs, const Item* __restrict__ items,
                                                        int64_t first, Arenas ar) {
-  __shared__ __align__(16) Acc sA[GK * GPAD];
-  __shared__ __align__(16) Acc sB[GK * GPAD];
+  __shared__ __align__(16) T sA[2][GK * GPAD];
+  __shared__ __align__(16) T sB[2][GK * GPAD];
   const Seg s = segs[first + blockIdx.x];
   const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
   const bool ta = s.flags & SF_TA, tb = s.flags & SF_TB, accum = s.flags & SF_ACC;
@@ -99,57 +117,58 @@ __global__ void __launch_bounds__(GNT) seg_gemm_kernel(const Seg* __restrict__ s
     for (int m0 = 0; m0 < M; m0 += TILE) {
       const int mc = min(TILE, M - m0);
       const bool live = (tid >> 5) * 16 < mc;  // this warp owns rows 16 w .. 16 w + 15
-      Acc acc[4][4];
+      T acc[4][4];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = Acc(0);
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
       if (s.flags & SF_SUM) {
         for (int q = 0; q < s.count; ++q) {
-          const View A = view(ar, it[q].a);
+          const T* A = ptr_of<T>(ar, it[q].a);
 #pragma unroll
           for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
               int r = 4 * ty + i, c = 4 * tx + j;
-              if (r < mc && c < nc) acc[i][j] += ld<Acc>(A, (int64_t)(m0 + r) * s.lda + n0 + c);
+              if (r < mc && c < nc) acc[i][j] += A[(int64_t)(m0 + r) * s.lda + n0 + c];
             }
         }
       } else {
         int q = 0, koff = 0, K = s.count ? bound(ar, it[0].kref, s.k) : 0;
-        while (q < s.count) {
+        // issue the copies of the next slice into buffer `buf`; returns its depth
+        auto fill = [&](int buf) -> int {
           int kfill = 0;
+          T* a_s = sA[buf];
+          T* b_s = sB[buf];
           while (q < s.count && kfill < GK) {
-            if (K == 0) {  // empty item
+            if (K == 0) {
               ++q;
               if (q < s.count) K = bound(ar, it[q].kref, s.k);
               continue;
             }
             const int take = min(K - koff, GK - kfill);
-            const View A = view(ar, it[q].a), B = view(ar, it[q].b);
-            // op(A)[m0 + r][koff + kk] -> sA[kfill + kk][r]; the fast thread index runs
-            // along the contiguous dimension of the stored matrix
+            const T* A = ptr_of<T>(ar, it[q].a);
+            const T* B = ptr_of<T>(ar, it[q].b);
             if (ta) {
               for (int kk = tid / TILE; kk < take; kk += GNT / TILE) {
                 const int r = tid % TILE;
-                if (r < mc) sA[(kfill + kk) * GPAD + r] = ld<Acc>(A, (int64_t)(koff + kk) * s.lda + (m0 + r));
+                if (r < mc) cp_async(&a_s[(kfill + kk) * GPAD + r], A + (int64_t)(koff + kk) * s.lda + (m0 + r));
               }
             } else {
               for (int r = tid / GK; r < mc; r += GNT / GK) {
                 const int kk = tid % GK;
-                if (kk < take) sA[(kfill + kk) * GPAD + r] = ld<Acc>(A, (int64_t)(m0 + r) * s.lda + (koff + kk));
+                if (kk < take) cp_async(&a_s[(kfill + kk) * GPAD + r], A + (int64_t)(m0 + r) * s.lda + (koff + kk));
               }
             }
-            // op(B)[koff + kk][n0 + c] -> sB[kfill + kk][c]
             if (tb) {
               for (int c = tid / GK; c < nc; c += GNT / GK) {
                 const int kk = tid % GK;
-                if (kk < take) sB[(kfill + kk) * GPAD + c] = ld<Acc>(B, (int64_t)(n0 + c) * s.ldb + (koff + kk));
+                if (kk < take) cp_async(&b_s[(kfill + kk) * GPAD + c], B + (int64_t)(n0 + c) * s.ldb + (koff + kk));
               }
             } else {
               for (int kk = tid / TILE; kk < take; kk += GNT / TILE) {
                 const int c = tid % TILE;
-                if (c < nc) sB[(kfill + kk) * GPAD + c] = ld<Acc>(B, (int64_t)(koff + kk) * s.ldb + (n0 + c));
+                if (c < nc) cp_async(&b_s[(kfill + kk) * GPAD + c], B + (int64_t)(koff + kk) * s.ldb + (n0 + c));
               }
             }
             kfill += take;
@@ -161,12 +180,23 @@ __global__ void __launch_bounds__(GNT) seg_gemm_kernel(const Seg* __restrict__ s
               if (q < s.count) K = bound(ar, it[q].kref, s.k);
             }
           }
+          return kfill;
+        };
+        int buf = 0;
+        int kf = fill(0);
+        cp_commit();
+        while (kf > 0) {
+          const int kf_next = fill(buf ^ 1);
+          cp_commit();
+          cp_wait1();
           __syncthreads();
           if (live) {
-            for (int kk = 0; kk < kfill; ++kk) {
-              Acc a[4], b[4];
-              Vec4<Acc>::load(&sA[kk * GPAD + 4 * ty], a);
-              Vec4<Acc>::load(&sB[kk * GPAD + 4 * tx], b);
+            const T* a_s = sA[buf];
+            const T* b_s = sB[buf];
+            for (int kk = 0; kk < kf; ++kk) {
+              T a[4], b[4];
+              Vec4<T>::load(&a_s[kk * GPAD + 4 * ty], a);
+              Vec4<T>::load(&b_s[kk * GPAD + 4 * tx], b);
 #pragma unroll
               for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -174,6 +204,8 @@ __global__ void __launch_bounds__(GNT) seg_gemm_kernel(const Seg* __restrict__ s
             }
           }
           __syncthreads();
+          buf ^= 1;
+          kf = kf_next;
         }
       }
 #pragma unroll
@@ -181,7 +213,7 @@ __global__ void __launch_bounds__(GNT) seg_gemm_kernel(const Seg* __restrict__ s
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           int r = 4 * ty + i, c = 4 * tx + j;
-          if (r < mc && c < nc) st<Acc>(out, (int64_t)(m0 + r) * s.ldc + n0 + c, acc[i][j], accum);
+          if (r < mc && c < nc) st<T>(out, (int64_t)(m0 + r) * s.ldc + n0 + c, acc[i][j], accum);
         }
     }
   }
@@ -350,7 +382,12 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
   __syncthreads();
   const int rank = s_rank;
   double* out = (double*)view(ar, t.out).base;  // the new bases are float64 (arena C)
-  for (int e = tid; e < t.n_pad * t.kcap; e += nt) out[e] = 0.0;
+  // float copy for the GEMMs of the mixed product (arena X mirrors C's basis region)
+  float* out32 = ar.p[AR_X] ? (float*)ar.p[AR_X] + (t.out & kOffMask) : nullptr;
+  for (int e = tid; e < t.n_pad * t.kcap; e += nt) {
+    out[e] = 0.0;
+    if (out32) out32[e] = 0.f;
+  }
   __syncthreads();
   // sign: the entry of largest magnitude (first such) is positive
   for (int c = tid; c < rank; c += nt) {
@@ -362,7 +399,11 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
       if (v > bv) { bv = v; best = a; }
     }
     double sg = V[best * lds + col] < 0.0 ? -1.0 : 1.0;
-    for (int a = 0; a < n; ++a) out[(int64_t)act[a] * t.kcap + c] = sg * V[a * lds + col];
+    for (int a = 0; a < n; ++a) {
+      const double v = sg * V[a * lds + col];
+      out[(int64_t)act[a] * t.kcap + c] = v;
+      if (out32) out32[(int64_t)act[a] * t.kcap + c] = (float)v;
+    }
   }
 }
 
@@ -606,8 +647,13 @@ __global__ void __launch_bounds__(256) eig_mixed_kernel(const EigTask* __restric
   }
   __syncthreads();
   const int rank = s_rank;
-  double* out = (double*)view(ar, t.out).base;
-  for (int e = tid; e < t.n_pad * t.kcap; e += nt) out[e] = 0.0;
+  double* out = (double*)view(ar, t.out).base;  // the new bases are float64 (arena C)
+  // float copy for the GEMMs of the mixed product (arena X mirrors C's basis region)
+  float* out32 = ar.p[AR_X] ? (float*)ar.p[AR_X] + (t.out & kOffMask) : nullptr;
+  for (int e = tid; e < t.n_pad * t.kcap; e += nt) {
+    out[e] = 0.0;
+    if (out32) out32[e] = 0.f;
+  }
   __syncthreads();
   for (int c = tid; c < rank; c += nt) {
     int col = order[c];
@@ -618,7 +664,11 @@ __global__ void __launch_bounds__(256) eig_mixed_kernel(const EigTask* __restric
       if (v > bv) { bv = v; best = a; }
     }
     double sg = V[best * lds + col] < 0.0 ? -1.0 : 1.0;
-    for (int a = 0; a < n; ++a) out[(int64_t)act[a] * t.kcap + c] = sg * V[a * lds + col];
+    for (int a = 0; a < n; ++a) {
+      const double v = sg * V[a * lds + col];
+      out[(int64_t)act[a] * t.kcap + c] = v;
+      if (out32) out32[(int64_t)act[a] * t.kcap + c] = (float)v;
+    }
   }
 }
 

@@ -213,6 +213,10 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
   auto tA = [&](int64_t o) { return tag(AR_A, o); };
   auto tB = [&](int64_t o) { return tag(AR_B, o); };
   auto tC = [&](int64_t o) { return tag(AR_C, o); };
+  // reads of C's new bases: in the mixed product the eigen step also writes a float
+  // copy of them (arena X), so that every GEMM operand has the product's type
+  const Arena basis_src = prm.precision == H2_MIXED_FP32 ? AR_X : AR_C;
+  auto tCb = [&](int64_t o) { return tag(basis_src, o); };
   auto G = [](int l) { return (l & 1) ? AR_G1 : AR_G0; };
   // rank references of cluster t of level l (loop bounds read on the device)
   auto AR = [](int l, int64_t t) { return rref(RK_AR, Structure::node(l, t)); };
@@ -594,23 +598,23 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
     pb.begin();
     for (int64_t t = 0; t < nc; ++t) {
       if (leaf) {
-        pb.gemm1(PA[l][t], rC(l), rA(l), LS, rC(l), rA(l), rA(l), SF_TA, tC(C.Vr(t)), tA(A.Vr(t)), CR(l, t), AR(l, t));
-        pb.gemm1(PB[l][t], cB(l), cC(l), LS, cB(l), cC(l), cC(l), SF_TA, tB(B.Vc(t)), tC(C.Vc(t)), BC(l, t), CC(l, t));
+        pb.gemm1(PA[l][t], rC(l), rA(l), LS, rC(l), rA(l), rA(l), SF_TA, tCb(C.Vr(t)), tA(A.Vr(t)), CR(l, t), AR(l, t));
+        pb.gemm1(PB[l][t], cB(l), cC(l), LS, cB(l), cC(l), cC(l), SF_TA, tB(B.Vc(t)), tCb(C.Vc(t)), BC(l, t), CC(l, t));
       } else {
-        pb.gemm1(PA[l][t], rC(l), rA(l), gr, rC(l), rA(l), rA(l), SF_TA, tC(C.Er(l, t)), Wr[t], CR(l, t), AR(l, t));
-        pb.gemm1(PB[l][t], cB(l), cC(l), gc, cB(l), cC(l), cC(l), SF_TA, Wc[t], tC(C.Ec(l, t)), BC(l, t), CC(l, t));
+        pb.gemm1(PA[l][t], rC(l), rA(l), gr, rC(l), rA(l), rA(l), SF_TA, tCb(C.Er(l, t)), Wr[t], CR(l, t), AR(l, t));
+        pb.gemm1(PB[l][t], cB(l), cC(l), gc, cB(l), cC(l), cC(l), SF_TA, Wc[t], tCb(C.Ec(l, t)), BC(l, t), CC(l, t));
       }
     }
     for (int64_t p = 0; p < nb; ++p) {
       const Block& b = bl[p];
       if (leaf && b.kind == KF) {
-        pb.gemm1(Ahat[l][p], rC(l), rB(l), LS, rC(l), rB(l), rB(l), SF_TA, tC(C.Vr(b.t)), Y[p], CR(l, b.t), BR(l, b.s));
-        pb.gemm1(Bhat[l][p], cA(l), cC(l), LS, LS, cC(l), cC(l), 0, Yb[p], tC(C.Vc(b.s)), AC(l, b.t), CC(l, b.s));
-        pb.gemm1(Ach[p], rC(l), LS, LS, rC(l), LS, LS, SF_TA, tC(C.Vr(b.t)), tA(A.F(b.idx)), CR(l, b.t));
-        pb.gemm1(Bch[p], LS, cC(l), LS, LS, cC(l), cC(l), 0, tB(B.F(b.idx)), tC(C.Vc(b.s)), -1, CC(l, b.s));
+        pb.gemm1(Ahat[l][p], rC(l), rB(l), LS, rC(l), rB(l), rB(l), SF_TA, tCb(C.Vr(b.t)), Y[p], CR(l, b.t), BR(l, b.s));
+        pb.gemm1(Bhat[l][p], cA(l), cC(l), LS, LS, cC(l), cC(l), 0, Yb[p], tCb(C.Vc(b.s)), AC(l, b.t), CC(l, b.s));
+        pb.gemm1(Ach[p], rC(l), LS, LS, rC(l), LS, LS, SF_TA, tCb(C.Vr(b.t)), tA(A.F(b.idx)), CR(l, b.t));
+        pb.gemm1(Bch[p], LS, cC(l), LS, LS, cC(l), cC(l), 0, tB(B.F(b.idx)), tCb(C.Vc(b.s)), -1, CC(l, b.s));
       } else if (!leaf && b.kind == KNL) {
-        pb.gemm1(Ahat[l][p], rC(l), rB(l), gr, rC(l), rB(l), rB(l), SF_TA, tC(C.Er(l, b.t)), Y[p], CR(l, b.t), BR(l, b.s));
-        pb.gemm1(Bhat[l][p], cA(l), cC(l), gc, gc, cC(l), cC(l), 0, Yb[p], tC(C.Ec(l, b.s)), AC(l, b.t), CC(l, b.s));
+        pb.gemm1(Ahat[l][p], rC(l), rB(l), gr, rC(l), rB(l), rB(l), SF_TA, tCb(C.Er(l, b.t)), Y[p], CR(l, b.t), BR(l, b.s));
+        pb.gemm1(Bhat[l][p], cA(l), cC(l), gc, gc, cC(l), cC(l), 0, Yb[p], tCb(C.Ec(l, b.s)), AC(l, b.t), CC(l, b.s));
       }
     }
     if (!leaf) {
@@ -623,7 +627,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
           std::vector<Item> it;
           for (int b = 0; b < 2; ++b) {
             auto f = LT[c].id.find(Structure::key(2 * T.i + a, 2 * T.k + b));
-            it.push_back({LT[c].tg[f->second].ssum, tC(C.Ec(l, T.k) + (int64_t)b * hc * cC(l)), CC(c, 2 * T.k + b)});
+            it.push_back({LT[c].tg[f->second].ssum, tCb(C.Ec(l, T.k) + (int64_t)b * hc * cC(l)), CC(c, 2 * T.k + b)});
           }
           pb.gemm(Mt[q] + (int64_t)a * hr * cC(l), hr, cC(l), hc, hc, cC(l), cC(l), 0, it, CR(c, 2 * T.i + a),
                   CC(l, T.k));
@@ -664,7 +668,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       if (T.cls == TC_F) continue;
       if (leaf) pb.gemm(T.ssum, rC(l), cC(l), LS, LS, cC(l), cC(l), SF_ACC, T.g1, CR(l, T.i), CC(l, T.k));  // case-1
       else if (Mt[q] >= 0)
-        pb.gemm1(T.ssum, rC(l), cC(l), gr, rC(l), cC(l), cC(l), SF_TA | SF_ACC, tC(C.Er(l, T.i)), Mt[q], CR(l, T.i),
+        pb.gemm1(T.ssum, rC(l), cC(l), gr, rC(l), cC(l), cC(l), SF_TA | SF_ACC, tCb(C.Er(l, T.i)), Mt[q], CR(l, T.i),
                  CC(l, T.k));
     }
     pb.end("coup", l);
@@ -720,13 +724,13 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
     pb.begin();
     for (size_t p = 0; p < bl.size(); ++p)
       if (Xt[p] >= 0)
-        pb.gemm1(Xt[p], rC(l), 2 * hc, cC(l), cC(l), cC(l), 2 * hc, SF_TB, H[l][p], tC(C.Ec(l, bl[p].s)),
+        pb.gemm1(Xt[p], rC(l), 2 * hc, cC(l), cC(l), cC(l), 2 * hc, SF_TB, H[l][p], tCb(C.Ec(l, bl[p].s)),
                  CR(l, bl[p].t), -1, CC(l, bl[p].s));
     pb.end("split", l);
     pb.begin();
     for (size_t p = 0; p < bl.size(); ++p)
       if (X[p] >= 0)
-        pb.gemm1(X[p], 2 * hr, 2 * hc, rC(l), rC(l), 2 * hc, 2 * hc, 0, tC(C.Er(l, bl[p].t)), Xt[p], -1, -1,
+        pb.gemm1(X[p], 2 * hr, 2 * hc, rC(l), rC(l), 2 * hc, 2 * hc, 0, tCb(C.Er(l, bl[p].t)), Xt[p], -1, -1,
                  CR(l, bl[p].t));
     pb.end("split", l);
     std::vector<std::pair<int64_t, int64_t>> Fupd;
@@ -745,7 +749,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
             pb.sum(H[c][cp], hr, hc, 2 * hc, cC(c), true, {xab});
           } else {
             int64_t tmp = pb.alloc(AR_S, (int64_t)rC(c) * LS);
-            pb.gemm1(tmp, rC(c), LS, cC(c), 2 * hc, cC(c), LS, SF_TB, xab, tC(C.Vc(cb.s)), CR(c, cb.t), -1,
+            pb.gemm1(tmp, rC(c), LS, cC(c), 2 * hc, cC(c), LS, SF_TB, xab, tCb(C.Vc(cb.s)), CR(c, cb.t), -1,
                      CC(c, cb.s));
             Fupd.push_back({tmp, tC(C.F(cb.idx))});
             Frow.push_back(cb.t);
@@ -755,7 +759,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
     pb.end("split", l);
     pb.begin();
     for (size_t q = 0; q < Fupd.size(); ++q)
-      pb.gemm1(Fupd[q].second, LS, LS, rC(c), rC(c), LS, LS, SF_ACC, tC(C.Vr(Frow[q])), Fupd[q].first, -1, -1,
+      pb.gemm1(Fupd[q].second, LS, LS, rC(c), rC(c), LS, LS, SF_ACC, tCb(C.Vr(Frow[q])), Fupd[q].first, -1, -1,
                CR(c, Frow[q]));
     pb.end("split", c);
     pb.close_memset(zS, AR_S);
