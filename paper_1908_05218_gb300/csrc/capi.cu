@@ -6,20 +6,31 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 
 #include "internal.hpp"
 
+// Product plans are cached process-wide by (structure, caps of A and B, options):
+// handles on equal points share one structure and, with equal caps, one plan and
+// its work regions.  Products that share a plan must run in stream order.
+struct PlanKey {
+  const h2::Structure* st;
+  std::vector<int> akr, akc, bkr, bkc;
+  int trunc, cap, precision;
+  bool operator==(const PlanKey& o) const {
+    return st == o.st && akr == o.akr && akc == o.akc && bkr == o.bkr && bkc == o.bkc && trunc == o.trunc &&
+           cap == o.cap && precision == o.precision;
+  }
+};
+struct PlanEntry {
+  h2::Plan plan;
+  ~PlanEntry() { h2::free_plan(plan); }
+};
+
 struct h2_matrix {
   h2::Mat m;
-  // product plans keyed by (B handle, B caps, trunc, cap); owned by A's handle
-  struct MmpEntry {
-    const h2_matrix* B = nullptr;
-    std::vector<int> Bkr, Bkc;
-    int trunc = 0, cap = 0, precision = 0;
-    h2::Plan plan;
-  };
-  std::vector<std::unique_ptr<MmpEntry>> mmp_plans;
+  std::vector<std::shared_ptr<PlanEntry>> plans_held;  // plans of products made from this handle
   std::map<int64_t, std::unique_ptr<h2::Plan>> mv_plans;  // by nrhs
   std::map<int64_t, std::pair<int64_t, int64_t>> mv_offs;
   int64_t* d_user = nullptr;  // padded tree row -> user index (-1: padding)
@@ -29,12 +40,58 @@ struct h2_matrix {
   bool trace_on = false;     // on A: trace the products made from it
   h2::Trace trace;           // on C: events of the product that made it
   const h2::Plan* trace_plan = nullptr;
+  std::shared_ptr<PlanEntry> made_by;  // on C: the plan of the product that made it
   const h2_matrix* origin_A = nullptr;
   const h2_matrix* origin_B = nullptr;
 };
 
 namespace {
 thread_local std::string g_err;
+std::mutex g_cache_mu;
+std::vector<std::pair<PlanKey, std::weak_ptr<PlanEntry>>> g_plans;
+struct StructKey {
+  uint64_t hash;
+  int64_t n;
+  int leaf;
+  double eta;
+};
+std::vector<std::pair<StructKey, std::weak_ptr<h2::Structure>>> g_structs;
+
+uint64_t fnv1a(const void* p, size_t bytes) {
+  const unsigned char* b = (const unsigned char*)p;
+  uint64_t h = 1469598103934665603ull;
+  for (size_t i = 0; i < bytes; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  return h;
+}
+
+// the structure of (points, leaf, eta), shared with live handles on equal points
+std::shared_ptr<h2::Structure> structure_for(const double* pts, int64_t n, int leaf, double eta) {
+  if (!pts || n < 1) return h2::build_structure(pts, n, leaf, eta);
+  StructKey key{fnv1a(pts, (size_t)n * 3 * sizeof(double)), n, leaf, eta};
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  for (auto it = g_structs.begin(); it != g_structs.end();) {
+    auto sp = it->second.lock();
+    if (!sp) {
+      it = g_structs.erase(it);
+      continue;
+    }
+    const StructKey& k = it->first;
+    if (k.hash == key.hash && k.n == n && k.leaf == leaf && k.eta == eta) {
+      bool same = true;
+      for (int64_t p = 0; p < n && same; ++p)
+        for (int d = 0; d < 3; ++d)
+          if (sp->pts[3 * p + d] != pts[3 * sp->perm[p] + d]) {
+            same = false;
+            break;
+          }
+      if (same) return sp;
+    }
+    ++it;
+  }
+  auto st = h2::build_structure(pts, n, leaf, eta);
+  g_structs.push_back({key, st});
+  return st;
+}
 
 h2_status fail(h2_status c, const std::string& m) {
   g_err = m;
@@ -457,7 +514,7 @@ h2_status h2_build(const double* points, int64_t n, const h2_kernel* kernel, int
     if (kernel->kind == H2_K_HELMHOLTZ) throw Error(H2_EUNSUPPORTED, "complex kernels are not supported on the GPU path");
     if (kernel->kind != H2_K_LAPLACE && kernel->kind != H2_K_INV_R2) throw Error(H2_EINVAL, "unknown kernel kind");
     auto h = std::make_unique<h2_matrix>();
-    h->m.st = build_structure(points, n, leaf_size, eta);
+    h->m.st = structure_for(points, n, leaf_size, eta);
     Packed p;
     build_h2_host(*h->m.st, *kernel, eps, p);
     unpack_to_device(p, h->m);
@@ -474,7 +531,7 @@ h2_status h2_import(const double* points, int64_t n, int32_t leaf_size, double e
   return guarded([&] {
     h2_opts o = defaults(opts);
     auto h = std::make_unique<h2_matrix>();
-    h->m.st = build_structure(points, n, leaf_size, eta);
+    h->m.st = structure_for(points, n, leaf_size, eta);
     const Structure& st = *h->m.st;
     const int nn = st.nnodes(), L = st.L;
     Packed p;
@@ -541,44 +598,49 @@ h2_status h2_mmp(h2_handle A, h2_handle B, double eps, const h2_opts* opts, h2_h
     if (o.trunc != H2_TRUNC_FULL && !(eps > 0 && eps < 1)) throw Error(H2_EINVAL, "eps must lie in (0, 1)");
     if (!same_structure(*A->m.st, *B->m.st)) throw Error(H2_ESTRUCT, "A and B have different trees or partitions");
     MmpParams prm{eps, o.trunc, o.rank_cap, o.precision};
-    // plan cache on A
-    h2_matrix::MmpEntry* ent = nullptr;
-    for (auto& e : A->mmp_plans)
-      if (e->B == B && e->Bkr == B->m.Kr && e->Bkc == B->m.Kc && e->trunc == o.trunc && e->cap == o.rank_cap &&
-          e->precision == o.precision)
-        ent = e.get();
-    Mat Ccaps;
-    Ccaps.st = A->m.st;
+    // plan cache, process-wide
+    PlanKey key{A->m.st.get(), A->m.Kr, A->m.Kc, B->m.Kr, B->m.Kc, o.trunc, o.rank_cap, o.precision};
+    std::shared_ptr<PlanEntry> ent;
+    {
+      std::lock_guard<std::mutex> lk(g_cache_mu);
+      for (auto it = g_plans.begin(); it != g_plans.end();) {
+        auto sp = it->second.lock();
+        if (!sp) {
+          it = g_plans.erase(it);
+          continue;
+        }
+        if (it->first == key) ent = sp;
+        ++it;
+      }
+    }
     if (!ent) {
-      auto e = std::make_unique<h2_matrix::MmpEntry>();
-      e->B = B;
-      e->Bkr = B->m.Kr;
-      e->Bkc = B->m.Kc;
-      e->trunc = o.trunc;
-      e->cap = o.rank_cap;
-      e->precision = o.precision;
-      build_mmp_plan(A->m, B->m, Ccaps, prm, e->plan);
-      e->plan.ckr = Ccaps.Kr;
-      e->plan.ckc = Ccaps.Kc;
+      ent = std::make_shared<PlanEntry>();
+      Mat Ccaps;
+      Ccaps.st = A->m.st;
+      build_mmp_plan(A->m, B->m, Ccaps, prm, ent->plan);
+      ent->plan.ckr = Ccaps.Kr;
+      ent->plan.ckc = Ccaps.Kc;
       {
         Mat probe;
         probe.st = A->m.st;
         probe.Kr = Ccaps.Kr;
         probe.Kc = Ccaps.Kc;
         int64_t csize = mat_elems(probe);
-        int64_t sizes[kArenas] = {A->m.arena_elems, B->m.arena_elems, csize, e->plan.region[AR_P],
-                                  e->plan.region[AR_G0], e->plan.region[AR_G1], e->plan.region[AR_S],
+        int64_t sizes[kArenas] = {A->m.arena_elems, B->m.arena_elems, csize, ent->plan.region[AR_P],
+                                  ent->plan.region[AR_G0], ent->plan.region[AR_G1], ent->plan.region[AR_S],
                                   o.precision == H2_MIXED_FP32 ? probe.off_S[0] : 0};
-        validate_plan(e->plan, sizes);
+        validate_plan(ent->plan, sizes);
       }
-      upload_plan(e->plan, o.precision == H2_MIXED_FP32 ? sizeof(float) : sizeof(double));
-      ent = e.get();
-      A->mmp_plans.push_back(std::move(e));
+      upload_plan(ent->plan, o.precision == H2_MIXED_FP32 ? sizeof(float) : sizeof(double));
+      std::lock_guard<std::mutex> lk(g_cache_mu);
+      g_plans.push_back({key, ent});
     }
+    bool held = false;
+    for (auto& p : A->plans_held) held = held || p == ent;
+    if (!held) A->plans_held.push_back(ent);
     h2_matrix* out = *C;
-    bool reuse = out && out->origin_A == A && out->origin_B == B && out->origin_trunc == o.trunc &&
-                 out->origin_cap == o.rank_cap && out->origin_prec == o.precision && out->m.Kr == ent->plan.ckr &&
-                 out->m.Kc == ent->plan.ckc;
+    bool reuse = out && out->m.st == A->m.st && out->origin_trunc == o.trunc && out->origin_cap == o.rank_cap &&
+                 out->origin_prec == o.precision && out->m.Kr == ent->plan.ckr && out->m.Kc == ent->plan.ckc;
     std::unique_ptr<h2_matrix> fresh;
     if (!reuse) {
       fresh = std::make_unique<h2_matrix>();
@@ -631,6 +693,7 @@ h2_status h2_mmp(h2_handle A, h2_handle B, double eps, const h2_opts* opts, h2_h
     ar.rk[RK_BC] = B->m.d_kc;
     ar.rk[RK_CR] = out->m.d_kr;
     ar.rk[RK_CC] = out->m.d_kc;
+    out->made_by = ent;
     out->trace_plan = A->trace_on ? &ent->plan : nullptr;
     if (A->trace_on) {
       ar.flops = out->m.d_cap + 1;  // second counter of the handle's counter block
@@ -824,7 +887,8 @@ void h2_destroy(h2_handle h) {
   if (!h) return;
   for (void* e : h->trace.ev) cudaEventDestroy((cudaEvent_t)e);
   cudaDeviceSynchronize();
-  for (auto& e : h->mmp_plans) free_plan(e->plan);
+  h->plans_held.clear();
+  h->made_by.reset();
   for (auto& kv : h->mv_plans) free_plan(*kv.second);
   if (h->d_user) cudaFree(h->d_user);
   if (h->ev0) cudaEventDestroy(h->ev0);
