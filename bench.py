@@ -194,7 +194,7 @@ def main():
     import torch
 
     from paper_1908_05218_gb300 import h2 as lib
-    from paper_1908_05218_gb300 import inputs
+    from paper_1908_05218_gb300 import inputs, replicas
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
@@ -236,17 +236,14 @@ def main():
     if dist:
         dist.barrier()
     ms = ev0.elapsed_time(ev1) / max(1, args.steps)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replicas.slowest(ms, dist, device="cuda")
     kinds, levels, lms, lfl, lnames = C.trace_read()
     executed_flops = C.trace_flops()
     A.trace_enable(False)
 
     ia, ib, ic = A.info(), B.info(), C.info()
     nbytes = ia["bytes_stored"] + ib["bytes_stored"] + ic["bytes_stored"]
-    value = nbytes * world / (ms * 1e-3) / 1e9
+    value = replicas.throughput(nbytes, world, ms)
 
     # accuracy of this product: Eq. error with exact H^2 matvecs, 4 random vectors
     x = torch.from_numpy(inputs.standard_normal((wa.points.shape[0], 4), seed=1)).cuda()
@@ -262,8 +259,11 @@ def main():
         tt[2] += 1
     dom = max(tot, key=lambda k: tot[k][0])
     peaks, src = _peaks()
-    fp64_peak = 1.01  # TFLOP/s, DFMA probe on this machine's GB300 (profiles/fp64_fp32_throughput_probe.txt)
-    fp32_peak = 67.0
+    # ALU peaks from unit counts and the maximum SM clock: 152 SMs x 128 float32 FMA
+    # lanes (resp. 2 float64 FMA per clock) x 2 flops x clock
+    clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    fp32_peak = 152 * 128 * 2 * clk / 1e12
+    fp64_peak = 152 * 2 * 2 * clk / 1e12
     peak = fp64_peak if args.precision == "fp64" else fp32_peak
     gemm_ms = tot.get("gemm", [0.0])[0]
     gemm_tf = executed_flops / (gemm_ms * 1e-3) / 1e12 if gemm_ms else 0.0
@@ -272,7 +272,7 @@ def main():
             "launches_per_step": tot["gemm"][2], "ms_per_step": gemm_ms,
             "executed_flops_per_step": executed_flops,
             "note": ("GEMM kernel: multiply-add flops executed at the actual ranks (device counter) / its "
-                     "CUDA-event time; peak = this pool's measured DFMA (fp64) or FFMA (fp32) probe rate")}
+                     "CUDA-event time; peak = float32 (float64) FMA units x 2 x max SM clock")}
     phase_ms = {k: round(v[0], 3) for k, v in tot.items()}
     by_phase = {}
     for nm, m_ in zip(lnames, lms):
