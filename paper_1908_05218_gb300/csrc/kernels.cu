@@ -413,9 +413,10 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
 // normalised Gram sum G (eigenvalue errors ~1e-7 lambda_1, far below the truncation
 // thresholds); (2) the float32 eigenvectors are re-orthonormalised in float64 by one
 // Newton-Schulz step V <- V (3 I - V^T V) / 2 (1e-7 -> 1e-14); (3) the eigenvalues
-// that decide the ranks are the float64 Rayleigh quotients v_j^T G v_j.  The new
-// bases are V's leading columns (float64, orthonormal to ~1e-14).  Shared memory:
-// G, V, T, each n x n float64 (n <= 96).
+// that decide the ranks are the float64 Rayleigh quotients v_j^T G v_j, or, for
+// thresholds below 5e-5 lambda_1, the eigenvalues of V^T G V after float64 Jacobi
+// refinement.  The new bases are V's leading columns (float64, orthonormal to
+// ~1e-14).  Shared memory: G, V, T, each n x n float64 (n <= 96).
 constexpr int kMixMax = 96;
 
 template <typename T>
@@ -606,17 +607,36 @@ __global__ void __launch_bounds__(256) eig_mixed_kernel(const EigTask* __restric
       __syncthreads();
     }
   }
-  // (3) float64 Rayleigh quotients lambda_j = v_j^T G v_j
+  // (3) float64 Rayleigh quotients lambda_j = v_j^T G v_j decide the ranks.  When the
+  // truncation threshold is below what float32 eigenvectors resolve (< 5e-5 of
+  // lambda_1), the float64 Rayleigh-Ritz matrix B = V^T G V is diagonalised by float64
+  // Jacobi sweeps first (rotations accumulated into V).
+  const double thr_rel = trunc == H2_TRUNC_SV ? eps * eps : eps;
   smem_gemm(G, false, V, false, T, nn, lds);   // T = G V
-  for (int j = tid; j < n; j += nt) {
-    double a0 = 0.0, a1 = 0.0;
-    int i = 0;
-    for (; i + 1 < nn; i += 2) {
-      a0 = fma(V[i * lds + j], T[i * lds + j], a0);
-      a1 = fma(V[(i + 1) * lds + j], T[(i + 1) * lds + j], a1);
+  if (trunc != H2_TRUNC_FULL && thr_rel < 5e-5) {
+    smem_gemm(V, true, T, false, G, nn, lds);  // G <- V^T T = B
+    for (int e = tid; e < nn * nn; e += nt) {
+      int a = e / nn, b = e % nn;
+      if (a < b) {
+        double v = 0.5 * (G[a * lds + b] + G[b * lds + a]);
+        G[a * lds + b] = v;
+        G[b * lds + a] = v;
+      }
     }
-    if (i < nn) a0 = fma(V[i * lds + j], T[i * lds + j], a0);
-    lam[j] = a0 + a1;
+    __syncthreads();
+    jacobi_sweeps<double>(G, V, nn, lds, 8, 1e-24, red, cs, sn, pp, qq);
+    for (int j = tid; j < n; j += nt) lam[j] = G[j * lds + j];
+  } else {
+    for (int j = tid; j < n; j += nt) {
+      double a0 = 0.0, a1 = 0.0;
+      int i = 0;
+      for (; i + 1 < nn; i += 2) {
+        a0 = fma(V[i * lds + j], T[i * lds + j], a0);
+        a1 = fma(V[(i + 1) * lds + j], T[(i + 1) * lds + j], a1);
+      }
+      if (i < nn) a0 = fma(V[i * lds + j], T[i * lds + j], a0);
+      lam[j] = a0 + a1;
+    }
   }
   __syncthreads();
   for (int a = tid; a < n; a += nt) {
