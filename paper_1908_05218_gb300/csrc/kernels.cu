@@ -521,7 +521,7 @@ __global__ void __launch_bounds__(256) eig_mixed_kernel(const EigTask* __restric
   __shared__ int pp[kMixMax / 2 + 1], qq[kMixMax / 2 + 1];
   __shared__ int order[kMixMax + 2];
   __shared__ double lam[kMixMax + 2];
-  __shared__ double rowbuf[8 * kMixMax];
+  __shared__ double rowbuf[4 * kMixMax];
   __shared__ int s_n, s_rank;
   const EigTask t = tasks[first + blockIdx.x];
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -588,9 +588,9 @@ __global__ void __launch_bounds__(256) eig_mixed_kernel(const EigTask* __restric
       T[e] = ((i == j) ? 1.5 : 0.0) - 0.5 * T[e];
     }
     __syncthreads();
-    // V <- V T, eight rows at a time through a small buffer
-    for (int i0 = 0; i0 < nn; i0 += 8) {
-      const int ni = min(8, nn - i0);
+    // V <- V T, four rows at a time through a small buffer
+    for (int i0 = 0; i0 < nn; i0 += 4) {
+      const int ni = min(4, nn - i0);
       for (int e = tid; e < ni * nn; e += nt) {
         int i = i0 + e / nn, j = e % nn;
         double a0 = 0.0, a1 = 0.0;
