@@ -79,9 +79,9 @@ typedef enum {
 typedef struct {
   int32_t precision;   /* h2_precision, default H2_FP64                          */
   int32_t trunc;       /* h2_trunc, default H2_TRUNC_PAPER                       */
-  int32_t rank_cap;    /* largest rank of a non-leaf cluster of C; 0 = default 48;
-                          ranks above it are cut to the cap and counted in
-                          h2_stats.cap_hits                                       */
+  int32_t rank_cap;    /* largest rank of a non-leaf cluster of C, 1..128; 0 =
+                          default 48; ranks above it are cut to the cap and
+                          counted in h2_stats.cap_hits                            */
   int32_t reserved;
   void* stream;        /* cudaStream_t, NULL = legacy default stream            */
 } h2_opts;             /* a NULL h2_opts* means all defaults */

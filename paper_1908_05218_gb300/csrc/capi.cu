@@ -135,7 +135,7 @@ h2_opts defaults(const h2_opts* o) {
   }
   if (d.precision != H2_FP64 && d.precision != H2_MIXED_FP32) throw h2::Error(H2_EINVAL, "bad precision");
   if (d.trunc < 0 || d.trunc > 2) throw h2::Error(H2_EINVAL, "bad truncation mode");
-  if (d.rank_cap > 64) throw h2::Error(H2_EINVAL, "rank_cap above 64");
+  if (d.rank_cap > 128) throw h2::Error(H2_EINVAL, "rank_cap above 128");
   return d;
 }
 

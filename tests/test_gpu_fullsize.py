@@ -60,19 +60,18 @@ def test_config2_cube_array_65536_properties(lib):
     A = lib.h2_build(wa.points, wa.kernel, 32, 1.0, 1e-4)
     B = lib.h2_build(wb.points, wb.kernel, 32, 1.0, 1e-4)
     res = {}
-    for eps in (1e-4, 1e-6):
-        C64 = A.mmp(B, eps, precision=lib.FP64)
+    for eps, cap in ((1e-4, 48), (1e-6, 96)):
+        C64 = A.mmp(B, eps, precision=lib.FP64, rank_cap=cap)
         e64, x = eq_error(lib, A, B, C64, n)
         assert e64 < math.sqrt(eps), (eps, e64)
-        Cm = A.mmp(B, eps, precision=lib.MIXED_FP32)
+        Cm = A.mmp(B, eps, precision=lib.MIXED_FP32, rank_cap=cap)
         em, _ = eq_error(lib, A, B, Cm, n)
         assert em < 1.2 * e64 + 1e-6
         diff = float((Cm.matvec(x) - C64.matvec(x)).norm() / C64.matvec(x).norm())
         # within 2 eps of float64; float32 Gram sums resolve eigenvalues to ~1e-7 of
         # lambda_1, so below eps = 2e-5 the mixed product tracks float64 to ~2e-5
         assert diff < 2 * max(eps, 2e-5), (eps, diff)
-        info = C64.info()
-        assert info["cap_hits"] == 0
+        assert C64.info()["cap_hits"] == 0 and Cm.info()["cap_hits"] == 0
         res[eps] = C64
     # A's partition is kept
     for l in range(A.info()["levels"]):
