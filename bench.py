@@ -261,9 +261,9 @@ def main():
     peaks, src = _peaks()
     # ALU peaks from unit counts and the maximum SM clock: 152 SMs x 128 float32 FMA
     # lanes (resp. 2 float64 FMA per clock) x 2 flops x clock
-    clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    fp32_peak = 152 * 128 * 2 * clk / 1e12
-    fp64_peak = 152 * 2 * 2 * clk / 1e12
+    clk_hz = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    fp32_peak = 152 * 128 * 2 * clk_hz / 1e12
+    fp64_peak = 152 * 2 * 2 * clk_hz / 1e12
     peak = fp64_peak if args.precision == "fp64" else fp32_peak
     gemm_ms = tot.get("gemm", [0.0])[0]
     gemm_tf = executed_flops / (gemm_ms * 1e-3) / 1e12 if gemm_ms else 0.0
