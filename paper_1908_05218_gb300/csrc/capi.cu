@@ -396,10 +396,13 @@ void validate_plan(const Plan& P, const int64_t sizes[kArenas]) {
         check(it.a, (int64_t)(s.m - 1) * s.lda + s.n, "sum input");
         continue;
       }
-      if ((!ta && s.lda < s.k) || (ta && s.lda < s.m) || (!tb && s.ldb < s.n) || (tb && s.ldb < s.k))
+      const int lda = it.lda ? it.lda : s.lda, ldb = it.ldb ? it.ldb : s.ldb;
+      const int kp = it.kpad ? it.kpad : s.k;
+      if (kp > s.k) throw Error(H2_EINTERNAL, "item k above the segment's");
+      if ((!ta && lda < kp) || (ta && lda < s.m) || (!tb && ldb < s.n) || (tb && ldb < kp))
         throw Error(H2_EINTERNAL, "segment leading dimension too small");
-      check(it.a, ta ? (int64_t)(s.k - 1) * s.lda + s.m : (int64_t)(s.m - 1) * s.lda + s.k, "segment A");
-      check(it.b, tb ? (int64_t)(s.n - 1) * s.ldb + s.k : (int64_t)(s.k - 1) * s.ldb + s.n, "segment B");
+      check(it.a, ta ? (int64_t)(kp - 1) * lda + s.m : (int64_t)(s.m - 1) * lda + kp, "segment A");
+      check(it.b, tb ? (int64_t)(s.n - 1) * ldb + kp : (int64_t)(kp - 1) * ldb + s.n, "segment B");
     }
   }
   for (const EigTask& e : P.eigs) {
@@ -429,7 +432,9 @@ void upload_plan(Plan& P, size_t region_esize) {
         const Seg& s = P.segs[q];
         mx = std::max<int>(mx, s.n);
         md = std::max<int>(md, std::max<int>(s.m, s.n));
-        if (!(s.flags & SF_SUM)) fl += 2.0 * s.m * s.n * s.k * s.count;
+        if (!(s.flags & SF_SUM))
+          for (int32_t q = s.first; q < s.first + s.count; ++q)
+            fl += 2.0 * s.m * s.n * (P.items[q].kpad ? P.items[q].kpad : s.k);
       }
       L.aux = mx;
       L.aux2 = md;

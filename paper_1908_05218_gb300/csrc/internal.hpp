@@ -125,10 +125,14 @@ struct Seg {
 };
 struct Item {
   int64_t a = 0, b = 0;
-  int32_t kref = -1;  // bound of this item's k (see Seg), -1 = none
-  int32_t pad = 0;
+  int32_t kref = -1;         // bound of this item's k (see Seg), -1 = none
+  int16_t lda = 0, ldb = 0;  // this item's leading dimensions, 0 = the segment's
+  int16_t kpad = 0;          // this item's padded k, 0 = the segment's
+  int16_t pad0 = 0;
+  int32_t pad1 = 0;
   Item() = default;
-  Item(int64_t a_, int64_t b_, int32_t k_ = -1) : a(a_), b(b_), kref(k_), pad(0) {}
+  Item(int64_t a_, int64_t b_, int32_t k_ = -1, int16_t lda_ = 0, int16_t ldb_ = 0, int16_t kpad_ = 0)
+      : a(a_), b(b_), kref(k_), lda(lda_), ldb(ldb_), kpad(kpad_) {}
 };
 
 // Normalised Gram sum + eigen-decomposition + truncation for one cluster.

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(GNT, 12) seg_gemm_kernel(const Seg* __restrict
             }
         }
       } else {
-        int q = 0, koff = 0, K = s.count ? bound(ar, it[0].kref, s.k) : 0;
+        int q = 0, koff = 0, K = s.count ? bound(ar, it[0].kref, it[0].kpad ? it[0].kpad : s.k) : 0;
         // issue the copies of the next slice into buffer `buf`; returns its depth
         auto fill = [&](int buf) -> int {
           int kfill = 0;
@@ -143,32 +143,34 @@ __global__ void __launch_bounds__(GNT, 12) seg_gemm_kernel(const Seg* __restrict
           while (q < s.count && kfill < GK) {
             if (K == 0) {
               ++q;
-              if (q < s.count) K = bound(ar, it[q].kref, s.k);
+              if (q < s.count) K = bound(ar, it[q].kref, it[q].kpad ? it[q].kpad : s.k);
               continue;
             }
             const int take = min(K - koff, GK - kfill);
-            const T* A = ptr_of<T>(ar, it[q].a);
-            const T* B = ptr_of<T>(ar, it[q].b);
+            const Item iq = it[q];
+            const T* A = ptr_of<T>(ar, iq.a);
+            const T* B = ptr_of<T>(ar, iq.b);
+            const int lda = iq.lda ? iq.lda : s.lda, ldb = iq.ldb ? iq.ldb : s.ldb;
             if (ta) {
               for (int kk = tid / TILE; kk < take; kk += GNT / TILE) {
                 const int r = tid % TILE;
-                if (r < mc) cp_async(&a_s[(kfill + kk) * GPAD + r], A + (int64_t)(koff + kk) * s.lda + (m0 + r));
+                if (r < mc) cp_async(&a_s[(kfill + kk) * GPAD + r], A + (int64_t)(koff + kk) * lda + (m0 + r));
               }
             } else {
               for (int r = tid / GK; r < mc; r += GNT / GK) {
                 const int kk = tid % GK;
-                if (kk < take) cp_async(&a_s[(kfill + kk) * GPAD + r], A + (int64_t)(m0 + r) * s.lda + (koff + kk));
+                if (kk < take) cp_async(&a_s[(kfill + kk) * GPAD + r], A + (int64_t)(m0 + r) * lda + (koff + kk));
               }
             }
             if (tb) {
               for (int c = tid / GK; c < nc; c += GNT / GK) {
                 const int kk = tid % GK;
-                if (kk < take) cp_async(&b_s[(kfill + kk) * GPAD + c], B + (int64_t)(n0 + c) * s.ldb + (koff + kk));
+                if (kk < take) cp_async(&b_s[(kfill + kk) * GPAD + c], B + (int64_t)(n0 + c) * ldb + (koff + kk));
               }
             } else {
               for (int kk = tid / TILE; kk < take; kk += GNT / TILE) {
                 const int c = tid % TILE;
-                if (c < nc) cp_async(&b_s[(kfill + kk) * GPAD + c], B + (int64_t)(koff + kk) * s.ldb + (n0 + c));
+                if (c < nc) cp_async(&b_s[(kfill + kk) * GPAD + c], B + (int64_t)(koff + kk) * ldb + (n0 + c));
               }
             }
             kfill += take;
@@ -177,7 +179,7 @@ __global__ void __launch_bounds__(GNT, 12) seg_gemm_kernel(const Seg* __restrict
             if (koff == K) {
               koff = 0;
               ++q;
-              if (q < s.count) K = bound(ar, it[q].kref, s.k);
+              if (q < s.count) K = bound(ar, it[q].kref, it[q].kpad ? it[q].kpad : s.k);
             }
           }
           return kfill;
@@ -577,7 +579,11 @@ __global__ void __launch_bounds__(256) eig_mixed_kernel(const EigTask* __restric
     V32[e] = (e / lds == e % lds) ? 1.f : 0.f;
   }
   __syncthreads();
-  jacobi_sweeps<float>(A32, V32, nn, lds, 12, 1e-10, red, cs32, sn32, pp, qq);
+  // stop at an off-diagonal of 1e-4 of the total when float64 Rayleigh quotients
+  // decide the ranks (thresholds >= 5e-5), at 1e-5 before a float64 refinement
+  const double thr_rel = trunc == H2_TRUNC_SV ? eps * eps : eps;
+  const bool refine = trunc != H2_TRUNC_FULL && thr_rel < 5e-5;
+  jacobi_sweeps<float>(A32, V32, nn, lds, 12, refine ? 1e-10 : 1e-8, red, cs32, sn32, pp, qq);
   for (int e = tid; e < sz; e += nt) V[e] = (double)V32[e];
   __syncthreads();
   // (2) one Newton-Schulz step: V <- V (3 I - V^T V) / 2, computed as T = V W
@@ -611,9 +617,8 @@ __global__ void __launch_bounds__(256) eig_mixed_kernel(const EigTask* __restric
   // truncation threshold is below what float32 eigenvectors resolve (< 5e-5 of
   // lambda_1), the float64 Rayleigh-Ritz matrix B = V^T G V is diagonalised by float64
   // Jacobi sweeps first (rotations accumulated into V).
-  const double thr_rel = trunc == H2_TRUNC_SV ? eps * eps : eps;
   smem_gemm(G, false, V, false, T, nn, lds);   // T = G V
-  if (trunc != H2_TRUNC_FULL && thr_rel < 5e-5) {
+  if (refine) {
     smem_gemm(V, true, T, false, G, nn, lds);  // G <- V^T T = B
     for (int e = tid; e < nn * nn; e += nt) {
       int a = e / nn, b = e % nn;

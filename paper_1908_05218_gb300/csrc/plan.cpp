@@ -100,7 +100,7 @@ struct PlanBuilder {
     if ((int64_t)P.items.size() + (int64_t)it.size() > INT32_MAX) throw Error(H2_ENOMEM, "plan too large");
     P.items.insert(P.items.end(), it.begin(), it.end());
     P.segs.push_back(s);
-    P.flops += 2LL * m * n * k * (int64_t)it.size();
+    for (const Item& x : it) P.flops += 2LL * m * n * (x.kpad ? x.kpad : k);
   }
   void gemm1(int64_t out, int m, int n, int k, int lda, int ldb, int ldc, uint8_t fl, int64_t a, int64_t b,
              int32_t mref = -1, int32_t nref = -1, int32_t kref = -1) {
@@ -651,37 +651,39 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
     }
     pb.end("rimage", l);
 
-    // ---- couplings (Eq. leafcoup_simple / nonleafcoup_simple), three passes per target
-    std::vector<std::vector<Item>> g24(lt.tg.size()), g3(lt.tg.size());
+    // ---- couplings (Eq. leafcoup_simple / nonleafcoup_simple), summed per target in
+    // one segment: case-1 (leaf: (V^C^T F)(F V^C)), case-2/4 (Ahat SBP), case-3 (PAS Bhat);
+    // above the leaf level case-1 (E^C^T (M E^C)) is a separate first pass
+    std::vector<std::vector<Item>> cpl(lt.tg.size());
+    for (size_t q = 0; q < lt.tg.size(); ++q)
+      if (leaf && lt.tg[q].cls != TC_F)
+        for (const Item& x : lt.tg[q].g1) cpl[q].push_back(Item(x.a, x.b, -1, LS, cC(l), LS));
     for (auto& tr : lt.trip) {
       const Block &ba = bl[tr.pa], &bb = bl[tr.pb];
       const Target& T = lt.tg[tr.tgt];
       if (T.cls == TC_F) continue;
       if (ba.kind == KNL && bb.kind == KNL) continue;
-      if (ba.kind == KF && bb.kind == KF) continue;                      // case-1 (leaf)
-      if (bb.kind == KR) g24[tr.tgt].push_back({Ahat[l][tr.pa], SBP[tr.pb], BR(l, ba.s)});  // case-2, case-4
-      else g3[tr.tgt].push_back({PAS[tr.pa], Bhat[l][tr.pb], AC(l, ba.s)});                  // case-3
+      if (ba.kind == KF && bb.kind == KF) continue;  // case-1 (leaf), above
+      if (bb.kind == KR)  // case-2, case-4
+        cpl[tr.tgt].push_back(Item(Ahat[l][tr.pa], SBP[tr.pb], BR(l, ba.s), rB(l), cC(l), rB(l)));
+      else  // case-3
+        cpl[tr.tgt].push_back(Item(PAS[tr.pa], Bhat[l][tr.pb], AC(l, ba.s), cA(l), cC(l), cA(l)));
     }
-    pb.begin();
-    for (size_t q = 0; q < lt.tg.size(); ++q) {
-      Target& T = lt.tg[q];
-      if (T.cls == TC_F) continue;
-      if (leaf) pb.gemm(T.ssum, rC(l), cC(l), LS, LS, cC(l), cC(l), SF_ACC, T.g1, CR(l, T.i), CC(l, T.k));  // case-1
-      else if (Mt[q] >= 0)
-        pb.gemm1(T.ssum, rC(l), cC(l), gr, rC(l), cC(l), cC(l), SF_TA | SF_ACC, tCb(C.Er(l, T.i)), Mt[q], CR(l, T.i),
-                 CC(l, T.k));
+    const int kmax = std::max(std::max(leaf ? LS : 0, rB(l)), cA(l));
+    if (!leaf) {
+      pb.begin();
+      for (size_t q = 0; q < lt.tg.size(); ++q) {
+        Target& T = lt.tg[q];
+        if (Mt[q] >= 0)
+          pb.gemm1(T.ssum, rC(l), cC(l), gr, rC(l), cC(l), cC(l), SF_TA | SF_ACC, tCb(C.Er(l, T.i)), Mt[q], CR(l, T.i),
+                   CC(l, T.k));
+      }
+      pb.end("coup", l);
     }
-    pb.end("coup", l);
     pb.begin();
     for (size_t q = 0; q < lt.tg.size(); ++q)
       if (lt.tg[q].cls != TC_F)
-        pb.gemm(lt.tg[q].ssum, rC(l), cC(l), rB(l), rB(l), cC(l), cC(l), SF_ACC, g24[q], CR(l, lt.tg[q].i),
-                CC(l, lt.tg[q].k));
-    pb.end("coup", l);
-    pb.begin();
-    for (size_t q = 0; q < lt.tg.size(); ++q)
-      if (lt.tg[q].cls != TC_F)
-        pb.gemm(lt.tg[q].ssum, rC(l), cC(l), cA(l), cA(l), cC(l), cC(l), SF_ACC, g3[q], CR(l, lt.tg[q].i),
+        pb.gemm(lt.tg[q].ssum, rC(l), cC(l), kmax, kmax, cC(l), cC(l), SF_ACC, cpl[q], CR(l, lt.tg[q].i),
                 CC(l, lt.tg[q].k));
     pb.end("coup", l);
     pb.close_memset(zG, g);
