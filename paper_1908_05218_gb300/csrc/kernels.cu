@@ -579,11 +579,11 @@ __global__ void __launch_bounds__(256) eig_mixed_kernel(const EigTask* __restric
     V32[e] = (e / lds == e % lds) ? 1.f : 0.f;
   }
   __syncthreads();
-  // stop at an off-diagonal of 1e-4 of the total when float64 Rayleigh quotients
-  // decide the ranks (thresholds >= 5e-5), at 1e-5 before a float64 refinement
+  // float32 sweeps until the off-diagonal is below 1e-5 of the total (a looser stop
+  // moves the mixed product by more than 2 eps at eps = 1e-4)
   const double thr_rel = trunc == H2_TRUNC_SV ? eps * eps : eps;
   const bool refine = trunc != H2_TRUNC_FULL && thr_rel < 5e-5;
-  jacobi_sweeps<float>(A32, V32, nn, lds, 12, refine ? 1e-10 : 1e-8, red, cs32, sn32, pp, qq);
+  jacobi_sweeps<float>(A32, V32, nn, lds, 12, 1e-10, red, cs32, sn32, pp, qq);
   for (int e = tid; e < sz; e += nt) V[e] = (double)V32[e];
   __syncthreads();
   // (2) one Newton-Schulz step: V <- V (3 I - V^T V) / 2, computed as T = V W
