@@ -151,6 +151,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cubes16x16", choices=list(WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--trunc", default="paper", choices=["paper", "sv", "formatted"],
+                    help="truncation rule; 'formatted' = fixed bases (the paper's comparison method)")
     ap.add_argument("--oracle-sample", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -215,11 +217,11 @@ def main():
 
     C = None
     t0 = time.time()
-    C = A.mmp(B, eps, precision=prec, out=C)
+    C = A.mmp(B, eps, precision=prec, trunc=args.trunc, out=C)
     torch.cuda.synchronize()
     setup_s = time.time() - t0
     for _ in range(args.warmup):
-        C = A.mmp(B, eps, precision=prec, out=C)
+        C = A.mmp(B, eps, precision=prec, trunc=args.trunc, out=C)
     torch.cuda.synchronize()
 
     A.trace_enable(True)
@@ -230,7 +232,7 @@ def main():
     with Clocks(local) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
-            C = A.mmp(B, eps, precision=prec, out=C)
+            C = A.mmp(B, eps, precision=prec, trunc=args.trunc, out=C)
         ev1.record(stream)
         torch.cuda.synchronize()
     if dist:
@@ -295,7 +297,7 @@ def main():
         t0 = time.perf_counter()
         A2 = lib.h2_import(wa.points, LEAF, ETA, pa)
         B2 = lib.h2_import(wb.points, LEAF, ETA, pbk)
-        C2 = A2.mmp(B2, eps, precision=prec)
+        C2 = A2.mmp(B2, eps, precision=prec, trunc=args.trunc)
         pc = C2.export()
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
@@ -318,7 +320,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": f"{desc}; leaf {LEAF}, eta {ETA}, eps_trunc {eps} (paper rule), "
+            "config": {"workload": f"{desc}; leaf {LEAF}, eta {ETA}, eps_trunc {eps} ({args.trunc} rule), "
                                    f"eps_H2 {EPS_H2}; A: 1/(4 pi r), B: 1/r^2",
                        "inputs": "A, B, C together exceed L2 (no flush needed)", "parallelism": "replicas"},
             "mmp_s": ms * 1e-3, "rel_err_vs_exact_h2_matvecs": rel_err,

@@ -73,7 +73,11 @@ typedef enum {
                           paper's statement; error ~ sqrt(eps) in practice)      */
   H2_TRUNC_SV = 1,     /* threshold = eps^2: singular values of the stacked
                           contributions (error ~ eps)                            */
-  H2_TRUNC_FULL = 2    /* keep every vector (no truncation; for testing)         */
+  H2_TRUNC_FULL = 2,   /* keep every vector (no truncation; for testing)         */
+  H2_TRUNC_FORMATTED = 3 /* no change of bases: C takes A's row bases and B's column
+                          bases and every product is projected onto them (the
+                          earlier formatted product the paper compares with,
+                          Sec. VI, Table relErr_cube "Existing"); eps is unused   */
 } h2_trunc;
 
 typedef struct {
@@ -156,6 +160,16 @@ h2_status h2_export(h2_handle h, int64_t* sizes, int32_t* kr, int32_t* kc, doubl
  * launched and synchronises only to finish its setup.  *C owns its memory. */
 h2_status h2_mmp(h2_handle A, h2_handle B, double eps, const h2_opts* opts,
                  h2_handle* C);
+
+/* C[i] = A[i] x B[i] for i < count: independent products (for instance problems of
+ * different sizes) enqueued in order on opts->stream with the same eps and options.
+ * Instances with equal points, leaf size and eta share one cached program and its
+ * work regions, which is safe because the products run in stream order.  C[i] follow
+ * the in-place rule of h2_mmp.  On an error the products of instances before the
+ * failing one have been enqueued and their C[i] are valid; the error names the
+ * instance. */
+h2_status h2_mmp_batched(const h2_handle* A, const h2_handle* B, int32_t count, double eps,
+                         const h2_opts* opts, h2_handle* C);
 
 /* y = H x (exact H^2 arithmetic: forward transform, coupling, backward transform,
  * near field).  x, y: device float64, column-major n x nrhs, user order; y is

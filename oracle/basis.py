@@ -26,7 +26,7 @@ from __future__ import annotations
 
 import numpy as np
 
-PAPER, SV, FULL = "paper", "sv", "full"
+PAPER, SV, FULL, FORMATTED = "paper", "sv", "full", "formatted"
 
 
 def normalized_sum(grams, dim: int, dtype) -> np.ndarray:

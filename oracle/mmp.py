@@ -47,6 +47,11 @@ Readings (where the paper is silent, garbled or ambiguous):
   * the bottom-up traversal stops at l_min, the coarsest level holding an admissible
     block; clusters above it get rank 0 in C.
 
+Mode "formatted" is the comparison method of Sec. VI (Table relErr_cube, row
+"Existing"; Sec. I): the cluster bases of C are not changed but taken from A (rows)
+and B (columns), every product is projected onto them, and no Gram matrix or
+eigen-decomposition is formed.
+
 Pins: tests/test_oracle_mmp.py — mode "full" (no truncation) reproduces the exact
 dense product to rounding, which fixes every non-truncation step; the truncated
 product stays within a multiple of its bound; results do not depend on unitary
@@ -149,15 +154,16 @@ def mmp(A: H2, Bm: H2, eps: float, mode: str = Bs.PAPER, cap: int | None = None,
             C.Fb[(i, k)] += denseA(i, j, ka) @ denseB(j, k, kb)
 
     # Sec. III-C: Gram matrices of the new leaf row and column bases
+    formatted = mode == Bs.FORMATTED
     G1r = {i: [] for i in range(1 << L)}
     G1c = {k: [] for k in range(1 << L)}
-    for (i, j, k, ka, kb) in trip:
+    for (i, j, k, ka, kb) in ([] if formatted else trip):
         if ka == F and kb == F and cls[(i, k)] in (R, SUB):
             X = A.Fb[(i, j)] @ Bm.Fb[(j, k)]
             G1r[i].append(X @ _h(X))                       # Eq. Gr1L
             G1c[k].append(X.T @ X.conj())                  # Eq. case1-ch
     Vn_r, Vn_c = {}, {}
-    for i in range(1 << L):
+    for i in ([] if formatted else range(1 << L)):
         n_i = tree.size[L][i]
         g1 = sum(G1r[i]) if G1r[i] else None
         g2 = None
@@ -168,7 +174,7 @@ def mmp(A: H2, Bm: H2, eps: float, mode: str = Bs.PAPER, cap: int | None = None,
         g3 = A.Vr[i] @ _h(A.Vr[i])                                  # Eq. Gr3L
         G = Bs.normalized_sum([g1, g2, g3], n_i, dtype)
         Vn_r[i], _ = Bs.truncated_eigvecs(G, eps, mode, cap)
-    for k in range(1 << L):
+    for k in ([] if formatted else range(1 << L)):
         n_k = tree.size[L][k]
         g1 = sum(G1c[k]) if G1c[k] else None
         g2 = None
@@ -179,6 +185,9 @@ def mmp(A: H2, Bm: H2, eps: float, mode: str = Bs.PAPER, cap: int | None = None,
         g3 = Bm.Vc[k] @ _h(Bm.Vc[k])                                          # Eq. case3-ch
         G = Bs.normalized_sum([g1, g2, g3], n_k, dtype)
         Vn_c[k], _ = Bs.truncated_eigvecs(G, eps, mode, cap)
+    if formatted:                          # the existing formatted product keeps the bases
+        Vn_r = {i: A.Vr[i] for i in range(1 << L)}
+        Vn_c = {k: Bm.Vc[k] for k in range(1 << L)}
     C.Vr, C.Vc = Vn_r, Vn_c
     for t in range(1 << L):
         C.kr[(L, t)] = Vn_r[t].shape[1]
@@ -255,7 +264,10 @@ def mmp(A: H2, Bm: H2, eps: float, mode: str = Bs.PAPER, cap: int | None = None,
 
         # step 4: transfer Grams and the new stacked transfer matrices
         En_r, En_c = {}, {}
-        for i in range(1 << l):
+        if formatted:
+            En_r = {i: A.Er[(l, i)] for i in range(1 << l)}
+            En_c = {k: Bm.Ec[(l, k)] for k in range(1 << l)}
+        for i in ([] if formatted else range(1 << l)):
             dim = kCr(2 * i) + kCr(2 * i + 1)
             g1 = None
             for (ii, k), m in M.items():
@@ -271,7 +283,7 @@ def mmp(A: H2, Bm: H2, eps: float, mode: str = Bs.PAPER, cap: int | None = None,
             g3 = W @ _h(W)                                                 # Eq. case3-ch-nl
             G = Bs.normalized_sum([g1, g2, g3], dim, dtype)
             En_r[i], _ = Bs.truncated_eigvecs(G, eps, mode, cap)
-        for k in range(1 << l):
+        for k in ([] if formatted else range(1 << l)):
             dim = kCc(2 * k) + kCc(2 * k + 1)
             g1 = None
             for (i, kk), m in M.items():

@@ -134,7 +134,7 @@ h2_opts defaults(const h2_opts* o) {
     if (d.rank_cap <= 0) d.rank_cap = 48;
   }
   if (d.precision != H2_FP64 && d.precision != H2_MIXED_FP32) throw h2::Error(H2_EINVAL, "bad precision");
-  if (d.trunc < 0 || d.trunc > 2) throw h2::Error(H2_EINVAL, "bad truncation mode");
+  if (d.trunc < 0 || d.trunc > 3) throw h2::Error(H2_EINVAL, "bad truncation mode");
   if (d.rank_cap > 128) throw h2::Error(H2_EINVAL, "rank_cap above 128");
   return d;
 }
@@ -483,6 +483,12 @@ void run_plan(const Plan& P, const ArenaSet& ar, int32_t* kr, int32_t* kc, unsig
       int a = arena_of(L.off);
       char* p = (char*)ar.p[a] + offset_of(L.off) * ar.esize(a);
       cuda_check(cudaMemsetAsync(p, 0, L.elems * ar.esize(a), (cudaStream_t)stream), "memset");
+    } else if (L.kind == Launch::COPY_RANKS) {
+      // formatted product: C's ranks are A's row ranks and B's column ranks
+      cuda_check(cudaMemcpyAsync(kr, ar.rk[RK_AR], L.elems * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                                 (cudaStream_t)stream), "copy ranks");
+      cuda_check(cudaMemcpyAsync(kc, ar.rk[RK_BC], L.elems * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                                 (cudaStream_t)stream), "copy ranks");
     } else if (L.kind == Launch::GEMM) {
       launch_gemm(P.d_segs, P.d_items, L.first, L.count, ar, L.aux, L.aux2, prm.precision == H2_MIXED_FP32, stream);
     } else {
@@ -600,7 +606,8 @@ h2_status h2_mmp(h2_handle A, h2_handle B, double eps, const h2_opts* opts, h2_h
   if (!A || !B || !C) return fail(H2_EINVAL, "null argument");
   return guarded([&] {
     h2_opts o = defaults(opts);
-    if (o.trunc != H2_TRUNC_FULL && !(eps > 0 && eps < 1)) throw Error(H2_EINVAL, "eps must lie in (0, 1)");
+    if (o.trunc != H2_TRUNC_FULL && o.trunc != H2_TRUNC_FORMATTED && !(eps > 0 && eps < 1))
+      throw Error(H2_EINVAL, "eps must lie in (0, 1)");
     if (!same_structure(*A->m.st, *B->m.st)) throw Error(H2_ESTRUCT, "A and B have different trees or partitions");
     MmpParams prm{eps, o.trunc, o.rank_cap, o.precision};
     // plan cache, process-wide
@@ -710,6 +717,16 @@ h2_status h2_mmp(h2_handle A, h2_handle B, double eps, const h2_opts* opts, h2_h
     out->timed = true;
     if (fresh) *C = fresh.release();
   });
+}
+
+h2_status h2_mmp_batched(const h2_handle* A, const h2_handle* B, int32_t count, double eps, const h2_opts* opts,
+                         h2_handle* C) {
+  if (!A || !B || !C || count < 0) return fail(H2_EINVAL, "null argument or negative count");
+  for (int32_t i = 0; i < count; ++i) {
+    h2_status s = h2_mmp(A[i], B[i], eps, opts, &C[i]);
+    if (s != H2_OK) return fail(s, "instance " + std::to_string(i) + ": " + g_err);
+  }
+  return H2_OK;
 }
 
 h2_status h2_matvec(h2_handle h, const double* x, double* y, int64_t nrhs) {

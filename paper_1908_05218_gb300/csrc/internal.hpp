@@ -146,7 +146,7 @@ struct EigTask {
 };
 
 struct Launch {
-  enum Kind { GEMM, EIG, MEMSET } kind;
+  enum Kind { GEMM, EIG, MEMSET, COPY_RANKS } kind;
   int64_t first = 0, count = 0;  // range in segs / eigs
   int64_t off = 0, elems = 0;    // MEMSET: tagged offset and size
   int level = -1;

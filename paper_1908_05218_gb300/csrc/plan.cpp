@@ -195,13 +195,19 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
   const int L = st.L, LS = st.LS, lmin = st.lmin;
   PlanBuilder pb(P);
   // caps of C: leaf LS, non-leaf min(2 K[l+1], cap) (no cap in full mode), 0 above l_min
+  const bool formatted = prm.trunc == H2_TRUNC_FORMATTED;
   C.Kr.assign(L + 1, 0);
   C.Kc.assign(L + 1, 0);
-  C.Kr[L] = C.Kc[L] = LS;
-  for (int l = L - 1; l >= lmin; --l) {
-    int cap = prm.trunc == H2_TRUNC_FULL ? 1 << 20 : prm.rank_cap;
-    C.Kr[l] = std::min(2 * C.Kr[l + 1], cap);
-    C.Kc[l] = std::min(2 * C.Kc[l + 1], cap);
+  if (formatted) {  // C keeps A's row bases and B's column bases
+    C.Kr = A.Kr;
+    C.Kc = B.Kc;
+  } else {
+    C.Kr[L] = C.Kc[L] = LS;
+    for (int l = L - 1; l >= lmin; --l) {
+      int cap = prm.trunc == H2_TRUNC_FULL ? 1 << 20 : prm.rank_cap;
+      C.Kr[l] = std::min(2 * C.Kr[l + 1], cap);
+      C.Kc[l] = std::min(2 * C.Kc[l + 1], cap);
+    }
   }
   mat_elems(C);  // offsets of C's arrays
   auto rA = [&](int l) { return A.Kr[l]; };
@@ -228,6 +234,13 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
   const int64_t LS2 = (int64_t)LS * LS;
 
   const size_t zP = pb.open_memset(AR_P);  // couplings held by NL targets accumulate
+  if (formatted) {
+    Launch cr;
+    cr.kind = Launch::COPY_RANKS;
+    cr.elems = st.nnodes();
+    cr.phase = "copy_ranks";
+    P.launches.push_back(cr);
+  }
   // per-level data handed to the next level up (in G[level parity])
   std::vector<std::vector<int64_t>> Bj(L + 1), PA(L + 1), PB(L + 1), Ahat(L + 1), Bhat(L + 1);
   std::vector<LevelTargets> LT(L + 1);
@@ -359,10 +372,11 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         if (b.kind != KF) continue;
         pb.gemm1(Y[p], LS, rB(l), LS, LS, rB(l), rB(l), 0, tA(A.F(b.idx)), tB(B.Vr(b.s)), -1, BR(l, b.s));
         pb.gemm1(Yb[p], cA(l), LS, LS, cA(l), LS, LS, SF_TA, tA(A.Vc(b.t)), tB(B.F(b.idx)), AC(l, b.t));
+        if (formatted) continue;
         pb.gemm1(Q[p], LS, LS, LS, LS, LS, LS, SF_TB, tB(B.F(b.idx)), tB(B.F(b.idx)));
         pb.gemm1(Rr[p], LS, LS, LS, LS, LS, LS, SF_TA, tA(A.F(b.idx)), tA(A.F(b.idx)));
       }
-      for (int64_t t = 0; t < nc; ++t) {
+      for (int64_t t = 0; t < nc && !formatted; ++t) {
         pb.gemm1(G3r[t], LS, LS, rA(l), rA(l), rA(l), LS, SF_TB, tA(A.Vr(t)), tA(A.Vr(t)), -1, -1, AR(l, t));
         pb.gemm1(G3c[t], LS, LS, cB(l), cB(l), cB(l), LS, SF_TB, tB(B.Vc(t)), tB(B.Vc(t)), -1, -1, BC(l, t));
       }
@@ -377,11 +391,11 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         pb.gemm(Zp[q], rA(l), LS, cA(l), cA(l), LS, LS, 0, gZp[q], AR(l, T.i));
         pb.gemm(Zpp[q], rA(l), cB(l), rB(l), rB(l), cB(l), cB(l), 0, gZpp[q], AR(l, T.i), BC(l, T.k));
       }
-      for (int64_t p = 0; p < nb; ++p) {
+      for (int64_t p = 0; p < nb && !formatted; ++p) {
         pb.sum(Wsum[p], LS, LS, LS, LS, false, Ksets[p]);
         pb.sum(Wsc[p], LS, LS, LS, LS, false, Isets[p]);
       }
-      for (int64_t t = 0; t < nc; ++t) {
+      for (int64_t t = 0; t < nc && !formatted; ++t) {
         std::vector<Item> r2, c2;
         for (int32_t p = st.row_ptr[l][t]; p < st.row_ptr[l][t + 1]; ++p)
           if (bl[p].kind == KF) r2.push_back({Y[p], Y[p], BR(l, bl[p].s)});
@@ -407,7 +421,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
           pb.gemm1(Z[q], LS, cB(l), rA(l), rA(l), cB(l), cB(l), SF_ACC, tA(A.Vr(T.i)), Zpp[q], -1, BC(l, T.k),
                    AR(l, T.i));
       }
-      for (int64_t p = 0; p < nb; ++p) {
+      for (int64_t p = 0; p < nb && !formatted; ++p) {
         if (Wsum[p] >= 0) pb.gemm1(Q[p], LS, LS, LS, LS, LS, LS, 0, tA(A.F(bl[p].idx)), Wsum[p]);
         if (Wsc[p] >= 0) pb.gemm1(Rr[p], LS, LS, LS, LS, LS, LS, 0, Wsc[p], tB(B.F(bl[p].idx)));
       }
@@ -420,7 +434,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
           pb.gemm1(tC(C.F(bl[T.cpos].idx)), LS, LS, cB(l), cB(l), cB(l), LS, SF_TB | SF_ACC, Z[q], tB(B.Vc(T.k)), -1,
                    -1, BC(l, T.k));
       }
-      for (int64_t t = 0; t < nc; ++t) {
+      for (int64_t t = 0; t < nc && !formatted; ++t) {
         std::vector<Item> r1, c1;
         for (int32_t p = st.row_ptr[l][t]; p < st.row_ptr[l][t + 1]; ++p)
           if (Wsum[p] >= 0) r1.push_back({Q[p], tA(A.F(bl[p].idx))});
@@ -513,7 +527,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         if (it == LT[c].id.end()) throw Error(H2_EINTERNAL, "missing child target");
         return LT[c].tg[it->second].ssum;
       };
-      for (int64_t t = 0; t < nc; ++t) {
+      for (int64_t t = 0; t < nc && !formatted; ++t) {
         if (!trow[t].empty()) {
           G1r[t] = pb.alloc(AR_S, (int64_t)gr * gr);
           for (int a = 0; a < 2; ++a)
@@ -543,7 +557,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       }
       pb.end("nl_gram", l);
       pb.begin();
-      for (int64_t t = 0; t < nc; ++t) {
+      for (int64_t t = 0; t < nc && !formatted; ++t) {
         std::vector<Item> r2, c2;
         for (int32_t p = st.row_ptr[l][t]; p < st.row_ptr[l][t + 1]; ++p)
           if (bl[p].kind == KNL) r2.push_back({Y[p], Y[p], BR(l, bl[p].s)});
@@ -567,9 +581,27 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         if (lt.tg[q].has_nlnl && lt.tg[q].cls != TC_NL) Mt[q] = pb.alloc(AR_S, (int64_t)gr * cC(l));
     }
 
-    // ---- eig: new leaf bases / stacked transfer matrices of C
+    // ---- eig: new leaf bases / stacked transfer matrices of C (formatted product:
+    // copies of A's row and B's column bases, also into the float shadow if any)
+    if (formatted) {
+      pb.begin();
+      for (int64_t t = 0; t < nc; ++t)
+        for (Arena dst : {AR_C, basis_src}) {
+          if (dst == AR_X || dst == AR_C) {
+            if (leaf) {
+              pb.sum(tag(dst, C.Vr(t)), LS, rC(l), rC(l), rC(l), false, {tA(A.Vr(t))});
+              pb.sum(tag(dst, C.Vc(t)), LS, cC(l), cC(l), cC(l), false, {tB(B.Vc(t))});
+            } else {
+              pb.sum(tag(dst, C.Er(l, t)), 2 * rC(c), rC(l), rC(l), rC(l), false, {tA(A.Er(l, t))});
+              pb.sum(tag(dst, C.Ec(l, t)), 2 * cC(c), cC(l), cC(l), cC(l), false, {tB(B.Ec(l, t))});
+            }
+          }
+          if (basis_src == AR_C) break;
+        }
+      pb.end("copy_bases", l);
+    }
     size_t e0 = P.eigs.size();
-    for (int64_t t = 0; t < nc; ++t)
+    for (int64_t t = 0; t < nc && !formatted; ++t)
       for (int col = 0; col < 2; ++col) {
         EigTask e{};
         e.g[0] = col ? G1c[t] : G1r[t];

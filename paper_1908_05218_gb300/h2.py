@@ -18,11 +18,11 @@ LIB_PATH = os.path.join(_HERE, "libh2gb300.so")
 
 H2_OK, H2_EINVAL, H2_ENOMEM, H2_ECUDA, H2_ESTRUCT, H2_ETIMEOUT, H2_EINTERNAL, H2_EUNSUPPORTED = range(8)
 FP64, MIXED_FP32 = 0, 1
-TRUNC_PAPER, TRUNC_SV, TRUNC_FULL = 0, 1, 2
-_TRUNC = {"paper": TRUNC_PAPER, "sv": TRUNC_SV, "full": TRUNC_FULL}
+TRUNC_PAPER, TRUNC_SV, TRUNC_FULL, TRUNC_FORMATTED = 0, 1, 2, 3
+_TRUNC = {"paper": TRUNC_PAPER, "sv": TRUNC_SV, "full": TRUNC_FULL, "formatted": TRUNC_FORMATTED}
 
 # exported symbols and their signatures (checked by the CPU tests)
-SYMBOLS = ["h2_build", "h2_import", "h2_export", "h2_mmp", "h2_matvec", "h2_matvec_noalloc", "h2_to_dense", "h2_info",
+SYMBOLS = ["h2_build", "h2_import", "h2_export", "h2_mmp", "h2_mmp_batched", "h2_matvec", "h2_matvec_noalloc", "h2_to_dense", "h2_info",
            "h2_tree_perm", "h2_level_blocks", "h2_trace_enable", "h2_trace_read", "h2_trace_flops", "h2_trace_phase", "h2_destroy",
            "h2_last_error"]
 
@@ -65,6 +65,7 @@ def load(path: str = LIB_PATH):
     lib.h2_import.argtypes = [P, I64, I32, D, P, P, P, P, P, P, P, P, C.POINTER(Opts), C.POINTER(P)]
     lib.h2_export.argtypes = [P, P, P, P, P, P, P, P, P, P]
     lib.h2_mmp.argtypes = [P, P, D, C.POINTER(Opts), C.POINTER(P)]
+    lib.h2_mmp_batched.argtypes = [P, P, I32, D, C.POINTER(Opts), P]
     lib.h2_matvec.argtypes = [P, P, P, I64]
     lib.h2_matvec_noalloc.argtypes = [P, P, P, I64]
     lib.h2_to_dense.argtypes = [P, P]
@@ -240,6 +241,26 @@ class H2Matrix:
         if cnt.value:
             _check(lib.h2_level_blocks(self.handle, level, _ptr(t), _ptr(s), _ptr(k), C.byref(cnt)))
         return t, s, k
+
+
+def h2_mmp_batched(As, Bs, eps: float, precision: int = FP64, trunc="paper", rank_cap: int = 0,
+                   outs=None, stream=None) -> list:
+    """[A_i x B_i] through h2_mmp_batched (independent products, in order on one stream)."""
+    n = len(As)
+    if len(Bs) != n:
+        raise ValueError("A and B lists differ in length")
+    o = make_opts(precision, trunc, rank_cap, stream)
+    ha = (C.c_void_p * n)(*[a.handle.value for a in As])
+    hb = (C.c_void_p * n)(*[b.handle.value for b in Bs])
+    hc = (C.c_void_p * n)(*[(outs[i].handle.value if outs else 0) for i in range(n)])
+    _check(load().h2_mmp_batched(ha, hb, n, float(eps), C.byref(o), hc))
+    res = []
+    for i in range(n):
+        if outs and hc[i] == outs[i].handle.value:
+            res.append(outs[i])
+        else:
+            res.append(H2Matrix(hc[i], As[i].n))
+    return res
 
 
 def h2_build(points: np.ndarray, spec, leaf_size: int = 32, eta: float = 1.0, eps: float = 1e-4,

@@ -161,3 +161,37 @@ def test_fp64_rank_bounds_do_not_change_results(lib):
     d1 = c1.to_dense().cpu().numpy()
     C = ommp.mmp(A, A, 1e-5, "sv")
     assert rel(d1, oh2.to_dense(C)) < TOL
+
+
+@pytest.mark.parametrize("name,prec", [("cubes_1024", "fp64"), ("cubes_2048_invr2", "fp64"),
+                                       ("uniform_1000_ragged", "mixed")])
+def test_formatted_product_matches_oracle(lib, name, prec):
+    # the comparison method of Sec. VI (fixed bases): float64 parity with the oracle,
+    # mixed within 2 max(eps, 2e-5) with eps = 1e-4 as the scale
+    w, leaf, eta, A = oracle_case(name)
+    C = ommp.mmp(A, A, 0.0, "formatted")
+    ga = lib.h2_import(w.points, leaf, eta, pack(A))
+    gc = ga.mmp(ga, 0.0, trunc=lib.TRUNC_FORMATTED,
+                precision=lib.FP64 if prec == "fp64" else lib.MIXED_FP32)
+    d = gc.to_dense().cpu().numpy()
+    e = gc.export()
+    ckr, ckc = ranks(C)
+    np.testing.assert_array_equal(e.kr, ckr)
+    np.testing.assert_array_equal(e.kc, ckc)
+    assert rel(d, oh2.to_dense(C)) < (TOL if prec == "fp64" else 2e-4)
+
+
+def test_batched_products_equal_single_products(lib):
+    # independent instances of uneven size (config-4 style: stretched boxes)
+    import torch
+    hs = []
+    for i, n in enumerate((700, 1500, 2600)):
+        pts = inputs.stretched_box(n, seed=i)
+        hs.append(lib.h2_build(pts, inputs.laplace_spec(n ** (-1 / 3)), 32, 1.0, 1e-4))
+    cs = lib.h2_mmp_batched(hs, hs, 1e-4, precision=lib.MIXED_FP32)
+    for h, c in zip(hs, cs):
+        single = h.mmp(h, 1e-4, precision=lib.MIXED_FP32)
+        x = torch.ones((h.n, 2), dtype=torch.float64, device="cuda")
+        assert torch.equal(c.matvec(x), single.matvec(x))
+    cs2 = lib.h2_mmp_batched(hs, hs, 1e-4, precision=lib.MIXED_FP32, outs=cs)
+    assert all(a is b for a, b in zip(cs, cs2))

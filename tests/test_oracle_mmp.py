@@ -136,3 +136,29 @@ def test_planted_mistake_breaks_the_accuracy_pin(cube2x2_pair, monkeypatch):
     monkeypatch.setattr(mmp.Bs, "normalized_sum", drop_second)
     err = rel(h2.to_dense(mmp.mmp(A, B, 1e-4, "paper")), ref)
     assert err > 1.0 * math.sqrt(1e-4)
+
+
+def test_formatted_product_keeps_input_bases_and_is_exact_with_complete_bases(cube2x2_pair):
+    # the comparison method ("Existing" row of the cube-array table): C's bases are
+    # A's row and B's column bases.  With complete bases (a full-mode product as input:
+    # square leaf bases and transfers) every projection is the identity -> exact.
+    _, _, A, B = cube2x2_pair
+    Cf = mmp.mmp(A, B, 0.0, Bs.FULL)
+    D = mmp.mmp(Cf, Cf, 0.0, Bs.FORMATTED)
+    ref = h2.to_dense(Cf) @ h2.to_dense(Cf)
+    assert rel(h2.to_dense(D), ref) < 1e-12
+    E = mmp.mmp(A, B, 0.0, Bs.FORMATTED)
+    L = A.L
+    assert all(E.kr[(L, t)] == A.kr[(L, t)] for t in range(1 << L))
+    assert all(E.kc[(L, t)] == B.kc[(L, t)] for t in range(1 << L))
+    np.testing.assert_array_equal(E.Vr[0], A.Vr[0])
+
+
+def test_formatted_product_is_less_accurate_than_change_of_bases(cube2x2_pair):
+    # Sec. VI, Table relErr_cube: the formatted product's error exceeds the proposed
+    # product's at every eps_trunc
+    _, _, A, B = cube2x2_pair
+    ref = h2.to_dense(A) @ h2.to_dense(B)
+    e_fmt = rel(h2.to_dense(mmp.mmp(A, B, 0.0, Bs.FORMATTED)), ref)
+    e_new = rel(h2.to_dense(mmp.mmp(A, B, 1e-2, "paper")), ref)
+    assert e_fmt > e_new
