@@ -408,7 +408,8 @@ void validate_plan(const Plan& P, const int64_t sizes[kArenas]) {
   for (const EigTask& e : P.eigs) {
     for (int m = 0; m < 3; ++m)
       if (e.g[m] >= 0) check(e.g[m], (int64_t)e.n_pad * e.n_pad, "eig Gram");
-    if (e.scratch >= 0) check(e.scratch, (int64_t)e.n_pad * e.n_pad, "eig scratch");
+    const int64_t ne = e.n_pad + (e.n_pad & 1);
+    if (e.scratch >= 0) check(e.scratch, ne * ne, "eig scratch");
     check(e.out, (int64_t)e.n_pad * e.kcap, "eig output");
     if (e.child1 < 0 && e.nleaf > e.n_pad) throw Error(H2_EINTERNAL, "eig leaf size above n_pad");
     if (e.child1 >= 0 && 2 * e.half > e.n_pad) throw Error(H2_EINTERNAL, "eig half above n_pad");

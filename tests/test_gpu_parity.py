@@ -195,3 +195,15 @@ def test_batched_products_equal_single_products(lib):
         assert torch.equal(c.matvec(x), single.matvec(x))
     cs2 = lib.h2_mmp_batched(hs, hs, 1e-4, precision=lib.MIXED_FP32, outs=cs)
     assert all(a is b for a, b in zip(cs, cs2))
+
+
+@pytest.mark.parametrize("n", [700, 2600])
+def test_mixed_product_is_deterministic_with_odd_leaf_sizes(lib, n):
+    # leaf clusters of 21 points give odd Gram dimensions; three runs must agree bit
+    # for bit (fixed summation orders, no shared scratch between clusters)
+    pts = inputs.stretched_box(n, seed=1)
+    h = lib.h2_build(pts, inputs.laplace_spec(n ** (-1 / 3)), 32, 1.0, 1e-4)
+    ex = [h.mmp(h, 1e-4, precision=lib.MIXED_FP32).export() for _ in range(3)]
+    for e in ex[1:]:
+        for f in ("kr", "kc", "vr", "vc", "er", "ec", "s", "f"):
+            np.testing.assert_array_equal(getattr(e, f), getattr(ex[0], f))
