@@ -408,8 +408,6 @@ void validate_plan(const Plan& P, const int64_t sizes[kArenas]) {
   for (const EigTask& e : P.eigs) {
     for (int m = 0; m < 3; ++m)
       if (e.g[m] >= 0) check(e.g[m], (int64_t)e.n_pad * e.n_pad, "eig Gram");
-    const int64_t ne = e.n_pad + (e.n_pad & 1);
-    if (e.scratch >= 0) check(e.scratch, ne * ne, "eig scratch");
     check(e.out, (int64_t)e.n_pad * e.kcap, "eig output");
     if (e.child1 < 0 && e.nleaf > e.n_pad) throw Error(H2_EINTERNAL, "eig leaf size above n_pad");
     if (e.child1 >= 0 && 2 * e.half > e.n_pad) throw Error(H2_EINTERNAL, "eig half above n_pad");
@@ -495,7 +493,7 @@ void run_plan(const Plan& P, const ArenaSet& ar, int32_t* kr, int32_t* kc, unsig
       launch_gemm(P.d_segs, P.d_items, L.first, L.count, ar, L.aux, L.aux2, prm.precision == H2_MIXED_FP32, stream);
     } else {
       if (prm.precision == H2_MIXED_FP32 && L.aux <= 96)
-        launch_eig_split(P.d_eigs, L.first, L.count, ar, kr, kc, prm.eps, prm.trunc, cap_hits, L.aux, stream);
+        launch_eig_mixed(P.d_eigs, L.first, L.count, ar, kr, kc, prm.eps, prm.trunc, cap_hits, L.aux, stream);
       else
         launch_eig(P.d_eigs, L.first, L.count, ar, kr, kc, prm.eps, prm.trunc, cap_hits, L.aux, P.d_scratch, stream);
     }

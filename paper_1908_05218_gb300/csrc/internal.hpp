@@ -139,8 +139,6 @@ struct Item {
 struct EigTask {
   int64_t g[3];      // tagged offsets of the three Gram matrices (-1: absent)
   int64_t out;       // tagged offset of the new basis / stacked transfer (n_pad x kcap)
-  int64_t scratch;   // tagged offset of n_pad x n_pad floats (mixed product: float32
-                     // eigenvectors handed from the Jacobi kernel to the float64 finish)
   int32_t rank_out;  // node id whose rank is written
   int32_t child1, child2;  // node ids of the children (ranks in the same rank array), -1: leaf
   int32_t nleaf;     // leaf: cluster size; active rows [0, nleaf)
@@ -214,8 +212,6 @@ void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, const Arena
                 int max_npad, double* scratch, void* stream);
 void launch_to_f32(const double* src, float* dst, int64_t n, void* stream);
 void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const ArenaSet& ar, int32_t* kr,
-                      int32_t* kc, double eps, int trunc, unsigned long long* cap_hits, int max_npad, void* stream);
-void launch_eig_split(const EigTask* d_eigs, int64_t first, int64_t count, const ArenaSet& ar, int32_t* kr,
                       int32_t* kc, double eps, int trunc, unsigned long long* cap_hits, int max_npad, void* stream);
 void launch_permute(const double* src, double* dst, const int64_t* user, int64_t rows, int64_t n,
                     int64_t nrhs, bool to_tree, void* stream);

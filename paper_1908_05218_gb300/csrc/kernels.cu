@@ -712,346 +712,6 @@ void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const
                                                                          cap_hits);
 }
 
-// ------------------------------------------------------------ split mixed eigen step
-// Kernel 1 (one warp per cluster, several clusters per CTA): normalised Gram sum in
-// float32 and cyclic round-robin Jacobi in float32, warp-synchronous: each rotation
-// pair belongs to lpp = 32 / (n/2) lanes (or a lane owns two pairs when n > 64),
-// rows are padded to n+1 so row and column sweeps are free of bank conflicts.  The
-// eigenvectors go to the task's float scratch.  Kernel 2 (one CTA per cluster):
-// float64 Rayleigh quotients v_j^T G v_j decide the ranks; one float64 Newton-Schulz
-// step re-orthonormalises the kept columns; for thresholds below 5e-5 lambda_1 the
-// float64 Rayleigh-Ritz matrix V^T G V is refined by float64 Jacobi sweeps first.
-__device__ __forceinline__ double warp_sum(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-__device__ int active_rows(const EigTask& t, const int32_t* ranks, int* act) {
-  int n = 0;
-  if (t.child1 < 0) {
-    for (int a = 0; a < t.nleaf; ++a) act[n++] = a;
-  } else {
-    int k1 = ranks[t.child1], k2 = ranks[t.child2];
-    for (int a = 0; a < k1; ++a) act[n++] = a;
-    for (int a = 0; a < k2; ++a) act[n++] = t.half + a;
-  }
-  return n;
-}
-
-__global__ void eig_jacobi32_warp_kernel(const EigTask* __restrict__ tasks, int64_t first, int64_t count, Arenas ar,
-                                         int32_t* kr, int32_t* kc, int nnmax) {
-  extern __shared__ float wsm[];
-  __shared__ int act_all[8][kMixMax + 2];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpc = blockDim.x >> 5;
-  const int64_t ti = (int64_t)blockIdx.x * wpc + w;
-  if (ti >= count) return;
-  const EigTask t = tasks[first + ti];
-  const int32_t* ranks = t.col ? kc : kr;
-  int* act = act_all[w];
-  int n = 0;
-  if (lane == 0) n = active_rows(t, ranks, act);
-  n = __shfl_sync(0xffffffffu, n, 0);
-  __syncwarp();
-  const int nn = n + (n & 1), lds = nn + 1, np = nn / 2;
-  float* A = wsm + (int64_t)w * 2 * nnmax * (nnmax + 1);
-  float* V = A + nnmax * (nnmax + 1);
-  for (int e = lane; e < nn * lds; e += 32) {
-    A[e] = 0.f;
-    V[e] = (e / lds == e % lds) ? 1.f : 0.f;
-  }
-  __syncwarp();
-  for (int m = 0; m < 3; ++m) {
-    if (t.g[m] < 0) continue;
-    const View G = view(ar, t.g[m]);
-    double loc = 0.0;
-    for (int e = lane; e < n * n; e += 32) {
-      double v = ld<double>(G, (int64_t)act[e / n] * t.n_pad + act[e % n]);
-      loc += v * v;
-    }
-    const double nrm2 = warp_sum(loc);
-    if (nrm2 > 0.0) {
-      const double inv = 1.0 / sqrt(nrm2);
-      for (int e = lane; e < n * n; e += 32) {
-        const int a = e / n, b = e % n;
-        A[a * lds + b] += (float)(ld<double>(G, (int64_t)act[a] * t.n_pad + act[b]) * inv);
-      }
-    }
-    __syncwarp();
-  }
-  for (int e = lane; e < nn * nn; e += 32) {  // symmetrise
-    const int a = e / nn, b = e % nn;
-    if (a < b) {
-      const float v = 0.5f * (A[a * lds + b] + A[b * lds + a]);
-      A[a * lds + b] = v;
-      A[b * lds + a] = v;
-    }
-  }
-  __syncwarp();
-  // lanes per pair (power of two) and pairs per lane
-  int lpp = 1;
-  while (lpp * 2 * np <= 32 && lpp < 32) lpp *= 2;
-  const int part = lane % lpp;
-  for (int sweep = 0; sweep < 12 && nn > 1; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (int e = lane; e < nn * nn; e += 32) {
-      const int a = e / nn, b = e % nn;
-      const double v = (double)A[a * lds + b] * (double)A[a * lds + b];
-      tot += v;
-      if (a != b) off += v;
-    }
-    off = warp_sum(off);
-    tot = warp_sum(tot);
-    if (!(off > 1e-10 * tot)) break;
-    for (int step = 0; step < nn - 1; ++step) {
-      int pk[2], qk[2];
-      float ck[2], sk[2];
-      int npairs = 0;
-      for (int k = lane / lpp; k < np; k += 32 / lpp) {
-        const int pa = (k == 0) ? 0 : ((k - 1 + step) % (nn - 1)) + 1;
-        const int pb = ((nn - 1 - k - 1 + step) % (nn - 1)) + 1;
-        const int p = min(pa, pb), q = max(pa, pb);
-        const float apq = A[p * lds + q];
-        float c = 1.f, s = 0.f;
-        if (apq != 0.f) {
-          const float tau = (A[q * lds + q] - A[p * lds + p]) / (2.f * apq);
-          const float tt = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-          c = 1.f / sqrtf(1.f + tt * tt);
-          s = tt * c;
-        }
-        pk[npairs] = p;
-        qk[npairs] = q;
-        ck[npairs] = c;
-        sk[npairs] = s;
-        ++npairs;
-      }
-      __syncwarp();
-      for (int u = 0; u < npairs; ++u) {  // rows p, q
-        if (sk[u] == 0.f) continue;
-        const int p = pk[u], q = qk[u];
-        const float c = ck[u], s = sk[u];
-        for (int j = part; j < nn; j += lpp) {
-          const float x = A[p * lds + j], y = A[q * lds + j];
-          A[p * lds + j] = c * x - s * y;
-          A[q * lds + j] = s * x + c * y;
-        }
-      }
-      __syncwarp();
-      for (int u = 0; u < npairs; ++u) {  // columns p, q of A and V
-        if (sk[u] == 0.f) continue;
-        const int p = pk[u], q = qk[u];
-        const float c = ck[u], s = sk[u];
-        for (int i = part; i < nn; i += lpp) {
-          const float x = A[i * lds + p], y = A[i * lds + q];
-          A[i * lds + p] = c * x - s * y;
-          A[i * lds + q] = s * x + c * y;
-          const float vx = V[i * lds + p], vy = V[i * lds + q];
-          V[i * lds + p] = c * vx - s * vy;
-          V[i * lds + q] = s * vx + c * vy;
-        }
-      }
-      __syncwarp();
-    }
-  }
-  float* out = (float*)ar.p[(t.scratch >> kTagShift) & 7] + (t.scratch & kOffMask);
-  for (int e = lane; e < nn * nn; e += 32) out[e] = V[(e / nn) * lds + (e % nn)];
-}
-
-__global__ void __launch_bounds__(256) eig_finish64_kernel(const EigTask* __restrict__ tasks, int64_t first,
-                                                           Arenas ar, int32_t* kr, int32_t* kc, double eps,
-                                                           int trunc, unsigned long long* cap_hits) {
-  extern __shared__ double smem[];
-  __shared__ int act[kMixMax + 2];
-  __shared__ double red[8];
-  __shared__ double cs[kMixMax / 2 + 1], sn[kMixMax / 2 + 1];
-  __shared__ int pp[kMixMax / 2 + 1], qq[kMixMax / 2 + 1];
-  __shared__ int order[kMixMax + 2];
-  __shared__ double lam[kMixMax + 2];
-  __shared__ double rowbuf[4 * kMixMax];
-  __shared__ int s_n, s_rank;
-  const EigTask t = tasks[first + blockIdx.x];
-  const int tid = threadIdx.x, nt = blockDim.x;
-  int32_t* ranks = t.col ? kc : kr;
-  if (tid == 0) s_n = active_rows(t, ranks, act);
-  __syncthreads();
-  const int n = s_n, nn = n + (n & 1), lds = nn + 1, sz = nn * lds;
-  double* G = smem;
-  double* V = smem + sz;
-  double* T = smem + 2 * sz;
-  for (int e = tid; e < sz; e += nt) G[e] = 0.0;
-  const float* v32 = (const float*)ar.p[(t.scratch >> kTagShift) & 7] + (t.scratch & kOffMask);
-  for (int e = tid; e < nn * nn; e += nt) V[(e / nn) * lds + (e % nn)] = (double)v32[e];
-  __syncthreads();
-  for (int m = 0; m < 3; ++m) {
-    if (t.g[m] < 0) continue;
-    const View Gm = view(ar, t.g[m]);
-    double loc = 0.0;
-    for (int e = tid; e < n * n; e += nt) {
-      double v = ld<double>(Gm, (int64_t)act[e / n] * t.n_pad + act[e % n]);
-      loc += v * v;
-    }
-    double nrm2 = block_sum(loc, red);
-    if (nrm2 > 0.0) {
-      double inv = 1.0 / sqrt(nrm2);
-      for (int e = tid; e < n * n; e += nt)
-        G[(e / n) * lds + (e % n)] += ld<double>(Gm, (int64_t)act[e / n] * t.n_pad + act[e % n]) * inv;
-    }
-    __syncthreads();
-  }
-  for (int e = tid; e < nn * nn; e += nt) {
-    int a = e / nn, b = e % nn;
-    if (a < b) {
-      double v = 0.5 * (G[a * lds + b] + G[b * lds + a]);
-      G[a * lds + b] = v;
-      G[b * lds + a] = v;
-    }
-  }
-  __syncthreads();
-  const double thr_rel = trunc == H2_TRUNC_SV ? eps * eps : eps;
-  const bool refine = trunc != H2_TRUNC_FULL && thr_rel < 5e-5;
-  auto newton_schulz = [&](int ncols) {  // V[:, :ncols] <- V (3 I - V^T V) / 2
-    for (int e = tid; e < ncols * ncols; e += nt) {
-      const int i = e / ncols, j = e % ncols;
-      double a0 = 0.0, a1 = 0.0;
-      int r = 0;
-      for (; r + 1 < nn; r += 2) {
-        a0 = fma(V[r * lds + i], V[r * lds + j], a0);
-        a1 = fma(V[(r + 1) * lds + i], V[(r + 1) * lds + j], a1);
-      }
-      if (r < nn) a0 = fma(V[r * lds + i], V[r * lds + j], a0);
-      T[i * lds + j] = ((i == j) ? 1.5 : 0.0) - 0.5 * (a0 + a1);
-    }
-    __syncthreads();
-    for (int i0 = 0; i0 < nn; i0 += 4) {
-      const int ni = min(4, nn - i0);
-      for (int e = tid; e < ni * ncols; e += nt) {
-        const int i = i0 + e / ncols, j = e % ncols;
-        double a0 = 0.0;
-        for (int k = 0; k < ncols; ++k) a0 = fma(V[i * lds + k], T[k * lds + j], a0);
-        rowbuf[e] = a0;
-      }
-      __syncthreads();
-      for (int e = tid; e < ni * ncols; e += nt) V[(i0 + e / ncols) * lds + e % ncols] = rowbuf[e];
-      __syncthreads();
-    }
-  };
-  if (refine) {
-    // full float64 path: orthonormalise all columns, Rayleigh-Ritz, Jacobi refinement
-    newton_schulz(nn);
-    smem_gemm(G, false, V, false, T, nn, lds);  // T = G V
-    smem_gemm(V, true, T, false, G, nn, lds);   // G <- V^T G V
-    for (int e = tid; e < nn * nn; e += nt) {
-      int a = e / nn, b = e % nn;
-      if (a < b) {
-        double v = 0.5 * (G[a * lds + b] + G[b * lds + a]);
-        G[a * lds + b] = v;
-        G[b * lds + a] = v;
-      }
-    }
-    __syncthreads();
-    jacobi_sweeps<double>(G, V, nn, lds, 8, 1e-24, red, cs, sn, pp, qq);
-    for (int j = tid; j < n; j += nt) lam[j] = G[j * lds + j];
-    __syncthreads();
-  } else {
-    smem_gemm(G, false, V, false, T, nn, lds);  // T = G V
-    for (int j = tid; j < n; j += nt) {
-      double a0 = 0.0, a1 = 0.0;
-      int i = 0;
-      for (; i + 1 < nn; i += 2) {
-        a0 = fma(V[i * lds + j], T[i * lds + j], a0);
-        a1 = fma(V[(i + 1) * lds + j], T[(i + 1) * lds + j], a1);
-      }
-      if (i < nn) a0 = fma(V[i * lds + j], T[i * lds + j], a0);
-      lam[j] = a0 + a1;
-    }
-    __syncthreads();
-  }
-  for (int a = tid; a < n; a += nt) {
-    int pos = 0;
-    for (int b = 0; b < n; ++b)
-      if (lam[b] > lam[a] || (lam[b] == lam[a] && b < a)) ++pos;
-    order[pos] = a;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    int r = 0;
-    if (n > 0) {
-      if (trunc == H2_TRUNC_FULL) {
-        r = n;
-      } else {
-        double l1 = lam[order[0]];
-        if (l1 > 0.0)
-          while (r < n && lam[order[r]] > thr_rel * l1) ++r;
-      }
-    }
-    if (r > t.kcap) {
-      r = t.kcap;
-      atomicAdd(cap_hits, 1ull);
-    }
-    s_rank = r;
-    ranks[t.rank_out] = r;
-  }
-  __syncthreads();
-  const int rank = s_rank;
-  if (!refine) {
-    // gather the kept columns to the front (through T), then one Newton-Schulz step
-    for (int e = tid; e < nn * rank; e += nt) {
-      const int i = e / rank, c = e % rank;
-      T[i * lds + c] = V[i * lds + order[c]];
-    }
-    __syncthreads();
-    for (int e = tid; e < nn * rank; e += nt) {
-      const int i = e / rank, c = e % rank;
-      V[i * lds + c] = T[i * lds + c];
-    }
-    __syncthreads();
-    if (rank > 0) newton_schulz(rank);
-  }
-  double* out = (double*)view(ar, t.out).base;
-  float* out32 = ar.p[AR_X] ? (float*)ar.p[AR_X] + (t.out & kOffMask) : nullptr;
-  for (int e = tid; e < t.n_pad * t.kcap; e += nt) {
-    out[e] = 0.0;
-    if (out32) out32[e] = 0.f;
-  }
-  __syncthreads();
-  for (int c = tid; c < rank; c += nt) {
-    const int col = refine ? order[c] : c;
-    int best = 0;
-    double bv = -1.0;
-    for (int a = 0; a < n; ++a) {
-      double v = fabs(V[a * lds + col]);
-      if (v > bv) { bv = v; best = a; }
-    }
-    double sg = V[best * lds + col] < 0.0 ? -1.0 : 1.0;
-    for (int a = 0; a < n; ++a) {
-      const double v = sg * V[a * lds + col];
-      out[(int64_t)act[a] * t.kcap + c] = v;
-      if (out32) out32[(int64_t)act[a] * t.kcap + c] = (float)v;
-    }
-  }
-}
-
-void launch_eig_split(const EigTask* d_eigs, int64_t first, int64_t count, const ArenaSet& a, int32_t* kr,
-                      int32_t* kc, double eps, int trunc, unsigned long long* cap_hits, int max_npad, void* stream) {
-  Arenas ar = to_dev(a);
-  const int nn = max_npad + (max_npad & 1);
-  const size_t per_warp = (size_t)2 * nn * (nn + 1) * sizeof(float);
-  int wpc = (int)((200 * 1024) / per_warp);
-  if (wpc > 8) wpc = 8;
-  if (wpc < 1) wpc = 1;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(eig_jacobi32_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-    cudaFuncSetAttribute(eig_finish64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(3 * kMixMax * (kMixMax + 1) * sizeof(double)));
-    attr = true;
-  }
-  const unsigned blocks = (unsigned)((count + wpc - 1) / wpc);
-  eig_jacobi32_warp_kernel<<<blocks, 32 * wpc, wpc * per_warp, (cudaStream_t)stream>>>(d_eigs, first, count, ar, kr,
-                                                                                         kc, nn);
-  eig_finish64_kernel<<<(unsigned)count, 256, (size_t)3 * nn * (nn + 1) * sizeof(double), (cudaStream_t)stream>>>(
-      d_eigs, first, ar, kr, kc, eps, trunc, cap_hits);
-}
-
 void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, const ArenaSet& a, int32_t* kr,
                 int32_t* kc, double eps, int trunc, unsigned long long* cap_hits, int max_npad, double* scratch,
                 void* stream) {

@@ -616,10 +616,6 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         e.half = leaf ? 0 : (int16_t)(col ? cC(c) : rC(c));
         e.kcap = (int16_t)(col ? cC(l) : rC(l));
         e.col = (int16_t)col;
-        // mixed product: float32 eigenvectors between the two eigen kernels (S holds floats)
-        // (the Jacobi works on an even dimension: size the slot for n_pad rounded up)
-        const int64_t ne = e.n_pad + (e.n_pad & 1);
-        e.scratch = prm.precision == H2_MIXED_FP32 ? pb.alloc(AR_S, ne * ne) : -1;
         P.eigs.push_back(e);
       }
     pb.eigs(e0, "eig", l);
