@@ -697,19 +697,338 @@ __global__ void __launch_bounds__(256) eig_mixed_kernel(const EigTask* __restric
   }
 }
 
+// ------------------------------------------------------------ mixed eigen kernel, kept columns only
+// The same result as eig_mixed_kernel for truncation thresholds of 5e-5 lambda_1 and
+// above (and the full mode), with the work cut where it does not decide the result:
+//   (1) float32 round-robin Jacobi on G padded with zero rows and columns to a
+//       multiple of four (pad indices are never rotated).  One step rotates rows and
+//       columns together: a thread takes the 2 x 2 block (pair k, pair l), k <= l, of
+//       A, forms M_k X M_l^T and writes the block and its mirror image; eigenvectors
+//       are the ROWS of Vt, so their update is a float4 row rotation.  Rotations with
+//       |a_pq| <= 2^-24 sqrt(|a_pp a_qq|) are skipped (below float32 resolution of
+//       their 2 x 2 problem; together they keep off(A)^2 far below the 1e-10 stop);
+//   (2) a_jj is v_j^T G v_j to float32 accuracy: the columns with a_jj above a
+//       quarter of the threshold are the only ones whose quotient can pass it, and
+//       only their float64 Rayleigh quotients v^T G v / v^T v are formed; these
+//       decide the rank (sorted decreasing, ties by index);
+//   (3) the kept columns go to float64 and one Newton-Schulz step on those columns,
+//       V <- V (3 I - V^T V) / 2, makes them orthonormal to ~1e-14.
+// Float64 work: n^2 per candidate plus 2 n r^2, against 3 n^3 in eig_mixed_kernel.
+// Shared memory: G (float64, nn x (nn+1)), A (float32, nn x (nn+1)), Vt (float32,
+// nn x (nn+4)) = nn (16 nn + 28) bytes; after (2) G's space holds the kept columns
+// (n x (r+1) float64) and A/Vt's the r x (r+1) Newton-Schulz matrix.
+constexpr int kKeptRows = 4;
+
+__host__ __device__ inline int round4(int n) { return (n + 3) & ~3; }
+
+// byte offsets of A and Vt and the total, shared by the kernel and its launch
+__host__ __device__ inline size_t eig_kept_off_a(int nn) { return (size_t)nn * (nn + 1) * sizeof(double); }
+__host__ __device__ inline size_t eig_kept_off_vt(int nn) {
+  return eig_kept_off_a(nn) + (size_t)nn * (nn + 1) * sizeof(float);
+}
+__host__ __device__ inline size_t eig_kept_smem(int nn) {
+  return eig_kept_off_vt(nn) + (size_t)nn * (nn + 4) * sizeof(float);
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(256) eig_mixed_kept_kernel(const EigTask* __restrict__ tasks, int64_t first,
+                                                             Arenas ar, int32_t* kr, int32_t* kc, double eps,
+                                                             int trunc, unsigned long long* cap_hits) {
+  extern __shared__ __align__(16) unsigned char esm[];
+  __shared__ int act[kMixMax + 4];
+  __shared__ double red[8];
+  __shared__ float cs[kMixMax / 2], sn[kMixMax / 2];
+  __shared__ int pp[kMixMax / 2], qq[kMixMax / 2];
+  __shared__ int cand[kMixMax], order[kMixMax];
+  __shared__ double rq[kMixMax], rqs[kMixMax];
+  __shared__ float lam32[kMixMax];
+  __shared__ double rowbuf[kKeptRows * kMixMax];
+  __shared__ int s_n, s_nc, s_rank;
+  const EigTask t = tasks[first + blockIdx.x];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, w = tid >> 5, nw = nt >> 5;
+  int32_t* ranks = t.col ? kc : kr;
+  if (tid == 0) {
+    int n = 0;
+    if (t.child1 < 0) {
+      for (int a = 0; a < t.nleaf; ++a) act[n++] = a;
+    } else {
+      const int k1 = ranks[t.child1], k2 = ranks[t.child2];
+      for (int a = 0; a < k1; ++a) act[n++] = a;
+      for (int a = 0; a < k2; ++a) act[n++] = t.half + a;
+    }
+    s_n = n;
+  }
+  __syncthreads();
+  const int n = s_n, nn = round4(n), np = nn / 2, la = nn + 1, lv = nn + 4;
+  double* G = (double*)esm;                            // row stride la
+  float* A = (float*)(esm + eig_kept_off_a(nn));       // row stride la
+  float* Vt = (float*)(esm + eig_kept_off_vt(nn));     // row stride lv; 16-byte aligned rows
+  for (int e = tid; e < nn * la; e += nt) G[e] = 0.0;
+  __syncthreads();
+  for (int m = 0; m < 3; ++m) {
+    if (t.g[m] < 0) continue;
+    const View Gm = view(ar, t.g[m]);
+    double loc = 0.0;
+    for (int e = tid; e < n * n; e += nt) {
+      const double v = ld<double>(Gm, (int64_t)act[e / n] * t.n_pad + act[e % n]);
+      loc += v * v;
+    }
+    const double nrm2 = block_sum(loc, red);
+    if (nrm2 > 0.0) {
+      const double inv = 1.0 / sqrt(nrm2);
+      for (int e = tid; e < n * n; e += nt)
+        G[(e / n) * la + (e % n)] += ld<double>(Gm, (int64_t)act[e / n] * t.n_pad + act[e % n]) * inv;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < nn * nn; e += nt) {
+    const int a = e / nn, b = e % nn;
+    if (a < b) {
+      const double v = 0.5 * (G[a * la + b] + G[b * la + a]);
+      G[a * la + b] = v;
+      G[b * la + a] = v;
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < nn * la; e += nt) A[e] = (float)G[e];
+  for (int e = tid; e < nn * lv; e += nt) Vt[e] = (e / lv == e % lv) ? 1.f : 0.f;
+  __syncthreads();
+  // (1) float32 Jacobi, stop when off(A)^2 <= 1e-10 |A|^2 (as eig_mixed_kernel)
+  const int half = np / 2, nq = nn / 4;
+  for (int sweep = 0; sweep < 12 && n > 1; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int e = tid; e < nn * nn; e += nt) {
+      const int i = e / nn, j = e - i * nn;
+      const double v = (double)A[i * la + j] * (double)A[i * la + j];
+      tot += v;
+      if (i != j) off += v;
+    }
+    off = block_sum(off, red);
+    tot = block_sum(tot, red);
+    if (!(off > 1e-10 * tot)) break;
+    for (int step = 0; step < nn - 1; ++step) {
+      if (tid < np) {
+        const int pa = (tid == 0) ? 0 : ((tid - 1 + step) % (nn - 1)) + 1;
+        const int pb = ((nn - 2 - tid + step) % (nn - 1)) + 1;
+        const int p = min(pa, pb), q = max(pa, pb);
+        const float apq = A[p * la + q], app = A[p * la + p], aqq = A[q * la + q];
+        float c = 1.f, s = 0.f;
+        if (apq != 0.f && fabsf(apq) > 5.9604645e-8f * sqrtf(fabsf(app) * fabsf(aqq))) {
+          const float tau = (aqq - app) / (2.f * apq);
+          const float tt = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+          c = 1.f / sqrtf(1.f + tt * tt);
+          s = tt * c;
+        }
+        pp[tid] = p;
+        qq[tid] = q;
+        cs[tid] = c;
+        sn[tid] = s;
+      }
+      __syncthreads();
+      // A <- M A M^T by 2 x 2 blocks; the triangle k <= l is folded into half x (np + 1)
+      for (int e = tid; e < half * (np + 1); e += nt) {
+        const int r = e / (np + 1), cc = e - r * (np + 1);
+        int k, l;
+        if (cc < np - r) {
+          k = r;
+          l = r + cc;
+        } else {
+          k = np - 1 - r;
+          l = k + cc - (np - r);
+        }
+        const float sk = sn[k], sl = sn[l];
+        if (sk == 0.f && sl == 0.f) continue;
+        const float ck = cs[k], cl = cs[l];
+        const int pk = pp[k], qk = qq[k], pl = pp[l], ql = qq[l];
+        const float x = A[pk * la + pl], y = A[pk * la + ql], z = A[qk * la + pl], u = A[qk * la + ql];
+        const float r00 = ck * x - sk * z, r01 = ck * y - sk * u;  // rows: M_k X
+        const float r10 = sk * x + ck * z, r11 = sk * y + ck * u;
+        const float b00 = cl * r00 - sl * r01, b10 = cl * r10 - sl * r11;  // columns: (M_k X) M_l^T
+        float b01 = sl * r00 + cl * r01, b11 = sl * r10 + cl * r11;
+        if (k == l) {
+          A[pk * la + pk] = b00;
+          A[qk * la + qk] = b11;
+          A[pk * la + qk] = 0.f;
+          A[qk * la + pk] = 0.f;
+        } else {
+          A[pk * la + pl] = b00;
+          A[pk * la + ql] = b01;
+          A[qk * la + pl] = b10;
+          A[qk * la + ql] = b11;
+          A[pl * la + pk] = b00;
+          A[ql * la + pk] = b01;
+          A[pl * la + qk] = b10;
+          A[ql * la + qk] = b11;
+        }
+      }
+      // Vt <- M Vt (rows p, q of each pair)
+      for (int e = tid; e < np * nq; e += nt) {
+        const int k = e / nq, j = (e - k * nq) * 4;
+        const float s = sn[k];
+        if (s == 0.f) continue;
+        const float c = cs[k];
+        float4* rp = reinterpret_cast<float4*>(Vt + pp[k] * lv + j);
+        float4* rr = reinterpret_cast<float4*>(Vt + qq[k] * lv + j);
+        const float4 x = *rp, y = *rr;
+        *rp = make_float4(c * x.x - s * y.x, c * x.y - s * y.y, c * x.z - s * y.z, c * x.w - s * y.w);
+        *rr = make_float4(s * x.x + c * y.x, s * x.y + c * y.y, s * x.z + c * y.z, s * x.w + c * y.w);
+      }
+      __syncthreads();
+    }
+  }
+  for (int j = tid; j < n; j += nt) lam32[j] = A[j * la + j];
+  __syncthreads();
+  // (2) candidates and their float64 Rayleigh quotients
+  const double thr = trunc == H2_TRUNC_SV ? eps * eps : eps;
+  if (tid == 0) {
+    float mx = 0.f;
+    for (int j = 0; j < n; ++j) mx = fmaxf(mx, lam32[j]);
+    int nc = 0;
+    for (int j = 0; j < n; ++j)
+      if (trunc == H2_TRUNC_FULL || (mx > 0.f && lam32[j] > 0.25f * (float)thr * mx)) cand[nc++] = j;
+    s_nc = nc;
+  }
+  __syncthreads();
+  const int nc = s_nc;
+  for (int ci = w; ci < nc; ci += nw) {
+    const float* v = Vt + cand[ci] * lv;
+    double num = 0.0, den = 0.0;
+    for (int a = lane; a < n; a += 32) {
+      const double* g = G + a * la;
+      double a0 = 0.0, a1 = 0.0;
+      int b = 0;
+      for (; b + 1 < n; b += 2) {
+        a0 = fma(g[b], (double)v[b], a0);
+        a1 = fma(g[b + 1], (double)v[b + 1], a1);
+      }
+      if (b < n) a0 = fma(g[b], (double)v[b], a0);
+      const double va = (double)v[a];
+      num = fma(va, a0 + a1, num);
+      den = fma(va, va, den);
+    }
+    num = warp_sum_d(num);
+    den = warp_sum_d(den);
+    if (lane == 0) rq[ci] = den > 0.0 ? num / den : 0.0;
+  }
+  __syncthreads();
+  for (int a = tid; a < nc; a += nt) {
+    int pos = 0;
+    for (int b = 0; b < nc; ++b)
+      if (rq[b] > rq[a] || (rq[b] == rq[a] && b < a)) ++pos;
+    order[pos] = cand[a];
+    rqs[pos] = rq[a];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int r = 0;
+    if (trunc == H2_TRUNC_FULL) {
+      r = nc;
+    } else if (nc > 0 && rqs[0] > 0.0) {
+      const double l1 = rqs[0];
+      while (r < nc && rqs[r] > thr * l1) ++r;
+    }
+    if (r > t.kcap) {
+      r = t.kcap;
+      atomicAdd(cap_hits, 1ull);
+    }
+    s_rank = r;
+    ranks[t.rank_out] = r;
+  }
+  __syncthreads();
+  // (3) kept columns in float64 (G's space), one Newton-Schulz step on them
+  const int rank = s_rank, lk = rank + 1;
+  double* Vk = G;
+  for (int e = tid; e < n * rank; e += nt) {
+    const int a = e / rank, c = e - a * rank;
+    Vk[a * lk + c] = (double)Vt[order[c] * lv + a];
+  }
+  __syncthreads();
+  if (rank > 0) {
+    double* T = reinterpret_cast<double*>(A);
+    const int lt = rank + 1;
+    for (int e = tid; e < rank * rank; e += nt) {
+      const int i = e / rank, j = e - i * rank;
+      double a0 = 0.0, a1 = 0.0;
+      int a = 0;
+      for (; a + 1 < n; a += 2) {
+        a0 = fma(Vk[a * lk + i], Vk[a * lk + j], a0);
+        a1 = fma(Vk[(a + 1) * lk + i], Vk[(a + 1) * lk + j], a1);
+      }
+      if (a < n) a0 = fma(Vk[a * lk + i], Vk[a * lk + j], a0);
+      T[i * lt + j] = (i == j ? 1.5 : 0.0) - 0.5 * (a0 + a1);
+    }
+    __syncthreads();
+    for (int r0 = 0; r0 < n; r0 += kKeptRows) {
+      const int na = min(kKeptRows, n - r0);
+      for (int e = tid; e < na * rank; e += nt) {
+        const int a = r0 + e / rank, j = e % rank;
+        double s0 = 0.0, s1 = 0.0;
+        int i = 0;
+        for (; i + 1 < rank; i += 2) {
+          s0 = fma(Vk[a * lk + i], T[i * lt + j], s0);
+          s1 = fma(Vk[a * lk + i + 1], T[(i + 1) * lt + j], s1);
+        }
+        if (i < rank) s0 = fma(Vk[a * lk + i], T[i * lt + j], s0);
+        rowbuf[e] = s0 + s1;
+      }
+      __syncthreads();
+      for (int e = tid; e < na * rank; e += nt) Vk[(r0 + e / rank) * lk + e % rank] = rowbuf[e];
+      __syncthreads();
+    }
+  }
+  double* out = (double*)view(ar, t.out).base;  // the new bases are float64 (arena C)
+  float* out32 = ar.p[AR_X] ? (float*)ar.p[AR_X] + (t.out & kOffMask) : nullptr;
+  for (int e = tid; e < t.n_pad * t.kcap; e += nt) {
+    out[e] = 0.0;
+    if (out32) out32[e] = 0.f;
+  }
+  __syncthreads();
+  // sign: the entry of largest magnitude (first such) is positive
+  for (int c = tid; c < rank; c += nt) {
+    int best = 0;
+    double bv = -1.0;
+    for (int a = 0; a < n; ++a) {
+      const double v = fabs(Vk[a * lk + c]);
+      if (v > bv) {
+        bv = v;
+        best = a;
+      }
+    }
+    const double sg = Vk[best * lk + c] < 0.0 ? -1.0 : 1.0;
+    for (int a = 0; a < n; ++a) {
+      const double v = sg * Vk[a * lk + c];
+      out[(int64_t)act[a] * t.kcap + c] = v;
+      if (out32) out32[(int64_t)act[a] * t.kcap + c] = (float)v;
+    }
+  }
+}
+
 void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const ArenaSet& a, int32_t* kr,
                       int32_t* kc, double eps, int trunc, unsigned long long* cap_hits, int max_npad, void* stream) {
   Arenas ar = to_dev(a);
-  int nn = max_npad + (max_npad & 1);
-  size_t smem = (size_t)3 * nn * (nn + 1) * sizeof(double);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(eig_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(3 * kMixMax * (kMixMax + 1) * sizeof(double)));
+    cudaFuncSetAttribute(eig_mixed_kept_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)eig_kept_smem(kMixMax));
     attr = true;
   }
-  eig_mixed_kernel<<<(unsigned)count, 256, smem, (cudaStream_t)stream>>>(d_eigs, first, ar, kr, kc, eps, trunc,
-                                                                         cap_hits);
+  const double thr = trunc == H2_TRUNC_SV ? eps * eps : eps;
+  if (trunc != H2_TRUNC_FULL && thr < 5e-5) {
+    // thresholds below float32 eigenvector resolution: float64 Rayleigh-Ritz refinement
+    const int nn = max_npad + (max_npad & 1);
+    const size_t smem = (size_t)3 * nn * (nn + 1) * sizeof(double);
+    eig_mixed_kernel<<<(unsigned)count, 256, smem, (cudaStream_t)stream>>>(d_eigs, first, ar, kr, kc, eps, trunc,
+                                                                           cap_hits);
+  } else {
+    eig_mixed_kept_kernel<<<(unsigned)count, 256, eig_kept_smem(round4(max_npad)), (cudaStream_t)stream>>>(
+        d_eigs, first, ar, kr, kc, eps, trunc, cap_hits);
+  }
 }
 
 void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, const ArenaSet& a, int32_t* kr,
