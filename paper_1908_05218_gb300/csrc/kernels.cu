@@ -737,7 +737,8 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 __global__ void __launch_bounds__(256) eig_mixed_kept_kernel(const EigTask* __restrict__ tasks, int64_t first,
                                                              Arenas ar, int32_t* kr, int32_t* kc, double eps,
-                                                             int trunc, unsigned long long* cap_hits) {
+                                                             int trunc, unsigned long long* cap_hits, int nn_lo,
+                                                             int nn_hi) {
   extern __shared__ __align__(16) unsigned char esm[];
   __shared__ int act[kMixMax + 4];
   __shared__ double red[8];
@@ -764,6 +765,9 @@ __global__ void __launch_bounds__(256) eig_mixed_kept_kernel(const EigTask* __re
   }
   __syncthreads();
   const int n = s_n, nn = round4(n), np = nn / 2, la = nn + 1, lv = nn + 4;
+  // one launch per size tier (nn_lo, nn_hi], shared memory sized for nn_hi: a task
+  // whose actual size is outside the tier is done by another launch
+  if (nn <= nn_lo || nn > nn_hi) return;
   double* G = (double*)esm;                            // row stride la
   float* A = (float*)(esm + eig_kept_off_a(nn));       // row stride la
   float* Vt = (float*)(esm + eig_kept_off_vt(nn));     // row stride lv; 16-byte aligned rows
@@ -800,15 +804,16 @@ __global__ void __launch_bounds__(256) eig_mixed_kept_kernel(const EigTask* __re
   // (1) float32 Jacobi, stop when off(A)^2 <= 1e-10 |A|^2 (as eig_mixed_kernel)
   const int half = np / 2, nq = nn / 4;
   for (int sweep = 0; sweep < 12 && n > 1; ++sweep) {
-    double off = 0.0, tot = 0.0;
+    // (sums of squares in float32: they only decide a stop at a 1e-10 ratio)
+    float offf = 0.f, totf = 0.f;
     for (int e = tid; e < nn * nn; e += nt) {
       const int i = e / nn, j = e - i * nn;
-      const double v = (double)A[i * la + j] * (double)A[i * la + j];
-      tot += v;
-      if (i != j) off += v;
+      const float v = A[i * la + j] * A[i * la + j];
+      totf += v;
+      if (i != j) offf += v;
     }
-    off = block_sum(off, red);
-    tot = block_sum(tot, red);
+    const double off = block_sum((double)offf, red);
+    const double tot = block_sum((double)totf, red);
     if (!(off > 1e-10 * tot)) break;
     for (int step = 0; step < nn - 1; ++step) {
       if (tid < np) {
@@ -884,17 +889,30 @@ __global__ void __launch_bounds__(256) eig_mixed_kept_kernel(const EigTask* __re
   __syncthreads();
   // (2) candidates and their float64 Rayleigh quotients
   const double thr = trunc == H2_TRUNC_SV ? eps * eps : eps;
+  // a_jj differs from the float64 quotient of v_j by ~1e-6 lambda_1 (float32 rounding
+  // of the accumulated rotations); the quotient is formed in float64 only where that
+  // can change the result: the top cluster (lambda_1) and the columns within
+  // 2e-5 lambda_1 of the threshold; elsewhere a_jj stands in for it
+  __shared__ int s_nd;
+  __shared__ int dq[kMixMax];
   if (tid == 0) {
     float mx = 0.f;
     for (int j = 0; j < n; ++j) mx = fmaxf(mx, lam32[j]);
-    int nc = 0;
+    const float del = 1e-5f * mx, tau = (float)thr * mx;
+    int nc = 0, nd = 0;
     for (int j = 0; j < n; ++j)
-      if (trunc == H2_TRUNC_FULL || (mx > 0.f && lam32[j] > 0.25f * (float)thr * mx)) cand[nc++] = j;
+      if (trunc == H2_TRUNC_FULL || (mx > 0.f && lam32[j] > 0.25f * tau)) {
+        rq[nc] = (double)lam32[j];
+        if (trunc != H2_TRUNC_FULL && (lam32[j] >= mx - del || fabsf(lam32[j] - tau) <= 2.f * del)) dq[nd++] = nc;
+        cand[nc++] = j;
+      }
     s_nc = nc;
+    s_nd = nd;
   }
   __syncthreads();
-  const int nc = s_nc;
-  for (int ci = w; ci < nc; ci += nw) {
+  const int nc = s_nc, nd = s_nd;
+  for (int di = w; di < nd; di += nw) {
+    const int ci = dq[di];
     const float* v = Vt + cand[ci] * lv;
     double num = 0.0, den = 0.0;
     for (int a = lane; a < n; a += 32) {
@@ -1026,8 +1044,24 @@ void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const
     eig_mixed_kernel<<<(unsigned)count, 256, smem, (cudaStream_t)stream>>>(d_eigs, first, ar, kr, kc, eps, trunc,
                                                                            cap_hits);
   } else {
-    eig_mixed_kept_kernel<<<(unsigned)count, 256, eig_kept_smem(round4(max_npad)), (cudaStream_t)stream>>>(
-        d_eigs, first, ar, kr, kc, eps, trunc, cap_hits);
+    // the level's padded size comes from the rank caps; the actual sizes (children's
+    // ranks) are only known on the device and are mostly far smaller, so tasks are
+    // launched in size tiers, each with the shared memory of its largest size (more
+    // CTAs per SM for the small ones)
+    // (tiers run one after the other: a level of few tasks takes one launch)
+    const int top = round4(max_npad);
+    int lo = -1;
+    const bool tiers = count >= 4 * 152;
+    for (int hi : {48, 64, kMixMax}) {
+      if (!tiers) hi = top;
+      const int h = hi < top ? hi : top;
+      // (128 threads are enough for nn <= 48: a step has <= 300 block and row tasks)
+      if (h > lo)
+        eig_mixed_kept_kernel<<<(unsigned)count, h <= 48 ? 128 : 256, eig_kept_smem(h), (cudaStream_t)stream>>>(
+            d_eigs, first, ar, kr, kc, eps, trunc, cap_hits, lo, h);
+      lo = h;
+      if (h == top) break;
+    }
   }
 }
 
