@@ -224,7 +224,8 @@ void sync_ranks_to_host(Mat& m) {
   m.ranks_on_host = true;
 }
 
-// packed host layout -> padded device arena (caps = largest rank per level)
+// packed host layout -> padded device arena (caps = largest rank per level, rounded
+// up to a multiple of four)
 void unpack_to_device(const Packed& p, Mat& m) {
   const Structure& st = *m.st;
   const int L = st.L, LS = st.LS, nn = st.nnodes();
@@ -249,6 +250,10 @@ void unpack_to_device(const Packed& p, Mat& m) {
       m.Kr[l] = std::max(m.Kr[l], kr);
       m.Kc[l] = std::max(m.Kc[l], kc);
     }
+  for (int l = 0; l <= L; ++l) {  // storage caps: multiples of four
+    m.Kr[l] = cap_round(m.Kr[l]);
+    m.Kc[l] = cap_round(m.Kc[l]);
+  }
   alloc_mat(m);
   std::vector<double> h(m.arena_elems, 0.0);
   size_t pos = 0;
@@ -379,13 +384,21 @@ void pack_from_device(Mat& m, Packed& p) {
 // Host-side check that every access of a plan stays inside its arena: run before a
 // plan's first upload so that an indexing error is reported instead of executed.
 void validate_plan(const Plan& P, const int64_t sizes[kArenas]) {
+  // live allocations of the work regions (start -> size), replayed in program order
+  std::map<int64_t, int64_t> live[kArenas];
+  size_t ev = 0;
+  auto is_work = [](int64_t a) { return a == AR_P || a == AR_G0 || a == AR_G1 || a == AR_S; };
   auto check = [&](int64_t tagged, int64_t extent, const char* what) {
     if (extent <= 0) return;
     int64_t a = arena_of(tagged), off = offset_of(tagged);
     if (tagged < 0 || off + extent > sizes[a])
       throw Error(H2_EINTERNAL, std::string("plan access out of bounds: ") + what);
+    if (!is_work(a)) return;
+    auto it = live[a].upper_bound(off);
+    if (it == live[a].begin() || std::prev(it)->first + std::prev(it)->second < off + extent)
+      throw Error(H2_EINTERNAL, std::string("plan access outside its allocation: ") + what);
   };
-  for (const Seg& s : P.segs) {
+  auto check_seg = [&](const Seg& s) {
     bool ta = s.flags & SF_TA, tb = s.flags & SF_TB;
     check(s.out, (int64_t)(s.m - 1) * s.ldc + s.n, "segment output");
     if (s.ldc < s.n) throw Error(H2_EINTERNAL, "segment ldc < n");
@@ -404,16 +417,35 @@ void validate_plan(const Plan& P, const int64_t sizes[kArenas]) {
       check(it.a, ta ? (int64_t)(kp - 1) * lda + s.m : (int64_t)(s.m - 1) * lda + kp, "segment A");
       check(it.b, tb ? (int64_t)(s.n - 1) * ldb + kp : (int64_t)(kp - 1) * ldb + s.n, "segment B");
     }
-  }
-  for (const EigTask& e : P.eigs) {
+  };
+  auto check_eig = [&](const EigTask& e) {
     for (int m = 0; m < 3; ++m)
       if (e.g[m] >= 0) check(e.g[m], (int64_t)e.n_pad * e.n_pad, "eig Gram");
     check(e.out, (int64_t)e.n_pad * e.kcap, "eig output");
+    if (e.klim < 0 || e.klim > e.kcap) throw Error(H2_EINTERNAL, "eig rank limit above its stride");
     if (e.child1 < 0 && e.nleaf > e.n_pad) throw Error(H2_EINTERNAL, "eig leaf size above n_pad");
     if (e.child1 >= 0 && 2 * e.half > e.n_pad) throw Error(H2_EINTERNAL, "eig half above n_pad");
+  };
+  size_t nseg = 0, neig = 0;
+  for (size_t li = 0; li < P.launches.size(); ++li) {
+    for (; ev < P.aev.size() && P.aev[ev].launch <= (int32_t)li; ++ev) {
+      const Plan::AllocEv& x = P.aev[ev];
+      if (x.reset) live[x.arena].clear();
+      else live[x.arena][x.start] = x.size;
+    }
+    const Launch& L = P.launches[li];
+    if (L.kind == Launch::GEMM) {
+      for (int64_t i = L.first; i < L.first + L.count; ++i) check_seg(P.segs[i]);
+      nseg += L.count;
+    } else if (L.kind == Launch::EIG) {
+      for (int64_t i = L.first; i < L.first + L.count; ++i) check_eig(P.eigs[i]);
+      neig += L.count;
+    } else if (L.kind == Launch::MEMSET) {
+      const int64_t a = arena_of(L.off);
+      if (L.off < 0 || offset_of(L.off) + L.elems > sizes[a]) throw Error(H2_EINTERNAL, "plan memset out of bounds");
+    }
   }
-  for (const Launch& L : P.launches)
-    if (L.kind == Launch::MEMSET) check(L.off, L.elems, "memset");
+  if (nseg != P.segs.size() || neig != P.eigs.size()) throw Error(H2_EINTERNAL, "plan work outside its launches");
 }
 
 void upload_plan(Plan& P, size_t region_esize) {

@@ -102,6 +102,8 @@ void sync_ranks_to_host(Mat& m);
 enum Arena : int64_t { AR_A = 0, AR_B = 1, AR_C = 2, AR_P = 3, AR_G0 = 4, AR_G1 = 5, AR_S = 6, AR_X = 7 };
 constexpr int kArenas = 8;
 constexpr int kTagShift = 60;
+// storage caps are multiples of four (16-byte rows and offsets for float32 copies)
+inline int cap_round(int k) { return (k + 3) & ~3; }
 constexpr int64_t kOffMask = (int64_t(1) << kTagShift) - 1;
 inline int64_t tag(Arena a, int64_t off) { return (a << kTagShift) | off; }
 inline int arena_of(int64_t t) { return (int)((t >> kTagShift) & 7); }
@@ -142,7 +144,9 @@ struct EigTask {
   int32_t rank_out;  // node id whose rank is written
   int32_t child1, child2;  // node ids of the children (ranks in the same rank array), -1: leaf
   int32_t nleaf;     // leaf: cluster size; active rows [0, nleaf)
-  int16_t n_pad, half, kcap, col;  // Gram dim, child offset, max rank, 1 = column basis
+  int16_t n_pad, half, kcap, col;  // Gram dim, child offset, output row stride, 1 = column basis
+  int16_t klim;                     // largest rank kept (the rank cap; <= kcap)
+  int16_t pad2[3];
 };
 
 struct Launch {
@@ -170,6 +174,15 @@ struct Plan {
   double* d_scratch = nullptr;  // eigen work space for Gram matrices above 112
   int64_t flops = 0;     // counted 2mnk over GEMM segments (padded dims)
   std::vector<int> ckr, ckc;  // caps of the product
+  // allocations and resets of the work regions in program order (launch = index of
+  // the first launch group emitted after the event); validate_plan replays them to
+  // check that every access stays inside one live allocation
+  struct AllocEv {
+    int32_t launch;
+    int8_t arena, reset;
+    int64_t start, size;
+  };
+  std::vector<AllocEv> aev;
 };
 
 struct MmpParams {

@@ -54,6 +54,7 @@ __device__ __forceinline__ int bound(const Arenas& a, int32_t ref, int padded) {
 }
 
 // ------------------------------------------------------------ segmented GEMM
+// (float64 products; the float32 ones take seg_gemm32_kernel below)
 // One CTA (64 threads) per segment (blockIdx.x) and 32-column slice (blockIdx.y);
 // the CTA walks 32 x 32 output tiles; thread (tx, ty) owns the contiguous 4 x 4
 // block rows 4 ty.., cols 4 tx.. and reads it from shared memory with vector
@@ -222,6 +223,266 @@ __global__ void __launch_bounds__(GNT, 12) seg_gemm_kernel(const Seg* __restrict
   if (ar.flops && tid == 0 && work) atomicAdd(ar.flops, work);
 }
 
+// ------------------------------------------------------------ segmented GEMM, float32
+// The float32 products of the mixed-precision product.  Same segments, tiles and
+// thread layout as seg_gemm_kernel, with the operand traffic cut to what the tile
+// needs:
+//   * each warp holds the metadata of 32 items at a time, one item per lane (its
+//     operand pointers, leading dims and k bound, the rank read once), and the fill
+//     loop takes an item's fields by shuffle: no dependent global loads per item;
+//   * A is staged in the layout it has in memory: row-major (m x k) as rows of k,
+//     transposed (k x m) as rows of m; B (k x n) as rows of n; each row is copied in
+//     16-byte pieces when the item's pointer and leading dim allow it (else element by
+//     element), so a 32 x 32 slice takes four copies per thread and operand;
+//   * items are packed along k in steps of four; k from an item's bound up to the
+//     next multiple of four is zero in both operands (cp.async zero-fills the tail
+//     of a piece, whole padded rows are written as zeros).
+constexpr int LDK = GK + 4;  // row stride of a row-major A slice (16-byte rows)
+constexpr int kSliceA = (TILE * LDK > GK * GPAD) ? TILE * LDK : GK * GPAD;
+
+__device__ __forceinline__ void cp_async16(float* dst, const float* src, int bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(bytes));
+}
+
+template <bool AMK>
+__device__ __forceinline__ void slice_fma(const float* __restrict__ a_s, const float* __restrict__ b_s, int kf,
+                                          int tx, int ty, float acc[4][4]) {
+  for (int kk = 0; kk < kf; kk += 4) {
+    float a[4][4], b[4][4];  // a[i][q]: row 4 ty + i, k kk + q;  b[q][j]: k kk + q, col 4 tx + j
+    if (AMK) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float4 v = *reinterpret_cast<const float4*>(&a_s[(4 * ty + i) * LDK + kk]);
+        a[i][0] = v.x; a[i][1] = v.y; a[i][2] = v.z; a[i][3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 v = *reinterpret_cast<const float4*>(&a_s[(kk + q) * GPAD + 4 * ty]);
+        a[0][q] = v.x; a[1][q] = v.y; a[2][q] = v.z; a[3][q] = v.w;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 v = *reinterpret_cast<const float4*>(&b_s[(kk + q) * GPAD + 4 * tx]);
+      b[q][0] = v.x; b[q][1] = v.y; b[q][2] = v.z; b[q][3] = v.w;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i][q], b[q][j], acc[i][j]);
+  }
+}
+
+__global__ void __launch_bounds__(GNT, 12) seg_gemm32_kernel(const Seg* __restrict__ segs,
+                                                             const Item* __restrict__ items, int64_t first,
+                                                             Arenas ar) {
+  __shared__ __align__(16) float sA[2][kSliceA];
+  __shared__ __align__(16) float sB[2][GK * GPAD];
+  const Seg s = segs[first + blockIdx.x];
+  const int tid = threadIdx.x, lane = tid & 31, tx = tid & 7, ty = tid >> 3;
+  const bool ta = s.flags & SF_TA, tb = s.flags & SF_TB, accum = s.flags & SF_ACC;
+  const int M = bound(ar, s.mref, s.m), N = bound(ar, s.nref, s.n);
+  const View out = view(ar, s.out);
+  const Item* it = items + s.first;
+  unsigned long long work = 0;
+  if (s.flags & SF_SUM) {
+    for (int n0 = blockIdx.y * TILE; n0 < N; n0 += gridDim.y * TILE) {
+      const int nc = min(TILE, N - n0);
+      for (int m0 = 0; m0 < M; m0 += TILE) {
+        const int mc = min(TILE, M - m0);
+        float acc[4][4] = {};
+        for (int q = 0; q < s.count; ++q) {
+          const float* A = ptr_of<float>(ar, it[q].a);
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int r = 4 * ty + i, c = 4 * tx + j;
+              if (r < mc && c < nc) acc[i][j] += A[(int64_t)(m0 + r) * s.lda + n0 + c];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int r = 4 * ty + i, c = 4 * tx + j;
+            if (r < mc && c < nc) st<float>(out, (int64_t)(m0 + r) * s.ldc + n0 + c, acc[i][j], accum);
+          }
+      }
+    }
+    return;
+  }
+  for (int n0 = blockIdx.y * TILE; n0 < N; n0 += gridDim.y * TILE) {
+    const int nc = min(TILE, N - n0);
+    for (int m0 = 0; m0 < M; m0 += TILE) {
+      const int mc = min(TILE, M - m0);
+      // the tile's live 4 x 4 blocks go to threads 0 .. nthr-1 (row-major), so a warp
+      // whose threads all lie beyond them skips the arithmetic (an m x n tile of at
+      // most 32 live blocks, e.g. 20 x 24, takes one warp); idle threads read block 0
+      const int ncq = (nc + 3) >> 2, nthr = ((mc + 3) >> 2) * ncq;
+      const bool mine = tid < nthr;
+      const int qy = mine ? tid / ncq : 0, qx = mine ? tid - qy * ncq : 0;
+      const bool live = (tid & ~31) < nthr;
+      float acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+      // this lane's item of the current group of 32
+      const float* pa = nullptr;
+      const float* pb = nullptr;
+      int la_ = 0, lb_ = 0, kb = 0, va = 0, vb = 0;
+      int base = -32;
+      auto stage = [&](int b0) {
+        base = b0;
+        const int qi = b0 + lane;
+        if (qi < s.count) {
+          const Item iq = it[qi];
+          pa = ptr_of<float>(ar, iq.a);
+          pb = ptr_of<float>(ar, iq.b);
+          la_ = iq.lda ? iq.lda : s.lda;
+          lb_ = iq.ldb ? iq.ldb : s.ldb;
+          kb = bound(ar, iq.kref, iq.kpad ? iq.kpad : s.k);
+          va = ((((uintptr_t)pa) & 15) == 0 && (la_ & 3) == 0);
+          vb = ((((uintptr_t)pb) & 15) == 0 && (lb_ & 3) == 0);
+        } else {
+          kb = 0;
+        }
+      };
+      int q = 0, koff = 0;
+      // fields of item q (uniform across the CTA)
+      const float *A = nullptr, *B = nullptr;
+      int lda = 0, ldb = 0, K = 0, K4 = 0;
+      bool vecA = false, vecB = false;
+      auto fetch = [&]() {
+        if (q >= base + 32) stage(q & ~31);
+        const int src = q - base;
+        A = (const float*)__shfl_sync(0xffffffffu, (unsigned long long)pa, src);
+        B = (const float*)__shfl_sync(0xffffffffu, (unsigned long long)pb, src);
+        lda = __shfl_sync(0xffffffffu, la_, src);
+        ldb = __shfl_sync(0xffffffffu, lb_, src);
+        K = __shfl_sync(0xffffffffu, kb, src);
+        vecA = __shfl_sync(0xffffffffu, va, src);
+        vecB = __shfl_sync(0xffffffffu, vb, src);
+        K4 = (K + 3) & ~3;
+      };
+      if (s.count > 0) fetch();
+      auto fill = [&](int buf) -> int {
+        int kfill = 0;
+        float* a_s = sA[buf];
+        float* b_s = sB[buf];
+        while (q < s.count && kfill < GK) {
+          if (K == 0) {
+            ++q;
+            if (q < s.count) fetch();
+            continue;
+          }
+          const int take = min(K4 - koff, GK - kfill);  // a multiple of four
+          if (!ta) {  // A row-major: rows of k into a_s[r * LDK + k]
+            if (vecA) {
+              for (int e = tid; e < TILE * (GK / 4); e += GNT) {
+                const int r = e >> 3, c4 = (e & 7) * 4;
+                if (r < mc && c4 < take) {
+                  const int kr = K - (koff + c4);
+                  cp_async16(&a_s[r * LDK + kfill + c4], A + (int64_t)(m0 + r) * lda + koff + c4,
+                             (kr >= 4 ? 4 : kr) * 4);
+                }
+              }
+            } else {
+              for (int e = tid; e < TILE * GK; e += GNT) {
+                const int r = e >> 5, kk = e & 31;
+                if (r < mc && kk < take) {
+                  if (koff + kk < K) cp_async(&a_s[r * LDK + kfill + kk], A + (int64_t)(m0 + r) * lda + koff + kk);
+                  else a_s[r * LDK + kfill + kk] = 0.f;
+                }
+              }
+            }
+          } else {  // A transposed (k x m): rows of m into a_s[k * GPAD + r]
+            for (int e = tid; e < GK * (TILE / 4); e += GNT) {
+              const int kk = e >> 3, r4 = (e & 7) * 4;
+              if (kk < take && r4 < mc) {
+                float* d = &a_s[(kfill + kk) * GPAD + r4];
+                const float* src = A + (int64_t)(koff + kk) * lda + m0 + r4;
+                if (koff + kk >= K) {
+                  *reinterpret_cast<float4*>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
+                } else if (vecA) {
+                  cp_async16(d, src, 16);
+                } else {
+                  for (int u = 0; u < 4 && r4 + u < mc; ++u) cp_async(d + u, src + u);
+                }
+              }
+            }
+          }
+          if (!tb) {  // B row-major (k x n): rows of n into b_s[k * GPAD + c]
+            for (int e = tid; e < GK * (TILE / 4); e += GNT) {
+              const int kk = e >> 3, c4 = (e & 7) * 4;
+              if (kk < take && c4 < nc) {
+                float* d = &b_s[(kfill + kk) * GPAD + c4];
+                const float* src = B + (int64_t)(koff + kk) * ldb + n0 + c4;
+                if (koff + kk >= K) {
+                  *reinterpret_cast<float4*>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
+                } else if (vecB) {
+                  cp_async16(d, src, 16);
+                } else {
+                  for (int u = 0; u < 4 && c4 + u < nc; ++u) cp_async(d + u, src + u);
+                }
+              }
+            }
+          } else {  // B transposed (n x k): element by element
+            for (int e = tid; e < TILE * GK; e += GNT) {
+              const int c = e >> 5, kk = e & 31;
+              if (c < nc && kk < take) {
+                if (koff + kk < K) cp_async(&b_s[(kfill + kk) * GPAD + c], B + (int64_t)(n0 + c) * ldb + koff + kk);
+                else b_s[(kfill + kk) * GPAD + c] = 0.f;
+              }
+            }
+          }
+          const int kact = min(take, K - koff);
+          work += 2ull * mc * nc * (kact > 0 ? kact : 0);
+          kfill += take;
+          koff += take;
+          if (koff == K4) {
+            koff = 0;
+            ++q;
+            if (q < s.count) fetch();
+          }
+        }
+        return kfill;
+      };
+      int buf = 0;
+      int kf = fill(0);
+      cp_commit();
+      while (kf > 0) {
+        const int kf_next = fill(buf ^ 1);
+        cp_commit();
+        cp_wait1();
+        __syncthreads();
+        if (live) {
+          if (!ta) slice_fma<true>(sA[buf], sB[buf], kf, qx, qy, acc);
+          else slice_fma<false>(sA[buf], sB[buf], kf, qx, qy, acc);
+        }
+        __syncthreads();
+        buf ^= 1;
+        kf = kf_next;
+      }
+      if (mine) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int r = 4 * qy + i, c = 4 * qx + j;
+            if (r < mc && c < nc) st<float>(out, (int64_t)(m0 + r) * s.ldc + n0 + c, acc[i][j], accum);
+          }
+      }
+    }
+  }
+  if (ar.flops && tid == 0 && work) atomicAdd(ar.flops, work);
+}
+
 static Arenas to_dev(const ArenaSet& a) {
   Arenas d;
   for (int i = 0; i < kArenas; ++i) d.p[i] = (char*)a.p[i];
@@ -241,7 +502,10 @@ static void gemm_launch(const Seg* d_segs, const Item* d_items, int64_t first, i
   for (int64_t off = 0; off < count; off += kMaxGrid) {
     int64_t c = count - off < kMaxGrid ? count - off : kMaxGrid;
     dim3 grid((unsigned)c, (unsigned)gy);
-    seg_gemm_kernel<Acc><<<grid, GNT, 0, (cudaStream_t)stream>>>(d_segs, d_items, first + off, ar);
+    if constexpr (sizeof(Acc) == 4)
+      seg_gemm32_kernel<<<grid, GNT, 0, (cudaStream_t)stream>>>(d_segs, d_items, first + off, ar);
+    else
+      seg_gemm_kernel<Acc><<<grid, GNT, 0, (cudaStream_t)stream>>>(d_segs, d_items, first + off, ar);
   }
 }
 
@@ -374,8 +638,8 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
           while (r < n && lam[order[r]] > thr * l1) ++r;
       }
     }
-    if (r > t.kcap) {
-      r = t.kcap;
+    if (r > t.klim) {
+      r = t.klim;
       atomicAdd(cap_hits, 1ull);
     }
     s_rank = r;
@@ -663,8 +927,8 @@ __global__ void __launch_bounds__(256) eig_mixed_kernel(const EigTask* __restric
           while (r < n && lam[order[r]] > thr * l1) ++r;
       }
     }
-    if (r > t.kcap) {
-      r = t.kcap;
+    if (r > t.klim) {
+      r = t.klim;
       atomicAdd(cap_hits, 1ull);
     }
     s_rank = r;
@@ -949,8 +1213,8 @@ __global__ void __launch_bounds__(256) eig_mixed_kept_kernel(const EigTask* __re
       const double l1 = rqs[0];
       while (r < nc && rqs[r] > thr * l1) ++r;
     }
-    if (r > t.kcap) {
-      r = t.kcap;
+    if (r > t.klim) {
+      r = t.klim;
       atomicAdd(cap_hits, 1ull);
     }
     s_rank = r;

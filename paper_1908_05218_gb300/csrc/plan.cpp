@@ -43,9 +43,13 @@ struct PlanBuilder {
     int64_t o = top[a];
     top[a] += (elems + 31) & ~int64_t(31);
     P.region[a] = std::max(P.region[a], top[a]);
+    P.aev.push_back({(int32_t)P.launches.size(), (int8_t)a, 0, o, elems});
     return tag(a, o);
   }
-  void reset(Arena a) { top[a] = 0; }
+  void reset(Arena a) {
+    top[a] = 0;
+    P.aev.push_back({(int32_t)P.launches.size(), (int8_t)a, 1, 0, 0});
+  }
   // zero [0, top) of a region at this point of the program; the size is patched by
   // close_memset once the level has been planned
   size_t open_memset(Arena a) {
@@ -194,7 +198,8 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
   const Structure& st = *A.st;
   const int L = st.L, LS = st.LS, lmin = st.lmin;
   PlanBuilder pb(P);
-  // caps of C: leaf LS, non-leaf min(2 K[l+1], cap) (no cap in full mode), 0 above l_min
+  // caps of C: leaf LS, non-leaf min(2 K[l+1], cap) (no cap in full mode), 0 above l_min;
+  // each rounded up to a multiple of four for storage
   const bool formatted = prm.trunc == H2_TRUNC_FORMATTED;
   C.Kr.assign(L + 1, 0);
   C.Kc.assign(L + 1, 0);
@@ -202,11 +207,12 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
     C.Kr = A.Kr;
     C.Kc = B.Kc;
   } else {
-    C.Kr[L] = C.Kc[L] = LS;
+    // (storage caps rounded up to multiples of four; the rank limit is kept apart)
+    C.Kr[L] = C.Kc[L] = cap_round(LS);
     for (int l = L - 1; l >= lmin; --l) {
       int cap = prm.trunc == H2_TRUNC_FULL ? 1 << 20 : prm.rank_cap;
-      C.Kr[l] = std::min(2 * C.Kr[l + 1], cap);
-      C.Kc[l] = std::min(2 * C.Kc[l + 1], cap);
+      C.Kr[l] = cap_round(std::min(2 * C.Kr[l + 1], cap));
+      C.Kc[l] = cap_round(std::min(2 * C.Kc[l + 1], cap));
     }
   }
   mat_elems(C);  // offsets of C's arrays
@@ -330,8 +336,10 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         if (bl[p].kind == KF) {
           Y[p] = pb.alloc(AR_S, (int64_t)LS * rB(l));
           Yb[p] = pb.alloc(AR_S, (int64_t)cA(l) * LS);
-          Q[p] = pb.alloc(AR_S, LS2);   // F F^T, later F W, later V^C^T F
-          Rr[p] = pb.alloc(AR_S, LS2);  // F^T F, later W F, later F V^C
+          // (C's leaf caps are LS rounded up to a multiple of four: V^C^T F has rC rows
+          // of LS, F V^C has LS rows of stride cC)
+          Q[p] = pb.alloc(AR_S, (int64_t)std::max(LS, rC(l)) * LS);   // F F^T, later F W, later V^C^T F
+          Rr[p] = pb.alloc(AR_S, (int64_t)LS * std::max(LS, cC(l)));  // F^T F, later W F, later F V^C
         }
       std::vector<std::vector<int64_t>> Ksets(nb), Isets(nb);
       std::vector<std::vector<Item>> gF(lt.tg.size()), gZ(lt.tg.size()), gZp(lt.tg.size()), gZpp(lt.tg.size()),
@@ -615,6 +623,8 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         e.n_pad = (int16_t)(col ? gc : gr);
         e.half = leaf ? 0 : (int16_t)(col ? cC(c) : rC(c));
         e.kcap = (int16_t)(col ? cC(l) : rC(l));
+        e.klim = leaf ? (int16_t)LS
+                      : (int16_t)std::min<int>(e.kcap, prm.trunc == H2_TRUNC_FULL ? 1 << 14 : prm.rank_cap);
         e.col = (int16_t)col;
         P.eigs.push_back(e);
       }
