@@ -49,7 +49,7 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
     for f in CU:
         src = os.path.join(CSRC, f)
         obj = os.path.join(OBJ, f + ".o")
-        cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fopenmp", "-c", src, "-o", obj]
         if ptxas_info:
             cmd.insert(1, "-Xptxas=-v")
         jobs.append((src, obj, cmd))

@@ -384,8 +384,9 @@ void pack_from_device(Mat& m, Packed& p) {
 // Host-side check that every access of a plan stays inside its arena: run before a
 // plan's first upload so that an indexing error is reported instead of executed.
 void validate_plan(const Plan& P, const int64_t sizes[kArenas]) {
-  // live allocations of the work regions (start -> size), replayed in program order
-  std::map<int64_t, int64_t> live[kArenas];
+  // live allocations of the work regions, replayed in program order; a region is
+  // bump-allocated between resets, so its live list stays sorted by start
+  std::vector<std::pair<int64_t, int64_t>> live[kArenas];
   size_t ev = 0;
   auto is_work = [](int64_t a) { return a == AR_P || a == AR_G0 || a == AR_G1 || a == AR_S; };
   auto check = [&](int64_t tagged, int64_t extent, const char* what) {
@@ -394,8 +395,9 @@ void validate_plan(const Plan& P, const int64_t sizes[kArenas]) {
     if (tagged < 0 || off + extent > sizes[a])
       throw Error(H2_EINTERNAL, std::string("plan access out of bounds: ") + what);
     if (!is_work(a)) return;
-    auto it = live[a].upper_bound(off);
-    if (it == live[a].begin() || std::prev(it)->first + std::prev(it)->second < off + extent)
+    const auto& v = live[a];
+    auto it = std::upper_bound(v.begin(), v.end(), std::make_pair(off, INT64_MAX));
+    if (it == v.begin() || std::prev(it)->first + std::prev(it)->second < off + extent)
       throw Error(H2_EINTERNAL, std::string("plan access outside its allocation: ") + what);
   };
   auto check_seg = [&](const Seg& s) {
@@ -430,12 +432,28 @@ void validate_plan(const Plan& P, const int64_t sizes[kArenas]) {
   for (size_t li = 0; li < P.launches.size(); ++li) {
     for (; ev < P.aev.size() && P.aev[ev].launch <= (int32_t)li; ++ev) {
       const Plan::AllocEv& x = P.aev[ev];
-      if (x.reset) live[x.arena].clear();
-      else live[x.arena][x.start] = x.size;
+      if (x.reset) {
+        live[x.arena].clear();
+      } else if (x.size > 0) {  // (an empty allocation shares the next one's start)
+        if (!live[x.arena].empty() && live[x.arena].back().first + live[x.arena].back().second > x.start)
+          throw Error(H2_EINTERNAL, "plan allocations overlap");
+        live[x.arena].push_back({x.start, x.size});
+      }
     }
     const Launch& L = P.launches[li];
     if (L.kind == Launch::GEMM) {
-      for (int64_t i = L.first; i < L.first + L.count; ++i) check_seg(P.segs[i]);
+      // segments of one launch are checked in parallel (the live lists are read only)
+      std::string err;
+#pragma omp parallel for schedule(dynamic, 4096)
+      for (int64_t i = L.first; i < L.first + L.count; ++i) {
+        try {
+          check_seg(P.segs[i]);
+        } catch (std::exception& e) {
+#pragma omp critical
+          if (err.empty()) err = e.what();
+        }
+      }
+      if (!err.empty()) throw Error(H2_EINTERNAL, err);
       nseg += L.count;
     } else if (L.kind == Launch::EIG) {
       for (int64_t i = L.first; i < L.first + L.count; ++i) check_eig(P.eigs[i]);
