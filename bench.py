@@ -34,7 +34,14 @@ WORKLOADS = {
     "cubes16x16": (16, 16, 4096, 1e-4, "N=1,048,576 panel centroids on a 16x16 array of unit cubes"),
     "cubes4x4": (4, 4, 4096, 1e-4, "N=65,536 panel centroids on a 4x4 array of unit cubes"),
     "cubes2x2": (2, 2, 1024, 1e-4, "N=4,096 panel centroids on a 2x2 array of unit cubes"),
+    "sample": (2, 2, 2048, 1e-4, "N=8,192 panel centroids on a 2x2 array of unit cubes"),
 }
+# DRAM traffic of the float32 GEMM kernel from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum over the 115 GEMM launches of one product of the N=65,536
+# cube-array workload; profiles/dram_traffic_h2mmp_N65536_mixed.md), valid only for the
+# kernel source it was taken on.  Other workloads scale it by the executed flops.
+TRAFFIC = {"kernel": "seg_gemm32_kernel", "src_sha256": "4613ef53d742e11d23e7114ccdddad38865bef2da825b32aee668705c2ed1532",
+           "bytes_per_product": 40.01e9, "executed_flops_per_product": 325285346924.0}
 LEAF, ETA, EPS_H2 = 32, 1.0, 1e-4
 
 
@@ -114,13 +121,13 @@ def reference_arm(args):
 
 
 def oracle_sample(steps: int):
-    """Child process: oracle product on N=4096 points of the cube-array geometry."""
+    """Child process: oracle product on N=8192 points of the cube-array geometry."""
     import numpy as np
 
     from oracle import h2 as oh2
     from oracle import mmp as ommp
     from paper_1908_05218_gb300 import inputs
-    nx, ny, ppc, eps, _ = WORKLOADS["cubes2x2"]
+    nx, ny, ppc, eps, _ = WORKLOADS["sample"]
     wa = inputs.workload_cube_array(nx, ny, ppc)
     wb = inputs.workload_cube_array(nx, ny, ppc, kernel="invr2")
     A = oh2.build(wa.points, wa.kernel, LEAF, ETA, EPS_H2)
@@ -175,7 +182,7 @@ def main():
         line = {"metric": metric, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus, "steps": r["steps"],
                 "warmup": 0, "ms_per_step": r["t"] * 1e3, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-                "config": {"workload": f"cube array 2x2, 1024 points per cube (N={r['n']}), leaf {LEAF}, "
+                "config": {"workload": f"cube array 2x2, 2048 points per cube (N={r['n']}), leaf {LEAF}, "
                                        f"eta {ETA}, eps {eps}, A: 1/(4 pi r), B: 1/r^2",
                            "sample_of": desc},
                 "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
@@ -230,11 +237,13 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     with Clocks(local) as clk:
+        n_launch0 = lib.kernel_launches()
         ev0.record(stream)
         for _ in range(args.steps):
             C = A.mmp(B, eps, precision=prec, trunc=args.trunc, out=C)
         ev1.record(stream)
         torch.cuda.synchronize()
+        n_launch = lib.kernel_launches() - n_launch0
     if dist:
         dist.barrier()
     ms = ev0.elapsed_time(ev1) / max(1, args.steps)
@@ -269,8 +278,19 @@ def main():
     peak = fp64_peak if args.precision == "fp64" else fp32_peak
     gemm_ms = tot.get("gemm", [0.0])[0]
     gemm_tf = executed_flops / (gemm_ms * 1e-3) / 1e12 if gemm_ms else 0.0
-    roof = {"bound": "alu", "kernel": "seg_gemm_kernel" if dom == "gemm" else "eig_kernel", "dominant": dom,
-            "achieved": gemm_tf, "peak": peak, "unit": "TFLOP/s", "frac": gemm_tf / peak, "traffic": None,
+    traffic = None
+    if args.precision != "fp64" and dom == "gemm" and tot["gemm"][2]:
+        import hashlib
+        with open(os.path.join(ROOT, "paper_1908_05218_gb300", "csrc", "kernels.cu"), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() == TRAFFIC["src_sha256"]:
+                traffic = (TRAFFIC["bytes_per_product"] * executed_flops / TRAFFIC["executed_flops_per_product"]
+                           / tot["gemm"][2])
+    gemm_name = "seg_gemm_kernel<double>" if args.precision == "fp64" else "seg_gemm32_kernel"
+    eig_name = "eig_kernel" if args.precision == "fp64" else "eig_mixed_kept_kernel"
+    roof = {"bound": "alu", "kernel": gemm_name if dom == "gemm" else eig_name, "dominant": dom,
+            "achieved": gemm_tf, "peak": peak, "unit": "TFLOP/s", "frac": gemm_tf / peak, "traffic": traffic,
+            "traffic_note": ("DRAM bytes per GEMM launch: ncu capture at N=65,536 scaled by executed flops"
+                             if traffic else "kernel changed since the capture (or float64 run)"),
             "launches_per_step": tot["gemm"][2], "ms_per_step": gemm_ms,
             "executed_flops_per_step": executed_flops,
             "note": ("GEMM kernel: multiply-add flops executed at the actual ranks (device counter) / its "
@@ -311,7 +331,7 @@ def main():
         cpu_line = None
         if cpu and "t" in cpu:
             cpu_line = {"value": cpu["bytes"] / cpu["t"] / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                        "sample": f"cube array 2x2, 1024 points per cube (N={cpu['n']}), one product, eps {eps}",
+                        "sample": f"cube array 2x2, 2048 points per cube (N={cpu['n']}), one product, eps {eps}",
                         "seconds": cpu["t"]}
         elif cpu:
             cpu_line = {"error": cpu.get("error")}
@@ -329,7 +349,7 @@ def main():
             "phase_ms": phase_ms, "phase_ms_by_name": {k: round(v, 3) for k, v in by_phase.items()},
             "ms_by_level": {k: round(v, 3) for k, v in sorted(by_level.items())},
             "eig_ms_by_level": {k: round(v, 3) for k, v in sorted(eig_by_level.items())}, "roofline": roof, "cpu_baseline": cpu_line, "e2e": e2e,
-            "gpu_launches": int(sum(tot[k][2] for k in tot if k != "memset")) * args.steps,
+            "gpu_launches": int(n_launch),
             "clocks": clk.summary(),
         }
         print(json.dumps(line))

@@ -216,6 +216,12 @@ h2_status h2_level_blocks(h2_handle h, int32_t level, int32_t* t, int32_t* s,
 h2_status h2_trace_enable(h2_handle A, int32_t on);
 h2_status h2_trace_read(h2_handle C, int32_t cap, int32_t* kind, int32_t* level, double* ms,
                         double* flops, int32_t* count);
+/* Number of CUDA kernels this library has launched in this process so far (GEMM,
+ * eigen, conversion and permutation kernels; not the no-allocation matvec's, and
+ * not the driver's memsets and copies).  The difference of two readings counts the
+ * kernels of the calls in between; pure host function, never fails for a non-NULL
+ * argument. */
+h2_status h2_kernel_launches(uint64_t* count);
 /* Multiply-add flops (2 per multiply-add) the GEMM kernel executed at the actual
  * ranks during the traced product that made C (counted on the device). */
 h2_status h2_trace_flops(h2_handle C, double* executed);

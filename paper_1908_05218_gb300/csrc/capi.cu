@@ -940,6 +940,12 @@ h2_status h2_trace_read(h2_handle C, int32_t cap, int32_t* kind, int32_t* level,
   });
 }
 
+h2_status h2_kernel_launches(uint64_t* count) {
+  if (!count) return fail(H2_EINVAL, "null argument");
+  *count = (uint64_t)kernel_launches();
+  return H2_OK;
+}
+
 h2_status h2_trace_flops(h2_handle C, double* executed) {
   if (!C || !executed) return fail(H2_EINVAL, "null argument");
   return guarded([&] {

@@ -223,6 +223,7 @@ void launch_gemm(const Seg* d_segs, const Item* d_items, int64_t first, int64_t 
 void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, const ArenaSet& ar,
                 int32_t* kr, int32_t* kc, double eps, int trunc, unsigned long long* cap_hits,
                 int max_npad, double* scratch, void* stream);
+unsigned long long kernel_launches();  // kernels launched by this library so far
 void launch_to_f32(const double* src, float* dst, int64_t n, void* stream);
 void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const ArenaSet& ar, int32_t* kr,
                       int32_t* kc, double eps, int trunc, unsigned long long* cap_hits, int max_npad, void* stream);

@@ -3,12 +3,17 @@
 // and the permutations between user order and padded tree order.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 
 #include "internal.hpp"
 
 namespace h2 {
+
+// kernel launches made by this library in this process (every launch site below adds)
+static std::atomic<unsigned long long> g_launches{0};
+unsigned long long kernel_launches() { return g_launches.load(); }
 
 struct Arenas {
   char* p[kArenas];
@@ -506,6 +511,7 @@ static void gemm_launch(const Seg* d_segs, const Item* d_items, int64_t first, i
       seg_gemm32_kernel<<<grid, GNT, 0, (cudaStream_t)stream>>>(d_segs, d_items, first + off, ar);
     else
       seg_gemm_kernel<Acc><<<grid, GNT, 0, (cudaStream_t)stream>>>(d_segs, d_items, first + off, ar);
+    g_launches += 1;
   }
 }
 
@@ -524,6 +530,7 @@ __global__ void to_f32_kernel(const double* __restrict__ s, float* __restrict__ 
 
 void launch_to_f32(const double* src, float* dst, int64_t n, void* stream) {
   to_f32_kernel<<<4 * 152, 256, 0, (cudaStream_t)stream>>>(src, dst, n);
+  g_launches += 1;
 }
 
 // ------------------------------------------------------------ eigen + truncation
@@ -1307,6 +1314,7 @@ void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const
     const size_t smem = (size_t)3 * nn * (nn + 1) * sizeof(double);
     eig_mixed_kernel<<<(unsigned)count, 256, smem, (cudaStream_t)stream>>>(d_eigs, first, ar, kr, kc, eps, trunc,
                                                                            cap_hits);
+    g_launches += 1;
   } else {
     // the level's padded size comes from the rank caps; the actual sizes (children's
     // ranks) are only known on the device and are mostly far smaller, so tasks are
@@ -1320,9 +1328,11 @@ void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const
       if (!tiers) hi = top;
       const int h = hi < top ? hi : top;
       // (128 threads are enough for nn <= 48: a step has <= 300 block and row tasks)
-      if (h > lo)
+      if (h > lo) {
         eig_mixed_kept_kernel<<<(unsigned)count, h <= 48 ? 128 : 256, eig_kept_smem(h), (cudaStream_t)stream>>>(
             d_eigs, first, ar, kr, kc, eps, trunc, cap_hits, lo, h);
+        g_launches += 1;
+      }
       lo = h;
       if (h == top) break;
     }
@@ -1350,6 +1360,7 @@ void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, const Arena
   }
   eig_kernel<<<(unsigned)count, 256, smem, (cudaStream_t)stream>>>(d_eigs, first, ar, kr, kc, eps, trunc, cap_hits,
                                                                      scratch, stride);
+  g_launches += 1;
 }
 
 // ------------------------------------------------------------ permutations
@@ -1380,6 +1391,7 @@ __global__ void identity_kernel(double* out, int64_t n) {
 
 void launch_identity(double* out, int64_t n, void* stream) {
   identity_kernel<<<(unsigned)((n * n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(out, n);
+  g_launches += 1;
 }
 
 void launch_permute(const double* src, double* dst, const int64_t* user, int64_t rows, int64_t n, int64_t nrhs,
@@ -1390,6 +1402,7 @@ void launch_permute(const double* src, double* dst, const int64_t* user, int64_t
     to_tree_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(src, dst, user, rows, n, nrhs);
   else
     from_tree_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(src, dst, user, rows, n, nrhs);
+  g_launches += 1;
 }
 
 }  // namespace h2

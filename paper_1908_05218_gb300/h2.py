@@ -24,7 +24,7 @@ _TRUNC = {"paper": TRUNC_PAPER, "sv": TRUNC_SV, "full": TRUNC_FULL, "formatted":
 # exported symbols and their signatures (checked by the CPU tests)
 SYMBOLS = ["h2_build", "h2_import", "h2_export", "h2_mmp", "h2_mmp_batched", "h2_matvec", "h2_matvec_noalloc", "h2_to_dense", "h2_info",
            "h2_tree_perm", "h2_level_blocks", "h2_trace_enable", "h2_trace_read", "h2_trace_flops", "h2_trace_phase", "h2_destroy",
-           "h2_last_error"]
+           "h2_last_error", "h2_kernel_launches"]
 
 
 class H2Error(RuntimeError):
@@ -75,6 +75,7 @@ def load(path: str = LIB_PATH):
     lib.h2_trace_enable.argtypes = [P, I32]
     lib.h2_trace_read.argtypes = [P, I32, P, P, P, P, P]
     lib.h2_trace_flops.argtypes = [P, P]
+    lib.h2_kernel_launches.argtypes = [P]
     lib.h2_trace_phase.argtypes = [P, I32]
     lib.h2_trace_phase.restype = C.c_char_p
     lib.h2_destroy.argtypes = [P]
@@ -241,6 +242,13 @@ class H2Matrix:
         if cnt.value:
             _check(lib.h2_level_blocks(self.handle, level, _ptr(t), _ptr(s), _ptr(k), C.byref(cnt)))
         return t, s, k
+
+
+def kernel_launches() -> int:
+    """CUDA kernels this library has launched in this process so far."""
+    v = C.c_uint64(0)
+    _check(load().h2_kernel_launches(C.byref(v)))
+    return int(v.value)
 
 
 def h2_mmp_batched(As, Bs, eps: float, precision: int = FP64, trunc="paper", rank_cap: int = 0,
