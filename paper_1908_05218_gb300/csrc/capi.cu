@@ -34,6 +34,10 @@ struct h2_matrix {
   std::map<int64_t, std::unique_ptr<h2::Plan>> mv_plans;  // by nrhs
   std::map<int64_t, std::pair<int64_t, int64_t>> mv_offs;
   int64_t* d_user = nullptr;  // padded tree row -> user index (-1: padding)
+  // device arena tables the kernels read: slot 0 for the product written into this
+  // handle, slot 1 for its matvec (stream-ordered uploads; concurrent use of one handle
+  // on two streams is not supported)
+  h2::Arenas* d_ars = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool timed = false;
   int origin_trunc = -1, origin_cap = -1, origin_prec = -1;
@@ -515,8 +519,8 @@ void free_plan(Plan& P) {
   P.d_scratch = nullptr;
 }
 
-void run_plan(const Plan& P, const ArenaSet& ar, int32_t* kr, int32_t* kc, unsigned long long* cap_hits,
-              const MmpParams& prm, void* stream, bool skip_memset, Trace* tr) {
+void run_plan(const Plan& P, const ArenaSet& ar, const Arenas* d_ars, const MmpParams& prm, void* stream,
+              bool skip_memset, Trace* tr) {
   if (tr) {
     while (tr->ev.size() < 2 * P.launches.size()) {
       cudaEvent_t e;
@@ -535,17 +539,15 @@ void run_plan(const Plan& P, const ArenaSet& ar, int32_t* kr, int32_t* kc, unsig
       cuda_check(cudaMemsetAsync(p, 0, L.elems * ar.esize(a), (cudaStream_t)stream), "memset");
     } else if (L.kind == Launch::COPY_RANKS) {
       // formatted product: C's ranks are A's row ranks and B's column ranks
-      cuda_check(cudaMemcpyAsync(kr, ar.rk[RK_AR], L.elems * sizeof(int32_t), cudaMemcpyDeviceToDevice,
-                                 (cudaStream_t)stream), "copy ranks");
-      cuda_check(cudaMemcpyAsync(kc, ar.rk[RK_BC], L.elems * sizeof(int32_t), cudaMemcpyDeviceToDevice,
-                                 (cudaStream_t)stream), "copy ranks");
+      launch_copy_ranks(d_ars, 0, L.elems, stream);
     } else if (L.kind == Launch::GEMM) {
-      launch_gemm(P.d_segs, P.d_items, L.first, L.count, ar, L.aux, L.aux2, prm.precision == H2_MIXED_FP32, stream);
+      launch_gemm(P.d_segs, P.d_items, L.first, L.count, d_ars, L.aux, L.aux2, prm.precision == H2_MIXED_FP32,
+                  stream);
     } else {
       if (prm.precision == H2_MIXED_FP32 && L.aux <= 96)
-        launch_eig_mixed(P.d_eigs, L.first, L.count, ar, kr, kc, prm.eps, prm.trunc, cap_hits, L.aux, stream);
+        launch_eig_mixed(P.d_eigs, L.first, L.count, d_ars, prm.eps, prm.trunc, L.aux, stream);
       else
-        launch_eig(P.d_eigs, L.first, L.count, ar, kr, kc, prm.eps, prm.trunc, cap_hits, L.aux, P.d_scratch, stream);
+        launch_eig(P.d_eigs, L.first, L.count, d_ars, prm.eps, prm.trunc, L.aux, P.d_scratch, stream);
     }
     cuda_check(cudaGetLastError(), L.phase);
     if (tr) cuda_check(cudaEventRecord((cudaEvent_t)tr->ev[2 * li + 1], (cudaStream_t)stream), "event");
@@ -559,6 +561,11 @@ using namespace h2;
 extern "C" {
 
 const char* h2_last_error(void) { return g_err.c_str(); }
+
+static Arenas* arena_slot(h2_matrix* h, int slot) {
+  if (!h->d_ars) h->d_ars = (Arenas*)dmalloc(2 * sizeof(Arenas));
+  return h->d_ars + slot;
+}
 
 static void finish_handle(h2_matrix* h, const h2_opts& o) {
   h->m.stream = o.stream;
@@ -761,8 +768,12 @@ h2_status h2_mmp(h2_handle A, h2_handle B, double eps, const h2_opts* opts, h2_h
       ar.flops = out->m.d_cap + 1;  // second counter of the handle's counter block
       cuda_check(cudaMemsetAsync(ar.flops, 0, sizeof(unsigned long long), s), "zero flop counter");
     }
-    run_plan(ent->plan, ar, out->m.d_kr, out->m.d_kc, out->m.d_cap, prm, o.stream, false,
-             A->trace_on ? &out->trace : nullptr);
+    ar.kr = out->m.d_kr;
+    ar.kc = out->m.d_kc;
+    ar.cap_hits = out->m.d_cap;
+    Arenas* d_ars = arena_slot(out, 0);
+    upload_arenas(d_ars, to_arenas(ar), o.stream);
+    run_plan(ent->plan, ar, d_ars, prm, o.stream, false, A->trace_on ? &out->trace : nullptr);
     cuda_check(cudaEventRecord(out->ev1, s), "event");
     out->timed = true;
     if (fresh) *C = fresh.release();
@@ -808,7 +819,9 @@ h2_status h2_matvec(h2_handle h, const double* x, double* y, int64_t nrhs) {
     ar.p[AR_A] = h->m.arena;
     ar.p[AR_P] = W;
     MmpParams prm{0, 0, 0, 0};
-    run_plan(P, ar, nullptr, nullptr, nullptr, prm, s, true);
+    Arenas* d_ars = arena_slot(h, 1);
+    upload_arenas(d_ars, to_arenas(ar), s);
+    run_plan(P, ar, d_ars, prm, s, true);
     launch_permute(yt, y, h->d_user, rows, st.n, nrhs, false, s);
     cuda_check(cudaGetLastError(), "matvec");
   });
@@ -969,6 +982,7 @@ void h2_destroy(h2_handle h) {
   h->made_by.reset();
   for (auto& kv : h->mv_plans) free_plan(*kv.second);
   if (h->d_user) cudaFree(h->d_user);
+  if (h->d_ars) cudaFree(h->d_ars);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   free_mat(h->m);

@@ -123,7 +123,9 @@ struct Seg {
   int16_t m, n, k, lda, ldb, ldc;
   int32_t mref, nref;
   uint8_t flags;
-  uint8_t pad[7];
+  uint8_t pad0;
+  int16_t inst;  // product instance: index into the launch's arena tables (0 for one product)
+  int32_t pad1;
 };
 struct Item {
   int64_t a = 0, b = 0;
@@ -146,7 +148,8 @@ struct EigTask {
   int32_t nleaf;     // leaf: cluster size; active rows [0, nleaf)
   int16_t n_pad, half, kcap, col;  // Gram dim, child offset, output row stride, 1 = column basis
   int16_t klim;                     // largest rank kept (the rank cap; <= kcap)
-  int16_t pad2[3];
+  int16_t inst;                     // product instance (index into the arena tables)
+  int16_t pad2[2];
 };
 
 struct Launch {
@@ -211,22 +214,39 @@ struct ArenaSet {
   uint32_t f32 = 0;
   const int32_t* rk[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   unsigned long long* flops = nullptr;  // executed-flop counter (tracing only)
+  int32_t* kr = nullptr;                // the output's rank arrays (written by the eigen step)
+  int32_t* kc = nullptr;
+  unsigned long long* cap_hits = nullptr;
   size_t esize(int a) const { return ((f32 >> a) & 1) ? 4 : 8; }
 };
-void run_plan(const Plan& plan, const ArenaSet& ar, int32_t* kr_out, int32_t* kc_out,
-              unsigned long long* cap_hits, const MmpParams& p, void* stream, bool skip_memset,
-              Trace* trace = nullptr);
+// The same table as the kernels read it, in device memory: one per product instance of
+// a launch (segments and eigen tasks carry the instance index).
+struct Arenas {
+  char* p[kArenas];
+  uint32_t f32;
+  const int32_t* rk[6];
+  unsigned long long* flops;
+  int32_t* kr;
+  int32_t* kc;
+  unsigned long long* cap_hits;
+};
+Arenas to_arenas(const ArenaSet& a);
+// writes `a` to device memory `dst` in stream order (a one-thread kernel taking it by value)
+void upload_arenas(Arenas* dst, const Arenas& a, void* stream);
+void run_plan(const Plan& plan, const ArenaSet& ar, const Arenas* d_ars, const MmpParams& p, void* stream,
+              bool skip_memset, Trace* trace = nullptr);
 
 // device helpers (kernels.cu)
-void launch_gemm(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const ArenaSet& ar,
+void launch_gemm(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const Arenas* d_ars,
                  int maxn, int maxdim, bool fp32, void* stream);
-void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, const ArenaSet& ar,
-                int32_t* kr, int32_t* kc, double eps, int trunc, unsigned long long* cap_hits,
+void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, const Arenas* d_ars, double eps, int trunc,
                 int max_npad, double* scratch, void* stream);
+// formatted product: C's ranks are A's row ranks and B's column ranks (instance inst)
+void launch_copy_ranks(const Arenas* d_ars, int inst, int64_t n, void* stream);
 unsigned long long kernel_launches();  // kernels launched by this library so far
 void launch_to_f32(const double* src, float* dst, int64_t n, void* stream);
-void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const ArenaSet& ar, int32_t* kr,
-                      int32_t* kc, double eps, int trunc, unsigned long long* cap_hits, int max_npad, void* stream);
+void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const Arenas* d_ars, double eps,
+                      int trunc, int max_npad, void* stream);
 void launch_permute(const double* src, double* dst, const int64_t* user, int64_t rows, int64_t n,
                     int64_t nrhs, bool to_tree, void* stream);
 void launch_identity(double* out, int64_t n, void* stream);

@@ -3,6 +3,7 @@
 // and the permutations between user order and padded tree order.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstdint>
 #include <cstdio>
@@ -15,13 +16,6 @@ namespace h2 {
 static std::atomic<unsigned long long> g_launches{0};
 unsigned long long kernel_launches() { return g_launches.load(); }
 
-struct Arenas {
-  char* p[kArenas];
-  uint32_t f32;
-  const int32_t* rk[6];
-  unsigned long long* flops;  // if set: executed multiply-add flops are added here
-};
-
 __device__ __forceinline__ int arena_idx(int64_t t) { return (int)((t >> kTagShift) & 7); }
 
 // typed view of one tagged matrix: float or double storage, read/written as Acc
@@ -30,10 +24,12 @@ struct View {
   bool f32;
 };
 
-__device__ __forceinline__ View view(const Arenas& a, int64_t t) {
+// (a points at the instance's table in device memory; a.flops, if set, collects the
+// executed multiply-add flops)
+__device__ __forceinline__ View view(const Arenas* a, int64_t t) {
   int ai = arena_idx(t);
-  bool f = (a.f32 >> ai) & 1;
-  return View{a.p[ai] + (t & kOffMask) * (f ? 4 : 8), f};
+  bool f = (a->f32 >> ai) & 1;
+  return View{a->p[ai] + (t & kOffMask) * (f ? 4 : 8), f};
 }
 
 template <typename Acc>
@@ -52,9 +48,9 @@ __device__ __forceinline__ void st(const View& v, int64_t i, Acc x, bool acc) {
   }
 }
 
-__device__ __forceinline__ int bound(const Arenas& a, int32_t ref, int padded) {
+__device__ __forceinline__ int bound(const Arenas* a, int32_t ref, int padded) {
   if (ref < 0) return padded;
-  int r = a.rk[ref >> kRefShift][ref & ((1 << kRefShift) - 1)];
+  int r = a->rk[ref >> kRefShift][ref & ((1 << kRefShift) - 1)];
   return r < padded ? r : padded;
 }
 
@@ -102,16 +98,17 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 __device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
 
 template <typename T>
-__device__ __forceinline__ const T* ptr_of(const Arenas& a, int64_t t) {
-  return (const T*)a.p[arena_idx(t)] + (t & kOffMask);
+__device__ __forceinline__ const T* ptr_of(const Arenas* a, int64_t t) {
+  return (const T*)a->p[arena_idx(t)] + (t & kOffMask);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(GNT, 12) seg_gemm_kernel(const Seg* __restrict__ segs, const Item* __restrict__ items,
-                                                       int64_t first, Arenas ar) {
+                                                       int64_t first, const Arenas* __restrict__ ars) {
   __shared__ __align__(16) T sA[2][GK * GPAD];
   __shared__ __align__(16) T sB[2][GK * GPAD];
   const Seg s = segs[first + blockIdx.x];
+  const Arenas* ar = ars + s.inst;
   const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
   const bool ta = s.flags & SF_TA, tb = s.flags & SF_TB, accum = s.flags & SF_ACC;
   const int M = bound(ar, s.mref, s.m), N = bound(ar, s.nref, s.n);
@@ -225,7 +222,7 @@ __global__ void __launch_bounds__(GNT, 12) seg_gemm_kernel(const Seg* __restrict
         }
     }
   }
-  if (ar.flops && tid == 0 && work) atomicAdd(ar.flops, work);
+  if (ar->flops && tid == 0 && work) atomicAdd(ar->flops, work);
 }
 
 // ------------------------------------------------------------ segmented GEMM, float32
@@ -284,10 +281,11 @@ __device__ __forceinline__ void slice_fma(const float* __restrict__ a_s, const f
 
 __global__ void __launch_bounds__(GNT, 12) seg_gemm32_kernel(const Seg* __restrict__ segs,
                                                              const Item* __restrict__ items, int64_t first,
-                                                             Arenas ar) {
+                                                             const Arenas* __restrict__ ars) {
   __shared__ __align__(16) float sA[2][kSliceA];
   __shared__ __align__(16) float sB[2][GK * GPAD];
   const Seg s = segs[first + blockIdx.x];
+  const Arenas* ar = ars + s.inst;
   const int tid = threadIdx.x, lane = tid & 31, tx = tid & 7, ty = tid >> 3;
   const bool ta = s.flags & SF_TA, tb = s.flags & SF_TB, accum = s.flags & SF_ACC;
   const int M = bound(ar, s.mref, s.m), N = bound(ar, s.nref, s.n);
@@ -485,20 +483,12 @@ __global__ void __launch_bounds__(GNT, 12) seg_gemm32_kernel(const Seg* __restri
       }
     }
   }
-  if (ar.flops && tid == 0 && work) atomicAdd(ar.flops, work);
+  if (ar->flops && tid == 0 && work) atomicAdd(ar->flops, work);
 }
 
-static Arenas to_dev(const ArenaSet& a) {
-  Arenas d;
-  for (int i = 0; i < kArenas; ++i) d.p[i] = (char*)a.p[i];
-  d.f32 = a.f32;
-  for (int i = 0; i < 6; ++i) d.rk[i] = a.rk[i];
-  d.flops = a.flops;
-  return d;
-}
 
 template <typename Acc>
-static void gemm_launch(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const Arenas& ar,
+static void gemm_launch(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const Arenas* ar,
                         int maxn, void* stream) {
   const int64_t kMaxGrid = 2147483647LL;
   int gy = (maxn + TILE - 1) / TILE;
@@ -515,12 +505,44 @@ static void gemm_launch(const Seg* d_segs, const Item* d_items, int64_t first, i
   }
 }
 
-void launch_gemm(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const ArenaSet& a, int maxn,
-                 int maxdim, bool fp32, void* stream) {
+void launch_gemm(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const Arenas* d_ars,
+                 int maxn, int maxdim, bool fp32, void* stream) {
   (void)maxdim;
-  Arenas ar = to_dev(a);
-  if (fp32) gemm_launch<float>(d_segs, d_items, first, count, ar, maxn, stream);
-  else gemm_launch<double>(d_segs, d_items, first, count, ar, maxn, stream);
+  if (fp32) gemm_launch<float>(d_segs, d_items, first, count, d_ars, maxn, stream);
+  else gemm_launch<double>(d_segs, d_items, first, count, d_ars, maxn, stream);
+}
+
+__global__ void set_arenas_kernel(Arenas* dst, Arenas a) { *dst = a; }
+
+void upload_arenas(Arenas* dst, const Arenas& a, void* stream) {
+  set_arenas_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(dst, a);
+  g_launches += 1;
+}
+
+Arenas to_arenas(const ArenaSet& a) {
+  Arenas d;
+  for (int i = 0; i < kArenas; ++i) d.p[i] = (char*)a.p[i];
+  d.f32 = a.f32;
+  for (int i = 0; i < 6; ++i) d.rk[i] = a.rk[i];
+  d.flops = a.flops;
+  d.kr = a.kr;
+  d.kc = a.kc;
+  d.cap_hits = a.cap_hits;
+  return d;
+}
+
+__global__ void copy_ranks_kernel(const Arenas* __restrict__ ars, int inst, int64_t n) {
+  const Arenas* a = ars + inst;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    a->kr[i] = a->rk[RK_AR][i];
+    a->kc[i] = a->rk[RK_BC][i];
+  }
+}
+
+void launch_copy_ranks(const Arenas* d_ars, int inst, int64_t n, void* stream) {
+  copy_ranks_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 1024)), 256, 0,
+                      (cudaStream_t)stream>>>(d_ars, inst, n);
+  g_launches += 1;
 }
 
 __global__ void to_f32_kernel(const double* __restrict__ s, float* __restrict__ d, int64_t n) {
@@ -555,10 +577,9 @@ template <typename T>
 __device__ void jacobi_sweeps(T* A, T* V, int nn, int lds, int max_sweeps, double tol, double* red, T* cs, T* sn,
                               int* pp, int* qq);
 
-__global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ tasks, int64_t first, Arenas ar,
-                                                  int32_t* kr, int32_t* kc, double eps, int trunc,
-                                                  unsigned long long* cap_hits, double* scratch,
-                                                  int64_t scratch_stride) {
+__global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ tasks, int64_t first,
+                                                  const Arenas* __restrict__ ars, double eps, int trunc,
+                                                  double* scratch, int64_t scratch_stride) {
   extern __shared__ double smem[];
   __shared__ int act[256];
   __shared__ double red[8];
@@ -568,6 +589,10 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
   __shared__ double lam[256];
   __shared__ int s_n, s_rank;
   const EigTask t = tasks[first + blockIdx.x];
+  const Arenas* ar = ars + t.inst;  // the task's product instance
+  int32_t* const kr = ar->kr;
+  int32_t* const kc = ar->kc;
+  unsigned long long* const cap_hits = ar->cap_hits;
   const int tid = threadIdx.x, nt = blockDim.x;
   int32_t* ranks = t.col ? kc : kr;
   if (tid == 0) {
@@ -656,7 +681,7 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
   const int rank = s_rank;
   double* out = (double*)view(ar, t.out).base;  // the new bases are float64 (arena C)
   // float copy for the GEMMs of the mixed product (arena X mirrors C's basis region)
-  float* out32 = ar.p[AR_X] ? (float*)ar.p[AR_X] + (t.out & kOffMask) : nullptr;
+  float* out32 = ar->p[AR_X] ? (float*)ar->p[AR_X] + (t.out & kOffMask) : nullptr;
   for (int e = tid; e < t.n_pad * t.kcap; e += nt) {
     out[e] = 0.0;
     if (out32) out32[e] = 0.f;
@@ -783,9 +808,8 @@ __device__ void smem_gemm(const double* X, bool tx, const double* Y, bool ty, do
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(256) eig_mixed_kernel(const EigTask* __restrict__ tasks, int64_t first, Arenas ar,
-                                                        int32_t* kr, int32_t* kc, double eps, int trunc,
-                                                        unsigned long long* cap_hits) {
+__global__ void __launch_bounds__(256) eig_mixed_kernel(const EigTask* __restrict__ tasks, int64_t first,
+                                                        const Arenas* __restrict__ ars, double eps, int trunc) {
   extern __shared__ double smem[];
   __shared__ int act[kMixMax + 2];
   __shared__ double red[8];
@@ -797,6 +821,10 @@ __global__ void __launch_bounds__(256) eig_mixed_kernel(const EigTask* __restric
   __shared__ double rowbuf[4 * kMixMax];
   __shared__ int s_n, s_rank;
   const EigTask t = tasks[first + blockIdx.x];
+  const Arenas* ar = ars + t.inst;  // the task's product instance
+  int32_t* const kr = ar->kr;
+  int32_t* const kc = ar->kc;
+  unsigned long long* const cap_hits = ar->cap_hits;
   const int tid = threadIdx.x, nt = blockDim.x;
   int32_t* ranks = t.col ? kc : kr;
   if (tid == 0) {
@@ -945,7 +973,7 @@ __global__ void __launch_bounds__(256) eig_mixed_kernel(const EigTask* __restric
   const int rank = s_rank;
   double* out = (double*)view(ar, t.out).base;  // the new bases are float64 (arena C)
   // float copy for the GEMMs of the mixed product (arena X mirrors C's basis region)
-  float* out32 = ar.p[AR_X] ? (float*)ar.p[AR_X] + (t.out & kOffMask) : nullptr;
+  float* out32 = ar->p[AR_X] ? (float*)ar->p[AR_X] + (t.out & kOffMask) : nullptr;
   for (int e = tid; e < t.n_pad * t.kcap; e += nt) {
     out[e] = 0.0;
     if (out32) out32[e] = 0.f;
@@ -1007,9 +1035,8 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 }
 
 __global__ void __launch_bounds__(256) eig_mixed_kept_kernel(const EigTask* __restrict__ tasks, int64_t first,
-                                                             Arenas ar, int32_t* kr, int32_t* kc, double eps,
-                                                             int trunc, unsigned long long* cap_hits, int nn_lo,
-                                                             int nn_hi) {
+                                                             const Arenas* __restrict__ ars, double eps, int trunc,
+                                                             int nn_lo, int nn_hi) {
   extern __shared__ __align__(16) unsigned char esm[];
   __shared__ int act[kMixMax + 4];
   __shared__ double red[8];
@@ -1021,6 +1048,10 @@ __global__ void __launch_bounds__(256) eig_mixed_kept_kernel(const EigTask* __re
   __shared__ double rowbuf[kKeptRows * kMixMax];
   __shared__ int s_n, s_nc, s_rank;
   const EigTask t = tasks[first + blockIdx.x];
+  const Arenas* ar = ars + t.inst;  // the task's product instance
+  int32_t* const kr = ar->kr;
+  int32_t* const kc = ar->kc;
+  unsigned long long* const cap_hits = ar->cap_hits;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, w = tid >> 5, nw = nt >> 5;
   int32_t* ranks = t.col ? kc : kr;
   if (tid == 0) {
@@ -1270,7 +1301,7 @@ __global__ void __launch_bounds__(256) eig_mixed_kept_kernel(const EigTask* __re
     }
   }
   double* out = (double*)view(ar, t.out).base;  // the new bases are float64 (arena C)
-  float* out32 = ar.p[AR_X] ? (float*)ar.p[AR_X] + (t.out & kOffMask) : nullptr;
+  float* out32 = ar->p[AR_X] ? (float*)ar->p[AR_X] + (t.out & kOffMask) : nullptr;
   for (int e = tid; e < t.n_pad * t.kcap; e += nt) {
     out[e] = 0.0;
     if (out32) out32[e] = 0.f;
@@ -1296,9 +1327,8 @@ __global__ void __launch_bounds__(256) eig_mixed_kept_kernel(const EigTask* __re
   }
 }
 
-void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const ArenaSet& a, int32_t* kr,
-                      int32_t* kc, double eps, int trunc, unsigned long long* cap_hits, int max_npad, void* stream) {
-  Arenas ar = to_dev(a);
+void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const Arenas* ar, double eps,
+                      int trunc, int max_npad, void* stream) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(eig_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1312,8 +1342,7 @@ void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const
     // thresholds below float32 eigenvector resolution: float64 Rayleigh-Ritz refinement
     const int nn = max_npad + (max_npad & 1);
     const size_t smem = (size_t)3 * nn * (nn + 1) * sizeof(double);
-    eig_mixed_kernel<<<(unsigned)count, 256, smem, (cudaStream_t)stream>>>(d_eigs, first, ar, kr, kc, eps, trunc,
-                                                                           cap_hits);
+    eig_mixed_kernel<<<(unsigned)count, 256, smem, (cudaStream_t)stream>>>(d_eigs, first, ar, eps, trunc);
     g_launches += 1;
   } else {
     // the level's padded size comes from the rank caps; the actual sizes (children's
@@ -1330,7 +1359,7 @@ void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const
       // (128 threads are enough for nn <= 48: a step has <= 300 block and row tasks)
       if (h > lo) {
         eig_mixed_kept_kernel<<<(unsigned)count, h <= 48 ? 128 : 256, eig_kept_smem(h), (cudaStream_t)stream>>>(
-            d_eigs, first, ar, kr, kc, eps, trunc, cap_hits, lo, h);
+            d_eigs, first, ar, eps, trunc, lo, h);
         g_launches += 1;
       }
       lo = h;
@@ -1339,10 +1368,8 @@ void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const
   }
 }
 
-void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, const ArenaSet& a, int32_t* kr,
-                int32_t* kc, double eps, int trunc, unsigned long long* cap_hits, int max_npad, double* scratch,
-                void* stream) {
-  Arenas ar = to_dev(a);
+void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, const Arenas* ar, double eps, int trunc,
+                int max_npad, double* scratch, void* stream) {
   int nn = max_npad + (max_npad & 1);
   size_t smem = 0;
   int64_t stride = 0;
@@ -1358,8 +1385,7 @@ void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, const Arena
                          (int)(2 * kEigSmemMax * (kEigSmemMax + 1) * sizeof(double)));
     attr = true;
   }
-  eig_kernel<<<(unsigned)count, 256, smem, (cudaStream_t)stream>>>(d_eigs, first, ar, kr, kc, eps, trunc, cap_hits,
-                                                                     scratch, stride);
+  eig_kernel<<<(unsigned)count, 256, smem, (cudaStream_t)stream>>>(d_eigs, first, ar, eps, trunc, scratch, stride);
   g_launches += 1;
 }
 
