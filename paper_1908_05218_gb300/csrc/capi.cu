@@ -659,135 +659,418 @@ h2_status h2_export(h2_handle h, int64_t* sizes, int32_t* kr, int32_t* kc, doubl
   });
 }
 
+}  // extern "C"
+
+namespace {
+
+// One product made ready to run: its plan (built or from the cache), its output
+// handle (reused or new, zeroed in stream order), float copies of A and B if mixed, and
+// its arena table.
+struct Prepared {
+  std::shared_ptr<PlanEntry> ent;
+  h2_matrix* out = nullptr;
+  std::unique_ptr<h2_matrix> fresh;
+  ArenaSet ar;
+  MmpParams prm{};
+  bool trace = false;
+};
+
+Prepared prepare_product(h2_handle A, h2_handle B, double eps, const h2_opts& o, h2_handle existing) {
+  Prepared pr;
+    if (o.trunc != H2_TRUNC_FULL && o.trunc != H2_TRUNC_FORMATTED && !(eps > 0 && eps < 1))
+    throw Error(H2_EINVAL, "eps must lie in (0, 1)");
+  if (!same_structure(*A->m.st, *B->m.st)) throw Error(H2_ESTRUCT, "A and B have different trees or partitions");
+  MmpParams prm{eps, o.trunc, o.rank_cap, o.precision};
+  // plan cache, process-wide
+  PlanKey key{A->m.st.get(), A->m.Kr, A->m.Kc, B->m.Kr, B->m.Kc, o.trunc, o.rank_cap, o.precision};
+  std::shared_ptr<PlanEntry> ent;
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    for (auto it = g_plans.begin(); it != g_plans.end();) {
+      auto sp = it->second.lock();
+      if (!sp) {
+        it = g_plans.erase(it);
+        continue;
+      }
+      if (it->first == key) ent = sp;
+      ++it;
+    }
+  }
+  if (!ent) {
+    ent = std::make_shared<PlanEntry>();
+    Mat Ccaps;
+    Ccaps.st = A->m.st;
+    build_mmp_plan(A->m, B->m, Ccaps, prm, ent->plan);
+    ent->plan.ckr = Ccaps.Kr;
+    ent->plan.ckc = Ccaps.Kc;
+    {
+      Mat probe;
+      probe.st = A->m.st;
+      probe.Kr = Ccaps.Kr;
+      probe.Kc = Ccaps.Kc;
+      int64_t csize = mat_elems(probe);
+      int64_t sizes[kArenas] = {A->m.arena_elems, B->m.arena_elems, csize, ent->plan.region[AR_P],
+                                ent->plan.region[AR_G0], ent->plan.region[AR_G1], ent->plan.region[AR_S],
+                                o.precision == H2_MIXED_FP32 ? probe.off_S[0] : 0};
+      validate_plan(ent->plan, sizes);
+    }
+    upload_plan(ent->plan, o.precision == H2_MIXED_FP32 ? sizeof(float) : sizeof(double));
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    g_plans.push_back({key, ent});
+  }
+  bool held = false;
+  for (auto& p : A->plans_held) held = held || p == ent;
+  if (!held) A->plans_held.push_back(ent);
+  h2_matrix* out = existing;
+  bool reuse = out && out->m.st == A->m.st && out->origin_trunc == o.trunc && out->origin_cap == o.rank_cap &&
+               out->origin_prec == o.precision && out->m.Kr == ent->plan.ckr && out->m.Kc == ent->plan.ckc;
+  std::unique_ptr<h2_matrix> fresh;
+  if (!reuse) {
+    fresh = std::make_unique<h2_matrix>();
+    fresh->m.st = A->m.st;
+    fresh->m.Kr = ent->plan.ckr;
+    fresh->m.Kc = ent->plan.ckc;
+    alloc_mat(fresh->m);
+    fresh->m.stream = o.stream;
+    make_user_map(fresh.get());
+    cudaEventCreate(&fresh->ev0);
+    cudaEventCreate(&fresh->ev1);
+    fresh->origin_A = A;
+    fresh->origin_B = B;
+    fresh->origin_trunc = o.trunc;
+    fresh->origin_cap = o.rank_cap;
+    fresh->origin_prec = o.precision;
+    out = fresh.get();
+  }
+  out->m.stream = o.stream;
+  out->m.ranks_on_host = false;
+  cudaStream_t s = (cudaStream_t)o.stream;
+  cuda_check(cudaEventRecord(out->ev0, s), "event");
+  cuda_check(cudaMemsetAsync(out->m.arena, 0, out->m.arena_elems * sizeof(double), s), "zero C");
+  cuda_check(cudaMemsetAsync(out->m.d_kr, 0, 2 * A->m.st->nnodes() * sizeof(int32_t) + 64, s), "zero ranks");
+  ArenaSet ar;
+  const bool mixed = o.precision == H2_MIXED_FP32;
+  if (mixed) {
+    for (h2_matrix* h : {A, B}) {
+      if (!h->m.arena32) {
+        h->m.arena32 = (float*)dmalloc(h->m.arena_elems * sizeof(float));
+        launch_to_f32(h->m.arena, h->m.arena32, h->m.arena_elems, o.stream);
+        cuda_check(cudaGetLastError(), "convert to float");
+      }
+    }
+    ar.p[AR_A] = A->m.arena32;
+    ar.p[AR_B] = B->m.arena32;
+    if (!out->m.arena32) out->m.arena32 = (float*)dmalloc(std::max<int64_t>(1, out->m.off_S[0]) * sizeof(float));
+    ar.p[AR_X] = out->m.arena32;  // float copy of C's bases, written by the eigen step
+    ar.f32 = (1u << AR_A) | (1u << AR_B) | (1u << AR_P) | (1u << AR_G0) | (1u << AR_G1) | (1u << AR_S) |
+             (1u << AR_X);
+  } else {
+    ar.p[AR_A] = A->m.arena;
+    ar.p[AR_B] = B->m.arena;
+  }
+  ar.p[AR_C] = out->m.arena;
+  for (int a = AR_P; a <= AR_S; ++a) ar.p[a] = ent->plan.d_region[a];
+  ar.rk[RK_AR] = A->m.d_kr;
+  ar.rk[RK_AC] = A->m.d_kc;
+  ar.rk[RK_BR] = B->m.d_kr;
+  ar.rk[RK_BC] = B->m.d_kc;
+  ar.rk[RK_CR] = out->m.d_kr;
+  ar.rk[RK_CC] = out->m.d_kc;
+  out->made_by = ent;
+  out->trace_plan = A->trace_on ? &ent->plan : nullptr;
+  if (A->trace_on) {
+    ar.flops = out->m.d_cap + 1;  // second counter of the handle's counter block
+    cuda_check(cudaMemsetAsync(ar.flops, 0, sizeof(unsigned long long), s), "zero flop counter");
+  }
+  ar.kr = out->m.d_kr;
+  ar.kc = out->m.d_kc;
+  ar.cap_hits = out->m.d_cap;
+  pr.ent = ent;
+  pr.out = out;
+  pr.fresh = std::move(fresh);
+  pr.ar = ar;
+  pr.prm = prm;
+  pr.trace = A->trace_on;
+  return pr;
+}
+
+}  // namespace
+
+extern "C" {
+
 h2_status h2_mmp(h2_handle A, h2_handle B, double eps, const h2_opts* opts, h2_handle* C) {
   if (!A || !B || !C) return fail(H2_EINVAL, "null argument");
   return guarded([&] {
     h2_opts o = defaults(opts);
-    if (o.trunc != H2_TRUNC_FULL && o.trunc != H2_TRUNC_FORMATTED && !(eps > 0 && eps < 1))
-      throw Error(H2_EINVAL, "eps must lie in (0, 1)");
-    if (!same_structure(*A->m.st, *B->m.st)) throw Error(H2_ESTRUCT, "A and B have different trees or partitions");
-    MmpParams prm{eps, o.trunc, o.rank_cap, o.precision};
-    // plan cache, process-wide
-    PlanKey key{A->m.st.get(), A->m.Kr, A->m.Kc, B->m.Kr, B->m.Kc, o.trunc, o.rank_cap, o.precision};
-    std::shared_ptr<PlanEntry> ent;
-    {
-      std::lock_guard<std::mutex> lk(g_cache_mu);
-      for (auto it = g_plans.begin(); it != g_plans.end();) {
-        auto sp = it->second.lock();
-        if (!sp) {
-          it = g_plans.erase(it);
-          continue;
-        }
-        if (it->first == key) ent = sp;
-        ++it;
-      }
-    }
-    if (!ent) {
-      ent = std::make_shared<PlanEntry>();
-      Mat Ccaps;
-      Ccaps.st = A->m.st;
-      build_mmp_plan(A->m, B->m, Ccaps, prm, ent->plan);
-      ent->plan.ckr = Ccaps.Kr;
-      ent->plan.ckc = Ccaps.Kc;
-      {
-        Mat probe;
-        probe.st = A->m.st;
-        probe.Kr = Ccaps.Kr;
-        probe.Kc = Ccaps.Kc;
-        int64_t csize = mat_elems(probe);
-        int64_t sizes[kArenas] = {A->m.arena_elems, B->m.arena_elems, csize, ent->plan.region[AR_P],
-                                  ent->plan.region[AR_G0], ent->plan.region[AR_G1], ent->plan.region[AR_S],
-                                  o.precision == H2_MIXED_FP32 ? probe.off_S[0] : 0};
-        validate_plan(ent->plan, sizes);
-      }
-      upload_plan(ent->plan, o.precision == H2_MIXED_FP32 ? sizeof(float) : sizeof(double));
-      std::lock_guard<std::mutex> lk(g_cache_mu);
-      g_plans.push_back({key, ent});
-    }
-    bool held = false;
-    for (auto& p : A->plans_held) held = held || p == ent;
-    if (!held) A->plans_held.push_back(ent);
-    h2_matrix* out = *C;
-    bool reuse = out && out->m.st == A->m.st && out->origin_trunc == o.trunc && out->origin_cap == o.rank_cap &&
-                 out->origin_prec == o.precision && out->m.Kr == ent->plan.ckr && out->m.Kc == ent->plan.ckc;
-    std::unique_ptr<h2_matrix> fresh;
-    if (!reuse) {
-      fresh = std::make_unique<h2_matrix>();
-      fresh->m.st = A->m.st;
-      fresh->m.Kr = ent->plan.ckr;
-      fresh->m.Kc = ent->plan.ckc;
-      alloc_mat(fresh->m);
-      fresh->m.stream = o.stream;
-      make_user_map(fresh.get());
-      cudaEventCreate(&fresh->ev0);
-      cudaEventCreate(&fresh->ev1);
-      fresh->origin_A = A;
-      fresh->origin_B = B;
-      fresh->origin_trunc = o.trunc;
-      fresh->origin_cap = o.rank_cap;
-      fresh->origin_prec = o.precision;
-      out = fresh.get();
-    }
-    out->m.stream = o.stream;
-    out->m.ranks_on_host = false;
-    cudaStream_t s = (cudaStream_t)o.stream;
-    cuda_check(cudaEventRecord(out->ev0, s), "event");
-    cuda_check(cudaMemsetAsync(out->m.arena, 0, out->m.arena_elems * sizeof(double), s), "zero C");
-    cuda_check(cudaMemsetAsync(out->m.d_kr, 0, 2 * A->m.st->nnodes() * sizeof(int32_t) + 64, s), "zero ranks");
-    ArenaSet ar;
-    const bool mixed = o.precision == H2_MIXED_FP32;
-    if (mixed) {
-      for (h2_matrix* h : {A, B}) {
-        if (!h->m.arena32) {
-          h->m.arena32 = (float*)dmalloc(h->m.arena_elems * sizeof(float));
-          launch_to_f32(h->m.arena, h->m.arena32, h->m.arena_elems, o.stream);
-          cuda_check(cudaGetLastError(), "convert to float");
-        }
-      }
-      ar.p[AR_A] = A->m.arena32;
-      ar.p[AR_B] = B->m.arena32;
-      if (!out->m.arena32) out->m.arena32 = (float*)dmalloc(std::max<int64_t>(1, out->m.off_S[0]) * sizeof(float));
-      ar.p[AR_X] = out->m.arena32;  // float copy of C's bases, written by the eigen step
-      ar.f32 = (1u << AR_A) | (1u << AR_B) | (1u << AR_P) | (1u << AR_G0) | (1u << AR_G1) | (1u << AR_S) |
-               (1u << AR_X);
-    } else {
-      ar.p[AR_A] = A->m.arena;
-      ar.p[AR_B] = B->m.arena;
-    }
-    ar.p[AR_C] = out->m.arena;
-    for (int a = AR_P; a <= AR_S; ++a) ar.p[a] = ent->plan.d_region[a];
-    ar.rk[RK_AR] = A->m.d_kr;
-    ar.rk[RK_AC] = A->m.d_kc;
-    ar.rk[RK_BR] = B->m.d_kr;
-    ar.rk[RK_BC] = B->m.d_kc;
-    ar.rk[RK_CR] = out->m.d_kr;
-    ar.rk[RK_CC] = out->m.d_kc;
-    out->made_by = ent;
-    out->trace_plan = A->trace_on ? &ent->plan : nullptr;
-    if (A->trace_on) {
-      ar.flops = out->m.d_cap + 1;  // second counter of the handle's counter block
-      cuda_check(cudaMemsetAsync(ar.flops, 0, sizeof(unsigned long long), s), "zero flop counter");
-    }
-    ar.kr = out->m.d_kr;
-    ar.kc = out->m.d_kc;
-    ar.cap_hits = out->m.d_cap;
+    Prepared pr = prepare_product(A, B, eps, o, *C);
+    h2_matrix* out = pr.out;
     Arenas* d_ars = arena_slot(out, 0);
-    upload_arenas(d_ars, to_arenas(ar), o.stream);
-    run_plan(ent->plan, ar, d_ars, prm, o.stream, false, A->trace_on ? &out->trace : nullptr);
-    cuda_check(cudaEventRecord(out->ev1, s), "event");
+    upload_arenas(d_ars, to_arenas(pr.ar), o.stream);
+    run_plan(pr.ent->plan, pr.ar, d_ars, pr.prm, o.stream, false, pr.trace ? &out->trace : nullptr);
+    cuda_check(cudaEventRecord(out->ev1, (cudaStream_t)o.stream), "event");
     out->timed = true;
-    if (fresh) *C = fresh.release();
+    if (pr.fresh) *C = pr.fresh.release();
   });
 }
+
+}  // extern "C"
+
+namespace {
+
+// ------------------------------------------------------------ batched products
+// The products of a batch run merged: every product's program is a chain of launch
+// groups, and round r of the batch takes group r of every product at once, so one
+// GEMM launch (and one eigen launch per eigen kernel) serves all products of a round.
+// Segments and eigen tasks carry their product's index into a table of arena sets.  A
+// product's own order of groups, and each segment's order of items, are kept, so the
+// results are bit for bit those of single products.  Products that share a plan share
+// its work regions, so such a batch runs as several groups of distinct plans.  The
+// merged program is cached per (plans, eps, truncation) and, from its second use, runs
+// as one captured CUDA graph; only the arena tables change between calls and they are
+// written just before the graph in stream order.
+struct Round {
+  int64_t gemm_first = 0, gemm_count = 0;
+  int gemm_aux = 1, gemm_aux2 = 1;
+  int64_t eigm_first = 0, eigm_count = 0;  // mixed-precision eigen kernels
+  int eigm_aux = 1;
+  int64_t eigd_first = 0, eigd_count = 0;  // float64 eigen kernel
+  int eigd_aux = 1;
+  std::vector<std::pair<int, size_t>> memsets;      // (instance, launch of its plan)
+  std::vector<std::pair<int, int64_t>> copy_ranks;  // (instance, node count)
+};
+
+struct BatchEntry {
+  std::vector<std::shared_ptr<PlanEntry>> plans;
+  double eps = 0;
+  int trunc = 0, precision = 0;
+  Seg* d_segs = nullptr;
+  Item* d_items = nullptr;
+  EigTask* d_eigs = nullptr;
+  double* d_scratch = nullptr;
+  Arenas* d_ars = nullptr;
+  std::vector<Round> rounds;
+  std::vector<ArenaSet> mem_ar;  // work-region pointers of each instance (for memsets)
+  int uses = 0;
+  long long kernels = 0;  // kernels of one run of the merged program
+  cudaGraphExec_t graph = nullptr;
+  ~BatchEntry() {
+    if (graph) cudaGraphExecDestroy(graph);
+    for (void* q : {(void*)d_segs, (void*)d_items, (void*)d_eigs, (void*)d_scratch, (void*)d_ars})
+      if (q) cudaFree(q);
+  }
+};
+
+std::mutex g_batch_mu;
+std::vector<std::shared_ptr<BatchEntry>> g_batches;  // most recent last, at most 4 kept
+
+std::shared_ptr<BatchEntry> build_batch(const std::vector<Prepared*>& grp) {
+  auto be = std::make_shared<BatchEntry>();
+  const MmpParams& prm = grp[0]->prm;
+  be->eps = prm.eps;
+  be->trunc = prm.trunc;
+  be->precision = prm.precision;
+  const bool mixed = prm.precision == H2_MIXED_FP32;
+  std::vector<Seg> segs;
+  std::vector<Item> items;
+  std::vector<EigTask> eigs;
+  size_t nr = 0;
+  for (Prepared* p : grp) {
+    be->plans.push_back(p->ent);
+    nr = std::max(nr, p->ent->plan.launches.size());
+  }
+  int64_t scratch = 0;
+  for (size_t r = 0; r < nr; ++r) {
+    Round rd;
+    rd.gemm_first = (int64_t)segs.size();
+    std::vector<EigTask> em, ed;
+    for (size_t i = 0; i < grp.size(); ++i) {
+      const Plan& P = grp[i]->ent->plan;
+      if (r >= P.launches.size()) continue;
+      const Launch& L = P.launches[r];
+      if (L.kind == Launch::MEMSET) {
+        rd.memsets.push_back({(int)i, r});
+      } else if (L.kind == Launch::COPY_RANKS) {
+        rd.copy_ranks.push_back({(int)i, L.elems});
+      } else if (L.kind == Launch::GEMM) {
+        for (int64_t q = L.first; q < L.first + L.count; ++q) {
+          Seg sg = P.segs[q];
+          const int32_t f = (int32_t)items.size();
+          items.insert(items.end(), P.items.begin() + sg.first, P.items.begin() + sg.first + sg.count);
+          sg.first = f;
+          sg.inst = (int16_t)i;
+          segs.push_back(sg);
+        }
+        rd.gemm_aux = std::max(rd.gemm_aux, L.aux);
+        rd.gemm_aux2 = std::max(rd.gemm_aux2, L.aux2);
+      } else if (L.kind == Launch::EIG) {
+        const bool m = mixed && L.aux <= 96;
+        for (int64_t q = L.first; q < L.first + L.count; ++q) {
+          EigTask e = P.eigs[q];
+          e.inst = (int16_t)i;
+          (m ? em : ed).push_back(e);
+        }
+        if (m) rd.eigm_aux = std::max(rd.eigm_aux, L.aux);
+        else rd.eigd_aux = std::max(rd.eigd_aux, L.aux);
+      }
+      if (items.size() > (size_t)INT32_MAX) throw Error(H2_EUNSUPPORTED, "batch too large for one merged program");
+    }
+    rd.gemm_count = (int64_t)segs.size() - rd.gemm_first;
+    rd.eigm_first = (int64_t)eigs.size();
+    rd.eigm_count = (int64_t)em.size();
+    eigs.insert(eigs.end(), em.begin(), em.end());
+    rd.eigd_first = (int64_t)eigs.size();
+    rd.eigd_count = (int64_t)ed.size();
+    eigs.insert(eigs.end(), ed.begin(), ed.end());
+    const int nn = rd.eigd_aux + (rd.eigd_aux & 1);
+    if (rd.eigd_count && nn > 112) scratch = std::max<int64_t>(scratch, rd.eigd_count * 2LL * nn * (nn + 1));
+    be->rounds.push_back(std::move(rd));
+  }
+  be->d_segs = (Seg*)dmalloc(std::max<size_t>(1, segs.size()) * sizeof(Seg));
+  be->d_items = (Item*)dmalloc(std::max<size_t>(1, items.size()) * sizeof(Item));
+  be->d_eigs = (EigTask*)dmalloc(std::max<size_t>(1, eigs.size()) * sizeof(EigTask));
+  be->d_scratch = (double*)dmalloc(std::max<int64_t>(1, scratch) * sizeof(double));
+  be->d_ars = (Arenas*)dmalloc(grp.size() * sizeof(Arenas));
+  if (!segs.empty())
+    cuda_check(cudaMemcpy(be->d_segs, segs.data(), segs.size() * sizeof(Seg), cudaMemcpyHostToDevice), "upload batch");
+  if (!items.empty())
+    cuda_check(cudaMemcpy(be->d_items, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice),
+               "upload batch");
+  if (!eigs.empty())
+    cuda_check(cudaMemcpy(be->d_eigs, eigs.data(), eigs.size() * sizeof(EigTask), cudaMemcpyHostToDevice),
+               "upload batch");
+  for (Prepared* p : grp) be->mem_ar.push_back(p->ar);
+  return be;
+}
+
+// the launches of a merged program, in order, on stream s
+void run_batch(const BatchEntry& be, void* s) {
+  const bool mixed = be.precision == H2_MIXED_FP32;
+  for (const Round& rd : be.rounds) {
+    for (auto& m : rd.memsets) {
+      const Launch& L = be.plans[m.first]->plan.launches[m.second];
+      if (L.elems == 0) continue;
+      const ArenaSet& ar = be.mem_ar[m.first];
+      const int a = arena_of(L.off);
+      char* p = (char*)ar.p[a] + offset_of(L.off) * ar.esize(a);
+      cuda_check(cudaMemsetAsync(p, 0, L.elems * ar.esize(a), (cudaStream_t)s), "memset");
+    }
+    for (auto& c : rd.copy_ranks) launch_copy_ranks(be.d_ars, c.first, c.second, s);
+    if (rd.gemm_count)
+      launch_gemm(be.d_segs, be.d_items, rd.gemm_first, rd.gemm_count, be.d_ars, rd.gemm_aux, rd.gemm_aux2, mixed,
+                  s);
+    if (rd.eigm_count)
+      launch_eig_mixed(be.d_eigs, rd.eigm_first, rd.eigm_count, be.d_ars, be.eps, be.trunc, rd.eigm_aux, s);
+    if (rd.eigd_count)
+      launch_eig(be.d_eigs, rd.eigd_first, rd.eigd_count, be.d_ars, be.eps, be.trunc, rd.eigd_aux, be.d_scratch, s);
+    cuda_check(cudaGetLastError(), "batched launch");
+  }
+}
+
+void run_group(std::vector<Prepared*>& grp, void* stream) {
+  std::shared_ptr<BatchEntry> be;
+  {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (auto& e : g_batches) {
+      if (e->plans.size() != grp.size() || e->eps != grp[0]->prm.eps || e->trunc != grp[0]->prm.trunc ||
+          e->precision != grp[0]->prm.precision)
+        continue;
+      bool same = true;
+      for (size_t i = 0; i < grp.size() && same; ++i) same = e->plans[i] == grp[i]->ent;
+      if (same) be = e;
+    }
+  }
+  if (!be) {
+    be = build_batch(grp);
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    g_batches.push_back(be);
+    if (g_batches.size() > 4) g_batches.erase(g_batches.begin());
+  }
+  // the work-region pointers are the plans' own (fixed); the tables change per call
+  for (size_t i = 0; i < grp.size(); ++i) upload_arenas(be->d_ars + i, to_arenas(grp[i]->ar), stream);
+  cuda_check(cudaGetLastError(), "arena tables");
+  if (be->graph) {
+    cuda_check(cudaGraphLaunch(be->graph, (cudaStream_t)stream), "graph launch");
+    add_kernel_launches(be->kernels);
+  } else {
+    const unsigned long long k0 = kernel_launches();
+    run_batch(*be, stream);  // first use: launches in order (this also sets kernel attributes)
+    be->kernels = (long long)(kernel_launches() - k0);
+    // capture the same launches once, on a private stream, for later calls
+    cudaStream_t cs;
+    cuda_check(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      try {
+        run_batch(*be, cs);
+        add_kernel_launches(-be->kernels);  // captured, not launched
+      } catch (...) {
+        cudaStreamEndCapture(cs, &g);
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cs);
+        throw;
+      }
+      e = cudaStreamEndCapture(cs, &g);
+    }
+    if (e == cudaSuccess && g) e = cudaGraphInstantiate(&be->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {  // no graph: later calls launch in order
+      be->graph = nullptr;
+      cudaGetLastError();
+    }
+  }
+  ++be->uses;
+}
+
+}  // namespace
+
+extern "C" {
 
 h2_status h2_mmp_batched(const h2_handle* A, const h2_handle* B, int32_t count, double eps, const h2_opts* opts,
                          h2_handle* C) {
   if (!A || !B || !C || count < 0) return fail(H2_EINVAL, "null argument or negative count");
-  for (int32_t i = 0; i < count; ++i) {
-    h2_status s = h2_mmp(A[i], B[i], eps, opts, &C[i]);
-    if (s != H2_OK) return fail(s, "instance " + std::to_string(i) + ": " + g_err);
+  for (int32_t i = 0; i < count; ++i)
+    if (!A[i] || !B[i]) return fail(H2_EINVAL, "null handle at instance " + std::to_string(i));
+  bool traced = false;
+  for (int32_t i = 0; i < count; ++i) traced = traced || A[i]->trace_on;
+  if (traced || count > 32767) {  // traced products keep their per-launch events: one at a time
+    for (int32_t i = 0; i < count; ++i) {
+      h2_status st = h2_mmp(A[i], B[i], eps, opts, &C[i]);
+      if (st != H2_OK) return fail(st, "instance " + std::to_string(i) + ": " + g_err);
+    }
+    return H2_OK;
   }
-  return H2_OK;
+  return guarded([&] {
+    h2_opts o = defaults(opts);
+    std::vector<Prepared> pr(count);
+    for (int32_t i = 0; i < count; ++i) {
+      try {
+        pr[i] = prepare_product(A[i], B[i], eps, o, C[i]);
+      } catch (Error& e) {
+        throw Error(e.code, "instance " + std::to_string(i) + ": " + e.what());
+      }
+    }
+    // groups of distinct plans (a plan's work regions serve one product at a time)
+    std::vector<char> done(count, 0);
+    for (int32_t first = 0; first < count; ++first) {
+      if (done[first]) continue;
+      std::vector<Prepared*> grp;
+      std::vector<const PlanEntry*> used;
+      for (int32_t i = first; i < count; ++i) {
+        if (done[i] || std::find(used.begin(), used.end(), pr[i].ent.get()) != used.end()) continue;
+        used.push_back(pr[i].ent.get());
+        grp.push_back(&pr[i]);
+        done[i] = 1;
+      }
+      run_group(grp, o.stream);
+    }
+    for (int32_t i = 0; i < count; ++i) {
+      cuda_check(cudaEventRecord(pr[i].out->ev1, (cudaStream_t)o.stream), "event");
+      pr[i].out->timed = true;
+      if (pr[i].fresh) C[i] = pr[i].fresh.release();
+    }
+  });
 }
 
 h2_status h2_matvec(h2_handle h, const double* x, double* y, int64_t nrhs) {

@@ -244,6 +244,7 @@ void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, const Arena
 // formatted product: C's ranks are A's row ranks and B's column ranks (instance inst)
 void launch_copy_ranks(const Arenas* d_ars, int inst, int64_t n, void* stream);
 unsigned long long kernel_launches();  // kernels launched by this library so far
+void add_kernel_launches(long long d);   // graph replays add their kernels; captures take theirs back
 void launch_to_f32(const double* src, float* dst, int64_t n, void* stream);
 void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const Arenas* d_ars, double eps,
                       int trunc, int max_npad, void* stream);

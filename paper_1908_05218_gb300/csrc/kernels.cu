@@ -15,6 +15,7 @@ namespace h2 {
 // kernel launches made by this library in this process (every launch site below adds)
 static std::atomic<unsigned long long> g_launches{0};
 unsigned long long kernel_launches() { return g_launches.load(); }
+void add_kernel_launches(long long d) { g_launches += (unsigned long long)d; }
 
 __device__ __forceinline__ int arena_idx(int64_t t) { return (int)((t >> kTagShift) & 7); }
 

@@ -207,3 +207,30 @@ def test_mixed_product_is_deterministic_with_odd_leaf_sizes(lib, n):
     for e in ex[1:]:
         for f in ("kr", "kc", "vr", "vc", "er", "ec", "s", "f"):
             np.testing.assert_array_equal(getattr(e, f), getattr(ex[0], f))
+
+
+@pytest.mark.parametrize("precision,trunc", [("mixed", "paper"), ("fp64", "paper"), ("mixed", "formatted")])
+def test_batched_merged_and_replayed_equal_single(lib, precision, trunc):
+    # instances of uneven size in one merged program; the repeated instance shares its
+    # plan with the first and runs in a second group; the second call replays the
+    # captured graph.  Every result equals its single product bit for bit.
+    import torch
+    prec = lib.MIXED_FP32 if precision == "mixed" else lib.FP64
+    specs = [(900, 11, "box"), (1700, 12, "box"), (900, 11, "box"), (1200, 13, "uniform")]
+    hs = []
+    for n, seed, kind in specs:
+        pts = inputs.stretched_box(n, seed=seed) if kind == "box" else inputs.workload_uniform(n, seed=seed).points
+        hs.append(lib.h2_build(pts, inputs.laplace_spec(n ** (-1 / 3)), 32, 1.0, 1e-4))
+    singles = [h.mmp(h, 1e-4, precision=prec, trunc=trunc) for h in hs]
+    n0 = lib.kernel_launches()
+    cs = lib.h2_mmp_batched(hs, hs, 1e-4, precision=prec, trunc=trunc)
+    n1 = lib.kernel_launches()
+    cs2 = lib.h2_mmp_batched(hs, hs, 1e-4, precision=prec, trunc=trunc, outs=cs)
+    n2 = lib.kernel_launches()
+    assert all(a is b for a, b in zip(cs, cs2))
+    # the replay counts the kernels of the captured program
+    assert n2 - n1 == n1 - n0 > 0
+    for h, c, s in zip(hs, cs2, singles):
+        x = torch.from_numpy(inputs.standard_normal((h.n, 3), seed=5)).cuda()
+        assert torch.equal(c.matvec(x), s.matvec(x))
+        assert c.info()["cap_hits"] == s.info()["cap_hits"]
