@@ -6,7 +6,7 @@ merges, the top-down split) on inputs resident in device memory.  The metric is
 algorithmic throughput: (bytes of A + B + C at their actual ranks) / product time,
 in GB/s, with the product time itself reported beside it.
 
-  python bench.py [--gpus N --steps K --warmup W] [--workload cubes16x16|cubes4x4]
+  python bench.py [--gpus N --steps K --warmup W] [--workload cubes16x16|cubes4x4|batched48]
                   [--precision fp64|mixed] [--impl ours|reference]
 
 --impl reference times the CPU oracle (the plain float64 restatement of the method)
@@ -150,13 +150,87 @@ def oracle_sample(steps: int):
     print(json.dumps({"t": t, "bytes": nbytes, "n": int(wa.points.shape[0]), "steps": len(times)}))
 
 
+def batched_main(args):
+    """Config 4: 48 independent products A_i x A_i of uneven size (N_i log-uniform in
+    [4096, 131072], points in stretched boxes), in chunks of 8 that fit the device
+    memory together with their outputs.  Each chunk is one h2_mmp_batched call (one
+    CUDA graph with a branch per product, captured once and replayed), timed against
+    the same products one h2_mmp call at a time; the value is the bytes of all 48
+    products over the sum of the chunks' times."""
+    import torch
+
+    from paper_1908_05218_gb300 import h2 as lib
+    from paper_1908_05218_gb300 import inputs
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    lib.load()
+    prec = lib.FP64 if args.precision == "fp64" else lib.MIXED_FP32
+    ws = inputs.workload_batch(48)
+    eps, chunk = 1e-4, 8
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tot_ms = tot_single = 0.0
+    nbytes = 0
+    nk = 0
+    errs, ns = [], []
+    build_s = 0.0
+    with Clocks(0) as clk:
+        for c0 in range(0, len(ws), chunk):
+            part = ws[c0:c0 + chunk]
+            t0 = time.time()
+            hs = [lib.h2_build(w.points, w.kernel, LEAF, ETA, 1e-4) for w in part]
+            build_s += time.time() - t0
+            cs = lib.h2_mmp_batched(hs, hs, eps, precision=prec, trunc=args.trunc)
+            for _ in range(args.warmup):
+                cs = lib.h2_mmp_batched(hs, hs, eps, precision=prec, trunc=args.trunc, outs=cs)
+            torch.cuda.synchronize()
+            n0 = lib.kernel_launches()
+            e0.record(stream)
+            for _ in range(args.steps):
+                cs = lib.h2_mmp_batched(hs, hs, eps, precision=prec, trunc=args.trunc, outs=cs)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            nk += lib.kernel_launches() - n0
+            tot_ms += e0.elapsed_time(e1) / args.steps
+            singles = [h.mmp(h, eps, precision=prec, trunc=args.trunc) for h in hs]
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(args.steps):
+                singles = [h.mmp(h, eps, precision=prec, trunc=args.trunc, out=c) for h, c in zip(hs, singles)]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot_single += e0.elapsed_time(e1) / args.steps
+            for h, c, s_ in zip(hs, cs, singles):
+                nbytes += 2 * h.info()["bytes_stored"] + c.info()["bytes_stored"]
+                x = torch.from_numpy(inputs.standard_normal((h.n, 4), seed=1)).cuda()
+                y = h.matvec(h.matvec(x))
+                errs.append(float(torch.linalg.norm(c.matvec(x) - y) / torch.linalg.norm(y)))
+                assert torch.equal(c.matvec(x), s_.matvec(x)), "merged and single products differ"
+                ns.append(h.n)
+            for h in singles + cs + hs:
+                h.destroy()
+            torch.cuda.empty_cache()
+    print(json.dumps({
+        "metric": "H2-MMP throughput, 48 independent products (bytes of A+A+C at actual ranks / batch time)",
+        "value": nbytes / (tot_ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+        "config": {"workload": "48 products A_i x A_i, N_i log-uniform in [4096, 131072] (total %d), points "
+                               "uniform in boxes with sides (1, s2, s3), s log-uniform in [1, 8]; 1/(4 pi r), "
+                               "leaf 32, eta 1, eps %g (%s rule)" % (sum(ns), eps, args.trunc),
+                   "parallelism": "6 chunks of 8; per chunk one CUDA graph, one concurrent branch per product"},
+        "ms_one_call_per_product": tot_single, "speedup_vs_one_call_per_product": tot_single / tot_ms,
+        "gpu_launches_per_step": nk // args.steps, "max_rel_err_vs_exact_h2_matvecs": max(errs),
+        "merged_equals_single": True, "n_min": min(ns), "n_max": max(ns), "build_s": build_s,
+        "bytes_alg": nbytes, "clocks": clk.summary()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cubes16x16", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="cubes16x16", choices=list(WORKLOADS) + ["batched48"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--trunc", default="paper", choices=["paper", "sv", "formatted"],
                     help="truncation rule; 'formatted' = fixed bases (the paper's comparison method)")
@@ -171,6 +245,11 @@ def main():
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.workload == "batched48":
+        if args.impl == "reference" or world > 1:
+            raise SystemExit("batched48 runs on one GPU, own implementation only")
+        batched_main(args)
+        return
     nx, ny, ppc, eps, desc = WORKLOADS[args.workload]
     metric = "H2-MMP throughput (bytes of A+B+C at actual ranks / product time)"
 

@@ -470,7 +470,7 @@ void validate_plan(const Plan& P, const int64_t sizes[kArenas]) {
   if (nseg != P.segs.size() || neig != P.eigs.size()) throw Error(H2_EINTERNAL, "plan work outside its launches");
 }
 
-void upload_plan(Plan& P, size_t region_esize) {
+void upload_plan(Plan& P, size_t region_esize, bool own_regions) {
   P.d_segs = (Seg*)dmalloc(std::max<size_t>(1, P.segs.size()) * sizeof(Seg));
   P.d_items = (Item*)dmalloc(std::max<size_t>(1, P.items.size()) * sizeof(Item));
   P.d_eigs = (EigTask*)dmalloc(std::max<size_t>(1, P.eigs.size()) * sizeof(EigTask));
@@ -503,7 +503,9 @@ void upload_plan(Plan& P, size_t region_esize) {
     }
   }
   P.d_scratch = (double*)dmalloc(std::max<int64_t>(1, scratch) * sizeof(double));
-  for (int a = AR_P; a <= AR_S; ++a) P.d_region[a] = (double*)dmalloc(std::max<int64_t>(1, P.region[a]) * region_esize);
+  P.region_esize = (int)region_esize;
+  if (own_regions)
+    for (int a = AR_P; a <= AR_S; ++a) P.d_region[a] = (double*)dmalloc(std::max<int64_t>(1, P.region[a]) * region_esize);
 }
 
 void free_plan(Plan& P) {
@@ -663,6 +665,51 @@ h2_status h2_export(h2_handle h, int64_t* sizes, int32_t* kr, int32_t* kc, doubl
 
 namespace {
 
+// ------------------------------------------------------------ work space
+// The work regions of a product (P, G0, G1, S) hold nothing between products, so they
+// come from one device buffer per stream, grown on demand and reused by every product
+// on that stream (a batch takes one slice per product of a merged group).  `gen`
+// changes when the buffer moves, which retires programs captured with the old one.
+struct Workspace {
+  char* base = nullptr;
+  size_t bytes = 0;
+  uint64_t gen = 0;
+};
+std::mutex g_ws_mu;
+std::map<void*, Workspace> g_ws;
+
+size_t region_bytes(const Plan& P) {
+  size_t b = 0;
+  for (int a = AR_P; a <= AR_S; ++a) b += ((size_t)std::max<int64_t>(1, P.region[a]) * P.region_esize + 255) & ~size_t(255);
+  return b;
+}
+
+Workspace workspace(void* stream, size_t bytes) {
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  Workspace& w = g_ws[stream];
+  if (w.bytes < bytes) {
+    if (w.base) {
+      cuda_check(cudaDeviceSynchronize(), "synchronise");
+      cudaFree(w.base);
+      w.base = nullptr;
+      w.bytes = 0;
+    }
+    w.base = (char*)dmalloc(bytes);
+    w.bytes = bytes;
+    ++w.gen;
+  }
+  return w;
+}
+
+// points the work regions of `ar` at `base` (region_bytes(P) bytes)
+void place_regions(const Plan& P, ArenaSet& ar, char* base) {
+  size_t off = 0;
+  for (int a = AR_P; a <= AR_S; ++a) {
+    ar.p[a] = base + off;
+    off += ((size_t)std::max<int64_t>(1, P.region[a]) * P.region_esize + 255) & ~size_t(255);
+  }
+}
+
 // One product made ready to run: its plan (built or from the cache), its output
 // handle (reused or new, zeroed in stream order), float copies of A and B if mixed, and
 // its arena table.
@@ -714,7 +761,7 @@ Prepared prepare_product(h2_handle A, h2_handle B, double eps, const h2_opts& o,
                                 o.precision == H2_MIXED_FP32 ? probe.off_S[0] : 0};
       validate_plan(ent->plan, sizes);
     }
-    upload_plan(ent->plan, o.precision == H2_MIXED_FP32 ? sizeof(float) : sizeof(double));
+    upload_plan(ent->plan, o.precision == H2_MIXED_FP32 ? sizeof(float) : sizeof(double), false);
     std::lock_guard<std::mutex> lk(g_cache_mu);
     g_plans.push_back({key, ent});
   }
@@ -769,7 +816,6 @@ Prepared prepare_product(h2_handle A, h2_handle B, double eps, const h2_opts& o,
     ar.p[AR_B] = B->m.arena;
   }
   ar.p[AR_C] = out->m.arena;
-  for (int a = AR_P; a <= AR_S; ++a) ar.p[a] = ent->plan.d_region[a];
   ar.rk[RK_AR] = A->m.d_kr;
   ar.rk[RK_AC] = A->m.d_kc;
   ar.rk[RK_BR] = B->m.d_kr;
@@ -804,6 +850,7 @@ h2_status h2_mmp(h2_handle A, h2_handle B, double eps, const h2_opts* opts, h2_h
     h2_opts o = defaults(opts);
     Prepared pr = prepare_product(A, B, eps, o, *C);
     h2_matrix* out = pr.out;
+    place_regions(pr.ent->plan, pr.ar, workspace(o.stream, region_bytes(pr.ent->plan)).base);
     Arenas* d_ars = arena_slot(out, 0);
     upload_arenas(d_ars, to_arenas(pr.ar), o.stream);
     run_plan(pr.ent->plan, pr.ar, d_ars, pr.prm, o.stream, false, pr.trace ? &out->trace : nullptr);
@@ -818,161 +865,95 @@ h2_status h2_mmp(h2_handle A, h2_handle B, double eps, const h2_opts* opts, h2_h
 namespace {
 
 // ------------------------------------------------------------ batched products
-// The products of a batch run merged: every product's program is a chain of launch
-// groups, and round r of the batch takes group r of every product at once, so one
-// GEMM launch (and one eigen launch per eigen kernel) serves all products of a round.
-// Segments and eigen tasks carry their product's index into a table of arena sets.  A
-// product's own order of groups, and each segment's order of items, are kept, so the
-// results are bit for bit those of single products.  Products that share a plan share
-// its work regions, so such a batch runs as several groups of distinct plans.  The
-// merged program is cached per (plans, eps, truncation) and, from its second use, runs
-// as one captured CUDA graph; only the arena tables change between calls and they are
-// written just before the graph in stream order.
-struct Round {
-  int64_t gemm_first = 0, gemm_count = 0;
-  int gemm_aux = 1, gemm_aux2 = 1;
-  int64_t eigm_first = 0, eigm_count = 0;  // mixed-precision eigen kernels
-  int eigm_aux = 1;
-  int64_t eigd_first = 0, eigd_count = 0;  // float64 eigen kernel
-  int eigd_aux = 1;
-  std::vector<std::pair<int, size_t>> memsets;      // (instance, launch of its plan)
-  std::vector<std::pair<int, int64_t>> copy_ranks;  // (instance, node count)
-};
-
+// The products of a batch are independent, so they run as one CUDA graph with one
+// branch per product: each branch is that product's own program (the same launches as
+// h2_mmp, on its plan's arrays), captured on its own stream forked from a common
+// start, and the branches join at the end.  The GPU runs the branches concurrently
+// (one product's eigen step beside another's GEMMs).  Each product of a group takes its
+// own slice of the work space.  The graph is captured once per (plans, work space, eps,
+// truncation, precision) and replayed; only the arena tables change between calls and
+// they are written just before the graph in stream order.  A product's launches and
+// each segment's order of items are those of h2_mmp, so the results are bit for bit
+// those of single products.
 struct BatchEntry {
   std::vector<std::shared_ptr<PlanEntry>> plans;
+  char* ws_base = nullptr;  // the work space the graph was captured with
+  uint64_t ws_gen = 0;
   double eps = 0;
   int trunc = 0, precision = 0;
-  Seg* d_segs = nullptr;
-  Item* d_items = nullptr;
-  EigTask* d_eigs = nullptr;
-  double* d_scratch = nullptr;
-  Arenas* d_ars = nullptr;
-  std::vector<Round> rounds;
-  std::vector<ArenaSet> mem_ar;  // work-region pointers of each instance (for memsets)
-  int uses = 0;
-  long long kernels = 0;  // kernels of one run of the merged program
+  Arenas* d_ars = nullptr;  // one table per product
+  long long kernels = 0;    // kernels of one run of the graph
   cudaGraphExec_t graph = nullptr;
   ~BatchEntry() {
     if (graph) cudaGraphExecDestroy(graph);
-    for (void* q : {(void*)d_segs, (void*)d_items, (void*)d_eigs, (void*)d_scratch, (void*)d_ars})
-      if (q) cudaFree(q);
+    if (d_ars) cudaFree(d_ars);
   }
 };
 
 std::mutex g_batch_mu;
 std::vector<std::shared_ptr<BatchEntry>> g_batches;  // most recent last, at most 4 kept
 
-std::shared_ptr<BatchEntry> build_batch(const std::vector<Prepared*>& grp) {
+std::shared_ptr<BatchEntry> capture_batch(const std::vector<Prepared*>& grp) {
   auto be = std::make_shared<BatchEntry>();
-  const MmpParams& prm = grp[0]->prm;
-  be->eps = prm.eps;
-  be->trunc = prm.trunc;
-  be->precision = prm.precision;
-  const bool mixed = prm.precision == H2_MIXED_FP32;
-  std::vector<Seg> segs;
-  std::vector<Item> items;
-  std::vector<EigTask> eigs;
-  size_t nr = 0;
-  for (Prepared* p : grp) {
-    be->plans.push_back(p->ent);
-    nr = std::max(nr, p->ent->plan.launches.size());
-  }
-  int64_t scratch = 0;
-  for (size_t r = 0; r < nr; ++r) {
-    Round rd;
-    rd.gemm_first = (int64_t)segs.size();
-    std::vector<EigTask> em, ed;
-    for (size_t i = 0; i < grp.size(); ++i) {
-      const Plan& P = grp[i]->ent->plan;
-      if (r >= P.launches.size()) continue;
-      const Launch& L = P.launches[r];
-      if (L.kind == Launch::MEMSET) {
-        rd.memsets.push_back({(int)i, r});
-      } else if (L.kind == Launch::COPY_RANKS) {
-        rd.copy_ranks.push_back({(int)i, L.elems});
-      } else if (L.kind == Launch::GEMM) {
-        for (int64_t q = L.first; q < L.first + L.count; ++q) {
-          Seg sg = P.segs[q];
-          const int32_t f = (int32_t)items.size();
-          items.insert(items.end(), P.items.begin() + sg.first, P.items.begin() + sg.first + sg.count);
-          sg.first = f;
-          sg.inst = (int16_t)i;
-          segs.push_back(sg);
-        }
-        rd.gemm_aux = std::max(rd.gemm_aux, L.aux);
-        rd.gemm_aux2 = std::max(rd.gemm_aux2, L.aux2);
-      } else if (L.kind == Launch::EIG) {
-        const bool m = mixed && L.aux <= 96;
-        for (int64_t q = L.first; q < L.first + L.count; ++q) {
-          EigTask e = P.eigs[q];
-          e.inst = (int16_t)i;
-          (m ? em : ed).push_back(e);
-        }
-        if (m) rd.eigm_aux = std::max(rd.eigm_aux, L.aux);
-        else rd.eigd_aux = std::max(rd.eigd_aux, L.aux);
-      }
-      if (items.size() > (size_t)INT32_MAX) throw Error(H2_EUNSUPPORTED, "batch too large for one merged program");
-    }
-    rd.gemm_count = (int64_t)segs.size() - rd.gemm_first;
-    rd.eigm_first = (int64_t)eigs.size();
-    rd.eigm_count = (int64_t)em.size();
-    eigs.insert(eigs.end(), em.begin(), em.end());
-    rd.eigd_first = (int64_t)eigs.size();
-    rd.eigd_count = (int64_t)ed.size();
-    eigs.insert(eigs.end(), ed.begin(), ed.end());
-    const int nn = rd.eigd_aux + (rd.eigd_aux & 1);
-    if (rd.eigd_count && nn > 112) scratch = std::max<int64_t>(scratch, rd.eigd_count * 2LL * nn * (nn + 1));
-    be->rounds.push_back(std::move(rd));
-  }
-  be->d_segs = (Seg*)dmalloc(std::max<size_t>(1, segs.size()) * sizeof(Seg));
-  be->d_items = (Item*)dmalloc(std::max<size_t>(1, items.size()) * sizeof(Item));
-  be->d_eigs = (EigTask*)dmalloc(std::max<size_t>(1, eigs.size()) * sizeof(EigTask));
-  be->d_scratch = (double*)dmalloc(std::max<int64_t>(1, scratch) * sizeof(double));
+  be->eps = grp[0]->prm.eps;
+  be->trunc = grp[0]->prm.trunc;
+  be->precision = grp[0]->prm.precision;
+  for (Prepared* p : grp) be->plans.push_back(p->ent);
   be->d_ars = (Arenas*)dmalloc(grp.size() * sizeof(Arenas));
-  if (!segs.empty())
-    cuda_check(cudaMemcpy(be->d_segs, segs.data(), segs.size() * sizeof(Seg), cudaMemcpyHostToDevice), "upload batch");
-  if (!items.empty())
-    cuda_check(cudaMemcpy(be->d_items, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice),
-               "upload batch");
-  if (!eigs.empty())
-    cuda_check(cudaMemcpy(be->d_eigs, eigs.data(), eigs.size() * sizeof(EigTask), cudaMemcpyHostToDevice),
-               "upload batch");
-  for (Prepared* p : grp) be->mem_ar.push_back(p->ar);
+  init_kernel_attributes();
+  std::vector<cudaStream_t> st(grp.size() + 1, nullptr);
+  std::vector<cudaEvent_t> ev(grp.size() + 1, nullptr);
+  auto release = [&] {
+    for (auto e : ev)
+      if (e) cudaEventDestroy(e);
+    for (auto x : st)
+      if (x) cudaStreamDestroy(x);
+  };
+  cudaGraph_t g = nullptr;
+  try {
+    for (auto& x : st) cuda_check(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking), "capture stream");
+    for (auto& e : ev) cuda_check(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "capture event");
+    const unsigned long long k0 = kernel_launches();
+    cuda_check(cudaStreamBeginCapture(st[0], cudaStreamCaptureModeThreadLocal), "begin capture");
+    cuda_check(cudaEventRecord(ev[0], st[0]), "fork");
+    for (size_t i = 0; i < grp.size(); ++i) {
+      cudaStream_t si = st[i + 1];
+      cuda_check(cudaStreamWaitEvent(si, ev[0], 0), "fork");
+      run_plan(grp[i]->ent->plan, grp[i]->ar, be->d_ars + i, grp[i]->prm, si, false, nullptr);
+      cuda_check(cudaEventRecord(ev[i + 1], si), "join");
+      cuda_check(cudaStreamWaitEvent(st[0], ev[i + 1], 0), "join");
+    }
+    cuda_check(cudaStreamEndCapture(st[0], &g), "end capture");
+    be->kernels = (long long)(kernel_launches() - k0);
+    add_kernel_launches(-be->kernels);  // captured, not launched
+    cuda_check(cudaGraphInstantiate(&be->graph, g, 0), "instantiate graph");
+    cudaGraphDestroy(g);
+  } catch (...) {
+    cudaGraph_t gg = nullptr;
+    if (st[0]) cudaStreamEndCapture(st[0], &gg);
+    if (gg) cudaGraphDestroy(gg);
+    if (g) cudaGraphDestroy(g);
+    release();
+    cudaGetLastError();
+    throw;
+  }
+  release();
   return be;
 }
 
-// the launches of a merged program, in order, on stream s
-void run_batch(const BatchEntry& be, void* s) {
-  const bool mixed = be.precision == H2_MIXED_FP32;
-  for (const Round& rd : be.rounds) {
-    for (auto& m : rd.memsets) {
-      const Launch& L = be.plans[m.first]->plan.launches[m.second];
-      if (L.elems == 0) continue;
-      const ArenaSet& ar = be.mem_ar[m.first];
-      const int a = arena_of(L.off);
-      char* p = (char*)ar.p[a] + offset_of(L.off) * ar.esize(a);
-      cuda_check(cudaMemsetAsync(p, 0, L.elems * ar.esize(a), (cudaStream_t)s), "memset");
-    }
-    for (auto& c : rd.copy_ranks) launch_copy_ranks(be.d_ars, c.first, c.second, s);
-    if (rd.gemm_count)
-      launch_gemm(be.d_segs, be.d_items, rd.gemm_first, rd.gemm_count, be.d_ars, rd.gemm_aux, rd.gemm_aux2, mixed,
-                  s);
-    if (rd.eigm_count)
-      launch_eig_mixed(be.d_eigs, rd.eigm_first, rd.eigm_count, be.d_ars, be.eps, be.trunc, rd.eigm_aux, s);
-    if (rd.eigd_count)
-      launch_eig(be.d_eigs, rd.eigd_first, rd.eigd_count, be.d_ars, be.eps, be.trunc, rd.eigd_aux, be.d_scratch, s);
-    cuda_check(cudaGetLastError(), "batched launch");
+void run_group(std::vector<Prepared*>& grp, const Workspace& ws, void* stream) {
+  // each product of the group takes its own slice of the work space
+  size_t off = 0;
+  for (Prepared* p : grp) {
+    place_regions(p->ent->plan, p->ar, ws.base + off);
+    off += region_bytes(p->ent->plan);
   }
-}
-
-void run_group(std::vector<Prepared*>& grp, void* stream) {
   std::shared_ptr<BatchEntry> be;
   {
     std::lock_guard<std::mutex> lk(g_batch_mu);
     for (auto& e : g_batches) {
       if (e->plans.size() != grp.size() || e->eps != grp[0]->prm.eps || e->trunc != grp[0]->prm.trunc ||
-          e->precision != grp[0]->prm.precision)
+          e->precision != grp[0]->prm.precision || e->ws_base != ws.base || e->ws_gen != ws.gen)
         continue;
       bool same = true;
       for (size_t i = 0; i < grp.size() && same; ++i) same = e->plans[i] == grp[i]->ent;
@@ -980,47 +961,17 @@ void run_group(std::vector<Prepared*>& grp, void* stream) {
     }
   }
   if (!be) {
-    be = build_batch(grp);
+    be = capture_batch(grp);
+    be->ws_base = ws.base;
+    be->ws_gen = ws.gen;
     std::lock_guard<std::mutex> lk(g_batch_mu);
     g_batches.push_back(be);
     if (g_batches.size() > 4) g_batches.erase(g_batches.begin());
   }
-  // the work-region pointers are the plans' own (fixed); the tables change per call
   for (size_t i = 0; i < grp.size(); ++i) upload_arenas(be->d_ars + i, to_arenas(grp[i]->ar), stream);
   cuda_check(cudaGetLastError(), "arena tables");
-  if (be->graph) {
-    cuda_check(cudaGraphLaunch(be->graph, (cudaStream_t)stream), "graph launch");
-    add_kernel_launches(be->kernels);
-  } else {
-    const unsigned long long k0 = kernel_launches();
-    run_batch(*be, stream);  // first use: launches in order (this also sets kernel attributes)
-    be->kernels = (long long)(kernel_launches() - k0);
-    // capture the same launches once, on a private stream, for later calls
-    cudaStream_t cs;
-    cuda_check(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-      try {
-        run_batch(*be, cs);
-        add_kernel_launches(-be->kernels);  // captured, not launched
-      } catch (...) {
-        cudaStreamEndCapture(cs, &g);
-        if (g) cudaGraphDestroy(g);
-        cudaStreamDestroy(cs);
-        throw;
-      }
-      e = cudaStreamEndCapture(cs, &g);
-    }
-    if (e == cudaSuccess && g) e = cudaGraphInstantiate(&be->graph, g, 0);
-    if (g) cudaGraphDestroy(g);
-    cudaStreamDestroy(cs);
-    if (e != cudaSuccess) {  // no graph: later calls launch in order
-      be->graph = nullptr;
-      cudaGetLastError();
-    }
-  }
-  ++be->uses;
+  cuda_check(cudaGraphLaunch(be->graph, (cudaStream_t)stream), "graph launch");
+  add_kernel_launches(be->kernels);
 }
 
 }  // namespace
@@ -1051,20 +1002,33 @@ h2_status h2_mmp_batched(const h2_handle* A, const h2_handle* B, int32_t count, 
         throw Error(e.code, "instance " + std::to_string(i) + ": " + e.what());
       }
     }
-    // groups of distinct plans (a plan's work regions serve one product at a time)
-    std::vector<char> done(count, 0);
-    for (int32_t first = 0; first < count; ++first) {
-      if (done[first]) continue;
-      std::vector<Prepared*> grp;
-      std::vector<const PlanEntry*> used;
-      for (int32_t i = first; i < count; ++i) {
-        if (done[i] || std::find(used.begin(), used.end(), pr[i].ent.get()) != used.end()) continue;
-        used.push_back(pr[i].ent.get());
-        grp.push_back(&pr[i]);
-        done[i] = 1;
-      }
-      run_group(grp, o.stream);
+    // groups of products whose work spaces fit together in 70 % of the free device
+    // memory (the first product of a group always joins)
+    size_t free_b = 0, total_b = 0;
+    cuda_check(cudaMemGetInfo(&free_b, &total_b), "memory info");
+    size_t have = 0;
+    {
+      std::lock_guard<std::mutex> lk(g_ws_mu);
+      auto it = g_ws.find(o.stream);
+      if (it != g_ws.end()) have = it->second.bytes;
     }
+    const size_t budget = (size_t)(0.7 * (double)(free_b + have));
+    std::vector<std::vector<Prepared*>> groups;
+    std::vector<size_t> need, wneed;
+    for (int32_t i = 0; i < count; ++i) {
+      const size_t w = region_bytes(pr[i].ent->plan);
+      const size_t b = w;
+      if (groups.empty() || need.back() + b > budget) {
+        groups.emplace_back();
+        need.push_back(0);
+        wneed.push_back(0);
+      }
+      groups.back().push_back(&pr[i]);
+      need.back() += b;
+      wneed.back() += w;
+    }
+    const Workspace ws = workspace(o.stream, *std::max_element(wneed.begin(), wneed.end()));
+    for (auto& grp : groups) run_group(grp, ws, o.stream);
     for (int32_t i = 0; i < count; ++i) {
       cuda_check(cudaEventRecord(pr[i].out->ev1, (cudaStream_t)o.stream), "event");
       pr[i].out->timed = true;
@@ -1084,7 +1048,7 @@ h2_status h2_matvec(h2_handle h, const double* x, double* y, int64_t nrhs) {
       build_matvec_plan(h->m, nrhs, *p, ox, oy);
       int64_t sizes[kArenas] = {h->m.arena_elems, 0, 0, p->region[AR_P], 0, 0, 0, 0};
       validate_plan(*p, sizes);
-      upload_plan(*p, sizeof(double));
+      upload_plan(*p, sizeof(double), true);
       h->mv_offs[nrhs] = {ox, oy};
       it = h->mv_plans.emplace(nrhs, std::move(p)).first;
     }

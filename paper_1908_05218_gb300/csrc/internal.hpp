@@ -173,7 +173,10 @@ struct Plan {
   Seg* d_segs = nullptr;
   Item* d_items = nullptr;
   EigTask* d_eigs = nullptr;
+  // work regions owned by the plan (matvec plans); product plans take theirs from the
+  // per-stream work space at run time (see region_bytes)
   double* d_region[kArenas] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int region_esize = 8;  // bytes per element of the work regions (4 for a mixed product)
   double* d_scratch = nullptr;  // eigen work space for Gram matrices above 112
   int64_t flops = 0;     // counted 2mnk over GEMM segments (padded dims)
   std::vector<int> ckr, ckc;  // caps of the product
@@ -199,7 +202,9 @@ struct MmpParams {
 void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& p, Plan& plan);
 void build_matvec_plan(const Mat& H, int64_t nrhs, Plan& plan, int64_t& off_x, int64_t& off_y);
 void validate_plan(const Plan& plan, const int64_t sizes[kArenas]);
-void upload_plan(Plan& plan, size_t region_esize);
+// uploads the program; own_regions: allocate the work regions with the plan (matvec
+// plans), else they come from the per-stream work space when the plan runs
+void upload_plan(Plan& plan, size_t region_esize, bool own_regions);
 void free_plan(Plan& plan);
 
 // Runs a plan: arenas[kArenas] device base pointers.
@@ -244,7 +249,8 @@ void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, const Arena
 // formatted product: C's ranks are A's row ranks and B's column ranks (instance inst)
 void launch_copy_ranks(const Arenas* d_ars, int inst, int64_t n, void* stream);
 unsigned long long kernel_launches();  // kernels launched by this library so far
-void add_kernel_launches(long long d);   // graph replays add their kernels; captures take theirs back
+void add_kernel_launches(long long d);
+void init_kernel_attributes();  // once per process, before launches or captures   // graph replays add their kernels; captures take theirs back
 void launch_to_f32(const double* src, float* dst, int64_t n, void* stream);
 void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const Arenas* d_ars, double eps,
                       int trunc, int max_npad, void* stream);

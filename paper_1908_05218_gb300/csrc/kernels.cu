@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <cstdint>
 #include <cstdio>
 
@@ -1328,16 +1329,23 @@ __global__ void __launch_bounds__(256) eig_mixed_kept_kernel(const EigTask* __re
   }
 }
 
-void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const Arenas* ar, double eps,
-                      int trunc, int max_npad, void* stream) {
-  static bool attr = false;
-  if (!attr) {
+// the eigen kernels' shared-memory limits, set once per process (before any launch or
+// stream capture)
+void init_kernel_attributes() {
+  static std::once_flag once;
+  std::call_once(once, [] {
     cudaFuncSetAttribute(eig_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(3 * kMixMax * (kMixMax + 1) * sizeof(double)));
     cudaFuncSetAttribute(eig_mixed_kept_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)eig_kept_smem(kMixMax));
-    attr = true;
-  }
+    cudaFuncSetAttribute(eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(2 * kEigSmemMax * (kEigSmemMax + 1) * sizeof(double)));
+  });
+}
+
+void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const Arenas* ar, double eps,
+                      int trunc, int max_npad, void* stream) {
+  init_kernel_attributes();
   const double thr = trunc == H2_TRUNC_SV ? eps * eps : eps;
   if (trunc != H2_TRUNC_FULL && thr < 5e-5) {
     // thresholds below float32 eigenvector resolution: float64 Rayleigh-Ritz refinement
@@ -1380,12 +1388,7 @@ void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, const Arena
     smem = (size_t)2 * kEigSmemMax * (kEigSmemMax + 1) * sizeof(double);
     stride = (int64_t)2 * nn * (nn + 1);
   }
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(2 * kEigSmemMax * (kEigSmemMax + 1) * sizeof(double)));
-    attr = true;
-  }
+  init_kernel_attributes();
   eig_kernel<<<(unsigned)count, 256, smem, (cudaStream_t)stream>>>(d_eigs, first, ar, eps, trunc, scratch, stride);
   g_launches += 1;
 }

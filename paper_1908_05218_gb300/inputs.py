@@ -115,6 +115,21 @@ def workload_uniform(n: int = 1024, seed: int = 0) -> Workload:
     return Workload(f"uniform_cube_N{n}", uniform_cube(n, seed), laplace_spec(h), h)
 
 
+def workload_batch(count: int = 48, n_min: int = 4096, n_max: int = 131072, seed: int = 0) -> list:
+    """Independent instances of uneven size: instance i has N_i log-uniform in
+    [n_min, n_max] and points uniform in a box with sides (1, s2, s3), s log-uniform in
+    [1, 8] (seed seed + i), with the Laplace kernel at the box's volume spacing."""
+    out = []
+    for i in range(count):
+        rng = np.random.default_rng(seed + i)
+        n = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+        s = np.exp(rng.uniform(0.0, math.log(8.0), size=2))
+        pts = rng.random((n, 3)) * np.array([1.0, s[0], s[1]])
+        h = (s[0] * s[1] / n) ** (1.0 / 3.0)
+        out.append(Workload(f"box_{i}_N{n}", pts, laplace_spec(h), h))
+    return out
+
+
 def workload_cube_array(nx: int, ny: int, pts_per_cube: int = 4096, kernel: str = "laplace",
                         seed: int = 0) -> Workload:
     """Capacitance-like surface points on an nx x ny array of unit cubes."""

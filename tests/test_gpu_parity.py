@@ -210,10 +210,11 @@ def test_mixed_product_is_deterministic_with_odd_leaf_sizes(lib, n):
 
 
 @pytest.mark.parametrize("precision,trunc", [("mixed", "paper"), ("fp64", "paper"), ("mixed", "formatted")])
-def test_batched_merged_and_replayed_equal_single(lib, precision, trunc):
-    # instances of uneven size in one merged program; the repeated instance shares its
-    # plan with the first and runs in a second group; the second call replays the
-    # captured graph.  Every result equals its single product bit for bit.
+def test_batched_graph_and_replay_equal_single(lib, precision, trunc):
+    # instances of uneven size in one captured graph, one branch per product (the
+    # repeated instance shares its plan with the first and gets its own slice of the
+    # work space); the second call replays the graph.  Every result equals its single
+    # product bit for bit.
     import torch
     prec = lib.MIXED_FP32 if precision == "mixed" else lib.FP64
     specs = [(900, 11, "box"), (1700, 12, "box"), (900, 11, "box"), (1200, 13, "uniform")]
