@@ -128,6 +128,18 @@ h2_status h2_build(const double* points, int64_t n, const h2_kernel* kernel,
                    int32_t leaf_size, double eta, double eps, const h2_opts* opts,
                    h2_handle* out);
 
+/* Host-only self-check of the product program (no device memory, no GPU needed):
+ * builds the tree, partition and H^2 ranks of the Laplace kernel (as h2_build, at
+ * ε = eps) for the points, then the program of C = A A for every truncation mode
+ * (paper, sv, full, formatted), both precisions and rank caps 24 and 48, and the
+ * matvec programs for 1 and 3 right-hand sides.  Each is validated: every operand and
+ * output of every segment and eigen task lies inside one live allocation of its
+ * region (replayed in program order) or inside its matrix.  *checked gets the number of
+ * programs checked (18).  H2_EINTERNAL names the first program and access that fails.
+ * The paper has no counterpart: this checks the build's own memory layout. */
+h2_status h2_plan_selfcheck(const double* points, int64_t n, int32_t leaf_size, double eta, double eps,
+                            int32_t* checked);
+
 /* Create a handle from host arrays that describe an H^2 matrix on the same tree
  * and partition that h2_build(points, n, kernel, leaf_size, eta, ...) makes.  Used
  * to feed matrices built elsewhere (e.g. by a reference implementation) to the

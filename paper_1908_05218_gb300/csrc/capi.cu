@@ -593,6 +593,63 @@ h2_status h2_build(const double* points, int64_t n, const h2_kernel* kernel, int
   });
 }
 
+h2_status h2_plan_selfcheck(const double* points, int64_t n, int32_t leaf_size, double eta, double eps,
+                            int32_t* checked) {
+  if (!points || !checked) return fail(H2_EINVAL, "null argument");
+  *checked = 0;
+  return guarded([&] {
+    if (!(eps > 0) || !(eps < 1)) throw Error(H2_EINVAL, "eps must lie in (0, 1)");
+    // host only: structure, H^2 ranks of the Laplace kernel, storage caps as an import
+    // would set them, then every program built and validated (no device memory)
+    auto st = build_structure(points, n, leaf_size, eta);
+    const double h = std::cbrt(1.0 / (double)n);
+    h2_kernel k{H2_K_LAPLACE, 0.0, 1.0 / (2.0 * M_PI * h), 0.0};
+    Packed p;
+    build_h2_host(*st, k, eps, p);
+    Mat m;
+    m.st = st;
+    m.Kr.assign(st->L + 1, 0);
+    m.Kc.assign(st->L + 1, 0);
+    for (int l = 0; l <= st->L; ++l)
+      for (int64_t t = 0; t < (1LL << l); ++t) {
+        m.Kr[l] = std::max(m.Kr[l], p.kr[Structure::node(l, t)]);
+        m.Kc[l] = std::max(m.Kc[l], p.kc[Structure::node(l, t)]);
+      }
+    for (int l = 0; l <= st->L; ++l) {
+      m.Kr[l] = cap_round(m.Kr[l]);
+      m.Kc[l] = cap_round(m.Kc[l]);
+    }
+    const int64_t asz = mat_elems(m);
+    for (int trunc : {H2_TRUNC_PAPER, H2_TRUNC_SV, H2_TRUNC_FULL, H2_TRUNC_FORMATTED})
+      for (int prec : {H2_FP64, H2_MIXED_FP32})
+        for (int cap : {24, 48}) {
+          Plan P;
+          Mat C;
+          C.st = st;
+          MmpParams prm{1e-4, trunc, cap, prec};
+          try {
+            build_mmp_plan(m, m, C, prm, P);
+            const int64_t csz = mat_elems(C);
+            int64_t sizes[kArenas] = {asz, asz, csz, P.region[AR_P], P.region[AR_G0], P.region[AR_G1], P.region[AR_S],
+                                      prec == H2_MIXED_FP32 ? C.off_S[0] : 0};
+            validate_plan(P, sizes);
+          } catch (Error& e) {
+            throw Error(e.code, "product plan (trunc " + std::to_string(trunc) + ", precision " +
+                                    std::to_string(prec) + ", cap " + std::to_string(cap) + "): " + e.what());
+          }
+          ++*checked;
+        }
+    for (int64_t nrhs : {1, 3}) {
+      Plan P;
+      int64_t ox, oy;
+      build_matvec_plan(m, nrhs, P, ox, oy);
+      int64_t sizes[kArenas] = {asz, 0, 0, P.region[AR_P], 0, 0, 0, 0};
+      validate_plan(P, sizes);
+      ++*checked;
+    }
+  });
+}
+
 h2_status h2_import(const double* points, int64_t n, int32_t leaf_size, double eta, const int32_t* kr,
                     const int32_t* kc, const double* vr, const double* vc, const double* er, const double* ec,
                     const double* s, const double* f, const h2_opts* opts, h2_handle* out) {

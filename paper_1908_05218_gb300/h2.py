@@ -24,7 +24,7 @@ _TRUNC = {"paper": TRUNC_PAPER, "sv": TRUNC_SV, "full": TRUNC_FULL, "formatted":
 # exported symbols and their signatures (checked by the CPU tests)
 SYMBOLS = ["h2_build", "h2_import", "h2_export", "h2_mmp", "h2_mmp_batched", "h2_matvec", "h2_matvec_noalloc", "h2_to_dense", "h2_info",
            "h2_tree_perm", "h2_level_blocks", "h2_trace_enable", "h2_trace_read", "h2_trace_flops", "h2_trace_phase", "h2_destroy",
-           "h2_last_error", "h2_kernel_launches"]
+           "h2_last_error", "h2_kernel_launches", "h2_plan_selfcheck"]
 
 
 class H2Error(RuntimeError):
@@ -76,6 +76,7 @@ def load(path: str = LIB_PATH):
     lib.h2_trace_read.argtypes = [P, I32, P, P, P, P, P]
     lib.h2_trace_flops.argtypes = [P, P]
     lib.h2_kernel_launches.argtypes = [P]
+    lib.h2_plan_selfcheck.argtypes = [P, I64, I32, C.c_double, C.c_double, P]
     lib.h2_trace_phase.argtypes = [P, I32]
     lib.h2_trace_phase.restype = C.c_char_p
     lib.h2_destroy.argtypes = [P]
@@ -242,6 +243,15 @@ class H2Matrix:
         if cnt.value:
             _check(lib.h2_level_blocks(self.handle, level, _ptr(t), _ptr(s), _ptr(k), C.byref(cnt)))
         return t, s, k
+
+
+def plan_selfcheck(points: np.ndarray, leaf_size: int = 32, eta: float = 1.0, eps: float = 1e-4) -> int:
+    """Builds and validates every product and matvec program for these points on the
+    host (no GPU); returns the number of programs checked, raises H2Error on a fault."""
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    n = C.c_int32(0)
+    _check(load().h2_plan_selfcheck(_ptr(pts), pts.shape[0], leaf_size, float(eta), float(eps), C.byref(n)))
+    return int(n.value)
 
 
 def kernel_launches() -> int:
