@@ -34,7 +34,7 @@ WORKLOADS = {
     "cubes16x16": (16, 16, 4096, 1e-4, "N=1,048,576 panel centroids on a 16x16 array of unit cubes"),
     "cubes4x4": (4, 4, 4096, 1e-4, "N=65,536 panel centroids on a 4x4 array of unit cubes"),
     "cubes2x2": (2, 2, 1024, 1e-4, "N=4,096 panel centroids on a 2x2 array of unit cubes"),
-    "sample": (2, 2, 2048, 1e-4, "N=8,192 panel centroids on a 2x2 array of unit cubes"),
+    "sample": (2, 2, 3072, 1e-4, "N=12,288 panel centroids on a 2x2 array of unit cubes"),
 }
 # DRAM traffic of the float32 GEMM kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum over the 115 GEMM launches of one product of the N=65,536
@@ -121,7 +121,7 @@ def reference_arm(args):
 
 
 def oracle_sample(steps: int):
-    """Child process: oracle product on N=8192 points of the cube-array geometry."""
+    """Child process: oracle product on N=12288 points of the cube-array geometry."""
     import numpy as np
 
     from oracle import h2 as oh2
@@ -261,7 +261,7 @@ def main():
         line = {"metric": metric, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus, "steps": r["steps"],
                 "warmup": 0, "ms_per_step": r["t"] * 1e3, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-                "config": {"workload": f"cube array 2x2, 2048 points per cube (N={r['n']}), leaf {LEAF}, "
+                "config": {"workload": f"cube array 2x2, 3072 points per cube (N={r['n']}), leaf {LEAF}, "
                                        f"eta {ETA}, eps {eps}, A: 1/(4 pi r), B: 1/r^2",
                            "sample_of": desc},
                 "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
@@ -410,7 +410,7 @@ def main():
         cpu_line = None
         if cpu and "t" in cpu:
             cpu_line = {"value": cpu["bytes"] / cpu["t"] / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                        "sample": f"cube array 2x2, 2048 points per cube (N={cpu['n']}), one product, eps {eps}",
+                        "sample": f"cube array 2x2, 3072 points per cube (N={cpu['n']}), one product, eps {eps}",
                         "seconds": cpu["t"]}
         elif cpu:
             cpu_line = {"error": cpu.get("error")}
