@@ -228,29 +228,88 @@ void sync_ranks_to_host(Mat& m) {
   m.ranks_on_host = true;
 }
 
-// packed host layout -> padded device arena (caps = largest rank per level, rounded
-// up to a multiple of four)
-void unpack_to_device(const Packed& p, Mat& m) {
+// Blocks of the packed layout (vr, vc, er, ec, s, f back to back, each block dense at
+// the actual ranks) and where they sit in the padded arena; len gets the six lengths.
+std::vector<CopyTask> copy_tasks(const Mat& m, const int32_t* kr, const int32_t* kc, int64_t len[6]) {
   const Structure& st = *m.st;
-  const int L = st.L, LS = st.LS, nn = st.nnodes();
-  if ((int)p.kr.size() != nn || (int)p.kc.size() != nn) throw Error(H2_EINVAL, "rank arrays have the wrong length");
+  const int L = st.L;
+  const int64_t LS = st.LS;
+  std::vector<CopyTask> tk;
+  int64_t off = 0;
+  auto add = [&](int64_t arena_off, int64_t rows, int64_t cols, int64_t ld) {
+    if (rows > 0 && cols > 0) tk.push_back({arena_off, off, (int32_t)rows, (int32_t)cols, (int32_t)ld, 0});
+    off += rows * cols;
+  };
+  int64_t mark = 0;
+  for (int col = 0; col < 2; ++col) {  // leaf bases
+    const int32_t* rk = col ? kc : kr;
+    const int K = col ? m.Kc[L] : m.Kr[L];
+    for (int64_t t = 0; t < (1LL << L); ++t) add(col ? m.Vc(t) : m.Vr(t), st.size[L][t], rk[Structure::node(L, t)], K);
+    len[col] = off - mark;
+    mark = off;
+  }
+  for (int col = 0; col < 2; ++col) {  // stacked transfers: child 1 rows, then child 2 rows
+    const int32_t* rk = col ? kc : kr;
+    const auto& K = col ? m.Kc : m.Kr;
+    for (int l = 0; l < L; ++l)
+      for (int64_t t = 0; t < (1LL << l); ++t) {
+        const int k = rk[Structure::node(l, t)], k1 = rk[Structure::node(l + 1, 2 * t)],
+                  k2 = rk[Structure::node(l + 1, 2 * t + 1)];
+        const int64_t base = col ? m.Ec(l, t) : m.Er(l, t);
+        add(base, k1, k, K[l]);
+        add(base + (int64_t)K[l + 1] * K[l], k2, k, K[l]);
+      }
+    len[2 + col] = off - mark;
+    mark = off;
+  }
+  for (int l = 0; l <= L; ++l)  // couplings
+    for (auto& b : st.blocks[l])
+      if (b.kind == KR) add(m.S(l, b.idx), kr[Structure::node(l, b.t)], kc[Structure::node(l, b.s)], m.Kc[l]);
+  len[4] = off - mark;
+  mark = off;
+  for (auto& b : st.blocks[L])  // dense leaf blocks
+    if (b.kind == KF) add(m.F(b.idx), st.size[L][b.t], st.size[L][b.s], LS);
+  len[5] = off - mark;
+  return tk;
+}
+
+void packed_lengths(const Structure& st, const int32_t* kr, const int32_t* kc, int64_t len[6]) {
+  const int L = st.L;
+  for (int i = 0; i < 6; ++i) len[i] = 0;
+  for (int64_t t = 0; t < (1LL << L); ++t) {
+    len[0] += st.size[L][t] * kr[Structure::node(L, t)];
+    len[1] += st.size[L][t] * kc[Structure::node(L, t)];
+  }
+  for (int l = 0; l < L; ++l)
+    for (int64_t t = 0; t < (1LL << l); ++t) {
+      len[2] += (int64_t)(kr[Structure::node(l + 1, 2 * t)] + kr[Structure::node(l + 1, 2 * t + 1)]) * kr[Structure::node(l, t)];
+      len[3] += (int64_t)(kc[Structure::node(l + 1, 2 * t)] + kc[Structure::node(l + 1, 2 * t + 1)]) * kc[Structure::node(l, t)];
+    }
+  for (int l = 0; l <= L; ++l)
+    for (auto& b : st.blocks[l]) {
+      if (b.kind == KR) len[4] += (int64_t)kr[Structure::node(l, b.t)] * kc[Structure::node(l, b.s)];
+      if (b.kind == KF) len[5] += st.size[L][b.t] * st.size[L][b.s];
+    }
+}
+
+// packed host arrays -> padded device arena (caps = largest rank per level, rounded up
+// to a multiple of four): the arrays are copied as they are into a device staging
+// buffer and scattered into the zeroed arena by transfer.cu's kernel
+void unpack_view_to_device(const PackedView& v, Mat& m) {
+  const Structure& st = *m.st;
+  const int L = st.L, nn = st.nnodes();
   m.Kr.assign(L + 1, 0);
   m.Kc.assign(L + 1, 0);
   for (int l = 0; l <= L; ++l)
     for (int64_t t = 0; t < (1LL << l); ++t) {
-      int kr = p.kr[Structure::node(l, t)], kc = p.kc[Structure::node(l, t)];
-      int64_t lim = st.size[l][t];
-      if (l < L) {
-        lim = std::min<int64_t>(lim, (int64_t)p.kr[Structure::node(l + 1, 2 * t)] + p.kr[Structure::node(l + 1, 2 * t + 1)]);
-      }
+      int kr = v.kr[Structure::node(l, t)], kc = v.kc[Structure::node(l, t)];
       if (kr < 0 || kc < 0 || kr > st.size[l][t] || kc > st.size[l][t] || kr > 128 || kc > 128)
         throw Error(H2_EINVAL, "rank out of range");
       if (l < L) {
-        int64_t lr = (int64_t)p.kr[Structure::node(l + 1, 2 * t)] + p.kr[Structure::node(l + 1, 2 * t + 1)];
-        int64_t lc = (int64_t)p.kc[Structure::node(l + 1, 2 * t)] + p.kc[Structure::node(l + 1, 2 * t + 1)];
+        int64_t lr = (int64_t)v.kr[Structure::node(l + 1, 2 * t)] + v.kr[Structure::node(l + 1, 2 * t + 1)];
+        int64_t lc = (int64_t)v.kc[Structure::node(l + 1, 2 * t)] + v.kc[Structure::node(l + 1, 2 * t + 1)];
         if (kr > lr || kc > lc) throw Error(H2_EINVAL, "rank above the sum of the children's ranks");
       }
-      (void)lim;
       m.Kr[l] = std::max(m.Kr[l], kr);
       m.Kc[l] = std::max(m.Kc[l], kc);
     }
@@ -258,131 +317,73 @@ void unpack_to_device(const Packed& p, Mat& m) {
     m.Kr[l] = cap_round(m.Kr[l]);
     m.Kc[l] = cap_round(m.Kc[l]);
   }
-  alloc_mat(m);
-  std::vector<double> h(m.arena_elems, 0.0);
-  size_t pos = 0;
-  auto need = [&](const std::vector<double>& v, size_t cnt) {
-    if (pos + cnt > v.size()) throw Error(H2_EINVAL, "packed array too short");
-  };
-  const int64_t nl = 1LL << L;
-  for (int col = 0; col < 2; ++col) {
-    const auto& v = col ? p.vc : p.vr;
-    const auto& rk = col ? p.kc : p.kr;
-    int K = col ? m.Kc[L] : m.Kr[L];
-    pos = 0;
-    for (int64_t t = 0; t < nl; ++t) {
-      int k = rk[Structure::node(L, t)];
-      int64_t n = st.size[L][t];
-      need(v, n * k);
-      double* dst = &h[(col ? m.Vc(t) : m.Vr(t))];
-      for (int64_t r = 0; r < n; ++r)
-        for (int c = 0; c < k; ++c) dst[r * K + c] = v[pos + r * k + c];
-      pos += n * k;
+  mat_elems(m);  // the arena layout (offsets) the copy tasks point into
+  int64_t len[6];
+  std::vector<CopyTask> tk = copy_tasks(m, v.kr, v.kc, len);
+  for (int i = 0; i < 6; ++i) {
+    if (v.len[i] != len[i]) throw Error(H2_EINVAL, "packed array has the wrong length");
+    if (len[i] && !v.arr[i]) throw Error(H2_EINVAL, "null array");
+  }
+  alloc_mat(m);  // zeroed: padded entries stay exactly zero
+  int64_t total = 0;
+  for (int i = 0; i < 6; ++i) total += len[i];
+  double* stage = (double*)dmalloc(std::max<int64_t>(1, total) * sizeof(double));
+  CopyTask* d_tk = (CopyTask*)dmalloc(std::max<size_t>(1, tk.size()) * sizeof(CopyTask));
+  try {
+    int64_t off = 0;
+    for (int i = 0; i < 6; ++i) {
+      if (len[i])
+        cuda_check(cudaMemcpy(stage + off, v.arr[i], len[i] * sizeof(double), cudaMemcpyHostToDevice), "upload arrays");
+      off += len[i];
     }
-    if (pos != v.size()) throw Error(H2_EINVAL, "leaf basis array has the wrong length");
+    if (!tk.empty())
+      cuda_check(cudaMemcpy(d_tk, tk.data(), tk.size() * sizeof(CopyTask), cudaMemcpyHostToDevice), "upload tasks");
+    launch_copy_tasks(d_tk, (int64_t)tk.size(), stage, m.arena, true, nullptr);
+    cuda_check(cudaGetLastError(), "scatter");
+    cuda_check(cudaDeviceSynchronize(), "scatter");
+  } catch (...) {
+    cudaFree(stage);
+    cudaFree(d_tk);
+    throw;
   }
-  for (int col = 0; col < 2; ++col) {
-    const auto& v = col ? p.ec : p.er;
-    const auto& rk = col ? p.kc : p.kr;
-    const auto& K = col ? m.Kc : m.Kr;
-    pos = 0;
-    for (int l = 0; l < L; ++l)
-      for (int64_t t = 0; t < (1LL << l); ++t) {
-        int k = rk[Structure::node(l, t)], k1 = rk[Structure::node(l + 1, 2 * t)], k2 = rk[Structure::node(l + 1, 2 * t + 1)];
-        need(v, (int64_t)(k1 + k2) * k);
-        double* dst = &h[col ? m.Ec(l, t) : m.Er(l, t)];
-        for (int r = 0; r < k1 + k2; ++r) {
-          int pr = r < k1 ? r : K[l + 1] + (r - k1);
-          for (int c = 0; c < k; ++c) dst[(int64_t)pr * K[l] + c] = v[pos + (int64_t)r * k + c];
-        }
-        pos += (int64_t)(k1 + k2) * k;
-      }
-    if (pos != v.size()) throw Error(H2_EINVAL, "transfer array has the wrong length");
-  }
-  pos = 0;
-  for (int l = 0; l <= L; ++l)
-    for (auto& b : st.blocks[l]) {
-      if (b.kind != KR) continue;
-      int kt = p.kr[Structure::node(l, b.t)], ks = p.kc[Structure::node(l, b.s)];
-      need(p.s, (int64_t)kt * ks);
-      double* dst = &h[m.S(l, b.idx)];
-      for (int r = 0; r < kt; ++r)
-        for (int c = 0; c < ks; ++c) dst[(int64_t)r * m.Kc[l] + c] = p.s[pos + (int64_t)r * ks + c];
-      pos += (int64_t)kt * ks;
-    }
-  if (pos != p.s.size()) throw Error(H2_EINVAL, "coupling array has the wrong length");
-  pos = 0;
-  for (auto& b : st.blocks[L]) {
-    if (b.kind != KF) continue;
-    int64_t nt = st.size[L][b.t], ns = st.size[L][b.s];
-    need(p.f, nt * ns);
-    double* dst = &h[m.F(b.idx)];
-    for (int64_t r = 0; r < nt; ++r)
-      for (int64_t c = 0; c < ns; ++c) dst[r * LS + c] = p.f[pos + r * ns + c];
-    pos += nt * ns;
-  }
-  if (pos != p.f.size()) throw Error(H2_EINVAL, "dense array has the wrong length");
-  cuda_check(cudaMemcpy(m.arena, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice), "upload arena");
-  cuda_check(cudaMemcpy(m.d_kr, p.kr.data(), nn * sizeof(int32_t), cudaMemcpyHostToDevice), "upload ranks");
-  cuda_check(cudaMemcpy(m.d_kc, p.kc.data(), nn * sizeof(int32_t), cudaMemcpyHostToDevice), "upload ranks");
-  m.h_kr = p.kr;
-  m.h_kc = p.kc;
+  cudaFree(stage);
+  cudaFree(d_tk);
+  cuda_check(cudaMemcpy(m.d_kr, v.kr, nn * sizeof(int32_t), cudaMemcpyHostToDevice), "upload ranks");
+  cuda_check(cudaMemcpy(m.d_kc, v.kc, nn * sizeof(int32_t), cudaMemcpyHostToDevice), "upload ranks");
+  m.h_kr.assign(v.kr, v.kr + nn);
+  m.h_kc.assign(v.kc, v.kc + nn);
   m.ranks_on_host = true;
 }
 
-void pack_from_device(Mat& m, Packed& p) {
+// padded device arena -> the packed arrays (gathered on the device into a staging
+// buffer, then one copy per requested array into the caller's memory)
+void pack_to_host(Mat& m, double* const out[6]) {
   sync_ranks_to_host(m);
-  const Structure& st = *m.st;
-  const int L = st.L, LS = st.LS;
-  std::vector<double> h(m.arena_elems);
-  cuda_check(cudaMemcpy(h.data(), m.arena, h.size() * sizeof(double), cudaMemcpyDeviceToHost), "download arena");
-  p.kr = m.h_kr;
-  p.kc = m.h_kc;
-  p.vr.clear();
-  p.vc.clear();
-  p.er.clear();
-  p.ec.clear();
-  p.s.clear();
-  p.f.clear();
-  for (int col = 0; col < 2; ++col) {
-    auto& v = col ? p.vc : p.vr;
-    const auto& rk = col ? p.kc : p.kr;
-    int K = col ? m.Kc[L] : m.Kr[L];
-    for (int64_t t = 0; t < (1LL << L); ++t) {
-      int k = rk[Structure::node(L, t)];
-      const double* src = &h[col ? m.Vc(t) : m.Vr(t)];
-      for (int64_t r = 0; r < st.size[L][t]; ++r)
-        for (int c = 0; c < k; ++c) v.push_back(src[r * K + c]);
+  int64_t len[6];
+  std::vector<CopyTask> tk = copy_tasks(m, m.h_kr.data(), m.h_kc.data(), len);
+  int64_t total = 0;
+  for (int i = 0; i < 6; ++i) total += len[i];
+  double* stage = (double*)dmalloc(std::max<int64_t>(1, total) * sizeof(double));
+  CopyTask* d_tk = (CopyTask*)dmalloc(std::max<size_t>(1, tk.size()) * sizeof(CopyTask));
+  try {
+    if (!tk.empty())
+      cuda_check(cudaMemcpy(d_tk, tk.data(), tk.size() * sizeof(CopyTask), cudaMemcpyHostToDevice), "upload tasks");
+    launch_copy_tasks(d_tk, (int64_t)tk.size(), stage, m.arena, false, nullptr);
+    cuda_check(cudaGetLastError(), "gather");
+    cuda_check(cudaDeviceSynchronize(), "gather");
+    int64_t off = 0;
+    for (int i = 0; i < 6; ++i) {
+      if (len[i] && out[i])
+        cuda_check(cudaMemcpy(out[i], stage + off, len[i] * sizeof(double), cudaMemcpyDeviceToHost), "download arrays");
+      off += len[i];
     }
+  } catch (...) {
+    cudaFree(stage);
+    cudaFree(d_tk);
+    throw;
   }
-  for (int col = 0; col < 2; ++col) {
-    auto& v = col ? p.ec : p.er;
-    const auto& rk = col ? p.kc : p.kr;
-    const auto& K = col ? m.Kc : m.Kr;
-    for (int l = 0; l < L; ++l)
-      for (int64_t t = 0; t < (1LL << l); ++t) {
-        int k = rk[Structure::node(l, t)], k1 = rk[Structure::node(l + 1, 2 * t)], k2 = rk[Structure::node(l + 1, 2 * t + 1)];
-        const double* src = &h[col ? m.Ec(l, t) : m.Er(l, t)];
-        for (int r = 0; r < k1 + k2; ++r) {
-          int pr = r < k1 ? r : K[l + 1] + (r - k1);
-          for (int c = 0; c < k; ++c) v.push_back(src[(int64_t)pr * K[l] + c]);
-        }
-      }
-  }
-  for (int l = 0; l <= L; ++l)
-    for (auto& b : st.blocks[l]) {
-      if (b.kind != KR) continue;
-      int kt = p.kr[Structure::node(l, b.t)], ks = p.kc[Structure::node(l, b.s)];
-      const double* src = &h[m.S(l, b.idx)];
-      for (int r = 0; r < kt; ++r)
-        for (int c = 0; c < ks; ++c) p.s.push_back(src[(int64_t)r * m.Kc[l] + c]);
-    }
-  for (auto& b : st.blocks[L]) {
-    if (b.kind != KF) continue;
-    const double* src = &h[m.F(b.idx)];
-    for (int64_t r = 0; r < st.size[L][b.t]; ++r)
-      for (int64_t c = 0; c < st.size[L][b.s]; ++c) p.f.push_back(src[r * LS + c]);
-  }
+  cudaFree(stage);
+  cudaFree(d_tk);
 }
 
 // Host-side check that every access of a plan stays inside its arena: run before a
@@ -587,7 +588,15 @@ h2_status h2_build(const double* points, int64_t n, const h2_kernel* kernel, int
     h->m.st = structure_for(points, n, leaf_size, eta);
     Packed p;
     build_h2_host(*h->m.st, *kernel, eps, p);
-    unpack_to_device(p, h->m);
+    PackedView v;
+    v.kr = p.kr.data();
+    v.kc = p.kc.data();
+    const std::vector<double>* a[6] = {&p.vr, &p.vc, &p.er, &p.ec, &p.s, &p.f};
+    for (int i = 0; i < 6; ++i) {
+      v.arr[i] = a[i]->data();
+      v.len[i] = (int64_t)a[i]->size();
+    }
+    unpack_view_to_device(v, h->m);
     finish_handle(h.get(), o);
     *out = h.release();
   });
@@ -659,35 +668,13 @@ h2_status h2_import(const double* points, int64_t n, int32_t leaf_size, double e
     h2_opts o = defaults(opts);
     auto h = std::make_unique<h2_matrix>();
     h->m.st = structure_for(points, n, leaf_size, eta);
-    const Structure& st = *h->m.st;
-    const int nn = st.nnodes(), L = st.L;
-    Packed p;
-    p.kr.assign(kr, kr + nn);
-    p.kc.assign(kc, kc + nn);
-    int64_t nvr = 0, nvc = 0, ner = 0, nec = 0, ns = 0, nf = 0;
-    for (int64_t t = 0; t < (1LL << L); ++t) {
-      nvr += st.size[L][t] * kr[Structure::node(L, t)];
-      nvc += st.size[L][t] * kc[Structure::node(L, t)];
-    }
-    for (int l = 0; l < L; ++l)
-      for (int64_t t = 0; t < (1LL << l); ++t) {
-        ner += (int64_t)(kr[Structure::node(l + 1, 2 * t)] + kr[Structure::node(l + 1, 2 * t + 1)]) * kr[Structure::node(l, t)];
-        nec += (int64_t)(kc[Structure::node(l + 1, 2 * t)] + kc[Structure::node(l + 1, 2 * t + 1)]) * kc[Structure::node(l, t)];
-      }
-    for (int l = 0; l <= L; ++l)
-      for (auto& b : st.blocks[l]) {
-        if (b.kind == KR) ns += (int64_t)kr[Structure::node(l, b.t)] * kc[Structure::node(l, b.s)];
-        if (b.kind == KF) nf += st.size[L][b.t] * st.size[L][b.s];
-      }
-    if ((nvr && !vr) || (nvc && !vc) || (ner && !er) || (nec && !ec) || (ns && !s) || (nf && !f))
-      throw Error(H2_EINVAL, "null array");
-    p.vr.assign(vr, vr + nvr);
-    p.vc.assign(vc, vc + nvc);
-    p.er.assign(er, er + ner);
-    p.ec.assign(ec, ec + nec);
-    p.s.assign(s, s + ns);
-    p.f.assign(f, f + nf);
-    unpack_to_device(p, h->m);
+    PackedView v;
+    v.kr = kr;
+    v.kc = kc;
+    packed_lengths(*h->m.st, kr, kc, v.len);
+    const double* a[6] = {vr, vc, er, ec, s, f};
+    for (int i = 0; i < 6; ++i) v.arr[i] = a[i];
+    unpack_view_to_device(v, h->m);
     finish_handle(h.get(), o);
     *out = h.release();
   });
@@ -697,24 +684,19 @@ h2_status h2_export(h2_handle h, int64_t* sizes, int32_t* kr, int32_t* kc, doubl
                     double* ec, double* s, double* f) {
   if (!h || !sizes) return fail(H2_EINVAL, "null argument");
   return guarded([&] {
-    Packed p;
-    pack_from_device(h->m, p);
-    sizes[0] = (int64_t)p.kr.size();
-    sizes[1] = (int64_t)p.vr.size();
-    sizes[2] = (int64_t)p.vc.size();
-    sizes[3] = (int64_t)p.er.size();
-    sizes[4] = (int64_t)p.ec.size();
-    sizes[5] = (int64_t)p.s.size();
-    sizes[6] = (int64_t)p.f.size();
+    // sizes from the ranks alone; the arrays only when asked for
+    sync_ranks_to_host(h->m);
+    int64_t len[6];
+    packed_lengths(*h->m.st, h->m.h_kr.data(), h->m.h_kc.data(), len);
+    sizes[0] = (int64_t)h->m.h_kr.size();
+    for (int i = 0; i < 6; ++i) sizes[1 + i] = len[i];
     sizes[7] = 0;
-    if (kr) std::copy(p.kr.begin(), p.kr.end(), kr);
-    if (kc) std::copy(p.kc.begin(), p.kc.end(), kc);
-    if (vr) std::copy(p.vr.begin(), p.vr.end(), vr);
-    if (vc) std::copy(p.vc.begin(), p.vc.end(), vc);
-    if (er) std::copy(p.er.begin(), p.er.end(), er);
-    if (ec) std::copy(p.ec.begin(), p.ec.end(), ec);
-    if (s) std::copy(p.s.begin(), p.s.end(), s);
-    if (f) std::copy(p.f.begin(), p.f.end(), f);
+    if (kr) std::copy(h->m.h_kr.begin(), h->m.h_kr.end(), kr);
+    if (kc) std::copy(h->m.h_kc.begin(), h->m.h_kc.end(), kc);
+    double* const out[6] = {vr, vc, er, ec, s, f};
+    bool any = false;
+    for (int i = 0; i < 6; ++i) any = any || out[i];
+    if (any) pack_to_host(h->m, out);
   });
 }
 

@@ -267,7 +267,29 @@ struct Packed {
   std::vector<double> vr, vc, er, ec, s, f;
 };
 void build_h2_host(const Structure& st, const h2_kernel& k, double eps, Packed& out);
-void unpack_to_device(const Packed& p, Mat& m);
-void pack_from_device(Mat& m, Packed& p);
+// One block moved between the packed layout and the padded arena: rows x cols, dense
+// (row-major) at packed_off of the concatenated packed arrays, row stride ld at
+// arena_off of the arena (transfer.cu).
+struct CopyTask {
+  int64_t arena_off, packed_off;
+  int32_t rows, cols, ld, pad;
+};
+void launch_copy_tasks(const CopyTask* d_tasks, int64_t ntasks, double* packed, double* arena, bool to_arena,
+                       void* stream);
+// The packed arrays of a matrix as caller pointers (h2_import / h2_export): ranks, then
+// vr, vc, er, ec, s, f and their lengths.
+struct PackedView {
+  const int32_t* kr = nullptr;
+  const int32_t* kc = nullptr;
+  const double* arr[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int64_t len[6] = {0, 0, 0, 0, 0, 0};
+};
+// lengths of the six packed arrays from the ranks (a structure's sizes and blocks)
+void packed_lengths(const Structure& st, const int32_t* kr, const int32_t* kc, int64_t len[6]);
+// the blocks of the packed layout in order and their places in m's arena (m's offsets set)
+std::vector<CopyTask> copy_tasks(const Mat& m, const int32_t* kr, const int32_t* kc, int64_t len[6]);
+void unpack_view_to_device(const PackedView& v, Mat& m);
+// writes the packed arrays of m into the non-null caller pointers (host memory)
+void pack_to_host(Mat& m, double* const out[6]);
 
 }  // namespace h2
