@@ -228,6 +228,21 @@ void sync_ranks_to_host(Mat& m) {
   m.ranks_on_host = true;
 }
 
+// Large copies between caller memory (pageable, e.g. numpy arrays) and the device:
+// the range is page-locked for the copy so that it goes by DMA, then released; if it
+// cannot be registered (already registered, or refused) the plain copy is used.
+static void copy_host(void* dst, const void* src, size_t bytes, cudaMemcpyKind kind, const char* what) {
+  void* host = (void*)(kind == cudaMemcpyHostToDevice ? src : dst);
+  bool reg = false;
+  if (bytes >= ((size_t)64 << 20)) {
+    reg = cudaHostRegister(host, bytes, cudaHostRegisterDefault) == cudaSuccess;
+    if (!reg) cudaGetLastError();
+  }
+  cudaError_t e = cudaMemcpy(dst, src, bytes, kind);
+  if (reg) cudaHostUnregister(host);
+  cuda_check(e, what);
+}
+
 // Blocks of the packed layout (vr, vc, er, ec, s, f back to back, each block dense at
 // the actual ranks) and where they sit in the padded arena; len gets the six lengths.
 std::vector<CopyTask> copy_tasks(const Mat& m, const int32_t* kr, const int32_t* kc, int64_t len[6]) {
@@ -333,7 +348,7 @@ void unpack_view_to_device(const PackedView& v, Mat& m) {
     int64_t off = 0;
     for (int i = 0; i < 6; ++i) {
       if (len[i])
-        cuda_check(cudaMemcpy(stage + off, v.arr[i], len[i] * sizeof(double), cudaMemcpyHostToDevice), "upload arrays");
+        copy_host(stage + off, v.arr[i], len[i] * sizeof(double), cudaMemcpyHostToDevice, "upload arrays");
       off += len[i];
     }
     if (!tk.empty())
@@ -374,7 +389,7 @@ void pack_to_host(Mat& m, double* const out[6]) {
     int64_t off = 0;
     for (int i = 0; i < 6; ++i) {
       if (len[i] && out[i])
-        cuda_check(cudaMemcpy(out[i], stage + off, len[i] * sizeof(double), cudaMemcpyDeviceToHost), "download arrays");
+        copy_host(out[i], stage + off, len[i] * sizeof(double), cudaMemcpyDeviceToHost, "download arrays");
       off += len[i];
     }
   } catch (...) {
