@@ -230,7 +230,7 @@ h2_status h2_trace_read(h2_handle C, int32_t cap, int32_t* kind, int32_t* level,
                         double* flops, int32_t* count);
 /* Number of CUDA kernels this library has launched in this process so far (GEMM,
  * eigen, conversion and permutation kernels; not the no-allocation matvec's, and
- * not the driver's memsets and copies).  The difference of two readings counts the
+ * not the memsets and copies made through the CUDA runtime).  The difference of two readings counts the
  * kernels of the calls in between; pure host function, never fails for a non-NULL
  * argument. */
 h2_status h2_kernel_launches(uint64_t* count);
