@@ -41,7 +41,7 @@ typedef enum {
   H2_ESTRUCT = 4,      /* A and B do not share one cluster tree and block partition */
   H2_ETIMEOUT = 5,     /* a bounded device-side wait gave up                        */
   H2_EINTERNAL = 6,    /* internal consistency check failed                          */
-  H2_EUNSUPPORTED = 7  /* valid request this build does not implement               */
+  H2_EUNSUPPORTED = 7  /* valid request this library does not implement             */
 } h2_status;
 
 /* Kernel functions K(x, y), r = |x - y|; the diagonal (x == y) takes diag_re. */
@@ -120,7 +120,7 @@ typedef struct {
  *           (sampled) far field with sigma / sigma_1 > eps.
  * Structure (Sec. II): cardinality-balanced bisection cluster tree with all leaves
  * on level L, block partition by Eq. admCond with bounding boxes.  The numeric
- * construction is not specified by the paper (it cites another method); this build
+ * construction is not specified by the paper (it cites another method); this library
  * uses nested far-field sampling with interpolative skeletons (sampled far field
  * per cluster, skeleton rows chosen by pivoted Gram-Schmidt).  Errors: H2_EINVAL for bad sizes or non-finite points,
  * H2_EUNSUPPORTED for a complex kernel. */
@@ -136,7 +136,7 @@ h2_status h2_build(const double* points, int64_t n, const h2_kernel* kernel,
  * output of every segment and eigen task lies inside one live allocation of its
  * region (replayed in program order) or inside its matrix.  *checked gets the number of
  * programs checked (18).  H2_EINTERNAL names the first program and access that fails.
- * The paper has no counterpart: this checks the build's own memory layout. */
+ * The paper has no counterpart: this checks the library's own memory layout. */
 h2_status h2_plan_selfcheck(const double* points, int64_t n, int32_t leaf_size, double eta, double eps,
                             int32_t* checked);
 
