@@ -128,6 +128,22 @@ h2_status h2_build(const double* points, int64_t n, const h2_kernel* kernel,
                    int32_t leaf_size, double eta, double eps, const h2_opts* opts,
                    h2_handle* out);
 
+/* Failure injection for tests: after n more device allocations (n >= 0) every further
+ * one fails, and the call that needed it returns H2_ENOMEM with no partial result;
+ * n < 0 lifts the limit (the default).  Process-wide; never fails.  The paper has no
+ * counterpart. */
+h2_status h2_set_alloc_limit(int64_t n);
+
+/* Host-only size of the product program of C = A A (no GPU needed): tree, partition
+ * and H^2 ranks of the Laplace kernel as h2_build makes them (at eps), storage caps as
+ * an import sets them, rank cap 48, truncation rule `trunc`.  *flops gets the
+ * multiply-add flops counted over all GEMM items at the padded caps (2 m n k), and
+ * *segments / *items the numbers of output matrices and of products.  At constant rank
+ * all three grow linearly in N (Sec. V, time complexity at constant rank).  Errors:
+ * H2_EINVAL for bad arguments. */
+h2_status h2_plan_stats(const double* points, int64_t n, int32_t leaf_size, double eta, double eps, int32_t trunc,
+                        double* flops, int64_t* segments, int64_t* items);
+
 /* Host-only self-check of the product program (no device memory, no GPU needed):
  * builds the tree, partition and H^2 ranks of the Laplace kernel (as h2_build, at
  * ε = eps) for the points, then the program of C = A A for every truncation mode

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -47,6 +48,16 @@ struct h2_matrix {
   std::shared_ptr<PlanEntry> made_by;  // on C: the plan of the product that made it
   const h2_matrix* origin_A = nullptr;
   const h2_matrix* origin_B = nullptr;
+  // frees everything the handle owns (also for a handle whose making failed halfway)
+  ~h2_matrix() {
+    for (void* e : trace.ev) cudaEventDestroy((cudaEvent_t)e);
+    for (auto& kv : mv_plans) h2::free_plan(*kv.second);
+    if (d_user) cudaFree(d_user);
+    if (d_ars) cudaFree(d_ars);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    h2::free_mat(m);
+  }
 };
 
 namespace {
@@ -116,9 +127,17 @@ h2_status guarded(F&& f) {
   }
 }
 
+// failure injection for tests: >= 0 = device allocations still allowed, -1 = no limit
+static std::atomic<int64_t> g_alloc_left{-1};
+
 void* dmalloc(size_t bytes) {
   void* p = nullptr;
   if (bytes == 0) bytes = 256;
+  int64_t left = g_alloc_left.load();
+  while (left > 0 && !g_alloc_left.compare_exchange_weak(left, left - 1)) {
+  }
+  if (left == 0)
+    throw h2::Error(H2_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes refused (allocation limit)");
   cudaError_t e = cudaMalloc(&p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -614,6 +633,47 @@ h2_status h2_build(const double* points, int64_t n, const h2_kernel* kernel, int
     unpack_view_to_device(v, h->m);
     finish_handle(h.get(), o);
     *out = h.release();
+  });
+}
+
+h2_status h2_set_alloc_limit(int64_t n) {
+  g_alloc_left.store(n < 0 ? -1 : n);
+  return H2_OK;
+}
+
+h2_status h2_plan_stats(const double* points, int64_t n, int32_t leaf_size, double eta, double eps, int32_t trunc,
+                        double* flops, int64_t* segments, int64_t* items) {
+  if (!points || !flops || !segments || !items) return fail(H2_EINVAL, "null argument");
+  return guarded([&] {
+    if (!(eps > 0) || !(eps < 1)) throw Error(H2_EINVAL, "eps must lie in (0, 1)");
+    if (trunc < H2_TRUNC_PAPER || trunc > H2_TRUNC_FORMATTED) throw Error(H2_EINVAL, "unknown truncation rule");
+    auto st = build_structure(points, n, leaf_size, eta);
+    const double h = std::cbrt(1.0 / (double)n);
+    h2_kernel k{H2_K_LAPLACE, 0.0, 1.0 / (2.0 * M_PI * h), 0.0};
+    Packed p;
+    build_h2_host(*st, k, eps, p);
+    Mat m;
+    m.st = st;
+    m.Kr.assign(st->L + 1, 0);
+    m.Kc.assign(st->L + 1, 0);
+    for (int l = 0; l <= st->L; ++l)
+      for (int64_t t = 0; t < (1LL << l); ++t) {
+        m.Kr[l] = std::max(m.Kr[l], p.kr[Structure::node(l, t)]);
+        m.Kc[l] = std::max(m.Kc[l], p.kc[Structure::node(l, t)]);
+      }
+    for (int l = 0; l <= st->L; ++l) {
+      m.Kr[l] = cap_round(m.Kr[l]);
+      m.Kc[l] = cap_round(m.Kc[l]);
+    }
+    mat_elems(m);
+    Plan P;
+    Mat C;
+    C.st = st;
+    MmpParams prm{1e-4, trunc, 48, H2_FP64};
+    build_mmp_plan(m, m, C, prm, P);
+    *flops = (double)P.flops;
+    *segments = (int64_t)P.segs.size();
+    *items = (int64_t)P.items.size();
   });
 }
 
@@ -1277,17 +1337,8 @@ const char* h2_trace_phase(h2_handle C, int32_t i) {
 
 void h2_destroy(h2_handle h) {
   if (!h) return;
-  for (void* e : h->trace.ev) cudaEventDestroy((cudaEvent_t)e);
   cudaDeviceSynchronize();
-  h->plans_held.clear();
-  h->made_by.reset();
-  for (auto& kv : h->mv_plans) free_plan(*kv.second);
-  if (h->d_user) cudaFree(h->d_user);
-  if (h->d_ars) cudaFree(h->d_ars);
-  if (h->ev0) cudaEventDestroy(h->ev0);
-  if (h->ev1) cudaEventDestroy(h->ev1);
-  free_mat(h->m);
-  delete h;
+  delete h;  // the handle's destructor frees what it owns; held plans go with it
 }
 
 }  // extern "C"

@@ -24,7 +24,7 @@ _TRUNC = {"paper": TRUNC_PAPER, "sv": TRUNC_SV, "full": TRUNC_FULL, "formatted":
 # exported symbols and their signatures (checked by the CPU tests)
 SYMBOLS = ["h2_build", "h2_import", "h2_export", "h2_mmp", "h2_mmp_batched", "h2_matvec", "h2_matvec_noalloc", "h2_to_dense", "h2_info",
            "h2_tree_perm", "h2_level_blocks", "h2_trace_enable", "h2_trace_read", "h2_trace_flops", "h2_trace_phase", "h2_destroy",
-           "h2_last_error", "h2_kernel_launches", "h2_plan_selfcheck"]
+           "h2_last_error", "h2_kernel_launches", "h2_plan_selfcheck", "h2_set_alloc_limit", "h2_plan_stats"]
 
 
 class H2Error(RuntimeError):
@@ -77,6 +77,8 @@ def load(path: str = LIB_PATH):
     lib.h2_trace_flops.argtypes = [P, P]
     lib.h2_kernel_launches.argtypes = [P]
     lib.h2_plan_selfcheck.argtypes = [P, I64, I32, C.c_double, C.c_double, P]
+    lib.h2_set_alloc_limit.argtypes = [I64]
+    lib.h2_plan_stats.argtypes = [P, I64, I32, D, D, I32, P, P, P]
     lib.h2_trace_phase.argtypes = [P, I32]
     lib.h2_trace_phase.restype = C.c_char_p
     lib.h2_destroy.argtypes = [P]
@@ -252,6 +254,21 @@ def plan_selfcheck(points: np.ndarray, leaf_size: int = 32, eta: float = 1.0, ep
     n = C.c_int32(0)
     _check(load().h2_plan_selfcheck(_ptr(pts), pts.shape[0], leaf_size, float(eta), float(eps), C.byref(n)))
     return int(n.value)
+
+
+def set_alloc_limit(n: int) -> None:
+    """Test hook: after n more device allocations every further one fails (n < 0: off)."""
+    _check(load().h2_set_alloc_limit(int(n)))
+
+
+def plan_stats(points: np.ndarray, leaf_size: int = 32, eta: float = 1.0, eps: float = 1e-4,
+               trunc: str = "paper") -> tuple:
+    """(flops, segments, items) of the program of C = A A for these points, on the host."""
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    fl, sg, it = C.c_double(0), C.c_int64(0), C.c_int64(0)
+    _check(load().h2_plan_stats(_ptr(pts), pts.shape[0], leaf_size, float(eta), float(eps), _TRUNC[trunc],
+                                C.byref(fl), C.byref(sg), C.byref(it)))
+    return fl.value, int(sg.value), int(it.value)
 
 
 def kernel_launches() -> int:

@@ -235,3 +235,26 @@ def test_batched_graph_and_replay_equal_single(lib, precision, trunc):
         x = torch.from_numpy(inputs.standard_normal((h.n, 3), seed=5)).cuda()
         assert torch.equal(c.matvec(x), s.matvec(x))
         assert c.info()["cap_hits"] == s.info()["cap_hits"]
+
+
+def test_allocation_failure_during_a_product_leaves_the_library_usable(lib):
+    # a product that needs a new plan and a new output is refused at its first, second,
+    # ... device allocation: each attempt fails with H2_ENOMEM, and afterwards the same
+    # product succeeds and an earlier one still gives bit-identical results
+    import torch
+    w, leaf, eta, A = oracle_case("cubes_1024")
+    ga = lib.h2_import(w.points, leaf, eta, pack(A))
+    ref = ga.mmp(ga, 1e-4, precision=lib.MIXED_FP32)
+    x = torch.from_numpy(inputs.standard_normal((ga.n, 2), seed=3)).cuda()
+    y_ref = ref.matvec(x)
+    for k in (0, 1, 2, 3, 5):
+        lib.set_alloc_limit(k)
+        try:
+            with pytest.raises(lib.H2Error) as e:
+                ga.mmp(ga, 1e-4, precision=lib.MIXED_FP32, rank_cap=40)
+            assert e.value.code == 2
+        finally:
+            lib.set_alloc_limit(-1)
+    c = ga.mmp(ga, 1e-4, precision=lib.MIXED_FP32, rank_cap=40)
+    assert c.info()["cap_hits"] == 0
+    assert torch.equal(ga.mmp(ga, 1e-4, precision=lib.MIXED_FP32).matvec(x), y_ref)

@@ -33,3 +33,31 @@ def test_every_program_stays_inside_its_allocations(lib, name, points, leaf, eta
 def test_selfcheck_rejects_bad_arguments(lib):
     with pytest.raises(lib.H2Error):
         lib.plan_selfcheck(np.zeros((10, 3)), 8, 1.0, 2.0)
+
+
+def test_program_cost_per_point_stays_bounded(lib):
+    # Sec. V: at constant rank the product costs O(N).  On the cube array (1024 points
+    # per cube) N goes from 16,384 to 65,536; the share of boundary clusters still falls
+    # (pre-asymptotic), so the cost per point may rise a little, but far less than
+    # the factor 4 of an O(N^2) method or of pairs emitted quadratically.
+    per = []
+    for nx in (4, 8):
+        w = inputs.workload_cube_array(nx, nx, 1024)
+        fl, sg, it = lib.plan_stats(w.points, 32, 1.0, 1e-4)
+        n = w.points.shape[0]
+        per.append((fl / n, sg / n, it / n))
+    for a, b in zip(per[0], per[1]):
+        assert b / a < 1.5, (per, b / a)
+
+
+def test_allocation_failure_is_reported_cleanly(lib):
+    # the first device allocation of h2_build is refused: the call fails with
+    # H2_ENOMEM before any device work, and the limit is lifted afterwards
+    pts = inputs.uniform_cube(500, 1)
+    lib.set_alloc_limit(0)
+    try:
+        with pytest.raises(lib.H2Error) as e:
+            lib.h2_build(pts, inputs.laplace_spec(500 ** (-1 / 3)), 32, 1.0, 1e-4)
+        assert e.value.code == 2 and "allocation limit" in str(e.value)
+    finally:
+        lib.set_alloc_limit(-1)
