@@ -1,9 +1,9 @@
 """New cluster bases from normalised Gram sums (oracle; test infrastructure only).
 
-Sec. III-C (leaf level) and Sec. IV-C (non-leaf level): the three Gram matrices of
-a cluster are each normalised, summed, and the summed matrix is decomposed; the
-singular vectors whose normalised singular values exceed eps_trunc form the new
-basis (or the new stacked transfer matrix).
+Sec. III-C (leaf level) and Sec. IV-C (non-leaf level): each of a cluster's three Gram
+matrices is scaled to unit norm, the scaled matrices are added, and the new basis (or
+the new stacked transfer matrix) is made of the eigenvectors of that sum whose
+eigenvalue, relative to the largest one, lies above the truncation threshold.
 
 Readings taken here:
   * "normalised" = divided by the Frobenius norm; a Gram matrix that is exactly zero
