@@ -35,6 +35,7 @@ WORKLOADS = {
     "cubes4x4": (4, 4, 4096, 1e-4, "N=65,536 panel centroids on a 4x4 array of unit cubes"),
     "cubes2x2": (2, 2, 1024, 1e-4, "N=4,096 panel centroids on a 2x2 array of unit cubes"),
     "sample": (2, 2, 3072, 1e-4, "N=12,288 panel centroids on a 2x2 array of unit cubes"),
+    "sample_ref": (2, 2, 2048, 1e-4, "N=8,192 panel centroids on a 2x2 array of unit cubes"),
 }
 # DRAM traffic of the float32 GEMM kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum over the 115 GEMM launches of one product of the N=65,536
@@ -107,12 +108,13 @@ class Clocks:
         return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def reference_arm(args):
+def reference_arm(args, sample="sample"):
     """The CPU oracle on a bounded sample of the workload (1 core, float64)."""
     env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
     t0 = time.time()
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-sample",
-                          "--steps", str(args.steps)], capture_output=True, text=True, env=env)
+                          "--steps", str(args.steps), "--workload", sample], capture_output=True, text=True,
+                         env=env)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
     res = json.loads(out.stdout.strip().splitlines()[-1])
@@ -120,14 +122,14 @@ def reference_arm(args):
     return res
 
 
-def oracle_sample(steps: int):
+def oracle_sample(steps: int, sample: str = "sample"):
     """Child process: oracle product on N=12288 points of the cube-array geometry."""
     import numpy as np
 
     from oracle import h2 as oh2
     from oracle import mmp as ommp
     from paper_1908_05218_gb300 import inputs
-    nx, ny, ppc, eps, _ = WORKLOADS["sample"]
+    nx, ny, ppc, eps, _ = WORKLOADS[sample]
     wa = inputs.workload_cube_array(nx, ny, ppc)
     wb = inputs.workload_cube_array(nx, ny, ppc, kernel="invr2")
     A = oh2.build(wa.points, wa.kernel, LEAF, ETA, EPS_H2)
@@ -240,7 +242,7 @@ def main():
     args = ap.parse_args()
 
     if args.oracle_sample:
-        oracle_sample(args.steps)
+        oracle_sample(args.steps, args.workload if args.workload.startswith("sample") else "sample")
         return
 
     rank = int(os.environ.get("RANK", "0"))
@@ -256,12 +258,14 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        r = reference_arm(args)
+        # (a smaller sample than the in-line CPU baseline, so that K steps stay within
+        # a few minutes: about 8 s per step on one Neoverse-V2 core)
+        r = reference_arm(args, "sample_ref")
         gbs = r["bytes"] / r["t"] / 1e9
         line = {"metric": metric, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus, "steps": r["steps"],
                 "warmup": 0, "ms_per_step": r["t"] * 1e3, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-                "config": {"workload": f"cube array 2x2, 3072 points per cube (N={r['n']}), leaf {LEAF}, "
+                "config": {"workload": f"cube array 2x2, 2048 points per cube (N={r['n']}), leaf {LEAF}, "
                                        f"eta {ETA}, eps {eps}, A: 1/(4 pi r), B: 1/r^2",
                            "sample_of": desc},
                 "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
