@@ -41,8 +41,8 @@ WORKLOADS = {
 # dram__bytes_write.sum over the 115 GEMM launches of one product of the N=65,536
 # cube-array workload; profiles/dram_traffic_h2mmp_N65536_mixed.md), valid only for the
 # kernel source it was taken on.  Other workloads scale it by the executed flops.
-TRAFFIC = {"kernel": "seg_gemm32_kernel", "src_sha256": "f7bcf9a6f74f948935028d9d95a9c5fd600dc64d4a6478f14c2f217dc95940c5",
-           "bytes_per_product": 38.56e9, "executed_flops_per_product": 325980932076.0}
+TRAFFIC = {"kernel": "seg_gemm32_kernel", "src_sha256": "f1a0945e10978651f03c38579a689c66fc4383c89917323954e4858c2a12238c",
+           "bytes_per_product": 38.557e9, "executed_flops_per_product": 325980932076.0}
 LEAF, ETA, EPS_H2 = 32, 1.0, 1e-4
 
 

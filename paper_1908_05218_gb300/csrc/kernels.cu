@@ -251,8 +251,8 @@ __device__ __forceinline__ void cp_async16(float* dst, const float* src, int byt
 
 template <bool AMK>
 __device__ __forceinline__ void slice_fma(const float* __restrict__ a_s, const float* __restrict__ b_s, int kf,
-                                          int tx, int ty, float acc[4][4]) {
-  for (int kk = 0; kk < kf; kk += 4) {
+                                          int tx, int ty, float acc[4][4], int k0, int kstep) {
+  for (int kk = k0; kk < kf; kk += kstep) {
     float a[4][4], b[4][4];  // a[i][q]: row 4 ty + i, k kk + q;  b[q][j]: k kk + q, col 4 tx + j
     if (AMK) {
 #pragma unroll
@@ -325,13 +325,18 @@ __global__ void __launch_bounds__(GNT, 12) seg_gemm32_kernel(const Seg* __restri
     const int nc = min(TILE, N - n0);
     for (int m0 = 0; m0 < M; m0 += TILE) {
       const int mc = min(TILE, M - m0);
-      // the tile's live 4 x 4 blocks go to threads 0 .. nthr-1 (row-major), so a warp
-      // whose threads all lie beyond them skips the arithmetic (an m x n tile of at
-      // most 32 live blocks, e.g. 20 x 24, takes one warp); idle threads read block 0
+      // the tile's live 4 x 4 blocks go to threads 0 .. nthr-1 (row-major); idle
+      // threads read block 0.  A tile of at most 32 live blocks (e.g. 20 x 24) is
+      // computed by both warps on the same blocks, each over every other k-chunk of
+      // four, and the two partial sums are added in a fixed order at the end;
+      // otherwise a warp whose threads all lie beyond the blocks skips the arithmetic
       const int ncq = (nc + 3) >> 2, nthr = ((mc + 3) >> 2) * ncq;
-      const bool mine = tid < nthr;
-      const int qy = mine ? tid / ncq : 0, qx = mine ? tid - qy * ncq : 0;
-      const bool live = (tid & ~31) < nthr;
+      const bool split = nthr <= 32;
+      const int me = split ? lane : tid;
+      const bool mine = me < nthr;
+      const int qy = mine ? me / ncq : 0, qx = mine ? me - qy * ncq : 0;
+      const bool live = split || (tid & ~31) < nthr;
+      const int k0 = split ? 4 * (tid >> 5) : 0, kstep = split ? 8 : 4;
       float acc[4][4];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
@@ -467,14 +472,27 @@ __global__ void __launch_bounds__(GNT, 12) seg_gemm32_kernel(const Seg* __restri
         cp_wait1();
         __syncthreads();
         if (live) {
-          if (!ta) slice_fma<true>(sA[buf], sB[buf], kf, qx, qy, acc);
-          else slice_fma<false>(sA[buf], sB[buf], kf, qx, qy, acc);
+          if (!ta) slice_fma<true>(sA[buf], sB[buf], kf, qx, qy, acc, k0, kstep);
+          else slice_fma<false>(sA[buf], sB[buf], kf, qx, qy, acc, k0, kstep);
         }
         __syncthreads();
         buf ^= 1;
         kf = kf_next;
       }
-      if (mine) {
+      if (split) {  // warp 0 adds warp 1's partial sums (the slices are done: sA is free)
+        float* red = sA[0];
+        if (tid >= 32) {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) red[e * 32 + lane] = acc[e >> 2][e & 3];
+        }
+        __syncthreads();
+        if (tid < 32) {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) acc[e >> 2][e & 3] += red[e * 32 + lane];
+        }
+        __syncthreads();
+      }
+      if (mine && (!split || tid < 32)) {
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
