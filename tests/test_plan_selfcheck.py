@@ -61,3 +61,15 @@ def test_allocation_failure_is_reported_cleanly(lib):
         assert e.value.code == 2 and "allocation limit" in str(e.value)
     finally:
         lib.set_alloc_limit(-1)
+
+
+def test_program_size_follows_the_truncation_rule(lib):
+    # the paper and sv rules differ only in the threshold the eigen step applies, so
+    # they share one program; the full rule keeps every eigenvector (larger caps, more
+    # work); the formatted product keeps A's and B's bases and skips the Gram sums and
+    # eigen-decompositions altogether (fewer segments and flops)
+    w = inputs.workload_cube_array(2, 2, 1024)
+    st = {t: lib.plan_stats(w.points, 32, 1.0, 1e-4, t) for t in ("paper", "sv", "full", "formatted")}
+    assert st["paper"] == st["sv"]
+    assert st["full"][0] > st["paper"][0]
+    assert st["formatted"][0] < st["paper"][0] and st["formatted"][1] < st["paper"][1]
