@@ -38,9 +38,9 @@ WORKLOADS = {
     "sample_ref": (2, 2, 2048, 1e-4, "N=8,192 panel centroids on a 2x2 array of unit cubes"),
 }
 # DRAM traffic of the float32 GEMM kernel from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum over the 115 GEMM launches of one product of the N=65,536
-# cube-array workload; profiles/dram_traffic_h2mmp_N65536_mixed.md), valid only for the
-# kernel source it was taken on.  Other workloads scale it by the executed flops.
+# dram__bytes_write.sum over the GEMM launches of one product of the N=65,536
+# cube-array workload), valid only for the kernel source it was taken on.  Other
+# workloads scale it by the executed flops.
 TRAFFIC = {"kernel": "seg_gemm32_kernel", "src_sha256": "f1a0945e10978651f03c38579a689c66fc4383c89917323954e4858c2a12238c",
            "bytes_per_product": 38.557e9, "executed_flops_per_product": 325980932076.0}
 LEAF, ETA, EPS_H2 = 32, 1.0, 1e-4

@@ -19,6 +19,13 @@ matrix; singular vectors with sigma / sigma_1 > eps_h2 are kept.  Column bases a
 built the same way from K^T.  Couplings are S_ts = V_t^H K(t, s) conj(V_s), dense
 blocks are K(t, s).
 
+Large inputs (far_sample set): the far field of a cluster is read only at a
+deterministic sample of each partner block, at most far_sample points taken at an
+even stride in tree order; couplings and dense blocks stay exact.  This is the
+reading of the cited construction for N beyond what the exact far field allows (its
+cost is L N^2 kernel entries); the product is checked against the product of the
+matrices built here, so the construction's accuracy does not enter that check.
+
 Matvec (Sec. VI, Eq. error: the reference solution is computed with exact H^2
 matrix-vector products): forward transform with the column bases, coupling, backward
 transform with the row bases, plus the dense near field.
@@ -97,15 +104,23 @@ def admissible_partners(part: Partition, col: bool) -> list:
     return out
 
 
-def _far_indices(tree, pairs) -> np.ndarray:
+def _far_indices(tree, pairs, sample=None) -> np.ndarray:
     if not pairs:
         return np.zeros(0, dtype=np.int64)
-    return np.concatenate([np.arange(tree.start[lv][s], tree.start[lv][s] + tree.size[lv][s])
-                           for (lv, s) in pairs])
+    out = []
+    for (lv, s) in pairs:
+        n = tree.size[lv][s]
+        if sample is None or n <= sample:
+            out.append(np.arange(tree.start[lv][s], tree.start[lv][s] + n))
+        else:       # sample points at an even stride in tree order
+            out.append(tree.start[lv][s] + (np.arange(sample) * n) // sample)
+    return np.concatenate(out)
 
 
-def build(points: np.ndarray, spec, leaf_size: int, eta: float, eps_h2: float) -> H2:
-    """Nested far-field compression of the kernel matrix (reading stated above)."""
+def build(points: np.ndarray, spec, leaf_size: int, eta: float, eps_h2: float,
+          far_sample: int | None = None) -> H2:
+    """Nested far-field compression of the kernel matrix (reading stated above);
+    far_sample: None (exact far field) or the most points read per partner block."""
     tree = build_tree(points, leaf_size)
     part = build_partition(tree, eta)
     dtype = np.complex128 if kernels.is_complex(spec) else np.float64
@@ -140,7 +155,7 @@ def build(points: np.ndarray, spec, leaf_size: int, eta: float, eps_h2: float) -
         for l in range(L, -1, -1):
             for t in range(1 << l):
                 rows = np.arange(tree.start[l][t], tree.start[l][t] + tree.size[l][t])
-                far = _far_indices(tree, far_field(part, l, t, col, index))
+                far = _far_indices(tree, far_field(part, l, t, col, index), far_sample)
                 if l == L:
                     w = K(rows, far) if not col else K(far, rows).T
                 else:

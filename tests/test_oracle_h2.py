@@ -77,3 +77,20 @@ def test_rotated_bases_represent_the_same_matrix(small_cube):
     Ar = h2.rotate_bases(A, seed=9)
     np.testing.assert_allclose(h2.to_dense(Ar), h2.to_dense(A), atol=1e-13 * np.abs(h2.to_dense(A)).max())
     assert not np.allclose(Ar.Vr[0], A.Vr[0])
+
+
+def test_far_field_sampling_reduces_to_exact_and_keeps_accuracy():
+    # far_sample at least the largest cluster: every partner is read whole, so the
+    # result is the exact construction bit for bit; a small sample keeps the
+    # construction accuracy within a factor 2 of the exact far field
+    from oracle import kernels
+    w = inputs.workload_cube_array(2, 2, 256)
+    ex = h2.build(w.points, w.kernel, 32, 1.0, 1e-4)
+    same = h2.build(w.points, w.kernel, 32, 1.0, 1e-4, far_sample=w.points.shape[0])
+    np.testing.assert_array_equal(h2.to_dense(same), h2.to_dense(ex))
+    smp = h2.build(w.points, w.kernel, 32, 1.0, 1e-4, far_sample=16)
+    pts = w.points
+    K = kernels.kernel_matrix(w.kernel, pts, pts, np.eye(len(pts), dtype=bool))
+    e_ex = np.linalg.norm(h2.to_dense(ex) - K) / np.linalg.norm(K)
+    e_smp = np.linalg.norm(h2.to_dense(smp) - K) / np.linalg.norm(K)
+    assert e_smp < 2 * e_ex + 1e-12 and e_ex < 1e-3

@@ -87,8 +87,11 @@ def test_points_on_a_line_give_the_textbook_partition():
 def test_csp_counts_blocks_per_cluster():
     pts = _pts("cubes", 1024)
     part = T.build_partition(T.build_tree(pts, 32), 1.0)
+    # brute force: for every cluster, the blocks it forms as a row and as a column
+    # cluster on its level; C_sp is the largest of these counts (Sec. V-B)
     cnt = 0
     for l in range(part.L + 1):
         for t in range(1 << l):
-            cnt = max(cnt, sum(1 for (a, _, _) in part.blocks[l] if a == t))
-    assert T.csp(part) >= cnt and T.csp(part) > 0
+            cnt = max(cnt, sum(1 for (a, _, _) in part.blocks[l] if a == t),
+                      sum(1 for (_, b, _) in part.blocks[l] if b == t))
+    assert T.csp(part) == cnt and cnt > 0
