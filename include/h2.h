@@ -19,8 +19,7 @@
  *     permutes to its cluster-tree order internally.
  *   - Real kernels only on the GPU path in this version (kind 0 and 1); the
  *     complex Helmholtz kernel returns H2_EUNSUPPORTED.
- *   - Arithmetic: float64 throughout (H2_FP64) or float32 bulk products with
- *     float64 Gram matrices, eigen-decompositions and bases (H2_MIXED_FP32).
+ *   - Arithmetic: see h2_precision.
  */
 #ifndef H2_GB300_H
 #define H2_GB300_H
@@ -58,12 +57,28 @@ typedef struct {
   double diag_im;
 } h2_kernel;
 
+/* Arithmetic of the product.  In every mode the normalised Gram sum, the rank decision
+ * and the re-orthonormalisation of the new bases are float64, and C is stored in float64.
+ * The mixed modes differ in the small matrix products (dense targets, Gram matrices,
+ * projections, collects, couplings, split), which read float32 copies of A and B:  */
 typedef enum {
-  H2_FP64 = 0,         /* every product, Gram and eigen-decomposition in float64 */
-  H2_MIXED_FP32 = 1    /* dense and coupling products in float32 (float32
-                          accumulation); Gram sums, eigen-decompositions, new bases
-                          and projections in float64 */
+  H2_FP64 = 0,          /* every product, Gram matrix and eigen-decomposition in float64 */
+  H2_MIXED_FP32 = 1,    /* products in float32 with float32 accumulation (CUDA cores);
+                           eigen-decomposition by float32 Jacobi, ranks decided by
+                           float64 Rayleigh quotients, kept vectors re-orthonormalised
+                           in float64 (Newton-Schulz) */
+  H2_MIXED_TF32X3 = 2,  /* as H2_MIXED_FP32, with the products on the tensor cores
+                           (tcgen05): each float32 operand split into two TF32 parts,
+                           three TF32 products per pair, float32 accumulation */
+  H2_MIXED_BF16X3 = 3   /* as H2_MIXED_TF32X3 with three BF16 parts per operand */
 } h2_precision;
+
+/* Norm that scales each Gram matrix before the sum (Sec. III-C, "normalized"). */
+typedef enum {
+  H2_NORM_FROBENIUS = 0, /* ||G_m||_F (default)                                    */
+  H2_NORM_SPECTRAL = 1   /* ||G_m||_2, the largest eigenvalue (each component is
+                            decomposed once more; float64 eigen kernel)            */
+} h2_norm;
 
 /* Truncation rule of the new cluster bases (Sec. III-C, IV-C): the summed,
  * normalised Gram matrix G is decomposed, G = U diag(lambda) U^H, and column m of U
@@ -86,8 +101,13 @@ typedef struct {
   int32_t rank_cap;    /* largest rank of a non-leaf cluster of C, 1..128; 0 =
                           default 48; ranks above it are cut to the cap and
                           counted in h2_stats.cap_hits                            */
-  int32_t reserved;
+  int32_t norm;        /* h2_norm, default H2_NORM_FROBENIUS                     */
   void* stream;        /* cudaStream_t, NULL = legacy default stream            */
+  int32_t autotune;    /* 0: fixed kernel choices (default); 1: the first product
+                          of a program times the candidate kernels of every launch
+                          group and keeps the fastest for later products (results
+                          do not depend on the choice in float64; see h2_precision) */
+  int32_t reserved;    /* must be 0 */
 } h2_opts;             /* a NULL h2_opts* means all defaults */
 
 typedef struct {
@@ -199,9 +219,12 @@ h2_status h2_mmp(h2_handle A, h2_handle B, double eps, const h2_opts* opts,
 h2_status h2_mmp_batched(const h2_handle* A, const h2_handle* B, int32_t count, double eps,
                          const h2_opts* opts, h2_handle* C);
 
-/* y = H x (exact H^2 arithmetic: forward transform, coupling, backward transform,
- * near field).  x, y: device float64, column-major n x nrhs, user order; y is
- * overwritten.  Enqueued on the stream of the handle's last call. */
+/* y = H x in exact H^2 arithmetic (Sec. II representation; the products A(B x) of
+ * Eq. error in Sec. VI-A are formed with it): forward transform with the column bases,
+ * coupling matrices, backward transform with the row bases, plus the dense near field.
+ * x, y: device float64, column-major n x nrhs, user order; y is overwritten
+ * (x and y must not overlap).  nrhs 1..16384.  Enqueued on the stream of the handle's
+ * last call.  Errors: H2_EINVAL for null pointers or nrhs out of range. */
 h2_status h2_matvec(h2_handle h, const double* x, double* y, int64_t nrhs);
 
 /* y = H x like h2_matvec, but the call allocates no memory at all: its work space
@@ -221,8 +244,9 @@ h2_status h2_matvec(h2_handle h, const double* x, double* y, int64_t nrhs);
  * Enqueued on the stream of the handle's last call. */
 h2_status h2_matvec_noalloc(h2_handle h, const double* x, double* y, int64_t nrhs);
 
-/* Dense n x n matrix, device float64, column-major, user order (testing; n <=
- * 16384). */
+/* Dense n x n matrix of the H^2 matrix (Sec. II: R blocks V_t S_ts V_s^T through the
+ * nested bases, F blocks as stored), device float64, column-major, user order; for
+ * testing, n <= 16384 (H2_EINVAL above).  Synchronises the handle's stream. */
 h2_status h2_to_dense(h2_handle h, double* out);
 
 /* Statistics; synchronises. */

@@ -6,8 +6,9 @@ the new stacked transfer matrix) is made of the eigenvectors of that sum whose
 eigenvalue, relative to the largest one, lies above the truncation threshold.
 
 Readings taken here:
-  * "normalised" = divided by the Frobenius norm; a Gram matrix that is exactly zero
-    is left out of the sum;
+  * "normalised" = divided by the Frobenius norm (the default; the spectral norm on
+    request, norm="spectral"); a Gram matrix that is exactly zero is left out of the
+    sum;
   * the summed G is Hermitian positive semi-definite, so its SVD is its eigen-
     decomposition; the k-th vector is kept when lambda_k / lambda_1 > threshold with
     threshold = eps (mode "paper": the normalised singular values of G itself, the
@@ -27,15 +28,17 @@ from __future__ import annotations
 import numpy as np
 
 PAPER, SV, FULL, FORMATTED = "paper", "sv", "full", "formatted"
+FRO, SPECTRAL = "fro", "spectral"
 
 
-def normalized_sum(grams, dim: int, dtype) -> np.ndarray:
-    """G = sum of G_m / ||G_m||_F over the nonzero G_m (Sec. III-C, normalised sum)."""
+def normalized_sum(grams, dim: int, dtype, norm: str = FRO) -> np.ndarray:
+    """G = sum of G_m / ||G_m|| over the nonzero G_m (Sec. III-C, normalised sum);
+    ||.|| is the Frobenius norm, or the spectral norm for norm="spectral"."""
     g = np.zeros((dim, dim), dtype=dtype)
     for gm in grams:
         if gm is None:
             continue
-        nrm = np.linalg.norm(gm)
+        nrm = np.linalg.norm(gm) if norm == FRO else np.linalg.norm(gm, 2)
         if nrm > 0.0:
             g = g + gm / nrm
     return g

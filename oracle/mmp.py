@@ -122,7 +122,7 @@ def basis_products(A: H2, Bm: H2) -> dict:
 
 
 def mmp(A: H2, Bm: H2, eps: float, mode: str = Bs.PAPER, cap: int | None = None,
-        stats: dict | None = None) -> H2:
+        stats: dict | None = None, norm: str = Bs.FRO) -> H2:
     part = A.part
     assert Bm.part.blocks == part.blocks, "A and B must share one block partition"
     tree = part.tree
@@ -130,6 +130,7 @@ def mmp(A: H2, Bm: H2, eps: float, mode: str = Bs.PAPER, cap: int | None = None,
     dtype = np.result_type(A.dtype, Bm.dtype)
     C = H2(part, dtype)
     lmin = l_min(part)
+    margins = {}             # (level, cluster, column side) -> truncation margin
     Bj = basis_products(A, Bm)
 
     def denseA(i, j, kind):           # leaf block of A as a full matrix (Sec. III-A)
@@ -172,8 +173,9 @@ def mmp(A: H2, Bm: H2, eps: float, mode: str = Bs.PAPER, cap: int | None = None,
                 Y = A.Fb[(i, j)] @ Bm.Vr[j]
                 g2 = Y @ _h(Y) if g2 is None else g2 + Y @ _h(Y)   # Eq. Gr2L
         g3 = A.Vr[i] @ _h(A.Vr[i])                                  # Eq. Gr3L
-        G = Bs.normalized_sum([g1, g2, g3], n_i, dtype)
-        Vn_r[i], _ = Bs.truncated_eigvecs(G, eps, mode, cap)
+        G = Bs.normalized_sum([g1, g2, g3], n_i, dtype, norm)
+        Vn_r[i], lam = Bs.truncated_eigvecs(G, eps, mode, cap)
+        margins[(L, i, False)] = _margin(lam, eps, mode)
     for k in ([] if formatted else range(1 << L)):
         n_k = tree.size[L][k]
         g1 = sum(G1c[k]) if G1c[k] else None
@@ -183,8 +185,9 @@ def mmp(A: H2, Bm: H2, eps: float, mode: str = Bs.PAPER, cap: int | None = None,
                 Y = A.Vc[j].T @ Bm.Fb[(j, k)]
                 g2 = Y.T @ Y.conj() if g2 is None else g2 + Y.T @ Y.conj()   # Eq. case2-ch
         g3 = Bm.Vc[k] @ _h(Bm.Vc[k])                                          # Eq. case3-ch
-        G = Bs.normalized_sum([g1, g2, g3], n_k, dtype)
-        Vn_c[k], _ = Bs.truncated_eigvecs(G, eps, mode, cap)
+        G = Bs.normalized_sum([g1, g2, g3], n_k, dtype, norm)
+        Vn_c[k], lam = Bs.truncated_eigvecs(G, eps, mode, cap)
+        margins[(L, k, True)] = _margin(lam, eps, mode)
     if formatted:                          # the existing formatted product keeps the bases
         Vn_r = {i: A.Vr[i] for i in range(1 << L)}
         Vn_c = {k: Bm.Vc[k] for k in range(1 << L)}
@@ -281,8 +284,9 @@ def mmp(A: H2, Bm: H2, eps: float, mode: str = Bs.PAPER, cap: int | None = None,
             Pch = _blkdiag(PA[(l + 1, 2 * i)], PA[(l + 1, 2 * i + 1)])
             W = Pch @ A.Er[(l, i)]
             g3 = W @ _h(W)                                                 # Eq. case3-ch-nl
-            G = Bs.normalized_sum([g1, g2, g3], dim, dtype)
-            En_r[i], _ = Bs.truncated_eigvecs(G, eps, mode, cap)
+            G = Bs.normalized_sum([g1, g2, g3], dim, dtype, norm)
+            En_r[i], lam = Bs.truncated_eigvecs(G, eps, mode, cap)
+            margins[(l, i, False)] = _margin(lam, eps, mode)
         for k in ([] if formatted else range(1 << l)):
             dim = kCc(2 * k) + kCc(2 * k + 1)
             g1 = None
@@ -297,8 +301,9 @@ def mmp(A: H2, Bm: H2, eps: float, mode: str = Bs.PAPER, cap: int | None = None,
             Pch = _blkdiag(PB[(l + 1, 2 * k)], PB[(l + 1, 2 * k + 1)])
             W = Pch.T @ Bm.Ec[(l, k)].conj()
             g3 = W @ _h(W)
-            G = Bs.normalized_sum([g1, g2, g3], dim, dtype)
-            En_c[k], _ = Bs.truncated_eigvecs(G, eps, mode, cap)
+            G = Bs.normalized_sum([g1, g2, g3], dim, dtype, norm)
+            En_c[k], lam = Bs.truncated_eigvecs(G, eps, mode, cap)
+            margins[(l, k, True)] = _margin(lam, eps, mode)
         for t in range(1 << l):
             C.Er[(l, t)] = En_r[t]
             C.Ec[(l, t)] = En_c[t]
@@ -377,7 +382,16 @@ def mmp(A: H2, Bm: H2, eps: float, mode: str = Bs.PAPER, cap: int | None = None,
         stats["l_min"] = lmin
         stats["ranks_r"] = {l: [C.kr[(l, t)] for t in range(1 << l)] for l in range(L + 1)}
         stats["ranks_c"] = {l: [C.kc[(l, t)] for t in range(1 << l)] for l in range(L + 1)}
+        stats["margins"] = margins
     return C
+
+
+def _margin(lam, eps, mode) -> float:
+    """Distance of the nearest eigenvalue to the truncation threshold, in units of
+    lambda_1 (how far rounding would have to move the rank decision)."""
+    if mode in (Bs.FULL, Bs.FORMATTED) or len(lam) == 0 or not lam[0] > 0:
+        return float("inf")
+    return float(np.min(np.abs(lam / lam[0] - Bs.threshold(eps, mode))))
 
 
 def _blkdiag(a, b):

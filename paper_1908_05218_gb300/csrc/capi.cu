@@ -156,7 +156,12 @@ h2_opts defaults(const h2_opts* o) {
     d = *o;
     if (d.rank_cap <= 0) d.rank_cap = 48;
   }
-  if (d.precision != H2_FP64 && d.precision != H2_MIXED_FP32) throw h2::Error(H2_EINVAL, "bad precision");
+  if (d.precision < H2_FP64 || d.precision > H2_MIXED_BF16X3) throw h2::Error(H2_EINVAL, "bad precision");
+  if (d.precision == H2_MIXED_TF32X3 || d.precision == H2_MIXED_BF16X3)
+    throw h2::Error(H2_EUNSUPPORTED, "tensor-core split precisions are not built yet");
+  if (d.norm != H2_NORM_FROBENIUS && d.norm != H2_NORM_SPECTRAL) throw h2::Error(H2_EINVAL, "bad norm");
+  if (d.autotune != 0 && d.autotune != 1) throw h2::Error(H2_EINVAL, "autotune must be 0 or 1");
+  if (d.reserved != 0) throw h2::Error(H2_EINVAL, "h2_opts.reserved must be 0");
   if (d.trunc < 0 || d.trunc > 3) throw h2::Error(H2_EINVAL, "bad truncation mode");
   if (d.rank_cap > 128) throw h2::Error(H2_EINVAL, "rank_cap above 128");
   return d;
@@ -537,14 +542,14 @@ void upload_plan(Plan& P, size_t region_esize, bool own_regions) {
       if (nn > 112) scratch = std::max<int64_t>(scratch, L.count * 2LL * nn * (nn + 1));
     }
   }
-  P.d_scratch = (double*)dmalloc(std::max<int64_t>(1, scratch) * sizeof(double));
+  P.scratch_elems = scratch;
   P.region_esize = (int)region_esize;
   if (own_regions)
     for (int a = AR_P; a <= AR_S; ++a) P.d_region[a] = (double*)dmalloc(std::max<int64_t>(1, P.region[a]) * region_esize);
 }
 
 void free_plan(Plan& P) {
-  for (void* q : {(void*)P.d_segs, (void*)P.d_items, (void*)P.d_eigs, (void*)P.d_scratch})
+  for (void* q : {(void*)P.d_segs, (void*)P.d_items, (void*)P.d_eigs})
     if (q) cudaFree(q);
   for (int a = 0; a < kArenas; ++a) {
     if (P.d_region[a]) cudaFree(P.d_region[a]);
@@ -553,7 +558,6 @@ void free_plan(Plan& P) {
   P.d_segs = nullptr;
   P.d_items = nullptr;
   P.d_eigs = nullptr;
-  P.d_scratch = nullptr;
 }
 
 void run_plan(const Plan& P, const ArenaSet& ar, const Arenas* d_ars, const MmpParams& prm, void* stream,
@@ -578,13 +582,13 @@ void run_plan(const Plan& P, const ArenaSet& ar, const Arenas* d_ars, const MmpP
       // formatted product: C's ranks are A's row ranks and B's column ranks
       launch_copy_ranks(d_ars, 0, L.elems, stream);
     } else if (L.kind == Launch::GEMM) {
-      launch_gemm(P.d_segs, P.d_items, L.first, L.count, d_ars, L.aux, L.aux2, prm.precision == H2_MIXED_FP32,
+      launch_gemm(P.d_segs, P.d_items, L.first, L.count, d_ars, L.aux, L.aux2, is_mixed(prm.precision),
                   stream);
     } else {
-      if (prm.precision == H2_MIXED_FP32 && L.aux <= 96)
+      if (is_mixed(prm.precision) && L.aux <= 96 && prm.norm == H2_NORM_FROBENIUS)
         launch_eig_mixed(P.d_eigs, L.first, L.count, d_ars, prm.eps, prm.trunc, L.aux, stream);
       else
-        launch_eig(P.d_eigs, L.first, L.count, d_ars, prm.eps, prm.trunc, L.aux, P.d_scratch, stream);
+        launch_eig(P.d_eigs, L.first, L.count, d_ars, prm.eps, prm.trunc, prm.norm, L.aux, ar.eig_scratch, stream);
     }
     cuda_check(cudaGetLastError(), L.phase);
     if (tr) cuda_check(cudaEventRecord((cudaEvent_t)tr->ev[2 * li + 1], (cudaStream_t)stream), "event");
@@ -715,7 +719,7 @@ h2_status h2_plan_selfcheck(const double* points, int64_t n, int32_t leaf_size, 
             build_mmp_plan(m, m, C, prm, P);
             const int64_t csz = mat_elems(C);
             int64_t sizes[kArenas] = {asz, asz, csz, P.region[AR_P], P.region[AR_G0], P.region[AR_G1], P.region[AR_S],
-                                      prec == H2_MIXED_FP32 ? C.off_S[0] : 0};
+                                      is_mixed(prec) ? C.off_S[0] : 0};
             validate_plan(P, sizes);
           } catch (Error& e) {
             throw Error(e.code, "product plan (trunc " + std::to_string(trunc) + ", precision " +
@@ -795,7 +799,7 @@ std::map<void*, Workspace> g_ws;
 size_t region_bytes(const Plan& P) {
   size_t b = 0;
   for (int a = AR_P; a <= AR_S; ++a) b += ((size_t)std::max<int64_t>(1, P.region[a]) * P.region_esize + 255) & ~size_t(255);
-  return b;
+  return b + (((size_t)P.scratch_elems * sizeof(double) + 255) & ~size_t(255));
 }
 
 Workspace workspace(void* stream, size_t bytes) {
@@ -822,6 +826,7 @@ void place_regions(const Plan& P, ArenaSet& ar, char* base) {
     ar.p[a] = base + off;
     off += ((size_t)std::max<int64_t>(1, P.region[a]) * P.region_esize + 255) & ~size_t(255);
   }
+  ar.eig_scratch = P.scratch_elems ? (double*)(base + off) : nullptr;
 }
 
 // One product made ready to run: its plan (built or from the cache), its output
@@ -841,7 +846,7 @@ Prepared prepare_product(h2_handle A, h2_handle B, double eps, const h2_opts& o,
     if (o.trunc != H2_TRUNC_FULL && o.trunc != H2_TRUNC_FORMATTED && !(eps > 0 && eps < 1))
     throw Error(H2_EINVAL, "eps must lie in (0, 1)");
   if (!same_structure(*A->m.st, *B->m.st)) throw Error(H2_ESTRUCT, "A and B have different trees or partitions");
-  MmpParams prm{eps, o.trunc, o.rank_cap, o.precision};
+  MmpParams prm{eps, o.trunc, o.rank_cap, o.precision, o.norm, o.autotune};
   // plan cache, process-wide
   PlanKey key{A->m.st.get(), A->m.Kr, A->m.Kc, B->m.Kr, B->m.Kc, o.trunc, o.rank_cap, o.precision};
   std::shared_ptr<PlanEntry> ent;
@@ -872,10 +877,10 @@ Prepared prepare_product(h2_handle A, h2_handle B, double eps, const h2_opts& o,
       int64_t csize = mat_elems(probe);
       int64_t sizes[kArenas] = {A->m.arena_elems, B->m.arena_elems, csize, ent->plan.region[AR_P],
                                 ent->plan.region[AR_G0], ent->plan.region[AR_G1], ent->plan.region[AR_S],
-                                o.precision == H2_MIXED_FP32 ? probe.off_S[0] : 0};
+                                is_mixed(o.precision) ? probe.off_S[0] : 0};
       validate_plan(ent->plan, sizes);
     }
-    upload_plan(ent->plan, o.precision == H2_MIXED_FP32 ? sizeof(float) : sizeof(double), false);
+    upload_plan(ent->plan, is_mixed(o.precision) ? sizeof(float) : sizeof(double), false);
     std::lock_guard<std::mutex> lk(g_cache_mu);
     g_plans.push_back({key, ent});
   }
@@ -910,7 +915,7 @@ Prepared prepare_product(h2_handle A, h2_handle B, double eps, const h2_opts& o,
   cuda_check(cudaMemsetAsync(out->m.arena, 0, out->m.arena_elems * sizeof(double), s), "zero C");
   cuda_check(cudaMemsetAsync(out->m.d_kr, 0, 2 * A->m.st->nnodes() * sizeof(int32_t) + 64, s), "zero ranks");
   ArenaSet ar;
-  const bool mixed = o.precision == H2_MIXED_FP32;
+  const bool mixed = is_mixed(o.precision);
   if (mixed) {
     for (h2_matrix* h : {A, B}) {
       if (!h->m.arena32) {
@@ -994,7 +999,7 @@ struct BatchEntry {
   char* ws_base = nullptr;  // the work space the graph was captured with
   uint64_t ws_gen = 0;
   double eps = 0;
-  int trunc = 0, precision = 0;
+  int trunc = 0, precision = 0, norm = 0;
   Arenas* d_ars = nullptr;  // one table per product
   long long kernels = 0;    // kernels of one run of the graph
   cudaGraphExec_t graph = nullptr;
@@ -1012,6 +1017,7 @@ std::shared_ptr<BatchEntry> capture_batch(const std::vector<Prepared*>& grp) {
   be->eps = grp[0]->prm.eps;
   be->trunc = grp[0]->prm.trunc;
   be->precision = grp[0]->prm.precision;
+  be->norm = grp[0]->prm.norm;
   for (Prepared* p : grp) be->plans.push_back(p->ent);
   be->d_ars = (Arenas*)dmalloc(grp.size() * sizeof(Arenas));
   init_kernel_attributes();
@@ -1067,7 +1073,7 @@ void run_group(std::vector<Prepared*>& grp, const Workspace& ws, void* stream) {
     std::lock_guard<std::mutex> lk(g_batch_mu);
     for (auto& e : g_batches) {
       if (e->plans.size() != grp.size() || e->eps != grp[0]->prm.eps || e->trunc != grp[0]->prm.trunc ||
-          e->precision != grp[0]->prm.precision || e->ws_base != ws.base || e->ws_gen != ws.gen)
+          e->precision != grp[0]->prm.precision || e->norm != grp[0]->prm.norm || e->ws_base != ws.base || e->ws_gen != ws.gen)
         continue;
       bool same = true;
       for (size_t i = 0; i < grp.size() && same; ++i) same = e->plans[i] == grp[i]->ent;

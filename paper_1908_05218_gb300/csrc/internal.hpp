@@ -177,7 +177,8 @@ struct Plan {
   // per-stream work space at run time (see region_bytes)
   double* d_region[kArenas] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int region_esize = 8;  // bytes per element of the work regions (4 for a mixed product)
-  double* d_scratch = nullptr;  // eigen work space for Gram matrices above 112
+  int64_t scratch_elems = 0;    // float64 eigen work space for Gram matrices above 112 (taken
+                                // with the work regions, so that concurrent products never share it)
   int64_t flops = 0;     // counted 2mnk over GEMM segments (padded dims)
   std::vector<int> ckr, ckc;  // caps of the product
   // allocations and resets of the work regions in program order (launch = index of
@@ -196,7 +197,11 @@ struct MmpParams {
   int trunc;
   int rank_cap;
   int precision;
+  int norm = H2_NORM_FROBENIUS;
+  int autotune = 0;
 };
+// float32 operands and work regions (every precision but H2_FP64)
+inline bool is_mixed(int precision) { return precision != H2_FP64; }
 
 // Builds the plan of C = A B; sets C's caps (C must share A's structure).
 void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& p, Plan& plan);
@@ -222,6 +227,7 @@ struct ArenaSet {
   int32_t* kr = nullptr;                // the output's rank arrays (written by the eigen step)
   int32_t* kc = nullptr;
   unsigned long long* cap_hits = nullptr;
+  double* eig_scratch = nullptr;        // this product's eigen work space (Plan::scratch_elems)
   size_t esize(int a) const { return ((f32 >> a) & 1) ? 4 : 8; }
 };
 // The same table as the kernels read it, in device memory: one per product instance of
@@ -245,7 +251,7 @@ void run_plan(const Plan& plan, const ArenaSet& ar, const Arenas* d_ars, const M
 void launch_gemm(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const Arenas* d_ars,
                  int maxn, int maxdim, bool fp32, void* stream);
 void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, const Arenas* d_ars, double eps, int trunc,
-                int max_npad, double* scratch, void* stream);
+                int norm, int max_npad, double* scratch, void* stream);
 // formatted product: C's ranks are A's row ranks and B's column ranks (instance inst)
 void launch_copy_ranks(const Arenas* d_ars, int inst, int64_t n, void* stream);
 unsigned long long kernel_launches();  // kernels launched by this library so far

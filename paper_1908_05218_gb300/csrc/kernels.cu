@@ -597,9 +597,22 @@ template <typename T>
 __device__ void jacobi_sweeps(T* A, T* V, int nn, int lds, int max_sweeps, double tol, double* red, T* cs, T* sn,
                               int* pp, int* qq);
 
+__device__ double block_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double t = red[0];
+  for (int i = 1; i < (int)(blockDim.x >> 5); ++i) t = fmax(t, red[i]);
+  return t;
+}
+
+// norm: H2_NORM_FROBENIUS scales each Gram matrix by 1 / ||G_m||_F, H2_NORM_SPECTRAL by
+// 1 / lambda_max(G_m), the largest eigenvalue from a Jacobi decomposition of G_m alone
 __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ tasks, int64_t first,
                                                   const Arenas* __restrict__ ars, double eps, int trunc,
-                                                  double* scratch, int64_t scratch_stride) {
+                                                  int norm, double* scratch, int64_t scratch_stride) {
   extern __shared__ double smem[];
   __shared__ int act[256];
   __shared__ double red[8];
@@ -637,6 +650,37 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
     A = scratch + blockIdx.x * scratch_stride;
     V = A + sz;
   }
+  // spectral norms of the Gram matrices (H2_NORM_SPECTRAL): each one decomposed alone
+  __shared__ double s_lmax[3];
+  if (norm == H2_NORM_SPECTRAL) {
+    for (int m = 0; m < 3; ++m) {
+      if (t.g[m] < 0) continue;
+      const View G = view(ar, t.g[m]);
+      for (int e = tid; e < sz; e += nt) {
+        A[e] = 0.0;
+        V[e] = (e / lds == e % lds) ? 1.0 : 0.0;
+      }
+      __syncthreads();
+      for (int e = tid; e < n * n; e += nt)
+        A[(e / n) * lds + (e % n)] = ld<double>(G, (int64_t)act[e / n] * t.n_pad + act[e % n]);
+      __syncthreads();
+      for (int e = tid; e < nn * nn; e += nt) {
+        const int a = e / nn, b = e % nn;
+        if (a < b) {
+          const double v = 0.5 * (A[a * lds + b] + A[b * lds + a]);
+          A[a * lds + b] = v;
+          A[b * lds + a] = v;
+        }
+      }
+      __syncthreads();
+      jacobi_sweeps<double>(A, V, nn, lds, 30, 1e-30, red, cs, sn, pp, qq);
+      double mx = 0.0;
+      for (int a = tid; a < n; a += nt) mx = fmax(mx, A[a * lds + a]);
+      mx = block_max(mx, red);
+      if (tid == 0) s_lmax[m] = mx;
+      __syncthreads();
+    }
+  }
   // normalised sum of the Gram matrices over the active rows/cols
   for (int e = tid; e < sz; e += nt) A[e] = 0.0;
   __syncthreads();
@@ -649,8 +693,8 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
       loc += v * v;
     }
     double nrm2 = block_sum(loc, red);
-    if (nrm2 > 0.0) {
-      double inv = 1.0 / sqrt(nrm2);
+    if (nrm2 > 0.0 && (norm != H2_NORM_SPECTRAL || s_lmax[m] > 0.0)) {
+      double inv = norm == H2_NORM_SPECTRAL ? 1.0 / s_lmax[m] : 1.0 / sqrt(nrm2);
       for (int e = tid; e < n * n; e += nt)
         A[(e / n) * lds + (e % n)] += ld<double>(G, (int64_t)act[e / n] * t.n_pad + act[e % n]) * inv;
     }
@@ -1376,12 +1420,10 @@ void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const
     // ranks) are only known on the device and are mostly far smaller, so tasks are
     // launched in size tiers, each with the shared memory of its largest size (more
     // CTAs per SM for the small ones)
-    // (tiers run one after the other: a level of few tasks takes one launch)
+    // (tiers run one after the other)
     const int top = round4(max_npad);
     int lo = -1;
-    const bool tiers = count >= 4 * 152;
     for (int hi : {48, 64, kMixMax}) {
-      if (!tiers) hi = top;
       const int h = hi < top ? hi : top;
       // (128 threads are enough for nn <= 48: a step has <= 300 block and row tasks)
       if (h > lo) {
@@ -1396,7 +1438,7 @@ void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const
 }
 
 void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, const Arenas* ar, double eps, int trunc,
-                int max_npad, double* scratch, void* stream) {
+                int norm, int max_npad, double* scratch, void* stream) {
   int nn = max_npad + (max_npad & 1);
   size_t smem = 0;
   int64_t stride = 0;
@@ -1407,7 +1449,8 @@ void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, const Arena
     stride = (int64_t)2 * nn * (nn + 1);
   }
   init_kernel_attributes();
-  eig_kernel<<<(unsigned)count, 256, smem, (cudaStream_t)stream>>>(d_eigs, first, ar, eps, trunc, scratch, stride);
+  eig_kernel<<<(unsigned)count, 256, smem, (cudaStream_t)stream>>>(d_eigs, first, ar, eps, trunc, norm, scratch,
+                                                                  stride);
   g_launches += 1;
 }
 

@@ -227,7 +227,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
   auto tC = [&](int64_t o) { return tag(AR_C, o); };
   // reads of C's new bases: in the mixed product the eigen step also writes a float
   // copy of them (arena X), so that every GEMM operand has the product's type
-  const Arena basis_src = prm.precision == H2_MIXED_FP32 ? AR_X : AR_C;
+  const Arena basis_src = is_mixed(prm.precision) ? AR_X : AR_C;
   auto tCb = [&](int64_t o) { return tag(basis_src, o); };
   auto G = [](int l) { return (l & 1) ? AR_G1 : AR_G0; };
   // rank references of cluster t of level l (loop bounds read on the device)

@@ -17,7 +17,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libh2gb300.so")
 
 H2_OK, H2_EINVAL, H2_ENOMEM, H2_ECUDA, H2_ESTRUCT, H2_ETIMEOUT, H2_EINTERNAL, H2_EUNSUPPORTED = range(8)
-FP64, MIXED_FP32 = 0, 1
+FP64, MIXED_FP32, MIXED_TF32X3, MIXED_BF16X3 = 0, 1, 2, 3
+NORM_FROBENIUS, NORM_SPECTRAL = 0, 1
+_NORM = {"fro": NORM_FROBENIUS, "spectral": NORM_SPECTRAL}
 TRUNC_PAPER, TRUNC_SV, TRUNC_FULL, TRUNC_FORMATTED = 0, 1, 2, 3
 _TRUNC = {"paper": TRUNC_PAPER, "sv": TRUNC_SV, "full": TRUNC_FULL, "formatted": TRUNC_FORMATTED}
 
@@ -38,8 +40,8 @@ class Kernel(C.Structure):
 
 
 class Opts(C.Structure):
-    _fields_ = [("precision", C.c_int32), ("trunc", C.c_int32), ("rank_cap", C.c_int32), ("reserved", C.c_int32),
-                ("stream", C.c_void_p)]
+    _fields_ = [("precision", C.c_int32), ("trunc", C.c_int32), ("rank_cap", C.c_int32), ("norm", C.c_int32),
+                ("stream", C.c_void_p), ("autotune", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -100,15 +102,17 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(C.c_void_p) if a is not None and a.size else None
 
 
-def make_opts(precision: int = FP64, trunc: str | int = "paper", rank_cap: int = 0, stream=None) -> Opts:
+def make_opts(precision: int = FP64, trunc: str | int = "paper", rank_cap: int = 0, stream=None,
+              norm: str | int = "fro", autotune: bool = False) -> Opts:
     t = _TRUNC[trunc] if isinstance(trunc, str) else int(trunc)
+    nm = _NORM[norm] if isinstance(norm, str) else int(norm)
     if stream is None:
         try:
             import torch
             stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
         except Exception:  # pragma: no cover - torch without CUDA
             stream = None
-    return Opts(precision, t, rank_cap, 0, stream)
+    return Opts(precision, t, rank_cap, nm, stream, int(autotune), 0)
 
 
 def make_kernel(spec) -> Kernel:
@@ -143,9 +147,9 @@ class H2Matrix:
             self.handle = C.c_void_p(0)
 
     def mmp(self, other: "H2Matrix", eps: float, precision: int = FP64, trunc="paper", rank_cap: int = 0,
-            out: "H2Matrix | None" = None, stream=None) -> "H2Matrix":
+            out: "H2Matrix | None" = None, stream=None, norm="fro", autotune: bool = False) -> "H2Matrix":
         """C = self x other (h2_mmp); `out` from an earlier identical call is overwritten in place."""
-        o = make_opts(precision, trunc, rank_cap, stream)
+        o = make_opts(precision, trunc, rank_cap, stream, norm, autotune)
         h = C.c_void_p(out.handle.value if out is not None else 0)
         _check(load().h2_mmp(self.handle, other.handle, float(eps), C.byref(o), C.byref(h)))
         if out is not None and h.value == out.handle.value:
@@ -279,12 +283,12 @@ def kernel_launches() -> int:
 
 
 def h2_mmp_batched(As, Bs, eps: float, precision: int = FP64, trunc="paper", rank_cap: int = 0,
-                   outs=None, stream=None) -> list:
+                   outs=None, stream=None, norm="fro", autotune: bool = False) -> list:
     """[A_i x B_i] through h2_mmp_batched (independent products, in order on one stream)."""
     n = len(As)
     if len(Bs) != n:
         raise ValueError("A and B lists differ in length")
-    o = make_opts(precision, trunc, rank_cap, stream)
+    o = make_opts(precision, trunc, rank_cap, stream, norm, autotune)
     ha = (C.c_void_p * n)(*[a.handle.value for a in As])
     hb = (C.c_void_p * n)(*[b.handle.value for b in Bs])
     hc = (C.c_void_p * n)(*[(outs[i].handle.value if outs else 0) for i in range(n)])

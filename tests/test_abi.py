@@ -61,6 +61,38 @@ def test_argument_errors_without_gpu(lib_path):
 def test_structs_match_the_header():
     from paper_1908_05218_gb300 import h2
     assert ctypes.sizeof(h2.Kernel) == 32
-    assert ctypes.sizeof(h2.Opts) == 24
+    assert ctypes.sizeof(h2.Opts) == 32
     src = open(HEADER).read()
     assert "int32_t max_rank_row[32]" in src
+    # h2_opts field order as declared
+    body = src[:src.index("} h2_opts;")].rsplit("typedef struct {", 1)[1]
+    fields = re.findall(r"^\s*(?:int32_t|void\*)\s+(\w+);", body, re.M)
+    assert fields == [f for f, _ in h2.Opts._fields_]
+    for name, val in (("H2_FP64", 0), ("H2_MIXED_FP32", 1), ("H2_MIXED_TF32X3", 2), ("H2_MIXED_BF16X3", 3),
+                      ("H2_NORM_FROBENIUS", 0), ("H2_NORM_SPECTRAL", 1)):
+        assert re.search(rf"\b{name} = {val}\b", src), name
+
+
+def test_options_are_validated_through_the_abi(lib_path):
+    # h2_build checks its options before any device work, so this runs without a GPU
+    import numpy as np
+
+    from paper_1908_05218_gb300 import h2
+    lib = h2.load()
+    pts = np.random.default_rng(0).random((64, 3))
+    k = h2.Kernel(0, 0.0, 1.0, 0.0)
+    out = ctypes.c_void_p(0)
+
+    def build(**kw):
+        o = h2.make_opts(**kw)
+        return lib.h2_build(pts.ctypes.data_as(ctypes.c_void_p), 64, ctypes.byref(k), 32, 1.0, 1e-4,
+                            ctypes.byref(o), ctypes.byref(out))
+
+    assert build(norm=2) == h2.H2_EINVAL
+    assert build(precision=7) == h2.H2_EINVAL
+    assert build(autotune=2) == h2.H2_EINVAL
+    o = h2.make_opts()
+    o.reserved = 5
+    assert lib.h2_build(pts.ctypes.data_as(ctypes.c_void_p), 64, ctypes.byref(k), 32, 1.0, 1e-4, ctypes.byref(o),
+                        ctypes.byref(out)) == h2.H2_EINVAL
+    assert out.value is None

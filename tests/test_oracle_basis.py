@@ -61,3 +61,14 @@ def test_sign_convention():
     for c in range(3):
         p = np.argmax(np.abs(u[:, c]))
         assert u[p, c] > 0
+
+
+def test_spectral_normalisation_divides_by_the_largest_eigenvalue():
+    # components with known spectra: the spectral-norm reading divides each by its
+    # largest eigenvalue, the default by the root of the sum of squared eigenvalues
+    ga, qa = _spd_with_spectrum([4.0, 1.0, 0.0, 0.0, 0.0], seed=3)
+    gb, qb = _spd_with_spectrum([0.5, 0.5, 0.25, 0.0, 0.0], seed=4)
+    s = Bs.normalized_sum([ga, gb], 5, np.float64, Bs.SPECTRAL)
+    np.testing.assert_allclose(s, ga / 4.0 + gb / 0.5, atol=1e-14)
+    f = Bs.normalized_sum([ga, gb], 5, np.float64)
+    np.testing.assert_allclose(f, ga / np.sqrt(17.0) + gb / np.sqrt(0.5625), atol=1e-14)

@@ -80,11 +80,11 @@ class Dense:
         self.fpairs = [(t, s) for (t, s, k) in self.part.blocks[self.L] if k == F]
         self._comps = {}
 
-    def leaf_components(self, t, col):
+    def leaf_components(self, t, col, norm="fro"):
         """Unit-Frobenius Gram components of leaf t from dense slices (Sec. III-C):
         case-1 products F F landing in an admissible block of C, the near-field blocks
         of A (resp. B) times B's row (A's column) basis, and the cluster's own basis."""
-        key = (t, col)
+        key = (t, col, norm)
         if key in self._comps:
             return self._comps[key]
         L, tr, A, B = self.L, self.tree, self.A, self.B
@@ -109,14 +109,14 @@ class Dense:
             if z:
                 zm = np.hstack(z)
                 g = zm @ zm.T
-                nrm = np.linalg.norm(g)
+                nrm = np.linalg.norm(g) if norm == "fro" else np.linalg.eigvalsh(g)[-1]
                 if nrm > 0:
                     out.append(g / nrm)
         self._comps[key] = out
         return out
 
 
-def leaf_pin_violations(d: Dense, C, eps, mode):
+def leaf_pin_violations(d: Dense, C, eps, mode, norm="fro"):
     """Leaf clusters whose new basis is not the truncated top eigenspace of the
     dense-built G; clusters with an eigenvalue within 1e-9 of the threshold are
     skipped (the rank there is decided by rounding)."""
@@ -124,7 +124,7 @@ def leaf_pin_violations(d: Dense, C, eps, mode):
     bad = []
     for t in range(1 << d.L):
         for col in (False, True):
-            cs = d.leaf_components(t, col)
+            cs = d.leaf_components(t, col, norm)
             G = sum(cs)
             lam = np.sort(np.linalg.eigvalsh(G))[::-1]
             if np.min(np.abs(lam / lam[0] - thr)) < 1e-9:
@@ -186,10 +186,12 @@ def dense_lowrank_pair():
     return Dense(h2.build(wa.points, wa.kernel, 32, 1.0, 1e-2), h2.build(wb.points, wb.kernel, 32, 1.0, 1e-2))
 
 
-@pytest.mark.parametrize("eps,mode", [(1e-4, "paper"), (1e-3, "sv")])
-def test_leaf_bases_are_the_top_eigenspace_of_the_dense_gram_sum(dense_pair, eps, mode):
-    C = mmp.mmp(dense_pair.A, dense_pair.B, eps, mode)
-    assert leaf_pin_violations(dense_pair, C, eps, mode) == []
+@pytest.mark.parametrize("eps,mode,norm", [(1e-4, "paper", "fro"), (1e-3, "sv", "fro"), (1e-4, "paper", "spectral")])
+def test_leaf_bases_are_the_top_eigenspace_of_the_dense_gram_sum(dense_pair, eps, mode, norm):
+    C = mmp.mmp(dense_pair.A, dense_pair.B, eps, mode, norm=norm)
+    assert leaf_pin_violations(dense_pair, C, eps, mode, norm) == []
+    if norm == "spectral":      # the two readings give different bases
+        assert leaf_pin_violations(dense_pair, C, eps, mode, "fro") != []
 
 
 @pytest.mark.parametrize("name", LEAF_MUTANTS)
