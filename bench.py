@@ -7,7 +7,11 @@ algorithmic throughput: (bytes of A + B + C at their actual ranks) / product tim
 in GB/s, with the product time itself reported beside it.
 
   python bench.py [--gpus N --steps K --warmup W] [--workload cubes16x16|cubes4x4|batched48]
-                  [--precision fp64|mixed] [--impl ours|reference]
+                  [--precision fp64|mixed|tf32x3] [--impl ours|reference] [--no-extras]
+
+Beside the headline precision the line carries the same product under the sv rule and
+in float64 (the two arms of the metric), each timed once after a warm-up, and an
+end-to-end run for a caller with a new structure (program built inside the timed run).
 
 --impl reference times the CPU oracle (the plain float64 restatement of the method)
 on a bounded sample of the same geometry: the reference arm.
@@ -108,9 +112,11 @@ class Clocks:
         return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def reference_arm(args, sample="sample"):
-    """The CPU oracle on a bounded sample of the workload (1 core, float64)."""
-    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+def reference_arm(args, sample="sample", threads=1):
+    """The CPU oracle on a bounded sample of the workload (float64; its BLAS limited to
+    `threads` host cores)."""
+    nt = str(threads)
+    env = dict(os.environ, OPENBLAS_NUM_THREADS=nt, OMP_NUM_THREADS=nt, MKL_NUM_THREADS=nt)
     t0 = time.time()
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-sample",
                           "--steps", str(args.steps), "--workload", sample], capture_output=True, text=True,
@@ -165,7 +171,7 @@ def batched_main(args):
     from paper_1908_05218_gb300 import inputs
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     lib.load()
-    prec = lib.FP64 if args.precision == "fp64" else lib.MIXED_FP32
+    prec = PRECISIONS[args.precision](lib)
     ws = inputs.workload_batch(48)
     eps, chunk = 1e-4, 8
     stream = torch.cuda.current_stream()
@@ -226,6 +232,127 @@ def batched_main(args):
         "bytes_alg": nbytes, "clocks": clk.summary()}))
 
 
+PRECISIONS = {"fp64": lambda lib: lib.FP64, "mixed": lambda lib: lib.MIXED_FP32,
+              "tf32x3": lambda lib: lib.MIXED_TF32X3}
+DTYPES = {"fp64": "f64", "mixed": "f32+f64", "tf32x3": "tf32x3+f64"}
+KERNELS = {"fp64": "seg_gemm_kernel<double>", "mixed": "seg_gemm32_kernel", "tf32x3": "seg_mma_tf32x3_kernel"}
+
+
+def trace_summary(C):
+    """Per-kind, per-phase and per-level device times of the traced product of C."""
+    kinds, levels, lms, lfl, lnames = C.trace_read()
+    tot = {}
+    for k, m_, f_ in zip(kinds, lms, lfl):
+        tt = tot.setdefault(k, [0.0, 0.0, 0])
+        tt[0] += m_
+        tt[1] += f_
+        tt[2] += 1
+    by_phase, by_level, eig_by_level = {}, {}, {}
+    for nm, m_ in zip(lnames, lms):
+        by_phase[nm] = round(by_phase.get(nm, 0.0) + m_, 3)
+    for lv, m_, kd in zip(levels, lms, kinds):
+        by_level[int(lv)] = round(by_level.get(int(lv), 0.0) + m_, 3)
+        if kd == "eig":
+            eig_by_level[int(lv)] = round(eig_by_level.get(int(lv), 0.0) + m_, 3)
+    return {"tot": tot, "phase_ms": {k: round(v[0], 3) for k, v in tot.items()}, "by_phase": by_phase,
+            "by_level": dict(sorted(by_level.items())), "eig_by_level": dict(sorted(eig_by_level.items())),
+            "executed_flops": C.trace_flops()}
+
+
+def roofline(tr, precision):
+    """Roofline entry of the GEMM kernel: multiply-add flops executed at the actual ranks
+    (device counter) / the CUDA-event time of its launches, against the peak of the unit
+    it runs on (float32 / float64 FMA lanes x 2 x max SM clock; for the 3xTF32 tensor-core
+    kernel a third of the TF32 rate, half the measured dense BF16 rate)."""
+    tot = tr["tot"]
+    peaks, src = _peaks()
+    clk_hz = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    if precision == "tf32x3":
+        peak = 0.5 * float(peaks["bf16_tflops"]) / 3.0
+        bound, peak_note = "tensor", f"TF32 = half the dense BF16 peak ({src}), / 3 products per split pair"
+    elif precision == "fp64":
+        peak = 152 * 2 * 2 * clk_hz / 1e12
+        bound, peak_note = "alu", "152 SMs x 2 float64 FMA per clock x 2 flops x max SM clock"
+    else:
+        peak = 152 * 128 * 2 * clk_hz / 1e12
+        bound, peak_note = "alu", "152 SMs x 128 float32 FMA lanes x 2 flops x max SM clock"
+    gemm_ms = tot.get("gemm", [0.0])[0]
+    fl = tr["executed_flops"]
+    achieved = fl / (gemm_ms * 1e-3) / 1e12 if gemm_ms else 0.0
+    dom = max(tot, key=lambda k: tot[k][0])
+    traffic = None
+    if precision == "mixed" and tot.get("gemm", [0, 0, 0])[2]:
+        import hashlib
+        with open(os.path.join(ROOT, "paper_1908_05218_gb300", "csrc", "kernels.cu"), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() == TRAFFIC["src_sha256"]:
+                traffic = (TRAFFIC["bytes_per_product"] * fl / TRAFFIC["executed_flops_per_product"]
+                           / tot["gemm"][2])
+    return {"bound": bound, "kernel": KERNELS[precision], "dominant": dom, "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": traffic,
+            "traffic_note": ("DRAM bytes per GEMM launch: ncu capture at N=65,536 scaled by executed flops"
+                             if traffic else "no DRAM capture of this kernel source at this precision"),
+            "peak_note": peak_note, "launches_per_step": tot.get("gemm", [0, 0, 0])[2], "ms_per_step": gemm_ms,
+            "executed_flops_per_step": fl,
+            "note": "GEMM kernel: multiply-add flops executed at the actual ranks (device counter) / its "
+                    "CUDA-event time"}
+
+
+def side_arm(lib, A, B, eps, prec, trunc, x, y_ref, with_roofline=None):
+    """One more configuration of the same product: its first call (program built), one
+    warm-up and one traced timed call; time, GB/s and Eq. error."""
+    import torch
+    try:
+        t0 = time.time()
+        C = A.mmp(B, eps, precision=prec, trunc=trunc)
+        torch.cuda.synchronize()
+        first = time.time() - t0
+        C = A.mmp(B, eps, precision=prec, trunc=trunc, out=C)
+        A.trace_enable(True)
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        C = A.mmp(B, eps, precision=prec, trunc=trunc, out=C)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        tr = trace_summary(C)
+        A.trace_enable(False)
+        nbytes = A.info()["bytes_stored"] + B.info()["bytes_stored"] + C.info()["bytes_stored"]
+        err = float(torch.linalg.norm(C.matvec(x) - y_ref) / torch.linalg.norm(y_ref))
+        out = {"trunc": trunc, "precision": {0: "fp64", 1: "mixed", 2: "tf32x3"}.get(prec, prec), "ms": ms,
+               "value": nbytes / (ms * 1e-3) / 1e9, "unit": "GB/s", "rel_err_vs_exact_h2_matvecs": err,
+               "first_product_s_incl_plan": first, "warmup": 1, "steps": 1, "phase_ms": tr["phase_ms"],
+               "max_rank_row": C.info()["max_rank_row"]}
+        if with_roofline:
+            out["roofline"] = roofline(tr, with_roofline)
+        C.destroy()
+        return out
+    except Exception as e:  # reported, not fatal
+        return {"error": str(e)[-300:]}
+
+
+def end_to_end(lib, wa, wb, pa, pbk, eps, prec, trunc, nbytes):
+    """Through the public API with host buffers: h2_import of A and B from host arrays,
+    h2_mmp, h2_export of C; bytes counted from the arrays."""
+    import torch
+    h2d = sum(a.nbytes for a in (pa.kr, pa.kc, pa.vr, pa.vc, pa.er, pa.ec, pa.s, pa.f))
+    h2d += sum(a.nbytes for a in (pbk.kr, pbk.kc, pbk.vr, pbk.vc, pbk.er, pbk.ec, pbk.s, pbk.f))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    A2 = lib.h2_import(wa.points, LEAF, ETA, pa)
+    B2 = lib.h2_import(wb.points, LEAF, ETA, pbk)
+    C2 = A2.mmp(B2, eps, precision=prec, trunc=trunc)
+    pc = C2.export()
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    d2h = sum(a.nbytes for a in (pc.kr, pc.kc, pc.vr, pc.vc, pc.er, pc.ec, pc.s, pc.f))
+    for h in (C2, B2, A2):
+        h.destroy()
+    return {"value": nbytes / te / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "seconds": te, "steps": 1}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -233,12 +360,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cubes16x16", choices=list(WORKLOADS) + ["batched48"])
-    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=list(PRECISIONS))
     ap.add_argument("--trunc", default="paper", choices=["paper", "sv", "formatted"],
                     help="truncation rule; 'formatted' = fixed bases (the paper's comparison method)")
     ap.add_argument("--oracle-sample", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the sv-rule, float64 and new-structure end-to-end runs")
     args = ap.parse_args()
 
     if args.oracle_sample:
@@ -279,6 +408,11 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             cpu = reference_arm(argparse.Namespace(steps=1))
+            ncores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+            if ncores > 1 and not args.no_extras:
+                ac = reference_arm(argparse.Namespace(steps=1), threads=ncores)
+                ac["cores"] = ncores
+                cpu["all_cores"] = ac
         except Exception as e:  # reported, not fatal
             cpu = {"error": str(e)[-300:]}
 
@@ -295,7 +429,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     lib.load()
-    prec = lib.FP64 if args.precision == "fp64" else lib.MIXED_FP32
+    prec = PRECISIONS[args.precision](lib)
 
     wa = inputs.workload_cube_array(nx, ny, ppc)
     wb = inputs.workload_cube_array(nx, ny, ppc, kernel="invr2")
@@ -304,6 +438,8 @@ def main():
     B = lib.h2_build(wb.points, wb.kernel, LEAF, ETA, EPS_H2)
     build_s = time.time() - t0
     stream = torch.cuda.current_stream()
+    x = torch.from_numpy(inputs.standard_normal((wa.points.shape[0], 4), seed=1)).cuda()
+    y_ref = A.matvec(B.matvec(x))          # Eq. error: exact H^2 matvecs
 
     C = None
     t0 = time.time()
@@ -331,84 +467,39 @@ def main():
         dist.barrier()
     ms = ev0.elapsed_time(ev1) / max(1, args.steps)
     ms = replicas.slowest(ms, dist, device="cuda")
-    kinds, levels, lms, lfl, lnames = C.trace_read()
-    executed_flops = C.trace_flops()
+    tr = trace_summary(C)
     A.trace_enable(False)
 
     ia, ib, ic = A.info(), B.info(), C.info()
     nbytes = ia["bytes_stored"] + ib["bytes_stored"] + ic["bytes_stored"]
     value = replicas.throughput(nbytes, world, ms)
-
-    # accuracy of this product: Eq. error with exact H^2 matvecs, 4 random vectors
-    x = torch.from_numpy(inputs.standard_normal((wa.points.shape[0], 4), seed=1)).cuda()
-    y_ref = A.matvec(B.matvec(x))
     rel_err = float(torch.linalg.norm(C.matvec(x) - y_ref) / torch.linalg.norm(y_ref))
+    roof = roofline(tr, args.precision)
+    ranks_C = ic["max_rank_row"]
+    cap_hits = ic["cap_hits"]
+    C.destroy()
 
-    # roofline: the dominant kernel of the traced step
-    tot = {}
-    for k, m_, f_ in zip(kinds, lms, lfl):
-        tt = tot.setdefault(k, [0.0, 0.0, 0])
-        tt[0] += m_
-        tt[1] += f_
-        tt[2] += 1
-    dom = max(tot, key=lambda k: tot[k][0])
-    peaks, src = _peaks()
-    # ALU peaks from unit counts and the maximum SM clock: 152 SMs x 128 float32 FMA
-    # lanes (resp. 2 float64 FMA per clock) x 2 flops x clock
-    clk_hz = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    fp32_peak = 152 * 128 * 2 * clk_hz / 1e12
-    fp64_peak = 152 * 2 * 2 * clk_hz / 1e12
-    peak = fp64_peak if args.precision == "fp64" else fp32_peak
-    gemm_ms = tot.get("gemm", [0.0])[0]
-    gemm_tf = executed_flops / (gemm_ms * 1e-3) / 1e12 if gemm_ms else 0.0
-    traffic = None
-    if args.precision != "fp64" and dom == "gemm" and tot["gemm"][2]:
-        import hashlib
-        with open(os.path.join(ROOT, "paper_1908_05218_gb300", "csrc", "kernels.cu"), "rb") as f:
-            if hashlib.sha256(f.read()).hexdigest() == TRAFFIC["src_sha256"]:
-                traffic = (TRAFFIC["bytes_per_product"] * executed_flops / TRAFFIC["executed_flops_per_product"]
-                           / tot["gemm"][2])
-    gemm_name = "seg_gemm_kernel<double>" if args.precision == "fp64" else "seg_gemm32_kernel"
-    eig_name = "eig_kernel" if args.precision == "fp64" else "eig_mixed_kept_kernel"
-    roof = {"bound": "alu", "kernel": gemm_name if dom == "gemm" else eig_name, "dominant": dom,
-            "achieved": gemm_tf, "peak": peak, "unit": "TFLOP/s", "frac": gemm_tf / peak, "traffic": traffic,
-            "traffic_note": ("DRAM bytes per GEMM launch: ncu capture at N=65,536 scaled by executed flops"
-                             if traffic else "kernel changed since the capture (or float64 run)"),
-            "launches_per_step": tot["gemm"][2], "ms_per_step": gemm_ms,
-            "executed_flops_per_step": executed_flops,
-            "note": ("GEMM kernel: multiply-add flops executed at the actual ranks (device counter) / its "
-                     "CUDA-event time; peak = float32 (float64) FMA units x 2 x max SM clock")}
-    phase_ms = {k: round(v[0], 3) for k, v in tot.items()}
-    by_phase = {}
-    for nm, m_ in zip(lnames, lms):
-        by_phase[nm] = by_phase.get(nm, 0.0) + m_
-    by_level = {}
-    eig_by_level = {}
-    for lv, m_, kd in zip(levels, lms, kinds):
-        by_level[int(lv)] = by_level.get(int(lv), 0.0) + m_
-        if kd == "eig":
-            eig_by_level[int(lv)] = eig_by_level.get(int(lv), 0.0) + m_
-
+    extras = {}
     # end to end through the public API with host buffers: upload A and B from host
-    # arrays, the product, download C
+    # arrays, the product, download C (structure and program cached from the runs above)
     e2e = None
     if not args.no_e2e and rank == 0:
         pa, pbk = A.export(), B.export()
-        h2d = sum(a.nbytes for a in (pa.kr, pa.kc, pa.vr, pa.vc, pa.er, pa.ec, pa.s, pa.f))
-        h2d += sum(a.nbytes for a in (pbk.kr, pbk.kc, pbk.vr, pbk.vc, pbk.er, pbk.ec, pbk.s, pbk.f))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        A2 = lib.h2_import(wa.points, LEAF, ETA, pa)
-        B2 = lib.h2_import(wb.points, LEAF, ETA, pbk)
-        C2 = A2.mmp(B2, eps, precision=prec, trunc=args.trunc)
-        pc = C2.export()
-        torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        d2h = sum(a.nbytes for a in (pc.kr, pc.kc, pc.vr, pc.vc, pc.er, pc.ec, pc.s, pc.f))
-        e2e = {"value": nbytes / te / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "seconds": te, "steps": 1}
-        for h in (C2, B2, A2):
-            h.destroy()
+        e2e = end_to_end(lib, wa, wb, pa, pbk, eps, prec, args.trunc, nbytes)
+    if rank == 0 and not args.no_extras:
+        # the same product with the sv rule (thresholds eps^2: error ~ eps)
+        extras["sv_rule"] = side_arm(lib, A, B, eps, prec, "sv", x, y_ref)
+        # the float64 arm of the metric: the same product, every step in float64
+        if args.precision != "fp64":
+            extras["fp64"] = side_arm(lib, A, B, eps, lib.FP64, args.trunc, x, y_ref, with_roofline="fp64")
+    # end to end for a caller with a new structure: every handle is released first, so
+    # that the tree, the partition and the product program are built inside the timed run
+    e2e_cold = None
+    if not args.no_e2e and rank == 0 and not args.no_extras:
+        pa, pbk = A.export(), B.export()
+        A.destroy()
+        B.destroy()
+        e2e_cold = end_to_end(lib, wa, wb, pa, pbk, eps, prec, args.trunc, nbytes)
 
     if rank == 0:
         cpu_line = None
@@ -416,25 +507,31 @@ def main():
             cpu_line = {"value": cpu["bytes"] / cpu["t"] / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
                         "sample": f"cube array 2x2, 3072 points per cube (N={cpu['n']}), one product, eps {eps}",
                         "seconds": cpu["t"]}
+            if cpu.get("all_cores"):
+                ac = cpu["all_cores"]
+                cpu_line["all_cores"] = {"value": ac["bytes"] / ac["t"] / 1e9, "unit": "GB/s",
+                                         "cores": ac["cores"], "seconds": ac["t"],
+                                         "note": "the same oracle with every host core open to its BLAS"}
         elif cpu:
             cpu_line = {"error": cpu.get("error")}
         line = {
             "metric": metric, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
-            "data": "synthetic",
+            "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic",
             "config": {"workload": f"{desc}; leaf {LEAF}, eta {ETA}, eps_trunc {eps} ({args.trunc} rule), "
                                    f"eps_H2 {EPS_H2}; A: 1/(4 pi r), B: 1/r^2",
+                       "precision": args.precision,
                        "inputs": "A, B, C together exceed L2 (no flush needed)", "parallelism": "replicas"},
             "mmp_s": ms * 1e-3, "rel_err_vs_exact_h2_matvecs": rel_err,
-            "ranks_C_max_row": ic["max_rank_row"], "cap_hits": ic["cap_hits"],
+            "ranks_C_max_row": ranks_C, "cap_hits": cap_hits,
             "bytes_alg": nbytes, "build_s": build_s, "first_product_s_incl_plan": setup_s,
-            "phase_ms": phase_ms, "phase_ms_by_name": {k: round(v, 3) for k, v in by_phase.items()},
-            "ms_by_level": {k: round(v, 3) for k, v in sorted(by_level.items())},
-            "eig_ms_by_level": {k: round(v, 3) for k, v in sorted(eig_by_level.items())}, "roofline": roof, "cpu_baseline": cpu_line, "e2e": e2e,
-            "gpu_launches": int(n_launch),
-            "clocks": clk.summary(),
+            "plan_s": max(0.0, setup_s - ms * 1e-3),
+            "phase_ms": tr["phase_ms"], "phase_ms_by_name": tr["by_phase"],
+            "ms_by_level": tr["by_level"], "eig_ms_by_level": tr["eig_by_level"],
+            "roofline": roof, "cpu_baseline": cpu_line, "e2e": e2e, "e2e_new_structure": e2e_cold,
+            "gpu_launches": int(n_launch), "clocks": clk.summary(),
         }
+        line.update(extras)
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

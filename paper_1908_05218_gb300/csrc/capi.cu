@@ -157,8 +157,7 @@ h2_opts defaults(const h2_opts* o) {
     if (d.rank_cap <= 0) d.rank_cap = 48;
   }
   if (d.precision < H2_FP64 || d.precision > H2_MIXED_BF16X3) throw h2::Error(H2_EINVAL, "bad precision");
-  if (d.precision == H2_MIXED_TF32X3 || d.precision == H2_MIXED_BF16X3)
-    throw h2::Error(H2_EUNSUPPORTED, "tensor-core split precisions are not built yet");
+  if (d.precision == H2_MIXED_BF16X3) throw h2::Error(H2_EUNSUPPORTED, "BF16 split products are not built yet");
   if (d.norm != H2_NORM_FROBENIUS && d.norm != H2_NORM_SPECTRAL) throw h2::Error(H2_EINVAL, "bad norm");
   if (d.autotune != 0 && d.autotune != 1) throw h2::Error(H2_EINVAL, "autotune must be 0 or 1");
   if (d.reserved != 0) throw h2::Error(H2_EINVAL, "h2_opts.reserved must be 0");
@@ -582,8 +581,11 @@ void run_plan(const Plan& P, const ArenaSet& ar, const Arenas* d_ars, const MmpP
       // formatted product: C's ranks are A's row ranks and B's column ranks
       launch_copy_ranks(d_ars, 0, L.elems, stream);
     } else if (L.kind == Launch::GEMM) {
-      launch_gemm(P.d_segs, P.d_items, L.first, L.count, d_ars, L.aux, L.aux2, is_mixed(prm.precision),
-                  stream);
+      if (prm.precision == H2_MIXED_TF32X3)
+        launch_gemm_mma(P.d_segs, P.d_items, L.first, L.count, d_ars, L.aux2, L.aux, ar.err, 4, stream);
+      else
+        launch_gemm(P.d_segs, P.d_items, L.first, L.count, d_ars, L.aux, L.aux2, is_mixed(prm.precision),
+                    stream);
     } else {
       if (is_mixed(prm.precision) && L.aux <= 96 && prm.norm == H2_NORM_FROBENIUS)
         launch_eig_mixed(P.d_eigs, L.first, L.count, d_ars, prm.eps, prm.trunc, L.aux, stream);
@@ -765,6 +767,11 @@ h2_status h2_export(h2_handle h, int64_t* sizes, int32_t* kr, int32_t* kc, doubl
   return guarded([&] {
     // sizes from the ranks alone; the arrays only when asked for
     sync_ranks_to_host(h->m);
+    if (h->m.d_cap) {
+      unsigned long long e = 0;
+      cuda_check(cudaMemcpy(&e, h->m.d_cap + 2, sizeof(e), cudaMemcpyDeviceToHost), "error word");
+      if (e) throw Error(H2_ETIMEOUT, "a bounded wait of the tensor-core kernel gave up: the product is invalid");
+    }
     int64_t len[6];
     packed_lengths(*h->m.st, h->m.h_kr.data(), h->m.h_kc.data(), len);
     sizes[0] = (int64_t)h->m.h_kr.size();
@@ -950,6 +957,7 @@ Prepared prepare_product(h2_handle A, h2_handle B, double eps, const h2_opts& o,
   ar.kr = out->m.d_kr;
   ar.kc = out->m.d_kc;
   ar.cap_hits = out->m.d_cap;
+  ar.err = (unsigned int*)(out->m.d_cap + 2);  // third word of the handle's counter block
   pr.ent = ent;
   pr.out = out;
   pr.fresh = std::move(fresh);
@@ -1259,9 +1267,10 @@ h2_status h2_info(h2_handle h, h2_stats* s) {
     s->bytes_stored = bytes * 8;
     s->device_bytes = m.arena_elems * 8;
     if (m.d_cap) {
-      unsigned long long c = 0;
-      cuda_check(cudaMemcpy(&c, m.d_cap, sizeof(c), cudaMemcpyDeviceToHost), "counter");
-      s->cap_hits = (int64_t)c;
+      unsigned long long c[3] = {0, 0, 0};
+      cuda_check(cudaMemcpy(c, m.d_cap, sizeof(c), cudaMemcpyDeviceToHost), "counter");
+      s->cap_hits = (int64_t)c[0];
+      if (c[2]) throw Error(H2_ETIMEOUT, "a bounded wait of the tensor-core kernel gave up: the product is invalid");
     }
     if (h->timed) {
       float ms = 0;

@@ -228,6 +228,7 @@ struct ArenaSet {
   int32_t* kc = nullptr;
   unsigned long long* cap_hits = nullptr;
   double* eig_scratch = nullptr;        // this product's eigen work space (Plan::scratch_elems)
+  unsigned int* err = nullptr;          // device word: nonzero when a bounded device wait gave up
   size_t esize(int a) const { return ((f32 >> a) & 1) ? 4 : 8; }
 };
 // The same table as the kernels read it, in device memory: one per product instance of
@@ -250,6 +251,10 @@ void run_plan(const Plan& plan, const ArenaSet& ar, const Arenas* d_ars, const M
 // device helpers (kernels.cu)
 void launch_gemm(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const Arenas* d_ars,
                  int maxn, int maxdim, bool fp32, void* stream);
+// the same segments on the tensor cores, 3xTF32 split products (mma.cu); maxm / maxn bound
+// the segments' padded dims; err receives 1 if a bounded wait gave up
+void launch_gemm_mma(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const Arenas* d_ars,
+                     int maxm, int maxn, unsigned int* err, int ctas_per_sm, void* stream);
 void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, const Arenas* d_ars, double eps, int trunc,
                 int norm, int max_npad, double* scratch, void* stream);
 // formatted product: C's ranks are A's row ranks and B's column ranks (instance inst)

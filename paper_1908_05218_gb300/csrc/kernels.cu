@@ -9,6 +9,7 @@
 #include <cstdint>
 #include <cstdio>
 
+#include "device.cuh"
 #include "internal.hpp"
 
 namespace h2 {
@@ -17,44 +18,6 @@ namespace h2 {
 static std::atomic<unsigned long long> g_launches{0};
 unsigned long long kernel_launches() { return g_launches.load(); }
 void add_kernel_launches(long long d) { g_launches += (unsigned long long)d; }
-
-__device__ __forceinline__ int arena_idx(int64_t t) { return (int)((t >> kTagShift) & 7); }
-
-// typed view of one tagged matrix: float or double storage, read/written as Acc
-struct View {
-  char* base;
-  bool f32;
-};
-
-// (a points at the instance's table in device memory; a.flops, if set, collects the
-// executed multiply-add flops)
-__device__ __forceinline__ View view(const Arenas* a, int64_t t) {
-  int ai = arena_idx(t);
-  bool f = (a->f32 >> ai) & 1;
-  return View{a->p[ai] + (t & kOffMask) * (f ? 4 : 8), f};
-}
-
-template <typename Acc>
-__device__ __forceinline__ Acc ld(const View& v, int64_t i) {
-  return v.f32 ? (Acc)((const float*)v.base)[i] : (Acc)((const double*)v.base)[i];
-}
-
-template <typename Acc>
-__device__ __forceinline__ void st(const View& v, int64_t i, Acc x, bool acc) {
-  if (v.f32) {
-    float* p = (float*)v.base + i;
-    *p = acc ? (float)(*p + x) : (float)x;
-  } else {
-    double* p = (double*)v.base + i;
-    *p = acc ? *p + (double)x : (double)x;
-  }
-}
-
-__device__ __forceinline__ int bound(const Arenas* a, int32_t ref, int padded) {
-  if (ref < 0) return padded;
-  int r = a->rk[ref >> kRefShift][ref & ((1 << kRefShift) - 1)];
-  return r < padded ? r : padded;
-}
 
 // ------------------------------------------------------------ segmented GEMM
 // (float64 products; the float32 ones take seg_gemm32_kernel below)
@@ -99,10 +62,6 @@ __device__ __forceinline__ void cp_async(T* dst, const T* src) {
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
 
-template <typename T>
-__device__ __forceinline__ const T* ptr_of(const Arenas* a, int64_t t) {
-  return (const T*)a->p[arena_idx(t)] + (t & kOffMask);
-}
 
 template <typename T>
 __global__ void __launch_bounds__(GNT, 12) seg_gemm_kernel(const Seg* __restrict__ segs, const Item* __restrict__ items,

@@ -2,9 +2,12 @@
 
 Tolerances (float64 path): the structure and the ranks must match exactly; every
 entry of the dense product (or of C x for N too large to expand) agrees with the
-oracle's to 1e-12 of the largest entry (the two sides sum in different orders and
-decompose with different eigensolvers; each cluster's kept subspace is then fixed to
-~1e-16 / relative gap, and the truncation decisions are compared exactly).
+oracle's to 1e-12 of the largest entry.  The two sides sum in different orders and
+decompose with different eigensolvers, so each cluster's kept subspace agrees only to
+u lambda_1 / (lambda_k - lambda_k+1), u = 2^-53, and the directions near the threshold
+carry ~sqrt(thr) of the content: the attainable agreement is ~u / sqrt(thr), which
+passes 1e-12 only for thresholds thr >= 1e-8; below, the bound is 20 u / sqrt(thr)
+(sv mode at eps = 1e-5: thr = 1e-10, measured 8.9e-11).
 Mixed precisions: within 2 eps of the oracle, no less accurate against the exact
 product, and equal ranks wherever the oracle's decision is clear of the threshold by
 more than what float32 Gram matrices can move (1e-5 lambda_1).
@@ -25,6 +28,15 @@ pytestmark = pytest.mark.gpu
 
 TOL = 1e-12     # float64: element-wise, relative to the largest entry
 MIXED_MARGIN = 1e-5
+
+
+def fp64_tol(eps, mode):
+    """Element-wise float64 bound (module docstring): 1e-12, or 20 u / sqrt(thr) when the
+    truncation threshold thr lies below 1e-8."""
+    thr = {"paper": eps, "sv": eps * eps}.get(mode)
+    if thr is None or thr >= 1e-8:
+        return TOL
+    return max(TOL, 20 * 2.0 ** -53 / math.sqrt(thr))
 
 
 def assert_entries_close(got, ref, tol=TOL):
@@ -95,6 +107,22 @@ def test_structure_is_bit_exact(lib, name):
         assert list(zip(t.tolist(), s.tolist(), k.tolist())) == [(a, b, kinds[c]) for (a, b, c) in ob]
 
 
+@pytest.mark.parametrize("nx,ppc,leaf", [(2, 1280, 32), (2, 5120, 32), (4, 1024, 32), (2, 1000, 20)])
+def test_structure_on_grid_geometries_is_bit_exact(lib, nx, ppc, leaf):
+    # panel centroids on a grid: many admissibility tests hold with equality in exact
+    # arithmetic, so the library's host rounding must be the oracle's (no fused
+    # multiply-add contraction on the host, also where FMA is baseline)
+    w = inputs.workload_cube_array(nx, nx, ppc)
+    g = lib.h2_build(w.points, w.kernel, leaf, 1.0, 1e-2)
+    tree = build_tree(w.points, leaf)
+    part = build_partition(tree, 1.0)
+    np.testing.assert_array_equal(g.tree_perm(), tree.perm)
+    kinds = {"R": 0, "F": 1, "NL": 2}
+    for l in range(tree.L + 1):
+        t, s, k = g.level_blocks(l)
+        assert list(zip(t.tolist(), s.tolist(), k.tolist())) == [(a, b, kinds[c]) for (a, b, c) in part.blocks[l]], l
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_import_export_roundtrip_and_matvec(lib, name):
     import torch
@@ -141,7 +169,7 @@ def test_product_matches_oracle(lib, name, mode, eps, norm):
     np.testing.assert_array_equal(e.kc[: len(ckc)], ckc)
     d_gpu = gc.to_dense().cpu().numpy()
     d_orc = oh2.to_dense(C)
-    assert_entries_close(d_gpu, d_orc)
+    assert_entries_close(d_gpu, d_orc, fp64_tol(eps, mode))
     if mode == "full":
         assert_entries_close(d_gpu, oh2.to_dense(A) @ oh2.to_dense(B))
 
@@ -168,17 +196,18 @@ def test_structure_mismatch_is_rejected(lib):
     assert ei.value.code == lib.H2_ESTRUCT
 
 
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
 @pytest.mark.parametrize("name,mode,eps", [("cubes_1024", "paper", 1e-4), ("cubes_2048_invr2", "paper", 1e-3),
                                            ("uniform_1000_ragged", "paper", 1e-4)])
-def test_mixed_product_within_2eps_of_oracle(lib, name, mode, eps):
-    # float32 products with float32 accumulation, float64 Grams/eigen/bases: the
-    # result must stay within 2 eps of the float64 oracle and be no less accurate
-    # against the exact product A B
+def test_mixed_product_within_2eps_of_oracle(lib, name, mode, eps, prec):
+    # products in float32 (CUDA cores) or as three TF32 products (tensor cores), float32
+    # accumulation; float64 rank decisions and bases: the result must stay within 2 eps
+    # of the float64 oracle and be no less accurate against the exact product A B
     w, leaf, eta, A = oracle_case(name)
     st = {}
     C = ommp.mmp(A, A, eps, mode, stats=st)
     ga = lib.h2_import(w.points, leaf, eta, pack(A))
-    gc = ga.mmp(ga, eps, precision=lib.MIXED_FP32, trunc=mode)
+    gc = ga.mmp(ga, eps, precision=lib.MIXED_FP32 if prec == "fp32" else lib.MIXED_TF32X3, trunc=mode)
     d_gpu = gc.to_dense().cpu().numpy()
     d_orc = oh2.to_dense(C)
     exact = oh2.to_dense(A) @ oh2.to_dense(A)
@@ -195,7 +224,7 @@ def test_fp64_rank_bounds_do_not_change_results(lib):
     c1 = ga.mmp(ga, 1e-5, trunc="sv", out=c1)
     d1 = c1.to_dense().cpu().numpy()
     C = ommp.mmp(A, A, 1e-5, "sv")
-    assert_entries_close(d1, oh2.to_dense(C))
+    assert_entries_close(d1, oh2.to_dense(C), fp64_tol(1e-5, "sv"))
 
 
 @pytest.mark.parametrize("name,prec", [("cubes_1024", "fp64"), ("cubes_2048_invr2", "fp64"),
@@ -276,25 +305,33 @@ def test_batched_graph_and_replay_equal_single(lib, precision, trunc):
 
 
 def test_allocation_failure_during_a_product_leaves_the_library_usable(lib):
-    # a product that needs a new plan and a new output is refused at its first, second,
-    # ... device allocation: each attempt fails with H2_ENOMEM, and afterwards the same
-    # product succeeds and an earlier one still gives bit-identical results
+    # a product that needs a new program and a new output is refused at its 1st, 2nd,
+    # ... device allocation until it gets through: every refused attempt fails with
+    # H2_ENOMEM and leaves the library usable (what a refused attempt already built, such
+    # as its cached program, is reused by the next one); the product that finally runs
+    # equals one made without refusals, and an earlier product is unchanged
     import torch
     w, leaf, eta, A = oracle_case("cubes_1024")
     ga = lib.h2_import(w.points, leaf, eta, pack(A))
     ref = ga.mmp(ga, 1e-4, precision=lib.MIXED_FP32)
     x = torch.from_numpy(inputs.standard_normal((ga.n, 2), seed=3)).cuda()
     y_ref = ref.matvec(x)
-    for k in (0, 1, 2, 3, 5):
+    refused = 0
+    c = None
+    for k in range(0, 32):
         lib.set_alloc_limit(k)
         try:
-            with pytest.raises(lib.H2Error) as e:
-                ga.mmp(ga, 1e-4, precision=lib.MIXED_FP32, rank_cap=40)
-            assert e.value.code == 2
+            c = ga.mmp(ga, 1e-4, precision=lib.MIXED_FP32, rank_cap=40)
+            break
+        except lib.H2Error as e:
+            assert e.code == lib.H2_ENOMEM
+            refused += 1
         finally:
             lib.set_alloc_limit(-1)
-    c = ga.mmp(ga, 1e-4, precision=lib.MIXED_FP32, rank_cap=40)
+    assert c is not None and refused >= 4
     assert c.info()["cap_hits"] == 0
+    c2 = ga.mmp(ga, 1e-4, precision=lib.MIXED_FP32, rank_cap=40)
+    assert torch.equal(c.matvec(x), c2.matvec(x))
     assert torch.equal(ga.mmp(ga, 1e-4, precision=lib.MIXED_FP32).matvec(x), y_ref)
 
 
@@ -345,15 +382,38 @@ def test_n20480_float64_product_matches_the_oracle(lib, big_case):
     assert_entries_close(y, oh2.matvec(C, x))
 
 
-def test_n20480_mixed_product_against_the_oracle(lib, big_case):
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+def test_n20480_mixed_product_against_the_oracle(lib, big_case, prec):
     import torch
     wa, wb, A, B, C, st, x = big_case
     ga = lib.h2_import(wa.points, 32, 1.0, pack(A))
     gb = lib.h2_import(wb.points, 32, 1.0, pack(B))
-    gm = ga.mmp(gb, 1e-4, precision=lib.MIXED_FP32)
+    gm = ga.mmp(gb, 1e-4, precision=lib.MIXED_FP32 if prec == "fp32" else lib.MIXED_TF32X3)
     ym = gm.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
     yo = oh2.matvec(C, x)
     y_exact = oh2.matvec(A, oh2.matvec(B, x))
     assert rel(ym, yo) < 2e-4
     assert rel(ym, y_exact) < 1.2 * rel(yo, y_exact)
     assert clear_rank_mismatches(gm.export(), st, A.L) == []
+
+
+@pytest.mark.parametrize("n", [700, 2600])
+def test_tensor_core_product_is_deterministic_and_tracks_float32(lib, n):
+    # the 3xTF32 tensor-core products: reruns bit for bit equal (fixed accumulation
+    # order), and within a few float32 roundings of the CUDA-core float32 products:
+    # Gram matrices agree to ~1e-6, so ranks may differ only where an eigenvalue lies
+    # within that of the threshold (at most 2 % of the clusters), and C x within 2e-5
+    import torch
+    pts = inputs.stretched_box(n, seed=1)
+    h = lib.h2_build(pts, inputs.laplace_spec(n ** (-1 / 3)), 32, 1.0, 1e-4)
+    t1 = h.mmp(h, 1e-4, precision=lib.MIXED_TF32X3)
+    t2 = h.mmp(h, 1e-4, precision=lib.MIXED_TF32X3)
+    f = h.mmp(h, 1e-4, precision=lib.MIXED_FP32)
+    e1, e2, ef = t1.export(), t2.export(), f.export()
+    for k in ("kr", "kc", "vr", "vc", "er", "ec", "s", "f"):
+        np.testing.assert_array_equal(getattr(e1, k), getattr(e2, k))
+    differ = int(np.sum(e1.kr != ef.kr) + np.sum(e1.kc != ef.kc))
+    assert differ <= 0.02 * (len(e1.kr) + len(e1.kc)), differ
+    x = torch.from_numpy(inputs.standard_normal((n, 3), seed=2)).cuda()
+    yt, yf = t1.matvec(x), f.matvec(x)
+    assert float(torch.linalg.norm(yt - yf) / torch.linalg.norm(yf)) < 2e-5
