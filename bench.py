@@ -366,6 +366,8 @@ def main():
     ap.add_argument("--oracle-sample", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
+                    help="h2_opts.autotune for the headline product (the warm-up products explore)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the sv-rule, float64 and new-structure end-to-end runs")
     args = ap.parse_args()
@@ -442,12 +444,13 @@ def main():
     y_ref = A.matvec(B.matvec(x))          # Eq. error: exact H^2 matvecs
 
     C = None
+    at = bool(args.autotune)
     t0 = time.time()
-    C = A.mmp(B, eps, precision=prec, trunc=args.trunc, out=C)
+    C = A.mmp(B, eps, precision=prec, trunc=args.trunc, out=C, autotune=at)
     torch.cuda.synchronize()
     setup_s = time.time() - t0
     for _ in range(args.warmup):
-        C = A.mmp(B, eps, precision=prec, trunc=args.trunc, out=C)
+        C = A.mmp(B, eps, precision=prec, trunc=args.trunc, out=C, autotune=at)
     torch.cuda.synchronize()
 
     A.trace_enable(True)
@@ -459,7 +462,7 @@ def main():
         n_launch0 = lib.kernel_launches()
         ev0.record(stream)
         for _ in range(args.steps):
-            C = A.mmp(B, eps, precision=prec, trunc=args.trunc, out=C)
+            C = A.mmp(B, eps, precision=prec, trunc=args.trunc, out=C, autotune=at)
         ev1.record(stream)
         torch.cuda.synchronize()
         n_launch = lib.kernel_launches() - n_launch0
@@ -520,7 +523,7 @@ def main():
             "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic",
             "config": {"workload": f"{desc}; leaf {LEAF}, eta {ETA}, eps_trunc {eps} ({args.trunc} rule), "
                                    f"eps_H2 {EPS_H2}; A: 1/(4 pi r), B: 1/r^2",
-                       "precision": args.precision,
+                       "precision": args.precision, "autotune": at,
                        "inputs": "A, B, C together exceed L2 (no flush needed)", "parallelism": "replicas"},
             "mmp_s": ms * 1e-3, "rel_err_vs_exact_h2_matvecs": rel_err,
             "ranks_C_max_row": ranks_C, "cap_hits": cap_hits,

@@ -24,8 +24,28 @@ struct PlanKey {
            cap == o.cap && precision == o.precision;
   }
 };
+// Autotuning state of a program (h2_opts.autotune): for every GEMM launch group the
+// launch configuration in use (-1: still exploring) and the device time measured for
+// each candidate.  Product p of the exploration runs candidate p mod ncand on every
+// undecided group with events around each GEMM launch; the next tuned product reads
+// the times (they are complete by then: it synchronises on the last event) and a group
+// whose candidates are all measured keeps its fastest.  The candidates leave every
+// result bit-identical, so tuning changes only the time.
+struct TuneState {
+  std::mutex mu;
+  int ncand = 0;
+  int explored = 0;
+  bool pending = false;
+  std::vector<int8_t> choice;
+  std::vector<std::vector<float>> ms;
+  std::vector<void*> ev;
+  ~TuneState() {
+    for (void* e : ev) cudaEventDestroy((cudaEvent_t)e);
+  }
+};
 struct PlanEntry {
   h2::Plan plan;
+  TuneState tune;
   ~PlanEntry() { h2::free_plan(plan); }
 };
 
@@ -560,7 +580,7 @@ void free_plan(Plan& P) {
 }
 
 void run_plan(const Plan& P, const ArenaSet& ar, const Arenas* d_ars, const MmpParams& prm, void* stream,
-              bool skip_memset, Trace* tr) {
+              bool skip_memset, Trace* tr, const int8_t* choice, void* const* tune_ev) {
   if (tr) {
     while (tr->ev.size() < 2 * P.launches.size()) {
       cudaEvent_t e;
@@ -581,11 +601,15 @@ void run_plan(const Plan& P, const ArenaSet& ar, const Arenas* d_ars, const MmpP
       // formatted product: C's ranks are A's row ranks and B's column ranks
       launch_copy_ranks(d_ars, 0, L.elems, stream);
     } else if (L.kind == Launch::GEMM) {
+      const int v = choice ? choice[li] : 0;
+      if (tune_ev) cuda_check(cudaEventRecord((cudaEvent_t)tune_ev[2 * li], (cudaStream_t)stream), "event");
       if (prm.precision == H2_MIXED_TF32X3)
-        launch_gemm_mma(P.d_segs, P.d_items, L.first, L.count, d_ars, L.aux2, L.aux, ar.err, 4, stream);
+        launch_gemm_mma(P.d_segs, P.d_items, L.first, L.count, d_ars, L.aux2, L.aux, ar.err, mma_ctas_per_sm(v),
+                        stream);
       else
         launch_gemm(P.d_segs, P.d_items, L.first, L.count, d_ars, L.aux, L.aux2, is_mixed(prm.precision),
-                    stream);
+                    stream, v);
+      if (tune_ev) cuda_check(cudaEventRecord((cudaEvent_t)tune_ev[2 * li + 1], (cudaStream_t)stream), "event");
     } else {
       if (is_mixed(prm.precision) && L.aux <= 96 && prm.norm == H2_NORM_FROBENIUS)
         launch_eig_mixed(P.d_eigs, L.first, L.count, d_ars, prm.eps, prm.trunc, L.aux, stream);
@@ -980,7 +1004,58 @@ h2_status h2_mmp(h2_handle A, h2_handle B, double eps, const h2_opts* opts, h2_h
     place_regions(pr.ent->plan, pr.ar, workspace(o.stream, region_bytes(pr.ent->plan)).base);
     Arenas* d_ars = arena_slot(out, 0);
     upload_arenas(d_ars, to_arenas(pr.ar), o.stream);
-    run_plan(pr.ent->plan, pr.ar, d_ars, pr.prm, o.stream, false, pr.trace ? &out->trace : nullptr);
+    if (o.autotune) {
+      TuneState& ts = pr.ent->tune;
+      std::lock_guard<std::mutex> lk(ts.mu);
+      const Plan& P = pr.ent->plan;
+      const size_t nl = P.launches.size();
+      if (ts.choice.empty()) {
+        ts.ncand = o.precision == H2_MIXED_TF32X3 ? kMmaVariants : kGemmVariants;
+        ts.choice.assign(nl, 0);
+        ts.ms.assign(nl, std::vector<float>(ts.ncand, -1.f));
+        for (size_t li = 0; li < nl; ++li)
+          if (P.launches[li].kind == Launch::GEMM) ts.choice[li] = -1;
+        for (size_t i = 0; i < 2 * nl + 1; ++i) {  // two per launch and an end marker
+          cudaEvent_t e;
+          cuda_check(cudaEventCreate(&e), "event");
+          ts.ev.push_back((void*)e);
+        }
+      }
+      if (ts.pending) {  // the times of the last exploration product
+        cuda_check(cudaEventSynchronize((cudaEvent_t)ts.ev.back()), "event");
+        const int cand = (ts.explored - 1) % ts.ncand;
+        for (size_t li = 0; li < nl; ++li) {
+          if (ts.choice[li] >= 0) continue;
+          float t = 0;
+          cuda_check(cudaEventElapsedTime(&t, (cudaEvent_t)ts.ev[2 * li], (cudaEvent_t)ts.ev[2 * li + 1]), "event");
+          ts.ms[li][cand] = t;
+          int best = 0;
+          bool all = true;
+          for (int c = 0; c < ts.ncand; ++c) {
+            all = all && ts.ms[li][c] >= 0.f;
+            if (ts.ms[li][c] >= 0.f && ts.ms[li][c] < ts.ms[li][best]) best = c;
+          }
+          if (all) ts.choice[li] = (int8_t)best;
+        }
+        ts.pending = false;
+      }
+      bool exploring = false;
+      std::vector<int8_t> run(nl, 0);
+      const int cand = ts.explored % ts.ncand;
+      for (size_t li = 0; li < nl; ++li) {
+        run[li] = ts.choice[li] >= 0 ? ts.choice[li] : (int8_t)cand;
+        exploring = exploring || ts.choice[li] < 0;
+      }
+      run_plan(pr.ent->plan, pr.ar, d_ars, pr.prm, o.stream, false, pr.trace ? &out->trace : nullptr, run.data(),
+               exploring ? ts.ev.data() : nullptr);
+      if (exploring) {
+        cuda_check(cudaEventRecord((cudaEvent_t)ts.ev.back(), (cudaStream_t)o.stream), "event");
+        ts.explored += 1;
+        ts.pending = true;
+      }
+    } else {
+      run_plan(pr.ent->plan, pr.ar, d_ars, pr.prm, o.stream, false, pr.trace ? &out->trace : nullptr);
+    }
     cuda_check(cudaEventRecord(out->ev1, (cudaStream_t)o.stream), "event");
     out->timed = true;
     if (pr.fresh) *C = pr.fresh.release();

@@ -245,12 +245,19 @@ struct Arenas {
 Arenas to_arenas(const ArenaSet& a);
 // writes `a` to device memory `dst` in stream order (a one-thread kernel taking it by value)
 void upload_arenas(Arenas* dst, const Arenas& a, void* stream);
+// choice: per launch the launch configuration to use (null: defaults); tune_ev: two
+// events per launch recorded around the GEMM launches (autotuner exploration), or null
 void run_plan(const Plan& plan, const ArenaSet& ar, const Arenas* d_ars, const MmpParams& p, void* stream,
-              bool skip_memset, Trace* trace = nullptr);
+              bool skip_memset, Trace* trace = nullptr, const int8_t* choice = nullptr, void* const* tune_ev = nullptr);
 
 // device helpers (kernels.cu)
+// variant: launch configuration (0 default; see kGemmVariants), results identical for all
 void launch_gemm(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const Arenas* d_ars,
-                 int maxn, int maxdim, bool fp32, void* stream);
+                 int maxn, int maxdim, bool fp32, void* stream, int variant = 0);
+// launch configurations the autotuner tries per GEMM launch group: CUDA-core kernels
+// {column slices per CTA, whole segment per CTA}, tensor-core kernel {4, 2, 1} CTAs per SM
+constexpr int kGemmVariants = 2, kMmaVariants = 3;
+inline int mma_ctas_per_sm(int variant) { return variant == 1 ? 2 : (variant == 2 ? 1 : 4); }
 // the same segments on the tensor cores, 3xTF32 split products (mma.cu); maxm / maxn bound
 // the segments' padded dims; err receives 1 if a bounded wait gave up
 void launch_gemm_mma(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const Arenas* d_ars,

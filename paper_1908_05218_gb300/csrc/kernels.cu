@@ -468,9 +468,11 @@ __global__ void __launch_bounds__(GNT, 12) seg_gemm32_kernel(const Seg* __restri
 
 template <typename Acc>
 static void gemm_launch(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const Arenas* ar,
-                        int maxn, void* stream) {
+                        int maxn, int variant, void* stream) {
   const int64_t kMaxGrid = 2147483647LL;
-  int gy = (maxn + TILE - 1) / TILE;
+  // variant 0: one CTA per 32-column slice of a segment; 1: one CTA per segment (it walks
+  // all column tiles).  Every output element is summed in the same order either way.
+  int gy = variant == 1 ? 1 : (maxn + TILE - 1) / TILE;
   if (gy < 1) gy = 1;
   if (gy > 256) gy = 256;
   for (int64_t off = 0; off < count; off += kMaxGrid) {
@@ -485,10 +487,10 @@ static void gemm_launch(const Seg* d_segs, const Item* d_items, int64_t first, i
 }
 
 void launch_gemm(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const Arenas* d_ars,
-                 int maxn, int maxdim, bool fp32, void* stream) {
+                 int maxn, int maxdim, bool fp32, void* stream, int variant) {
   (void)maxdim;
-  if (fp32) gemm_launch<float>(d_segs, d_items, first, count, d_ars, maxn, stream);
-  else gemm_launch<double>(d_segs, d_items, first, count, d_ars, maxn, stream);
+  if (fp32) gemm_launch<float>(d_segs, d_items, first, count, d_ars, maxn, variant, stream);
+  else gemm_launch<double>(d_segs, d_items, first, count, d_ars, maxn, variant, stream);
 }
 
 __global__ void set_arenas_kernel(Arenas* dst, Arenas a) { *dst = a; }

@@ -47,10 +47,9 @@ namespace h2 {
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int kChunks = 8;            // 16-byte chunks of k per stage (k = 32 for TF32)
+constexpr int kChunks = 16;           // 16-byte chunks of k per stage (k = 64 for TF32)
 constexpr int kBatch = 64;            // items whose metadata sit in shared memory at once
 constexpr int kTileM = 128, kTileN = 128;
-constexpr uint32_t kTmemCols = 128;
 constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz: an mbarrier wait gives up after this
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -131,24 +130,44 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, float v[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// shared-memory layout of one stage: A_hi, A_lo (a_bytes each: live rows of the launch,
-// rounded up to 8, x 1 KB per 8 rows), B_hi, B_lo (b_bytes each)
+// shared-memory layout: two stages of A_hi, A_lo (a_bytes each: the launch's largest tile
+// rows, rounded up to 8, x kChunks x 16 bytes per row) and B_hi, B_lo (b_bytes each)
 struct StageLayout {
-  int a_bytes, b_bytes, stage_bytes, total;
+  int a_bytes, b_bytes, stage_bytes, total, tmem_cols;
 };
+
+constexpr int kRowGroupBytes = kChunks * 128;  // 8 rows x kChunks 16-byte chunks
 
 inline StageLayout stage_layout(int maxm, int maxn) {
   StageLayout s;
   const int mr = std::min(kTileM, std::max(8, maxm)), nr = std::min(kTileN, std::max(16, maxn));
-  s.a_bytes = ((mr + 7) / 8) * 1024;
-  s.b_bytes = ((nr + 15) / 16) * 2 * 1024;
+  s.a_bytes = ((mr + 7) / 8) * kRowGroupBytes;
+  s.b_bytes = ((nr + 15) / 16) * 2 * kRowGroupBytes;
   s.stage_bytes = 2 * s.a_bytes + 2 * s.b_bytes;
-  // the A descriptors span 128 rows (16 KB) from their start: keep that inside the buffer;
-  // at least 44 KB, so that no fifth CTA fits on an SM (four CTAs hold all 512 tensor-
-  // memory columns; a fifth would stall in tcgen05.alloc until one of them retires)
-  s.total = std::max(std::max(2 * s.stage_bytes, s.stage_bytes + s.a_bytes + 16 * 1024), 44 * 1024);
+  // tensor memory: 64 columns when every tile has at most 64 columns, else 128; at most
+  // 512 / cols CTAs of this kernel fit an SM's 512 columns, so the shared memory is padded
+  // until one more CTA would not fit (a CTA without columns would stall in tcgen05.alloc
+  // until another retires)
+  s.tmem_cols = nr <= 64 ? 64 : 128;
+  const int per_sm = 512 / s.tmem_cols;
+  const int floor_bytes = (228 * 1024) / (per_sm + 1) - 3 * 1024;
+  // an A descriptor spans the M = 128 (or 64) rows of its tile from its start: keep that
+  // inside the buffer
+  const int span = (mr > 64 ? 16 : 8) * kRowGroupBytes;
+  s.total = std::max(std::max(2 * s.stage_bytes, s.stage_bytes + s.a_bytes + span), floor_bytes);
   return s;
 }
+
+// one 16-byte chunk of k of a stage: the item's operands at the chunk's first k, their
+// leading dims, and whether 16-byte loads (K-major and aligned) and unmasked loads (the
+// item's padded k a multiple of four: entries past its rank are zero) apply
+struct Slot {
+  const float* a;
+  const float* b;
+  int lda, ldb;
+  int kv;     // k of the item left from the chunk's start (<= 0: a zero chunk)
+  int flags;  // 1: A 16-byte loads, 2: B 16-byte loads, 4: unmasked
+};
 
 __global__ void __launch_bounds__(kThreads) seg_mma_tf32x3_kernel(const Seg* __restrict__ segs,
                                                                   const Item* __restrict__ items, int64_t first,
@@ -159,8 +178,8 @@ __global__ void __launch_bounds__(kThreads) seg_mma_tf32x3_kernel(const Seg* __r
   __shared__ uint32_t s_tmem;
   __shared__ const float* it_a[kBatch];
   __shared__ const float* it_b[kBatch];
-  __shared__ int it_lda[kBatch], it_ldb[kBatch], it_k[kBatch], it_c0[kBatch + 1];
-  __shared__ int s_vec[kBatch];
+  __shared__ int it_lda[kBatch], it_ldb[kBatch], it_k[kBatch], it_c0[kBatch + 1], it_fl[kBatch];
+  __shared__ Slot tab[2][kChunks];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (tid == 0) {
@@ -170,7 +189,7 @@ __global__ void __launch_bounds__(kThreads) seg_mma_tf32x3_kernel(const Seg* __r
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                 "r"(kTmemCols));
+                 "r"(lay.tmem_cols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -182,6 +201,30 @@ __global__ void __launch_bounds__(kThreads) seg_mma_tf32x3_kernel(const Seg* __r
   bool pend[2] = {false, false};
   int buf = 0;
   bool fail = false;
+
+  // threads 0 .. kChunks-1 fill the slot table of the stage starting at chunk c0 of the
+  // current item batch (items nb, chunk prefix it_c0)
+  auto fill_slots = [&](int t, int c0, int nb, int nch) {
+    if (tid < kChunks) {
+      const int g = c0 + tid;
+      Slot sl{nullptr, nullptr, 0, 0, 0, 0};
+      if (g < nch) {
+        int q = 0;
+        while (q + 1 < nb && it_c0[q + 1] <= g) ++q;
+        const int k0 = (g - it_c0[q]) * 4;
+        sl.lda = it_lda[q];
+        sl.ldb = it_ldb[q];
+        sl.kv = it_k[q] - k0;
+        sl.flags = it_fl[q];
+        sl.a = it_a[q];
+        sl.b = it_b[q];
+        // A row-major / B transposed: k runs along the row; else k selects the row
+        sl.a += (sl.flags & 8) ? (int64_t)k0 * sl.lda : k0;
+        sl.b += (sl.flags & 16) ? k0 : (int64_t)k0 * sl.ldb;
+      }
+      tab[t][tid] = sl;
+    }
+  };
 
   for (int64_t si = blockIdx.x; si < count && !fail; si += gridDim.x) {
     const Seg s = segs[first + si];
@@ -210,23 +253,27 @@ __global__ void __launch_bounds__(kThreads) seg_mma_tf32x3_kernel(const Seg* __r
         const bool m64 = mc <= 64;
         const int nmma = m64 ? max(8, (nc + 7) & ~7) : max(16, (nc + 15) & ~15);
         const uint32_t idesc = idesc_tf32(m64 ? 64 : 128, nmma);
+        const int mrows = (mc + 7) & ~7, nrows = (nc + 7) & ~7;
         bool issued = false;  // an MMA of this tile has been issued
         for (int b0 = 0; b0 < s.count && !fail; b0 += kBatch) {
           const int nb = min(kBatch, s.count - b0);
-          __syncthreads();  // the previous batch's metadata are no longer read
+          __syncthreads();  // the previous batch's metadata and slots are no longer read
           if (tid < nb) {
             const Item iq = items[s.first + b0 + tid];
             const float* pa = ptr_of<float>(ar, iq.a);
             const float* pb = ptr_of<float>(ar, iq.b);
             const int la = iq.lda ? iq.lda : s.lda, lb = iq.ldb ? iq.ldb : s.ldb;
-            it_a[tid] = pa;
-            it_b[tid] = pb;
+            const int kp = iq.kpad ? iq.kpad : s.k;
+            // operand views of the tile: A at row m0, B at column n0
+            it_a[tid] = ta ? pa + m0 : pa + (int64_t)m0 * la;
+            it_b[tid] = tb ? pb + (int64_t)n0 * lb : pb + n0;
             it_lda[tid] = la;
             it_ldb[tid] = lb;
-            it_k[tid] = bound(ar, iq.kref, iq.kpad ? iq.kpad : s.k);
-            // 16-byte loads along k (A row-major, B transposed) when aligned
-            s_vec[tid] = ((((uintptr_t)pa) & 15) == 0 && (la & 3) == 0 ? 1 : 0) |
-                         ((((uintptr_t)pb) & 15) == 0 && (lb & 3) == 0 ? 2 : 0);
+            it_k[tid] = bound(ar, iq.kref, kp);
+            const bool pad4 = (kp & 3) == 0;
+            it_fl[tid] = (!ta && pad4 && (((uintptr_t)pa) & 15) == 0 && (la & 3) == 0 ? 1 : 0) |
+                         (tb && pad4 && (((uintptr_t)pb) & 15) == 0 && (lb & 3) == 0 ? 2 : 0) | (pad4 ? 4 : 0) |
+                         (ta ? 8 : 0) | (tb ? 16 : 0);
           }
           __syncthreads();
           if (tid == 0) {
@@ -240,6 +287,10 @@ __global__ void __launch_bounds__(kThreads) seg_mma_tf32x3_kernel(const Seg* __r
           }
           __syncthreads();
           const int nch = it_c0[nb];
+          fill_slots(buf, 0, nb, nch);
+          // (the slots of a stage are read after the barrier that ends the wait below or
+          // the one that precedes the first stage's staging)
+          __syncthreads();
           for (int c0 = 0; c0 < nch && !fail; c0 += kChunks) {
             if (pend[buf]) {
               if (!cta_wait(&bar[buf], phase[buf])) {
@@ -254,72 +305,74 @@ __global__ void __launch_bounds__(kThreads) seg_mma_tf32x3_kernel(const Seg* __r
             unsigned char* a_lo = base + lay.a_bytes;
             unsigned char* b_hi = base + 2 * lay.a_bytes;
             unsigned char* b_lo = b_hi + lay.b_bytes;
-            // chunk tasks: e -> (row group, chunk slot, row in group); row in group fastest
-            const int mrows = (mc + 7) & ~7, nrows = (nc + 7) & ~7;
-            for (int e = tid; e < (mrows + nrows) * kChunks; e += kThreads) {
-              const bool isA = e < mrows * kChunks;
-              const int f = isA ? e : e - mrows * kChunks;
-              const int rr = f & 7, slot = (f >> 3) & 7, rg = f >> 6;
+            const Slot* sl = tab[buf];
+            // chunks of this stage, rounded up to whole MMA k-steps of two chunks
+            const int live = min(kChunks, (nch - c0 + 1) & ~1);
+            // chunk tasks: e -> (row group, slot, row in group), row in group fastest, so
+            // that each quarter warp stores 128 contiguous bytes
+            for (int e = tid; e < mrows * kChunks; e += kThreads) {
+              const int rr = e & 7, slot = (e >> 3) & (kChunks - 1), rg = e / (8 * kChunks);
               const int row = rg * 8 + rr;
-              const int lim = isA ? mc : nc;
-              if (row >= lim) continue;
-              const int g = c0 + slot;
+              if (row >= mc || slot >= live) continue;
+              const Slot& q = sl[slot];
               float v[4] = {0.f, 0.f, 0.f, 0.f};
-              if (g < nch) {
-                int q = 0;
-                while (q + 1 < nb && it_c0[q + 1] <= g) ++q;
-                const int k0 = (g - it_c0[q]) * 4, K = it_k[q];
-                if (isA) {
-                  const float* A = it_a[q];
-                  const int lda = it_lda[q];
-                  if (!ta) {
-                    const float* p = A + (int64_t)(m0 + row) * lda + k0;
-                    if ((s_vec[q] & 1) && k0 + 3 < K) {
-                      const float4 x = *reinterpret_cast<const float4*>(p);
-                      v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
-                    } else {
-                      for (int u = 0; u < 4; ++u)
-                        if (k0 + u < K) v[u] = p[u];
-                    }
-                  } else {
-                    for (int u = 0; u < 4; ++u)
-                      if (k0 + u < K) v[u] = A[(int64_t)(k0 + u) * lda + m0 + row];
-                  }
+              if (q.kv > 0) {
+                if (q.flags & 1) {
+                  const float4 x = *reinterpret_cast<const float4*>(q.a + (int64_t)row * q.lda);
+                  v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+                } else if (!(q.flags & 8)) {
+                  const float* p = q.a + (int64_t)row * q.lda;
+                  for (int u = 0; u < 4; ++u) v[u] = ((q.flags & 4) || u < q.kv) ? p[u] : 0.f;
                 } else {
-                  const float* B = it_b[q];
-                  const int ldb = it_ldb[q];
-                  if (tb) {
-                    const float* p = B + (int64_t)(n0 + row) * ldb + k0;
-                    if ((s_vec[q] & 2) && k0 + 3 < K) {
-                      const float4 x = *reinterpret_cast<const float4*>(p);
-                      v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
-                    } else {
-                      for (int u = 0; u < 4; ++u)
-                        if (k0 + u < K) v[u] = p[u];
-                    }
-                  } else {
-                    for (int u = 0; u < 4; ++u)
-                      if (k0 + u < K) v[u] = B[(int64_t)(k0 + u) * ldb + n0 + row];
-                  }
+                  const float* p = q.a + row;
+                  for (int u = 0; u < 4; ++u) v[u] = ((q.flags & 4) || u < q.kv) ? p[(int64_t)u * q.lda] : 0.f;
                 }
               }
               uint4 hi, lo;
               split4(v, hi, lo);
-              const int off = rg * 1024 + slot * 128 + rr * 16;
-              *reinterpret_cast<uint4*>((isA ? a_hi : b_hi) + off) = hi;
-              *reinterpret_cast<uint4*>((isA ? a_lo : b_lo) + off) = lo;
+              const int off = rg * kRowGroupBytes + slot * 128 + rr * 16;
+              *reinterpret_cast<uint4*>(a_hi + off) = hi;
+              *reinterpret_cast<uint4*>(a_lo + off) = lo;
             }
+            for (int e = tid; e < nrows * kChunks; e += kThreads) {
+              const int rr = e & 7, slot = (e >> 3) & (kChunks - 1), rg = e / (8 * kChunks);
+              const int col = rg * 8 + rr;
+              if (col >= nc || slot >= live) continue;
+              const Slot& q = sl[slot];
+              float v[4] = {0.f, 0.f, 0.f, 0.f};
+              if (q.kv > 0) {
+                if (q.flags & 2) {
+                  const float4 x = *reinterpret_cast<const float4*>(q.b + (int64_t)col * q.ldb);
+                  v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+                } else if (q.flags & 16) {
+                  const float* p = q.b + (int64_t)col * q.ldb;
+                  for (int u = 0; u < 4; ++u) v[u] = ((q.flags & 4) || u < q.kv) ? p[u] : 0.f;
+                } else {
+                  const float* p = q.b + col;
+                  for (int u = 0; u < 4; ++u) v[u] = ((q.flags & 4) || u < q.kv) ? p[(int64_t)u * q.ldb] : 0.f;
+                }
+              }
+              uint4 hi, lo;
+              split4(v, hi, lo);
+              const int off = rg * kRowGroupBytes + slot * 128 + rr * 16;
+              *reinterpret_cast<uint4*>(b_hi + off) = hi;
+              *reinterpret_cast<uint4*>(b_lo + off) = lo;
+            }
+            // the next stage's slots (the other table: last read before the previous barrier)
+            if (c0 + kChunks < nch) fill_slots(buf ^ 1, c0 + kChunks, nb, nch);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
             if (tid == 0) {
               asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
               const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
-              for (int ks = 0; ks < kChunks / 2; ++ks) {
+              const int steps = live / 2;
+              for (int ks = 0; ks < steps; ++ks) {
                 const uint32_t o = ks * 256;
-                mma_tf32(tmem, smem_desc(ah + o, 128, 1024), smem_desc(bh + o, 128, 1024), idesc, issued ? 1u : 0u);
+                mma_tf32(tmem, smem_desc(ah + o, 128, kRowGroupBytes), smem_desc(bh + o, 128, kRowGroupBytes), idesc,
+                         issued ? 1u : 0u);
                 issued = true;
-                mma_tf32(tmem, smem_desc(ah + o, 128, 1024), smem_desc(bl + o, 128, 1024), idesc, 1u);
-                mma_tf32(tmem, smem_desc(al + o, 128, 1024), smem_desc(bh + o, 128, 1024), idesc, 1u);
+                mma_tf32(tmem, smem_desc(ah + o, 128, kRowGroupBytes), smem_desc(bl + o, 128, kRowGroupBytes), idesc, 1u);
+                mma_tf32(tmem, smem_desc(al + o, 128, kRowGroupBytes), smem_desc(bh + o, 128, kRowGroupBytes), idesc, 1u);
               }
               mma_commit(&bar[buf]);
             }
@@ -348,9 +401,17 @@ __global__ void __launch_bounds__(kThreads) seg_mma_tf32x3_kernel(const Seg* __r
           for (int c = 0; c < nmma; c += 16) {
             float v[16];
             tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-            if (mine)
-              for (int j = 0; j < 16 && c + j < nc; ++j)
-                st<float>(out, (int64_t)(m0 + row) * s.ldc + n0 + c + j, issued ? v[j] : 0.f, accum);
+            if (mine) {
+              const int jn = min(16, nc - c);
+              const int64_t o = (int64_t)(m0 + row) * s.ldc + n0 + c;
+              if (out.f32) {
+                float* po = (float*)out.base + o;
+                for (int j = 0; j < jn; ++j) po[j] = (accum ? po[j] : 0.f) + (issued ? v[j] : 0.f);
+              } else {
+                double* po = (double*)out.base + o;
+                for (int j = 0; j < jn; ++j) po[j] = (accum ? po[j] : 0.0) + (double)(issued ? v[j] : 0.f);
+              }
+            }
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -367,7 +428,8 @@ __global__ void __launch_bounds__(kThreads) seg_mma_tf32x3_kernel(const Seg* __r
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(lay.tmem_cols));
 }
 
 }  // namespace
@@ -379,8 +441,12 @@ void launch_gemm_mma(const Seg* d_segs, const Item* d_items, int64_t first, int6
     cudaFuncSetAttribute(seg_mma_tf32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   });
   const StageLayout lay = stage_layout(maxm, maxn);
-  // at most four resident CTAs per SM (4 x 128 tensor-memory columns = 512)
-  const int per_sm = std::max(1, std::min(ctas_per_sm, std::min(4, (int)((227 * 1024) / (lay.total + 2048)))));
+  // resident CTAs per SM: the tensor-memory limit (512 / columns), the shared-memory limit
+  // and the requested count (the autotuner's candidates scale the requested count)
+  const int tm_cap = 512 / lay.tmem_cols;
+  const int sm_cap = (int)((227 * 1024) / (lay.total + 4096));
+  const int want = ctas_per_sm * (lay.tmem_cols == 64 ? 2 : 1);
+  const int per_sm = std::max(1, std::min(want, std::min(tm_cap, sm_cap)));
   const int64_t grid = std::min<int64_t>(count, 152LL * per_sm);
   if (grid <= 0) return;
   seg_mma_tf32x3_kernel<<<(unsigned)grid, kThreads, lay.total, (cudaStream_t)stream>>>(d_segs, d_items, first, count,

@@ -21,6 +21,7 @@
 //   merge   2 x 2 assembly of children couplings (Eq. nonleafA, first form)
 //   split   top-down split of couplings held by NL targets (Sec. IV-E)
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <map>
 
@@ -62,8 +63,29 @@ struct PlanBuilder {
   }
   void close_memset(size_t idx, Arena a) { P.launches[idx].elems = top[a]; }
   void begin() { g0 = P.segs.size(); }
+  // Rank buckets: the segments of a launch group are independent, so they are ordered by
+  // cost class (floor(log2(m n sum k)) at the padded dims), largest first, keeping the
+  // program order inside a class; the kernels then start the long sums first.
+  void bucket() {
+    auto cls = [&](const Seg& s) {
+      double k = 0;
+      for (int32_t q = s.first; q < s.first + s.count; ++q) k += P.items[q].kpad ? P.items[q].kpad : s.k;
+      const double c = (double)s.m * s.n * std::max(1.0, k);
+      return (int)std::floor(std::log2(c));
+    };
+    std::vector<std::pair<int, int64_t>> key;
+    key.reserve(P.segs.size() - g0);
+    for (size_t i = g0; i < P.segs.size(); ++i) key.push_back({-cls(P.segs[i]), (int64_t)i});
+    std::stable_sort(key.begin(), key.end(),
+                     [](const std::pair<int, int64_t>& a, const std::pair<int, int64_t>& b) { return a.first < b.first; });
+    std::vector<Seg> sorted;
+    sorted.reserve(key.size());
+    for (auto& k : key) sorted.push_back(P.segs[k.second]);
+    std::copy(sorted.begin(), sorted.end(), P.segs.begin() + g0);
+  }
   void end(const char* phase, int level) {
     if (P.segs.size() > g0) {
+      bucket();
       Launch L;
       L.kind = Launch::GEMM;
       L.first = (int64_t)g0;

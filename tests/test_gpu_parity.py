@@ -402,7 +402,8 @@ def test_tensor_core_product_is_deterministic_and_tracks_float32(lib, n):
     # the 3xTF32 tensor-core products: reruns bit for bit equal (fixed accumulation
     # order), and within a few float32 roundings of the CUDA-core float32 products:
     # Gram matrices agree to ~1e-6, so ranks may differ only where an eigenvalue lies
-    # within that of the threshold (at most 2 % of the clusters), and C x within 2e-5
+    # within that of the threshold (at most 2 % of the clusters); such a flip moves C by
+    # the content of one near-threshold direction, so C x agrees within 2 eps
     import torch
     pts = inputs.stretched_box(n, seed=1)
     h = lib.h2_build(pts, inputs.laplace_spec(n ** (-1 / 3)), 32, 1.0, 1e-4)
@@ -416,4 +417,21 @@ def test_tensor_core_product_is_deterministic_and_tracks_float32(lib, n):
     assert differ <= 0.02 * (len(e1.kr) + len(e1.kc)), differ
     x = torch.from_numpy(inputs.standard_normal((n, 3), seed=2)).cuda()
     yt, yf = t1.matvec(x), f.matvec(x)
-    assert float(torch.linalg.norm(yt - yf) / torch.linalg.norm(yf)) < 2e-5
+    assert float(torch.linalg.norm(yt - yf) / torch.linalg.norm(yf)) < 2e-4
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+def test_autotuned_products_equal_fixed_ones(lib, prec):
+    # h2_opts.autotune: the first products of a program try the candidate launch
+    # configurations of every GEMM launch group and then keep the fastest; every
+    # candidate sums each output in the same order, so all products equal the untuned one
+    w, leaf, eta, A = oracle_case("cubes_2048_invr2")
+    ga = lib.h2_import(w.points, leaf, eta, pack(A))
+    p = {"fp64": lib.FP64, "fp32": lib.MIXED_FP32, "tf32x3": lib.MIXED_TF32X3}[prec]
+    ref = ga.mmp(ga, 1e-4, precision=p).export()
+    c = None
+    for _ in range(5):
+        c = ga.mmp(ga, 1e-4, precision=p, autotune=True, out=c)
+        e = c.export()
+        for f in ("kr", "kc", "vr", "vc", "er", "ec", "s", "f"):
+            np.testing.assert_array_equal(getattr(e, f), getattr(ref, f))
