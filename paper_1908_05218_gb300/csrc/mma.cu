@@ -47,7 +47,7 @@ namespace h2 {
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int kChunks = 16;           // 16-byte chunks of k per stage (k = 64 for TF32)
+constexpr int kChunks = 8;            // 16-byte chunks of k per stage (k = 32 for TF32)
 constexpr int kBatch = 64;            // items whose metadata sit in shared memory at once
 constexpr int kTileM = 128, kTileN = 128;
 constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz: an mbarrier wait gives up after this
@@ -95,26 +95,28 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-// bounded wait for the given phase parity of an mbarrier; false if it gave up
+// bounded wait for the given phase parity of an mbarrier; false if it gave up.  Each
+// try_wait may suspend the thread until the phase completes (at most ~0.1 ms per try).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   const uint32_t a = smem_u32(bar);
   const long long t0 = clock64();
   for (;;) {
     uint32_t done;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(a), "r"(parity)
+        : "r"(a), "r"(parity), "r"(100000)
         : "memory");
     if (done) return true;
     if (clock64() - t0 > kWaitCycles) return false;
   }
 }
 
-// the wait of every thread of the CTA, then one decision for all (a thread that gave up
-// makes the CTA give up, so that no thread is left alone at a barrier)
+// one thread waits for the phase, the others at the barrier (no issue slots spent on
+// polling); the barrier hands its outcome to every thread, so all give up together
 __device__ __forceinline__ bool cta_wait(uint64_t* bar, uint32_t parity) {
-  const bool ok = mbar_wait(bar, parity);
+  int ok = 1;
+  if (threadIdx.x == 0) ok = mbar_wait(bar, parity) ? 1 : 0;
   return !__syncthreads_or(!ok);
 }
 
@@ -423,8 +425,9 @@ __global__ void __launch_bounds__(kThreads) seg_mma_tf32x3_kernel(const Seg* __r
   if (fail) {
     if (tid == 0 && err) atomicOr(err, 1u);
     // drain: the products this CTA issued must finish before its tensor memory is freed
-    for (int b = 0; b < 2; ++b)
-      if (pend[b]) mbar_wait(&bar[b], phase[b]);
+    if (tid == 0)
+      for (int b = 0; b < 2; ++b)
+        if (pend[b]) mbar_wait(&bar[b], phase[b]);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
