@@ -17,8 +17,9 @@
  *     stream).  Calls that return host data synchronise that stream.
  *   - Point and vector data are in the caller's ("user") order; the library
  *     permutes to its cluster-tree order internally.
- *   - Real kernels only on the GPU path in this version (kind 0 and 1); the
- *     complex Helmholtz kernel returns H2_EUNSUPPORTED.
+ *   - Complex matrices (the Helmholtz kernel, or h2_import_complex): every complex
+ *     number is two doubles (real part, then imaginary part) in host and device
+ *     arrays; element counts count complex numbers.  Complex products run in float64.
  *   - Arithmetic: see h2_precision.
  */
 #ifndef H2_GB300_H
@@ -47,14 +48,14 @@ typedef enum {
 typedef enum {
   H2_K_LAPLACE = 0,    /* 1 / (4 pi r)                                   */
   H2_K_INV_R2 = 1,     /* 1 / r^2                                        */
-  H2_K_HELMHOLTZ = 2   /* exp(-j k r) / (4 pi r)  (oracle only for now)  */
+  H2_K_HELMHOLTZ = 2   /* exp(-j k r) / (4 pi r), complex (Sec. VI-B)    */
 } h2_kernel_kind;
 
 typedef struct {
   int32_t kind;        /* h2_kernel_kind */
   double wavenumber;   /* k of the Helmholtz kernel, ignored otherwise */
-  double diag_re;      /* value on the diagonal */
-  double diag_im;
+  double diag_re;      /* value on the diagonal (real part) */
+  double diag_im;      /* imaginary part of the diagonal (Helmholtz only) */
 } h2_kernel;
 
 /* Arithmetic of the product.  In every mode the normalised Gram sum, the rank decision
@@ -128,6 +129,8 @@ typedef struct {
   int64_t cap_hits;          /* clusters whose rank was cut at rank_cap (product) */
   double mmp_ms;             /* device time of the product that made this handle
                                 (0 for built handles)                             */
+  int32_t is_complex;        /* 1: complex elements (bytes above count 16 per element) */
+  int32_t reserved;
 } h2_stats;
 
 /* Build an H^2 approximation of the kernel matrix K(points_a, points_b) on the
@@ -142,8 +145,9 @@ typedef struct {
  * on level L, block partition by Eq. admCond with bounding boxes.  The numeric
  * construction is not specified by the paper (it cites another method); this library
  * uses nested far-field sampling with interpolative skeletons (sampled far field
- * per cluster, skeleton rows chosen by pivoted Gram-Schmidt).  Errors: H2_EINVAL for bad sizes or non-finite points,
- * H2_EUNSUPPORTED for a complex kernel. */
+ * per cluster, skeleton rows chosen by pivoted Gram-Schmidt).  The Helmholtz kernel gives a
+ * complex matrix (complex-symmetric: column bases equal row bases).  Errors: H2_EINVAL for
+ * bad sizes, non-finite points or an unknown kernel. */
 h2_status h2_build(const double* points, int64_t n, const h2_kernel* kernel,
                    int32_t leaf_size, double eta, double eps, const h2_opts* opts,
                    h2_handle* out);
@@ -193,8 +197,17 @@ h2_status h2_import(const double* points, int64_t n, int32_t leaf_size, double e
                     const double* s, const double* f, const h2_opts* opts,
                     h2_handle* out);
 
+/* h2_import for a complex matrix: the same arguments and layout, every array element a
+ * complex number stored as two doubles (real, imaginary); kr, kc as for h2_import.  The
+ * handle multiplies with complex handles only (H2_FP64).  Errors as h2_import. */
+h2_status h2_import_complex(const double* points, int64_t n, int32_t leaf_size, double eta,
+                            const int32_t* kr, const int32_t* kc, const double* vr,
+                            const double* vc, const double* er, const double* ec,
+                            const double* s, const double* f, const h2_opts* opts,
+                            h2_handle* out);
+
 /* The inverse of h2_import: copy the representation to host arrays in the same
- * packed layout.  Pass NULL for the arrays to query sizes only: the element counts
+ * packed layout (a complex handle: two doubles per element, h2_stats.is_complex).  Pass NULL for the arrays to query sizes only: the element counts
  * are written to sizes[0..5] = {ranks (each of kr, kc), vr, vc, er, ec, s, f}
  * (sizes has 8 entries: nranks, nvr, nvc, ner, nec, ns, nf, 0). */
 h2_status h2_export(h2_handle h, int64_t* sizes, int32_t* kr, int32_t* kc, double* vr,
@@ -222,12 +235,13 @@ h2_status h2_mmp_batched(const h2_handle* A, const h2_handle* B, int32_t count, 
 /* y = H x in exact H^2 arithmetic (Sec. II representation; the products A(B x) of
  * Eq. error in Sec. VI-A are formed with it): forward transform with the column bases,
  * coupling matrices, backward transform with the row bases, plus the dense near field.
- * x, y: device float64, column-major n x nrhs, user order; y is overwritten
- * (x and y must not overlap).  nrhs 1..16384.  Enqueued on the stream of the handle's
+ * x, y: device float64 (complex handles: two doubles per entry), column-major n x nrhs,
+ * user order; y is overwritten (x and y must not overlap).  nrhs 1..16384.  Enqueued on the stream of the handle's
  * last call.  Errors: H2_EINVAL for null pointers or nrhs out of range. */
 h2_status h2_matvec(h2_handle h, const double* x, double* y, int64_t nrhs);
 
-/* y = H x like h2_matvec, but the call allocates no memory at all: its work space
+/* y = H x like h2_matvec (real handles; H2_EUNSUPPORTED for complex ones), but the call
+ * allocates no memory at all: its work space
  * (the tree-ordered copies of x and y, the coefficient vectors of every level and
  * the block lists) lives in one fixed 32 MiB array compiled into the library.  The
  * paper has no counterpart; it exists for callers that may not allocate device
@@ -245,8 +259,9 @@ h2_status h2_matvec(h2_handle h, const double* x, double* y, int64_t nrhs);
 h2_status h2_matvec_noalloc(h2_handle h, const double* x, double* y, int64_t nrhs);
 
 /* Dense n x n matrix of the H^2 matrix (Sec. II: R blocks V_t S_ts V_s^T through the
- * nested bases, F blocks as stored), device float64, column-major, user order; for
- * testing, n <= 16384 (H2_EINVAL above).  Synchronises the handle's stream. */
+ * nested bases, F blocks as stored), device float64 (complex: two doubles per entry),
+ * column-major, user order; for testing, n <= 16384 (H2_EINVAL above).  Synchronises the
+ * handle's stream. */
 h2_status h2_to_dense(h2_handle h, double* out);
 
 /* Statistics; synchronises. */

@@ -19,9 +19,10 @@ struct PlanKey {
   const h2::Structure* st;
   std::vector<int> akr, akc, bkr, bkc;
   int trunc, cap, precision;
+  bool cplx;
   bool operator==(const PlanKey& o) const {
     return st == o.st && akr == o.akr && akc == o.akc && bkr == o.bkr && bkc == o.bkc && trunc == o.trunc &&
-           cap == o.cap && precision == o.precision;
+           cap == o.cap && precision == o.precision && cplx == o.cplx;
   }
 };
 // Autotuning state of a program (h2_opts.autotune): for every GEMM launch group the
@@ -240,8 +241,8 @@ int64_t mat_elems(Mat& m) {
 void alloc_mat(Mat& m) {
   const Structure& st = *m.st;
   int64_t o = mat_elems(m);
-  m.arena = (double*)dmalloc(o * sizeof(double));
-  cuda_check(cudaMemset(m.arena, 0, o * sizeof(double)), "zero arena");
+  m.arena = (double*)dmalloc(o * m.esize());
+  cuda_check(cudaMemset(m.arena, 0, o * m.esize()), "zero arena");
   const int nn = st.nnodes();
   m.d_kr = (int32_t*)dmalloc(2 * nn * sizeof(int32_t) + 64);
   m.d_kc = m.d_kr + nn;
@@ -350,6 +351,16 @@ void packed_lengths(const Structure& st, const int32_t* kr, const int32_t* kc, i
     }
 }
 
+// the copy tasks of a complex matrix as tasks over doubles (two per element)
+static void scale_tasks(std::vector<CopyTask>& tk) {
+  for (CopyTask& c : tk) {
+    c.arena_off *= 2;
+    c.packed_off *= 2;
+    c.cols *= 2;
+    c.ld *= 2;
+  }
+}
+
 // packed host arrays -> padded device arena (caps = largest rank per level, rounded up
 // to a multiple of four): the arrays are copied as they are into a device staging
 // buffer and scattered into the zeroed arena by transfer.cu's kernel
@@ -383,16 +394,19 @@ void unpack_view_to_device(const PackedView& v, Mat& m) {
     if (len[i] && !v.arr[i]) throw Error(H2_EINVAL, "null array");
   }
   alloc_mat(m);  // zeroed: padded entries stay exactly zero
+  // complex elements are two doubles: the same blocks, twice as wide in doubles
+  const int w = m.cplx ? 2 : 1;
+  if (w == 2) scale_tasks(tk);
   int64_t total = 0;
-  for (int i = 0; i < 6; ++i) total += len[i];
+  for (int i = 0; i < 6; ++i) total += len[i] * w;
   double* stage = (double*)dmalloc(std::max<int64_t>(1, total) * sizeof(double));
   CopyTask* d_tk = (CopyTask*)dmalloc(std::max<size_t>(1, tk.size()) * sizeof(CopyTask));
   try {
     int64_t off = 0;
     for (int i = 0; i < 6; ++i) {
       if (len[i])
-        copy_host(stage + off, v.arr[i], len[i] * sizeof(double), cudaMemcpyHostToDevice, "upload arrays");
-      off += len[i];
+        copy_host(stage + off, v.arr[i], len[i] * w * sizeof(double), cudaMemcpyHostToDevice, "upload arrays");
+      off += len[i] * w;
     }
     if (!tk.empty())
       cuda_check(cudaMemcpy(d_tk, tk.data(), tk.size() * sizeof(CopyTask), cudaMemcpyHostToDevice), "upload tasks");
@@ -419,8 +433,10 @@ void pack_to_host(Mat& m, double* const out[6]) {
   sync_ranks_to_host(m);
   int64_t len[6];
   std::vector<CopyTask> tk = copy_tasks(m, m.h_kr.data(), m.h_kc.data(), len);
+  const int w = m.cplx ? 2 : 1;
+  if (w == 2) scale_tasks(tk);
   int64_t total = 0;
-  for (int i = 0; i < 6; ++i) total += len[i];
+  for (int i = 0; i < 6; ++i) total += len[i] * w;
   double* stage = (double*)dmalloc(std::max<int64_t>(1, total) * sizeof(double));
   CopyTask* d_tk = (CopyTask*)dmalloc(std::max<size_t>(1, tk.size()) * sizeof(CopyTask));
   try {
@@ -432,8 +448,8 @@ void pack_to_host(Mat& m, double* const out[6]) {
     int64_t off = 0;
     for (int i = 0; i < 6; ++i) {
       if (len[i] && out[i])
-        copy_host(out[i], stage + off, len[i] * sizeof(double), cudaMemcpyDeviceToHost, "download arrays");
-      off += len[i];
+        copy_host(out[i], stage + off, len[i] * w * sizeof(double), cudaMemcpyDeviceToHost, "download arrays");
+      off += len[i] * w;
     }
   } catch (...) {
     cudaFree(stage);
@@ -553,12 +569,19 @@ void upload_plan(Plan& P, size_t region_esize, bool own_regions) {
       L.aux2 = md;
       L.flops = fl;
     } else if (L.kind == Launch::EIG) {
-      int mx = 1;
-      for (int64_t q = L.first; q < L.first + L.count; ++q) mx = std::max<int>(mx, P.eigs[q].n_pad);
+      int mx = 1, kl = 1;
+      for (int64_t q = L.first; q < L.first + L.count; ++q) {
+        mx = std::max<int>(mx, P.eigs[q].n_pad);
+        kl = std::max<int>(kl, P.eigs[q].klim);
+      }
+      L.aux2 = kl;
       if (mx > 256) throw Error(H2_EUNSUPPORTED, "Gram matrix larger than 256 (raise no caps in full mode)");
       L.aux = mx;
       int nn = mx + (mx & 1);
-      if (nn > 112) scratch = std::max<int64_t>(scratch, L.count * 2LL * nn * (nn + 1));
+      if (P.cplx)
+        scratch = std::max<int64_t>(scratch, zeig_scratch_elems(mx, L.count));
+      else if (nn > 112)
+        scratch = std::max<int64_t>(scratch, L.count * 2LL * nn * (nn + 1));
     }
   }
   P.scratch_elems = scratch;
@@ -603,7 +626,9 @@ void run_plan(const Plan& P, const ArenaSet& ar, const Arenas* d_ars, const MmpP
     } else if (L.kind == Launch::GEMM) {
       const int v = choice ? choice[li] : 0;
       if (tune_ev) cuda_check(cudaEventRecord((cudaEvent_t)tune_ev[2 * li], (cudaStream_t)stream), "event");
-      if (prm.precision == H2_MIXED_TF32X3)
+      if (P.cplx)
+        launch_zgemm(P.d_segs, P.d_items, L.first, L.count, d_ars, L.aux, stream);
+      else if (prm.precision == H2_MIXED_TF32X3)
         launch_gemm_mma(P.d_segs, P.d_items, L.first, L.count, d_ars, L.aux2, L.aux, ar.err, mma_ctas_per_sm(v),
                         stream);
       else
@@ -611,8 +636,11 @@ void run_plan(const Plan& P, const ArenaSet& ar, const Arenas* d_ars, const MmpP
                     stream, v);
       if (tune_ev) cuda_check(cudaEventRecord((cudaEvent_t)tune_ev[2 * li + 1], (cudaStream_t)stream), "event");
     } else {
-      if (is_mixed(prm.precision) && L.aux <= 96 && prm.norm == H2_NORM_FROBENIUS)
-        launch_eig_mixed(P.d_eigs, L.first, L.count, d_ars, prm.eps, prm.trunc, L.aux, stream);
+      if (P.cplx)
+        launch_zeig(P.d_eigs, L.first, L.count, d_ars, prm.eps, prm.trunc, prm.norm, L.aux, ar.eig_scratch, stream);
+      else if (is_mixed(prm.precision) && L.aux <= 96 && prm.norm == H2_NORM_FROBENIUS &&
+               (prm.trunc == H2_TRUNC_FULL || (prm.trunc == H2_TRUNC_SV ? prm.eps * prm.eps : prm.eps) >= 5e-5))
+        launch_eig_mixed(P.d_eigs, L.first, L.count, d_ars, prm.eps, prm.trunc, L.aux, L.aux2, stream);
       else
         launch_eig(P.d_eigs, L.first, L.count, d_ars, prm.eps, prm.trunc, prm.norm, L.aux, ar.eig_scratch, stream);
     }
@@ -646,10 +674,13 @@ h2_status h2_build(const double* points, int64_t n, const h2_kernel* kernel, int
   return guarded([&] {
     h2_opts o = defaults(opts);
     if (!(eps > 0) || !(eps < 1)) throw Error(H2_EINVAL, "eps must lie in (0, 1)");
-    if (kernel->kind == H2_K_HELMHOLTZ) throw Error(H2_EUNSUPPORTED, "complex kernels are not supported on the GPU path");
-    if (kernel->kind != H2_K_LAPLACE && kernel->kind != H2_K_INV_R2) throw Error(H2_EINVAL, "unknown kernel kind");
+    if (kernel->kind != H2_K_LAPLACE && kernel->kind != H2_K_INV_R2 && kernel->kind != H2_K_HELMHOLTZ)
+      throw Error(H2_EINVAL, "unknown kernel kind");
+    if (kernel->kind == H2_K_HELMHOLTZ && !(kernel->wavenumber >= 0 && std::isfinite(kernel->wavenumber)))
+      throw Error(H2_EINVAL, "the Helmholtz kernel needs a finite wavenumber >= 0");
     auto h = std::make_unique<h2_matrix>();
     h->m.st = structure_for(points, n, leaf_size, eta);
+    h->m.cplx = kernel->kind == H2_K_HELMHOLTZ;
     Packed p;
     build_h2_host(*h->m.st, *kernel, eps, p);
     PackedView v;
@@ -785,6 +816,28 @@ h2_status h2_import(const double* points, int64_t n, int32_t leaf_size, double e
   });
 }
 
+h2_status h2_import_complex(const double* points, int64_t n, int32_t leaf_size, double eta, const int32_t* kr,
+                            const int32_t* kc, const double* vr, const double* vc, const double* er, const double* ec,
+                            const double* s, const double* f, const h2_opts* opts, h2_handle* out) {
+  if (!points || !kr || !kc || !out) return fail(H2_EINVAL, "null argument");
+  *out = nullptr;
+  return guarded([&] {
+    h2_opts o = defaults(opts);
+    auto h = std::make_unique<h2_matrix>();
+    h->m.st = structure_for(points, n, leaf_size, eta);
+    h->m.cplx = true;
+    PackedView v;
+    v.kr = kr;
+    v.kc = kc;
+    packed_lengths(*h->m.st, kr, kc, v.len);
+    const double* a[6] = {vr, vc, er, ec, s, f};
+    for (int i = 0; i < 6; ++i) v.arr[i] = a[i];
+    unpack_view_to_device(v, h->m);
+    finish_handle(h.get(), o);
+    *out = h.release();
+  });
+}
+
 h2_status h2_export(h2_handle h, int64_t* sizes, int32_t* kr, int32_t* kc, double* vr, double* vc, double* er,
                     double* ec, double* s, double* f) {
   if (!h || !sizes) return fail(H2_EINVAL, "null argument");
@@ -877,9 +930,12 @@ Prepared prepare_product(h2_handle A, h2_handle B, double eps, const h2_opts& o,
     if (o.trunc != H2_TRUNC_FULL && o.trunc != H2_TRUNC_FORMATTED && !(eps > 0 && eps < 1))
     throw Error(H2_EINVAL, "eps must lie in (0, 1)");
   if (!same_structure(*A->m.st, *B->m.st)) throw Error(H2_ESTRUCT, "A and B have different trees or partitions");
+  if (A->m.cplx != B->m.cplx) throw Error(H2_EINVAL, "A and B must both be real or both complex");
+  if (A->m.cplx && o.precision != H2_FP64)
+    throw Error(H2_EUNSUPPORTED, "complex products run in float64 (H2_FP64) only");
   MmpParams prm{eps, o.trunc, o.rank_cap, o.precision, o.norm, o.autotune};
   // plan cache, process-wide
-  PlanKey key{A->m.st.get(), A->m.Kr, A->m.Kc, B->m.Kr, B->m.Kc, o.trunc, o.rank_cap, o.precision};
+  PlanKey key{A->m.st.get(), A->m.Kr, A->m.Kc, B->m.Kr, B->m.Kc, o.trunc, o.rank_cap, o.precision, A->m.cplx};
   std::shared_ptr<PlanEntry> ent;
   {
     std::lock_guard<std::mutex> lk(g_cache_mu);
@@ -911,7 +967,8 @@ Prepared prepare_product(h2_handle A, h2_handle B, double eps, const h2_opts& o,
                                 is_mixed(o.precision) ? probe.off_S[0] : 0};
       validate_plan(ent->plan, sizes);
     }
-    upload_plan(ent->plan, is_mixed(o.precision) ? sizeof(float) : sizeof(double), false);
+    upload_plan(ent->plan, A->m.cplx ? 2 * sizeof(double) : (is_mixed(o.precision) ? sizeof(float) : sizeof(double)),
+                false);
     std::lock_guard<std::mutex> lk(g_cache_mu);
     g_plans.push_back({key, ent});
   }
@@ -920,13 +977,15 @@ Prepared prepare_product(h2_handle A, h2_handle B, double eps, const h2_opts& o,
   if (!held) A->plans_held.push_back(ent);
   h2_matrix* out = existing;
   bool reuse = out && out->m.st == A->m.st && out->origin_trunc == o.trunc && out->origin_cap == o.rank_cap &&
-               out->origin_prec == o.precision && out->m.Kr == ent->plan.ckr && out->m.Kc == ent->plan.ckc;
+               out->origin_prec == o.precision && out->m.Kr == ent->plan.ckr && out->m.Kc == ent->plan.ckc &&
+               out->m.cplx == A->m.cplx;
   std::unique_ptr<h2_matrix> fresh;
   if (!reuse) {
     fresh = std::make_unique<h2_matrix>();
     fresh->m.st = A->m.st;
     fresh->m.Kr = ent->plan.ckr;
     fresh->m.Kc = ent->plan.ckc;
+    fresh->m.cplx = A->m.cplx;
     alloc_mat(fresh->m);
     fresh->m.stream = o.stream;
     make_user_map(fresh.get());
@@ -943,7 +1002,7 @@ Prepared prepare_product(h2_handle A, h2_handle B, double eps, const h2_opts& o,
   out->m.ranks_on_host = false;
   cudaStream_t s = (cudaStream_t)o.stream;
   cuda_check(cudaEventRecord(out->ev0, s), "event");
-  cuda_check(cudaMemsetAsync(out->m.arena, 0, out->m.arena_elems * sizeof(double), s), "zero C");
+  cuda_check(cudaMemsetAsync(out->m.arena, 0, out->m.arena_elems * out->m.esize(), s), "zero C");
   cuda_check(cudaMemsetAsync(out->m.d_kr, 0, 2 * A->m.st->nnodes() * sizeof(int32_t) + 64, s), "zero ranks");
   ArenaSet ar;
   const bool mixed = is_mixed(o.precision);
@@ -964,6 +1023,8 @@ Prepared prepare_product(h2_handle A, h2_handle B, double eps, const h2_opts& o,
   } else {
     ar.p[AR_A] = A->m.arena;
     ar.p[AR_B] = B->m.arena;
+    if (A->m.cplx)
+      ar.c16 = (1u << AR_A) | (1u << AR_B) | (1u << AR_C) | (1u << AR_P) | (1u << AR_G0) | (1u << AR_G1) | (1u << AR_S);
   }
   ar.p[AR_C] = out->m.arena;
   ar.rk[RK_AR] = A->m.d_kr;
@@ -1251,7 +1312,7 @@ h2_status h2_matvec(h2_handle h, const double* x, double* y, int64_t nrhs) {
       build_matvec_plan(h->m, nrhs, *p, ox, oy);
       int64_t sizes[kArenas] = {h->m.arena_elems, 0, 0, p->region[AR_P], 0, 0, 0, 0};
       validate_plan(*p, sizes);
-      upload_plan(*p, sizeof(double), true);
+      upload_plan(*p, h->m.esize(), true);
       h->mv_offs[nrhs] = {ox, oy};
       it = h->mv_plans.emplace(nrhs, std::move(p)).first;
     }
@@ -1261,24 +1322,33 @@ h2_status h2_matvec(h2_handle h, const double* x, double* y, int64_t nrhs) {
     int64_t rows = (1LL << st.L) * st.LS;
     cudaStream_t s = (cudaStream_t)h->m.stream;
     double* W = P.d_region[AR_P];
-    cuda_check(cudaMemsetAsync(W, 0, P.region[AR_P] * sizeof(double), s), "zero workspace");
-    double* xt = W + offset_of(offs.first);
-    double* yt = W + offset_of(offs.second);
-    launch_permute(x, xt, h->d_user, rows, st.n, nrhs, true, s);
+    const int w = h->m.cplx ? 2 : 1;  // doubles per element
+    cuda_check(cudaMemsetAsync(W, 0, P.region[AR_P] * h->m.esize(), s), "zero workspace");
+    double* xt = W + offset_of(offs.first) * w;
+    double* yt = W + offset_of(offs.second) * w;
+    if (h->m.cplx)
+      launch_zpermute(x, xt, h->d_user, rows, st.n, nrhs, true, s);
+    else
+      launch_permute(x, xt, h->d_user, rows, st.n, nrhs, true, s);
     ArenaSet ar;
     ar.p[AR_A] = h->m.arena;
     ar.p[AR_P] = W;
+    if (h->m.cplx) ar.c16 = (1u << AR_A) | (1u << AR_P);
     MmpParams prm{0, 0, 0, 0};
     Arenas* d_ars = arena_slot(h, 1);
     upload_arenas(d_ars, to_arenas(ar), s);
     run_plan(P, ar, d_ars, prm, s, true);
-    launch_permute(yt, y, h->d_user, rows, st.n, nrhs, false, s);
+    if (h->m.cplx)
+      launch_zpermute(yt, y, h->d_user, rows, st.n, nrhs, false, s);
+    else
+      launch_permute(yt, y, h->d_user, rows, st.n, nrhs, false, s);
     cuda_check(cudaGetLastError(), "matvec");
   });
 }
 
 h2_status h2_matvec_noalloc(h2_handle h, const double* x, double* y, int64_t nrhs) {
   if (!h || !x || !y) return fail(H2_EINVAL, "null argument");
+  if (h->m.cplx) return fail(H2_EUNSUPPORTED, "the no-allocation matvec is real only");
   std::string err;
   h2_status st = h2::matvec_noalloc(h->m, h->d_user, x, y, nrhs, err);
   if (st != H2_OK) return fail(st, err);
@@ -1290,9 +1360,12 @@ h2_status h2_to_dense(h2_handle h, double* out) {
   int64_t n = h->m.st->n;
   if (n > 16384) return fail(H2_EINVAL, "to_dense is for n <= 16384");
   return guarded([&] {
-    double* eye = (double*)dmalloc(n * n * sizeof(double));
+    double* eye = (double*)dmalloc(n * n * h->m.esize());
     cudaStream_t s = (cudaStream_t)h->m.stream;
-    launch_identity(eye, n, s);
+    if (h->m.cplx)
+      launch_zidentity(eye, n, s);
+    else
+      launch_identity(eye, n, s);
     cuda_check(cudaGetLastError(), "identity");
     h2_status st = h2_matvec(h, eye, out, n);
     cudaStreamSynchronize(s);
@@ -1339,8 +1412,9 @@ h2_status h2_info(h2_handle h, h2_stats* s) {
         bytes += (int64_t)(m.h_kc[Structure::node(l + 1, 2 * t)] + m.h_kc[Structure::node(l + 1, 2 * t + 1)]) *
                  m.h_kc[Structure::node(l, t)];
       }
-    s->bytes_stored = bytes * 8;
-    s->device_bytes = m.arena_elems * 8;
+    s->bytes_stored = bytes * (int64_t)m.esize();
+    s->device_bytes = m.arena_elems * (int64_t)m.esize();
+    s->is_complex = m.cplx ? 1 : 0;
     if (m.d_cap) {
       unsigned long long c[3] = {0, 0, 0};
       cuda_check(cudaMemcpy(c, m.d_cap, sizeof(c), cudaMemcpyDeviceToHost), "counter");

@@ -79,6 +79,8 @@ struct Mat {
   unsigned long long* d_cap = nullptr;  // device counter of ranks cut at the cap
   void* stream = nullptr;
   std::vector<void*> extra_allocs;  // device buffers owned by the handle
+  bool cplx = false;                // complex float64 (double2) elements: complex kernel functions
+  size_t esize() const { return cplx ? 16 : 8; }
 
   int64_t Vr(int64_t t) const { return off_Vr + t * st->LS * Kr[st->L]; }
   int64_t Vc(int64_t t) const { return off_Vc + t * st->LS * Kc[st->L]; }
@@ -113,7 +115,8 @@ inline int64_t offset_of(int64_t t) { return t & kOffMask; }
 // m, n, k are the padded dims; a dim reference (rank array << kRefShift | cluster node,
 // -1 = none) bounds the loop by the actual rank read on the device, so padded zeros
 // are skipped.  Rank arrays: 0 A.kr, 1 A.kc, 2 B.kr, 3 B.kc, 4 C.kr, 5 C.kc.
-enum SegFlags : uint8_t { SF_TA = 1, SF_TB = 2, SF_ACC = 4, SF_SUM = 8 };
+// SF_CA / SF_CB: conjugate A / B (complex operands; real kernels ignore them)
+enum SegFlags : uint8_t { SF_TA = 1, SF_TB = 2, SF_ACC = 4, SF_SUM = 8, SF_CA = 16, SF_CB = 32 };
 enum RankSrc : int32_t { RK_AR = 0, RK_AC = 1, RK_BR = 2, RK_BC = 3, RK_CR = 4, RK_CC = 5 };
 constexpr int kRefShift = 26;
 inline int32_t rref(RankSrc s, int node) { return (int32_t)((s << kRefShift) | node); }
@@ -158,7 +161,7 @@ struct Launch {
   int64_t off = 0, elems = 0;    // MEMSET: tagged offset and size
   int level = -1;
   int aux = 0;                   // GEMM: largest n; EIG: largest Gram dim
-  int aux2 = 0;                  // GEMM: largest max(m, n)
+  int aux2 = 0;                  // GEMM: largest max(m, n); EIG: largest rank limit
   const char* phase = "";
   double flops = 0;              // GEMM: counted 2 m n k over the group
 };
@@ -176,7 +179,8 @@ struct Plan {
   // work regions owned by the plan (matvec plans); product plans take theirs from the
   // per-stream work space at run time (see region_bytes)
   double* d_region[kArenas] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  int region_esize = 8;  // bytes per element of the work regions (4 for a mixed product)
+  int region_esize = 8;  // bytes per element of the work regions (4 for a mixed product, 16 complex)
+  bool cplx = false;     // complex operands: complex GEMM and Hermitian eigen kernels
   int64_t scratch_elems = 0;    // float64 eigen work space for Gram matrices above 112 (taken
                                 // with the work regions, so that concurrent products never share it)
   int64_t flops = 0;     // counted 2mnk over GEMM segments (padded dims)
@@ -229,7 +233,8 @@ struct ArenaSet {
   unsigned long long* cap_hits = nullptr;
   double* eig_scratch = nullptr;        // this product's eigen work space (Plan::scratch_elems)
   unsigned int* err = nullptr;          // device word: nonzero when a bounded device wait gave up
-  size_t esize(int a) const { return ((f32 >> a) & 1) ? 4 : 8; }
+  uint32_t c16 = 0;                     // arenas of complex float64 elements (bit per arena)
+  size_t esize(int a) const { return ((c16 >> a) & 1) ? 16 : (((f32 >> a) & 1) ? 4 : 8); }
 };
 // The same table as the kernels read it, in device memory: one per product instance of
 // a launch (segments and eigen tasks carry the instance index).
@@ -271,7 +276,7 @@ void add_kernel_launches(long long d);
 void init_kernel_attributes();  // once per process, before launches or captures   // graph replays add their kernels; captures take theirs back
 void launch_to_f32(const double* src, float* dst, int64_t n, void* stream);
 void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const Arenas* d_ars, double eps,
-                      int trunc, int max_npad, void* stream);
+                      int trunc, int max_npad, int max_klim, void* stream);
 void launch_permute(const double* src, double* dst, const int64_t* user, int64_t rows, int64_t n,
                     int64_t nrhs, bool to_tree, void* stream);
 void launch_identity(double* out, int64_t n, void* stream);
@@ -279,7 +284,18 @@ h2_status matvec_noalloc(const Mat& m, const int64_t* d_user, const double* x, d
                          std::string& err);
 void cuda_check(int err, const char* what);
 
-// construction (builder.cpp): fills host arrays of the packed import layout
+// complex float64 kernels (zkernels.cu)
+void launch_zgemm(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const Arenas* d_ars, int maxn,
+                  void* stream);
+int64_t zeig_scratch_elems(int max_npad, int64_t count);  // float64 words of eigen work space
+void launch_zeig(const EigTask* d_eigs, int64_t first, int64_t count, const Arenas* d_ars, double eps, int trunc,
+                 int norm, int max_npad, double* scratch, void* stream);
+void launch_zpermute(const double* src, double* dst, const int64_t* user, int64_t rows, int64_t n, int64_t nrhs,
+                     bool to_tree, void* stream);
+void launch_zidentity(double* out, int64_t n, void* stream);
+
+// construction (builder.cpp): fills host arrays of the packed import layout (complex
+// kernels: two doubles, real and imaginary part, per element)
 struct Packed {
   std::vector<int32_t> kr, kc;
   std::vector<double> vr, vc, er, ec, s, f;

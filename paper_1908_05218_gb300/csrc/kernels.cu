@@ -1025,33 +1025,37 @@ __global__ void __launch_bounds__(256) eig_mixed_kernel(const EigTask* __restric
 // The same result as eig_mixed_kernel for truncation thresholds of 5e-5 lambda_1 and
 // above (and the full mode), with the work cut where it does not decide the result:
 //   (1) float32 round-robin Jacobi on G padded with zero rows and columns to a
-//       multiple of four (pad indices are never rotated).  One step rotates rows and
-//       columns together: a thread takes the 2 x 2 block (pair k, pair l), k <= l, of
-//       A, forms M_k X M_l^T and writes the block and its mirror image; eigenvectors
-//       are the ROWS of Vt, so their update is a float4 row rotation.  Rotations with
-//       |a_pq| <= 2^-24 sqrt(|a_pp a_qq|) are skipped (below float32 resolution of
-//       their 2 x 2 problem; together they keep off(A)^2 far below the 1e-10 stop);
+//       multiple of four (pad indices are never rotated).  G is summed straight from the
+//       three Gram matrices in global memory into float32 (no float64 copy of G is
+//       kept).  One step rotates rows and columns together: a thread takes the 2 x 2
+//       block (pair k, pair l), k <= l, of A, forms M_k X M_l^T and writes the block and
+//       its mirror image; eigenvectors are the ROWS of Vt, so their update is a float4
+//       row rotation.  Rotations with |a_pq| <= 2^-24 sqrt(|a_pp a_qq|) are skipped
+//       (below float32 resolution of their 2 x 2 problem; together they keep off(A)^2 far
+//       below the 1e-10 stop);
 //   (2) a_jj is v_j^T G v_j to float32 accuracy: the columns with a_jj above a
-//       quarter of the threshold are the only ones whose quotient can pass it, and
-//       only their float64 Rayleigh quotients v^T G v / v^T v are formed; these
-//       decide the rank (sorted decreasing, ties by index);
+//       quarter of the threshold are the only ones whose quotient can pass it, and for
+//       the decisive ones (the top cluster and those within 2e-5 lambda_1 of the
+//       threshold) the float64 Rayleigh quotient v^T G v / v^T v is formed, G read from
+//       the Gram matrices in global memory; these decide the rank (sorted decreasing,
+//       ties by index);
 //   (3) the kept columns go to float64 and one Newton-Schulz step on those columns,
 //       V <- V (3 I - V^T V) / 2, makes them orthonormal to ~1e-14.
-// Float64 work: n^2 per candidate plus 2 n r^2, against 3 n^3 in eig_mixed_kernel.
-// Shared memory: G (float64, nn x (nn+1)), A (float32, nn x (nn+1)), Vt (float32,
-// nn x (nn+4)) = nn (16 nn + 28) bytes; after (2) G's space holds the kept columns
-// (n x (r+1) float64) and A/Vt's the r x (r+1) Newton-Schulz matrix.
+// Float64 work: n^2 per decisive candidate plus 2 n r^2, against 3 n^3 in eig_mixed_kernel.
+// Shared memory (kk = the launch's largest rank limit, at most nn): buffer 1 holds A
+// (float32, nn x (nn+1)) and later the kept columns (float64, nn x (kk+1)); buffer 2
+// holds Vt (float32, nn x (nn+4)) and later the Newton-Schulz matrix (float64, kk x (kk+1)).
 constexpr int kKeptRows = 4;
 
 __host__ __device__ inline int round4(int n) { return (n + 3) & ~3; }
 
-// byte offsets of A and Vt and the total, shared by the kernel and its launch
-__host__ __device__ inline size_t eig_kept_off_a(int nn) { return (size_t)nn * (nn + 1) * sizeof(double); }
-__host__ __device__ inline size_t eig_kept_off_vt(int nn) {
-  return eig_kept_off_a(nn) + (size_t)nn * (nn + 1) * sizeof(float);
+__host__ __device__ inline size_t eig_kept_buf1(int nn, int kk) {
+  const size_t a = (size_t)nn * (nn + 1) * sizeof(float), v = (size_t)nn * (kk + 1) * sizeof(double);
+  return ((a > v ? a : v) + 15) & ~(size_t)15;
 }
-__host__ __device__ inline size_t eig_kept_smem(int nn) {
-  return eig_kept_off_vt(nn) + (size_t)nn * (nn + 4) * sizeof(float);
+__host__ __device__ inline size_t eig_kept_smem(int nn, int kk) {
+  const size_t t = (size_t)nn * (nn + 4) * sizeof(float), w = (size_t)kk * (kk + 1) * sizeof(double);
+  return eig_kept_buf1(nn, kk) + (t > w ? t : w);
 }
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -1061,7 +1065,7 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 __global__ void __launch_bounds__(256) eig_mixed_kept_kernel(const EigTask* __restrict__ tasks, int64_t first,
                                                              const Arenas* __restrict__ ars, double eps, int trunc,
-                                                             int nn_lo, int nn_hi) {
+                                                             int nn_lo, int nn_hi, int kk_max) {
   extern __shared__ __align__(16) unsigned char esm[];
   __shared__ int act[kMixMax + 4];
   __shared__ double red[8];
@@ -1071,6 +1075,7 @@ __global__ void __launch_bounds__(256) eig_mixed_kept_kernel(const EigTask* __re
   __shared__ double rq[kMixMax], rqs[kMixMax];
   __shared__ float lam32[kMixMax];
   __shared__ double rowbuf[kKeptRows * kMixMax];
+  __shared__ double s_inv[3];
   __shared__ int s_n, s_nc, s_rank;
   const EigTask t = tasks[first + blockIdx.x];
   const Arenas* ar = ars + t.inst;  // the task's product instance
@@ -1095,38 +1100,42 @@ __global__ void __launch_bounds__(256) eig_mixed_kept_kernel(const EigTask* __re
   // one launch per size tier (nn_lo, nn_hi], shared memory sized for nn_hi: a task
   // whose actual size is outside the tier is done by another launch
   if (nn <= nn_lo || nn > nn_hi) return;
-  double* G = (double*)esm;                            // row stride la
-  float* A = (float*)(esm + eig_kept_off_a(nn));       // row stride la
-  float* Vt = (float*)(esm + eig_kept_off_vt(nn));     // row stride lv; 16-byte aligned rows
-  for (int e = tid; e < nn * la; e += nt) G[e] = 0.0;
-  __syncthreads();
+  const int kk = min(kk_max, nn_hi);
+  float* A = (float*)esm;                                   // row stride la (buffer 1)
+  float* Vt = (float*)(esm + eig_kept_buf1(nn_hi, kk));     // row stride lv; 16-byte aligned rows (buffer 2)
+  // scale of each Gram matrix: 1 / ||G_m||_F (0: absent or zero, left out of the sum)
   for (int m = 0; m < 3; ++m) {
-    if (t.g[m] < 0) continue;
-    const View Gm = view(ar, t.g[m]);
     double loc = 0.0;
-    for (int e = tid; e < n * n; e += nt) {
-      const double v = ld<double>(Gm, (int64_t)act[e / n] * t.n_pad + act[e % n]);
-      loc += v * v;
+    if (t.g[m] >= 0) {
+      const View Gm = view(ar, t.g[m]);
+      for (int e = tid; e < n * n; e += nt) {
+        const double v = ld<double>(Gm, (int64_t)act[e / n] * t.n_pad + act[e % n]);
+        loc += v * v;
+      }
     }
     const double nrm2 = block_sum(loc, red);
-    if (nrm2 > 0.0) {
-      const double inv = 1.0 / sqrt(nrm2);
-      for (int e = tid; e < n * n; e += nt)
-        G[(e / n) * la + (e % n)] += ld<double>(Gm, (int64_t)act[e / n] * t.n_pad + act[e % n]) * inv;
-    }
-    __syncthreads();
+    if (tid == 0) s_inv[m] = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0;
   }
+  __syncthreads();
+  // A = the normalised sum (float32), zero padding, symmetrised; Vt = I
+  for (int e = tid; e < nn * la; e += nt) {
+    const int a = e / la, b = e - a * la;
+    double v = 0.0;
+    if (a < n && b < n)
+      for (int m = 0; m < 3; ++m)
+        if (s_inv[m] > 0.0) v += ld<double>(view(ar, t.g[m]), (int64_t)act[a] * t.n_pad + act[b]) * s_inv[m];
+    A[e] = (float)v;
+  }
+  for (int e = tid; e < nn * lv; e += nt) Vt[e] = (e / lv == e % lv) ? 1.f : 0.f;
+  __syncthreads();
   for (int e = tid; e < nn * nn; e += nt) {
     const int a = e / nn, b = e % nn;
     if (a < b) {
-      const double v = 0.5 * (G[a * la + b] + G[b * la + a]);
-      G[a * la + b] = v;
-      G[b * la + a] = v;
+      const float v = 0.5f * (A[a * la + b] + A[b * la + a]);
+      A[a * la + b] = v;
+      A[b * la + a] = v;
     }
   }
-  __syncthreads();
-  for (int e = tid; e < nn * la; e += nt) A[e] = (float)G[e];
-  for (int e = tid; e < nn * lv; e += nt) Vt[e] = (e / lv == e % lv) ? 1.f : 0.f;
   __syncthreads();
   // (1) float32 Jacobi, stop when off(A)^2 <= 1e-10 |A|^2 (as eig_mixed_kernel)
   const int half = np / 2, nq = nn / 4;
@@ -1243,16 +1252,22 @@ __global__ void __launch_bounds__(256) eig_mixed_kept_kernel(const EigTask* __re
     const float* v = Vt + cand[ci] * lv;
     double num = 0.0, den = 0.0;
     for (int a = lane; a < n; a += 32) {
-      const double* g = G + a * la;
-      double a0 = 0.0, a1 = 0.0;
-      int b = 0;
-      for (; b + 1 < n; b += 2) {
-        a0 = fma(g[b], (double)v[b], a0);
-        a1 = fma(g[b + 1], (double)v[b + 1], a1);
+      double ga = 0.0;
+      for (int m = 0; m < 3; ++m) {
+        if (!(s_inv[m] > 0.0)) continue;
+        const View Gm = view(ar, t.g[m]);
+        const int64_t row = (int64_t)act[a] * t.n_pad;
+        double a0 = 0.0, a1 = 0.0;
+        int b = 0;
+        for (; b + 1 < n; b += 2) {
+          a0 = fma(ld<double>(Gm, row + act[b]), (double)v[b], a0);
+          a1 = fma(ld<double>(Gm, row + act[b + 1]), (double)v[b + 1], a1);
+        }
+        if (b < n) a0 = fma(ld<double>(Gm, row + act[b]), (double)v[b], a0);
+        ga = fma(a0 + a1, s_inv[m], ga);
       }
-      if (b < n) a0 = fma(g[b], (double)v[b], a0);
       const double va = (double)v[a];
-      num = fma(va, a0 + a1, num);
+      num = fma(va, ga, num);
       den = fma(va, va, den);
     }
     num = warp_sum_d(num);
@@ -1284,16 +1299,17 @@ __global__ void __launch_bounds__(256) eig_mixed_kept_kernel(const EigTask* __re
     ranks[t.rank_out] = r;
   }
   __syncthreads();
-  // (3) kept columns in float64 (G's space), one Newton-Schulz step on them
+  // (3) kept columns in float64 (buffer 1), one Newton-Schulz step on them (its matrix
+  // in buffer 2 once Vt has been read)
   const int rank = s_rank, lk = rank + 1;
-  double* Vk = G;
+  double* Vk = reinterpret_cast<double*>(esm);
   for (int e = tid; e < n * rank; e += nt) {
     const int a = e / rank, c = e - a * rank;
     Vk[a * lk + c] = (double)Vt[order[c] * lv + a];
   }
   __syncthreads();
   if (rank > 0) {
-    double* T = reinterpret_cast<double*>(A);
+    double* T = reinterpret_cast<double*>(Vt);
     const int lt = rank + 1;
     for (int e = tid; e < rank * rank; e += nt) {
       const int i = e / rank, j = e - i * rank;
@@ -1360,14 +1376,14 @@ void init_kernel_attributes() {
     cudaFuncSetAttribute(eig_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(3 * kMixMax * (kMixMax + 1) * sizeof(double)));
     cudaFuncSetAttribute(eig_mixed_kept_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)eig_kept_smem(kMixMax));
+                         (int)eig_kept_smem(kMixMax, kMixMax));
     cudaFuncSetAttribute(eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(2 * kEigSmemMax * (kEigSmemMax + 1) * sizeof(double)));
   });
 }
 
 void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const Arenas* ar, double eps,
-                      int trunc, int max_npad, void* stream) {
+                      int trunc, int max_npad, int max_klim, void* stream) {
   init_kernel_attributes();
   const double thr = trunc == H2_TRUNC_SV ? eps * eps : eps;
   if (trunc != H2_TRUNC_FULL && thr < 5e-5) {
@@ -1380,16 +1396,16 @@ void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const
     // the level's padded size comes from the rank caps; the actual sizes (children's
     // ranks) are only known on the device and are mostly far smaller, so tasks are
     // launched in size tiers, each with the shared memory of its largest size (more
-    // CTAs per SM for the small ones)
-    // (tiers run one after the other)
+    // CTAs per SM for the small ones); the tiers run one after the other
     const int top = round4(max_npad);
     int lo = -1;
-    for (int hi : {48, 64, kMixMax}) {
+    for (int hi : {32, 48, 56, 64, 80, kMixMax}) {
       const int h = hi < top ? hi : top;
       // (128 threads are enough for nn <= 48: a step has <= 300 block and row tasks)
       if (h > lo) {
-        eig_mixed_kept_kernel<<<(unsigned)count, h <= 48 ? 128 : 256, eig_kept_smem(h), (cudaStream_t)stream>>>(
-            d_eigs, first, ar, eps, trunc, lo, h);
+        const int kk = std::min(h, std::max(1, max_klim));
+        eig_mixed_kept_kernel<<<(unsigned)count, h <= 48 ? 128 : 256, eig_kept_smem(h, kk), (cudaStream_t)stream>>>(
+            d_eigs, first, ar, eps, trunc, lo, h, kk);
         g_launches += 1;
       }
       lo = h;

@@ -220,6 +220,12 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
   const Structure& st = *A.st;
   const int L = st.L, LS = st.LS, lmin = st.lmin;
   PlanBuilder pb(P);
+  // complex operands (complex kernel functions): the program is the same, with the
+  // conjugations of the paper's formulas on the operands (flags SF_CA / SF_CB, ignored
+  // for real operands), and P^B of the nested projection formed without conjugation
+  const bool cplx = A.cplx;
+  P.cplx = cplx;
+  C.cplx = cplx;
   // caps of C: leaf LS, non-leaf min(2 K[l+1], cap) (no cap in full mode), 0 above l_min;
   // each rounded up to a multiple of four for storage
   const bool formatted = prm.trunc == H2_TRUNC_FORMATTED;
@@ -348,7 +354,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
     const int gr = leaf ? LS : 2 * rC(c), gc = leaf ? LS : 2 * cC(c);
     std::vector<int64_t> G1r(nc, -1), G2r(nc, -1), G3r(nc, -1), G1c(nc, -1), G2c(nc, -1), G3c(nc, -1);
     // per-block factors reused after the eigen step
-    std::vector<int64_t> Y(nb, -1), Yb(nb, -1), Ach(nb, -1), Bch(nb, -1), Wr(nc, -1), Wc(nc, -1);
+    std::vector<int64_t> Y(nb, -1), Yb(nb, -1), Ach(nb, -1), Bch(nb, -1), Wr(nc, -1), Wc(nc, -1), Wcp(nc, -1);
     std::vector<int64_t> Mt(lt.tg.size(), -1);
 
     if (leaf) {
@@ -403,12 +409,12 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         pb.gemm1(Y[p], LS, rB(l), LS, LS, rB(l), rB(l), 0, tA(A.F(b.idx)), tB(B.Vr(b.s)), -1, BR(l, b.s));
         pb.gemm1(Yb[p], cA(l), LS, LS, cA(l), LS, LS, SF_TA, tA(A.Vc(b.t)), tB(B.F(b.idx)), AC(l, b.t));
         if (formatted) continue;
-        pb.gemm1(Q[p], LS, LS, LS, LS, LS, LS, SF_TB, tB(B.F(b.idx)), tB(B.F(b.idx)));
-        pb.gemm1(Rr[p], LS, LS, LS, LS, LS, LS, SF_TA, tA(A.F(b.idx)), tA(A.F(b.idx)));
+        pb.gemm1(Q[p], LS, LS, LS, LS, LS, LS, SF_TB | SF_CB, tB(B.F(b.idx)), tB(B.F(b.idx)));
+        pb.gemm1(Rr[p], LS, LS, LS, LS, LS, LS, SF_TA | SF_CB, tA(A.F(b.idx)), tA(A.F(b.idx)));
       }
       for (int64_t t = 0; t < nc && !formatted; ++t) {
-        pb.gemm1(G3r[t], LS, LS, rA(l), rA(l), rA(l), LS, SF_TB, tA(A.Vr(t)), tA(A.Vr(t)), -1, -1, AR(l, t));
-        pb.gemm1(G3c[t], LS, LS, cB(l), cB(l), cB(l), LS, SF_TB, tB(B.Vc(t)), tB(B.Vc(t)), -1, -1, BC(l, t));
+        pb.gemm1(G3r[t], LS, LS, rA(l), rA(l), rA(l), LS, SF_TB | SF_CB, tA(A.Vr(t)), tA(A.Vr(t)), -1, -1, AR(l, t));
+        pb.gemm1(G3c[t], LS, LS, cB(l), cB(l), cB(l), LS, SF_TB | SF_CB, tB(B.Vc(t)), tB(B.Vc(t)), -1, -1, BC(l, t));
       }
       pb.end("leaf_blockprod", l);
       // L2: dense targets (Sec. III-A) and Gram pieces
@@ -435,11 +441,11 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         }
         if (!r2.empty()) {
           G2r[t] = pb.alloc(AR_S, LS2);
-          pb.gemm(G2r[t], LS, LS, rB(l), rB(l), rB(l), LS, SF_TB, r2);  // Eq. Gr2L
+          pb.gemm(G2r[t], LS, LS, rB(l), rB(l), rB(l), LS, SF_TB | SF_CB, r2);  // Eq. Gr2L
         }
         if (!c2.empty()) {
           G2c[t] = pb.alloc(AR_S, LS2);
-          pb.gemm(G2c[t], LS, LS, cA(l), LS, LS, LS, SF_TA, c2);  // Eq. case2-ch
+          pb.gemm(G2c[t], LS, LS, cA(l), LS, LS, LS, SF_TA | SF_CB, c2);  // Eq. case2-ch
         }
       }
       pb.end("leaf_dense_gram", l);
@@ -453,7 +459,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       }
       for (int64_t p = 0; p < nb && !formatted; ++p) {
         if (Wsum[p] >= 0) pb.gemm1(Q[p], LS, LS, LS, LS, LS, LS, 0, tA(A.F(bl[p].idx)), Wsum[p]);
-        if (Wsc[p] >= 0) pb.gemm1(Rr[p], LS, LS, LS, LS, LS, LS, 0, Wsc[p], tB(B.F(bl[p].idx)));
+        if (Wsc[p] >= 0) pb.gemm1(Rr[p], LS, LS, LS, LS, LS, LS, SF_CB, Wsc[p], tB(B.F(bl[p].idx)));
       }
       pb.end("leaf_dense_gram", l);
       // L4: Eq. Gr1L / case1-ch regrouped; dense targets, F += Z V^B_k^T
@@ -474,7 +480,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         }
         if (!r1.empty()) {
           G1r[t] = pb.alloc(AR_S, LS2);
-          pb.gemm(G1r[t], LS, LS, LS, LS, LS, LS, SF_TB, r1);
+          pb.gemm(G1r[t], LS, LS, LS, LS, LS, LS, SF_TB | SF_CB, r1);
         }
         if (!c1.empty()) {
           G1c[t] = pb.alloc(AR_S, LS2);
@@ -526,6 +532,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       for (int64_t t = 0; t < nc; ++t) {
         Wr[t] = pb.alloc(AR_S, (int64_t)gr * rA(l));
         Wc[t] = pb.alloc(AR_S, (int64_t)gc * cB(l));
+        if (cplx) Wcp[t] = pb.alloc(AR_S, (int64_t)gc * cB(l));
         G3r[t] = pb.alloc(AR_S, (int64_t)gr * gr);
         G3c[t] = pb.alloc(AR_S, (int64_t)gc * gc);
       }
@@ -540,8 +547,11 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         for (int a = 0; a < 2; ++a) {
           pb.gemm1(Wr[t] + (int64_t)a * hr * rA(l), hr, rA(l), rA(c), rA(c), rA(l), rA(l), 0, PA[c][2 * t + a],
                    tA(A.Er(l, t) + (int64_t)a * rA(c) * rA(l)), CR(c, 2 * t + a), AR(l, t), AR(c, 2 * t + a));
-          pb.gemm1(Wc[t] + (int64_t)a * hc * cB(l), hc, cB(l), cB(c), hc, cB(l), cB(l), SF_TA, PB[c][2 * t + a],
+          pb.gemm1(Wc[t] + (int64_t)a * hc * cB(l), hc, cB(l), cB(c), hc, cB(l), cB(l), SF_TA | SF_CB, PB[c][2 * t + a],
                    tB(B.Ec(l, t) + (int64_t)a * cB(c) * cB(l)), CC(c, 2 * t + a), BC(l, t), BC(c, 2 * t + a));
+          if (cplx)  // P^B_ch^T E^B without conjugation, for the nested projection (Eq. nonleafproj)
+            pb.gemm1(Wcp[t] + (int64_t)a * hc * cB(l), hc, cB(l), cB(c), hc, cB(l), cB(l), SF_TA, PB[c][2 * t + a],
+                     tB(B.Ec(l, t) + (int64_t)a * cB(c) * cB(l)), CC(c, 2 * t + a), BC(l, t), BC(c, 2 * t + a));
         }
       // Eq. case1-ch-nl from the children's summed couplings, without assembling M:
       // block (a, a') of G1r_i = sum over targets (i, k), b of S_{ia,kb} S_{ia',kb}^T
@@ -567,7 +577,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
                 for (int b = 0; b < 2; ++b)
                   it.push_back({child_ssum(lt.tg[tq.first], a, b), child_ssum(lt.tg[tq.first], a2, b),
                                 CC(c, 2 * lt.tg[tq.first].k + b)});
-              pb.gemm(G1r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr, hr, hr, hc, hc, hc, gr, SF_TB, it,
+              pb.gemm(G1r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr, hr, hr, hc, hc, hc, gr, SF_TB | SF_CB, it,
                       CR(c, 2 * t + a), CR(c, 2 * t + a2));
             }
         }
@@ -580,7 +590,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
                 for (int a = 0; a < 2; ++a)
                   it.push_back({child_ssum(lt.tg[tq.first], a, b), child_ssum(lt.tg[tq.first], a, b2),
                                 CR(c, 2 * lt.tg[tq.first].i + a)});
-              pb.gemm(G1c[t] + (int64_t)b * hc * gc + (int64_t)b2 * hc, hc, hc, hr, hc, hc, gc, SF_TA, it,
+              pb.gemm(G1c[t] + (int64_t)b * hc * gc + (int64_t)b2 * hc, hc, hc, hr, hc, hc, gc, SF_TA | SF_CB, it,
                       CC(c, 2 * t + b), CC(c, 2 * t + b2));
             }
         }
@@ -597,14 +607,14 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         }
         if (!r2.empty()) {
           G2r[t] = pb.alloc(AR_S, (int64_t)gr * gr);
-          pb.gemm(G2r[t], gr, gr, rB(l), rB(l), rB(l), gr, SF_TB, r2);  // Eq. case2-ch-nl
+          pb.gemm(G2r[t], gr, gr, rB(l), rB(l), rB(l), gr, SF_TB | SF_CB, r2);  // Eq. case2-ch-nl
         }
         if (!c2.empty()) {
           G2c[t] = pb.alloc(AR_S, (int64_t)gc * gc);
-          pb.gemm(G2c[t], gc, gc, cA(l), gc, gc, gc, SF_TA, c2);
+          pb.gemm(G2c[t], gc, gc, cA(l), gc, gc, gc, SF_TA | SF_CB, c2);
         }
-        pb.gemm1(G3r[t], gr, gr, rA(l), rA(l), rA(l), gr, SF_TB, Wr[t], Wr[t], -1, -1, AR(l, t));  // Eq. case3-ch-nl
-        pb.gemm1(G3c[t], gc, gc, cB(l), cB(l), cB(l), gc, SF_TB, Wc[t], Wc[t], -1, -1, BC(l, t));
+        pb.gemm1(G3r[t], gr, gr, rA(l), rA(l), rA(l), gr, SF_TB | SF_CB, Wr[t], Wr[t], -1, -1, AR(l, t));  // Eq. case3-ch-nl
+        pb.gemm1(G3c[t], gc, gc, cB(l), cB(l), cB(l), gc, SF_TB | SF_CB, Wc[t], Wc[t], -1, -1, BC(l, t));
       }
       pb.end("nl_gram", l);
       for (size_t q = 0; q < lt.tg.size(); ++q)
@@ -662,23 +672,30 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
     pb.begin();
     for (int64_t t = 0; t < nc; ++t) {
       if (leaf) {
-        pb.gemm1(PA[l][t], rC(l), rA(l), LS, rC(l), rA(l), rA(l), SF_TA, tCb(C.Vr(t)), tA(A.Vr(t)), CR(l, t), AR(l, t));
-        pb.gemm1(PB[l][t], cB(l), cC(l), LS, cB(l), cC(l), cC(l), SF_TA, tB(B.Vc(t)), tCb(C.Vc(t)), BC(l, t), CC(l, t));
+        pb.gemm1(PA[l][t], rC(l), rA(l), LS, rC(l), rA(l), rA(l), SF_TA | SF_CA, tCb(C.Vr(t)), tA(A.Vr(t)), CR(l, t),
+                 AR(l, t));
+        pb.gemm1(PB[l][t], cB(l), cC(l), LS, cB(l), cC(l), cC(l), SF_TA | SF_CB, tB(B.Vc(t)), tCb(C.Vc(t)), BC(l, t),
+                 CC(l, t));
       } else {
-        pb.gemm1(PA[l][t], rC(l), rA(l), gr, rC(l), rA(l), rA(l), SF_TA, tCb(C.Er(l, t)), Wr[t], CR(l, t), AR(l, t));
-        pb.gemm1(PB[l][t], cB(l), cC(l), gc, cB(l), cC(l), cC(l), SF_TA, Wc[t], tCb(C.Ec(l, t)), BC(l, t), CC(l, t));
+        pb.gemm1(PA[l][t], rC(l), rA(l), gr, rC(l), rA(l), rA(l), SF_TA | SF_CA, tCb(C.Er(l, t)), Wr[t], CR(l, t),
+                 AR(l, t));
+        pb.gemm1(PB[l][t], cB(l), cC(l), gc, cB(l), cC(l), cC(l), SF_TA | SF_CB, cplx ? Wcp[t] : Wc[t], tCb(C.Ec(l, t)),
+                 BC(l, t), CC(l, t));
       }
     }
     for (int64_t p = 0; p < nb; ++p) {
       const Block& b = bl[p];
       if (leaf && b.kind == KF) {
-        pb.gemm1(Ahat[l][p], rC(l), rB(l), LS, rC(l), rB(l), rB(l), SF_TA, tCb(C.Vr(b.t)), Y[p], CR(l, b.t), BR(l, b.s));
-        pb.gemm1(Bhat[l][p], cA(l), cC(l), LS, LS, cC(l), cC(l), 0, Yb[p], tCb(C.Vc(b.s)), AC(l, b.t), CC(l, b.s));
-        pb.gemm1(Ach[p], rC(l), LS, LS, rC(l), LS, LS, SF_TA, tCb(C.Vr(b.t)), tA(A.F(b.idx)), CR(l, b.t));
-        pb.gemm1(Bch[p], LS, cC(l), LS, LS, cC(l), cC(l), 0, tB(B.F(b.idx)), tCb(C.Vc(b.s)), -1, CC(l, b.s));
+        pb.gemm1(Ahat[l][p], rC(l), rB(l), LS, rC(l), rB(l), rB(l), SF_TA | SF_CA, tCb(C.Vr(b.t)), Y[p], CR(l, b.t),
+                 BR(l, b.s));
+        pb.gemm1(Bhat[l][p], cA(l), cC(l), LS, LS, cC(l), cC(l), SF_CB, Yb[p], tCb(C.Vc(b.s)), AC(l, b.t), CC(l, b.s));
+        pb.gemm1(Ach[p], rC(l), LS, LS, rC(l), LS, LS, SF_TA | SF_CA, tCb(C.Vr(b.t)), tA(A.F(b.idx)), CR(l, b.t));
+        pb.gemm1(Bch[p], LS, cC(l), LS, LS, cC(l), cC(l), SF_CB, tB(B.F(b.idx)), tCb(C.Vc(b.s)), -1, CC(l, b.s));
       } else if (!leaf && b.kind == KNL) {
-        pb.gemm1(Ahat[l][p], rC(l), rB(l), gr, rC(l), rB(l), rB(l), SF_TA, tCb(C.Er(l, b.t)), Y[p], CR(l, b.t), BR(l, b.s));
-        pb.gemm1(Bhat[l][p], cA(l), cC(l), gc, gc, cC(l), cC(l), 0, Yb[p], tCb(C.Ec(l, b.s)), AC(l, b.t), CC(l, b.s));
+        pb.gemm1(Ahat[l][p], rC(l), rB(l), gr, rC(l), rB(l), rB(l), SF_TA | SF_CA, tCb(C.Er(l, b.t)), Y[p], CR(l, b.t),
+                 BR(l, b.s));
+        pb.gemm1(Bhat[l][p], cA(l), cC(l), gc, gc, cC(l), cC(l), SF_CB, Yb[p], tCb(C.Ec(l, b.s)), AC(l, b.t),
+                 CC(l, b.s));
       }
     }
     if (!leaf) {
@@ -693,7 +710,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
             auto f = LT[c].id.find(Structure::key(2 * T.i + a, 2 * T.k + b));
             it.push_back({LT[c].tg[f->second].ssum, tCb(C.Ec(l, T.k) + (int64_t)b * hc * cC(l)), CC(c, 2 * T.k + b)});
           }
-          pb.gemm(Mt[q] + (int64_t)a * hr * cC(l), hr, cC(l), hc, hc, cC(l), cC(l), 0, it, CR(c, 2 * T.i + a),
+          pb.gemm(Mt[q] + (int64_t)a * hr * cC(l), hr, cC(l), hc, hc, cC(l), cC(l), SF_CB, it, CR(c, 2 * T.i + a),
                   CC(l, T.k));
         }
       }
@@ -739,8 +756,8 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       for (size_t q = 0; q < lt.tg.size(); ++q) {
         Target& T = lt.tg[q];
         if (Mt[q] >= 0)
-          pb.gemm1(T.ssum, rC(l), cC(l), gr, rC(l), cC(l), cC(l), SF_TA | SF_ACC, tCb(C.Er(l, T.i)), Mt[q], CR(l, T.i),
-                   CC(l, T.k));
+          pb.gemm1(T.ssum, rC(l), cC(l), gr, rC(l), cC(l), cC(l), SF_TA | SF_CA | SF_ACC, tCb(C.Er(l, T.i)), Mt[q],
+                   CR(l, T.i), CC(l, T.k));
       }
       pb.end("coup", l);
     }
@@ -837,6 +854,7 @@ void build_matvec_plan(const Mat& H, int64_t nrhs, Plan& P, int64_t& off_x, int6
   const Structure& st = *H.st;
   const int L = st.L, LS = st.LS;
   PlanBuilder pb(P);
+  P.cplx = H.cplx;
   const int64_t nl = 1LL << L;
   const int nr = (int)nrhs;
   const Arena W = AR_P;

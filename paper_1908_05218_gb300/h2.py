@@ -24,7 +24,7 @@ TRUNC_PAPER, TRUNC_SV, TRUNC_FULL, TRUNC_FORMATTED = 0, 1, 2, 3
 _TRUNC = {"paper": TRUNC_PAPER, "sv": TRUNC_SV, "full": TRUNC_FULL, "formatted": TRUNC_FORMATTED}
 
 # exported symbols and their signatures (checked by the CPU tests)
-SYMBOLS = ["h2_build", "h2_import", "h2_export", "h2_mmp", "h2_mmp_batched", "h2_matvec", "h2_matvec_noalloc", "h2_to_dense", "h2_info",
+SYMBOLS = ["h2_build", "h2_import", "h2_import_complex", "h2_export", "h2_mmp", "h2_mmp_batched", "h2_matvec", "h2_matvec_noalloc", "h2_to_dense", "h2_info",
            "h2_tree_perm", "h2_level_blocks", "h2_trace_enable", "h2_trace_read", "h2_trace_flops", "h2_trace_phase", "h2_destroy",
            "h2_last_error", "h2_kernel_launches", "h2_plan_selfcheck", "h2_set_alloc_limit", "h2_plan_stats"]
 
@@ -48,7 +48,8 @@ class Stats(C.Structure):
     _fields_ = [("n", C.c_int64), ("levels", C.c_int32), ("leaf_size", C.c_int32), ("l_min", C.c_int32),
                 ("csp", C.c_int32), ("n_admissible", C.c_int64), ("n_dense", C.c_int64),
                 ("max_rank_row", C.c_int32 * 32), ("max_rank_col", C.c_int32 * 32), ("bytes_stored", C.c_int64),
-                ("device_bytes", C.c_int64), ("cap_hits", C.c_int64), ("mmp_ms", C.c_double)]
+                ("device_bytes", C.c_int64), ("cap_hits", C.c_int64), ("mmp_ms", C.c_double),
+                ("is_complex", C.c_int32), ("reserved", C.c_int32)]
 
 
 _lib = None
@@ -65,6 +66,7 @@ def load(path: str = LIB_PATH):
     P, I32, I64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_double
     lib.h2_build.argtypes = [P, I64, C.POINTER(Kernel), I32, D, D, C.POINTER(Opts), C.POINTER(P)]
     lib.h2_import.argtypes = [P, I64, I32, D, P, P, P, P, P, P, P, P, C.POINTER(Opts), C.POINTER(P)]
+    lib.h2_import_complex.argtypes = [P, I64, I32, D, P, P, P, P, P, P, P, P, C.POINTER(Opts), C.POINTER(P)]
     lib.h2_export.argtypes = [P, P, P, P, P, P, P, P, P, P]
     lib.h2_mmp.argtypes = [P, P, D, C.POINTER(Opts), C.POINTER(P)]
     lib.h2_mmp_batched.argtypes = [P, P, I32, D, C.POINTER(Opts), P]
@@ -132,11 +134,17 @@ class Packed:
 
 
 class H2Matrix:
-    """Owning wrapper of an h2_handle."""
+    """Owning wrapper of an h2_handle (complex: the Helmholtz kernel or h2_import_complex)."""
 
-    def __init__(self, handle: int, n: int):
+    def __init__(self, handle: int, n: int, is_complex: bool = False):
         self.handle = C.c_void_p(handle)
         self.n = n
+        self.is_complex = is_complex
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.complex128 if self.is_complex else torch.float64
 
     def __del__(self):
         self.destroy()
@@ -154,11 +162,17 @@ class H2Matrix:
         _check(load().h2_mmp(self.handle, other.handle, float(eps), C.byref(o), C.byref(h)))
         if out is not None and h.value == out.handle.value:
             return out
-        return H2Matrix(h.value, self.n)
+        return H2Matrix(h.value, self.n, self.is_complex)
 
     def matvec(self, x, y=None):
-        """y = H x for torch CUDA float64 x of shape (n,) or (n, nrhs) (h2_matvec)."""
+        """y = H x for a torch CUDA float64 (complex handles: complex128) x of shape (n,)
+        or (n, nrhs) (h2_matvec)."""
         import torch
+        if x.dtype != self.dtype:
+            if self.is_complex:
+                x = x.to(torch.complex128)
+            else:
+                raise TypeError("a real H^2 matrix multiplies float64 vectors")
         squeeze = x.dim() == 1
         X = x.reshape(self.n, -1)
         nrhs = X.shape[1]
@@ -188,7 +202,7 @@ class H2Matrix:
 
     def to_dense(self):
         import torch
-        out = torch.empty((self.n, self.n), dtype=torch.float64, device="cuda")
+        out = torch.empty((self.n, self.n), dtype=self.dtype, device="cuda")
         _check(load().h2_to_dense(self.handle, C.c_void_p(out.data_ptr())))
         return out.t()                   # column-major buffer -> row-major view
 
@@ -200,7 +214,7 @@ class H2Matrix:
                 "n_admissible": s.n_admissible, "n_dense": s.n_dense,
                 "max_rank_row": list(s.max_rank_row[:L]), "max_rank_col": list(s.max_rank_col[:L]),
                 "bytes_stored": s.bytes_stored, "device_bytes": s.device_bytes, "cap_hits": s.cap_hits,
-                "mmp_ms": s.mmp_ms}
+                "mmp_ms": s.mmp_ms, "is_complex": bool(s.is_complex)}
 
     def export(self) -> Packed:
         lib = load()
@@ -208,7 +222,8 @@ class H2Matrix:
         _check(lib.h2_export(self.handle, _ptr(sizes), None, None, None, None, None, None, None, None))
         kr = np.zeros(sizes[0], np.int32)
         kc = np.zeros(sizes[0], np.int32)
-        arrs = [np.zeros(sizes[i], np.float64) for i in range(1, 7)]
+        dt = np.complex128 if self.is_complex else np.float64
+        arrs = [np.zeros(sizes[i], dt) for i in range(1, 7)]
         _check(lib.h2_export(self.handle, _ptr(sizes), _ptr(kr), _ptr(kc), *[_ptr(a) for a in arrs]))
         return Packed(kr, kc, *arrs)
 
@@ -298,7 +313,7 @@ def h2_mmp_batched(As, Bs, eps: float, precision: int = FP64, trunc="paper", ran
         if outs and hc[i] == outs[i].handle.value:
             res.append(outs[i])
         else:
-            res.append(H2Matrix(hc[i], As[i].n))
+            res.append(H2Matrix(hc[i], As[i].n, As[i].is_complex))
     return res
 
 
@@ -310,16 +325,23 @@ def h2_build(points: np.ndarray, spec, leaf_size: int = 32, eta: float = 1.0, ep
     h = C.c_void_p(0)
     _check(load().h2_build(_ptr(pts), pts.shape[0], C.byref(k), int(leaf_size), float(eta), float(eps),
                            C.byref(o), C.byref(h)))
-    return H2Matrix(h.value, pts.shape[0])
+    return H2Matrix(h.value, pts.shape[0], int(spec.kind) == 2)
 
 
 def h2_import(points: np.ndarray, leaf_size: int, eta: float, p: Packed, stream=None) -> H2Matrix:
+    """h2_import, or h2_import_complex when any array of p is complex (passed as
+    interleaved real and imaginary parts)."""
     pts = np.ascontiguousarray(points, dtype=np.float64)
-    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (p.vr, p.vc, p.er, p.ec, p.s, p.f)]
+    cplx = any(np.iscomplexobj(a) for a in (p.vr, p.vc, p.er, p.ec, p.s, p.f))
+    if cplx:
+        arrs = [np.ascontiguousarray(a, dtype=np.complex128).view(np.float64) for a in (p.vr, p.vc, p.er, p.ec, p.s, p.f)]
+    else:
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (p.vr, p.vc, p.er, p.ec, p.s, p.f)]
     kr = np.ascontiguousarray(p.kr, dtype=np.int32)
     kc = np.ascontiguousarray(p.kc, dtype=np.int32)
     o = make_opts(stream=stream)
     h = C.c_void_p(0)
-    _check(load().h2_import(_ptr(pts), pts.shape[0], int(leaf_size), float(eta), _ptr(kr), _ptr(kc),
-                            *[_ptr(a) for a in arrs], C.byref(o), C.byref(h)))
-    return H2Matrix(h.value, pts.shape[0])
+    fn = load().h2_import_complex if cplx else load().h2_import
+    _check(fn(_ptr(pts), pts.shape[0], int(leaf_size), float(eta), _ptr(kr), _ptr(kc),
+              *[_ptr(a) for a in arrs], C.byref(o), C.byref(h)))
+    return H2Matrix(h.value, pts.shape[0], cplx)

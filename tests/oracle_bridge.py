@@ -11,9 +11,11 @@ def pack(h):
     kr = np.array([h.kr[(l, t)] for l in range(L + 1) for t in range(1 << l)], dtype=np.int32)
     kc = np.array([h.kc[(l, t)] for l in range(L + 1) for t in range(1 << l)], dtype=np.int32)
 
+    dt = np.complex128 if np.issubdtype(h.dtype, np.complexfloating) else np.float64
+
     def cat(mats):
-        mats = [np.asarray(m, dtype=np.float64).ravel() for m in mats]
-        return np.concatenate(mats) if mats else np.zeros(0)
+        mats = [np.asarray(m, dtype=dt).ravel() for m in mats]
+        return np.concatenate(mats) if mats else np.zeros(0, dtype=dt)
 
     vr = cat(h.Vr[t] for t in range(1 << L))
     vc = cat(h.Vc[t] for t in range(1 << L))

@@ -435,3 +435,86 @@ def test_autotuned_products_equal_fixed_ones(lib, prec):
         e = c.export()
         for f in ("kr", "kc", "vr", "vc", "er", "ec", "s", "f"):
             np.testing.assert_array_equal(getattr(e, f), getattr(ref, f))
+
+
+# ---------------------------------------------------------------- complex kernels
+# The Helmholtz kernel exp(-j k r) / (4 pi r) (Sec. VI-B, scattering): complex matrices,
+# complex float64 products on the GPU against the complex128 oracle.
+ZCASES = {
+    # name: (points, leaf, eta, eps_h2 of A, eps_h2 of B, wavenumber)
+    "sphere_640": (lambda: inputs.fibonacci_sphere(640, 1.5), 20, 1.0, 1e-5, 1e-3, 2 * math.pi),
+    "sphere_2048_4lambda": (lambda: inputs.fibonacci_sphere(2048, 4.0), 64, 1.0, 1e-3, 1e-3, 2 * math.pi),
+}
+
+
+def zcase(name):
+    key = "z_" + name
+    if key not in _cache:
+        fac, leaf, eta, ea, eb, k = ZCASES[name]
+        pts = fac()
+        n = pts.shape[0]
+        h = math.sqrt(4 * math.pi * float(np.max(np.linalg.norm(pts, axis=1))) ** 2 / n)
+        spec = inputs.helmholtz_spec(h, k)
+        A = oh2.rotate_bases(oh2.build(pts, spec, leaf, eta, ea), seed=1)
+        B = oh2.rotate_bases(oh2.build(pts, spec, leaf, eta, eb), seed=2)
+        _cache[key] = (pts, leaf, eta, spec, A, B)
+    return _cache[key]
+
+
+@pytest.mark.parametrize("name", list(ZCASES))
+def test_complex_import_export_matvec_and_dense(lib, name):
+    import torch
+    pts, leaf, eta, spec, A, B = zcase(name)
+    p = pack(A)
+    g = lib.h2_import(pts, leaf, eta, p)
+    assert g.is_complex and g.info()["is_complex"]
+    e = g.export()
+    for f in ("kr", "kc", "vr", "vc", "er", "ec", "s", "f"):
+        np.testing.assert_array_equal(getattr(e, f), getattr(p, f))
+    x = inputs.standard_normal((pts.shape[0], 3), seed=2) + 1j * inputs.standard_normal((pts.shape[0], 3), seed=3)
+    y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert_entries_close(y, oh2.matvec(A, x), 1e-13)
+    assert_entries_close(g.to_dense().cpu().numpy(), oh2.to_dense(A), 1e-13)
+
+
+@pytest.mark.parametrize("name,mode,eps,norm", [("sphere_640", "full", 0.0, "fro"), ("sphere_640", "paper", 1e-3, "fro"),
+                                                ("sphere_640", "sv", 1e-3, "fro"), ("sphere_640", "paper", 1e-4, "spectral"),
+                                                ("sphere_2048_4lambda", "paper", 1e-3, "fro"),
+                                                ("sphere_2048_4lambda", "sv", 1e-2, "fro")])
+def test_complex_product_matches_oracle(lib, name, mode, eps, norm):
+    pts, leaf, eta, spec, A, B = zcase(name)
+    st = {}
+    C = ommp.mmp(A, B, eps, mode, stats=st, norm=norm)
+    ga = lib.h2_import(pts, leaf, eta, pack(A))
+    gb = lib.h2_import(pts, leaf, eta, pack(B))
+    gc = ga.mmp(gb, eps, trunc=mode, rank_cap=128 if mode == "full" else 96, norm=norm)
+    assert gc.is_complex and gc.info()["cap_hits"] == 0
+    ckr, ckc = ranks(C)
+    e = gc.export()
+    np.testing.assert_array_equal(e.kr, ckr)
+    np.testing.assert_array_equal(e.kc, ckc)
+    d_gpu = gc.to_dense().cpu().numpy()
+    assert_entries_close(d_gpu, oh2.to_dense(C), fp64_tol(eps, mode))
+    if mode == "full":
+        assert_entries_close(d_gpu, oh2.to_dense(A) @ oh2.to_dense(B))
+
+
+def test_complex_build_approximates_the_helmholtz_kernel(lib):
+    # h2_build with the Helmholtz kernel: the library's own complex construction
+    from oracle import kernels
+    import torch
+    pts = inputs.fibonacci_sphere(2048, 4.0)
+    spec = inputs.helmholtz_spec(math.sqrt(4 * math.pi * 16.0 / 2048), 2 * math.pi)
+    g = lib.h2_build(pts, spec, 64, 1.0, 1e-4)
+    assert g.is_complex
+    K = kernels.dense(spec, pts)
+    x = inputs.standard_normal((2048, 2), seed=4) + 1j * inputs.standard_normal((2048, 2), seed=5)
+    y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y, K @ x) < 1e-3
+    c = g.mmp(g, 1e-3)
+    y2 = c.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = g.matvec(g.matvec(torch.from_numpy(x).cuda())).cpu().numpy()
+    assert rel(y2, ref) < math.sqrt(1e-3)
+    with pytest.raises(lib.H2Error) as ei:
+        g.mmp(g, 1e-3, precision=lib.MIXED_FP32)
+    assert ei.value.code == lib.H2_EUNSUPPORTED
