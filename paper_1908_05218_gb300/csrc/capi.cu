@@ -638,8 +638,7 @@ void run_plan(const Plan& P, const ArenaSet& ar, const Arenas* d_ars, const MmpP
     } else {
       if (P.cplx)
         launch_zeig(P.d_eigs, L.first, L.count, d_ars, prm.eps, prm.trunc, prm.norm, L.aux, ar.eig_scratch, stream);
-      else if (is_mixed(prm.precision) && L.aux <= 96 && prm.norm == H2_NORM_FROBENIUS &&
-               (prm.trunc == H2_TRUNC_FULL || (prm.trunc == H2_TRUNC_SV ? prm.eps * prm.eps : prm.eps) >= 5e-5))
+      else if (is_mixed(prm.precision) && L.aux <= 96 && prm.norm == H2_NORM_FROBENIUS)
         launch_eig_mixed(P.d_eigs, L.first, L.count, d_ars, prm.eps, prm.trunc, L.aux, L.aux2, stream);
       else
         launch_eig(P.d_eigs, L.first, L.count, d_ars, prm.eps, prm.trunc, prm.norm, L.aux, ar.eig_scratch, stream);
@@ -687,9 +686,9 @@ h2_status h2_build(const double* points, int64_t n, const h2_kernel* kernel, int
     v.kr = p.kr.data();
     v.kc = p.kc.data();
     const std::vector<double>* a[6] = {&p.vr, &p.vc, &p.er, &p.ec, &p.s, &p.f};
-    for (int i = 0; i < 6; ++i) {
+    for (int i = 0; i < 6; ++i) {  // lengths in elements (a complex element is two doubles)
       v.arr[i] = a[i]->data();
-      v.len[i] = (int64_t)a[i]->size();
+      v.len[i] = (int64_t)a[i]->size() / (h->m.cplx ? 2 : 1);
     }
     unpack_view_to_device(v, h->m);
     finish_handle(h.get(), o);
