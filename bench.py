@@ -48,6 +48,15 @@ WORKLOADS = {
 TRAFFIC = {"kernel": "seg_gemm32_kernel", "src_sha256": "f1a0945e10978651f03c38579a689c66fc4383c89917323954e4858c2a12238c",
            "bytes_per_product": 38.557e9, "executed_flops_per_product": 325980932076.0}
 LEAF, ETA, EPS_H2 = 32, 1.0, 1e-4
+# the variable-rank complex case: Fibonacci-sphere points, radius 4 wavelengths, Helmholtz
+# kernel exp(-j k r) / (4 pi r) with k = 2 pi, leaf 64, eta 1, eps_trunc = eps_H2 = 1e-3,
+# C = A A in complex float64
+SPHERES = {
+    # name: (points, leaf, eps, description)
+    "sphere262k": (262144, 64, 1e-3, "N=262,144 points on a sphere of radius 4 wavelengths, Helmholtz kernel"),
+    "sphere16k": (16384, 64, 1e-3, "N=16,384 points on a sphere of radius 4 wavelengths, Helmholtz kernel"),
+    "sphere_sample": (4096, 64, 1e-3, "N=4,096 points on a sphere of radius 4 wavelengths, Helmholtz kernel"),
+}
 
 
 def _peaks():
@@ -135,17 +144,23 @@ def oracle_sample(steps: int, sample: str = "sample"):
     from oracle import h2 as oh2
     from oracle import mmp as ommp
     from paper_1908_05218_gb300 import inputs
-    nx, ny, ppc, eps, _ = WORKLOADS[sample]
-    wa = inputs.workload_cube_array(nx, ny, ppc)
-    wb = inputs.workload_cube_array(nx, ny, ppc, kernel="invr2")
-    A = oh2.build(wa.points, wa.kernel, LEAF, ETA, EPS_H2)
-    B = oh2.build(wb.points, wb.kernel, LEAF, ETA, EPS_H2)
+    if sample in SPHERES:
+        n, leaf, eps, _ = SPHERES[sample]
+        wa = inputs.workload_sphere(n)
+        A = oh2.build(wa.points, wa.kernel, leaf, ETA, eps)
+        B = A
+    else:
+        nx, ny, ppc, eps, _ = WORKLOADS[sample]
+        wa = inputs.workload_cube_array(nx, ny, ppc)
+        wb = inputs.workload_cube_array(nx, ny, ppc, kernel="invr2")
+        A = oh2.build(wa.points, wa.kernel, LEAF, ETA, EPS_H2)
+        B = oh2.build(wb.points, wb.kernel, LEAF, ETA, EPS_H2)
 
     def size(h):
         n = sum(v.size for v in h.Vr.values()) + sum(v.size for v in h.Vc.values())
         n += sum(v.size for v in h.Er.values()) + sum(v.size for v in h.Ec.values())
         n += sum(v.size for v in h.S.values()) + sum(v.size for v in h.Fb.values())
-        return 8 * n
+        return (16 if np.iscomplexobj(next(iter(h.Fb.values()))) else 8) * n
 
     times = []
     C = None
@@ -235,7 +250,8 @@ def batched_main(args):
 PRECISIONS = {"fp64": lambda lib: lib.FP64, "mixed": lambda lib: lib.MIXED_FP32,
               "tf32x3": lambda lib: lib.MIXED_TF32X3}
 DTYPES = {"fp64": "f64", "mixed": "f32+f64", "tf32x3": "tf32x3+f64"}
-KERNELS = {"fp64": "seg_gemm_kernel<double>", "mixed": "seg_gemm32_kernel", "tf32x3": "seg_mma_tf32x3_kernel"}
+KERNELS = {"fp64": "seg_gemm_kernel<double>", "mixed": "seg_gemm32_kernel", "tf32x3": "seg_mma_tf32x3_kernel",
+           "fp64c": "seg_zgemm_kernel"}
 
 
 def trace_summary(C):
@@ -270,7 +286,7 @@ def roofline(tr, precision):
     if precision == "tf32x3":
         peak = 0.5 * float(peaks["bf16_tflops"]) / 3.0
         bound, peak_note = "tensor", f"TF32 = half the dense BF16 peak ({src}), / 3 products per split pair"
-    elif precision == "fp64":
+    elif precision in ("fp64", "fp64c"):
         peak = 152 * 2 * 2 * clk_hz / 1e12
         bound, peak_note = "alu", "152 SMs x 2 float64 FMA per clock x 2 flops x max SM clock"
     else:
@@ -353,13 +369,85 @@ def end_to_end(lib, wa, wb, pa, pbk, eps, prec, trunc, nbytes):
             "d2h_bytes_per_step": int(d2h), "seconds": te, "steps": 1}
 
 
+def sphere_main(args):
+    """The variable-rank complex case (scattering, Sec. VI-B): C = A A for the Helmholtz
+    kernel on a sphere, complex float64 on the GPU, against the oracle's complex128
+    product on a 4,096-point sample of the same geometry (one core)."""
+    import torch
+
+    from paper_1908_05218_gb300 import h2 as lib
+    from paper_1908_05218_gb300 import inputs
+    cpu = None
+    if not args.no_cpu_baseline:
+        try:
+            cpu = reference_arm(argparse.Namespace(steps=1), "sphere_sample")
+        except Exception as e:  # reported, not fatal
+            cpu = {"error": str(e)[-300:]}
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    lib.load()
+    n, leaf, eps, desc = SPHERES[args.workload]
+    w = inputs.workload_sphere(n)
+    t0 = time.time()
+    A = lib.h2_build(w.points, w.kernel, leaf, ETA, eps)
+    build_s = time.time() - t0
+    stream = torch.cuda.current_stream()
+    t0 = time.time()
+    # (rank cap 128: ranks of the oscillatory kernel grow with the electrical size of the
+    # coarse clusters)
+    cap = 128
+    C = A.mmp(A, eps, precision=lib.FP64, rank_cap=cap)
+    torch.cuda.synchronize()
+    setup_s = time.time() - t0
+    for _ in range(args.warmup):
+        C = A.mmp(A, eps, precision=lib.FP64, rank_cap=cap, out=C)
+    A.trace_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with Clocks(0) as clk:
+        n0 = lib.kernel_launches()
+        e0.record(stream)
+        for _ in range(args.steps):
+            C = A.mmp(A, eps, precision=lib.FP64, rank_cap=cap, out=C)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        nk = lib.kernel_launches() - n0
+    ms = e0.elapsed_time(e1) / max(1, args.steps)
+    tr = trace_summary(C)
+    A.trace_enable(False)
+    ia, ic = A.info(), C.info()
+    nbytes = 2 * ia["bytes_stored"] + ic["bytes_stored"]
+    x = torch.from_numpy(inputs.standard_normal((n, 4), seed=1) + 1j * inputs.standard_normal((n, 4), seed=2)).cuda()
+    y_ref = A.matvec(A.matvec(x))
+    err = float(torch.linalg.norm(C.matvec(x) - y_ref) / torch.linalg.norm(y_ref))
+    cpu_line = None
+    if cpu and "t" in cpu:
+        cpu_line = {"value": cpu["bytes"] / cpu["t"] / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                    "sample": f"sphere of radius 4 wavelengths, N={cpu['n']}, one product A A, eps {eps}",
+                    "seconds": cpu["t"]}
+    elif cpu:
+        cpu_line = {"error": cpu.get("error")}
+    print(json.dumps({
+        "metric": "H2-MMP throughput, complex (bytes of A+A+C at actual ranks / product time)",
+        "value": nbytes / (ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": {"workload": f"{desc}: exp(-j k r)/(4 pi r), k = 2 pi; leaf {leaf}, eta {ETA}, "
+                               f"eps_trunc {eps} (paper rule), eps_H2 {eps}; rank cap {cap}; C = A A",
+                   "inputs": "A, C together exceed L2 (no flush needed)", "parallelism": "replicas"},
+        "mmp_s": ms * 1e-3, "rel_err_vs_exact_h2_matvecs": err, "ranks_C_max_row": ic["max_rank_row"],
+        "cap_hits": ic["cap_hits"], "bytes_alg": nbytes, "build_s": build_s, "first_product_s_incl_plan": setup_s,
+        "phase_ms": tr["phase_ms"], "phase_ms_by_name": tr["by_phase"], "eig_ms_by_level": tr["eig_by_level"],
+        "roofline": roofline(tr, "fp64c"), "cpu_baseline": cpu_line, "gpu_launches": int(nk),
+        "clocks": clk.summary()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cubes16x16", choices=list(WORKLOADS) + ["batched48"])
+    ap.add_argument("--workload", default="cubes16x16", choices=list(WORKLOADS) + ["batched48"] + list(SPHERES))
     ap.add_argument("--precision", default="mixed", choices=list(PRECISIONS))
     ap.add_argument("--trunc", default="paper", choices=["paper", "sv", "formatted"],
                     help="truncation rule; 'formatted' = fixed bases (the paper's comparison method)")
@@ -373,7 +461,8 @@ def main():
     args = ap.parse_args()
 
     if args.oracle_sample:
-        oracle_sample(args.steps, args.workload if args.workload.startswith("sample") else "sample")
+        oracle_sample(args.steps, args.workload if (args.workload.startswith("sample") or args.workload in SPHERES)
+                      else "sample")
         return
 
     rank = int(os.environ.get("RANK", "0"))
@@ -382,6 +471,11 @@ def main():
         if args.impl == "reference" or world > 1:
             raise SystemExit("batched48 runs on one GPU, own implementation only")
         batched_main(args)
+        return
+    if args.workload in SPHERES:
+        if args.impl == "reference" or world > 1:
+            raise SystemExit("the sphere workloads run on one GPU, own implementation only")
+        sphere_main(args)
         return
     nx, ny, ppc, eps, desc = WORKLOADS[args.workload]
     metric = "H2-MMP throughput (bytes of A+B+C at actual ranks / product time)"

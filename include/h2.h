@@ -152,6 +152,15 @@ h2_status h2_build(const double* points, int64_t n, const h2_kernel* kernel,
                    int32_t leaf_size, double eta, double eps, const h2_opts* opts,
                    h2_handle* out);
 
+/* The construction of h2_build on the host only (no GPU, no device memory): the packed
+ * arrays of h2_import (complex kernels: two doubles per element) for the points.  Pass
+ * NULL arrays to get the element counts in sizes[0..7] (as h2_export: ranks per array,
+ * vr, vc, er, ec, s, f, 0); each call runs the construction.  Errors as h2_build.  The
+ * paper has no counterpart: its inputs come from a cited construction method. */
+h2_status h2_build_packed(const double* points, int64_t n, const h2_kernel* kernel, int32_t leaf_size,
+                          double eta, double eps, int64_t* sizes, int32_t* kr, int32_t* kc, double* vr,
+                          double* vc, double* er, double* ec, double* s, double* f);
+
 /* Failure injection for tests: after n more device allocations (n >= 0) every further
  * one fails, and the call that needed it returns H2_ENOMEM with no partial result;
  * n < 0 lifts the limit (the default).  Process-wide; never fails.  The paper has no

@@ -23,6 +23,7 @@
 #include <cmath>
 #include <complex>
 #include <numeric>
+#include <type_traits>
 
 #include "internal.hpp"
 
@@ -30,7 +31,10 @@ namespace h2 {
 
 namespace {
 
-constexpr int kSamples = 24;
+// far-field points read per partner block: 24 suffice for the smooth real kernels; the
+// oscillatory Helmholtz kernel needs more (its far-field ranks grow with the electrical
+// size of the blocks)
+constexpr int kSamplesReal = 24, kSamplesComplex = 128;
 constexpr int kAllRows = 64;
 constexpr int kOver = 8;
 constexpr int kMaxRank = 64;
@@ -252,6 +256,7 @@ void build_typed(const Structure& st, const h2_kernel& kern, double eps, Packed&
     for (auto& b : st.blocks[l])
       if (b.kind == KR) partners[l][b.t].push_back(b.s);
   }
+  const int kSamples = std::is_same<T, double>::value ? kSamplesReal : kSamplesComplex;
   auto sample = [&](int lv, int32_t s, std::vector<int64_t>& cols) {
     int64_t s0 = st.start[lv][s], m = st.size[lv][s];
     if (m <= kSamples) {

@@ -696,6 +696,30 @@ h2_status h2_build(const double* points, int64_t n, const h2_kernel* kernel, int
   });
 }
 
+h2_status h2_build_packed(const double* points, int64_t n, const h2_kernel* kernel, int32_t leaf_size, double eta,
+                          double eps, int64_t* sizes, int32_t* kr, int32_t* kc, double* vr, double* vc, double* er,
+                          double* ec, double* s, double* f) {
+  if (!points || !kernel || !sizes) return fail(H2_EINVAL, "null argument");
+  return guarded([&] {
+    if (!(eps > 0) || !(eps < 1)) throw Error(H2_EINVAL, "eps must lie in (0, 1)");
+    if (kernel->kind != H2_K_LAPLACE && kernel->kind != H2_K_INV_R2 && kernel->kind != H2_K_HELMHOLTZ)
+      throw Error(H2_EINVAL, "unknown kernel kind");
+    auto st = build_structure(points, n, leaf_size, eta);
+    Packed p;
+    build_h2_host(*st, *kernel, eps, p);
+    const int w = kernel->kind == H2_K_HELMHOLTZ ? 2 : 1;
+    const std::vector<double>* a[6] = {&p.vr, &p.vc, &p.er, &p.ec, &p.s, &p.f};
+    sizes[0] = (int64_t)p.kr.size();
+    for (int i = 0; i < 6; ++i) sizes[1 + i] = (int64_t)a[i]->size() / w;
+    sizes[7] = 0;
+    if (kr) std::copy(p.kr.begin(), p.kr.end(), kr);
+    if (kc) std::copy(p.kc.begin(), p.kc.end(), kc);
+    double* out[6] = {vr, vc, er, ec, s, f};
+    for (int i = 0; i < 6; ++i)
+      if (out[i]) std::copy(a[i]->begin(), a[i]->end(), out[i]);
+  });
+}
+
 h2_status h2_set_alloc_limit(int64_t n) {
   g_alloc_left.store(n < 0 ? -1 : n);
   return H2_OK;

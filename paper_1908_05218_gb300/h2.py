@@ -26,7 +26,8 @@ _TRUNC = {"paper": TRUNC_PAPER, "sv": TRUNC_SV, "full": TRUNC_FULL, "formatted":
 # exported symbols and their signatures (checked by the CPU tests)
 SYMBOLS = ["h2_build", "h2_import", "h2_import_complex", "h2_export", "h2_mmp", "h2_mmp_batched", "h2_matvec", "h2_matvec_noalloc", "h2_to_dense", "h2_info",
            "h2_tree_perm", "h2_level_blocks", "h2_trace_enable", "h2_trace_read", "h2_trace_flops", "h2_trace_phase", "h2_destroy",
-           "h2_last_error", "h2_kernel_launches", "h2_plan_selfcheck", "h2_set_alloc_limit", "h2_plan_stats"]
+           "h2_last_error", "h2_kernel_launches", "h2_plan_selfcheck", "h2_set_alloc_limit", "h2_plan_stats",
+           "h2_build_packed"]
 
 
 class H2Error(RuntimeError):
@@ -83,6 +84,7 @@ def load(path: str = LIB_PATH):
     lib.h2_plan_selfcheck.argtypes = [P, I64, I32, C.c_double, C.c_double, P]
     lib.h2_set_alloc_limit.argtypes = [I64]
     lib.h2_plan_stats.argtypes = [P, I64, I32, D, D, I32, P, P, P]
+    lib.h2_build_packed.argtypes = [P, I64, C.POINTER(Kernel), I32, D, D, P, P, P, P, P, P, P, P, P]
     lib.h2_trace_phase.argtypes = [P, I32]
     lib.h2_trace_phase.restype = C.c_char_p
     lib.h2_destroy.argtypes = [P]
@@ -273,6 +275,24 @@ def plan_selfcheck(points: np.ndarray, leaf_size: int = 32, eta: float = 1.0, ep
     n = C.c_int32(0)
     _check(load().h2_plan_selfcheck(_ptr(pts), pts.shape[0], leaf_size, float(eta), float(eps), C.byref(n)))
     return int(n.value)
+
+
+def build_packed(points: np.ndarray, spec, leaf_size: int = 32, eta: float = 1.0, eps: float = 1e-4) -> Packed:
+    """The host construction of h2_build as packed arrays (no GPU; complex kernels give
+    complex128 arrays)."""
+    lib = load()
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    k = make_kernel(spec)
+    sizes = np.zeros(8, dtype=np.int64)
+    args = (_ptr(pts), pts.shape[0], C.byref(k), int(leaf_size), float(eta), float(eps))
+    _check(lib.h2_build_packed(*args, _ptr(sizes), None, None, None, None, None, None, None, None))
+    kr = np.zeros(sizes[0], np.int32)
+    kc = np.zeros(sizes[0], np.int32)
+    dt = np.complex128 if int(spec.kind) == 2 else np.float64
+    arrs = [np.zeros(max(1, sizes[i]), dt) for i in range(1, 7)]
+    ptrs = [a.view(np.float64).ctypes.data_as(C.c_void_p) for a in arrs]
+    _check(lib.h2_build_packed(*args, _ptr(sizes), _ptr(kr), _ptr(kc), *ptrs))
+    return Packed(kr, kc, *[a[:sizes[i + 1]] for i, a in enumerate(arrs)])
 
 
 def set_alloc_limit(n: int) -> None:
