@@ -41,12 +41,14 @@ WORKLOADS = {
     "sample": (2, 2, 3072, 1e-4, "N=12,288 panel centroids on a 2x2 array of unit cubes"),
     "sample_ref": (2, 2, 2048, 1e-4, "N=8,192 panel centroids on a 2x2 array of unit cubes"),
 }
-# DRAM traffic of the float32 GEMM kernel from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum over the GEMM launches of one product of the N=65,536
-# cube-array workload), valid only for the kernel source it was taken on.  Other
-# workloads scale it by the executed flops.
-TRAFFIC = {"kernel": "seg_gemm32_kernel", "src_sha256": "f1a0945e10978651f03c38579a689c66fc4383c89917323954e4858c2a12238c",
-           "bytes_per_product": 38.557e9, "executed_flops_per_product": 325980932076.0}
+# DRAM traffic of the float32 GEMM kernel (dram__bytes_read.sum + dram__bytes_write.sum)
+# from one ncu capture of three of its launches -- the leaf-level projections, R images
+# and couplings of the N=65,536 cube-array product, 4.610 GB over 1.2807e11 padded flops
+# (2 m n k at the padded dims of their segments) -- valid only for the kernel source it
+# was taken on (the hash of seg_gemm32_kernel's text).  A run's traffic per GEMM launch
+# is that ratio times its own padded flops per GEMM launch.
+TRAFFIC = {"kernel": "seg_gemm32_kernel", "src_sha256": "fcaf5b47a52cf177a2dd6d4fd6dc897efa6427657cc844ef960069a869ccec44",
+           "bytes": 4610484992.0, "padded_flops": 1.28074e11}
 LEAF, ETA, EPS_H2 = 32, 1.0, 1e-4
 # the variable-rank complex case: Fibonacci-sphere points, radius 4 wavelengths, Helmholtz
 # kernel exp(-j k r) / (4 pi r) with k = 2 pi, leaf 64, eta 1, eps_trunc = eps_H2 = 1e-3,
@@ -299,13 +301,15 @@ def roofline(tr, precision):
     traffic = None
     if precision == "mixed" and tot.get("gemm", [0, 0, 0])[2]:
         import hashlib
-        with open(os.path.join(ROOT, "paper_1908_05218_gb300", "csrc", "kernels.cu"), "rb") as f:
-            if hashlib.sha256(f.read()).hexdigest() == TRAFFIC["src_sha256"]:
-                traffic = (TRAFFIC["bytes_per_product"] * fl / TRAFFIC["executed_flops_per_product"]
-                           / tot["gemm"][2])
+        src = open(os.path.join(ROOT, "paper_1908_05218_gb300", "csrc", "kernels.cu")).read()
+        a = src.find("// ------------------------------------------------------------ segmented GEMM, float32")
+        b = src.find("template <typename Acc>\nstatic void gemm_launch(")
+        if a >= 0 and b > a and hashlib.sha256(src[a:b].encode()).hexdigest() == TRAFFIC["src_sha256"]:
+            traffic = TRAFFIC["bytes"] / TRAFFIC["padded_flops"] * tot["gemm"][1] / tot["gemm"][2]
     return {"bound": bound, "kernel": KERNELS[precision], "dominant": dom, "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": traffic,
-            "traffic_note": ("DRAM bytes per GEMM launch: ncu capture at N=65,536 scaled by executed flops"
+            "traffic_note": ("DRAM bytes per GEMM launch: bytes per padded flop of three captured launches "
+                             "(N=65,536) x this run's padded flops per GEMM launch"
                              if traffic else "no DRAM capture of this kernel source at this precision"),
             "peak_note": peak_note, "launches_per_step": tot.get("gemm", [0, 0, 0])[2], "ms_per_step": gemm_ms,
             "executed_flops_per_step": fl,

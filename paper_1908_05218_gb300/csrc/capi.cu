@@ -629,19 +629,23 @@ void run_plan(const Plan& P, const ArenaSet& ar, const Arenas* d_ars, const MmpP
       if (P.cplx)
         launch_zgemm(P.d_segs, P.d_items, L.first, L.count, d_ars, L.aux, stream);
       else if (prm.precision == H2_MIXED_TF32X3)
-        launch_gemm_mma(P.d_segs, P.d_items, L.first, L.count, d_ars, L.aux2, L.aux, ar.err, mma_ctas_per_sm(v),
+        launch_gemm_mma(P.d_segs, P.d_items, L.first, L.count, d_ars, L.aux2, L.aux, ar.err, v % kMmaVariants,
                         stream);
       else
         launch_gemm(P.d_segs, P.d_items, L.first, L.count, d_ars, L.aux, L.aux2, is_mixed(prm.precision),
-                    stream, v);
+                    stream, v % kGemmVariants);
       if (tune_ev) cuda_check(cudaEventRecord((cudaEvent_t)tune_ev[2 * li + 1], (cudaStream_t)stream), "event");
     } else {
-      if (P.cplx)
+      const int v = choice ? choice[li] : 0;
+      if (P.cplx) {
         launch_zeig(P.d_eigs, L.first, L.count, d_ars, prm.eps, prm.trunc, prm.norm, L.aux, ar.eig_scratch, stream);
-      else if (is_mixed(prm.precision) && L.aux <= 96 && prm.norm == H2_NORM_FROBENIUS)
-        launch_eig_mixed(P.d_eigs, L.first, L.count, d_ars, prm.eps, prm.trunc, L.aux, L.aux2, stream);
-      else
+      } else if (eig_kept_path(prm, L)) {
+        if (tune_ev) cuda_check(cudaEventRecord((cudaEvent_t)tune_ev[2 * li], (cudaStream_t)stream), "event");
+        launch_eig_mixed(P.d_eigs, L.first, L.count, d_ars, prm.eps, prm.trunc, L.aux, v % kEigVariants, stream);
+        if (tune_ev) cuda_check(cudaEventRecord((cudaEvent_t)tune_ev[2 * li + 1], (cudaStream_t)stream), "event");
+      } else {
         launch_eig(P.d_eigs, L.first, L.count, d_ars, prm.eps, prm.trunc, prm.norm, L.aux, ar.eig_scratch, stream);
+      }
     }
     cuda_check(cudaGetLastError(), L.phase);
     if (tr) cuda_check(cudaEventRecord((cudaEvent_t)tr->ev[2 * li + 1], (cudaStream_t)stream), "event");
@@ -1094,11 +1098,15 @@ h2_status h2_mmp(h2_handle A, h2_handle B, double eps, const h2_opts* opts, h2_h
       const Plan& P = pr.ent->plan;
       const size_t nl = P.launches.size();
       if (ts.choice.empty()) {
-        ts.ncand = o.precision == H2_MIXED_TF32X3 ? kMmaVariants : kGemmVariants;
+        // candidates: every launch kind's variants, taken modulo its own count
+        ts.ncand = kTuneCandidates;
         ts.choice.assign(nl, 0);
         ts.ms.assign(nl, std::vector<float>(ts.ncand, -1.f));
-        for (size_t li = 0; li < nl; ++li)
-          if (P.launches[li].kind == Launch::GEMM) ts.choice[li] = -1;
+        for (size_t li = 0; li < nl; ++li) {
+          const Launch& L = P.launches[li];
+          if ((L.kind == Launch::GEMM && !P.cplx) || (L.kind == Launch::EIG && !P.cplx && eig_kept_path(pr.prm, L)))
+            ts.choice[li] = -1;
+        }
         for (size_t i = 0; i < 2 * nl + 1; ++i) {  // two per launch and an end marker
           cudaEvent_t e;
           cuda_check(cudaEventCreate(&e), "event");

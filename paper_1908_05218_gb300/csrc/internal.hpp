@@ -206,6 +206,10 @@ struct MmpParams {
 };
 // float32 operands and work regions (every precision but H2_FP64)
 inline bool is_mixed(int precision) { return precision != H2_FP64; }
+// the eigen launches of the mixed product that take the kept-columns kernel (launch_eig_mixed)
+inline bool eig_kept_path(const MmpParams& p, const Launch& L) {
+  return is_mixed(p.precision) && L.aux <= 96 && p.norm == H2_NORM_FROBENIUS;
+}
 
 // Builds the plan of C = A B; sets C's caps (C must share A's structure).
 void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& p, Plan& plan);
@@ -261,12 +265,12 @@ void launch_gemm(const Seg* d_segs, const Item* d_items, int64_t first, int64_t 
                  int maxn, int maxdim, bool fp32, void* stream, int variant = 0);
 // launch configurations the autotuner tries per GEMM launch group: CUDA-core kernels
 // {column slices per CTA, whole segment per CTA}, tensor-core kernel {4, 2, 1} CTAs per SM
-constexpr int kGemmVariants = 2, kMmaVariants = 3;
-inline int mma_ctas_per_sm(int variant) { return variant == 1 ? 2 : (variant == 2 ? 1 : 4); }
+constexpr int kGemmVariants = 2, kMmaVariants = 3, kEigVariants = 3, kTuneCandidates = 3;
 // the same segments on the tensor cores, 3xTF32 split products (mma.cu); maxm / maxn bound
-// the segments' padded dims; err receives 1 if a bounded wait gave up
+// the segments' padded dims; err receives 1 if a bounded wait gave up; variant: launch
+// configuration (k per stage, CTAs per SM; results identical for all)
 void launch_gemm_mma(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const Arenas* d_ars,
-                     int maxm, int maxn, unsigned int* err, int ctas_per_sm, void* stream);
+                     int maxm, int maxn, unsigned int* err, int variant, void* stream);
 void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, const Arenas* d_ars, double eps, int trunc,
                 int norm, int max_npad, double* scratch, void* stream);
 // formatted product: C's ranks are A's row ranks and B's column ranks (instance inst)
@@ -275,8 +279,9 @@ unsigned long long kernel_launches();  // kernels launched by this library so fa
 void add_kernel_launches(long long d);
 void init_kernel_attributes();  // once per process, before launches or captures   // graph replays add their kernels; captures take theirs back
 void launch_to_f32(const double* src, float* dst, int64_t n, void* stream);
+// variant: which size tiers run on 128 threads instead of 256 (results identical for all)
 void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const Arenas* d_ars, double eps,
-                      int trunc, int max_npad, int max_klim, void* stream);
+                      int trunc, int max_npad, int variant, void* stream);
 void launch_permute(const double* src, double* dst, const int64_t* user, int64_t rows, int64_t n,
                     int64_t nrhs, bool to_tree, void* stream);
 void launch_identity(double* out, int64_t n, void* stream);

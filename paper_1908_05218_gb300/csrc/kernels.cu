@@ -1030,32 +1030,38 @@ __global__ void __launch_bounds__(256) eig_mixed_kernel(const EigTask* __restric
 //       kept).  One step rotates rows and columns together: a thread takes the 2 x 2
 //       block (pair k, pair l), k <= l, of A, forms M_k X M_l^T and writes the block and
 //       its mirror image; eigenvectors are the ROWS of Vt, so their update is a float4
-//       row rotation.  Rotations with |a_pq| <= 2^-24 sqrt(|a_pp a_qq|) are skipped
-//       (below float32 resolution of their 2 x 2 problem; together they keep off(A)^2 far
-//       below the 1e-10 stop);
+//       row rotation.  The (k, l) and (pair, row piece) tasks of a step are read from
+//       tables built once per CTA.  Rotations with |a_pq| <= 2^-24 sqrt(|a_pp a_qq|) are
+//       skipped (below float32 resolution of their 2 x 2 problem; together they keep
+//       off(A)^2 far below the 1e-10 stop);
 //   (2) a_jj is v_j^T G v_j to float32 accuracy: the columns with a_jj above a
 //       quarter of the threshold are the only ones whose quotient can pass it, and for
 //       the decisive ones (the top cluster and those within 2e-5 lambda_1 of the
 //       threshold) the float64 Rayleigh quotient v^T G v / v^T v is formed, G read from
 //       the Gram matrices in global memory; these decide the rank (sorted decreasing,
 //       ties by index);
-//   (3) the kept columns go to float64 and one Newton-Schulz step on those columns,
-//       V <- V (3 I - V^T V) / 2, makes them orthonormal to ~1e-14.
+//   (3) the kept columns go to float64, in place in the output (rows act[a]), and one
+//       Newton-Schulz step on those columns, V <- V (3 I - V^T V) / 2, makes them
+//       orthonormal to the square of their float32 error.
+// Every sum whose rounding could change a decision (the norms of the Gram matrices, the
+// stopping sums) is taken over 128 fixed partial sums, so the result does not depend on
+// the block size (128 or 256 threads: a launch parameter).
 // Float64 work: n^2 per decisive candidate plus 2 n r^2, against 3 n^3 in eig_mixed_kernel.
-// Shared memory (kk = the launch's largest rank limit, at most nn): buffer 1 holds A
-// (float32, nn x (nn+1)) and later the kept columns (float64, nn x (kk+1)); buffer 2
-// holds Vt (float32, nn x (nn+4)) and later the Newton-Schulz matrix (float64, kk x (kk+1)).
+// Shared memory: buffer 1 holds A (float32, nn x (nn+1)) and later the Newton-Schulz
+// matrix (float64, packed lower triangle); buffer 2 holds Vt (float32, nn x (nn+4)) and
+// later a few new rows of the kept columns; then the step's task tables.
 constexpr int kKeptRows = 4;
+constexpr int kFixedParts = 128;
 
 __host__ __device__ inline int round4(int n) { return (n + 3) & ~3; }
 
-__host__ __device__ inline size_t eig_kept_buf1(int nn, int kk) {
-  const size_t a = (size_t)nn * (nn + 1) * sizeof(float), v = (size_t)nn * (kk + 1) * sizeof(double);
-  return ((a > v ? a : v) + 15) & ~(size_t)15;
-}
-__host__ __device__ inline size_t eig_kept_smem(int nn, int kk) {
-  const size_t t = (size_t)nn * (nn + 4) * sizeof(float), w = (size_t)kk * (kk + 1) * sizeof(double);
-  return eig_kept_buf1(nn, kk) + (t > w ? t : w);
+__host__ __device__ inline size_t eig_kept_buf1(int nn) { return ((size_t)nn * (nn + 1) * sizeof(float) + 15) & ~(size_t)15; }
+__host__ __device__ inline size_t eig_kept_buf2(int nn) { return (size_t)nn * (nn + 4) * sizeof(float); }
+__host__ __device__ inline int eig_kept_nblk(int nn) { return (nn / 4) * (nn / 2 + 1); }
+__host__ __device__ inline int eig_kept_nvt(int nn) { return (nn / 2) * (nn / 4); }
+__host__ __device__ inline size_t eig_kept_smem(int nn) {
+  return eig_kept_buf1(nn) + eig_kept_buf2(nn) +
+         (((size_t)(eig_kept_nblk(nn) + eig_kept_nvt(nn)) * sizeof(uint16_t) + 15) & ~(size_t)15);
 }
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -1063,18 +1069,32 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+// the sum of parts[0 .. kFixedParts) in a fixed order, returned to every thread
+__device__ double fixed_total(const double* parts, double* bc) {
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double r = 0.0;
+    for (int u = threadIdx.x; u < kFixedParts; u += 32) r += parts[u];
+    r = warp_sum_d(r);
+    if (threadIdx.x == 0) *bc = r;
+  }
+  __syncthreads();
+  return *bc;
+}
+
 __global__ void __launch_bounds__(256) eig_mixed_kept_kernel(const EigTask* __restrict__ tasks, int64_t first,
                                                              const Arenas* __restrict__ ars, double eps, int trunc,
-                                                             int nn_lo, int nn_hi, int kk_max) {
+                                                             int nn_lo, int nn_hi) {
   extern __shared__ __align__(16) unsigned char esm[];
   __shared__ int act[kMixMax + 4];
-  __shared__ double red[8];
-  __shared__ float cs[kMixMax / 2], sn[kMixMax / 2];
-  __shared__ int pp[kMixMax / 2], qq[kMixMax / 2];
+  __shared__ double parts[kFixedParts];
+  __shared__ float2 parts2[kFixedParts];
+  __shared__ double s_bc;
+  __shared__ float2 csn[kMixMax / 2];  // (c, s) of pair k
+  __shared__ int pq[kMixMax / 2];      // p | q << 16 of pair k
   __shared__ int cand[kMixMax], order[kMixMax];
   __shared__ double rq[kMixMax], rqs[kMixMax];
   __shared__ float lam32[kMixMax];
-  __shared__ double rowbuf[kKeptRows * kMixMax];
   __shared__ double s_inv[3];
   __shared__ int s_n, s_nc, s_rank;
   const EigTask t = tasks[first + blockIdx.x];
@@ -1100,20 +1120,40 @@ __global__ void __launch_bounds__(256) eig_mixed_kept_kernel(const EigTask* __re
   // one launch per size tier (nn_lo, nn_hi], shared memory sized for nn_hi: a task
   // whose actual size is outside the tier is done by another launch
   if (nn <= nn_lo || nn > nn_hi) return;
-  const int kk = min(kk_max, nn_hi);
-  float* A = (float*)esm;                                   // row stride la (buffer 1)
-  float* Vt = (float*)(esm + eig_kept_buf1(nn_hi, kk));     // row stride lv; 16-byte aligned rows (buffer 2)
+  float* A = (float*)esm;                                  // row stride la (buffer 1)
+  float* Vt = (float*)(esm + eig_kept_buf1(nn_hi));        // row stride lv; 16-byte aligned rows (buffer 2)
+  uint16_t* blk = (uint16_t*)(esm + eig_kept_buf1(nn_hi) + eig_kept_buf2(nn_hi));
+  const int half = np / 2, nq = nn / 4, nblk = half * (np + 1), nvt = np * nq;
+  uint16_t* vtk = blk + nblk;
+  // step tasks: the triangle k <= l of 2 x 2 blocks folded into half x (np + 1), as
+  // k | l << 8; the Vt row pieces as pair | piece << 8
+  for (int e = tid; e < nblk; e += nt) {
+    const int r = e / (np + 1), cc = e - r * (np + 1);
+    int k, l;
+    if (cc < np - r) {
+      k = r;
+      l = r + cc;
+    } else {
+      k = np - 1 - r;
+      l = k + cc - (np - r);
+    }
+    blk[e] = (uint16_t)(k | (l << 8));
+  }
+  for (int e = tid; e < nvt; e += nt) vtk[e] = (uint16_t)((e / nq) | ((e % nq) << 8));
   // scale of each Gram matrix: 1 / ||G_m||_F (0: absent or zero, left out of the sum)
   for (int m = 0; m < 3; ++m) {
-    double loc = 0.0;
-    if (t.g[m] >= 0) {
-      const View Gm = view(ar, t.g[m]);
-      for (int e = tid; e < n * n; e += nt) {
-        const double v = ld<double>(Gm, (int64_t)act[e / n] * t.n_pad + act[e % n]);
-        loc += v * v;
+    for (int v = tid; v < kFixedParts; v += nt) {
+      double loc = 0.0;
+      if (t.g[m] >= 0) {
+        const View Gm = view(ar, t.g[m]);
+        for (int e = v; e < n * n; e += kFixedParts) {
+          const double x = ld<double>(Gm, (int64_t)act[e / n] * t.n_pad + act[e % n]);
+          loc += x * x;
+        }
       }
+      parts[v] = loc;
     }
-    const double nrm2 = block_sum(loc, red);
+    const double nrm2 = fixed_total(parts, &s_bc);
     if (tid == 0) s_inv[m] = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0;
   }
   __syncthreads();
@@ -1138,23 +1178,42 @@ __global__ void __launch_bounds__(256) eig_mixed_kept_kernel(const EigTask* __re
   }
   __syncthreads();
   // (1) float32 Jacobi, stop when off(A)^2 <= 1e-10 |A|^2 (as eig_mixed_kernel)
-  const int half = np / 2, nq = nn / 4;
   for (int sweep = 0; sweep < 12 && n > 1; ++sweep) {
     // (sums of squares in float32: they only decide a stop at a 1e-10 ratio)
-    float offf = 0.f, totf = 0.f;
-    for (int e = tid; e < nn * nn; e += nt) {
-      const int i = e / nn, j = e - i * nn;
-      const float v = A[i * la + j] * A[i * la + j];
-      totf += v;
-      if (i != j) offf += v;
+    for (int v = tid; v < kFixedParts; v += nt) {
+      float offf = 0.f, totf = 0.f;
+      for (int e = v; e < nn * nn; e += kFixedParts) {
+        const int i = e / nn, j = e - i * nn;
+        const float x = A[i * la + j] * A[i * la + j];
+        totf += x;
+        if (i != j) offf += x;
+      }
+      parts2[v] = make_float2(offf, totf);
     }
-    const double off = block_sum((double)offf, red);
-    const double tot = block_sum((double)totf, red);
-    if (!(off > 1e-10 * tot)) break;
+    __syncthreads();
+    if (tid < 32) {
+      double o = 0.0, tt = 0.0;
+      for (int u = tid; u < kFixedParts; u += 32) {
+        o += (double)parts2[u].x;
+        tt += (double)parts2[u].y;
+      }
+      o = warp_sum_d(o);
+      tt = warp_sum_d(tt);
+      if (tid == 0) s_bc = (o > 1e-10 * tt) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    if (!(s_bc > 0.0)) break;
     for (int step = 0; step < nn - 1; ++step) {
       if (tid < np) {
-        const int pa = (tid == 0) ? 0 : ((tid - 1 + step) % (nn - 1)) + 1;
-        const int pb = ((nn - 2 - tid + step) % (nn - 1)) + 1;
+        int pa = 0;
+        if (tid > 0) {
+          pa = tid - 1 + step;
+          if (pa >= nn - 1) pa -= nn - 1;
+          pa += 1;
+        }
+        int pb = nn - 2 - tid + step;
+        if (pb >= nn - 1) pb -= nn - 1;
+        pb += 1;
         const int p = min(pa, pb), q = max(pa, pb);
         const float apq = A[p * la + q], app = A[p * la + p], aqq = A[q * la + q];
         float c = 1.f, s = 0.f;
@@ -1164,27 +1223,18 @@ __global__ void __launch_bounds__(256) eig_mixed_kept_kernel(const EigTask* __re
           c = 1.f / sqrtf(1.f + tt * tt);
           s = tt * c;
         }
-        pp[tid] = p;
-        qq[tid] = q;
-        cs[tid] = c;
-        sn[tid] = s;
+        pq[tid] = p | (q << 16);
+        csn[tid] = make_float2(c, s);
       }
       __syncthreads();
-      // A <- M A M^T by 2 x 2 blocks; the triangle k <= l is folded into half x (np + 1)
-      for (int e = tid; e < half * (np + 1); e += nt) {
-        const int r = e / (np + 1), cc = e - r * (np + 1);
-        int k, l;
-        if (cc < np - r) {
-          k = r;
-          l = r + cc;
-        } else {
-          k = np - 1 - r;
-          l = k + cc - (np - r);
-        }
-        const float sk = sn[k], sl = sn[l];
-        if (sk == 0.f && sl == 0.f) continue;
-        const float ck = cs[k], cl = cs[l];
-        const int pk = pp[k], qk = qq[k], pl = pp[l], ql = qq[l];
+      // A <- M A M^T by 2 x 2 blocks (k, l), k <= l, and their mirror images
+      for (int e = tid; e < nblk; e += nt) {
+        const int kl = blk[e], k = kl & 255, l = kl >> 8;
+        const float2 rk = csn[k], rl = csn[l];
+        if (rk.y == 0.f && rl.y == 0.f) continue;
+        const float ck = rk.x, sk = rk.y, cl = rl.x, sl = rl.y;
+        const int pqk = pq[k], pql = pq[l];
+        const int pk = pqk & 0xffff, qk = pqk >> 16, pl = pql & 0xffff, ql = pql >> 16;
         const float x = A[pk * la + pl], y = A[pk * la + ql], z = A[qk * la + pl], u = A[qk * la + ql];
         const float r00 = ck * x - sk * z, r01 = ck * y - sk * u;  // rows: M_k X
         const float r10 = sk * x + ck * z, r11 = sk * y + ck * u;
@@ -1207,13 +1257,15 @@ __global__ void __launch_bounds__(256) eig_mixed_kept_kernel(const EigTask* __re
         }
       }
       // Vt <- M Vt (rows p, q of each pair)
-      for (int e = tid; e < np * nq; e += nt) {
-        const int k = e / nq, j = (e - k * nq) * 4;
-        const float s = sn[k];
+      for (int e = tid; e < nvt; e += nt) {
+        const int kj = vtk[e], k = kj & 255, j = (kj >> 8) * 4;
+        const float2 r = csn[k];
+        const float s = r.y;
         if (s == 0.f) continue;
-        const float c = cs[k];
-        float4* rp = reinterpret_cast<float4*>(Vt + pp[k] * lv + j);
-        float4* rr = reinterpret_cast<float4*>(Vt + qq[k] * lv + j);
+        const float c = r.x;
+        const int pqk = pq[k];
+        float4* rp = reinterpret_cast<float4*>(Vt + (pqk & 0xffff) * lv + j);
+        float4* rr = reinterpret_cast<float4*>(Vt + (pqk >> 16) * lv + j);
         const float4 x = *rp, y = *rr;
         *rp = make_float4(c * x.x - s * y.x, c * x.y - s * y.y, c * x.z - s * y.z, c * x.w - s * y.w);
         *rr = make_float4(s * x.x + c * y.x, s * x.y + c * y.y, s * x.z + c * y.z, s * x.w + c * y.w);
@@ -1299,71 +1351,84 @@ __global__ void __launch_bounds__(256) eig_mixed_kept_kernel(const EigTask* __re
     ranks[t.rank_out] = r;
   }
   __syncthreads();
-  // (3) kept columns in float64 (buffer 1), one Newton-Schulz step on them (its matrix
-  // in buffer 2 once Vt has been read)
-  const int rank = s_rank, lk = rank + 1;
-  double* Vk = reinterpret_cast<double*>(esm);
+  // (3) kept columns in float64 in the output (the new bases are float64, arena C): row
+  // act[a] holds v_a; everything else is zero
+  const int rank = s_rank;
+  double* out = (double*)view(ar, t.out).base;
+  float* out32 = ar->p[AR_X] ? (float*)ar->p[AR_X] + (t.out & kOffMask) : nullptr;
+  const int ko = t.kcap;
+  for (int e = tid; e < t.n_pad * ko; e += nt) out[e] = 0.0;
+  __syncthreads();
   for (int e = tid; e < n * rank; e += nt) {
     const int a = e / rank, c = e - a * rank;
-    Vk[a * lk + c] = (double)Vt[order[c] * lv + a];
+    out[(int64_t)act[a] * ko + c] = (double)Vt[order[c] * lv + a];
   }
   __syncthreads();
   if (rank > 0) {
-    double* T = reinterpret_cast<double*>(Vt);
-    const int lt = rank + 1;
+    // the Newton-Schulz matrix (3 I - V^T V) / 2, symmetric: lower triangle, packed, in
+    // buffer 1 (A is no longer read)
+    double* T = reinterpret_cast<double*>(esm);
     for (int e = tid; e < rank * rank; e += nt) {
       const int i = e / rank, j = e - i * rank;
+      if (j > i) continue;
       double a0 = 0.0, a1 = 0.0;
       int a = 0;
       for (; a + 1 < n; a += 2) {
-        a0 = fma(Vk[a * lk + i], Vk[a * lk + j], a0);
-        a1 = fma(Vk[(a + 1) * lk + i], Vk[(a + 1) * lk + j], a1);
+        const double* r0 = out + (int64_t)act[a] * ko;
+        const double* r1 = out + (int64_t)act[a + 1] * ko;
+        a0 = fma(r0[i], r0[j], a0);
+        a1 = fma(r1[i], r1[j], a1);
       }
-      if (a < n) a0 = fma(Vk[a * lk + i], Vk[a * lk + j], a0);
-      T[i * lt + j] = (i == j ? 1.5 : 0.0) - 0.5 * (a0 + a1);
+      if (a < n) {
+        const double* r0 = out + (int64_t)act[a] * ko;
+        a0 = fma(r0[i], r0[j], a0);
+      }
+      T[i * (i + 1) / 2 + j] = (i == j ? 1.5 : 0.0) - 0.5 * (a0 + a1);
     }
     __syncthreads();
+    // V <- V T, a few rows at a time through buffer 2 (Vt is no longer read)
+    double* rowbuf = reinterpret_cast<double*>(Vt);
     for (int r0 = 0; r0 < n; r0 += kKeptRows) {
       const int na = min(kKeptRows, n - r0);
       for (int e = tid; e < na * rank; e += nt) {
         const int a = r0 + e / rank, j = e % rank;
+        const double* row = out + (int64_t)act[a] * ko;
         double s0 = 0.0, s1 = 0.0;
         int i = 0;
         for (; i + 1 < rank; i += 2) {
-          s0 = fma(Vk[a * lk + i], T[i * lt + j], s0);
-          s1 = fma(Vk[a * lk + i + 1], T[(i + 1) * lt + j], s1);
+          const double t0 = i >= j ? T[i * (i + 1) / 2 + j] : T[j * (j + 1) / 2 + i];
+          const double t1 = i + 1 >= j ? T[(i + 1) * (i + 2) / 2 + j] : T[j * (j + 1) / 2 + i + 1];
+          s0 = fma(row[i], t0, s0);
+          s1 = fma(row[i + 1], t1, s1);
         }
-        if (i < rank) s0 = fma(Vk[a * lk + i], T[i * lt + j], s0);
+        if (i < rank) s0 = fma(row[i], i >= j ? T[i * (i + 1) / 2 + j] : T[j * (j + 1) / 2 + i], s0);
         rowbuf[e] = s0 + s1;
       }
       __syncthreads();
-      for (int e = tid; e < na * rank; e += nt) Vk[(r0 + e / rank) * lk + e % rank] = rowbuf[e];
+      for (int e = tid; e < na * rank; e += nt) out[(int64_t)act[r0 + e / rank] * ko + e % rank] = rowbuf[e];
       __syncthreads();
     }
   }
-  double* out = (double*)view(ar, t.out).base;  // the new bases are float64 (arena C)
-  float* out32 = ar->p[AR_X] ? (float*)ar->p[AR_X] + (t.out & kOffMask) : nullptr;
-  for (int e = tid; e < t.n_pad * t.kcap; e += nt) {
-    out[e] = 0.0;
-    if (out32) out32[e] = 0.f;
-  }
-  __syncthreads();
-  // sign: the entry of largest magnitude (first such) is positive
+  // sign: the entry of largest magnitude (first such) is positive; the float copy for the
+  // GEMMs of the mixed product (arena X mirrors C's basis region)
+  if (out32)
+    for (int e = tid; e < t.n_pad * ko; e += nt) out32[e] = 0.f;
   for (int c = tid; c < rank; c += nt) {
     int best = 0;
     double bv = -1.0;
     for (int a = 0; a < n; ++a) {
-      const double v = fabs(Vk[a * lk + c]);
+      const double v = fabs(out[(int64_t)act[a] * ko + c]);
       if (v > bv) {
         bv = v;
         best = a;
       }
     }
-    const double sg = Vk[best * lk + c] < 0.0 ? -1.0 : 1.0;
+    const double sg = out[(int64_t)act[best] * ko + c] < 0.0 ? -1.0 : 1.0;
     for (int a = 0; a < n; ++a) {
-      const double v = sg * Vk[a * lk + c];
-      out[(int64_t)act[a] * t.kcap + c] = v;
-      if (out32) out32[(int64_t)act[a] * t.kcap + c] = (float)v;
+      const int64_t o = (int64_t)act[a] * ko + c;
+      const double v = sg * out[o];
+      out[o] = v;
+      if (out32) out32[o] = (float)v;
     }
   }
 }
@@ -1376,14 +1441,14 @@ void init_kernel_attributes() {
     cudaFuncSetAttribute(eig_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(3 * kMixMax * (kMixMax + 1) * sizeof(double)));
     cudaFuncSetAttribute(eig_mixed_kept_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)eig_kept_smem(kMixMax, kMixMax));
+                         (int)eig_kept_smem(kMixMax));
     cudaFuncSetAttribute(eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(2 * kEigSmemMax * (kEigSmemMax + 1) * sizeof(double)));
   });
 }
 
 void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const Arenas* ar, double eps,
-                      int trunc, int max_npad, int max_klim, void* stream) {
+                      int trunc, int max_npad, int variant, void* stream) {
   init_kernel_attributes();
   const double thr = trunc == H2_TRUNC_SV ? eps * eps : eps;
   if (trunc != H2_TRUNC_FULL && thr < 5e-5) {
@@ -1396,16 +1461,24 @@ void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const
     // the level's padded size comes from the rank caps; the actual sizes (children's
     // ranks) are only known on the device and are mostly far smaller, so tasks are
     // launched in size tiers, each with the shared memory of its largest size (more
-    // CTAs per SM for the small ones); the tiers run one after the other
+    // CTAs per SM for the small ones); the tiers run one after the other.  Variants:
+    // tiers up to 48 / 64 / 96 run on 128 threads (256 above); results are identical
+    const int small = variant == 1 ? 64 : (variant == 2 ? kMixMax : 48);
     const int top = round4(max_npad);
+    // a level with fewer tasks than a few CTAs per SM is one launch: its tiers would run
+    // one after the other, each as long as its slowest task
+    if (count < 4 * 152) {
+      eig_mixed_kept_kernel<<<(unsigned)count, top <= small ? 128 : 256, eig_kept_smem(top), (cudaStream_t)stream>>>(
+          d_eigs, first, ar, eps, trunc, -1, top);
+      g_launches += 1;
+      return;
+    }
     int lo = -1;
     for (int hi : {32, 48, 56, 64, 80, kMixMax}) {
       const int h = hi < top ? hi : top;
-      // (128 threads are enough for nn <= 48: a step has <= 300 block and row tasks)
       if (h > lo) {
-        const int kk = std::min(h, std::max(1, max_klim));
-        eig_mixed_kept_kernel<<<(unsigned)count, h <= 48 ? 128 : 256, eig_kept_smem(h, kk), (cudaStream_t)stream>>>(
-            d_eigs, first, ar, eps, trunc, lo, h, kk);
+        eig_mixed_kept_kernel<<<(unsigned)count, h <= small ? 128 : 256, eig_kept_smem(h), (cudaStream_t)stream>>>(
+            d_eigs, first, ar, eps, trunc, lo, h);
         g_launches += 1;
       }
       lo = h;
