@@ -306,13 +306,21 @@ def roofline(tr, precision):
         b = src.find("template <typename Acc>\nstatic void gemm_launch(")
         if a >= 0 and b > a and hashlib.sha256(src[a:b].encode()).hexdigest() == TRAFFIC["src_sha256"]:
             traffic = TRAFFIC["bytes"] / TRAFFIC["padded_flops"] * tot["gemm"][1] / tot["gemm"][2]
+    eig = None
+    if tot.get("eig", [0, 0, 0])[1]:
+        e_ms, e_tasks, e_n = tot["eig"]
+        eig = {"kernel": "eig_mixed_kept_kernel" if precision in ("mixed", "tf32x3") else "eig_kernel",
+               "bound": "latency", "ms_per_step": e_ms, "tasks_per_step": int(e_tasks), "launches_per_step": e_n,
+               "sm_us_per_task": e_ms * 1e3 * 152 / e_tasks,
+               "note": "one CTA per cluster basis: normalised Gram sum, Jacobi (barrier-separated "
+                       "rotation steps), truncation; no throughput peak applies"}
     return {"bound": bound, "kernel": KERNELS[precision], "dominant": dom, "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": traffic,
             "traffic_note": ("DRAM bytes per GEMM launch: bytes per padded flop of three captured launches "
                              "(N=65,536) x this run's padded flops per GEMM launch"
                              if traffic else "no DRAM capture of this kernel source at this precision"),
             "peak_note": peak_note, "launches_per_step": tot.get("gemm", [0, 0, 0])[2], "ms_per_step": gemm_ms,
-            "executed_flops_per_step": fl,
+            "executed_flops_per_step": fl, "eig": eig,
             "note": "GEMM kernel: multiply-add flops executed at the actual ranks (device counter) / its "
                     "CUDA-event time"}
 

@@ -287,8 +287,9 @@ h2_status h2_level_blocks(h2_handle h, int32_t level, int32_t* t, int32_t* s,
  * launch group of h2_mmp; off by default because it adds event records).  After a
  * product, h2_trace_read returns, for up to `cap` launch groups in program order,
  * the kernel kind (0 GEMM, 1 eigen, 2 memset), the level, the device time in ms and
- * the counted float64 multiply-add flops (2 m n k per product at the actual padded
- * dims) of that group; *count gets the number of groups.  Synchronises. */
+ * a work count: for a GEMM group the multiply-add flops at the plan's padded dims
+ * (2 m n k per product), for an eigen group the number of cluster bases it decomposes;
+ * *count gets the number of groups.  Synchronises. */
 h2_status h2_trace_enable(h2_handle A, int32_t on);
 h2_status h2_trace_read(h2_handle C, int32_t cap, int32_t* kind, int32_t* level, double* ms,
                         double* flops, int32_t* count);

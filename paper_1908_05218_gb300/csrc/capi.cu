@@ -1202,11 +1202,17 @@ std::shared_ptr<BatchEntry> capture_batch(const std::vector<Prepared*>& grp) {
     for (auto e : ev)
       if (e) cudaEventDestroy(e);
     for (auto x : st)
-      if (x) cudaStreamDestroy(x);
+      if (x) {
+        release_eig_streams(x);
+        cudaStreamDestroy(x);
+      }
   };
   cudaGraph_t g = nullptr;
   try {
-    for (auto& x : st) cuda_check(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking), "capture stream");
+    for (auto& x : st) {
+      cuda_check(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking), "capture stream");
+      prepare_eig_streams(x);  // (no stream or event is made inside the capture)
+    }
     for (auto& e : ev) cuda_check(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "capture event");
     const unsigned long long k0 = kernel_launches();
     cuda_check(cudaStreamBeginCapture(st[0], cudaStreamCaptureModeThreadLocal), "begin capture");
@@ -1504,7 +1510,7 @@ h2_status h2_trace_read(h2_handle C, int32_t cap, int32_t* kind, int32_t* level,
       if (kind) kind[i] = L.kind == Launch::GEMM ? 0 : (L.kind == Launch::EIG ? 1 : 2);
       if (level) level[i] = L.level;
       if (ms) ms[i] = t;
-      if (flops) flops[i] = L.flops;
+      if (flops) flops[i] = L.kind == Launch::EIG ? (double)L.count : L.flops;
     }
   });
 }

@@ -279,6 +279,11 @@ unsigned long long kernel_launches();  // kernels launched by this library so fa
 void add_kernel_launches(long long d);
 void init_kernel_attributes();  // once per process, before launches or captures   // graph replays add their kernels; captures take theirs back
 void launch_to_f32(const double* src, float* dst, int64_t n, void* stream);
+// the auxiliary streams on which launch_eig_mixed runs its size tiers concurrently, one
+// set per calling stream: made before a stream capture that will use them, and handed
+// back before the calling stream is destroyed
+void prepare_eig_streams(void* stream);
+void release_eig_streams(void* stream);
 // variant: which size tiers run on 128 threads instead of 256 (results identical for all)
 void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const Arenas* d_ars, double eps,
                       int trunc, int max_npad, int variant, void* stream);

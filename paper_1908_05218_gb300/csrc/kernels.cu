@@ -5,7 +5,9 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <vector>
 #include <cstdint>
 #include <cstdio>
 
@@ -1052,6 +1054,7 @@ __global__ void __launch_bounds__(256) eig_mixed_kernel(const EigTask* __restric
 // later a few new rows of the kept columns; then the step's task tables.
 constexpr int kKeptRows = 4;
 constexpr int kFixedParts = 128;
+constexpr int kEigTiers = 6;  // size tiers of the mixed eigen step (up to 32, 48, 56, 64, 80, 96)
 
 __host__ __device__ inline int round4(int n) { return (n + 3) & ~3; }
 
@@ -1447,6 +1450,57 @@ void init_kernel_attributes() {
   });
 }
 
+// auxiliary streams of the concurrent eigen tiers, one set per (device, calling stream);
+// nullptr if they cannot be made (the tiers then run in order on the calling stream)
+struct TierStreams {
+  cudaStream_t s[kEigTiers];
+  cudaEvent_t fork, join[kEigTiers];
+};
+
+static std::mutex g_tier_mu;
+static std::map<std::pair<int, cudaStream_t>, TierStreams*> g_tier_sets;  // by (device, calling stream)
+static std::map<int, std::vector<TierStreams*>> g_tier_free;            // released sets, by device
+
+static const TierStreams* tier_streams(cudaStream_t caller) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(g_tier_mu);
+  auto key = std::make_pair(dev, caller);
+  auto f = g_tier_sets.find(key);
+  if (f != g_tier_sets.end()) return f->second;
+  TierStreams* t = nullptr;
+  auto& fr = g_tier_free[dev];
+  if (!fr.empty()) {
+    t = fr.back();
+    fr.pop_back();
+  } else {
+    t = new TierStreams();
+    bool ok = cudaEventCreateWithFlags(&t->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; i < kEigTiers && ok; ++i)
+      ok = cudaStreamCreateWithFlags(&t->s[i], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&t->join[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      delete t;  // (a partly made set is left to the process's end)
+      t = nullptr;
+    }
+  }
+  g_tier_sets[key] = t;
+  return t;
+}
+
+void prepare_eig_streams(void* stream) { tier_streams((cudaStream_t)stream); }
+
+void release_eig_streams(void* stream) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  std::lock_guard<std::mutex> lk(g_tier_mu);
+  auto f = g_tier_sets.find(std::make_pair(dev, (cudaStream_t)stream));
+  if (f == g_tier_sets.end()) return;
+  if (f->second) g_tier_free[dev].push_back(f->second);
+  g_tier_sets.erase(f);
+}
+
 void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const Arenas* ar, double eps,
                       int trunc, int max_npad, int variant, void* stream) {
   init_kernel_attributes();
@@ -1461,7 +1515,7 @@ void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const
     // the level's padded size comes from the rank caps; the actual sizes (children's
     // ranks) are only known on the device and are mostly far smaller, so tasks are
     // launched in size tiers, each with the shared memory of its largest size (more
-    // CTAs per SM for the small ones); the tiers run one after the other.  Variants:
+    // CTAs per SM for the small ones).  Variants:
     // tiers up to 48 / 64 / 96 run on 128 threads (256 above); results are identical
     const int small = variant == 1 ? 64 : (variant == 2 ? kMixMax : 48);
     const int top = round4(max_npad);
@@ -1473,13 +1527,27 @@ void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const
       g_launches += 1;
       return;
     }
-    int lo = -1;
+    // the tiers are independent (each task belongs to one), so they run concurrently on
+    // auxiliary streams forked from the calling stream and joined back to it
+    const TierStreams* ts = tier_streams((cudaStream_t)stream);
+    if (ts) cudaEventRecord(ts->fork, (cudaStream_t)stream);
+    int lo = -1, ti = 0;
     for (int hi : {32, 48, 56, 64, 80, kMixMax}) {
       const int h = hi < top ? hi : top;
       if (h > lo) {
-        eig_mixed_kept_kernel<<<(unsigned)count, h <= small ? 128 : 256, eig_kept_smem(h), (cudaStream_t)stream>>>(
-            d_eigs, first, ar, eps, trunc, lo, h);
+        cudaStream_t st = (cudaStream_t)stream;
+        if (ts) {
+          st = ts->s[ti];
+          cudaStreamWaitEvent(st, ts->fork, 0);
+        }
+        eig_mixed_kept_kernel<<<(unsigned)count, h <= small ? 128 : 256, eig_kept_smem(h), st>>>(d_eigs, first, ar,
+                                                                                                 eps, trunc, lo, h);
         g_launches += 1;
+        if (ts) {
+          cudaEventRecord(ts->join[ti], st);
+          cudaStreamWaitEvent((cudaStream_t)stream, ts->join[ti], 0);
+        }
+        ++ti;
       }
       lo = h;
       if (h == top) break;

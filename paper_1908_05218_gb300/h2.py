@@ -233,7 +233,8 @@ class H2Matrix:
         _check(load().h2_trace_enable(self.handle, int(on)))
 
     def trace_read(self) -> list:
-        """Per launch group of the product that made this handle: (kind, level, ms, flops)."""
+        """Per launch group of the product that made this handle: (kind, level, ms, work):
+        work = padded multiply-add flops of a GEMM group, clusters of an eigen group."""
         lib = load()
         cnt = C.c_int32(0)
         _check(lib.h2_trace_read(self.handle, 0, None, None, None, None, C.byref(cnt)))
