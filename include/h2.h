@@ -145,15 +145,21 @@ typedef struct {
  * on level L, block partition by Eq. admCond with bounding boxes.  The numeric
  * construction is not specified by the paper (it cites another method); this library
  * uses nested far-field sampling with interpolative skeletons (sampled far field
- * per cluster, skeleton rows chosen by pivoted Gram-Schmidt).  The Helmholtz kernel gives a
+ * per cluster, skeleton rows chosen by pivoted Gram-Schmidt).  The real kernels are built
+ * on the GPU, level by level, straight into the device arena (the sampled Gram matrices
+ * from float32 kernel values with float64 sums, float64 eigen-decompositions, skeletons,
+ * couplings and dense blocks); the Helmholtz kernel is built on the host and gives a
  * complex matrix (complex-symmetric: column bases equal row bases).  Errors: H2_EINVAL for
- * bad sizes, non-finite points or an unknown kernel. */
+ * bad sizes, non-finite points or an unknown kernel; H2_ENOMEM. */
 h2_status h2_build(const double* points, int64_t n, const h2_kernel* kernel,
                    int32_t leaf_size, double eta, double eps, const h2_opts* opts,
                    h2_handle* out);
 
 /* The construction of h2_build on the host only (no GPU, no device memory): the packed
- * arrays of h2_import (complex kernels: two doubles per element) for the points.  Pass
+ * arrays of h2_import (complex kernels: two doubles per element) for the points.  For the
+ * real kernels h2_build runs the same steps on the GPU with float32 kernel values in the
+ * sampled Gram matrices, so a rank may differ by one or two where an eigenvalue lies
+ * within float32 noise of eps^2 lambda_1; the accuracy is the same.  Pass
  * NULL arrays to get the element counts in sizes[0..7] (as h2_export: ranks per array,
  * vr, vc, er, ec, s, f, 0); each call runs the construction.  Errors as h2_build.  The
  * paper has no counterpart: its inputs come from a cited construction method. */
@@ -168,7 +174,7 @@ h2_status h2_build_packed(const double* points, int64_t n, const h2_kernel* kern
 h2_status h2_set_alloc_limit(int64_t n);
 
 /* Host-only size of the product program of C = A A (no GPU needed): tree, partition
- * and H^2 ranks of the Laplace kernel as h2_build makes them (at eps), storage caps as
+ * and H^2 ranks of the Laplace kernel as h2_build_packed makes them (at eps), storage caps as
  * an import sets them, rank cap 48, truncation rule `trunc`.  *flops gets the
  * multiply-add flops counted over all GEMM items at the padded caps (2 m n k), and
  * *segments / *items the numbers of output matrices and of products.  At constant rank
@@ -178,7 +184,7 @@ h2_status h2_plan_stats(const double* points, int64_t n, int32_t leaf_size, doub
                         double* flops, int64_t* segments, int64_t* items);
 
 /* Host-only self-check of the product program (no device memory, no GPU needed):
- * builds the tree, partition and H^2 ranks of the Laplace kernel (as h2_build, at
+ * builds the tree, partition and H^2 ranks of the Laplace kernel (as h2_build_packed, at
  * ε = eps) for the points, then the program of C = A A for every truncation mode
  * (paper, sv, full, formatted), both precisions and rank caps 24 and 48, and the
  * matvec programs for 1 and 3 right-hand sides.  Each is validated: every operand and

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libh2gb300.so")
 OBJ = os.path.join(HERE, "_build")
 
-CU = ["kernels.cu", "mma.cu", "zkernels.cu", "capi.cu", "noalloc.cu", "transfer.cu"]
+CU = ["kernels.cu", "mma.cu", "zkernels.cu", "gbuild.cu", "capi.cu", "noalloc.cu", "transfer.cu"]
 CPP = ["structure.cpp", "builder.cpp", "plan.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -39,6 +39,7 @@ def _stale(src: str, obj: str) -> bool:
         return True
     t = os.path.getmtime(obj)
     deps = [src, os.path.join(CSRC, "internal.hpp"), os.path.join(CSRC, "device.cuh"),
+            os.path.join(CSRC, "jacobi.cuh"),
             os.path.join(HERE, "..", "include", "h2.h"), os.path.abspath(__file__)]
     return any(os.path.getmtime(d) > t for d in deps)
 

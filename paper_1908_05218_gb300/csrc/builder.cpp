@@ -34,10 +34,10 @@ namespace {
 // far-field points read per partner block: 24 suffice for the smooth real kernels; the
 // oscillatory Helmholtz kernel needs more (its far-field ranks grow with the electrical
 // size of the blocks)
-constexpr int kSamplesReal = 24, kSamplesComplex = 128;
-constexpr int kAllRows = 64;
-constexpr int kOver = 8;
-constexpr int kMaxRank = 64;
+constexpr int kSamplesReal = kBuildSamples, kSamplesComplex = 128;
+constexpr int kAllRows = kBuildAllRows;
+constexpr int kOver = kBuildOver;
+constexpr int kMaxRank = kBuildMaxRank;
 
 using cd = std::complex<double>;
 inline double cj(double x) { return x; }

@@ -203,6 +203,8 @@ void make_user_map(h2_matrix* h) {
 
 namespace h2 {
 
+void* dev_alloc(size_t bytes) { return dmalloc(bytes); }
+
 void cuda_check(int err, const char* what) {
   if (err != cudaSuccess) {
     cudaGetLastError();
@@ -684,6 +686,12 @@ h2_status h2_build(const double* points, int64_t n, const h2_kernel* kernel, int
     auto h = std::make_unique<h2_matrix>();
     h->m.st = structure_for(points, n, leaf_size, eta);
     h->m.cplx = kernel->kind == H2_K_HELMHOLTZ;
+    if (!h->m.cplx) {  // real kernels: built on the GPU, straight into the arena
+      build_h2_device(*h->m.st, *kernel, eps, h->m);
+      finish_handle(h.get(), o);
+      *out = h.release();
+      return;
+    }
     Packed p;
     build_h2_host(*h->m.st, *kernel, eps, p);
     PackedView v;

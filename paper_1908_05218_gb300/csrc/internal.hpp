@@ -311,6 +311,15 @@ struct Packed {
   std::vector<double> vr, vc, er, ec, s, f;
 };
 void build_h2_host(const Structure& st, const h2_kernel& k, double eps, Packed& out);
+// the construction's parameters (builder.cpp, gbuild.cu): sampled far-field points per
+// partner block (real kernels), clusters whose rows are all skeleton rows, extra
+// skeleton rows above the rank, largest rank
+constexpr int kBuildSamples = 24, kBuildAllRows = 64, kBuildOver = 8, kBuildMaxRank = 64;
+// the same construction on the GPU for the real kernels, into m's arena (m.st set; caps,
+// arena and ranks made here); H2_EUNSUPPORTED for the complex kernel
+void build_h2_device(const Structure& st, const h2_kernel& k, double eps, Mat& m);
+// device allocation with the library's failure injection (h2_set_alloc_limit)
+void* dev_alloc(size_t bytes);
 // One block moved between the packed layout and the padded arena: rows x cols, dense
 // (row-major) at packed_off of the concatenated packed arrays, row stride ld at
 // arena_off of the arena (transfer.cu).

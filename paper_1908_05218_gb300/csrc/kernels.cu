@@ -12,6 +12,7 @@
 #include <cstdio>
 
 #include "device.cuh"
+#include "jacobi.cuh"
 #include "internal.hpp"
 
 namespace h2 {
@@ -539,26 +540,10 @@ void launch_to_f32(const double* src, float* dst, int64_t n, void* stream) {
 }
 
 // ------------------------------------------------------------ eigen + truncation
-// Cyclic two-sided Jacobi with the round-robin (tournament) ordering: each step
-// applies n/2 disjoint rotations in parallel; a sweep is n-1 steps.  The rotation
-// zeroing a_pq is the symmetric 2 x 2 Schur rotation: tau = (a_qq - a_pp)/(2 a_pq),
-// t = sign(tau)/(|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1 + t^2), s = t c.
+// (the round-robin Jacobi sweeps and block sums are in jacobi.cuh)
 constexpr int kEigSmemMax = 112;
 
-__device__ double block_sum(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  double t = 0.0;
-  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
-  return t;
-}
 
-template <typename T>
-__device__ void jacobi_sweeps(T* A, T* V, int nn, int lds, int max_sweeps, double tol, double* red, T* cs, T* sn,
-                              int* pp, int* qq);
 
 __device__ double block_max(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -743,70 +728,6 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
 // refinement.  The new bases are V's leading columns (float64, orthonormal to
 // ~1e-14).  Shared memory: G, V, T, each n x n float64 (n <= 96).
 constexpr int kMixMax = 96;
-
-template <typename T>
-__device__ void jacobi_sweeps(T* A, T* V, int nn, int lds, int max_sweeps, double tol, double* red, T* cs, T* sn,
-                              int* pp, int* qq) {
-  const int tid = threadIdx.x, nt = blockDim.x, np = nn / 2;
-  const int lane = tid & 31, w = tid >> 5, nw = nt >> 5;
-  for (int sweep = 0; sweep < max_sweeps && nn > 1; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (int i = w; i < nn; i += nw)
-      for (int j = lane; j < nn; j += 32) {
-        double v = (double)A[i * lds + j] * (double)A[i * lds + j];
-        tot += v;
-        if (i != j) off += v;
-      }
-    off = block_sum(off, red);
-    tot = block_sum(tot, red);
-    if (!(off > tol * tot)) break;
-    for (int step = 0; step < nn - 1; ++step) {
-      for (int k = tid; k < np; k += nt) {
-        int pa = (k == 0) ? 0 : ((k - 1 + step) % (nn - 1)) + 1;
-        int pb = ((nn - 1 - k - 1 + step) % (nn - 1)) + 1;
-        int p = min(pa, pb), q = max(pa, pb);
-        T apq = A[p * lds + q];
-        T c = T(1), s = T(0);
-        if (apq != T(0)) {
-          T tau = (A[q * lds + q] - A[p * lds + p]) / (T(2) * apq);
-          T tt = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
-          c = T(1) / sqrt(T(1) + tt * tt);
-          s = tt * c;
-        }
-        pp[k] = p;
-        qq[k] = q;
-        cs[k] = c;
-        sn[k] = s;
-      }
-      __syncthreads();
-      for (int k = w; k < np; k += nw) {  // rows p, q
-        if (sn[k] == T(0)) continue;
-        const int p = pp[k], q = qq[k];
-        const T c = cs[k], s = sn[k];
-        for (int j = lane; j < nn; j += 32) {
-          T x = A[p * lds + j], y = A[q * lds + j];
-          A[p * lds + j] = c * x - s * y;
-          A[q * lds + j] = s * x + c * y;
-        }
-      }
-      __syncthreads();
-      for (int k = w; k < np; k += nw) {  // columns p, q of A and V
-        if (sn[k] == T(0)) continue;
-        const int p = pp[k], q = qq[k];
-        const T c = cs[k], s = sn[k];
-        for (int i = lane; i < nn; i += 32) {
-          T x = A[i * lds + p], y = A[i * lds + q];
-          A[i * lds + p] = c * x - s * y;
-          A[i * lds + q] = s * x + c * y;
-          T vx = V[i * lds + p], vy = V[i * lds + q];
-          V[i * lds + p] = c * vx - s * vy;
-          V[i * lds + q] = s * vx + c * vy;
-        }
-      }
-      __syncthreads();
-    }
-  }
-}
 
 // C = op(X) op(Y) for nn x nn float64 matrices in shared memory, row stride lds
 // (C distinct from X, Y); each thread computes four outputs of one row with

@@ -67,20 +67,26 @@ struct PlanBuilder {
   // cost class (floor(log2(m n sum k)) at the padded dims), largest first, keeping the
   // program order inside a class; the kernels then start the long sums first.
   void bucket() {
-    auto cls = [&](const Seg& s) {
+    const size_t n = P.segs.size() - g0;
+    if (n < 2) return;
+    std::vector<int> cls(n);
+    int cmin = INT32_MAX, cmax = INT32_MIN;
+    for (size_t i = 0; i < n; ++i) {
+      const Seg& sg = P.segs[g0 + i];
       double k = 0;
-      for (int32_t q = s.first; q < s.first + s.count; ++q) k += P.items[q].kpad ? P.items[q].kpad : s.k;
-      const double c = (double)s.m * s.n * std::max(1.0, k);
-      return (int)std::floor(std::log2(c));
-    };
-    std::vector<std::pair<int, int64_t>> key;
-    key.reserve(P.segs.size() - g0);
-    for (size_t i = g0; i < P.segs.size(); ++i) key.push_back({-cls(P.segs[i]), (int64_t)i});
-    std::stable_sort(key.begin(), key.end(),
-                     [](const std::pair<int, int64_t>& a, const std::pair<int, int64_t>& b) { return a.first < b.first; });
-    std::vector<Seg> sorted;
-    sorted.reserve(key.size());
-    for (auto& k : key) sorted.push_back(P.segs[k.second]);
+      for (int32_t q = sg.first; q < sg.first + sg.count; ++q) k += P.items[q].kpad ? P.items[q].kpad : sg.k;
+      const double c = (double)sg.m * sg.n * std::max(1.0, k);
+      cls[i] = -(int)std::floor(std::log2(c));
+      cmin = std::min(cmin, cls[i]);
+      cmax = std::max(cmax, cls[i]);
+    }
+    if (cmin == cmax) return;
+    // stable counting sort on the class (largest cost first)
+    std::vector<size_t> start((size_t)(cmax - cmin) + 2, 0);
+    for (size_t i = 0; i < n; ++i) ++start[(size_t)(cls[i] - cmin) + 1];
+    for (size_t c = 1; c < start.size(); ++c) start[c] += start[c - 1];
+    std::vector<Seg> sorted(n);
+    for (size_t i = 0; i < n; ++i) sorted[start[(size_t)(cls[i] - cmin)]++] = P.segs[g0 + i];
     std::copy(sorted.begin(), sorted.end(), P.segs.begin() + g0);
   }
   void end(const char* phase, int level) {
@@ -108,12 +114,16 @@ struct PlanBuilder {
   }
   void gemm(int64_t out, int m, int n, int k, int lda, int ldb, int ldc, uint8_t fl,
             const std::vector<Item>& it, int32_t mref = -1, int32_t nref = -1) {
-    if (m <= 0 || n <= 0 || it.empty()) return;
+    gemm(out, m, n, k, lda, ldb, ldc, fl, it.data(), it.size(), mref, nref);
+  }
+  void gemm(int64_t out, int m, int n, int k, int lda, int ldb, int ldc, uint8_t fl, const Item* it, size_t nit,
+            int32_t mref = -1, int32_t nref = -1) {
+    if (m <= 0 || n <= 0 || nit == 0) return;
     if (k <= 0) return;  // zero contribution; outputs start at zero
     Seg s{};
     s.out = out;
     s.first = (int32_t)P.items.size();
-    s.count = (int32_t)it.size();
+    s.count = (int32_t)nit;
     s.m = (int16_t)m;
     s.n = (int16_t)n;
     s.k = (int16_t)k;
@@ -123,14 +133,15 @@ struct PlanBuilder {
     s.mref = mref;
     s.nref = nref;
     s.flags = fl;
-    if ((int64_t)P.items.size() + (int64_t)it.size() > INT32_MAX) throw Error(H2_ENOMEM, "plan too large");
-    P.items.insert(P.items.end(), it.begin(), it.end());
+    if ((int64_t)P.items.size() + (int64_t)nit > INT32_MAX) throw Error(H2_ENOMEM, "plan too large");
+    P.items.insert(P.items.end(), it, it + nit);
     P.segs.push_back(s);
-    for (const Item& x : it) P.flops += 2LL * m * n * (x.kpad ? x.kpad : k);
+    for (size_t q = 0; q < nit; ++q) P.flops += 2LL * m * n * (it[q].kpad ? it[q].kpad : k);
   }
   void gemm1(int64_t out, int m, int n, int k, int lda, int ldb, int ldc, uint8_t fl, int64_t a, int64_t b,
              int32_t mref = -1, int32_t nref = -1, int32_t kref = -1) {
-    gemm(out, m, n, k, lda, ldb, ldc, fl, {Item{a, b, kref}}, mref, nref);
+    const Item x{a, b, kref};
+    gemm(out, m, n, k, lda, ldb, ldc, fl, &x, 1, mref, nref);
   }
   void sum(int64_t out, int m, int n, int lda, int ldc, bool acc, const std::vector<int64_t>& mats) {
     if (m <= 0 || n <= 0 || mats.empty()) return;
@@ -190,23 +201,31 @@ int8_t classify(const Structure& st, int l, int64_t i, int64_t k, int32_t& pos) 
 void enumerate(const Structure& st, int l, LevelTargets& lt) {
   const auto& bl = st.blocks[l];
   const auto& rp = st.row_ptr[l];
+  // target ids of the current row cluster i by column cluster k (blocks are sorted by
+  // row cluster, so each i is one run of blocks); reset after each run
+  std::vector<int32_t> mark((size_t)1 << l, -1);
+  std::vector<int64_t> touched;
+  int64_t cur_i = -1;
   for (int32_t pa = 0; pa < (int32_t)bl.size(); ++pa) {
     int64_t i = bl[pa].t, j = bl[pa].s;
+    if (i != cur_i) {
+      for (int64_t k : touched) mark[k] = -1;
+      touched.clear();
+      cur_i = i;
+    }
     for (int32_t pb = rp[j]; pb < rp[j + 1]; ++pb) {
       int64_t k = bl[pb].s;
-      int64_t key = Structure::key(i, k);
-      auto it = lt.id.find(key);
-      int32_t id;
-      if (it == lt.id.end()) {
+      int32_t id = mark[k];
+      if (id < 0) {
         id = (int32_t)lt.tg.size();
-        lt.id[key] = id;
+        mark[k] = id;
+        touched.push_back(k);
+        lt.id[Structure::key(i, k)] = id;
         Target t;
         t.i = (int32_t)i;
         t.k = (int32_t)k;
         t.cls = classify(st, l, i, k, t.cpos);
         lt.tg.push_back(t);
-      } else {
-        id = it->second;
       }
       lt.trip.push_back({pa, pb, id});
       if (bl[pa].kind == KNL && bl[pb].kind == KNL) lt.tg[id].has_nlnl = true;
@@ -735,20 +754,33 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
     // ---- couplings (Eq. leafcoup_simple / nonleafcoup_simple), summed per target in
     // one segment: case-1 (leaf: (V^C^T F)(F V^C)), case-2/4 (Ahat SBP), case-3 (PAS Bhat);
     // above the leaf level case-1 (E^C^T (M E^C)) is a separate first pass
-    std::vector<std::vector<Item>> cpl(lt.tg.size());
-    for (size_t q = 0; q < lt.tg.size(); ++q)
-      if (leaf && lt.tg[q].cls != TC_F)
-        for (const Item& x : lt.tg[q].g1) cpl[q].push_back(Item(x.a, x.b, -1, LS, cC(l), LS));
-    for (auto& tr : lt.trip) {
+    // the items of each target, in one array: case-1 first, then the triples in order
+    const size_t ntg = lt.tg.size();
+    auto counted = [&](const Triple& tr) {
       const Block &ba = bl[tr.pa], &bb = bl[tr.pb];
-      const Target& T = lt.tg[tr.tgt];
-      if (T.cls == TC_F) continue;
-      if (ba.kind == KNL && bb.kind == KNL) continue;
-      if (ba.kind == KF && bb.kind == KF) continue;  // case-1 (leaf), above
+      if (lt.tg[tr.tgt].cls == TC_F) return false;
+      if (ba.kind == KNL && bb.kind == KNL) return false;
+      if (ba.kind == KF && bb.kind == KF) return false;  // case-1 (leaf), above
+      return true;
+    };
+    std::vector<int64_t> coff(ntg + 1, 0);
+    for (size_t q = 0; q < ntg; ++q)
+      if (leaf && lt.tg[q].cls != TC_F) coff[q + 1] += (int64_t)lt.tg[q].g1.size();
+    for (auto& tr : lt.trip)
+      if (counted(tr)) ++coff[tr.tgt + 1];
+    for (size_t q = 0; q < ntg; ++q) coff[q + 1] += coff[q];
+    std::vector<Item> cpl((size_t)coff[ntg]);
+    std::vector<int64_t> cur(coff.begin(), coff.end() - 1);
+    for (size_t q = 0; q < ntg; ++q)
+      if (leaf && lt.tg[q].cls != TC_F)
+        for (const Item& x : lt.tg[q].g1) cpl[cur[q]++] = Item(x.a, x.b, -1, LS, cC(l), LS);
+    for (auto& tr : lt.trip) {
+      if (!counted(tr)) continue;
+      const Block &ba = bl[tr.pa], &bb = bl[tr.pb];
       if (bb.kind == KR)  // case-2, case-4
-        cpl[tr.tgt].push_back(Item(Ahat[l][tr.pa], SBP[tr.pb], BR(l, ba.s), rB(l), cC(l), rB(l)));
+        cpl[cur[tr.tgt]++] = Item(Ahat[l][tr.pa], SBP[tr.pb], BR(l, ba.s), rB(l), cC(l), rB(l));
       else  // case-3
-        cpl[tr.tgt].push_back(Item(PAS[tr.pa], Bhat[l][tr.pb], AC(l, ba.s), cA(l), cC(l), cA(l)));
+        cpl[cur[tr.tgt]++] = Item(PAS[tr.pa], Bhat[l][tr.pb], AC(l, ba.s), cA(l), cC(l), cA(l));
     }
     const int kmax = std::max(std::max(leaf ? LS : 0, rB(l)), cA(l));
     if (!leaf) {
@@ -762,10 +794,10 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       pb.end("coup", l);
     }
     pb.begin();
-    for (size_t q = 0; q < lt.tg.size(); ++q)
+    for (size_t q = 0; q < ntg; ++q)
       if (lt.tg[q].cls != TC_F)
-        pb.gemm(lt.tg[q].ssum, rC(l), cC(l), kmax, kmax, cC(l), cC(l), SF_ACC, cpl[q], CR(l, lt.tg[q].i),
-                CC(l, lt.tg[q].k));
+        pb.gemm(lt.tg[q].ssum, rC(l), cC(l), kmax, kmax, cC(l), cC(l), SF_ACC, cpl.data() + coff[q],
+                (size_t)(coff[q + 1] - coff[q]), CR(l, lt.tg[q].i), CC(l, lt.tg[q].k));
     pb.end("coup", l);
     pb.close_memset(zG, g);
     pb.close_memset(zS, AR_S);

@@ -279,8 +279,8 @@ def plan_selfcheck(points: np.ndarray, leaf_size: int = 32, eta: float = 1.0, ep
 
 
 def build_packed(points: np.ndarray, spec, leaf_size: int = 32, eta: float = 1.0, eps: float = 1e-4) -> Packed:
-    """The host construction of h2_build as packed arrays (no GPU; complex kernels give
-    complex128 arrays)."""
+    """The host construction as packed arrays (no GPU; complex kernels give complex128
+    arrays); h2_build runs the same steps on the GPU for the real kernels."""
     lib = load()
     pts = np.ascontiguousarray(points, dtype=np.float64)
     k = make_kernel(spec)

@@ -1,5 +1,5 @@
-"""CPU tests of the library's host construction (h2_build_packed: the construction of
-h2_build without a GPU), read back into the oracle's representation.
+"""CPU tests of the library's host construction (h2_build_packed: the steps of h2_build
+without a GPU), read back into the oracle's representation.
 
 The paper cites but does not describe its construction; what it must deliver is an H^2
 matrix on the library's partition that approximates the kernel matrix to about eps_H2,
