@@ -9,15 +9,18 @@
 //     [Q_t1 K(I_t1, far(t)); Q_t2 K(I_t2, far(t))] (non-leaf t; I_c are the skeleton
 //     rows of child c, Q_c maps samples on I_c to coefficients).  The kernel values are
 //     float32, taken from float64 coordinate differences (relative error ~1e-7, far
-//     below eps); products and sums are float64, because the kept eigenvalues reach
-//     eps^2 lambda_1;
+//     below eps); the Gram sums must resolve eigenvalues down to eps^2 lambda_1, so each
+//     product is split exactly into two float32 values (x y = p + e, e = fma(x, y, -p))
+//     and summed in double-float arithmetic (an unevaluated sum hi + lo of two float32
+//     values, Knuth's TwoSum; relative error ~1e-13), on the float32 pipes;
 //   * a float64 Jacobi decomposition of G_t: the eigenvectors with lambda > eps^2
 //     lambda_1 (at most kBuildMaxRank) are the leaf basis V_t or the stacked transfer
 //     E_t;
 //   * skeleton rows I_t (all candidate rows while |t| <= kBuildAllRows, else k_t +
 //     kBuildOver rows by greedy pivoted Gram-Schmidt on the rows of V_t), Q_t =
-//     pinv(V_t[I_t, :]) (leaf: V_t^T), couplings Q_t K(I_t, I_s) Q_s^T and dense blocks
-//     K(t, s), in float64;
+//     pinv(V_t[I_t, :]) (leaf: V_t^T) in float64, couplings Q_t K(I_t, I_s) Q_s^T in
+//     float32 (stored as float64; relative error ~1e-6, far below eps) and dense blocks
+//     K(t, s) in float64;
 //   * symmetric kernel and partition: the column bases equal the row bases.
 // Real kernels only (1/(4 pi r), 1/r^2); the complex Helmholtz kernel is built on the
 // host.
@@ -72,6 +75,19 @@ struct GramTask {
   int32_t c1, c2;  // non-leaf: the children
 };
 
+// (h, l) += x y in double-float arithmetic: the product split exactly (x y = p + e),
+// p added to h by Knuth's TwoSum, the rounding errors gathered in l
+// (the _rn intrinsics keep the compiler from contracting these steps into FMAs)
+__device__ __forceinline__ void df_fma(float x, float y, float& h, float& l) {
+  const float p = __fmul_rn(x, y);
+  const float e = fmaf(x, y, -p);
+  const float s = __fadd_rn(h, p);
+  const float bp = __fsub_rn(s, h);
+  const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+  h = s;
+  l = __fadd_rn(l, __fadd_rn(err, e));
+}
+
 // the sample point of column c of a cluster's stream (binary search over its partners)
 __device__ __forceinline__ int64_t column_point(const Part* parts, int32_t nseg, int32_t c) {
   int lo = 0, hi = nseg - 1;
@@ -122,7 +138,7 @@ __global__ void __launch_bounds__(256) gb_gram_kernel(const GramTask* __restrict
   // the lower-triangle entries (i, j), i >= j, this thread sums
   const int ne = m * (m + 1) / 2;
   int gi[U], gj[U];
-  double acc[U];
+  float hi[U], lo[U];  // G_ij = hi + lo (double-float)
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     const int e = tid + 256 * u;
@@ -131,7 +147,8 @@ __global__ void __launch_bounds__(256) gb_gram_kernel(const GramTask* __restrict
     while ((i + 1) * (i + 2) / 2 <= e) ++i;
     gi[u] = i;
     gj[u] = e - i * (i + 1) / 2;
-    acc[u] = 0.0;
+    hi[u] = 0.f;
+    lo[u] = 0.f;
   }
   const Part* pp = parts + tk.seg0;
   const float* W = leaf ? Kc : Wc;
@@ -179,16 +196,19 @@ __global__ void __launch_bounds__(256) gb_gram_kernel(const GramTask* __restrict
       if (tid + 256 * u < ne) {
         const float4* a = reinterpret_cast<const float4*>(W + gi[u] * kCW);
         const float4* b = reinterpret_cast<const float4*>(W + gj[u] * kCW);
-        double s = acc[u];
+        float h = hi[u], l = lo[u];
 #pragma unroll 8
         for (int c = 0; c < kCW / 4; ++c) {
           const float4 x = a[c], y = b[c];
-          s = fma((double)x.x, (double)y.x, s);
-          s = fma((double)x.y, (double)y.y, s);
-          s = fma((double)x.z, (double)y.z, s);
-          s = fma((double)x.w, (double)y.w, s);
+          df_fma(x.x, y.x, h, l);
+          df_fma(x.y, y.y, h, l);
+          df_fma(x.z, y.z, h, l);
+          df_fma(x.w, y.w, h, l);
         }
-        acc[u] = s;
+        // renormalise (Fast2Sum: |h| >= |l|)
+        const float sum = __fadd_rn(h, l);
+        lo[u] = __fsub_rn(l, __fsub_rn(sum, h));
+        hi[u] = sum;
       }
     }
   }
@@ -196,8 +216,9 @@ __global__ void __launch_bounds__(256) gb_gram_kernel(const GramTask* __restrict
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     if (tid + 256 * u < ne) {
-      g[gi[u] * m + gj[u]] = acc[u];
-      g[gj[u] * m + gi[u]] = acc[u];
+      const double v = (double)hi[u] + (double)lo[u];
+      g[gi[u] * m + gj[u]] = v;
+      g[gj[u] * m + gi[u]] = v;
     }
   }
 }
@@ -467,7 +488,8 @@ struct CoupTask {
   int64_t off;  // arena offset of S_ts (row stride ld)
 };
 
-// S_ts = Q_t K(I_t, I_s) Q_s^T (kt x ks) into the arena, one block per CTA
+// S_ts = Q_t K(I_t, I_s) Q_s^T (kt x ks) into the arena, one block per CTA, in float32
+// (kernel values from float64 coordinate differences)
 __global__ void __launch_bounds__(128) gb_coup_kernel(const CoupTask* __restrict__ tasks, const double* __restrict__ pts,
                                                       int kind, double diag, const int32_t* __restrict__ skel,
                                                       int skel_stride, const int32_t* __restrict__ np,
@@ -478,26 +500,35 @@ __global__ void __launch_bounds__(128) gb_coup_kernel(const CoupTask* __restrict
   const int tid = threadIdx.x, nt = blockDim.x;
   const int kt = kk[tk.t], ks = kk[tk.s], nt_ = np[tk.t], ns = np[tk.s];
   if (kt == 0 || ks == 0) return;
-  double* K = (double*)csm;                  // nt_ x ns
-  double* T = K + (size_t)nt_ * ns;          // kt x ns
+  float* K = (float*)csm;                    // nt_ x ns
+  float* T = K + (size_t)nt_ * ns;           // kt x ns
+  float* Qt = T + (size_t)kt * ns;           // kt x nt_
+  float* Qs = Qt + (size_t)kt * nt_;         // ks x ns
   const int32_t* it = skel + (int64_t)tk.t * skel_stride;
   const int32_t* is = skel + (int64_t)tk.s * skel_stride;
-  for (int e = tid; e < nt_ * ns; e += nt) K[e] = kval64(kind, diag, pts, it[e / ns], is[e % ns]);
-  __syncthreads();
+  for (int e = tid; e < nt_ * ns; e += nt) {
+    const int64_t a = it[e / ns], b = is[e % ns];
+    const float dx = (float)(pts[3 * a] - pts[3 * b]), dy = (float)(pts[3 * a + 1] - pts[3 * b + 1]),
+                dz = (float)(pts[3 * a + 2] - pts[3 * b + 2]);
+    K[e] = kfar32(kind, dx * dx + dy * dy + dz * dz);
+  }
   const double* qt = Q + (int64_t)tk.t * q_stride;
   const double* qs = Q + (int64_t)tk.s * q_stride;
+  for (int e = tid; e < kt * nt_; e += nt) Qt[e] = (float)qt[e];
+  for (int e = tid; e < ks * ns; e += nt) Qs[e] = (float)qs[e];
+  __syncthreads();
   for (int e = tid; e < kt * ns; e += nt) {
     const int a = e / ns, j = e % ns;
-    double s = 0.0;
-    for (int i = 0; i < nt_; ++i) s += qt[a * nt_ + i] * K[i * ns + j];
+    float s = 0.f;
+    for (int i = 0; i < nt_; ++i) s = fmaf(Qt[a * nt_ + i], K[i * ns + j], s);
     T[e] = s;
   }
   __syncthreads();
   for (int e = tid; e < kt * ks; e += nt) {
     const int a = e / ks, c = e % ks;
-    double s = 0.0;
-    for (int j = 0; j < ns; ++j) s += T[a * ns + j] * qs[c * ns + j];
-    arena[tk.off + (int64_t)a * ld + c] = s;
+    float s = 0.f;
+    for (int j = 0; j < ns; ++j) s = fmaf(T[a * ns + j], Qs[c * ns + j], s);
+    arena[tk.off + (int64_t)a * ld + c] = (double)s;
   }
 }
 
@@ -790,7 +821,8 @@ void build_h2_device(const Structure& st, const h2_kernel& kern, double eps, Mat
     for (auto& b : st.blocks[l])
       if (b.kind == KR) {
         ct.push_back({b.t, b.s, m.S(l, b.idx)});
-        const size_t need = ((size_t)lv[l].p[b.t] * lv[l].p[b.s] + (size_t)lv[l].k[b.t] * lv[l].p[b.s]) * 8;
+        const size_t need = ((size_t)lv[l].p[b.t] * lv[l].p[b.s] + (size_t)lv[l].k[b.t] * lv[l].p[b.s] +
+                             (size_t)lv[l].k[b.t] * lv[l].p[b.t] + (size_t)lv[l].k[b.s] * lv[l].p[b.s]) * 4;
         smem = std::max(smem, need);
       }
     if (ct.empty()) continue;

@@ -965,13 +965,14 @@ __global__ void __launch_bounds__(256) eig_mixed_kernel(const EigTask* __restric
 //       ties by index);
 //   (3) the kept columns go to float64, in place in the output (rows act[a]), and one
 //       Newton-Schulz step on those columns, V <- V (3 I - V^T V) / 2, makes them
-//       orthonormal to the square of their float32 error.
+//       orthonormal to the square of their float32 error (V^T V in float64; the small
+//       correction V (V^T V - I) / 2 in float32).
 // Every sum whose rounding could change a decision (the norms of the Gram matrices, the
 // stopping sums) is taken over 128 fixed partial sums, so the result does not depend on
 // the block size (128 or 256 threads: a launch parameter).
-// Float64 work: n^2 per decisive candidate plus 2 n r^2, against 3 n^3 in eig_mixed_kernel.
-// Shared memory: buffer 1 holds A (float32, nn x (nn+1)) and later the Newton-Schulz
-// matrix (float64, packed lower triangle); buffer 2 holds Vt (float32, nn x (nn+4)) and
+// Float64 work: n^2 per decisive candidate plus n r^2 / 2, against 3 n^3 in eig_mixed_kernel.
+// Shared memory: buffer 1 holds A (float32, nn x (nn+1)) and later V^T V - I (float32,
+// packed lower triangle); buffer 2 holds Vt (float32, nn x (nn+4)) and
 // later a few new rows of the kept columns; then the step's task tables.
 constexpr int kKeptRows = 4;
 constexpr int kFixedParts = 128;
@@ -1084,11 +1085,11 @@ __global__ void __launch_bounds__(256) eig_mixed_kept_kernel(const EigTask* __re
   // A = the normalised sum (float32), zero padding, symmetrised; Vt = I
   for (int e = tid; e < nn * la; e += nt) {
     const int a = e / la, b = e - a * la;
-    double v = 0.0;
+    float v = 0.f;
     if (a < n && b < n)
       for (int m = 0; m < 3; ++m)
-        if (s_inv[m] > 0.0) v += ld<double>(view(ar, t.g[m]), (int64_t)act[a] * t.n_pad + act[b]) * s_inv[m];
-    A[e] = (float)v;
+        if (s_inv[m] > 0.0) v = fmaf(ld<float>(view(ar, t.g[m]), (int64_t)act[a] * t.n_pad + act[b]), (float)s_inv[m], v);
+    A[e] = v;
   }
   for (int e = tid; e < nn * lv; e += nt) Vt[e] = (e / lv == e % lv) ? 1.f : 0.f;
   __syncthreads();
@@ -1289,9 +1290,11 @@ __global__ void __launch_bounds__(256) eig_mixed_kept_kernel(const EigTask* __re
   }
   __syncthreads();
   if (rank > 0) {
-    // the Newton-Schulz matrix (3 I - V^T V) / 2, symmetric: lower triangle, packed, in
-    // buffer 1 (A is no longer read)
-    double* T = reinterpret_cast<double*>(esm);
+    // the Newton-Schulz step V <- V (3 I - V^T V) / 2 = V - V E / 2 with E = V^T V - I:
+    // E (~1e-6: the float32 rotations' drift) is summed in float64 and kept in float32
+    // (absolute error ~1e-13), so that V E can be formed in float32; E is symmetric:
+    // lower triangle, packed, in buffer 1 (A is no longer read)
+    float* E = reinterpret_cast<float*>(esm);
     for (int e = tid; e < rank * rank; e += nt) {
       const int i = e / rank, j = e - i * rank;
       if (j > i) continue;
@@ -1307,26 +1310,26 @@ __global__ void __launch_bounds__(256) eig_mixed_kept_kernel(const EigTask* __re
         const double* r0 = out + (int64_t)act[a] * ko;
         a0 = fma(r0[i], r0[j], a0);
       }
-      T[i * (i + 1) / 2 + j] = (i == j ? 1.5 : 0.0) - 0.5 * (a0 + a1);
+      E[i * (i + 1) / 2 + j] = (float)((a0 + a1) - (i == j ? 1.0 : 0.0));
     }
     __syncthreads();
-    // V <- V T, a few rows at a time through buffer 2 (Vt is no longer read)
+    // V <- V - V E / 2, a few rows at a time through buffer 2 (Vt is no longer read)
     double* rowbuf = reinterpret_cast<double*>(Vt);
     for (int r0 = 0; r0 < n; r0 += kKeptRows) {
       const int na = min(kKeptRows, n - r0);
       for (int e = tid; e < na * rank; e += nt) {
         const int a = r0 + e / rank, j = e % rank;
         const double* row = out + (int64_t)act[a] * ko;
-        double s0 = 0.0, s1 = 0.0;
+        float s0 = 0.f, s1 = 0.f;
         int i = 0;
         for (; i + 1 < rank; i += 2) {
-          const double t0 = i >= j ? T[i * (i + 1) / 2 + j] : T[j * (j + 1) / 2 + i];
-          const double t1 = i + 1 >= j ? T[(i + 1) * (i + 2) / 2 + j] : T[j * (j + 1) / 2 + i + 1];
-          s0 = fma(row[i], t0, s0);
-          s1 = fma(row[i + 1], t1, s1);
+          const float e0 = i >= j ? E[i * (i + 1) / 2 + j] : E[j * (j + 1) / 2 + i];
+          const float e1 = i + 1 >= j ? E[(i + 1) * (i + 2) / 2 + j] : E[j * (j + 1) / 2 + i + 1];
+          s0 = fmaf((float)row[i], e0, s0);
+          s1 = fmaf((float)row[i + 1], e1, s1);
         }
-        if (i < rank) s0 = fma(row[i], i >= j ? T[i * (i + 1) / 2 + j] : T[j * (j + 1) / 2 + i], s0);
-        rowbuf[e] = s0 + s1;
+        if (i < rank) s0 = fmaf((float)row[i], i >= j ? E[i * (i + 1) / 2 + j] : E[j * (j + 1) / 2 + i], s0);
+        rowbuf[e] = row[j] - 0.5 * (double)(s0 + s1);
       }
       __syncthreads();
       for (int e = tid; e < na * rank; e += nt) out[(int64_t)act[r0 + e / rank] * ko + e % rank] = rowbuf[e];

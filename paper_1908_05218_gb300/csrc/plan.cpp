@@ -144,13 +144,14 @@ struct PlanBuilder {
     gemm(out, m, n, k, lda, ldb, ldc, fl, &x, 1, mref, nref);
   }
   void sum(int64_t out, int m, int n, int lda, int ldc, bool acc, const std::vector<int64_t>& mats) {
-    if (m <= 0 || n <= 0 || mats.empty()) return;
-    std::vector<Item> it;
-    for (auto a : mats) it.push_back(Item{a, 0});
+    sum(out, m, n, lda, ldc, acc, mats.data(), mats.size());
+  }
+  void sum(int64_t out, int m, int n, int lda, int ldc, bool acc, const int64_t* mats, size_t nm) {
+    if (m <= 0 || n <= 0 || nm == 0) return;
     Seg s{};
     s.out = out;
     s.first = (int32_t)P.items.size();
-    s.count = (int32_t)it.size();
+    s.count = (int32_t)nm;
     s.m = (int16_t)m;
     s.n = (int16_t)n;
     s.k = 0;
@@ -160,7 +161,7 @@ struct PlanBuilder {
     s.mref = -1;
     s.nref = -1;
     s.flags = SF_SUM | (acc ? SF_ACC : 0);
-    P.items.insert(P.items.end(), it.begin(), it.end());
+    for (size_t q = 0; q < nm; ++q) P.items.push_back(Item{mats[q], 0});
     P.segs.push_back(s);
   }
 };
@@ -176,13 +177,42 @@ struct Target {
   int64_t ssum = -1;   // tagged offset of the summed coupling (R: C's S; SUB/NL: W)
   int32_t cpos = -1;   // position of the block in C's level list (R, F, NL targets)
   bool has_nlnl = false;
-  std::vector<Item> g1;  // leaf case-1 items (V^C_i^T F_ij, F_jk V^C_k)
+};
+
+// lists of values by key in one array (CSR), filled in two passes over the same
+// sequence of (key, value): count, then put; each list keeps the order of its puts
+template <typename V>
+struct Lists {
+  std::vector<int64_t> off, cur;
+  std::vector<V> val;
+  explicit Lists(size_t nkeys = 0) : off(nkeys + 1, 0) {}
+  void count(size_t key) { ++off[key + 1]; }
+  void finish_count() {
+    for (size_t k = 1; k < off.size(); ++k) off[k] += off[k - 1];
+    val.resize((size_t)off.back());
+    cur.assign(off.begin(), off.end() - 1);
+  }
+  void put(size_t key, const V& v) { val[(size_t)cur[key]++] = v; }
+  const V* ptr(size_t key) const { return val.data() + off[key]; }
+  size_t size(size_t key) const { return (size_t)(off[key + 1] - off[key]); }
+  bool empty(size_t key) const { return off[key + 1] == off[key]; }
 };
 
 struct LevelTargets {
-  std::vector<Target> tg;
-  std::unordered_map<int64_t, int32_t> id;
+  std::vector<Target> tg;       // by row cluster i, then in order of first appearance
+  std::vector<int64_t> first;   // targets of row cluster i: [first[i], first[i + 1])
+  std::vector<int32_t> byk;     // the same ranges, ids sorted by column cluster k
   std::vector<Triple> trip;
+  Lists<Item> g1;               // leaf case-1 items by target (V^C_i^T F_ij, F_jk V^C_k)
+  int32_t find(int64_t i, int64_t k) const {
+    int64_t lo = first[i], hi = first[i + 1];
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (tg[byk[mid]].k < k) lo = mid + 1;
+      else hi = mid;
+    }
+    return (lo < first[i + 1] && tg[byk[lo]].k == k) ? byk[lo] : -1;
+  }
 };
 
 int8_t classify(const Structure& st, int l, int64_t i, int64_t k, int32_t& pos) {
@@ -201,34 +231,67 @@ int8_t classify(const Structure& st, int l, int64_t i, int64_t k, int32_t& pos) 
 void enumerate(const Structure& st, int l, LevelTargets& lt) {
   const auto& bl = st.blocks[l];
   const auto& rp = st.row_ptr[l];
-  // target ids of the current row cluster i by column cluster k (blocks are sorted by
-  // row cluster, so each i is one run of blocks); reset after each run
-  std::vector<int32_t> mark((size_t)1 << l, -1);
-  std::vector<int64_t> touched;
-  int64_t cur_i = -1;
-  for (int32_t pa = 0; pa < (int32_t)bl.size(); ++pa) {
-    int64_t i = bl[pa].t, j = bl[pa].s;
-    if (i != cur_i) {
-      for (int64_t k : touched) mark[k] = -1;
-      touched.clear();
-      cur_i = i;
-    }
-    for (int32_t pb = rp[j]; pb < rp[j + 1]; ++pb) {
-      int64_t k = bl[pb].s;
-      int32_t id = mark[k];
-      if (id < 0) {
-        id = (int32_t)lt.tg.size();
-        mark[k] = id;
-        touched.push_back(k);
-        lt.id[Structure::key(i, k)] = id;
-        Target t;
-        t.i = (int32_t)i;
-        t.k = (int32_t)k;
-        t.cls = classify(st, l, i, k, t.cpos);
-        lt.tg.push_back(t);
+  const int64_t nc = (int64_t)1 << l;
+  // each row cluster i independently (its blocks are one run, sorted by column): the
+  // targets (i, k) in order of first appearance and the triples in block order; counted
+  // in a first pass, written at their offsets in a second
+  std::vector<int64_t> ntg(nc + 1, 0), ntr(nc + 1, 0);
+  for (int pass = 0; pass < 2; ++pass) {
+#pragma omp parallel
+    {
+      std::vector<int32_t> mark((size_t)nc, -1);  // local target number by column cluster k
+      std::vector<int64_t> touched;
+#pragma omp for schedule(dynamic, 64)
+      for (int64_t i = 0; i < nc; ++i) {
+        int32_t nt = 0;
+        int64_t ntrip = 0;
+        for (int32_t pa = rp[i]; pa < rp[i + 1]; ++pa) {
+          const int64_t j = bl[pa].s;
+          for (int32_t pb = rp[j]; pb < rp[j + 1]; ++pb) {
+            const int64_t k = bl[pb].s;
+            int32_t id = mark[k];
+            if (id < 0) {
+              id = nt++;
+              mark[k] = id;
+              touched.push_back(k);
+              if (pass == 1) {
+                Target t;
+                t.i = (int32_t)i;
+                t.k = (int32_t)k;
+                t.cls = classify(st, l, i, k, t.cpos);
+                lt.tg[ntg[i] + id] = t;
+              }
+            }
+            if (pass == 1) {
+              const int32_t gid = (int32_t)(ntg[i] + id);
+              lt.trip[ntr[i] + ntrip] = {pa, pb, gid};
+              if (bl[pa].kind == KNL && bl[pb].kind == KNL) lt.tg[gid].has_nlnl = true;
+            }
+            ++ntrip;
+          }
+        }
+        for (int64_t k : touched) mark[k] = -1;
+        touched.clear();
+        if (pass == 1) {
+          int32_t* b = lt.byk.data() + ntg[i];
+          for (int32_t q = 0; q < nt; ++q) b[q] = (int32_t)(ntg[i] + q);
+          std::sort(b, b + nt, [&](int32_t x, int32_t y) { return lt.tg[x].k < lt.tg[y].k; });
+        }
+        if (pass == 0) {
+          ntg[i + 1] = nt;
+          ntr[i + 1] = ntrip;
+        }
       }
-      lt.trip.push_back({pa, pb, id});
-      if (bl[pa].kind == KNL && bl[pb].kind == KNL) lt.tg[id].has_nlnl = true;
+    }
+    if (pass == 0) {
+      for (int64_t i = 0; i < nc; ++i) {
+        ntg[i + 1] += ntg[i];
+        ntr[i + 1] += ntr[i];
+      }
+      lt.tg.assign((size_t)ntg[nc], Target());
+      lt.trip.resize((size_t)ntr[nc]);
+      lt.byk.resize((size_t)ntg[nc]);
+      lt.first = ntg;
     }
   }
 }
@@ -388,33 +451,59 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
           Q[p] = pb.alloc(AR_S, (int64_t)std::max(LS, rC(l)) * LS);   // F F^T, later F W, later V^C^T F
           Rr[p] = pb.alloc(AR_S, (int64_t)LS * std::max(LS, cC(l)));  // F^T F, later W F, later F V^C
         }
-      std::vector<std::vector<int64_t>> Ksets(nb), Isets(nb);
-      std::vector<std::vector<Item>> gF(lt.tg.size()), gZ(lt.tg.size()), gZp(lt.tg.size()), gZpp(lt.tg.size()),
-          g1(lt.tg.size());
-      std::vector<int64_t> Z(lt.tg.size(), -1), Zp(lt.tg.size(), -1), Zpp(lt.tg.size(), -1);
-      for (auto& tr : lt.trip) {
-        const Block &ba = bl[tr.pa], &bb = bl[tr.pb];
-        const Target& T = lt.tg[tr.tgt];
-        if (T.cls == TC_F) {
-          if (ba.kind == KF && bb.kind == KF) gF[tr.tgt].push_back({tA(A.F(ba.idx)), tB(B.F(bb.idx))});
-          else if (ba.kind == KF) gZ[tr.tgt].push_back({Y[tr.pa], tB(B.S(l, bb.idx)), BR(l, ba.s)});
-          else if (bb.kind == KF) gZp[tr.tgt].push_back({tA(A.S(l, ba.idx)), Yb[tr.pb], AC(l, ba.s)});
-          else gZpp[tr.tgt].push_back({T1[tr.pa], tB(B.S(l, bb.idx)), BR(l, ba.s)});
-        } else if (ba.kind == KF && bb.kind == KF) {
-          Ksets[tr.pa].push_back(Q[tr.pb]);
-          Isets[tr.pb].push_back(Rr[tr.pa]);
-          g1[tr.tgt].push_back({Q[tr.pa], Rr[tr.pb]});  // (V^C_i^T F_ij)(F_jk V^C_k) after the eig
+      Lists<int64_t> Ksets(nb), Isets(nb);
+      const size_t ntg = lt.tg.size();
+      Lists<Item> gF(ntg), gZ(ntg), gZp(ntg), gZpp(ntg), g1(ntg);
+      for (int pass = 0; pass < 2; ++pass) {
+        for (auto& tr : lt.trip) {
+          const Block &ba = bl[tr.pa], &bb = bl[tr.pb];
+          const Target& T = lt.tg[tr.tgt];
+          if (T.cls == TC_F) {
+            if (ba.kind == KF && bb.kind == KF) {
+              if (pass) gF.put(tr.tgt, {tA(A.F(ba.idx)), tB(B.F(bb.idx))});
+              else gF.count(tr.tgt);
+            } else if (ba.kind == KF) {
+              if (pass) gZ.put(tr.tgt, {Y[tr.pa], tB(B.S(l, bb.idx)), BR(l, ba.s)});
+              else gZ.count(tr.tgt);
+            } else if (bb.kind == KF) {
+              if (pass) gZp.put(tr.tgt, {tA(A.S(l, ba.idx)), Yb[tr.pb], AC(l, ba.s)});
+              else gZp.count(tr.tgt);
+            } else {
+              if (pass) gZpp.put(tr.tgt, {T1[tr.pa], tB(B.S(l, bb.idx)), BR(l, ba.s)});
+              else gZpp.count(tr.tgt);
+            }
+          } else if (ba.kind == KF && bb.kind == KF) {
+            if (pass) {
+              Ksets.put(tr.pa, Q[tr.pb]);
+              Isets.put(tr.pb, Rr[tr.pa]);
+              g1.put(tr.tgt, {Q[tr.pa], Rr[tr.pb]});  // (V^C_i^T F_ij)(F_jk V^C_k) after the eig
+            } else {
+              Ksets.count(tr.pa);
+              Isets.count(tr.pb);
+              g1.count(tr.tgt);
+            }
+          }
+        }
+        if (pass == 0) {
+          gF.finish_count();
+          gZ.finish_count();
+          gZp.finish_count();
+          gZpp.finish_count();
+          g1.finish_count();
+          Ksets.finish_count();
+          Isets.finish_count();
         }
       }
+      std::vector<int64_t> Z(lt.tg.size(), -1), Zp(lt.tg.size(), -1), Zpp(lt.tg.size(), -1);
       for (size_t q = 0; q < lt.tg.size(); ++q) {
         if (lt.tg[q].cls != TC_F) continue;
-        if (!gZ[q].empty() || !gZpp[q].empty()) Z[q] = pb.alloc(AR_S, (int64_t)LS * cB(l));
-        if (!gZp[q].empty()) Zp[q] = pb.alloc(AR_S, (int64_t)rA(l) * LS);
-        if (!gZpp[q].empty()) Zpp[q] = pb.alloc(AR_S, (int64_t)rA(l) * cB(l));
+        if (!gZ.empty(q) || !gZpp.empty(q)) Z[q] = pb.alloc(AR_S, (int64_t)LS * cB(l));
+        if (!gZp.empty(q)) Zp[q] = pb.alloc(AR_S, (int64_t)rA(l) * LS);
+        if (!gZpp.empty(q)) Zpp[q] = pb.alloc(AR_S, (int64_t)rA(l) * cB(l));
       }
       for (int64_t p = 0; p < nb; ++p) {
-        if (!Ksets[p].empty()) Wsum[p] = pb.alloc(AR_S, LS2);
-        if (!Isets[p].empty()) Wsc[p] = pb.alloc(AR_S, LS2);
+        if (!Ksets.empty(p)) Wsum[p] = pb.alloc(AR_S, LS2);
+        if (!Isets.empty(p)) Wsc[p] = pb.alloc(AR_S, LS2);
       }
       for (int64_t t = 0; t < nc; ++t) {
         G3r[t] = pb.alloc(AR_S, LS2);
@@ -441,14 +530,15 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       for (size_t q = 0; q < lt.tg.size(); ++q) {
         const Target& T = lt.tg[q];
         if (T.cls != TC_F) continue;
-        pb.gemm(tC(C.F(bl[T.cpos].idx)), LS, LS, LS, LS, LS, LS, SF_ACC, gF[q]);
-        pb.gemm(Z[q], LS, cB(l), rB(l), rB(l), cB(l), cB(l), 0, gZ[q], -1, BC(l, T.k));
-        pb.gemm(Zp[q], rA(l), LS, cA(l), cA(l), LS, LS, 0, gZp[q], AR(l, T.i));
-        pb.gemm(Zpp[q], rA(l), cB(l), rB(l), rB(l), cB(l), cB(l), 0, gZpp[q], AR(l, T.i), BC(l, T.k));
+        pb.gemm(tC(C.F(bl[T.cpos].idx)), LS, LS, LS, LS, LS, LS, SF_ACC, gF.ptr(q), gF.size(q));
+        pb.gemm(Z[q], LS, cB(l), rB(l), rB(l), cB(l), cB(l), 0, gZ.ptr(q), gZ.size(q), -1, BC(l, T.k));
+        pb.gemm(Zp[q], rA(l), LS, cA(l), cA(l), LS, LS, 0, gZp.ptr(q), gZp.size(q), AR(l, T.i));
+        pb.gemm(Zpp[q], rA(l), cB(l), rB(l), rB(l), cB(l), cB(l), 0, gZpp.ptr(q), gZpp.size(q), AR(l, T.i),
+                BC(l, T.k));
       }
       for (int64_t p = 0; p < nb && !formatted; ++p) {
-        pb.sum(Wsum[p], LS, LS, LS, LS, false, Ksets[p]);
-        pb.sum(Wsc[p], LS, LS, LS, LS, false, Isets[p]);
+        pb.sum(Wsum[p], LS, LS, LS, LS, false, Ksets.ptr(p), Ksets.size(p));
+        pb.sum(Wsc[p], LS, LS, LS, LS, false, Isets.ptr(p), Isets.size(p));
       }
       for (int64_t t = 0; t < nc && !formatted; ++t) {
         std::vector<Item> r2, c2;
@@ -520,7 +610,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         Ach[p] = Q[p];
         Bch[p] = Rr[p];
       }
-      for (size_t q = 0; q < lt.tg.size(); ++q) lt.tg[q].g1 = std::move(g1[q]);
+      lt.g1 = std::move(g1);
     } else {
       // ================================================ non-leaf level (Sec. IV)
       std::vector<int64_t> Ac(nb, -1), Bc(nb, -1);
@@ -582,9 +672,9 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         tcol[T.k].push_back({(int32_t)q, 0});
       }
       auto child_ssum = [&](const Target& T, int a, int b) {
-        auto it = LT[c].id.find(Structure::key(2 * T.i + a, 2 * T.k + b));
-        if (it == LT[c].id.end()) throw Error(H2_EINTERNAL, "missing child target");
-        return LT[c].tg[it->second].ssum;
+        const int32_t id = LT[c].find(2 * T.i + a, 2 * T.k + b);
+        if (id < 0) throw Error(H2_EINTERNAL, "missing child target");
+        return LT[c].tg[id].ssum;
       };
       for (int64_t t = 0; t < nc && !formatted; ++t) {
         if (!trow[t].empty()) {
@@ -726,8 +816,9 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         for (int a = 0; a < 2; ++a) {
           std::vector<Item> it;
           for (int b = 0; b < 2; ++b) {
-            auto f = LT[c].id.find(Structure::key(2 * T.i + a, 2 * T.k + b));
-            it.push_back({LT[c].tg[f->second].ssum, tCb(C.Ec(l, T.k) + (int64_t)b * hc * cC(l)), CC(c, 2 * T.k + b)});
+            const int32_t f = LT[c].find(2 * T.i + a, 2 * T.k + b);
+            if (f < 0) throw Error(H2_EINTERNAL, "missing child target");
+            it.push_back({LT[c].tg[f].ssum, tCb(C.Ec(l, T.k) + (int64_t)b * hc * cC(l)), CC(c, 2 * T.k + b)});
           }
           pb.gemm(Mt[q] + (int64_t)a * hr * cC(l), hr, cC(l), hc, hc, cC(l), cC(l), SF_CB, it, CR(c, 2 * T.i + a),
                   CC(l, T.k));
@@ -754,7 +845,9 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
     // ---- couplings (Eq. leafcoup_simple / nonleafcoup_simple), summed per target in
     // one segment: case-1 (leaf: (V^C^T F)(F V^C)), case-2/4 (Ahat SBP), case-3 (PAS Bhat);
     // above the leaf level case-1 (E^C^T (M E^C)) is a separate first pass
-    // the items of each target, in one array: case-1 first, then the triples in order
+    // the items of each target: case-1 first, then its triples in order.  The triples
+    // are grouped by target (a stable counting sort); the targets' segments and items are
+    // then written in parallel, in the order one gemm call per target would give
     const size_t ntg = lt.tg.size();
     auto counted = [&](const Triple& tr) {
       const Block &ba = bl[tr.pa], &bb = bl[tr.pb];
@@ -763,24 +856,15 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       if (ba.kind == KF && bb.kind == KF) return false;  // case-1 (leaf), above
       return true;
     };
-    std::vector<int64_t> coff(ntg + 1, 0);
-    for (size_t q = 0; q < ntg; ++q)
-      if (leaf && lt.tg[q].cls != TC_F) coff[q + 1] += (int64_t)lt.tg[q].g1.size();
+    std::vector<int64_t> toff(ntg + 1, 0);  // counted triples per target
     for (auto& tr : lt.trip)
-      if (counted(tr)) ++coff[tr.tgt + 1];
-    for (size_t q = 0; q < ntg; ++q) coff[q + 1] += coff[q];
-    std::vector<Item> cpl((size_t)coff[ntg]);
-    std::vector<int64_t> cur(coff.begin(), coff.end() - 1);
-    for (size_t q = 0; q < ntg; ++q)
-      if (leaf && lt.tg[q].cls != TC_F)
-        for (const Item& x : lt.tg[q].g1) cpl[cur[q]++] = Item(x.a, x.b, -1, LS, cC(l), LS);
-    for (auto& tr : lt.trip) {
-      if (!counted(tr)) continue;
-      const Block &ba = bl[tr.pa], &bb = bl[tr.pb];
-      if (bb.kind == KR)  // case-2, case-4
-        cpl[cur[tr.tgt]++] = Item(Ahat[l][tr.pa], SBP[tr.pb], BR(l, ba.s), rB(l), cC(l), rB(l));
-      else  // case-3
-        cpl[cur[tr.tgt]++] = Item(PAS[tr.pa], Bhat[l][tr.pb], AC(l, ba.s), cA(l), cC(l), cA(l));
+      if (counted(tr)) ++toff[tr.tgt + 1];
+    for (size_t q = 0; q < ntg; ++q) toff[q + 1] += toff[q];
+    std::vector<int32_t> tord((size_t)toff[ntg]);
+    {
+      std::vector<int64_t> cur(toff.begin(), toff.end() - 1);
+      for (int32_t x = 0; x < (int32_t)lt.trip.size(); ++x)
+        if (counted(lt.trip[x])) tord[cur[lt.trip[x].tgt]++] = x;
     }
     const int kmax = std::max(std::max(leaf ? LS : 0, rB(l)), cA(l));
     if (!leaf) {
@@ -794,10 +878,60 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       pb.end("coup", l);
     }
     pb.begin();
-    for (size_t q = 0; q < ntg; ++q)
-      if (lt.tg[q].cls != TC_F)
-        pb.gemm(lt.tg[q].ssum, rC(l), cC(l), kmax, kmax, cC(l), cC(l), SF_ACC, cpl.data() + coff[q],
-                (size_t)(coff[q + 1] - coff[q]), CR(l, lt.tg[q].i), CC(l, lt.tg[q].k));
+    {
+      const int cm = rC(l), cn = cC(l);
+      // a segment per target with items (gemm's rules: no segment for empty sums)
+      std::vector<int64_t> sidx(ntg + 1, 0), ioff(ntg + 1, 0);
+      for (size_t q = 0; q < ntg; ++q) {
+        const int64_t cnt = lt.tg[q].cls == TC_F
+                                ? 0
+                                : (leaf ? (int64_t)lt.g1.size(q) : 0) + (toff[q + 1] - toff[q]);
+        const bool emit = cnt > 0 && cm > 0 && cn > 0 && kmax > 0;
+        sidx[q + 1] = sidx[q] + (emit ? 1 : 0);
+        ioff[q + 1] = ioff[q] + (emit ? cnt : 0);
+      }
+      const size_t s0 = P.segs.size(), i0 = P.items.size();
+      if ((int64_t)i0 + ioff[ntg] > INT32_MAX) throw Error(H2_ENOMEM, "plan too large");
+      P.segs.resize(s0 + (size_t)sidx[ntg]);
+      P.items.resize(i0 + (size_t)ioff[ntg]);
+      int64_t fl = 0;
+#pragma omp parallel for schedule(dynamic, 1024) reduction(+ : fl)
+      for (int64_t q = 0; q < (int64_t)ntg; ++q) {
+        if (sidx[q + 1] == sidx[q]) continue;
+        const Target& T = lt.tg[q];
+        Item* it = P.items.data() + i0 + ioff[q];
+        int64_t n = 0;
+        if (leaf)
+          for (size_t x = 0; x < lt.g1.size(q); ++x) {
+            const Item& g = lt.g1.ptr(q)[x];
+            it[n++] = Item(g.a, g.b, -1, LS, cn, LS);
+          }
+        for (int64_t y = toff[q]; y < toff[q + 1]; ++y) {
+          const Triple& tr = lt.trip[tord[y]];
+          const Block &ba = bl[tr.pa], &bb = bl[tr.pb];
+          if (bb.kind == KR)  // case-2, case-4
+            it[n++] = Item(Ahat[l][tr.pa], SBP[tr.pb], BR(l, ba.s), rB(l), cn, rB(l));
+          else  // case-3
+            it[n++] = Item(PAS[tr.pa], Bhat[l][tr.pb], AC(l, ba.s), cA(l), cn, cA(l));
+        }
+        Seg sg{};
+        sg.out = T.ssum;
+        sg.first = (int32_t)(i0 + ioff[q]);
+        sg.count = (int32_t)n;
+        sg.m = (int16_t)cm;
+        sg.n = (int16_t)cn;
+        sg.k = (int16_t)kmax;
+        sg.lda = (int16_t)kmax;
+        sg.ldb = (int16_t)cn;
+        sg.ldc = (int16_t)cn;
+        sg.mref = CR(l, T.i);
+        sg.nref = CC(l, T.k);
+        sg.flags = SF_ACC;
+        P.segs[s0 + sidx[q]] = sg;
+        for (int64_t x = 0; x < n; ++x) fl += 2LL * cm * cn * (it[x].kpad ? it[x].kpad : kmax);
+      }
+      P.flops += fl;
+    }
     pb.end("coup", l);
     pb.close_memset(zG, g);
     pb.close_memset(zS, AR_S);
