@@ -265,7 +265,7 @@ void launch_gemm(const Seg* d_segs, const Item* d_items, int64_t first, int64_t 
                  int maxn, int maxdim, bool fp32, void* stream, int variant = 0);
 // launch configurations the autotuner tries per GEMM launch group: CUDA-core kernels
 // {column slices per CTA, whole segment per CTA}, tensor-core kernel {4, 2, 1} CTAs per SM
-constexpr int kGemmVariants = 2, kMmaVariants = 3, kEigVariants = 3, kTuneCandidates = 3;
+constexpr int kGemmVariants = 2, kMmaVariants = 3, kEigVariants = 4, kTuneCandidates = 4;
 // the same segments on the tensor cores, 3xTF32 split products (mma.cu); maxm / maxn bound
 // the segments' padded dims; err receives 1 if a bounded wait gave up; variant: launch
 // configuration (k per stage, CTAs per SM; results identical for all)
@@ -284,7 +284,7 @@ void launch_to_f32(const double* src, float* dst, int64_t n, void* stream);
 // back before the calling stream is destroyed
 void prepare_eig_streams(void* stream);
 void release_eig_streams(void* stream);
-// variant: which size tiers run on 128 threads instead of 256 (results identical for all)
+// variant: the threads per size tier (64, 128 or 256; results identical for all)
 void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const Arenas* d_ars, double eps,
                       int trunc, int max_npad, int variant, void* stream);
 void launch_permute(const double* src, double* dst, const int64_t* user, int64_t rows, int64_t n,

@@ -1439,14 +1439,19 @@ void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const
     // the level's padded size comes from the rank caps; the actual sizes (children's
     // ranks) are only known on the device and are mostly far smaller, so tasks are
     // launched in size tiers, each with the shared memory of its largest size (more
-    // CTAs per SM for the small ones).  Variants:
-    // tiers up to 48 / 64 / 96 run on 128 threads (256 above); results are identical
-    const int small = variant == 1 ? 64 : (variant == 2 ? kMixMax : 48);
+    // CTAs per SM for the small ones).  Threads per tier by variant (results are
+    // identical): 0: 128 up to 48, 256 above; 1: 128 up to 64; 2: 64 up to 32, 128 up
+    // to 64; 3: 64 up to 32, 128 up to 48
+    auto threads = [&](int h) {
+      if (variant >= 2 && h <= 32) return 64;
+      if (h <= 48 || (h <= 64 && (variant == 1 || variant == 2))) return 128;
+      return 256;
+    };
     const int top = round4(max_npad);
     // a level with fewer tasks than a few CTAs per SM is one launch: its tiers would run
     // one after the other, each as long as its slowest task
     if (count < 4 * 152) {
-      eig_mixed_kept_kernel<<<(unsigned)count, top <= small ? 128 : 256, eig_kept_smem(top), (cudaStream_t)stream>>>(
+      eig_mixed_kept_kernel<<<(unsigned)count, threads(top), eig_kept_smem(top), (cudaStream_t)stream>>>(
           d_eigs, first, ar, eps, trunc, -1, top);
       g_launches += 1;
       return;
@@ -1464,8 +1469,8 @@ void launch_eig_mixed(const EigTask* d_eigs, int64_t first, int64_t count, const
           st = ts->s[ti];
           cudaStreamWaitEvent(st, ts->fork, 0);
         }
-        eig_mixed_kept_kernel<<<(unsigned)count, h <= small ? 128 : 256, eig_kept_smem(h), st>>>(d_eigs, first, ar,
-                                                                                                 eps, trunc, lo, h);
+        eig_mixed_kept_kernel<<<(unsigned)count, threads(h), eig_kept_smem(h), st>>>(d_eigs, first, ar, eps, trunc,
+                                                                                    lo, h);
         g_launches += 1;
         if (ts) {
           cudaEventRecord(ts->join[ti], st);

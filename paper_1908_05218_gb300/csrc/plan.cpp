@@ -308,6 +308,21 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
   const bool cplx = A.cplx;
   P.cplx = cplx;
   C.cplx = cplx;
+  {
+    // room for the program up front (the arrays reach GBs at N = 1M: growing them by
+    // reallocation copies them several times): about 1.5 items per triple (i, j, k) and
+    // 18 segments per block on the cube-array workloads; the estimate only sizes the
+    // reservation
+    int64_t trip = 0, nblk = 0;
+    for (int l = 0; l <= L; ++l) {
+      const auto& rp = st.row_ptr[l];
+      const auto& cp = st.col_ptr[l];
+      for (int64_t j = 0; j < ((int64_t)1 << l); ++j) trip += (int64_t)(cp[j + 1] - cp[j]) * (rp[j + 1] - rp[j]);
+      nblk += (int64_t)st.blocks[l].size();
+    }
+    P.items.reserve(P.items.size() + (size_t)(trip + trip / 2 + 16 * nblk));
+    P.segs.reserve(P.segs.size() + (size_t)(20 * nblk));
+  }
   // caps of C: leaf LS, non-leaf min(2 K[l+1], cap) (no cap in full mode), 0 above l_min;
   // each rounded up to a multiple of four for storage
   const bool formatted = prm.trunc == H2_TRUNC_FORMATTED;
@@ -632,8 +647,8 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
             int32_t cp = st.find(c, 2 * b.t + a, 2 * b.s + bb);
             if (cp < 0) throw Error(H2_EINTERNAL, "missing child block");
             pb.sum(Ac[p] + (int64_t)a * hr * 2 * rB(c) + (int64_t)bb * rB(c), hr, rB(c), rB(c), 2 * rB(c), false,
-                   {Ahat[c][cp]});
-            pb.sum(Bc[p] + (int64_t)a * cA(c) * gc + (int64_t)bb * hc, cA(c), hc, hc, gc, false, {Bhat[c][cp]});
+                   &Ahat[c][cp], 1);
+            pb.sum(Bc[p] + (int64_t)a * cA(c) * gc + (int64_t)bb * hc, cA(c), hc, hc, gc, false, &Bhat[c][cp], 1);
           }
       }
       pb.end("collect", l);
@@ -671,11 +686,22 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         trow[T.i].push_back({(int32_t)q, 0});
         tcol[T.k].push_back({(int32_t)q, 0});
       }
-      auto child_ssum = [&](const Target& T, int a, int b) {
-        const int32_t id = LT[c].find(2 * T.i + a, 2 * T.k + b);
-        if (id < 0) throw Error(H2_EINTERNAL, "missing child target");
-        return LT[c].tg[id].ssum;
-      };
+      // the children's summed couplings S_{ia,kb} of each such target, looked up once
+      std::vector<int64_t> css(lt.tg.size() * 4, -1);
+      int missing = 0;
+#pragma omp parallel for schedule(dynamic, 1024) reduction(+ : missing)
+      for (int64_t q = 0; q < (int64_t)lt.tg.size(); ++q) {
+        const Target& T = lt.tg[q];
+        if (!T.has_nlnl || T.cls == TC_NL) continue;
+        for (int a = 0; a < 2; ++a)
+          for (int b = 0; b < 2; ++b) {
+            const int32_t id = LT[c].find(2 * T.i + a, 2 * T.k + b);
+            if (id < 0) ++missing;
+            else css[q * 4 + a * 2 + b] = LT[c].tg[id].ssum;
+          }
+      }
+      if (missing) throw Error(H2_EINTERNAL, "missing child target");
+      auto child_ssum = [&](int32_t q, int a, int b) { return css[(size_t)q * 4 + a * 2 + b]; };
       for (int64_t t = 0; t < nc && !formatted; ++t) {
         if (!trow[t].empty()) {
           G1r[t] = pb.alloc(AR_S, (int64_t)gr * gr);
@@ -684,7 +710,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
               std::vector<Item> it;
               for (auto& tq : trow[t])
                 for (int b = 0; b < 2; ++b)
-                  it.push_back({child_ssum(lt.tg[tq.first], a, b), child_ssum(lt.tg[tq.first], a2, b),
+                  it.push_back({child_ssum(tq.first, a, b), child_ssum(tq.first, a2, b),
                                 CC(c, 2 * lt.tg[tq.first].k + b)});
               pb.gemm(G1r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr, hr, hr, hc, hc, hc, gr, SF_TB | SF_CB, it,
                       CR(c, 2 * t + a), CR(c, 2 * t + a2));
@@ -697,7 +723,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
               std::vector<Item> it;
               for (auto& tq : tcol[t])
                 for (int a = 0; a < 2; ++a)
-                  it.push_back({child_ssum(lt.tg[tq.first], a, b), child_ssum(lt.tg[tq.first], a, b2),
+                  it.push_back({child_ssum(tq.first, a, b), child_ssum(tq.first, a, b2),
                                 CR(c, 2 * lt.tg[tq.first].i + a)});
               pb.gemm(G1c[t] + (int64_t)b * hc * gc + (int64_t)b2 * hc, hc, hc, hr, hc, hc, gc, SF_TA | SF_CB, it,
                       CC(c, 2 * t + b), CC(c, 2 * t + b2));

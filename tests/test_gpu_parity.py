@@ -423,8 +423,9 @@ def test_tensor_core_product_is_deterministic_and_tracks_float32(lib, n):
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
 def test_autotuned_products_equal_fixed_ones(lib, prec):
     # h2_opts.autotune: the first products of a program try the candidate launch
-    # configurations of every GEMM launch group and then keep the fastest; every
-    # candidate sums each output in the same order, so all products equal the untuned one
+    # configurations of every GEMM and mixed eigen launch group and then keep the
+    # fastest; every candidate sums each output in the same order, so all products equal
+    # the untuned one
     w, leaf, eta, A = oracle_case("cubes_2048_invr2")
     ga = lib.h2_import(w.points, leaf, eta, pack(A))
     p = {"fp64": lib.FP64, "fp32": lib.MIXED_FP32, "tf32x3": lib.MIXED_TF32X3}[prec]
