@@ -253,7 +253,7 @@ PRECISIONS = {"fp64": lambda lib: lib.FP64, "mixed": lambda lib: lib.MIXED_FP32,
               "tf32x3": lambda lib: lib.MIXED_TF32X3}
 DTYPES = {"fp64": "f64", "mixed": "f32+f64", "tf32x3": "tf32x3+f64"}
 KERNELS = {"fp64": "seg_gemm_kernel<double>", "mixed": "seg_gemm32_kernel", "tf32x3": "seg_mma_tf32x3_kernel",
-           "fp64c": "seg_zgemm_kernel"}
+           "fp64c": "seg_zgemm_kernel", "mixedc": "seg_zgemm32_kernel"}
 
 
 def trace_summary(C):
@@ -325,22 +325,23 @@ def roofline(tr, precision):
                     "CUDA-event time"}
 
 
-def side_arm(lib, A, B, eps, prec, trunc, x, y_ref, with_roofline=None):
+def side_arm(lib, A, B, eps, prec, trunc, x, y_ref, with_roofline=None, cap=None):
     """One more configuration of the same product: its first call (program built), one
     warm-up and one traced timed call; time, GB/s and Eq. error."""
     import torch
+    kw = {} if cap is None else {"rank_cap": cap}
     try:
         t0 = time.time()
-        C = A.mmp(B, eps, precision=prec, trunc=trunc)
+        C = A.mmp(B, eps, precision=prec, trunc=trunc, **kw)
         torch.cuda.synchronize()
         first = time.time() - t0
-        C = A.mmp(B, eps, precision=prec, trunc=trunc, out=C)
+        C = A.mmp(B, eps, precision=prec, trunc=trunc, out=C, **kw)
         A.trace_enable(True)
         stream = torch.cuda.current_stream()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
-        C = A.mmp(B, eps, precision=prec, trunc=trunc, out=C)
+        C = A.mmp(B, eps, precision=prec, trunc=trunc, out=C, **kw)
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
@@ -383,8 +384,10 @@ def end_to_end(lib, wa, wb, pa, pbk, eps, prec, trunc, nbytes):
 
 def sphere_main(args):
     """The variable-rank complex case (scattering, Sec. VI-B): C = A A for the Helmholtz
-    kernel on a sphere, complex float64 on the GPU, against the oracle's complex128
-    product on a 4,096-point sample of the same geometry (one core)."""
+    kernel on a sphere on the GPU (mixed: complex float32 products with the float64
+    Hermitian eigen step; or complex float64), against the oracle's complex128 product on
+    a 4,096-point sample of the same geometry (one core).  With a mixed headline the
+    line also carries the complex float64 product of the same matrices."""
     import torch
 
     from paper_1908_05218_gb300 import h2 as lib
@@ -407,11 +410,14 @@ def sphere_main(args):
     # (rank cap 128: ranks of the oscillatory kernel grow with the electrical size of the
     # coarse clusters)
     cap = 128
-    C = A.mmp(A, eps, precision=lib.FP64, rank_cap=cap)
+    if args.precision not in ("fp64", "mixed"):
+        raise SystemExit("complex products run in fp64 or mixed precision")
+    prec = PRECISIONS[args.precision](lib)
+    C = A.mmp(A, eps, precision=prec, rank_cap=cap)
     torch.cuda.synchronize()
     setup_s = time.time() - t0
     for _ in range(args.warmup):
-        C = A.mmp(A, eps, precision=lib.FP64, rank_cap=cap, out=C)
+        C = A.mmp(A, eps, precision=prec, rank_cap=cap, out=C)
     A.trace_enable(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -419,7 +425,7 @@ def sphere_main(args):
         n0 = lib.kernel_launches()
         e0.record(stream)
         for _ in range(args.steps):
-            C = A.mmp(A, eps, precision=lib.FP64, rank_cap=cap, out=C)
+            C = A.mmp(A, eps, precision=prec, rank_cap=cap, out=C)
         e1.record(stream)
         torch.cuda.synchronize()
         nk = lib.kernel_launches() - n0
@@ -431,6 +437,14 @@ def sphere_main(args):
     x = torch.from_numpy(inputs.standard_normal((n, 4), seed=1) + 1j * inputs.standard_normal((n, 4), seed=2)).cuda()
     y_ref = A.matvec(A.matvec(x))
     err = float(torch.linalg.norm(C.matvec(x) - y_ref) / torch.linalg.norm(y_ref))
+    roof = roofline(tr, "fp64c" if args.precision == "fp64" else "mixedc")
+    ranks_C, cap_hits = ic["max_rank_row"], ic["cap_hits"]
+    extras = {}
+    if args.precision != "fp64" and not args.no_extras:
+        C.destroy()
+        C = None
+        # the complex float64 product of the same matrices (one warm-up, one traced call)
+        extras["fp64"] = side_arm(lib, A, A, eps, lib.FP64, "paper", x, y_ref, with_roofline="fp64c", cap=cap)
     cpu_line = None
     if cpu and "t" in cpu:
         cpu_line = {"value": cpu["bytes"] / cpu["t"] / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
@@ -438,19 +452,22 @@ def sphere_main(args):
                     "seconds": cpu["t"]}
     elif cpu:
         cpu_line = {"error": cpu.get("error")}
-    print(json.dumps({
+    line = {
         "metric": "H2-MMP throughput, complex (bytes of A+A+C at actual ranks / product time)",
         "value": nbytes / (ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "vs_baseline": None, "dtype": "c128" if args.precision == "fp64" else "c64+c128", "data": "synthetic",
         "config": {"workload": f"{desc}: exp(-j k r)/(4 pi r), k = 2 pi; leaf {leaf}, eta {ETA}, "
                                f"eps_trunc {eps} (paper rule), eps_H2 {eps}; rank cap {cap}; C = A A",
+                   "precision": args.precision,
                    "inputs": "A, C together exceed L2 (no flush needed)", "parallelism": "replicas"},
-        "mmp_s": ms * 1e-3, "rel_err_vs_exact_h2_matvecs": err, "ranks_C_max_row": ic["max_rank_row"],
-        "cap_hits": ic["cap_hits"], "bytes_alg": nbytes, "build_s": build_s, "first_product_s_incl_plan": setup_s,
+        "mmp_s": ms * 1e-3, "rel_err_vs_exact_h2_matvecs": err, "ranks_C_max_row": ranks_C,
+        "cap_hits": cap_hits, "bytes_alg": nbytes, "build_s": build_s, "first_product_s_incl_plan": setup_s,
         "phase_ms": tr["phase_ms"], "phase_ms_by_name": tr["by_phase"], "eig_ms_by_level": tr["eig_by_level"],
-        "roofline": roofline(tr, "fp64c"), "cpu_baseline": cpu_line, "gpu_launches": int(nk),
-        "clocks": clk.summary()}))
+        "roofline": roof, "cpu_baseline": cpu_line, "gpu_launches": int(nk),
+        "clocks": clk.summary()}
+    line.update(extras)
+    print(json.dumps(line))
 
 
 def main():

@@ -19,7 +19,8 @@
  *     permutes to its cluster-tree order internally.
  *   - Complex matrices (the Helmholtz kernel, or h2_import_complex): every complex
  *     number is two doubles (real part, then imaginary part) in host and device
- *     arrays; element counts count complex numbers.  Complex products run in float64.
+ *     arrays; element counts count complex numbers.  Complex products run in float64
+ *     or mixed float32 (h2_precision).
  *   - Arithmetic: see h2_precision.
  */
 #ifndef H2_GB300_H
@@ -58,10 +59,13 @@ typedef struct {
   double diag_im;      /* imaginary part of the diagonal (Helmholtz only) */
 } h2_kernel;
 
-/* Arithmetic of the product.  In every mode the normalised Gram sum, the rank decision
- * and the re-orthonormalisation of the new bases are float64, and C is stored in float64.
- * The mixed modes differ in the small matrix products (dense targets, Gram matrices,
- * projections, collects, couplings, split), which read float32 copies of A and B:  */
+/* Arithmetic of the product.  In every mode the rank decisions (float64 Rayleigh
+ * quotients of the normalised Gram sum where float32 could change them) and the
+ * re-orthonormalisation of the new bases are float64, and C is stored in float64.  The
+ * mixed modes compute the small matrix products (dense targets, Gram matrices,
+ * projections, collects, couplings, split) in float32 from float32 copies of A and B, so
+ * their Gram matrices carry float32 rounding.  Complex matrices take H2_FP64 and
+ * H2_MIXED_FP32 (complex float32 products, float64 Hermitian eigen-decomposition):  */
 typedef enum {
   H2_FP64 = 0,          /* every product, Gram matrix and eigen-decomposition in float64 */
   H2_MIXED_FP32 = 1,    /* products in float32 with float32 accumulation (CUDA cores);
@@ -214,7 +218,8 @@ h2_status h2_import(const double* points, int64_t n, int32_t leaf_size, double e
 
 /* h2_import for a complex matrix: the same arguments and layout, every array element a
  * complex number stored as two doubles (real, imaginary); kr, kc as for h2_import.  The
- * handle multiplies with complex handles only (H2_FP64).  Errors as h2_import. */
+ * handle multiplies with complex handles only (H2_FP64, H2_MIXED_FP32).  Errors as
+ * h2_import. */
 h2_status h2_import_complex(const double* points, int64_t n, int32_t leaf_size, double eta,
                             const int32_t* kr, const int32_t* kc, const double* vr,
                             const double* vc, const double* er, const double* ec,
@@ -233,7 +238,13 @@ h2_status h2_export(h2_handle h, int64_t* sizes, int32_t* kr, int32_t* kc, doubl
  * partition and gets new orthonormal nested bases truncated at eps (see h2_trunc).
  * A and B must come from the same points, leaf size and eta (else H2_ESTRUCT).
  * The product is enqueued on opts->stream; the call returns after it has been
- * launched and synchronises only to finish its setup.  *C owns its memory. */
+ * launched and synchronises only to finish its setup.  *C owns its memory.
+ * In place: when *C holds, on entry, a handle made by an earlier product with the same
+ * structure, storage caps, truncation, rank cap and precision, the product is written
+ * into it (its old contents are replaced); any other handle in *C is left untouched and
+ * replaced by a new one (the caller still owns and destroys the old).  *C must not be A
+ * or B (H2_EINVAL).  A product's output may be an operand of later products in any
+ * precision. */
 h2_status h2_mmp(h2_handle A, h2_handle B, double eps, const h2_opts* opts,
                  h2_handle* C);
 

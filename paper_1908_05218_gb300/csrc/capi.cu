@@ -255,7 +255,8 @@ void alloc_mat(Mat& m) {
 void free_mat(Mat& m) {
   if (m.arena) cudaFree(m.arena);
   if (m.arena32) cudaFree(m.arena32);
-  m.arena32 = nullptr;
+  if (m.bases32) cudaFree(m.bases32);
+  m.arena32 = m.bases32 = nullptr;
   if (m.d_kr) cudaFree(m.d_kr);
   for (void* p : m.extra_allocs) cudaFree(p);
   m.arena = nullptr;
@@ -628,7 +629,9 @@ void run_plan(const Plan& P, const ArenaSet& ar, const Arenas* d_ars, const MmpP
     } else if (L.kind == Launch::GEMM) {
       const int v = choice ? choice[li] : 0;
       if (tune_ev) cuda_check(cudaEventRecord((cudaEvent_t)tune_ev[2 * li], (cudaStream_t)stream), "event");
-      if (P.cplx)
+      if (P.cplx && is_mixed(prm.precision))
+        launch_zgemm32(P.d_segs, P.d_items, L.first, L.count, d_ars, L.aux, stream);
+      else if (P.cplx)
         launch_zgemm(P.d_segs, P.d_items, L.first, L.count, d_ars, L.aux, stream);
       else if (prm.precision == H2_MIXED_TF32X3)
         launch_gemm_mma(P.d_segs, P.d_items, L.first, L.count, d_ars, L.aux2, L.aux, ar.err, v % kMmaVariants,
@@ -962,12 +965,14 @@ struct Prepared {
 
 Prepared prepare_product(h2_handle A, h2_handle B, double eps, const h2_opts& o, h2_handle existing) {
   Prepared pr;
-    if (o.trunc != H2_TRUNC_FULL && o.trunc != H2_TRUNC_FORMATTED && !(eps > 0 && eps < 1))
+  if (o.trunc != H2_TRUNC_FULL && o.trunc != H2_TRUNC_FORMATTED && !(eps > 0 && eps < 1))
     throw Error(H2_EINVAL, "eps must lie in (0, 1)");
+  if (existing && (existing == A || existing == B))
+    throw Error(H2_EINVAL, "the output handle must not be an operand of the product");
   if (!same_structure(*A->m.st, *B->m.st)) throw Error(H2_ESTRUCT, "A and B have different trees or partitions");
   if (A->m.cplx != B->m.cplx) throw Error(H2_EINVAL, "A and B must both be real or both complex");
-  if (A->m.cplx && o.precision != H2_FP64)
-    throw Error(H2_EUNSUPPORTED, "complex products run in float64 (H2_FP64) only");
+  if (A->m.cplx && o.precision != H2_FP64 && o.precision != H2_MIXED_FP32)
+    throw Error(H2_EUNSUPPORTED, "complex products run in float64 or mixed float32 (H2_FP64, H2_MIXED_FP32)");
   MmpParams prm{eps, o.trunc, o.rank_cap, o.precision, o.norm, o.autotune};
   // plan cache, process-wide
   PlanKey key{A->m.st.get(), A->m.Kr, A->m.Kc, B->m.Kr, B->m.Kc, o.trunc, o.rank_cap, o.precision, A->m.cplx};
@@ -1002,7 +1007,7 @@ Prepared prepare_product(h2_handle A, h2_handle B, double eps, const h2_opts& o,
                                 is_mixed(o.precision) ? probe.off_S[0] : 0};
       validate_plan(ent->plan, sizes);
     }
-    upload_plan(ent->plan, A->m.cplx ? 2 * sizeof(double) : (is_mixed(o.precision) ? sizeof(float) : sizeof(double)),
+    upload_plan(ent->plan, (A->m.cplx ? 2 : 1) * (is_mixed(o.precision) ? sizeof(float) : sizeof(double)),
                 false);
     std::lock_guard<std::mutex> lk(g_cache_mu);
     g_plans.push_back({key, ent});
@@ -1035,6 +1040,7 @@ Prepared prepare_product(h2_handle A, h2_handle B, double eps, const h2_opts& o,
   }
   out->m.stream = o.stream;
   out->m.ranks_on_host = false;
+  out->m.arena32_stale = true;  // this product rewrites C's arena
   cudaStream_t s = (cudaStream_t)o.stream;
   cuda_check(cudaEventRecord(out->ev0, s), "event");
   cuda_check(cudaMemsetAsync(out->m.arena, 0, out->m.arena_elems * out->m.esize(), s), "zero C");
@@ -1042,19 +1048,27 @@ Prepared prepare_product(h2_handle A, h2_handle B, double eps, const h2_opts& o,
   ArenaSet ar;
   const bool mixed = is_mixed(o.precision);
   if (mixed) {
+    const int w = A->m.cplx ? 2 : 1;  // floats per element
     for (h2_matrix* h : {A, B}) {
-      if (!h->m.arena32) {
-        h->m.arena32 = (float*)dmalloc(h->m.arena_elems * sizeof(float));
-        launch_to_f32(h->m.arena, h->m.arena32, h->m.arena_elems, o.stream);
+      // the float copy of the whole arena: made on first use, made again when a product
+      // has rewritten the arena since (a product's output used as an input)
+      if (!h->m.arena32 || h->m.arena32_stale) {
+        if (!h->m.arena32) h->m.arena32 = (float*)dmalloc(h->m.arena_elems * w * sizeof(float));
+        launch_to_f32(h->m.arena, h->m.arena32, h->m.arena_elems * w, o.stream);
         cuda_check(cudaGetLastError(), "convert to float");
+        h->m.arena32_stale = false;
       }
     }
     ar.p[AR_A] = A->m.arena32;
     ar.p[AR_B] = B->m.arena32;
-    if (!out->m.arena32) out->m.arena32 = (float*)dmalloc(std::max<int64_t>(1, out->m.off_S[0]) * sizeof(float));
-    ar.p[AR_X] = out->m.arena32;  // float copy of C's bases, written by the eigen step
+    if (!out->m.bases32)
+      out->m.bases32 = (float*)dmalloc(std::max<int64_t>(1, out->m.off_S[0]) * w * sizeof(float));
+    ar.p[AR_X] = out->m.bases32;  // float copy of C's bases, written by the eigen step
     ar.f32 = (1u << AR_A) | (1u << AR_B) | (1u << AR_P) | (1u << AR_G0) | (1u << AR_G1) | (1u << AR_S) |
              (1u << AR_X);
+    if (A->m.cplx)  // complex: float2 in the float arenas, double2 in C
+      ar.c16 = (1u << AR_A) | (1u << AR_B) | (1u << AR_C) | (1u << AR_P) | (1u << AR_G0) | (1u << AR_G1) |
+               (1u << AR_S) | (1u << AR_X);
   } else {
     ar.p[AR_A] = A->m.arena;
     ar.p[AR_B] = B->m.arena;

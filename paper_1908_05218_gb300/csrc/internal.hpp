@@ -74,6 +74,8 @@ struct Mat {
   int32_t* d_kr = nullptr;  // device ranks, indexed by Structure::node
   int32_t* d_kc = nullptr;
   float* arena32 = nullptr;  // float copy of the arena (mixed precision), made on first use
+  bool arena32_stale = false;  // the arena was rewritten (by a product) since arena32 was made
+  float* bases32 = nullptr;  // float copy of the bases written by a mixed product into this matrix
   std::vector<int32_t> h_kr, h_kc;  // host copies
   bool ranks_on_host = false;
   unsigned long long* d_cap = nullptr;  // device counter of ranks cut at the cap
@@ -237,8 +239,10 @@ struct ArenaSet {
   unsigned long long* cap_hits = nullptr;
   double* eig_scratch = nullptr;        // this product's eigen work space (Plan::scratch_elems)
   unsigned int* err = nullptr;          // device word: nonzero when a bounded device wait gave up
-  uint32_t c16 = 0;                     // arenas of complex float64 elements (bit per arena)
-  size_t esize(int a) const { return ((c16 >> a) & 1) ? 16 : (((f32 >> a) & 1) ? 4 : 8); }
+  uint32_t c16 = 0;                     // arenas of complex elements (bit per arena; with f32: float2)
+  size_t esize(int a) const {  // complex: 16 (float64) or 8 (float32); real: 8 or 4
+    return ((c16 >> a) & 1) ? (((f32 >> a) & 1) ? 8 : 16) : (((f32 >> a) & 1) ? 4 : 8);
+  }
 };
 // The same table as the kernels read it, in device memory: one per product instance of
 // a launch (segments and eigen tasks carry the instance index).
@@ -297,6 +301,9 @@ void cuda_check(int err, const char* what);
 // complex float64 kernels (zkernels.cu)
 void launch_zgemm(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const Arenas* d_ars, int maxn,
                   void* stream);
+// the same in complex float32 (mixed product: float2 operands, float2 or double2 output)
+void launch_zgemm32(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const Arenas* d_ars,
+                    int maxn, void* stream);
 int64_t zeig_scratch_elems(int max_npad, int64_t count);  // float64 words of eigen work space
 void launch_zeig(const EigTask* d_eigs, int64_t first, int64_t count, const Arenas* d_ars, double eps, int trunc,
                  int norm, int max_npad, double* scratch, void* stream);

@@ -1021,7 +1021,7 @@ __global__ void __launch_bounds__(256) eig_mixed_kept_kernel(const EigTask* __re
   __shared__ double rq[kMixMax], rqs[kMixMax];
   __shared__ float lam32[kMixMax];
   __shared__ double s_inv[3];
-  __shared__ int s_n, s_nc, s_rank;
+  __shared__ int s_nc, s_rank;
   const EigTask t = tasks[first + blockIdx.x];
   const Arenas* ar = ars + t.inst;  // the task's product instance
   int32_t* const kr = ar->kr;
@@ -1029,22 +1029,15 @@ __global__ void __launch_bounds__(256) eig_mixed_kept_kernel(const EigTask* __re
   unsigned long long* const cap_hits = ar->cap_hits;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, w = tid >> 5, nw = nt >> 5;
   int32_t* ranks = t.col ? kc : kr;
-  if (tid == 0) {
-    int n = 0;
-    if (t.child1 < 0) {
-      for (int a = 0; a < t.nleaf; ++a) act[n++] = a;
-    } else {
-      const int k1 = ranks[t.child1], k2 = ranks[t.child2];
-      for (int a = 0; a < k1; ++a) act[n++] = a;
-      for (int a = 0; a < k2; ++a) act[n++] = t.half + a;
-    }
-    s_n = n;
-  }
-  __syncthreads();
-  const int n = s_n, nn = round4(n), np = nn / 2, la = nn + 1, lv = nn + 4;
-  // one launch per size tier (nn_lo, nn_hi], shared memory sized for nn_hi: a task
-  // whose actual size is outside the tier is done by another launch
+  // the task's size first: one launch per size tier (nn_lo, nn_hi], shared memory sized
+  // for nn_hi; a task whose size is outside the tier returns at once (another launch
+  // does it)
+  const int k1 = t.child1 < 0 ? t.nleaf : ranks[t.child1], k2 = t.child1 < 0 ? 0 : ranks[t.child2];
+  const int n = k1 + k2, nn = round4(n), np = nn / 2, la = nn + 1, lv = nn + 4;
   if (nn <= nn_lo || nn > nn_hi) return;
+  // active rows: child 1's kept rows, then child 2's (at offset half)
+  for (int a = tid; a < n; a += nt) act[a] = a < k1 ? a : t.half + (a - k1);
+  __syncthreads();
   float* A = (float*)esm;                                  // row stride la (buffer 1)
   float* Vt = (float*)(esm + eig_kept_buf1(nn_hi));        // row stride lv; 16-byte aligned rows (buffer 2)
   uint16_t* blk = (uint16_t*)(esm + eig_kept_buf1(nn_hi) + eig_kept_buf2(nn_hi));

@@ -1,10 +1,13 @@
-// Complex float64 kernels of the product for complex kernel functions (the Helmholtz
-// kernel exp(-j k r) / (4 pi r) of the scattering workloads, Sec. VI-B): the segmented
-// batched GEMM with a conjugation flag per operand, the Hermitian eigen-decomposition
-// with truncation (Sec. III-C, IV-C), and the permutations of complex vectors.
+// Complex kernels of the product for complex kernel functions (the Helmholtz kernel
+// exp(-j k r) / (4 pi r) of the scattering workloads, Sec. VI-B): the segmented batched
+// GEMM with a conjugation flag per operand (complex float64, and complex float32 for
+// the mixed product), the Hermitian eigen-decomposition with truncation (Sec. III-C,
+// IV-C; float64, reading float32 or float64 Gram matrices), and the permutations of
+// complex vectors.
 //
-// Complex numbers are double2 (x = real part, y = imaginary part); arenas of a complex
-// matrix hold double2 elements at the same offsets as a real matrix holds doubles.
+// Complex numbers are double2 / float2 (x = real part, y = imaginary part); arenas of a
+// complex matrix hold complex elements at the same offsets as a real matrix holds reals
+// (an arena's float32 bit selects float2).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,6 +39,22 @@ __device__ __forceinline__ const double2* zptr(const Arenas* a, int64_t t) {
 }
 __device__ __forceinline__ double2* zptr_w(const Arenas* a, int64_t t) {
   return (double2*)a->p[arena_idx(t)] + (t & kOffMask);
+}
+// element i of a complex matrix in float32 or float64 storage, as double2
+__device__ __forceinline__ double2 zld(const Arenas* a, int64_t t, int64_t i) {
+  const int ai = arena_idx(t);
+  if ((a->f32 >> ai) & 1) {
+    const float2 v = ((const float2*)a->p[ai] + (t & kOffMask))[i];
+    return make_double2((double)v.x, (double)v.y);
+  }
+  return ((const double2*)a->p[ai] + (t & kOffMask))[i];
+}
+__device__ __forceinline__ float2 cmul_add(float2 a, float2 b, float2 acc) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+  return acc;
 }
 
 // ------------------------------------------------------------ complex segmented GEMM
@@ -130,6 +149,110 @@ __global__ void __launch_bounds__(ZNT) seg_zgemm_kernel(const Seg* __restrict__ 
               *p = v;
             } else {
               *p = acc[i][j];
+            }
+          }
+        }
+    }
+  }
+  if (ar->flops && tid == 0 && work) atomicAdd(ar->flops, work);
+}
+
+// The same segments in complex float32 (the mixed product): every operand is float2
+// (float copies of A and B, float work regions, the float shadow of C's bases); sums
+// in float32; the output is float2 or, in C's arena, double2.
+__global__ void __launch_bounds__(ZNT) seg_zgemm32_kernel(const Seg* __restrict__ segs, const Item* __restrict__ items,
+                                                          int64_t first, const Arenas* __restrict__ ars) {
+  __shared__ float2 sA[ZK][ZPAD];
+  __shared__ float2 sB[ZK][ZPAD];
+  const Seg s = segs[first + blockIdx.x];
+  const Arenas* ar = ars + s.inst;
+  const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+  const bool ta = s.flags & SF_TA, tb = s.flags & SF_TB, accum = s.flags & SF_ACC;
+  const bool ca = s.flags & SF_CA, cb = s.flags & SF_CB;
+  const int M = bound(ar, s.mref, s.m), N = bound(ar, s.nref, s.n);
+  const int oa = arena_idx(s.out);
+  const bool out32 = (ar->f32 >> oa) & 1;
+  char* obase = ar->p[oa];
+  const int64_t ooff = s.out & kOffMask;
+  const Item* it = items + s.first;
+  unsigned long long work = 0;
+  for (int n0 = blockIdx.y * ZT; n0 < N; n0 += gridDim.y * ZT) {
+    const int nc = min(ZT, N - n0);
+    for (int m0 = 0; m0 < M; m0 += ZT) {
+      const int mc = min(ZT, M - m0);
+      float2 acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+      if (s.flags & SF_SUM) {
+        for (int q = 0; q < s.count; ++q) {
+          const float2* A = (const float2*)ar->p[arena_idx(it[q].a)] + (it[q].a & kOffMask);
+          for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) {
+              const int r = 4 * ty + i, c = 4 * tx + j;
+              if (r < mc && c < nc) {
+                const float2 v = A[(int64_t)(m0 + r) * s.lda + n0 + c];
+                acc[i][j].x += v.x;
+                acc[i][j].y += v.y;
+              }
+            }
+        }
+      } else {
+        for (int q = 0; q < s.count; ++q) {
+          const Item iq = it[q];
+          const int K = bound(ar, iq.kref, iq.kpad ? iq.kpad : s.k);
+          const float2* A = (const float2*)ar->p[arena_idx(iq.a)] + (iq.a & kOffMask);
+          const float2* B = (const float2*)ar->p[arena_idx(iq.b)] + (iq.b & kOffMask);
+          const int lda = iq.lda ? iq.lda : s.lda, ldb = iq.ldb ? iq.ldb : s.ldb;
+          for (int k0 = 0; k0 < K; k0 += ZK) {
+            const int kc = min(ZK, K - k0);
+            for (int e = tid; e < ZK * ZT; e += ZNT) {
+              const int kk = e / ZT, r = e % ZT;
+              float2 va = make_float2(0.f, 0.f), vb = make_float2(0.f, 0.f);
+              if (kk < kc && r < mc) va = ta ? A[(int64_t)(k0 + kk) * lda + m0 + r] : A[(int64_t)(m0 + r) * lda + k0 + kk];
+              if (kk < kc && r < nc) vb = tb ? B[(int64_t)(n0 + r) * ldb + k0 + kk] : B[(int64_t)(k0 + kk) * ldb + n0 + r];
+              if (ca) va.y = -va.y;
+              if (cb) vb.y = -vb.y;
+              sA[kk][r] = va;
+              sB[kk][r] = vb;
+            }
+            __syncthreads();
+            for (int kk = 0; kk < kc; ++kk) {
+              float2 a[4], b[4];
+#pragma unroll
+              for (int i = 0; i < 4; ++i) a[i] = sA[kk][4 * ty + i];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) b[j] = sB[kk][4 * tx + j];
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = cmul_add(a[i], b[j], acc[i][j]);
+            }
+            __syncthreads();
+            work += 8ull * mc * nc * kc;
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int r = 4 * ty + i, c = 4 * tx + j;
+          if (r < mc && c < nc) {
+            const int64_t o = ooff + (int64_t)(m0 + r) * s.ldc + n0 + c;
+            if (out32) {
+              float2* p = (float2*)obase + o;
+              float2 v = accum ? *p : make_float2(0.f, 0.f);
+              v.x += acc[i][j].x;
+              v.y += acc[i][j].y;
+              *p = v;
+            } else {
+              double2* p = (double2*)obase + o;
+              double2 v = accum ? *p : make_double2(0.0, 0.0);
+              v.x += (double)acc[i][j].x;
+              v.y += (double)acc[i][j].y;
+              *p = v;
             }
           }
         }
@@ -241,7 +364,7 @@ __device__ void zload_sum(const EigTask& t, const Arenas* ar, const int* act, in
     if (a < n && b < n)
       for (int m = 0; m < 3; ++m)
         if (scale[m] != 0.0) {
-          const double2 g = zptr(ar, t.g[m])[(int64_t)act[a] * t.n_pad + act[b]];
+          const double2 g = zld(ar, t.g[m], (int64_t)act[a] * t.n_pad + act[b]);
           v.x += g.x * scale[m];
           v.y += g.y * scale[m];
         }
@@ -305,9 +428,8 @@ __global__ void __launch_bounds__(256) zeig_kernel(const EigTask* __restrict__ t
   for (int m = 0; m < 3; ++m) {
     double loc = 0.0;
     if (t.g[m] >= 0) {
-      const double2* G = zptr(ar, t.g[m]);
       for (int e = tid; e < n * n; e += nt) {
-        const double2 g = G[(int64_t)act[e / n] * t.n_pad + act[e % n]];
+        const double2 g = zld(ar, t.g[m], (int64_t)act[e / n] * t.n_pad + act[e % n]);
         loc += g.x * g.x + g.y * g.y;
       }
     }
@@ -360,7 +482,13 @@ __global__ void __launch_bounds__(256) zeig_kernel(const EigTask* __restrict__ t
   __syncthreads();
   const int rank = s_rank;
   double2* out = zptr_w(ar, t.out);
-  for (int e = tid; e < t.n_pad * t.kcap; e += nt) out[e] = make_double2(0.0, 0.0);
+  // the float copy of C's new bases for the GEMMs of the mixed product (arena X mirrors
+  // C's basis region; absent in float64)
+  float2* out32 = ar->p[AR_X] ? (float2*)ar->p[AR_X] + (t.out & kOffMask) : nullptr;
+  for (int e = tid; e < t.n_pad * t.kcap; e += nt) {
+    out[e] = make_double2(0.0, 0.0);
+    if (out32) out32[e] = make_float2(0.f, 0.f);
+  }
   __syncthreads();
   // phase: the entry of largest magnitude (first such) is made real and positive
   for (int c = tid; c < rank; c += nt) {
@@ -378,7 +506,11 @@ __global__ void __launch_bounds__(256) zeig_kernel(const EigTask* __restrict__ t
     const double2 pv = V[best * lds + col];
     const double mag = sqrt(pv.x * pv.x + pv.y * pv.y);
     const double2 f = mag > 0.0 ? make_double2(pv.x / mag, -pv.y / mag) : make_double2(1.0, 0.0);
-    for (int a = 0; a < n; ++a) out[(int64_t)act[a] * t.kcap + c] = zmul(V[a * lds + col], f);
+    for (int a = 0; a < n; ++a) {
+      const double2 v = zmul(V[a * lds + col], f);
+      out[(int64_t)act[a] * t.kcap + c] = v;
+      if (out32) out32[(int64_t)act[a] * t.kcap + c] = make_float2((float)v.x, (float)v.y);
+    }
   }
 }
 
@@ -414,6 +546,18 @@ void launch_zgemm(const Seg* d_segs, const Item* d_items, int64_t first, int64_t
     const int64_t c = std::min(count - off, kMaxGrid);
     seg_zgemm_kernel<<<dim3((unsigned)c, (unsigned)gy), ZNT, 0, (cudaStream_t)stream>>>(d_segs, d_items, first + off,
                                                                                       d_ars);
+    add_kernel_launches(1);
+  }
+}
+
+void launch_zgemm32(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const Arenas* d_ars,
+                    int maxn, void* stream) {
+  const int64_t kMaxGrid = 2147483647LL;
+  int gy = std::max(1, std::min(256, (maxn + ZT - 1) / ZT));
+  for (int64_t off = 0; off < count; off += kMaxGrid) {
+    const int64_t c = std::min(count - off, kMaxGrid);
+    seg_zgemm32_kernel<<<dim3((unsigned)c, (unsigned)gy), ZNT, 0, (cudaStream_t)stream>>>(d_segs, d_items,
+                                                                                        first + off, d_ars);
     add_kernel_launches(1);
   }
 }

@@ -184,6 +184,35 @@ def test_product_is_deterministic_and_reusable(lib):
     d2 = c1.to_dense().cpu().numpy()
     np.testing.assert_array_equal(d1, d2)
     assert_entries_close(d1, oh2.to_dense(ommp.mmp(A, A, 1e-4)))
+    with pytest.raises(lib.H2Error) as ei:
+        ga.mmp(ga, 1e-4, out=ga)       # the output must not be an operand
+    assert ei.value.code == lib.H2_EINVAL
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_products_of_products(lib, prec):
+    # a product's output as an operand of later products (powers, solver iterations):
+    # D = (A A) A against the oracle's chain, and an output rewritten in place and then
+    # used again as an operand gives what fresh handles give
+    w, leaf, eta, A = oracle_case("cubes_1024")
+    p = lib.FP64 if prec == "fp64" else lib.MIXED_FP32
+    ga = lib.h2_import(w.points, leaf, eta, pack(A))
+    c = ga.mmp(ga, 1e-4, precision=p)
+    d = c.mmp(ga, 1e-4, precision=p)
+    C = ommp.mmp(A, A, 1e-4)
+    D = ommp.mmp(C, A, 1e-4)
+    if prec == "fp64":
+        assert_entries_close(d.to_dense().cpu().numpy(), oh2.to_dense(D))
+    else:
+        assert rel(d.to_dense().cpu().numpy(), oh2.to_dense(D)) < 4e-4
+    # c rewritten in place with another product, then an operand again
+    ga.mmp(c, 1e-4, precision=p)                # c as the right operand too
+    c3 = ga.mmp(ga, 1e-3, precision=p, out=c)   # in place: A A at another threshold
+    assert c3 is c
+    e1 = c.mmp(ga, 1e-4, precision=p).to_dense().cpu().numpy()
+    f = ga.mmp(ga, 1e-3, precision=p)
+    e2 = f.mmp(ga, 1e-4, precision=p).to_dense().cpu().numpy()
+    np.testing.assert_array_equal(e1, e2)
 
 
 def test_structure_mismatch_is_rejected(lib):
@@ -440,7 +469,8 @@ def test_autotuned_products_equal_fixed_ones(lib, prec):
 
 # ---------------------------------------------------------------- complex kernels
 # The Helmholtz kernel exp(-j k r) / (4 pi r) (Sec. VI-B, scattering): complex matrices,
-# complex float64 products on the GPU against the complex128 oracle.
+# complex float64 and mixed (complex float32) products on the GPU against the complex128
+# oracle.
 ZCASES = {
     # name: (points, leaf, eta, eps_h2 of A, eps_h2 of B, wavenumber)
     "sphere_640": (lambda: inputs.fibonacci_sphere(640, 1.5), 20, 1.0, 1e-5, 1e-3, 2 * math.pi),
@@ -517,5 +547,33 @@ def test_complex_build_approximates_the_helmholtz_kernel(lib):
     ref = g.matvec(g.matvec(torch.from_numpy(x).cuda())).cpu().numpy()
     assert rel(y2, ref) < math.sqrt(1e-3)
     with pytest.raises(lib.H2Error) as ei:
-        g.mmp(g, 1e-3, precision=lib.MIXED_FP32)
+        g.mmp(g, 1e-3, precision=lib.MIXED_TF32X3)
     assert ei.value.code == lib.H2_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("name,mode,eps", [("sphere_640", "paper", 1e-3), ("sphere_640", "sv", 1e-3),
+                                           ("sphere_2048_4lambda", "paper", 1e-3),
+                                           ("sphere_2048_4lambda", "sv", 1e-2)])
+def test_complex_mixed_product_against_the_oracle(lib, name, mode, eps):
+    # complex float32 products (float2 operands and sums) with the float64 Hermitian
+    # eigen-decomposition of the (float32) Gram sums: within 2 eps of the complex128
+    # oracle, no less accurate against the exact product, equal ranks wherever the
+    # oracle's decision is clear of the threshold, and reruns bitwise equal
+    pts, leaf, eta, spec, A, B = zcase(name)
+    st = {}
+    C = ommp.mmp(A, B, eps, mode, stats=st)
+    ga = lib.h2_import(pts, leaf, eta, pack(A))
+    gb = lib.h2_import(pts, leaf, eta, pack(B))
+    gm = ga.mmp(gb, eps, trunc=mode, rank_cap=96, precision=lib.MIXED_FP32)
+    assert gm.is_complex and gm.info()["cap_hits"] == 0
+    d_gpu = gm.to_dense().cpu().numpy()
+    d_orc = oh2.to_dense(C)
+    exact = oh2.to_dense(A) @ oh2.to_dense(B)
+    assert rel(d_gpu, d_orc) < 2 * eps
+    assert rel(d_gpu, exact) < 1.2 * rel(d_orc, exact) + 1e-6
+    assert clear_rank_mismatches(gm.export(), st, A.L) == []
+    e1 = gm.export()
+    gm2 = ga.mmp(gb, eps, trunc=mode, rank_cap=96, precision=lib.MIXED_FP32)
+    e2 = gm2.export()
+    for f in ("kr", "kc", "vr", "vc", "er", "ec", "s", "f"):
+        np.testing.assert_array_equal(getattr(e1, f), getattr(e2, f))
