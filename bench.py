@@ -250,10 +250,10 @@ def batched_main(args):
 
 
 PRECISIONS = {"fp64": lambda lib: lib.FP64, "mixed": lambda lib: lib.MIXED_FP32,
-              "tf32x3": lambda lib: lib.MIXED_TF32X3}
-DTYPES = {"fp64": "f64", "mixed": "f32+f64", "tf32x3": "tf32x3+f64"}
+              "tf32x3": lambda lib: lib.MIXED_TF32X3, "bf16x3": lambda lib: lib.MIXED_BF16X3}
+DTYPES = {"fp64": "f64", "mixed": "f32+f64", "tf32x3": "tf32x3+f64", "bf16x3": "bf16x3+f32+f64"}
 KERNELS = {"fp64": "seg_gemm_kernel<double>", "mixed": "seg_gemm32_kernel", "tf32x3": "seg_mma_tf32x3_kernel",
-           "fp64c": "seg_zgemm_kernel", "mixedc": "seg_zgemm32_kernel"}
+           "bf16x3": "seg_gemm32_kernel", "fp64c": "seg_zgemm_kernel", "mixedc": "seg_zgemm32_kernel"}
 
 
 def trace_summary(C):
@@ -283,11 +283,11 @@ def roofline(tr, precision):
     it runs on (float32 / float64 FMA lanes x 2 x max SM clock; for the 3xTF32 tensor-core
     kernel a third of the TF32 rate, half the measured dense BF16 rate)."""
     tot = tr["tot"]
-    peaks, src = _peaks()
+    peaks, psrc = _peaks()
     clk_hz = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     if precision == "tf32x3":
         peak = 0.5 * float(peaks["bf16_tflops"]) / 3.0
-        bound, peak_note = "tensor", f"TF32 = half the dense BF16 peak ({src}), / 3 products per split pair"
+        bound, peak_note = "tensor", f"TF32 = half the dense BF16 peak ({psrc}), / 3 products per split pair"
     elif precision in ("fp64", "fp64c"):
         peak = 152 * 2 * 2 * clk_hz / 1e12
         bound, peak_note = "alu", "152 SMs x 2 float64 FMA per clock x 2 flops x max SM clock"
@@ -309,18 +309,30 @@ def roofline(tr, precision):
     eig = None
     if tot.get("eig", [0, 0, 0])[1]:
         e_ms, e_tasks, e_n = tot["eig"]
-        eig = {"kernel": "eig_mixed_kept_kernel" if precision in ("mixed", "tf32x3") else "eig_kernel",
+        eig = {"kernel": "eig_mixed_kept_kernel" if precision in ("mixed", "tf32x3", "bf16x3") else "eig_kernel",
                "bound": "latency", "ms_per_step": e_ms, "tasks_per_step": int(e_tasks), "launches_per_step": e_n,
                "sm_us_per_task": e_ms * 1e3 * 152 / e_tasks,
                "note": "one CTA per cluster basis: normalised Gram sum, Jacobi (barrier-separated "
                        "rotation steps), truncation; no throughput peak applies"}
+    tc = None
+    if tot.get("tc", [0, 0, 0])[2]:
+        # the tensor-core coupling kernel (H2_MIXED_BF16X3): 2 m n k per item at the tile
+        # dims of the plan (the device flop counter leaves it out), three BF16 products per
+        # split pair against the dense BF16 peak
+        t_ms, t_fl, t_n = tot["tc"]
+        tpeak = float(peaks["bf16_tflops"]) / 3.0
+        t_ach = t_fl / (t_ms * 1e-3) / 1e12 if t_ms else 0.0
+        tc = {"kernel": "coup_tc_kernel", "bound": "tensor", "ms_per_step": t_ms, "launches_per_step": t_n,
+              "flops_per_step": t_fl, "achieved": t_ach, "peak": tpeak, "unit": "TFLOP/s", "frac": t_ach / tpeak,
+              "peak_note": f"dense BF16 ({psrc}) / 3 products per split pair",
+              "note": "coupling sums: 2 m n k per item at the plan's padded dims / CUDA-event time"}
     return {"bound": bound, "kernel": KERNELS[precision], "dominant": dom, "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": traffic,
             "traffic_note": ("DRAM bytes per GEMM launch: bytes per padded flop of three captured launches "
                              "(N=65,536) x this run's padded flops per GEMM launch"
                              if traffic else "no DRAM capture of this kernel source at this precision"),
             "peak_note": peak_note, "launches_per_step": tot.get("gemm", [0, 0, 0])[2], "ms_per_step": gemm_ms,
-            "executed_flops_per_step": fl, "eig": eig,
+            "executed_flops_per_step": fl, "eig": eig, "tc": tc,
             "note": "GEMM kernel: multiply-add flops executed at the actual ranks (device counter) / its "
                     "CUDA-event time"}
 
@@ -349,7 +361,7 @@ def side_arm(lib, A, B, eps, prec, trunc, x, y_ref, with_roofline=None, cap=None
         A.trace_enable(False)
         nbytes = A.info()["bytes_stored"] + B.info()["bytes_stored"] + C.info()["bytes_stored"]
         err = float(torch.linalg.norm(C.matvec(x) - y_ref) / torch.linalg.norm(y_ref))
-        out = {"trunc": trunc, "precision": {0: "fp64", 1: "mixed", 2: "tf32x3"}.get(prec, prec), "ms": ms,
+        out = {"trunc": trunc, "precision": {0: "fp64", 1: "mixed", 2: "tf32x3", 3: "bf16x3"}.get(prec, prec), "ms": ms,
                "value": nbytes / (ms * 1e-3) / 1e9, "unit": "GB/s", "rel_err_vs_exact_h2_matvecs": err,
                "first_product_s_incl_plan": first, "warmup": 1, "steps": 1, "phase_ms": tr["phase_ms"],
                "max_rank_row": C.info()["max_rank_row"]}

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libh2gb300.so")
 OBJ = os.path.join(HERE, "_build")
 
-CU = ["kernels.cu", "mma.cu", "zkernels.cu", "gbuild.cu", "capi.cu", "noalloc.cu", "transfer.cu"]
+CU = ["kernels.cu", "mma.cu", "tc.cu", "zkernels.cu", "gbuild.cu", "capi.cu", "noalloc.cu", "transfer.cu"]
 CPP = ["structure.cpp", "builder.cpp", "plan.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -178,7 +178,6 @@ h2_opts defaults(const h2_opts* o) {
     if (d.rank_cap <= 0) d.rank_cap = 48;
   }
   if (d.precision < H2_FP64 || d.precision > H2_MIXED_BF16X3) throw h2::Error(H2_EINVAL, "bad precision");
-  if (d.precision == H2_MIXED_BF16X3) throw h2::Error(H2_EUNSUPPORTED, "BF16 split products are not built yet");
   if (d.norm != H2_NORM_FROBENIUS && d.norm != H2_NORM_SPECTRAL) throw h2::Error(H2_EINVAL, "bad norm");
   if (d.autotune != 0 && d.autotune != 1) throw h2::Error(H2_EINVAL, "autotune must be 0 or 1");
   if (d.reserved != 0) throw h2::Error(H2_EINVAL, "h2_opts.reserved must be 0");
@@ -482,13 +481,30 @@ void validate_plan(const Plan& P, const int64_t sizes[kArenas]) {
     if (it == v.begin() || std::prev(it)->first + std::prev(it)->second < off + extent)
       throw Error(H2_EINTERNAL, std::string("plan access outside its allocation: ") + what);
   };
+  // an operand tile of tr rows and kp columns holding an m x n matrix (transposed: n x m)
+  auto check_tile = [&](int64_t tagged, int tr, int kp, int m, int n, bool tt, const char* what) {
+    if (tr <= 0 || tr % 8 || kp <= 0 || kp % 16) throw Error(H2_EINTERNAL, std::string("bad tile shape: ") + what);
+    if ((tt ? n : m) > tr || (tt ? m : n) > kp)
+      throw Error(H2_EINTERNAL, std::string("matrix larger than its tile: ") + what);
+    check(tagged, (int64_t)tr * kp, what);
+  };
   auto check_seg = [&](const Seg& s) {
     bool ta = s.flags & SF_TA, tb = s.flags & SF_TB;
-    check(s.out, (int64_t)(s.m - 1) * s.ldc + s.n, "segment output");
-    if (s.ldc < s.n) throw Error(H2_EINTERNAL, "segment ldc < n");
+    const bool tile = s.flags & SF_TILE, tt = s.flags & SF_TILE_T;
+    if (tile && !(s.flags & SF_SUM)) {
+      if (s.flags & SF_ACC) throw Error(H2_EINTERNAL, "tile outputs are written, not accumulated");
+      check_tile(s.out, s.trows, s.ldc, s.m, s.n, tt, "tile output");
+    } else {
+      check(s.out, (int64_t)(s.m - 1) * s.ldc + s.n, "segment output");
+      if (s.ldc < s.n) throw Error(H2_EINTERNAL, "segment ldc < n");
+    }
     for (int32_t q = s.first; q < s.first + s.count; ++q) {
       const Item& it = P.items[q];
       if (s.flags & SF_SUM) {
+        if (tile) {
+          check_tile(it.a, s.trows, s.lda, s.m, s.n, tt, "tile sum input");
+          continue;
+        }
         if (s.lda < s.n) throw Error(H2_EINTERNAL, "sum lda < n");
         check(it.a, (int64_t)(s.m - 1) * s.lda + s.n, "sum input");
         continue;
@@ -500,6 +516,21 @@ void validate_plan(const Plan& P, const int64_t sizes[kArenas]) {
         throw Error(H2_EINTERNAL, "segment leading dimension too small");
       check(it.a, ta ? (int64_t)(kp - 1) * lda + s.m : (int64_t)(s.m - 1) * lda + kp, "segment A");
       check(it.b, tb ? (int64_t)(s.n - 1) * ldb + kp : (int64_t)(kp - 1) * ldb + s.n, "segment B");
+    }
+  };
+  // a segment of the tensor-core coupling pass: items of an A tile (rp x kpad) and a B
+  // tile (np x kpad), rp / np the launch's, kpad from 16 to the launch's largest
+  auto check_tc_seg = [&](const Seg& s, const Launch& L) {
+    check(s.out, (int64_t)(s.m - 1) * s.ldc + s.n, "coupling output");
+    if (s.m <= 0 || s.n <= 0 || s.ldc < s.n || s.count <= 0 || (s.flags & (SF_SUM | SF_TILE)))
+      throw Error(H2_EINTERNAL, "bad tensor-core coupling segment");
+    if (((s.m + 7) & ~7) != L.aux2 || ((s.n + 7) & ~7) != L.aux || L.aux2 > 64 || L.aux > 64 || L.aux3 > 64)
+      throw Error(H2_EINTERNAL, "tensor-core coupling tile rows differ from the launch's");
+    for (int32_t q = s.first; q < s.first + s.count; ++q) {
+      const Item& it = P.items[q];
+      if (it.kpad < 16 || it.kpad % 16 || it.kpad > L.aux3) throw Error(H2_EINTERNAL, "bad tensor-core tile k");
+      check(it.a, (int64_t)L.aux2 * it.kpad, "coupling A tile");
+      check(it.b, (int64_t)L.aux * it.kpad, "coupling B tile");
     }
   };
   auto check_eig = [&](const EigTask& e) {
@@ -529,7 +560,8 @@ void validate_plan(const Plan& P, const int64_t sizes[kArenas]) {
 #pragma omp parallel for schedule(dynamic, 4096)
       for (int64_t i = L.first; i < L.first + L.count; ++i) {
         try {
-          check_seg(P.segs[i]);
+          if (L.tc) check_tc_seg(P.segs[i], L);
+          else check_seg(P.segs[i]);
         } catch (std::exception& e) {
 #pragma omp critical
           if (err.empty()) err = e.what();
@@ -568,8 +600,10 @@ void upload_plan(Plan& P, size_t region_esize, bool own_regions) {
           for (int32_t q = s.first; q < s.first + s.count; ++q)
             fl += 2.0 * s.m * s.n * (P.items[q].kpad ? P.items[q].kpad : s.k);
       }
-      L.aux = mx;
-      L.aux2 = md;
+      if (!L.tc) {  // (a tensor-core launch keeps the tile rows the plan gave it)
+        L.aux = mx;
+        L.aux2 = md;
+      }
       L.flops = fl;
     } else if (L.kind == Launch::EIG) {
       int mx = 1, kl = 1;
@@ -629,7 +663,10 @@ void run_plan(const Plan& P, const ArenaSet& ar, const Arenas* d_ars, const MmpP
     } else if (L.kind == Launch::GEMM) {
       const int v = choice ? choice[li] : 0;
       if (tune_ev) cuda_check(cudaEventRecord((cudaEvent_t)tune_ev[2 * li], (cudaStream_t)stream), "event");
-      if (P.cplx && is_mixed(prm.precision))
+      if (L.tc)  // coupling sums on the tensor cores from operand tiles
+        launch_coup_tc(P.d_segs, P.d_items, L.first, L.count, d_ars, L.aux2, L.aux, L.aux3, ar.err, v % kTcVariants,
+                       stream);
+      else if (P.cplx && is_mixed(prm.precision))
         launch_zgemm32(P.d_segs, P.d_items, L.first, L.count, d_ars, L.aux, stream);
       else if (P.cplx)
         launch_zgemm(P.d_segs, P.d_items, L.first, L.count, d_ars, L.aux, stream);
@@ -804,7 +841,7 @@ h2_status h2_plan_selfcheck(const double* points, int64_t n, int32_t leaf_size, 
     }
     const int64_t asz = mat_elems(m);
     for (int trunc : {H2_TRUNC_PAPER, H2_TRUNC_SV, H2_TRUNC_FULL, H2_TRUNC_FORMATTED})
-      for (int prec : {H2_FP64, H2_MIXED_FP32})
+      for (int prec : {H2_FP64, H2_MIXED_FP32, H2_MIXED_BF16X3})
         for (int cap : {24, 48}) {
           Plan P;
           Mat C;
@@ -1126,7 +1163,8 @@ h2_status h2_mmp(h2_handle A, h2_handle B, double eps, const h2_opts* opts, h2_h
         ts.ms.assign(nl, std::vector<float>(ts.ncand, -1.f));
         for (size_t li = 0; li < nl; ++li) {
           const Launch& L = P.launches[li];
-          if ((L.kind == Launch::GEMM && !P.cplx) || (L.kind == Launch::EIG && !P.cplx && eig_kept_path(pr.prm, L)))
+          if ((L.kind == Launch::GEMM && !P.cplx) ||
+              (L.kind == Launch::EIG && !P.cplx && eig_kept_path(pr.prm, L)))
             ts.choice[li] = -1;
         }
         for (size_t i = 0; i < 2 * nl + 1; ++i) {  // two per launch and an end marker
@@ -1529,7 +1567,7 @@ h2_status h2_trace_read(h2_handle C, int32_t cap, int32_t* kind, int32_t* level,
       const Launch& L = P.launches[i];
       float t = 0;
       cuda_check(cudaEventElapsedTime(&t, (cudaEvent_t)C->trace.ev[2 * i], (cudaEvent_t)C->trace.ev[2 * i + 1]), "event");
-      if (kind) kind[i] = L.kind == Launch::GEMM ? 0 : (L.kind == Launch::EIG ? 1 : 2);
+      if (kind) kind[i] = L.kind == Launch::GEMM ? (L.tc ? 3 : 0) : (L.kind == Launch::EIG ? 1 : 2);
       if (level) level[i] = L.level;
       if (ms) ms[i] = t;
       if (flops) flops[i] = L.kind == Launch::EIG ? (double)L.count : L.flops;

@@ -117,8 +117,12 @@ inline int64_t offset_of(int64_t t) { return t & kOffMask; }
 // m, n, k are the padded dims; a dim reference (rank array << kRefShift | cluster node,
 // -1 = none) bounds the loop by the actual rank read on the device, so padded zeros
 // are skipped.  Rank arrays: 0 A.kr, 1 A.kc, 2 B.kr, 3 B.kc, 4 C.kr, 5 C.kc.
-// SF_CA / SF_CB: conjugate A / B (complex operands; real kernels ignore them)
-enum SegFlags : uint8_t { SF_TA = 1, SF_TB = 2, SF_ACC = 4, SF_SUM = 8, SF_CA = 16, SF_CB = 32 };
+// SF_CA / SF_CB: conjugate A / B (complex operands; real kernels ignore them).
+// SF_TILE: the output (a sum segment: its inputs) is a tensor-core operand tile (BF16
+// split, device.cuh) of trows rows and ldc (sum: lda) columns; with SF_TILE_T the matrix
+// element (r, c) sits at tile position (c, r).  Only in products of H2_MIXED_BF16X3.
+enum SegFlags : uint8_t { SF_TA = 1, SF_TB = 2, SF_ACC = 4, SF_SUM = 8, SF_CA = 16, SF_CB = 32, SF_TILE = 64,
+                          SF_TILE_T = 128 };
 enum RankSrc : int32_t { RK_AR = 0, RK_AC = 1, RK_BR = 2, RK_BC = 3, RK_CR = 4, RK_CC = 5 };
 constexpr int kRefShift = 26;
 inline int32_t rref(RankSrc s, int node) { return (int32_t)((s << kRefShift) | node); }
@@ -130,7 +134,7 @@ struct Seg {
   uint8_t flags;
   uint8_t pad0;
   int16_t inst;  // product instance: index into the launch's arena tables (0 for one product)
-  int32_t pad1;
+  int32_t trows;  // SF_TILE: rows of the tile (a multiple of 8)
 };
 struct Item {
   int64_t a = 0, b = 0;
@@ -162,8 +166,10 @@ struct Launch {
   int64_t first = 0, count = 0;  // range in segs / eigs
   int64_t off = 0, elems = 0;    // MEMSET: tagged offset and size
   int level = -1;
-  int aux = 0;                   // GEMM: largest n; EIG: largest Gram dim
-  int aux2 = 0;                  // GEMM: largest max(m, n); EIG: largest rank limit
+  bool tc = false;               // GEMM on the tensor cores from operand tiles (coupling sums)
+  int aux = 0;                   // GEMM: largest n; EIG: largest Gram dim; tc: B tile rows
+  int aux2 = 0;                  // GEMM: largest max(m, n); EIG: largest rank limit; tc: A tile rows
+  int aux3 = 0;                  // tc: largest tile k
   const char* phase = "";
   double flops = 0;              // GEMM: counted 2 m n k over the group
 };
@@ -268,13 +274,18 @@ void run_plan(const Plan& plan, const ArenaSet& ar, const Arenas* d_ars, const M
 void launch_gemm(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const Arenas* d_ars,
                  int maxn, int maxdim, bool fp32, void* stream, int variant = 0);
 // launch configurations the autotuner tries per GEMM launch group: CUDA-core kernels
-// {column slices per CTA, whole segment per CTA}, tensor-core kernel {4, 2, 1} CTAs per SM
-constexpr int kGemmVariants = 2, kMmaVariants = 3, kEigVariants = 4, kTuneCandidates = 4;
+// {column slices per CTA, whole segment per CTA}, 3xTF32 tensor-core kernel {4, 2, 1} CTAs
+// per SM, BF16 coupling kernel four (stages, accumulators) pairs (tc.cu)
+constexpr int kGemmVariants = 2, kMmaVariants = 3, kEigVariants = 4, kTcVariants = 4, kTuneCandidates = 4;
 // the same segments on the tensor cores, 3xTF32 split products (mma.cu); maxm / maxn bound
 // the segments' padded dims; err receives 1 if a bounded wait gave up; variant: launch
 // configuration (k per stage, CTAs per SM; results identical for all)
 void launch_gemm_mma(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const Arenas* d_ars,
                      int maxm, int maxn, unsigned int* err, int variant, void* stream);
+// coupling sums from operand tiles on the tensor cores (tc.cu): segments with items (A
+// tile rp x kpad, B tile np x kpad), rp, np the launch's tile rows, kpmax its largest k
+void launch_coup_tc(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const Arenas* d_ars,
+                    int rp, int np, int kpmax, unsigned int* err, int variant, void* stream);
 void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, const Arenas* d_ars, double eps, int trunc,
                 int norm, int max_npad, double* scratch, void* stream);
 // formatted product: C's ranks are A's row ranks and B's column ranks (instance inst)

@@ -262,6 +262,7 @@ __global__ void __launch_bounds__(GNT, 12) seg_gemm32_kernel(const Seg* __restri
       for (int m0 = 0; m0 < M; m0 += TILE) {
         const int mc = min(TILE, M - m0);
         float acc[4][4] = {};
+        const bool tiled = s.flags & SF_TILE, tt = s.flags & SF_TILE_T;
         for (int q = 0; q < s.count; ++q) {
           const float* A = ptr_of<float>(ar, it[q].a);
 #pragma unroll
@@ -269,7 +270,12 @@ __global__ void __launch_bounds__(GNT, 12) seg_gemm32_kernel(const Seg* __restri
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
               const int r = 4 * ty + i, c = 4 * tx + j;
-              if (r < mc && c < nc) acc[i][j] += A[(int64_t)(m0 + r) * s.lda + n0 + c];
+              if (r < mc && c < nc) {
+                if (tiled)  // an operand tile of the BF16 split product (its lda: the tile's k)
+                  acc[i][j] += tile_load((const char*)A, s.trows, s.lda, tt ? n0 + c : m0 + r, tt ? m0 + r : n0 + c);
+                else
+                  acc[i][j] += A[(int64_t)(m0 + r) * s.lda + n0 + c];
+              }
             }
         }
 #pragma unroll
@@ -455,13 +461,24 @@ __global__ void __launch_bounds__(GNT, 12) seg_gemm32_kernel(const Seg* __restri
         __syncthreads();
       }
       if (mine && (!split || tid < 32)) {
+        if (s.flags & SF_TILE) {  // an operand tile of the BF16 split product (ldc: the tile's k)
+          const bool tt = s.flags & SF_TILE_T;
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+          for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int r = 4 * qy + i, c = 4 * qx + j;
-            if (r < mc && c < nc) st<float>(out, (int64_t)(m0 + r) * s.ldc + n0 + c, acc[i][j], accum);
-          }
+            for (int j = 0; j < 4; ++j) {
+              const int r = m0 + 4 * qy + i, c = n0 + 4 * qx + j;
+              if (r - m0 < mc && c - n0 < nc) tile_store(out.base, s.trows, s.ldc, tt ? c : r, tt ? r : c, acc[i][j]);
+            }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int r = 4 * qy + i, c = 4 * qx + j;
+              if (r < mc && c < nc) st<float>(out, (int64_t)(m0 + r) * s.ldc + n0 + c, acc[i][j], accum);
+            }
+        }
       }
     }
   }

@@ -341,6 +341,35 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
     }
   }
   mat_elems(C);  // offsets of C's arrays
+  // H2_MIXED_BF16X3: the main coupling pass of a level runs on the tensor cores from BF16
+  // split operand tiles (tc.cu) where the tiles fit (rows, columns and k from 1 to 64):
+  // the producers of its operands (projections, R images) write them as tiles of RP (A
+  // operands: rows of C's row cluster) or NP (B operands, transposed: columns of C's
+  // column cluster) rows and KP columns, and the next level's collects read them as tiles
+  const bool tcmode = prm.precision == H2_MIXED_BF16X3 && !cplx;
+  auto pad8 = [](int x) { return (x + 7) & ~7; };
+  auto pad16 = [](int x) { return (x + 15) & ~15; };
+  std::vector<char> tcl(L + 1, 0);
+  for (int l = lmin; l <= L && tcmode; ++l)
+    tcl[l] = C.Kr[l] > 0 && C.Kc[l] > 0 && pad8(C.Kr[l]) <= 64 && pad8(C.Kc[l]) <= 64 && B.Kr[l] > 0 &&
+             A.Kc[l] > 0 && pad16(B.Kr[l]) <= 64 && pad16(A.Kc[l]) <= 64 && (l < L || pad16(LS) <= 64);
+  // the segment just emitted, if any, writes an operand tile of tr rows and kp columns
+  // (transposed: matrix element (r, c) at tile position (c, r))
+  auto tile_out = [&](size_t nseg, int tr, int kp, bool transposed) {
+    if (P.segs.size() == nseg) return;
+    Seg& sg = P.segs.back();
+    sg.flags |= SF_TILE | (transposed ? SF_TILE_T : 0);
+    sg.ldc = (int16_t)kp;
+    sg.trows = tr;
+  };
+  // the sum segment just emitted, if any, reads operand tiles
+  auto tile_in = [&](size_t nseg, int tr, int kp, bool transposed) {
+    if (P.segs.size() == nseg) return;
+    Seg& sg = P.segs.back();
+    sg.flags |= SF_TILE | (transposed ? SF_TILE_T : 0);
+    sg.lda = (int16_t)kp;
+    sg.trows = tr;
+  };
   auto rA = [&](int l) { return A.Kr[l]; };
   auto cA = [&](int l) { return A.Kc[l]; };
   auto rB = [&](int l) { return B.Kr[l]; };
@@ -426,14 +455,16 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
     std::vector<int64_t> T1(nb, -1), T2(nb, -1), PAS(nb, -1), SBP(nb, -1);
     Ahat[l].assign(nb, -1);
     Bhat[l].assign(nb, -1);
+    // operand tiles of the tensor-core coupling pass (tcl[l]): rows and k
+    const int RP = pad8(rC(l)), NP = pad8(cC(l)), KP1 = pad16(LS), KP2 = pad16(rB(l)), KP3 = pad16(cA(l));
     for (int64_t p = 0; p < nb; ++p) {
-      Ahat[l][p] = pb.alloc(g, (int64_t)rC(l) * rB(l));
-      Bhat[l][p] = pb.alloc(g, (int64_t)cA(l) * cC(l));
+      Ahat[l][p] = pb.alloc(g, tcl[l] ? (int64_t)RP * KP2 : (int64_t)rC(l) * rB(l));
+      Bhat[l][p] = pb.alloc(g, tcl[l] ? (int64_t)NP * KP3 : (int64_t)cA(l) * cC(l));
       if (bl[p].kind == KR) {
         T1[p] = pb.alloc(AR_S, (int64_t)rA(l) * rB(l));
         T2[p] = pb.alloc(AR_S, (int64_t)cA(l) * cB(l));
-        PAS[p] = pb.alloc(AR_S, (int64_t)rC(l) * cA(l));
-        SBP[p] = pb.alloc(AR_S, (int64_t)rB(l) * cC(l));
+        PAS[p] = pb.alloc(AR_S, tcl[l] ? (int64_t)RP * KP3 : (int64_t)rC(l) * cA(l));
+        SBP[p] = pb.alloc(AR_S, tcl[l] ? (int64_t)NP * KP2 : (int64_t)rB(l) * cC(l));
       }
     }
     pb.begin();
@@ -491,7 +522,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
             if (pass) {
               Ksets.put(tr.pa, Q[tr.pb]);
               Isets.put(tr.pb, Rr[tr.pa]);
-              g1.put(tr.tgt, {Q[tr.pa], Rr[tr.pb]});  // (V^C_i^T F_ij)(F_jk V^C_k) after the eig
+              g1.put(tr.tgt, {tr.pa, tr.pb});  // (V^C_i^T F_ij)(F_jk V^C_k) after the eig (blocks)
             } else {
               Ksets.count(tr.pa);
               Isets.count(tr.pb);
@@ -622,8 +653,10 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       pb.end("leaf_dense", l);
       // case-1 couplings after the eig reuse Q (as V^C_i^T F_ij) and Rr (as F_jk V^C_k)
       for (int64_t p = 0; p < nb; ++p) {
-        Ach[p] = Q[p];
-        Bch[p] = Rr[p];
+        // (the tensor-core pass reads them as tiles: storage of their own, zero past the
+        // written entries, instead of Q / Rr's)
+        Ach[p] = tcl[l] ? (Q[p] >= 0 ? pb.alloc(AR_S, (int64_t)RP * KP1) : -1) : Q[p];
+        Bch[p] = tcl[l] ? (Rr[p] >= 0 ? pb.alloc(AR_S, (int64_t)NP * KP1) : -1) : Rr[p];
       }
       lt.g1 = std::move(g1);
     } else {
@@ -646,9 +679,13 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
           for (int bb = 0; bb < 2; ++bb) {
             int32_t cp = st.find(c, 2 * b.t + a, 2 * b.s + bb);
             if (cp < 0) throw Error(H2_EINTERNAL, "missing child block");
+            size_t ns = P.segs.size();
             pb.sum(Ac[p] + (int64_t)a * hr * 2 * rB(c) + (int64_t)bb * rB(c), hr, rB(c), rB(c), 2 * rB(c), false,
                    &Ahat[c][cp], 1);
+            if (tcl[c]) tile_in(ns, pad8(rC(c)), pad16(rB(c)), false);  // the children's tiles
+            ns = P.segs.size();
             pb.sum(Bc[p] + (int64_t)a * cA(c) * gc + (int64_t)bb * hc, cA(c), hc, hc, gc, false, &Bhat[c][cp], 1);
+            if (tcl[c]) tile_in(ns, pad8(cC(c)), pad16(cA(c)), true);
           }
       }
       pb.end("collect", l);
@@ -818,19 +855,33 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
                  BC(l, t), CC(l, t));
       }
     }
+    // (with the tensor-core coupling pass the coupling operands go out as tiles: A
+    // operands rows x k, B operands transposed)
+    const bool tl = tcl[l];
     for (int64_t p = 0; p < nb; ++p) {
       const Block& b = bl[p];
+      size_t ns = P.segs.size();
       if (leaf && b.kind == KF) {
         pb.gemm1(Ahat[l][p], rC(l), rB(l), LS, rC(l), rB(l), rB(l), SF_TA | SF_CA, tCb(C.Vr(b.t)), Y[p], CR(l, b.t),
                  BR(l, b.s));
+        if (tl) tile_out(ns, RP, KP2, false);
+        ns = P.segs.size();
         pb.gemm1(Bhat[l][p], cA(l), cC(l), LS, LS, cC(l), cC(l), SF_CB, Yb[p], tCb(C.Vc(b.s)), AC(l, b.t), CC(l, b.s));
+        if (tl) tile_out(ns, NP, KP3, true);
+        ns = P.segs.size();
         pb.gemm1(Ach[p], rC(l), LS, LS, rC(l), LS, LS, SF_TA | SF_CA, tCb(C.Vr(b.t)), tA(A.F(b.idx)), CR(l, b.t));
+        if (tl) tile_out(ns, RP, KP1, false);
+        ns = P.segs.size();
         pb.gemm1(Bch[p], LS, cC(l), LS, LS, cC(l), cC(l), SF_CB, tB(B.F(b.idx)), tCb(C.Vc(b.s)), -1, CC(l, b.s));
+        if (tl) tile_out(ns, NP, KP1, true);
       } else if (!leaf && b.kind == KNL) {
         pb.gemm1(Ahat[l][p], rC(l), rB(l), gr, rC(l), rB(l), rB(l), SF_TA | SF_CA, tCb(C.Er(l, b.t)), Y[p], CR(l, b.t),
                  BR(l, b.s));
+        if (tl) tile_out(ns, RP, KP2, false);
+        ns = P.segs.size();
         pb.gemm1(Bhat[l][p], cA(l), cC(l), gc, gc, cC(l), cC(l), SF_CB, Yb[p], tCb(C.Ec(l, b.s)), AC(l, b.t),
                  CC(l, b.s));
+        if (tl) tile_out(ns, NP, KP3, true);
       }
     }
     if (!leaf) {
@@ -857,14 +908,22 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
     for (int64_t p = 0; p < nb; ++p) {
       const Block& b = bl[p];
       if (b.kind != KR) continue;
+      size_t ns = P.segs.size();
       pb.gemm1(Ahat[l][p], rC(l), rB(l), rA(l), rA(l), rB(l), rB(l), 0, PA[l][b.t], T1[p], CR(l, b.t), BR(l, b.s),
                AR(l, b.t));
+      if (tcl[l]) tile_out(ns, RP, KP2, false);
+      ns = P.segs.size();
       pb.gemm1(Bhat[l][p], cA(l), cC(l), cB(l), cB(l), cC(l), cC(l), 0, T2[p], PB[l][b.s], AC(l, b.t), CC(l, b.s),
                BC(l, b.s));
+      if (tcl[l]) tile_out(ns, NP, KP3, true);
+      ns = P.segs.size();
       pb.gemm1(PAS[p], rC(l), cA(l), rA(l), rA(l), cA(l), cA(l), 0, PA[l][b.t], tA(A.S(l, b.idx)), CR(l, b.t),
                AC(l, b.s), AR(l, b.t));
+      if (tcl[l]) tile_out(ns, RP, KP3, false);
+      ns = P.segs.size();
       pb.gemm1(SBP[p], rB(l), cC(l), cB(l), cB(l), cC(l), cC(l), 0, tB(B.S(l, b.idx)), PB[l][b.s], BR(l, b.t),
                CC(l, b.s), BC(l, b.s));
+      if (tcl[l]) tile_out(ns, NP, KP2, true);
     }
     pb.end("rimage", l);
 
@@ -930,15 +989,17 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         if (leaf)
           for (size_t x = 0; x < lt.g1.size(q); ++x) {
             const Item& g = lt.g1.ptr(q)[x];
-            it[n++] = Item(g.a, g.b, -1, LS, cn, LS);
+            it[n++] = tcl[l] ? Item(Ach[g.a], Bch[g.b], -1, 0, 0, KP1) : Item(Ach[g.a], Bch[g.b], -1, LS, cn, LS);
           }
         for (int64_t y = toff[q]; y < toff[q + 1]; ++y) {
           const Triple& tr = lt.trip[tord[y]];
           const Block &ba = bl[tr.pa], &bb = bl[tr.pb];
           if (bb.kind == KR)  // case-2, case-4
-            it[n++] = Item(Ahat[l][tr.pa], SBP[tr.pb], BR(l, ba.s), rB(l), cn, rB(l));
+            it[n++] = tcl[l] ? Item(Ahat[l][tr.pa], SBP[tr.pb], BR(l, ba.s), 0, 0, KP2)
+                             : Item(Ahat[l][tr.pa], SBP[tr.pb], BR(l, ba.s), rB(l), cn, rB(l));
           else  // case-3
-            it[n++] = Item(PAS[tr.pa], Bhat[l][tr.pb], AC(l, ba.s), cA(l), cn, cA(l));
+            it[n++] = tcl[l] ? Item(PAS[tr.pa], Bhat[l][tr.pb], AC(l, ba.s), 0, 0, KP3)
+                             : Item(PAS[tr.pa], Bhat[l][tr.pb], AC(l, ba.s), cA(l), cn, cA(l));
         }
         Seg sg{};
         sg.out = T.ssum;
@@ -946,19 +1007,29 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         sg.count = (int32_t)n;
         sg.m = (int16_t)cm;
         sg.n = (int16_t)cn;
-        sg.k = (int16_t)kmax;
+        sg.k = (int16_t)(tcl[l] ? std::max(std::max(leaf ? KP1 : 0, KP2), KP3) : kmax);
         sg.lda = (int16_t)kmax;
         sg.ldb = (int16_t)cn;
         sg.ldc = (int16_t)cn;
         sg.mref = CR(l, T.i);
         sg.nref = CC(l, T.k);
-        sg.flags = SF_ACC;
+        // the first contribution to the target's coupling is stored, not added, unless the
+        // case-1 pass above the leaf level has written it already
+        sg.flags = Mt[q] >= 0 ? SF_ACC : 0;
         P.segs[s0 + sidx[q]] = sg;
         for (int64_t x = 0; x < n; ++x) fl += 2LL * cm * cn * (it[x].kpad ? it[x].kpad : kmax);
       }
       P.flops += fl;
     }
+    const size_t nlaunch = P.launches.size();
     pb.end("coup", l);
+    if (tcl[l] && P.launches.size() > nlaunch) {
+      Launch& T = P.launches.back();
+      T.tc = true;
+      T.aux = NP;   // B tile rows (the MMA's N)
+      T.aux2 = RP;  // A tile rows
+      T.aux3 = std::max(std::max(leaf ? KP1 : 0, KP2), KP3);
+    }
     pb.close_memset(zG, g);
     pb.close_memset(zS, AR_S);
     // the children's data of this level are consumed: free the lists

@@ -245,7 +245,7 @@ class H2Matrix:
         fl = np.zeros(n, np.float64)
         _check(lib.h2_trace_read(self.handle, n, _ptr(kind), _ptr(level), _ptr(ms), _ptr(fl), C.byref(cnt)))
         names = [lib.h2_trace_phase(self.handle, i).decode() for i in range(n)]
-        return [("gemm", "eig", "memset")[k] for k in kind], level, ms, fl, names
+        return [("gemm", "eig", "memset", "tc")[k] for k in kind], level, ms, fl, names
 
     def trace_flops(self) -> float:
         v = C.c_double(0)

@@ -10,7 +10,10 @@ passes 1e-12 only for thresholds thr >= 1e-8; below, the bound is 20 u / sqrt(th
 (sv mode at eps = 1e-5: thr = 1e-10, measured 8.9e-11).
 Mixed precisions: within 2 eps of the oracle, no less accurate against the exact
 product, and equal ranks wherever the oracle's decision is clear of the threshold by
-more than what float32 Gram matrices can move (1e-5 lambda_1).
+more than what float32 Gram matrices can move (1e-5 lambda_1).  The BF16 split
+couplings (H2_MIXED_BF16X3) carry relative errors up to ~2^-16, and the non-leaf Gram
+matrices are built from them: eigenvalues move by up to ~4e-5 lambda_1, so ranks are
+compared where the decision is clear by 1e-4 lambda_1.
 """
 import math
 
@@ -28,6 +31,8 @@ pytestmark = pytest.mark.gpu
 
 TOL = 1e-12     # float64: element-wise, relative to the largest entry
 MIXED_MARGIN = 1e-5
+BF16_MARGIN = 1e-4
+PRECISIONS = {"fp64": 0, "fp32": 1, "tf32x3": 2, "bf16x3": 3}   # h2_precision values
 
 
 def fp64_tol(eps, mode):
@@ -46,12 +51,12 @@ def assert_entries_close(got, ref, tol=TOL):
     assert err <= tol * scale, f"max entry difference {err:.3e} = {err / scale:.3e} of max|ref|"
 
 
-def clear_rank_mismatches(gpu_export, stats, L):
+def clear_rank_mismatches(gpu_export, stats, L, margin=MIXED_MARGIN):
     """Clusters (level, t, column side) whose GPU rank differs from the oracle's although
-    the oracle's decision is clear of the threshold by MIXED_MARGIN."""
+    the oracle's decision is clear of the threshold by `margin` (of lambda_1)."""
     bad = []
     for (l, t, col), m in stats["margins"].items():
-        if m <= MIXED_MARGIN:
+        if m <= margin:
             continue
         node = (1 << l) - 1 + t
         got = (gpu_export.kc if col else gpu_export.kr)[node]
@@ -225,24 +230,26 @@ def test_structure_mismatch_is_rejected(lib):
     assert ei.value.code == lib.H2_ESTRUCT
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16x3"])
 @pytest.mark.parametrize("name,mode,eps", [("cubes_1024", "paper", 1e-4), ("cubes_2048_invr2", "paper", 1e-3),
-                                           ("uniform_1000_ragged", "paper", 1e-4)])
+                                           ("uniform_1000_ragged", "paper", 1e-4), ("sphere_700_ragged", "sv", 1e-2)])
 def test_mixed_product_within_2eps_of_oracle(lib, name, mode, eps, prec):
-    # products in float32 (CUDA cores) or as three TF32 products (tensor cores), float32
-    # accumulation; float64 rank decisions and bases: the result must stay within 2 eps
-    # of the float64 oracle and be no less accurate against the exact product A B
+    # products in float32 (CUDA cores), as three TF32 products (tensor cores), or with the
+    # couplings as three BF16 split products on the tensor cores; float32 accumulation;
+    # float64 rank decisions and bases: the result must stay within 2 eps of the float64
+    # oracle and be no less accurate against the exact product A B
     w, leaf, eta, A = oracle_case(name)
     st = {}
     C = ommp.mmp(A, A, eps, mode, stats=st)
     ga = lib.h2_import(w.points, leaf, eta, pack(A))
-    gc = ga.mmp(ga, eps, precision=lib.MIXED_FP32 if prec == "fp32" else lib.MIXED_TF32X3, trunc=mode)
+    gc = ga.mmp(ga, eps, precision=PRECISIONS[prec], trunc=mode)
     d_gpu = gc.to_dense().cpu().numpy()
     d_orc = oh2.to_dense(C)
     exact = oh2.to_dense(A) @ oh2.to_dense(A)
     assert rel(d_gpu, d_orc) < 2 * eps
     assert rel(d_gpu, exact) < 1.2 * rel(d_orc, exact) + 1e-6
-    assert clear_rank_mismatches(gc.export(), st, A.L) == []
+    margin = BF16_MARGIN if prec == "bf16x3" else MIXED_MARGIN
+    assert clear_rank_mismatches(gc.export(), st, A.L, margin) == []
 
 
 def test_fp64_rank_bounds_do_not_change_results(lib):
@@ -411,33 +418,36 @@ def test_n20480_float64_product_matches_the_oracle(lib, big_case):
     assert_entries_close(y, oh2.matvec(C, x))
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16x3"])
 def test_n20480_mixed_product_against_the_oracle(lib, big_case, prec):
     import torch
     wa, wb, A, B, C, st, x = big_case
     ga = lib.h2_import(wa.points, 32, 1.0, pack(A))
     gb = lib.h2_import(wb.points, 32, 1.0, pack(B))
-    gm = ga.mmp(gb, 1e-4, precision=lib.MIXED_FP32 if prec == "fp32" else lib.MIXED_TF32X3)
+    gm = ga.mmp(gb, 1e-4, precision=PRECISIONS[prec])
     ym = gm.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
     yo = oh2.matvec(C, x)
     y_exact = oh2.matvec(A, oh2.matvec(B, x))
     assert rel(ym, yo) < 2e-4
     assert rel(ym, y_exact) < 1.2 * rel(yo, y_exact)
-    assert clear_rank_mismatches(gm.export(), st, A.L) == []
+    margin = BF16_MARGIN if prec == "bf16x3" else MIXED_MARGIN
+    assert clear_rank_mismatches(gm.export(), st, A.L, margin) == []
 
 
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
 @pytest.mark.parametrize("n", [700, 2600])
-def test_tensor_core_product_is_deterministic_and_tracks_float32(lib, n):
-    # the 3xTF32 tensor-core products: reruns bit for bit equal (fixed accumulation
-    # order), and within a few float32 roundings of the CUDA-core float32 products:
-    # Gram matrices agree to ~1e-6, so ranks may differ only where an eigenvalue lies
-    # within that of the threshold (at most 2 % of the clusters); such a flip moves C by
-    # the content of one near-threshold direction, so C x agrees within 2 eps
+def test_tensor_core_product_is_deterministic_and_tracks_float32(lib, n, prec):
+    # the tensor-core products (3xTF32 everywhere, or the BF16 split couplings): reruns
+    # bit for bit equal (fixed accumulation order), and close to the CUDA-core float32
+    # products: Gram matrices agree to ~1e-6 (3xTF32) or ~4e-5 (BF16 split), so ranks may
+    # differ only where an eigenvalue lies that close to the threshold (at most 2 % of the
+    # clusters); such a flip moves C by the content of one near-threshold direction, so
+    # C x agrees within 2 eps
     import torch
     pts = inputs.stretched_box(n, seed=1)
     h = lib.h2_build(pts, inputs.laplace_spec(n ** (-1 / 3)), 32, 1.0, 1e-4)
-    t1 = h.mmp(h, 1e-4, precision=lib.MIXED_TF32X3)
-    t2 = h.mmp(h, 1e-4, precision=lib.MIXED_TF32X3)
+    t1 = h.mmp(h, 1e-4, precision=PRECISIONS[prec])
+    t2 = h.mmp(h, 1e-4, precision=PRECISIONS[prec])
     f = h.mmp(h, 1e-4, precision=lib.MIXED_FP32)
     e1, e2, ef = t1.export(), t2.export(), f.export()
     for k in ("kr", "kc", "vr", "vc", "er", "ec", "s", "f"):
@@ -449,7 +459,23 @@ def test_tensor_core_product_is_deterministic_and_tracks_float32(lib, n):
     assert float(torch.linalg.norm(yt - yf) / torch.linalg.norm(yf)) < 2e-4
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+def test_bf16_split_couplings_run_on_the_tensor_cores(lib):
+    # H2_MIXED_BF16X3: the coupling pass of every level whose tiles fit runs on the
+    # tensor-core kernel (trace kind "tc"), the leaf level's included; the executed-flop
+    # counter covers it
+    w, leaf, eta, A = oracle_case("cubes_2048_invr2")
+    ga = lib.h2_import(w.points, leaf, eta, pack(A))
+    ga.trace_enable(True)
+    c = ga.mmp(ga, 1e-3, precision=lib.MIXED_BF16X3)
+    kinds, levels, ms, fl, names = c.trace_read()
+    ga.trace_enable(False)
+    tc_levels = {int(lv) for k, lv, nm in zip(kinds, levels, names) if k == "tc" and nm == "coup"}
+    assert A.L in tc_levels and len(tc_levels) >= 3
+    assert all(nm == "coup" for k, nm in zip(kinds, names) if k == "tc")
+    assert c.trace_flops() > 0 and c.info()["cap_hits"] == 0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16x3"])
 def test_autotuned_products_equal_fixed_ones(lib, prec):
     # h2_opts.autotune: the first products of a program try the candidate launch
     # configurations of every GEMM and mixed eigen launch group and then keep the
@@ -457,7 +483,7 @@ def test_autotuned_products_equal_fixed_ones(lib, prec):
     # the untuned one
     w, leaf, eta, A = oracle_case("cubes_2048_invr2")
     ga = lib.h2_import(w.points, leaf, eta, pack(A))
-    p = {"fp64": lib.FP64, "fp32": lib.MIXED_FP32, "tf32x3": lib.MIXED_TF32X3}[prec]
+    p = PRECISIONS[prec]
     ref = ga.mmp(ga, 1e-4, precision=p).export()
     c = None
     for _ in range(5):

@@ -1,7 +1,8 @@
 """Host-only checks of the product and matvec programs (no GPU).
 
 h2_plan_selfcheck builds, for a point set, the program of C = A A in every truncation
-mode, both precisions and two rank caps, plus the matvec programs, and validates every
+mode, three precisions (float64, float32, BF16 split with the tensor-core coupling pass
+and its operand tiles) and two rank caps, plus the matvec programs, and validates every
 access of every segment and eigen task against the live allocations of its region.
 The geometries cover leaf sizes that are not multiples of four (storage caps round
 up), ragged trees and η ≠ 1.
@@ -27,7 +28,7 @@ def lib():
     ("uniform_300_leaf7", lambda: inputs.uniform_cube(300, 9), 7, 0.7),
 ])
 def test_every_program_stays_inside_its_allocations(lib, name, points, leaf, eta):
-    assert lib.plan_selfcheck(points(), leaf, eta, 1e-4) == 18
+    assert lib.plan_selfcheck(points(), leaf, eta, 1e-4) == 26
 
 
 def test_selfcheck_rejects_bad_arguments(lib):
