@@ -604,6 +604,9 @@ void upload_plan(Plan& P, size_t region_esize, bool own_regions) {
         L.aux = mx;
         L.aux2 = md;
       }
+      bool sums = L.count > 0 && !L.tc;
+      for (int64_t q = L.first; q < L.first + L.count && sums; ++q) sums = P.segs[q].flags & SF_SUM;
+      L.sums = sums;
       L.flops = fl;
     } else if (L.kind == Launch::EIG) {
       int mx = 1, kl = 1;
@@ -663,7 +666,9 @@ void run_plan(const Plan& P, const ArenaSet& ar, const Arenas* d_ars, const MmpP
     } else if (L.kind == Launch::GEMM) {
       const int v = choice ? choice[li] : 0;
       if (tune_ev) cuda_check(cudaEventRecord((cudaEvent_t)tune_ev[2 * li], (cudaStream_t)stream), "event");
-      if (L.tc)  // coupling sums on the tensor cores from operand tiles
+      if (L.sums && !P.cplx)  // plain sums: one warp per segment
+        launch_sum(P.d_segs, P.d_items, L.first, L.count, d_ars, is_mixed(prm.precision), stream);
+      else if (L.tc)  // coupling sums on the tensor cores from operand tiles
         launch_coup_tc(P.d_segs, P.d_items, L.first, L.count, d_ars, L.aux2, L.aux, L.aux3, ar.err, v % kTcVariants,
                        stream);
       else if (P.cplx && is_mixed(prm.precision))

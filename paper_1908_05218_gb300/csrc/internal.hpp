@@ -167,6 +167,7 @@ struct Launch {
   int64_t off = 0, elems = 0;    // MEMSET: tagged offset and size
   int level = -1;
   bool tc = false;               // GEMM on the tensor cores from operand tiles (coupling sums)
+  bool sums = false;             // GEMM whose segments are all plain sums (SF_SUM)
   int aux = 0;                   // GEMM: largest n; EIG: largest Gram dim; tc: B tile rows
   int aux2 = 0;                  // GEMM: largest max(m, n); EIG: largest rank limit; tc: A tile rows
   int aux3 = 0;                  // tc: largest tile k
@@ -273,6 +274,9 @@ void run_plan(const Plan& plan, const ArenaSet& ar, const Arenas* d_ars, const M
 // variant: launch configuration (0 default; see kGemmVariants), results identical for all
 void launch_gemm(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const Arenas* d_ars,
                  int maxn, int maxdim, bool fp32, void* stream, int variant = 0);
+// a launch group of plain sums only (real operands; fp32: float, else double)
+void launch_sum(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const Arenas* d_ars, bool fp32,
+                void* stream);
 // launch configurations the autotuner tries per GEMM launch group: CUDA-core kernels
 // {column slices per CTA, whole segment per CTA}, 3xTF32 tensor-core kernel {4, 2, 1} CTAs
 // per SM, BF16 coupling kernel four (stages, accumulators) pairs (tc.cu)

@@ -513,6 +513,62 @@ void launch_gemm(const Seg* d_segs, const Item* d_items, int64_t first, int64_t 
   else gemm_launch<double>(d_segs, d_items, first, count, d_ars, maxn, variant, stream);
 }
 
+// ------------------------------------------------------------ plain sums
+// A launch group whose segments are all plain sums of matrices (the collects of Eq.
+// nonleafA / nonleafB, the split's additions): out (=|+=) sum over the items of A_q (m x n,
+// leading dim lda; or operand tiles, SF_TILE), one warp per segment, each output element
+// summed from zero in item order as in the GEMM kernels' sum path, four elements per lane
+// in flight.
+template <typename T>
+__global__ void __launch_bounds__(256) seg_sum_kernel(const Seg* __restrict__ segs, const Item* __restrict__ items,
+                                                      int64_t first, int64_t count, const Arenas* __restrict__ ars) {
+  const int64_t si = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (si >= count) return;
+  const int lane = threadIdx.x & 31;
+  const Seg s = segs[first + si];
+  const Arenas* ar = ars + s.inst;
+  const View out = view(ar, s.out);
+  const bool accum = s.flags & SF_ACC, tiled = s.flags & SF_TILE, tt = s.flags & SF_TILE_T;
+  const int M = bound(ar, s.mref, s.m), N = bound(ar, s.nref, s.n), total = M * N;
+  const Item* it = items + s.first;
+  for (int e0 = 0; e0 < total; e0 += 128) {
+    T acc[4];
+    int r[4], c[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = e0 + 32 * u + lane;
+      r[u] = e / N;
+      c[u] = e - r[u] * N;
+      acc[u] = T(0);
+    }
+    for (int q = 0; q < s.count; ++q) {
+      const T* A = ptr_of<T>(ar, it[q].a);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (e0 + 32 * u + lane < total)
+          acc[u] += tiled ? (T)tile_load((const char*)A, s.trows, s.lda, tt ? c[u] : r[u], tt ? r[u] : c[u])
+                          : A[(int64_t)r[u] * s.lda + c[u]];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (e0 + 32 * u + lane < total) st<T>(out, (int64_t)r[u] * s.ldc + c[u], acc[u], accum);
+  }
+}
+
+void launch_sum(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const Arenas* d_ars, bool fp32,
+                void* stream) {
+  const int64_t kMaxGrid = 2147483647LL;
+  for (int64_t off = 0; off < count; off += 8 * kMaxGrid) {
+    const int64_t c = std::min(count - off, 8 * kMaxGrid);
+    const unsigned grid = (unsigned)((c + 7) / 8);
+    if (fp32)
+      seg_sum_kernel<float><<<grid, 256, 0, (cudaStream_t)stream>>>(d_segs, d_items, first + off, c, d_ars);
+    else
+      seg_sum_kernel<double><<<grid, 256, 0, (cudaStream_t)stream>>>(d_segs, d_items, first + off, c, d_ars);
+    g_launches += 1;
+  }
+}
+
 __global__ void set_arenas_kernel(Arenas* dst, Arenas a) { *dst = a; }
 
 void upload_arenas(Arenas* dst, const Arenas& a, void* stream) {

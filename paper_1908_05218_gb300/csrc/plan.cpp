@@ -1081,6 +1081,10 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
     pb.end("split", l);
     std::vector<std::pair<int64_t, int64_t>> Fupd;
     std::vector<int32_t> Frow;
+    // the children's parts of X: added to R children's couplings and to NL children's
+    // held ones (plain sums, one launch); F children's parts go through X E^C (a second
+    // launch) into F += V^C (X E^C) (a third)
+    std::vector<std::pair<int64_t, int32_t>> fpart;  // (part of X, child block)
     pb.begin();
     for (size_t p = 0; p < bl.size(); ++p) {
       if (X[p] < 0) continue;
@@ -1089,18 +1093,20 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
           int32_t cp = st.find(c, 2 * bl[p].t + a, 2 * bl[p].s + bb);
           const Block& cb = st.blocks[c][cp];
           int64_t xab = X[p] + (int64_t)a * hr * 2 * hc + (int64_t)bb * hc;
-          if (cb.kind == KR) {
-            pb.sum(tC(C.S(c, cb.idx)), hr, hc, 2 * hc, cC(c), true, {xab});
-          } else if (cb.kind == KNL) {
-            pb.sum(H[c][cp], hr, hc, 2 * hc, cC(c), true, {xab});
-          } else {
-            int64_t tmp = pb.alloc(AR_S, (int64_t)rC(c) * LS);
-            pb.gemm1(tmp, rC(c), LS, cC(c), 2 * hc, cC(c), LS, SF_TB, xab, tCb(C.Vc(cb.s)), CR(c, cb.t), -1,
-                     CC(c, cb.s));
-            Fupd.push_back({tmp, tC(C.F(cb.idx))});
-            Frow.push_back(cb.t);
-          }
+          if (cb.kind == KR) pb.sum(tC(C.S(c, cb.idx)), hr, hc, 2 * hc, cC(c), true, {xab});
+          else if (cb.kind == KNL) pb.sum(H[c][cp], hr, hc, 2 * hc, cC(c), true, {xab});
+          else fpart.push_back({xab, cp});
         }
+    }
+    pb.end("split", l);
+    pb.begin();
+    for (const auto& f : fpart) {
+      const Block& cb = st.blocks[c][f.second];
+      int64_t tmp = pb.alloc(AR_S, (int64_t)rC(c) * LS);
+      pb.gemm1(tmp, rC(c), LS, cC(c), 2 * hc, cC(c), LS, SF_TB, f.first, tCb(C.Vc(cb.s)), CR(c, cb.t), -1,
+               CC(c, cb.s));
+      Fupd.push_back({tmp, tC(C.F(cb.idx))});
+      Frow.push_back(cb.t);
     }
     pb.end("split", l);
     pb.begin();
