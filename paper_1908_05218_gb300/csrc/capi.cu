@@ -518,19 +518,27 @@ void validate_plan(const Plan& P, const int64_t sizes[kArenas]) {
       check(it.b, tb ? (int64_t)(s.n - 1) * ldb + kp : (int64_t)(kp - 1) * ldb + s.n, "segment B");
     }
   };
-  // a segment of the tensor-core coupling pass: items of an A tile (rp x kpad) and a B
-  // tile (np x kpad), rp / np the launch's, kpad from 16 to the launch's largest
-  auto check_tc_seg = [&](const Seg& s, const Launch& L) {
-    check(s.out, (int64_t)(s.m - 1) * s.ldc + s.n, "coupling output");
-    if (s.m <= 0 || s.n <= 0 || s.ldc < s.n || s.count <= 0 || (s.flags & (SF_SUM | SF_TILE)))
-      throw Error(H2_EINTERNAL, "bad tensor-core coupling segment");
-    if (((s.m + 7) & ~7) != L.aux2 || ((s.n + 7) & ~7) != L.aux || L.aux2 > 64 || L.aux > 64 || L.aux3 > 64)
+  // a group of the tensor-core coupling pass: up to two outputs, steps of A tiles
+  // (rp x kpad) and a B tile (np x kpad), rp / np the launch's, kpad from 16 to the
+  // launch's largest
+  auto check_tc_group = [&](const TcGroup& g, const Launch& L) {
+    if (g.m <= 0 || g.n <= 0 || g.ldc < g.n || g.count <= 0 || (g.out[0] < 0 && g.out[1] < 0))
+      throw Error(H2_EINTERNAL, "bad tensor-core coupling group");
+    if (((g.m + 7) & ~7) != L.aux2 || ((g.n + 7) & ~7) != L.aux || L.aux2 > 64 || L.aux > 64 || L.aux3 > 64)
       throw Error(H2_EINTERNAL, "tensor-core coupling tile rows differ from the launch's");
-    for (int32_t q = s.first; q < s.first + s.count; ++q) {
-      const Item& it = P.items[q];
-      if (it.kpad < 16 || it.kpad % 16 || it.kpad > L.aux3) throw Error(H2_EINTERNAL, "bad tensor-core tile k");
-      check(it.a, (int64_t)L.aux2 * it.kpad, "coupling A tile");
-      check(it.b, (int64_t)L.aux * it.kpad, "coupling B tile");
+    if (g.first < 0 || (size_t)g.first + (size_t)g.count > P.tsteps.size())
+      throw Error(H2_EINTERNAL, "tensor-core coupling steps out of range");
+    for (int sl = 0; sl < 2; ++sl)
+      if (g.out[sl] >= 0) check(g.out[sl], (int64_t)(g.m - 1) * g.ldc + g.n, "coupling output");
+    for (int32_t q = g.first; q < g.first + g.count; ++q) {
+      const TcStep& st = P.tsteps[q];
+      if (st.kpad < 16 || st.kpad % 16 || st.kpad > L.aux3) throw Error(H2_EINTERNAL, "bad tensor-core tile k");
+      for (int sl = 0; sl < 2; ++sl) {
+        if (st.a[sl] >= 0 && g.out[sl] < 0) throw Error(H2_EINTERNAL, "coupling term of an empty slot");
+        if (st.a[sl] >= 0) check(st.a[sl], (int64_t)L.aux2 * st.kpad, "coupling A tile");
+      }
+      if (st.a[0] < 0 && st.a[1] < 0) throw Error(H2_EINTERNAL, "coupling step without a term");
+      check(st.b, (int64_t)L.aux * st.kpad, "coupling B tile");
     }
   };
   auto check_eig = [&](const EigTask& e) {
@@ -541,7 +549,7 @@ void validate_plan(const Plan& P, const int64_t sizes[kArenas]) {
     if (e.child1 < 0 && e.nleaf > e.n_pad) throw Error(H2_EINTERNAL, "eig leaf size above n_pad");
     if (e.child1 >= 0 && 2 * e.half > e.n_pad) throw Error(H2_EINTERNAL, "eig half above n_pad");
   };
-  size_t nseg = 0, neig = 0;
+  size_t nseg = 0, neig = 0, ngrp = 0;
   for (size_t li = 0; li < P.launches.size(); ++li) {
     for (; ev < P.aev.size() && P.aev[ev].launch <= (int32_t)li; ++ev) {
       const Plan::AllocEv& x = P.aev[ev];
@@ -560,7 +568,7 @@ void validate_plan(const Plan& P, const int64_t sizes[kArenas]) {
 #pragma omp parallel for schedule(dynamic, 4096)
       for (int64_t i = L.first; i < L.first + L.count; ++i) {
         try {
-          if (L.tc) check_tc_seg(P.segs[i], L);
+          if (L.tc) check_tc_group(P.tgroups[i], L);
           else check_seg(P.segs[i]);
         } catch (std::exception& e) {
 #pragma omp critical
@@ -568,7 +576,8 @@ void validate_plan(const Plan& P, const int64_t sizes[kArenas]) {
         }
       }
       if (!err.empty()) throw Error(H2_EINTERNAL, err);
-      nseg += L.count;
+      if (L.tc) ngrp += L.count;
+      else nseg += L.count;
     } else if (L.kind == Launch::EIG) {
       for (int64_t i = L.first; i < L.first + L.count; ++i) check_eig(P.eigs[i]);
       neig += L.count;
@@ -577,7 +586,8 @@ void validate_plan(const Plan& P, const int64_t sizes[kArenas]) {
       if (L.off < 0 || offset_of(L.off) + L.elems > sizes[a]) throw Error(H2_EINTERNAL, "plan memset out of bounds");
     }
   }
-  if (nseg != P.segs.size() || neig != P.eigs.size()) throw Error(H2_EINTERNAL, "plan work outside its launches");
+  if (nseg != P.segs.size() || neig != P.eigs.size() || ngrp != P.tgroups.size())
+    throw Error(H2_EINTERNAL, "plan work outside its launches");
 }
 
 void upload_plan(Plan& P, size_t region_esize, bool own_regions) {
@@ -587,9 +597,18 @@ void upload_plan(Plan& P, size_t region_esize, bool own_regions) {
   if (!P.segs.empty()) cuda_check(cudaMemcpy(P.d_segs, P.segs.data(), P.segs.size() * sizeof(Seg), cudaMemcpyHostToDevice), "upload segs");
   if (!P.items.empty()) cuda_check(cudaMemcpy(P.d_items, P.items.data(), P.items.size() * sizeof(Item), cudaMemcpyHostToDevice), "upload items");
   if (!P.eigs.empty()) cuda_check(cudaMemcpy(P.d_eigs, P.eigs.data(), P.eigs.size() * sizeof(EigTask), cudaMemcpyHostToDevice), "upload eigs");
+  if (!P.tgroups.empty()) {
+    P.d_tgroups = (TcGroup*)dmalloc(P.tgroups.size() * sizeof(TcGroup));
+    P.d_tsteps = (TcStep*)dmalloc(std::max<size_t>(1, P.tsteps.size()) * sizeof(TcStep));
+    cuda_check(cudaMemcpy(P.d_tgroups, P.tgroups.data(), P.tgroups.size() * sizeof(TcGroup), cudaMemcpyHostToDevice),
+               "upload coupling groups");
+    if (!P.tsteps.empty())
+      cuda_check(cudaMemcpy(P.d_tsteps, P.tsteps.data(), P.tsteps.size() * sizeof(TcStep), cudaMemcpyHostToDevice),
+                 "upload coupling steps");
+  }
   int64_t scratch = 0;
   for (auto& L : P.launches) {
-    if (L.kind == Launch::GEMM) {
+    if (L.kind == Launch::GEMM && !L.tc) {  // (a tensor-core launch has its tile sizes and flops from the plan)
       int mx = 1, md = 1;
       double fl = 0;
       for (int64_t q = L.first; q < L.first + L.count; ++q) {
@@ -600,11 +619,9 @@ void upload_plan(Plan& P, size_t region_esize, bool own_regions) {
           for (int32_t q = s.first; q < s.first + s.count; ++q)
             fl += 2.0 * s.m * s.n * (P.items[q].kpad ? P.items[q].kpad : s.k);
       }
-      if (!L.tc) {  // (a tensor-core launch keeps the tile rows the plan gave it)
-        L.aux = mx;
-        L.aux2 = md;
-      }
-      bool sums = L.count > 0 && !L.tc;
+      L.aux = mx;
+      L.aux2 = md;
+      bool sums = L.count > 0;
       for (int64_t q = L.first; q < L.first + L.count && sums; ++q) sums = P.segs[q].flags & SF_SUM;
       L.sums = sums;
       L.flops = fl;
@@ -631,7 +648,7 @@ void upload_plan(Plan& P, size_t region_esize, bool own_regions) {
 }
 
 void free_plan(Plan& P) {
-  for (void* q : {(void*)P.d_segs, (void*)P.d_items, (void*)P.d_eigs})
+  for (void* q : {(void*)P.d_segs, (void*)P.d_items, (void*)P.d_eigs, (void*)P.d_tgroups, (void*)P.d_tsteps})
     if (q) cudaFree(q);
   for (int a = 0; a < kArenas; ++a) {
     if (P.d_region[a]) cudaFree(P.d_region[a]);
@@ -640,6 +657,8 @@ void free_plan(Plan& P) {
   P.d_segs = nullptr;
   P.d_items = nullptr;
   P.d_eigs = nullptr;
+  P.d_tgroups = nullptr;
+  P.d_tsteps = nullptr;
 }
 
 void run_plan(const Plan& P, const ArenaSet& ar, const Arenas* d_ars, const MmpParams& prm, void* stream,
@@ -669,8 +688,8 @@ void run_plan(const Plan& P, const ArenaSet& ar, const Arenas* d_ars, const MmpP
       if (L.sums && !P.cplx)  // plain sums: one warp per segment
         launch_sum(P.d_segs, P.d_items, L.first, L.count, d_ars, is_mixed(prm.precision), stream);
       else if (L.tc)  // coupling sums on the tensor cores from operand tiles
-        launch_coup_tc(P.d_segs, P.d_items, L.first, L.count, d_ars, L.aux2, L.aux, L.aux3, ar.err, v % kTcVariants,
-                       stream);
+        launch_coup_tc(P.d_tgroups, P.d_tsteps, L.first, L.count, d_ars, L.aux2, L.aux, L.aux3, ar.err,
+                       v % kTcVariants, stream);
       else if (P.cplx && is_mixed(prm.precision))
         launch_zgemm32(P.d_segs, P.d_items, L.first, L.count, d_ars, L.aux, stream);
       else if (P.cplx)

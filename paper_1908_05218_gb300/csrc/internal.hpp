@@ -148,6 +148,30 @@ struct Item {
       : a(a_), b(b_), kref(k_), lda(lda_), ldb(ldb_), kpad(kpad_) {}
 };
 
+// The tensor-core coupling pass (H2_MIXED_BF16X3) sums targets in pairs: the targets
+// (i, k) and (i', k) of sibling row clusters i, i' share the B operand of every common
+// term, so one step multiplies the two stacked A tiles (slot 0: the even cluster, slot 1:
+// the odd one) by that B tile.  A group is one such pair (or a single target); its steps
+// are the union of the two targets' terms, ordered by B tile.
+struct TcGroup {
+  int64_t out[2];        // tagged outputs of the slots (-1: no target in the slot)
+  int32_t mref[2];       // row rank references of the slots
+  int32_t nref;          // column rank reference (the shared k)
+  int32_t first, count;  // steps
+  int16_t m, n, ldc;     // output caps (rows, columns) and leading dim
+  uint8_t acc;           // bit s: slot s adds to its output (else stores it)
+  uint8_t pad0;
+  int16_t inst;          // product instance
+  int16_t pad1;
+};
+struct TcStep {
+  int64_t a[2];          // A tiles of the slots (rp x kpad; -1: no term for the slot)
+  int64_t b;             // the B tile (np x kpad)
+  int32_t kref;          // rank reference bounding k (-1: kpad)
+  int16_t kpad;          // tile k, a multiple of 16
+  int16_t pad0;
+};
+
 // Normalised Gram sum + eigen-decomposition + truncation for one cluster.
 struct EigTask {
   int64_t g[3];      // tagged offsets of the three Gram matrices (-1: absent)
@@ -166,7 +190,8 @@ struct Launch {
   int64_t first = 0, count = 0;  // range in segs / eigs
   int64_t off = 0, elems = 0;    // MEMSET: tagged offset and size
   int level = -1;
-  bool tc = false;               // GEMM on the tensor cores from operand tiles (coupling sums)
+  bool tc = false;               // coupling pass on the tensor cores: first / count index the
+                                 // plan's TcGroups
   bool sums = false;             // GEMM whose segments are all plain sums (SF_SUM)
   int aux = 0;                   // GEMM: largest n; EIG: largest Gram dim; tc: B tile rows
   int aux2 = 0;                  // GEMM: largest max(m, n); EIG: largest rank limit; tc: A tile rows
@@ -179,12 +204,16 @@ struct Plan {
   std::vector<Seg> segs;
   std::vector<Item> items;
   std::vector<EigTask> eigs;
+  std::vector<TcGroup> tgroups;
+  std::vector<TcStep> tsteps;
   std::vector<Launch> launches;
   int64_t region[kArenas] = {0, 0, 0, 0, 0, 0, 0, 0};  // sizes of P, G0, G1, S (others 0)
   // device copies
   Seg* d_segs = nullptr;
   Item* d_items = nullptr;
   EigTask* d_eigs = nullptr;
+  TcGroup* d_tgroups = nullptr;
+  TcStep* d_tsteps = nullptr;
   // work regions owned by the plan (matvec plans); product plans take theirs from the
   // per-stream work space at run time (see region_bytes)
   double* d_region[kArenas] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -286,10 +315,11 @@ constexpr int kGemmVariants = 2, kMmaVariants = 3, kEigVariants = 4, kTcVariants
 // configuration (k per stage, CTAs per SM; results identical for all)
 void launch_gemm_mma(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const Arenas* d_ars,
                      int maxm, int maxn, unsigned int* err, int variant, void* stream);
-// coupling sums from operand tiles on the tensor cores (tc.cu): segments with items (A
-// tile rp x kpad, B tile np x kpad), rp, np the launch's tile rows, kpmax its largest k
-void launch_coup_tc(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const Arenas* d_ars,
-                    int rp, int np, int kpmax, unsigned int* err, int variant, void* stream);
+// coupling sums from operand tiles on the tensor cores (tc.cu): groups of up to two
+// targets with their steps (A tiles rp x kpad, B tile np x kpad), rp, np the launch's tile
+// rows, kpmax its largest k
+void launch_coup_tc(const TcGroup* d_groups, const TcStep* d_steps, int64_t first, int64_t count,
+                    const Arenas* d_ars, int rp, int np, int kpmax, unsigned int* err, int variant, void* stream);
 void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, const Arenas* d_ars, double eps, int trunc,
                 int norm, int max_npad, double* scratch, void* stream);
 // formatted product: C's ranks are A's row ranks and B's column ranks (instance inst)

@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <array>
 #include <map>
 
 #include "internal.hpp"
@@ -962,15 +963,132 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       }
       pb.end("coup", l);
     }
-    pb.begin();
-    {
+    if (tcl[l]) {
+      // ---- the tensor-core pass (tc.cu): the targets in sibling pairs, each pair's terms
+      // merged by B tile into steps (TcGroup / TcStep)
+      const int cm = rC(l), cn = cC(l);
+      auto has_terms = [&](int64_t q) {
+        return lt.tg[q].cls != TC_F && ((leaf ? (int64_t)lt.g1.size(q) : 0) + (toff[q + 1] - toff[q])) > 0;
+      };
+      // a target's terms (case 1, cases 2/4, case 3) as operand tiles, ordered by B tile
+      auto terms = [&](int64_t q, std::vector<Item>& out) {
+        out.clear();
+        if (q < 0) return;
+        if (leaf)
+          for (size_t x = 0; x < lt.g1.size(q); ++x) {
+            const Item& g1 = lt.g1.ptr(q)[x];
+            out.push_back(Item(Ach[g1.a], Bch[g1.b], -1, 0, 0, KP1));
+          }
+        for (int64_t y = toff[q]; y < toff[q + 1]; ++y) {
+          const Triple& tr = lt.trip[tord[y]];
+          const Block &ba = bl[tr.pa], &bb = bl[tr.pb];
+          if (bb.kind == KR) out.push_back(Item(Ahat[l][tr.pa], SBP[tr.pb], BR(l, ba.s), 0, 0, KP2));
+          else out.push_back(Item(PAS[tr.pa], Bhat[l][tr.pb], AC(l, ba.s), 0, 0, KP3));
+        }
+        std::sort(out.begin(), out.end(), [](const Item& x, const Item& y) { return x.b < y.b; });
+      };
+      // groups: a target of an even row cluster with the target of the next cluster and
+      // the same column cluster, if that one has terms; an odd-row target alone otherwise
+      std::vector<std::array<int32_t, 2>> grp;
+      for (int64_t q = 0; q < (int64_t)ntg; ++q) {
+        if (!has_terms(q)) continue;
+        const Target& T = lt.tg[q];
+        const int32_t sib = lt.find(T.i ^ 1, T.k);
+        const bool paired = sib >= 0 && has_terms(sib);
+        if (!(T.i & 1)) grp.push_back({(int32_t)q, paired ? sib : -1});
+        else if (!paired) grp.push_back({-1, (int32_t)q});
+      }
+      const int64_t ng = (int64_t)grp.size();
+      // the union of the two targets' B tiles: steps counted, then written
+      auto merge = [&](const std::vector<Item>& t0, const std::vector<Item>& t1, TcStep* out) {
+        size_t i0 = 0, i1 = 0;
+        int64_t n = 0;
+        while (i0 < t0.size() || i1 < t1.size()) {
+          const bool take0 = i0 < t0.size() && (i1 >= t1.size() || t0[i0].b <= t1[i1].b);
+          const bool take1 = i1 < t1.size() && (i0 >= t0.size() || t1[i1].b <= t0[i0].b);
+          const Item& x = take0 ? t0[i0] : t1[i1];
+          if (out) {
+            TcStep& st = out[n];
+            st.a[0] = take0 ? t0[i0].a : -1;
+            st.a[1] = take1 ? t1[i1].a : -1;
+            st.b = x.b;
+            st.kref = x.kref;
+            st.kpad = x.kpad;
+            st.pad0 = 0;
+          }
+          ++n;
+          if (take0) ++i0;
+          if (take1) ++i1;
+        }
+        return n;
+      };
+      std::vector<int64_t> goff(ng + 1, 0);
+#pragma omp parallel
+      {
+        std::vector<Item> t0, t1;
+#pragma omp for schedule(dynamic, 1024)
+        for (int64_t gq = 0; gq < ng; ++gq) {
+          terms(grp[gq][0], t0);
+          terms(grp[gq][1], t1);
+          goff[gq + 1] = merge(t0, t1, nullptr);
+        }
+      }
+      for (int64_t gq = 0; gq < ng; ++gq) goff[gq + 1] += goff[gq];
+      const size_t st0 = P.tsteps.size(), gr0 = P.tgroups.size();
+      if ((int64_t)st0 + goff[ng] > INT32_MAX) throw Error(H2_ENOMEM, "plan too large");
+      P.tsteps.resize(st0 + (size_t)goff[ng]);
+      P.tgroups.resize(gr0 + (size_t)ng);
+      int64_t fl = 0;
+#pragma omp parallel reduction(+ : fl)
+      {
+        std::vector<Item> t0, t1;
+#pragma omp for schedule(dynamic, 1024)
+        for (int64_t gq = 0; gq < ng; ++gq) {
+          terms(grp[gq][0], t0);
+          terms(grp[gq][1], t1);
+          TcStep* stp = P.tsteps.data() + st0 + goff[gq];
+          const int64_t n = merge(t0, t1, stp);
+          TcGroup G{};
+          for (int sl = 0; sl < 2; ++sl) {
+            const int32_t q = grp[gq][sl];
+            G.out[sl] = q >= 0 ? lt.tg[q].ssum : -1;
+            G.mref[sl] = q >= 0 ? CR(l, lt.tg[q].i) : -1;
+            // the first contribution is stored, unless the case-1 pass above has written
+            if (q >= 0 && Mt[q] >= 0) G.acc |= (uint8_t)(1u << sl);
+          }
+          G.nref = CC(l, lt.tg[grp[gq][0] >= 0 ? grp[gq][0] : grp[gq][1]].k);
+          G.first = (int32_t)(st0 + goff[gq]);
+          G.count = (int32_t)n;
+          G.m = (int16_t)cm;
+          G.n = (int16_t)cn;
+          G.ldc = (int16_t)cn;
+          P.tgroups[gr0 + gq] = G;
+          for (int64_t x = 0; x < n; ++x)
+            fl += 2LL * cm * cn * stp[x].kpad * ((stp[x].a[0] >= 0) + (stp[x].a[1] >= 0));
+        }
+      }
+      P.flops += fl;
+      if (ng > 0) {
+        Launch Lc;
+        Lc.kind = Launch::GEMM;
+        Lc.tc = true;
+        Lc.first = (int64_t)gr0;
+        Lc.count = ng;
+        Lc.level = l;
+        Lc.phase = "coup";
+        Lc.aux = NP;   // B tile rows (the MMA's N)
+        Lc.aux2 = RP;  // A tile rows
+        Lc.aux3 = std::max(std::max(leaf ? KP1 : 0, KP2), KP3);
+        Lc.flops = (double)fl;
+        P.launches.push_back(Lc);
+      }
+    } else {
+      pb.begin();
       const int cm = rC(l), cn = cC(l);
       // a segment per target with items (gemm's rules: no segment for empty sums)
       std::vector<int64_t> sidx(ntg + 1, 0), ioff(ntg + 1, 0);
       for (size_t q = 0; q < ntg; ++q) {
-        const int64_t cnt = lt.tg[q].cls == TC_F
-                                ? 0
-                                : (leaf ? (int64_t)lt.g1.size(q) : 0) + (toff[q + 1] - toff[q]);
+        const int64_t cnt = lt.tg[q].cls == TC_F ? 0 : (leaf ? (int64_t)lt.g1.size(q) : 0) + (toff[q + 1] - toff[q]);
         const bool emit = cnt > 0 && cm > 0 && cn > 0 && kmax > 0;
         sidx[q + 1] = sidx[q] + (emit ? 1 : 0);
         ioff[q + 1] = ioff[q] + (emit ? cnt : 0);
@@ -989,17 +1107,15 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         if (leaf)
           for (size_t x = 0; x < lt.g1.size(q); ++x) {
             const Item& g = lt.g1.ptr(q)[x];
-            it[n++] = tcl[l] ? Item(Ach[g.a], Bch[g.b], -1, 0, 0, KP1) : Item(Ach[g.a], Bch[g.b], -1, LS, cn, LS);
+            it[n++] = Item(Ach[g.a], Bch[g.b], -1, LS, cn, LS);
           }
         for (int64_t y = toff[q]; y < toff[q + 1]; ++y) {
           const Triple& tr = lt.trip[tord[y]];
           const Block &ba = bl[tr.pa], &bb = bl[tr.pb];
           if (bb.kind == KR)  // case-2, case-4
-            it[n++] = tcl[l] ? Item(Ahat[l][tr.pa], SBP[tr.pb], BR(l, ba.s), 0, 0, KP2)
-                             : Item(Ahat[l][tr.pa], SBP[tr.pb], BR(l, ba.s), rB(l), cn, rB(l));
+            it[n++] = Item(Ahat[l][tr.pa], SBP[tr.pb], BR(l, ba.s), rB(l), cn, rB(l));
           else  // case-3
-            it[n++] = tcl[l] ? Item(PAS[tr.pa], Bhat[l][tr.pb], AC(l, ba.s), 0, 0, KP3)
-                             : Item(PAS[tr.pa], Bhat[l][tr.pb], AC(l, ba.s), cA(l), cn, cA(l));
+            it[n++] = Item(PAS[tr.pa], Bhat[l][tr.pb], AC(l, ba.s), cA(l), cn, cA(l));
         }
         Seg sg{};
         sg.out = T.ssum;
@@ -1007,7 +1123,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         sg.count = (int32_t)n;
         sg.m = (int16_t)cm;
         sg.n = (int16_t)cn;
-        sg.k = (int16_t)(tcl[l] ? std::max(std::max(leaf ? KP1 : 0, KP2), KP3) : kmax);
+        sg.k = (int16_t)kmax;
         sg.lda = (int16_t)kmax;
         sg.ldb = (int16_t)cn;
         sg.ldc = (int16_t)cn;
@@ -1020,15 +1136,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         for (int64_t x = 0; x < n; ++x) fl += 2LL * cm * cn * (it[x].kpad ? it[x].kpad : kmax);
       }
       P.flops += fl;
-    }
-    const size_t nlaunch = P.launches.size();
-    pb.end("coup", l);
-    if (tcl[l] && P.launches.size() > nlaunch) {
-      Launch& T = P.launches.back();
-      T.tc = true;
-      T.aux = NP;   // B tile rows (the MMA's N)
-      T.aux2 = RP;  // A tile rows
-      T.aux3 = std::max(std::max(leaf ? KP1 : 0, KP2), KP3);
+      pb.end("coup", l);
     }
     pb.close_memset(zG, g);
     pb.close_memset(zS, AR_S);

@@ -1,34 +1,40 @@
 // Coupling sums on the fifth-generation tensor cores (tcgen05) for H2_MIXED_BF16X3: the
 // main coupling pass of every level (Eq. leafcoup_simple / nonleafcoup_simple: leaf case 1,
-// cases 2/4 and case 3, summed per target), S_ik += sum over items of A_item B_item.
+// cases 2/4 and case 3, summed per target), S_ik (=|+=) sum over the terms of A_t B_t.
 //
 // The operands were written by their producers (the projections and R images of the
 // level) as BF16 split tiles (device.cuh): an A operand (rows of the target, k) as an
 // rp x kp tile, a B operand transposed (columns of the target, k) as an np x kp tile, each
 // in the K-major core-matrix layout of tcgen05 without swizzle, high parts then low parts.
-// So an item's operands reach shared memory by two bulk copies (cp.async.bulk, completing
-// on an mbarrier), and the tensor cores read them there without any rearrangement.
+// So a term's operands reach shared memory by bulk copies (cp.async.bulk, completing on
+// an mbarrier), and the tensor cores read them there without any rearrangement.
 //
-// A persistent CTA of six warps walks the launch's segments (one per target) at a stride
-// of the grid:
-//   * warp 4 copies the items' tiles into a ring of shared-memory stages (its lanes read
-//     the metadata of 32 items at a time, lane 0 issues), a stage being reused once the
-//     products reading it have completed; each stage's slot tells the issuing thread the
-//     item's k and whether it starts or ends its target's sum;
+// Targets are summed in pairs (TcGroup): the targets (i, k) and (i', k) of two sibling row
+// clusters share the B operand of every term with a common middle cluster, so one step
+// multiplies the two stacked A tiles (slot 0 in rows 0 .. sr-1, slot 1 in rows sr ..
+// 2 sr - 1; sr = 32 or 64) by one B tile with an MMA of M = 2 sr rows.  A slot without a
+// term in a step gets zero rows (copied from a zero block).  The MMA reads operands from
+// shared memory, and this stacking halves the operand traffic of a term.
+//
+// A persistent CTA of six warps walks the launch's groups at a stride of the grid:
+//   * warp 4 copies the steps' tiles into a ring of shared-memory stages (its lanes read
+//     the metadata of 32 steps at a time, lane 0 issues), only the rows up to each
+//     target's rank (rounded up to 8), a stage being reused once the products reading it
+//     have completed; each stage's slot tells the issuing thread the step's k, its k-steps
+//     (the rank of the middle cluster, rounded up to 16: the tiles hold zeros beyond it)
+//     and whether it starts or ends the group;
 //   * warp 5 (one thread) issues, per k-step of 16, the three products hi*hi, hi*lo and
-//     lo*hi (tcgen05.mma kind::f16 with BF16 A and B, M = 64, N = np, float32 accumulation
+//     lo*hi (tcgen05.mma kind::f16 with BF16 A and B, M = 2 sr, N = np, float32 accumulation
 //     in tensor memory; the dropped lo*lo term is below 2^-16 of the product) into one of
-//     nacc accumulators, commits each stage to its "empty" mbarrier and the target's last
+//     nacc accumulators, commits each stage to its "empty" mbarrier and the group's last
 //     product to the accumulator's "full" mbarrier;
-//   * warps 0-3 read the finished accumulator (tcgen05.ld; the M = 64 layout puts row r in
-//     lane 32 (r / 16) + r % 16, so warp w holds rows 16 w .. 16 w + 15) and add it to the
-//     target's coupling in its arena (or store it, for the target's first contribution),
-//     then release the accumulator; a target's metadata is read before its products are
-//     waited for.
-// Rows of the A stage beyond the tile (the MMA reads 64) lie inside the stage and only
-// reach accumulator rows that are never stored; k beyond an item's rank is zero in both
-// tiles, so it adds nothing.  The products of a target run in item order, so results are
-// bitwise reproducible.
+//   * warps 0-3 read the finished accumulator (tcgen05.ld) and store or add each slot's
+//     rows to its target's coupling (warps 0, 1: slot 0; warps 2, 3: slot 1: with M = 64
+//     row r sits in lane 32 (r / 16) + r % 16, with M = 128 in lane r), then release the
+//     accumulator; a group's metadata is read before its products are waited for.
+// Rows of a stage beyond the copied ones hold stale data: they only reach accumulator rows
+// or columns that are never stored.  The products of a group run in step order, so results
+// are bitwise reproducible.
 //
 // The executed-flop counter of tracing (Arenas::flops) counts the CUDA-core kernels only.
 //
@@ -57,37 +63,44 @@ constexpr int kProducer = kEpiWarps, kIssuer = kEpiWarps + 1;
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
 constexpr int kMaxSmem = 200 * 1024;
 
+// zero rows for a slot without a term in a step: 64 rows x 64 k of BF16
+__device__ __align__(128) unsigned char g_zero_rows[64 * 64 * 2];
+
 struct TcLayout {
-  int rp, np;      // A tile rows (a multiple of 8, at most 64), B tile rows = the MMA's N
+  int rp, np;      // A tile rows, B tile rows (multiples of 8, at most 64)
+  int sr, m;       // rows per slot (32 or 64) and the MMA's M (2 sr)
+  int nm;          // the MMA's N: np, rounded up to 16 when M = 128
+  int kpmax;       // largest tile k of the launch (a multiple of 16)
   int nst;         // stages of the copy ring
   int nacc;        // accumulators
-  int trim;        // copy only the rows up to the target's ranks (four copies per item; else two)
-  int kpmax;       // largest tile k of the launch (a multiple of 16)
-  int stage_bytes;  // a stage: the item's A tile, then its B tile (offset rp * kp * 4)
+  int trim;        // copy only the rows up to the targets' ranks (else whole tiles)
+  int dynm;        // M = 64 for the groups whose ranks fit 32 rows per slot
+  int stage_bytes; // a stage: A hi (m rows), A lo, B hi (np rows), B lo, at the step's k
   int ncols;       // tensor-memory columns of one accumulator (np rounded up to 16)
   int tmem_cols;   // allocated columns: nacc accumulators, a power of two >= 32
   int total;       // dynamic shared memory
 };
 
-// launch configurations (stages, accumulators), all with the same products in the same
-// order: the autotuner picks one per launch group
-constexpr int kTcConfigs[kTcVariants][3] = {{4, 2, 1}, {4, 2, 0}, {6, 2, 1}, {6, 2, 0}};
+// launch configurations (stages, accumulators, trimmed copies, M per group), all with the
+// same products in the same order: the autotuner picks one per launch group
+constexpr int kTcConfigs[kTcVariants][4] = {{4, 2, 1, 1}, {4, 2, 1, 0}, {4, 4, 1, 1}, {3, 2, 1, 0}};
 
 TcLayout tc_layout(int rp, int np, int kpmax, int variant) {
   TcLayout t;
   t.rp = rp;
   t.np = np;
+  t.sr = rp <= 32 ? 32 : 64;
+  t.m = 2 * t.sr;
   t.kpmax = kpmax;
-  const int kc = kpmax / 8;  // 16-byte k-chunks
-  // the stage holds both tiles; the M = 64 descriptor of A's low part spans 8 row groups
-  // from its start, which may reach into the B tile (rows that only feed accumulator
-  // rows never stored) but must stay inside the stage
-  t.stage_bytes = std::max((rp + np) * kpmax * 4, (rp / 8 + 8) * kc * 128);
-  t.stage_bytes = (t.stage_bytes + 1023) & ~1023;
-  t.ncols = (np + 15) & ~15;
   t.nst = kTcConfigs[variant][0];
   t.nacc = kTcConfigs[variant][1];
   t.trim = kTcConfigs[variant][2];
+  t.dynm = kTcConfigs[variant][3];
+  t.nm = t.m == 128 ? (np + 15) & ~15 : np;
+  // (the MMA reads nm rows from B's lo part, which starts np rows into B: the stage holds
+  // m + nm rows of each part)
+  t.stage_bytes = ((t.m + t.nm) * kpmax * 4 + 1023) & ~1023;
+  t.ncols = (np + 15) & ~15;
   int c = 32;
   while (c < t.nacc * t.ncols) c <<= 1;
   t.tmem_cols = c;
@@ -176,15 +189,21 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, float v[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// what the copying warp tells the issuing thread about the item in a stage
-enum : int { kFirst = 1, kLast = 2, kEnd = 4 };
+// what the copying warp tells the issuing thread about the step in a stage
+enum : int { kFirst = 1, kLast = 2, kEnd = 4, kM128 = 8 };
 
-__global__ void __launch_bounds__(kThreads, 6) coup_tc_kernel(const Seg* __restrict__ segs, const Item* __restrict__ items,
-                                                           int64_t first, int64_t count, const Arenas* __restrict__ ars,
-                                                           TcLayout lay, unsigned int* __restrict__ err) {
+// a group's rows per slot: 32 when both targets' ranks fit (M = 64), else the launch's
+__device__ __forceinline__ int group_sr(const TcLayout& lay, const int m8[2]) {
+  return lay.sr == 32 || (lay.dynm && m8[0] <= 32 && m8[1] <= 32) ? 32 : 64;
+}
+
+__global__ void __launch_bounds__(kThreads, 6) coup_tc_kernel(const TcGroup* __restrict__ groups,
+                                                              const TcStep* __restrict__ steps, int64_t first,
+                                                              int64_t count, const Arenas* __restrict__ ars,
+                                                              TcLayout lay, unsigned int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages], accf[kMaxAcc], acce[kMaxAcc], done;
-  // per stage: the item's tile k and k-steps, kFirst | kLast | kEnd
+  // per stage: the step's tile k and k-steps, kFirst | kLast | kEnd
   __shared__ int slot_k[kMaxStages], slot_s[kMaxStages], slot_f[kMaxStages];
   __shared__ uint32_t s_tmem;
   __shared__ volatile int s_abort;
@@ -215,36 +234,38 @@ __global__ void __launch_bounds__(kThreads, 6) coup_tc_kernel(const Seg* __restr
   const uint32_t nst = (uint32_t)lay.nst;
 
   if (warp == kProducer) {
-    // the copying warp: its lanes read the metadata of 32 items at once; lane 0 waits for
-    // a free stage, describes the item in the stage's slot and starts the two copies
-    uint32_t it = 0;  // items copied by this CTA
+    // the copying warp
+    uint32_t it = 0;  // steps copied by this CTA
     bool ok = true;
-    int64_t si = blockIdx.x;
-    Seg sn{};
-    if (si < count) sn = segs[first + si];
-    while (si < count && ok) {
-      const Seg s = sn;
-      const int64_t si2 = si + gridDim.x;
-      if (si2 < count) sn = segs[first + si2];  // the next segment's, while this one is copied
-      const Arenas* ar = ars + s.inst;
-      // only the tiles' rows up to the target's ranks (rounded up to 8) are copied: the
-      // rest are zeros that only reach accumulator rows / columns never stored
-      const int m8 = lay.trim ? max(8, (bound(ar, s.mref, s.m) + 7) & ~7) : lay.rp;
-      const int n8 = lay.trim ? max(8, (bound(ar, s.nref, s.n) + 7) & ~7) : lay.np;
-      for (int b0 = 0; b0 < s.count && ok; b0 += 32) {
-        const int nb = min(32, s.count - b0);
-        unsigned long long pa = 0, pb = 0;
+    int64_t gi = blockIdx.x;
+    TcGroup gn{};
+    if (gi < count) gn = groups[first + gi];
+    while (gi < count && ok) {
+      const TcGroup g = gn;
+      const int64_t gi2 = gi + gridDim.x;
+      if (gi2 < count) gn = groups[first + gi2];  // the next group's, while this one is copied
+      const Arenas* ar = ars + g.inst;
+      // rows copied per slot (0: no target) and of B: up to the ranks, rounded up to 8
+      int m8[2];
+      for (int sl = 0; sl < 2; ++sl)
+        m8[sl] = g.out[sl] < 0 ? 0 : (lay.trim ? max(8, (bound(ar, g.mref[sl], g.m) + 7) & ~7) : lay.rp);
+      const int n8 = lay.trim ? max(8, (bound(ar, g.nref, g.n) + 7) & ~7) : lay.np;
+      const int sr = group_sr(lay, m8), mm = 2 * sr;  // this group's rows per slot and M
+      for (int b0 = 0; b0 < g.count && ok; b0 += 32) {
+        const int nb = min(32, g.count - b0);
+        unsigned long long pa0 = 0, pa1 = 0, pb = 0;
         int kp = 0, ks = 0;
         if (lane < nb) {
-          const Item iq = items[s.first + b0 + lane];
-          pa = (unsigned long long)ptr_of<float>(ar, iq.a);
-          pb = (unsigned long long)ptr_of<float>(ar, iq.b);
-          kp = iq.kpad;
-          // k-steps of 16 up to the item's rank: the tiles hold zeros beyond it
-          ks = max(1, (bound(ar, iq.kref, kp) + 15) >> 4);
+          const TcStep sp = steps[g.first + b0 + lane];
+          pa0 = sp.a[0] >= 0 ? (unsigned long long)ptr_of<float>(ar, sp.a[0]) : 0ull;
+          pa1 = sp.a[1] >= 0 ? (unsigned long long)ptr_of<float>(ar, sp.a[1]) : 0ull;
+          pb = (unsigned long long)ptr_of<float>(ar, sp.b);
+          kp = sp.kpad;
+          ks = max(1, (bound(ar, sp.kref, kp) + 15) >> 4);
         }
         for (int q = 0; q < nb; ++q, ++it) {
-          const unsigned long long a = __shfl_sync(0xffffffffu, pa, q), b = __shfl_sync(0xffffffffu, pb, q);
+          const unsigned long long a0 = __shfl_sync(0xffffffffu, pa0, q), a1 = __shfl_sync(0xffffffffu, pa1, q);
+          const unsigned long long b = __shfl_sync(0xffffffffu, pb, q);
           const int k = __shfl_sync(0xffffffffu, kp, q), ksteps = __shfl_sync(0xffffffffu, ks, q);
           int good = 1;
           if (lane == 0) {
@@ -253,29 +274,36 @@ __global__ void __launch_bounds__(kThreads, 6) coup_tc_kernel(const Seg* __restr
             if (use > 0 && !mbar_wait(&empty[st], (use - 1) & 1u, &s_abort)) {
               good = 0;
             } else {
-              // hi and lo parts of A (rp rows each in the tile) and of B (np rows): the
-              // first m8 / n8 rows of each part
-              const uint32_t ha = (uint32_t)lay.rp * k * 2, hb = (uint32_t)lay.np * k * 2;
-              const uint32_t ca = (uint32_t)m8 * k * 2, cb = (uint32_t)n8 * k * 2;
+              // stage: A hi (M rows), A lo (M rows), B hi (np rows), B lo (np rows); a tile
+              // holds its hi part, then its lo part rows x k further
+              const uint32_t part_a = (uint32_t)mm * k * 2, tile_a = (uint32_t)lay.rp * k * 2;
+              const uint32_t part_b = (uint32_t)lay.np * k * 2, cb = (uint32_t)n8 * k * 2;
               unsigned char* sa = smem + st * lay.stage_bytes;
-              unsigned char* sb = sa + 2 * ha;
-              const unsigned char* ga = (const unsigned char*)a;
-              const unsigned char* gb = (const unsigned char*)b;
+              unsigned char* sb = sa + 2 * part_a;
+              uint32_t tx = 2 * cb;
+              for (int sl = 0; sl < 2; ++sl) tx += 4u * m8[sl] * k;
               slot_k[st] = k;
               slot_s[st] = ksteps;
-              slot_f[st] = (b0 + q == 0 ? kFirst : 0) | (b0 + q == s.count - 1 ? kLast : 0);
-              mbar_expect_tx(&full[st], 2 * (ca + cb));
-              if (m8 == lay.rp) {  // whole tiles: one copy each
-                bulk_copy(sa, ga, 2 * ca, &full[st]);
-              } else {
-                bulk_copy(sa, ga, ca, &full[st]);
-                bulk_copy(sa + ha, ga + ha, ca, &full[st]);
+              slot_f[st] = (b0 + q == 0 ? kFirst : 0) | (b0 + q == g.count - 1 ? kLast : 0) | (mm == 128 ? kM128 : 0);
+              mbar_expect_tx(&full[st], tx);
+              for (int sl = 0; sl < 2; ++sl) {
+                if (!m8[sl]) continue;
+                const unsigned long long a = sl ? a1 : a0;
+                const uint32_t ca = (uint32_t)m8[sl] * k * 2;
+                unsigned char* d = sa + (uint32_t)sl * sr * k * 2;
+                if (a) {
+                  bulk_copy(d, (const void*)a, ca, &full[st]);
+                  bulk_copy(d + part_a, (const void*)(a + tile_a), ca, &full[st]);
+                } else {  // no term for this slot: zero rows
+                  bulk_copy(d, g_zero_rows, ca, &full[st]);
+                  bulk_copy(d + part_a, g_zero_rows, ca, &full[st]);
+                }
               }
               if (n8 == lay.np) {
-                bulk_copy(sb, gb, 2 * cb, &full[st]);
+                bulk_copy(sb, (const void*)b, 2 * cb, &full[st]);
               } else {
-                bulk_copy(sb, gb, cb, &full[st]);
-                bulk_copy(sb + hb, gb + hb, cb, &full[st]);
+                bulk_copy(sb, (const void*)b, cb, &full[st]);
+                bulk_copy(sb + part_b, (const void*)(b + part_b), cb, &full[st]);
               }
             }
           }
@@ -285,7 +313,7 @@ __global__ void __launch_bounds__(kThreads, 6) coup_tc_kernel(const Seg* __restr
           }
         }
       }
-      si = si2;
+      gi = gi2;
     }
     if (lane == 0) {
       if (ok) {  // the end marker: a stage with no copies
@@ -293,12 +321,13 @@ __global__ void __launch_bounds__(kThreads, 6) coup_tc_kernel(const Seg* __restr
         const uint32_t use = it / nst;
         if (use == 0 || mbar_wait(&empty[st], (use - 1) & 1u, &s_abort)) {
           slot_k[st] = 0;
+          slot_s[st] = 0;
           slot_f[st] = kEnd;
           mbar_arrive(&full[st]);
         }
       } else {
         // the copies in flight land before the CTA leaves: wait for the last use of each
-        // stage (stage st served items st, st + nst, ...: its last use is (it - 1 - st) / nst)
+        // stage (stage st served steps st, st + nst, ...: its last use is (it - 1 - st) / nst)
         for (uint32_t st = 0; st < nst && st < it; ++st) {
           volatile int never = 0;
           mbar_wait(&full[st], ((it - 1 - st) / nst) & 1u, &never);
@@ -308,9 +337,9 @@ __global__ void __launch_bounds__(kThreads, 6) coup_tc_kernel(const Seg* __restr
   } else if (warp == kIssuer) {
     if (lane == 0) {
       // the issuing thread: stages in order until the end marker
-      uint32_t it = 0, seg_i = 0, use_acc[kMaxAcc];
+      uint32_t it = 0, grp_i = 0, use_acc[kMaxAcc];
       for (int b = 0; b < kMaxAcc; ++b) use_acc[b] = 0u;
-      const uint32_t idesc = idesc_bf16(64, lay.np);
+      const uint32_t idesc64 = idesc_bf16(64, lay.np), idesc128 = idesc_bf16(128, (lay.np + 15) & ~15);
       int b = 0;
       bool issued = false;
       for (;; ++it) {
@@ -319,16 +348,18 @@ __global__ void __launch_bounds__(kThreads, 6) coup_tc_kernel(const Seg* __restr
         const int kp = slot_k[st], nks = slot_s[st], fl = slot_f[st];
         if (fl & kEnd) break;
         if (fl & kFirst) {
-          b = (int)(seg_i % (uint32_t)lay.nacc);
+          b = (int)(grp_i % (uint32_t)lay.nacc);
           if (use_acc[b] > 0 && !mbar_wait(&acce[b], (use_acc[b] - 1) & 1u, &s_abort)) break;
           // (the accumulator's last reads by the epilogue come before these products)
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           issued = false;
         }
         const uint32_t d = tmem + (uint32_t)(b * lay.ncols);
+        const int mm = (fl & kM128) ? 128 : 64;
+        const uint32_t idesc = mm == 128 ? idesc128 : idesc64;
         const uint32_t sbo = (uint32_t)(kp / 8) * 128;
-        const uint32_t a_hi = smem_u32(smem + st * lay.stage_bytes), a_lo = a_hi + (uint32_t)(lay.rp / 8) * sbo;
-        const uint32_t b_hi = a_hi + (uint32_t)(lay.rp / 4) * sbo, b_lo = b_hi + (uint32_t)(lay.np / 8) * sbo;
+        const uint32_t a_hi = smem_u32(smem + st * lay.stage_bytes), a_lo = a_hi + (uint32_t)(mm / 8) * sbo;
+        const uint32_t b_hi = a_hi + (uint32_t)(mm / 4) * sbo, b_lo = b_hi + (uint32_t)(lay.np / 8) * sbo;
         for (int ks = 0; ks < nks; ++ks) {
           const uint32_t o = (uint32_t)ks * 256;
           mma_bf16(d, smem_desc(a_hi + o, 128, sbo), smem_desc(b_hi + o, 128, sbo), idesc, issued ? 1u : 0u);
@@ -340,7 +371,7 @@ __global__ void __launch_bounds__(kThreads, 6) coup_tc_kernel(const Seg* __restr
         if (fl & kLast) {
           mma_commit(&accf[b]);
           use_acc[b] += 1;
-          seg_i += 1;
+          grp_i += 1;
         }
       }
       // every product issued above has finished once this commit's phase completes
@@ -349,27 +380,35 @@ __global__ void __launch_bounds__(kThreads, 6) coup_tc_kernel(const Seg* __restr
       mbar_wait(&done, 0u, &never);
     }
   } else {
-    // epilogue: warp w holds accumulator rows 16 w .. 16 w + 15 in its lanes 0 .. 15; the
-    // segment's metadata and rank bounds are read before its products are waited for
-    uint32_t seg_i = 0, use_acc[kMaxAcc];
+    // epilogue: warps 2 sl and 2 sl + 1 hold slot sl's rows; with M = 64 warp w holds rows
+    // 16 w .. 16 w + 15 of the accumulator in its lanes 0 .. 15, with M = 128 rows 32 w ..
+    // 32 w + 31
+    const int sl = warp >> 1;
+    uint32_t grp_i = 0, use_acc[kMaxAcc];
     for (int b = 0; b < kMaxAcc; ++b) use_acc[b] = 0u;
-    const int row = 16 * warp + lane;
-    for (int64_t si = blockIdx.x; si < count; si += gridDim.x, ++seg_i) {
-      const Seg s = segs[first + si];
-      const Arenas* ar = ars + s.inst;
-      const int M = bound(ar, s.mref, s.m), N = bound(ar, s.nref, s.n);
-      const View out = view(ar, s.out);
-      const bool accum = s.flags & SF_ACC;
-      const int b = (int)(seg_i % (uint32_t)lay.nacc);
+    for (int64_t gi = blockIdx.x; gi < count; gi += gridDim.x, ++grp_i) {
+      const TcGroup g = groups[first + gi];
+      const Arenas* ar = ars + g.inst;
+      const bool have = g.out[sl] >= 0;
+      const int M = have ? bound(ar, g.mref[sl], g.m) : 0, N = bound(ar, g.nref, g.n);
+      // the group's M, decided from the slots' ranks as the copying warp did
+      int m8[2];
+      for (int s2 = 0; s2 < 2; ++s2)
+        m8[s2] = g.out[s2] < 0 ? 0 : (lay.trim ? max(8, (bound(ar, g.mref[s2], g.m) + 7) & ~7) : lay.rp);
+      const int rows_w = group_sr(lay, m8) == 32 ? 16 : 32;
+      const int row = rows_w * (warp & 1) + lane;  // row within the slot
+      const View out = view(ar, have ? g.out[sl] : g.out[sl ^ 1]);
+      const bool accum = (g.acc >> sl) & 1;
+      const int b = (int)(grp_i % (uint32_t)lay.nacc);
       if (!mbar_wait(&accf[b], use_acc[b] & 1u, &s_abort)) break;
       use_acc[b] += 1;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (16 * warp < M) {
+      if (rows_w * (warp & 1) < M) {
         for (int c0 = 0; c0 < N; c0 += 16) {
           float v[16];
           tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(b * lay.ncols + c0), v);
-          if (lane < 16 && row < M) {
-            const int64_t o = (int64_t)row * s.ldc + c0;
+          if (lane < rows_w && row < M) {
+            const int64_t o = (int64_t)row * g.ldc + c0;
             if (out.f32) {
               float* po = (float*)out.base + o;
               if (accum) {  // all loads first, then the stores
@@ -408,8 +447,8 @@ __global__ void __launch_bounds__(kThreads, 6) coup_tc_kernel(const Seg* __restr
 
 }  // namespace
 
-void launch_coup_tc(const Seg* d_segs, const Item* d_items, int64_t first, int64_t count, const Arenas* d_ars,
-                    int rp, int np, int kpmax, unsigned int* err, int variant, void* stream) {
+void launch_coup_tc(const TcGroup* d_groups, const TcStep* d_steps, int64_t first, int64_t count,
+                    const Arenas* d_ars, int rp, int np, int kpmax, unsigned int* err, int variant, void* stream) {
   if (count <= 0) return;
   static std::once_flag once;
   std::call_once(once, [] {
@@ -431,7 +470,7 @@ void launch_coup_tc(const Seg* d_segs, const Item* d_items, int64_t first, int64
   const int reg_cap = 65536 / (kThreads * regs), thr_cap = 2048 / kThreads;
   const int per_sm = std::max(1, std::min(std::min(sm_cap, reg_cap), std::min(thr_cap, 512 / lay.tmem_cols)));
   const int64_t grid = std::min<int64_t>(count, 152LL * per_sm);
-  coup_tc_kernel<<<(unsigned)grid, kThreads, lay.total, (cudaStream_t)stream>>>(d_segs, d_items, first, count, d_ars,
+  coup_tc_kernel<<<(unsigned)grid, kThreads, lay.total, (cudaStream_t)stream>>>(d_groups, d_steps, first, count, d_ars,
                                                                                 lay, err);
   add_kernel_launches(1);
 }
