@@ -6,12 +6,15 @@ merges, the top-down split) on inputs resident in device memory.  The metric is
 algorithmic throughput: (bytes of A + B + C at their actual ranks) / product time,
 in GB/s, with the product time itself reported beside it.
 
-  python bench.py [--gpus N --steps K --warmup W] [--workload cubes16x16|cubes4x4|batched48]
-                  [--precision fp64|mixed|tf32x3] [--impl ours|reference] [--no-extras]
+  python bench.py [--gpus N --steps K --warmup W] [--workload cubes16x16|cubes4x4|batched48|sphere262k]
+                  [--precision bf16x3|mixed|tf32x3|fp64] [--impl ours|reference] [--no-extras]
 
-Beside the headline precision the line carries the same product under the sv rule and
-in float64 (the two arms of the metric), each timed once after a warm-up, and an
-end-to-end run for a caller with a new structure (program built inside the timed run).
+The headline precision is the BF16 split one (H2_MIXED_BF16X3: the coupling products on
+the tensor cores as three BF16 products per split pair, the rest in float32, rank
+decisions and bases in float64), the large-scale configuration's arithmetic.  Beside it
+the line carries the same product in float32 (H2_MIXED_FP32), in float64 (the other arm
+of the metric) and under the sv rule, each timed once after a warm-up, and an end-to-end
+run for a caller with a new structure (program built inside the timed run).
 
 --impl reference times the CPU oracle (the plain float64 restatement of the method)
 on a bounded sample of the same geometry: the reference arm.
@@ -422,8 +425,10 @@ def sphere_main(args):
     # (rank cap 128: ranks of the oscillatory kernel grow with the electrical size of the
     # coarse clusters)
     cap = 128
+    # complex products run in float64 or complex float32 (the tensor-core splits are real
+    # only): the split precisions take the complex float32 product
     if args.precision not in ("fp64", "mixed"):
-        raise SystemExit("complex products run in fp64 or mixed precision")
+        args.precision = "mixed"
     prec = PRECISIONS[args.precision](lib)
     C = A.mmp(A, eps, precision=prec, rank_cap=cap)
     torch.cuda.synchronize()
@@ -489,7 +494,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cubes16x16", choices=list(WORKLOADS) + ["batched48"] + list(SPHERES))
-    ap.add_argument("--precision", default="mixed", choices=list(PRECISIONS))
+    ap.add_argument("--precision", default="bf16x3", choices=list(PRECISIONS))
     ap.add_argument("--trunc", default="paper", choices=["paper", "sv", "formatted"],
                     help="truncation rule; 'formatted' = fixed bases (the paper's comparison method)")
     ap.add_argument("--oracle-sample", action="store_true")
@@ -630,6 +635,9 @@ def main():
         # the float64 arm of the metric: the same product, every step in float64
         if args.precision != "fp64":
             extras["fp64"] = side_arm(lib, A, B, eps, lib.FP64, args.trunc, x, y_ref, with_roofline="fp64")
+        # the float32 product (every small product on the CUDA cores)
+        if args.precision not in ("fp64", "mixed"):
+            extras["mixed_fp32"] = side_arm(lib, A, B, eps, lib.MIXED_FP32, args.trunc, x, y_ref, with_roofline="mixed")
     # end to end for a caller with a new structure: every handle is released first, so
     # that the tree, the partition and the product program are built inside the timed run
     e2e_cold = None

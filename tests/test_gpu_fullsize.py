@@ -105,16 +105,24 @@ def test_config2_cube_array_65536_properties(lib):
 
 
 def test_config5_cube_array_1m_mixed(lib):
-    # the benchmark's workload and launch configuration: N = 1,048,576, mixed precision
+    # the benchmark's workload and launch configuration: N = 1,048,576, the BF16 split
+    # product (the headline) and the float32 one; both within the truncation bound
+    # against A(Bx), and within 2 eps of each other
     wa = inputs.workload_cube_array(16, 16, 4096)
     wb = inputs.workload_cube_array(16, 16, 4096, kernel="invr2")
     n = wa.points.shape[0]
     A = lib.h2_build(wa.points, wa.kernel, 32, 1.0, 1e-4)
     B = lib.h2_build(wb.points, wb.kernel, 32, 1.0, 1e-4)
-    C = A.mmp(B, 1e-4, precision=lib.MIXED_FP32)
-    C = A.mmp(B, 1e-4, precision=lib.MIXED_FP32, out=C)
-    err, _ = eq_error(lib, A, B, C, n)
-    assert err < math.sqrt(1e-4), err
-    info = C.info()
-    assert info["cap_hits"] == 0 and info["n"] == n
-    assert max(info["max_rank_row"]) <= 48
+    ys = {}
+    for p in (lib.MIXED_BF16X3, lib.MIXED_FP32):
+        C = A.mmp(B, 1e-4, precision=p, autotune=True)
+        C = A.mmp(B, 1e-4, precision=p, autotune=True, out=C)
+        err, x = eq_error(lib, A, B, C, n)
+        assert err < math.sqrt(1e-4), err
+        info = C.info()
+        assert info["cap_hits"] == 0 and info["n"] == n
+        assert max(info["max_rank_row"]) <= 48
+        ys[p] = C.matvec(x)
+        C.destroy()
+    yb, yf = ys[lib.MIXED_BF16X3], ys[lib.MIXED_FP32]
+    assert float((yb - yf).norm() / yf.norm()) < 2e-4
