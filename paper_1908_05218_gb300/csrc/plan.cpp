@@ -698,12 +698,28 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         G3r[t] = pb.alloc(AR_S, (int64_t)gr * gr);
         G3c[t] = pb.alloc(AR_S, (int64_t)gc * gc);
       }
+      // (every stacked operand is taken per child half, each bounded by the child's rank:
+      // the rows / columns and k past a child's rank are zero padding)
       pb.begin();
       for (int64_t p = 0; p < nb; ++p) {
         const Block& b = bl[p];
         if (b.kind != KNL) continue;
-        pb.gemm1(Y[p], gr, rB(l), 2 * rB(c), 2 * rB(c), rB(l), rB(l), 0, Ac[p], tB(B.Er(l, b.s)), -1, BR(l, b.s));
-        pb.gemm1(Yb[p], cA(l), gc, 2 * cA(c), cA(l), gc, gc, SF_TA, tA(A.Ec(l, b.t)), Bc[p], AC(l, b.t));
+        for (int a = 0; a < 2; ++a) {  // rows of C's row child a; k over B's row children
+          std::vector<Item> it;
+          for (int bb = 0; bb < 2; ++bb)
+            it.push_back(Item(Ac[p] + (int64_t)a * hr * 2 * rB(c) + (int64_t)bb * rB(c),
+                              tB(B.Er(l, b.s) + (int64_t)bb * rB(c) * rB(l)), BR(c, 2 * b.s + bb)));
+          pb.gemm(Y[p] + (int64_t)a * hr * rB(l), hr, rB(l), rB(c), 2 * rB(c), rB(l), rB(l), 0, it,
+                  CR(c, 2 * b.t + a), BR(l, b.s));
+        }
+        for (int bc = 0; bc < 2; ++bc) {  // columns of C's column child bc; k over A's column children
+          std::vector<Item> it;
+          for (int aa = 0; aa < 2; ++aa)
+            it.push_back(Item(tA(A.Ec(l, b.t) + (int64_t)aa * cA(c) * cA(l)),
+                              Bc[p] + (int64_t)aa * cA(c) * gc + (int64_t)bc * hc, AC(c, 2 * b.t + aa)));
+          pb.gemm(Yb[p] + (int64_t)bc * hc, cA(l), hc, cA(c), cA(l), gc, gc, SF_TA, it, AC(l, b.t),
+                  CC(c, 2 * b.s + bc));
+        }
       }
       for (int64_t t = 0; t < nc; ++t)
         for (int a = 0; a < 2; ++a) {
@@ -778,16 +794,37 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
           int32_t p = st.col_list[l][q];
           if (bl[p].kind == KNL) c2.push_back({Yb[p], Yb[p], AC(l, bl[p].t)});
         }
-        if (!r2.empty()) {
+        // (each Gram matrix in its 2 x 2 blocks of children, bounded by the children's ranks)
+        if (!r2.empty()) {  // Eq. case2-ch-nl
           G2r[t] = pb.alloc(AR_S, (int64_t)gr * gr);
-          pb.gemm(G2r[t], gr, gr, rB(l), rB(l), rB(l), gr, SF_TB | SF_CB, r2);  // Eq. case2-ch-nl
+          for (int a = 0; a < 2; ++a)
+            for (int a2 = 0; a2 < 2; ++a2) {
+              std::vector<Item> it;
+              for (const Item& y : r2)
+                it.push_back(Item(y.a + (int64_t)a * hr * rB(l), y.b + (int64_t)a2 * hr * rB(l), y.kref));
+              pb.gemm(G2r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr, hr, hr, rB(l), rB(l), rB(l), gr,
+                      SF_TB | SF_CB, it, CR(c, 2 * t + a), CR(c, 2 * t + a2));
+            }
         }
         if (!c2.empty()) {
           G2c[t] = pb.alloc(AR_S, (int64_t)gc * gc);
-          pb.gemm(G2c[t], gc, gc, cA(l), gc, gc, gc, SF_TA | SF_CB, c2);
+          for (int b = 0; b < 2; ++b)
+            for (int b2 = 0; b2 < 2; ++b2) {
+              std::vector<Item> it;
+              for (const Item& y : c2) it.push_back(Item(y.a + (int64_t)b * hc, y.b + (int64_t)b2 * hc, y.kref));
+              pb.gemm(G2c[t] + (int64_t)b * hc * gc + (int64_t)b2 * hc, hc, hc, cA(l), gc, gc, gc, SF_TA | SF_CB, it,
+                      CC(c, 2 * t + b), CC(c, 2 * t + b2));
+            }
         }
-        pb.gemm1(G3r[t], gr, gr, rA(l), rA(l), rA(l), gr, SF_TB | SF_CB, Wr[t], Wr[t], -1, -1, AR(l, t));  // Eq. case3-ch-nl
-        pb.gemm1(G3c[t], gc, gc, cB(l), cB(l), cB(l), gc, SF_TB | SF_CB, Wc[t], Wc[t], -1, -1, BC(l, t));
+        for (int a = 0; a < 2; ++a)  // Eq. case3-ch-nl
+          for (int a2 = 0; a2 < 2; ++a2) {
+            pb.gemm1(G3r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr, hr, hr, rA(l), rA(l), rA(l), gr, SF_TB | SF_CB,
+                     Wr[t] + (int64_t)a * hr * rA(l), Wr[t] + (int64_t)a2 * hr * rA(l), CR(c, 2 * t + a),
+                     CR(c, 2 * t + a2), AR(l, t));
+            pb.gemm1(G3c[t] + (int64_t)a * hc * gc + (int64_t)a2 * hc, hc, hc, cB(l), cB(l), cB(l), gc, SF_TB | SF_CB,
+                     Wc[t] + (int64_t)a * hc * cB(l), Wc[t] + (int64_t)a2 * hc * cB(l), CC(c, 2 * t + a),
+                     CC(c, 2 * t + a2), BC(l, t));
+          }
       }
       pb.end("nl_gram", l);
       for (size_t q = 0; q < lt.tg.size(); ++q)
@@ -849,11 +886,16 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
                  AR(l, t));
         pb.gemm1(PB[l][t], cB(l), cC(l), LS, cB(l), cC(l), cC(l), SF_TA | SF_CB, tB(B.Vc(t)), tCb(C.Vc(t)), BC(l, t),
                  CC(l, t));
-      } else {
-        pb.gemm1(PA[l][t], rC(l), rA(l), gr, rC(l), rA(l), rA(l), SF_TA | SF_CA, tCb(C.Er(l, t)), Wr[t], CR(l, t),
-                 AR(l, t));
-        pb.gemm1(PB[l][t], cB(l), cC(l), gc, cB(l), cC(l), cC(l), SF_TA | SF_CB, cplx ? Wcp[t] : Wc[t], tCb(C.Ec(l, t)),
-                 BC(l, t), CC(l, t));
+      } else {  // (k over the children, each bounded by its rank)
+        const int hr = rC(c), hc = cC(c);
+        std::vector<Item> ia, ib;
+        for (int a = 0; a < 2; ++a) {
+          ia.push_back(Item(tCb(C.Er(l, t) + (int64_t)a * hr * rC(l)), Wr[t] + (int64_t)a * hr * rA(l), CR(c, 2 * t + a)));
+          ib.push_back(Item((cplx ? Wcp[t] : Wc[t]) + (int64_t)a * hc * cB(l), tCb(C.Ec(l, t) + (int64_t)a * hc * cC(l)),
+                            CC(c, 2 * t + a)));
+        }
+        pb.gemm(PA[l][t], rC(l), rA(l), hr, rC(l), rA(l), rA(l), SF_TA | SF_CA, ia, CR(l, t), AR(l, t));
+        pb.gemm(PB[l][t], cB(l), cC(l), hc, cB(l), cC(l), cC(l), SF_TA | SF_CB, ib, BC(l, t), CC(l, t));
       }
     }
     // (with the tensor-core coupling pass the coupling operands go out as tiles: A
@@ -875,13 +917,18 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         ns = P.segs.size();
         pb.gemm1(Bch[p], LS, cC(l), LS, LS, cC(l), cC(l), SF_CB, tB(B.F(b.idx)), tCb(C.Vc(b.s)), -1, CC(l, b.s));
         if (tl) tile_out(ns, NP, KP1, true);
-      } else if (!leaf && b.kind == KNL) {
-        pb.gemm1(Ahat[l][p], rC(l), rB(l), gr, rC(l), rB(l), rB(l), SF_TA | SF_CA, tCb(C.Er(l, b.t)), Y[p], CR(l, b.t),
-                 BR(l, b.s));
+      } else if (!leaf && b.kind == KNL) {  // (k over the children, each bounded by its rank)
+        const int hr = rC(c), hc = cC(c);
+        std::vector<Item> ia, ib;
+        for (int a = 0; a < 2; ++a) {
+          ia.push_back(Item(tCb(C.Er(l, b.t) + (int64_t)a * hr * rC(l)), Y[p] + (int64_t)a * hr * rB(l),
+                            CR(c, 2 * b.t + a)));
+          ib.push_back(Item(Yb[p] + (int64_t)a * hc, tCb(C.Ec(l, b.s) + (int64_t)a * hc * cC(l)), CC(c, 2 * b.s + a)));
+        }
+        pb.gemm(Ahat[l][p], rC(l), rB(l), hr, rC(l), rB(l), rB(l), SF_TA | SF_CA, ia, CR(l, b.t), BR(l, b.s));
         if (tl) tile_out(ns, RP, KP2, false);
         ns = P.segs.size();
-        pb.gemm1(Bhat[l][p], cA(l), cC(l), gc, gc, cC(l), cC(l), SF_CB, Yb[p], tCb(C.Ec(l, b.s)), AC(l, b.t),
-                 CC(l, b.s));
+        pb.gemm(Bhat[l][p], cA(l), cC(l), hc, gc, cC(l), cC(l), SF_CB, ib, AC(l, b.t), CC(l, b.s));
         if (tl) tile_out(ns, NP, KP3, true);
       }
     }
@@ -957,9 +1004,14 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       pb.begin();
       for (size_t q = 0; q < lt.tg.size(); ++q) {
         Target& T = lt.tg[q];
-        if (Mt[q] >= 0)
-          pb.gemm1(T.ssum, rC(l), cC(l), gr, rC(l), cC(l), cC(l), SF_TA | SF_CA | SF_ACC, tCb(C.Er(l, T.i)), Mt[q],
-                   CR(l, T.i), CC(l, T.k));
+        if (Mt[q] >= 0) {  // (k over the children of i, each bounded by its rank)
+          const int hr = rC(c);
+          std::vector<Item> it;
+          for (int a = 0; a < 2; ++a)
+            it.push_back(Item(tCb(C.Er(l, T.i) + (int64_t)a * hr * rC(l)), Mt[q] + (int64_t)a * hr * cC(l),
+                              CR(c, 2 * T.i + a)));
+          pb.gemm(T.ssum, rC(l), cC(l), hr, rC(l), cC(l), cC(l), SF_TA | SF_CA | SF_ACC, it, CR(l, T.i), CC(l, T.k));
+        }
       }
       pb.end("coup", l);
     }
@@ -1175,17 +1227,23 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
           int32_t pp = st.find(l, st.blocks[c][p].t >> 1, st.blocks[c][p].s >> 1);
           if (pp >= 0 && X[pp] >= 0) H[c][p] = pb.alloc(AR_P, (int64_t)rC(c) * cC(c));
         }
+    // (the children's halves of Xt and X, each bounded by the children's ranks)
     pb.begin();
     for (size_t p = 0; p < bl.size(); ++p)
       if (Xt[p] >= 0)
-        pb.gemm1(Xt[p], rC(l), 2 * hc, cC(l), cC(l), cC(l), 2 * hc, SF_TB, H[l][p], tCb(C.Ec(l, bl[p].s)),
-                 CR(l, bl[p].t), -1, CC(l, bl[p].s));
+        for (int b = 0; b < 2; ++b)
+          pb.gemm1(Xt[p] + (int64_t)b * hc, rC(l), hc, cC(l), cC(l), cC(l), 2 * hc, SF_TB, H[l][p],
+                   tCb(C.Ec(l, bl[p].s) + (int64_t)b * hc * cC(l)), CR(l, bl[p].t), CC(c, 2 * bl[p].s + b),
+                   CC(l, bl[p].s));
     pb.end("split", l);
     pb.begin();
     for (size_t p = 0; p < bl.size(); ++p)
       if (X[p] >= 0)
-        pb.gemm1(X[p], 2 * hr, 2 * hc, rC(l), rC(l), 2 * hc, 2 * hc, 0, tCb(C.Er(l, bl[p].t)), Xt[p], -1, -1,
-                 CR(l, bl[p].t));
+        for (int a = 0; a < 2; ++a)
+          for (int b = 0; b < 2; ++b)
+            pb.gemm1(X[p] + (int64_t)a * hr * 2 * hc + (int64_t)b * hc, hr, hc, rC(l), rC(l), 2 * hc, 2 * hc, 0,
+                     tCb(C.Er(l, bl[p].t) + (int64_t)a * hr * rC(l)), Xt[p] + (int64_t)b * hc, CR(c, 2 * bl[p].t + a),
+                     CC(c, 2 * bl[p].s + b), CR(l, bl[p].t));
     pb.end("split", l);
     std::vector<std::pair<int64_t, int64_t>> Fupd;
     std::vector<int32_t> Frow;
