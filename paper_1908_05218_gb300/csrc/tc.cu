@@ -75,7 +75,8 @@ struct TcLayout {
   int nacc;        // accumulators
   int trim;        // copy only the rows up to the targets' ranks (else whole tiles)
   int dynm;        // M = 64 for the groups whose ranks fit 32 rows per slot
-  int stage_bytes; // a stage: A hi (m rows), A lo, B hi (np rows), B lo, at the step's k
+  int stage_bytes; // a stage: A hi (64 rows), A lo, B hi (np rows), B lo, at the step's k;
+                   // a step of M = 128 takes two consecutive stages
   int ncols;       // tensor-memory columns of one accumulator (np rounded up to 16)
   int tmem_cols;   // allocated columns: nacc accumulators, a power of two >= 32
   int total;       // dynamic shared memory
@@ -83,7 +84,7 @@ struct TcLayout {
 
 // launch configurations (stages, accumulators, trimmed copies, M per group), all with the
 // same products in the same order: the autotuner picks one per launch group
-constexpr int kTcConfigs[kTcVariants][4] = {{4, 2, 1, 1}, {4, 2, 1, 0}, {4, 4, 1, 1}, {3, 2, 1, 0}};
+constexpr int kTcConfigs[kTcVariants][4] = {{4, 2, 1, 1}, {3, 2, 1, 1}, {6, 2, 1, 1}, {4, 4, 1, 1}};
 
 TcLayout tc_layout(int rp, int np, int kpmax, int variant) {
   TcLayout t;
@@ -99,7 +100,7 @@ TcLayout tc_layout(int rp, int np, int kpmax, int variant) {
   t.nm = t.m == 128 ? (np + 15) & ~15 : np;
   // (the MMA reads nm rows from B's lo part, which starts np rows into B: the stage holds
   // m + nm rows of each part)
-  t.stage_bytes = ((t.m + t.nm) * kpmax * 4 + 1023) & ~1023;
+  t.stage_bytes = ((64 + (t.sr == 64 ? t.nm : np)) * kpmax * 4 + 1023) & ~1023;
   t.ncols = (np + 15) & ~15;
   int c = 32;
   while (c < t.nacc * t.ncols) c <<= 1;
@@ -190,7 +191,9 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, float v[16]) {
 }
 
 // what the copying warp tells the issuing thread about the step in a stage
-enum : int { kFirst = 1, kLast = 2, kEnd = 4, kM128 = 8 };
+// kDouble: the step (M = 128) takes this stage and the next; kCont: the second stage of
+// such a step; kSkip: a stage passed over (a double step does not wrap around the ring)
+enum : int { kFirst = 1, kLast = 2, kEnd = 4, kM128 = 8, kDouble = 16, kCont = 32, kSkip = 64 };
 
 // a group's rows per slot: 32 when both targets' ranks fit (M = 64), else the launch's
 __device__ __forceinline__ int group_sr(const TcLayout& lay, const int m8[2]) {
@@ -263,15 +266,32 @@ __global__ void __launch_bounds__(kThreads, 6) coup_tc_kernel(const TcGroup* __r
           kp = sp.kpad;
           ks = max(1, (bound(ar, sp.kref, kp) + 15) >> 4);
         }
-        for (int q = 0; q < nb; ++q, ++it) {
+        for (int q = 0; q < nb; ++q) {
           const unsigned long long a0 = __shfl_sync(0xffffffffu, pa0, q), a1 = __shfl_sync(0xffffffffu, pa1, q);
           const unsigned long long b = __shfl_sync(0xffffffffu, pb, q);
           const int k = __shfl_sync(0xffffffffu, kp, q), ksteps = __shfl_sync(0xffffffffu, ks, q);
           int good = 1;
           if (lane == 0) {
+            // a stage is taken once its previous use's products have completed
+            auto take = [&](uint32_t i) {
+              const uint32_t use = i / nst;
+              return use == 0 || mbar_wait(&empty[i % nst], (use - 1) & 1u, &s_abort);
+            };
+            const bool dbl = mm == 128;
+            if (dbl && it % nst == nst - 1) {  // no room for two stages before the ring's end
+              if (!take(it)) {
+                good = 0;
+              } else {
+                const int st = (int)(it % nst);
+                slot_k[st] = 0;
+                slot_s[st] = 0;
+                slot_f[st] = kSkip;
+                mbar_arrive(&full[st]);
+                ++it;
+              }
+            }
             const int st = (int)(it % nst);
-            const uint32_t use = it / nst;
-            if (use > 0 && !mbar_wait(&empty[st], (use - 1) & 1u, &s_abort)) {
+            if (!good || !take(it) || (dbl && !take(it + 1))) {
               good = 0;
             } else {
               // stage: A hi (M rows), A lo (M rows), B hi (np rows), B lo (np rows); a tile
@@ -284,7 +304,7 @@ __global__ void __launch_bounds__(kThreads, 6) coup_tc_kernel(const TcGroup* __r
               for (int sl = 0; sl < 2; ++sl) tx += 4u * m8[sl] * k;
               slot_k[st] = k;
               slot_s[st] = ksteps;
-              slot_f[st] = (b0 + q == 0 ? kFirst : 0) | (b0 + q == g.count - 1 ? kLast : 0) | (mm == 128 ? kM128 : 0);
+              slot_f[st] = (b0 + q == 0 ? kFirst : 0) | (b0 + q == g.count - 1 ? kLast : 0) | (dbl ? kM128 | kDouble : 0);
               mbar_expect_tx(&full[st], tx);
               for (int sl = 0; sl < 2; ++sl) {
                 if (!m8[sl]) continue;
@@ -305,8 +325,16 @@ __global__ void __launch_bounds__(kThreads, 6) coup_tc_kernel(const TcGroup* __r
                 bulk_copy(sb, (const void*)b, cb, &full[st]);
                 bulk_copy(sb + part_b, (const void*)(b + part_b), cb, &full[st]);
               }
+              if (dbl) {  // the second stage of the step: no copies of its own
+                slot_k[st + 1] = 0;
+                slot_s[st + 1] = 0;
+                slot_f[st + 1] = kCont;
+                mbar_arrive(&full[st + 1]);
+              }
+              it += dbl ? 2 : 1;
             }
           }
+          it = __shfl_sync(0xffffffffu, it, 0);
           if (!__shfl_sync(0xffffffffu, good, 0)) {
             ok = false;
             break;
@@ -347,6 +375,10 @@ __global__ void __launch_bounds__(kThreads, 6) coup_tc_kernel(const TcGroup* __r
         if (!mbar_wait(&full[st], (it / nst) & 1u, &s_abort)) break;
         const int kp = slot_k[st], nks = slot_s[st], fl = slot_f[st];
         if (fl & kEnd) break;
+        if (fl & (kSkip | kCont)) {  // (a continuation's stage is free once the step's products are)
+          mma_commit(&empty[st]);
+          continue;
+        }
         if (fl & kFirst) {
           b = (int)(grp_i % (uint32_t)lay.nacc);
           if (use_acc[b] > 0 && !mbar_wait(&acce[b], (use_acc[b] - 1) & 1u, &s_abort)) break;
