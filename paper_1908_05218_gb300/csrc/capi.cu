@@ -505,6 +505,11 @@ void validate_plan(const Plan& P, const int64_t sizes[kArenas]) {
           check_tile(it.a, s.trows, s.lda, s.m, s.n, tt, "tile sum input");
           continue;
         }
+        if (ta) {  // a transposed input (n x m)
+          if (s.lda < s.m) throw Error(H2_EINTERNAL, "sum lda < m");
+          check(it.a, (int64_t)(s.n - 1) * s.lda + s.m, "sum input");
+          continue;
+        }
         if (s.lda < s.n) throw Error(H2_EINTERNAL, "sum lda < n");
         check(it.a, (int64_t)(s.m - 1) * s.lda + s.n, "sum input");
         continue;

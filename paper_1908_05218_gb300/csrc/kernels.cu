@@ -97,7 +97,8 @@ __global__ void __launch_bounds__(GNT, 12) seg_gemm_kernel(const Seg* __restrict
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
               int r = 4 * ty + i, c = 4 * tx + j;
-              if (r < mc && c < nc) acc[i][j] += A[(int64_t)(m0 + r) * s.lda + n0 + c];
+              if (r < mc && c < nc)  // (SF_TA: the input is read transposed)
+                acc[i][j] += ta ? A[(int64_t)(n0 + c) * s.lda + m0 + r] : A[(int64_t)(m0 + r) * s.lda + n0 + c];
             }
         }
       } else {
@@ -274,7 +275,7 @@ __global__ void __launch_bounds__(GNT, 12) seg_gemm32_kernel(const Seg* __restri
                 if (tiled)  // an operand tile of the BF16 split product (its lda: the tile's k)
                   acc[i][j] += tile_load((const char*)A, s.trows, s.lda, tt ? n0 + c : m0 + r, tt ? m0 + r : n0 + c);
                 else
-                  acc[i][j] += A[(int64_t)(m0 + r) * s.lda + n0 + c];
+                  acc[i][j] += ta ? A[(int64_t)(n0 + c) * s.lda + m0 + r] : A[(int64_t)(m0 + r) * s.lda + n0 + c];
               }
             }
         }
@@ -547,7 +548,7 @@ __global__ void __launch_bounds__(256) seg_sum_kernel(const Seg* __restrict__ se
       for (int u = 0; u < 4; ++u)
         if (e0 + 32 * u + lane < total)
           acc[u] += tiled ? (T)tile_load((const char*)A, s.trows, s.lda, tt ? c[u] : r[u], tt ? r[u] : c[u])
-                          : A[(int64_t)r[u] * s.lda + c[u]];
+                          : (s.flags & SF_TA) ? A[(int64_t)c[u] * s.lda + r[u]] : A[(int64_t)r[u] * s.lda + c[u]];
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u)

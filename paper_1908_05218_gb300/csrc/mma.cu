@@ -377,7 +377,8 @@ __global__ void __launch_bounds__(kThreads) seg_mma_tf32x3_kernel(const Seg* __r
       for (int e = tid; e < M * N; e += kThreads) {
         const int r = e / N, c = e - r * N;
         float acc = 0.f;
-        for (int q = 0; q < s.count; ++q) acc += ptr_of<float>(ar, it[q].a)[(int64_t)r * s.lda + c];
+        for (int q = 0; q < s.count; ++q)  // (SF_TA: the input is read transposed)
+          acc += ptr_of<float>(ar, it[q].a)[ta ? (int64_t)c * s.lda + r : (int64_t)r * s.lda + c];
         st<float>(out, (int64_t)r * s.ldc + c, acc, accum);
       }
       continue;

@@ -756,11 +756,19 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       }
       if (missing) throw Error(H2_EINTERNAL, "missing child target");
       auto child_ssum = [&](int32_t q, int a, int b) { return css[(size_t)q * 4 + a * 2 + b]; };
+      // the Gram matrices are symmetric (real) or Hermitian: of their 2 x 2 child blocks
+      // the block (1, 0) of a real one is the transpose of (0, 1), copied after the Gram
+      // launches instead of computed (the same products in the same order give exactly
+      // the transposed values)
+      std::vector<std::array<int64_t, 3>> mirror;  // (Gram matrix, half, leading dim)
+      auto skip_10 = [&](int a, int a2) { return !cplx && a == 1 && a2 == 0; };
       for (int64_t t = 0; t < nc && !formatted; ++t) {
         if (!trow[t].empty()) {
           G1r[t] = pb.alloc(AR_S, (int64_t)gr * gr);
+          if (!cplx) mirror.push_back({G1r[t], hr, gr});
           for (int a = 0; a < 2; ++a)
             for (int a2 = 0; a2 < 2; ++a2) {
+              if (skip_10(a, a2)) continue;
               std::vector<Item> it;
               for (auto& tq : trow[t])
                 for (int b = 0; b < 2; ++b)
@@ -772,8 +780,10 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         }
         if (!tcol[t].empty()) {
           G1c[t] = pb.alloc(AR_S, (int64_t)gc * gc);
+          if (!cplx) mirror.push_back({G1c[t], hc, gc});
           for (int b = 0; b < 2; ++b)
             for (int b2 = 0; b2 < 2; ++b2) {
+              if (skip_10(b, b2)) continue;
               std::vector<Item> it;
               for (auto& tq : tcol[t])
                 for (int a = 0; a < 2; ++a)
@@ -797,8 +807,10 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         // (each Gram matrix in its 2 x 2 blocks of children, bounded by the children's ranks)
         if (!r2.empty()) {  // Eq. case2-ch-nl
           G2r[t] = pb.alloc(AR_S, (int64_t)gr * gr);
+          if (!cplx) mirror.push_back({G2r[t], hr, gr});
           for (int a = 0; a < 2; ++a)
             for (int a2 = 0; a2 < 2; ++a2) {
+              if (skip_10(a, a2)) continue;
               std::vector<Item> it;
               for (const Item& y : r2)
                 it.push_back(Item(y.a + (int64_t)a * hr * rB(l), y.b + (int64_t)a2 * hr * rB(l), y.kref));
@@ -808,16 +820,23 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         }
         if (!c2.empty()) {
           G2c[t] = pb.alloc(AR_S, (int64_t)gc * gc);
+          if (!cplx) mirror.push_back({G2c[t], hc, gc});
           for (int b = 0; b < 2; ++b)
             for (int b2 = 0; b2 < 2; ++b2) {
+              if (skip_10(b, b2)) continue;
               std::vector<Item> it;
               for (const Item& y : c2) it.push_back(Item(y.a + (int64_t)b * hc, y.b + (int64_t)b2 * hc, y.kref));
               pb.gemm(G2c[t] + (int64_t)b * hc * gc + (int64_t)b2 * hc, hc, hc, cA(l), gc, gc, gc, SF_TA | SF_CB, it,
                       CC(c, 2 * t + b), CC(c, 2 * t + b2));
             }
         }
+        if (!cplx) {
+          mirror.push_back({G3r[t], hr, gr});
+          mirror.push_back({G3c[t], hc, gc});
+        }
         for (int a = 0; a < 2; ++a)  // Eq. case3-ch-nl
           for (int a2 = 0; a2 < 2; ++a2) {
+            if (skip_10(a, a2)) continue;
             pb.gemm1(G3r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr, hr, hr, rA(l), rA(l), rA(l), gr, SF_TB | SF_CB,
                      Wr[t] + (int64_t)a * hr * rA(l), Wr[t] + (int64_t)a2 * hr * rA(l), CR(c, 2 * t + a),
                      CR(c, 2 * t + a2), AR(l, t));
@@ -825,6 +844,14 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
                      Wc[t] + (int64_t)a * hc * cB(l), Wc[t] + (int64_t)a2 * hc * cB(l), CC(c, 2 * t + a),
                      CC(c, 2 * t + a2), BC(l, t));
           }
+      }
+      pb.end("nl_gram", l);
+      pb.begin();  // the (1, 0) blocks: transposes of the (0, 1) blocks (plain sums)
+      for (const auto& mm : mirror) {
+        if (mm[1] <= 0) continue;
+        const int64_t src = mm[0] + mm[1];
+        pb.sum(mm[0] + mm[1] * mm[2], (int)mm[1], (int)mm[1], (int)mm[2], (int)mm[2], false, &src, 1);
+        P.segs.back().flags |= SF_TA;
       }
       pb.end("nl_gram", l);
       for (size_t q = 0; q < lt.tg.size(); ++q)
