@@ -491,6 +491,8 @@ void validate_plan(const Plan& P, const int64_t sizes[kArenas]) {
   auto check_seg = [&](const Seg& s) {
     bool ta = s.flags & SF_TA, tb = s.flags & SF_TB;
     const bool tile = s.flags & SF_TILE, tt = s.flags & SF_TILE_T;
+    if ((s.flags2 & SF2_SYM) && (s.m != s.n || s.mref != s.nref || (s.flags & (SF_SUM | SF_TILE))))
+      throw Error(H2_EINTERNAL, "symmetric block that is not square");
     if (tile && !(s.flags & SF_SUM)) {
       if (s.flags & SF_ACC) throw Error(H2_EINTERNAL, "tile outputs are written, not accumulated");
       check_tile(s.out, s.trows, s.ldc, s.m, s.n, tt, "tile output");

@@ -123,6 +123,10 @@ inline int64_t offset_of(int64_t t) { return t & kOffMask; }
 // element (r, c) sits at tile position (c, r).  Only in products of H2_MIXED_BF16X3.
 enum SegFlags : uint8_t { SF_TA = 1, SF_TB = 2, SF_ACC = 4, SF_SUM = 8, SF_CA = 16, SF_CB = 32, SF_TILE = 64,
                           SF_TILE_T = 128 };
+// Seg::flags2, SF2_SYM: the output block lies on the diagonal of a symmetric matrix (m ==
+// n, mref == nref): the float32 kernel computes its lower tiles and 4 x 4 blocks and writes
+// each off-diagonal one to both positions (mixed real products only)
+enum SegFlags2 : uint8_t { SF2_SYM = 1 };
 enum RankSrc : int32_t { RK_AR = 0, RK_AC = 1, RK_BR = 2, RK_BC = 3, RK_CR = 4, RK_CC = 5 };
 constexpr int kRefShift = 26;
 inline int32_t rref(RankSrc s, int node) { return (int32_t)((s << kRefShift) | node); }
@@ -132,7 +136,7 @@ struct Seg {
   int16_t m, n, k, lda, ldb, ldc;
   int32_t mref, nref;
   uint8_t flags;
-  uint8_t pad0;
+  uint8_t flags2;  // SegFlags2
   int16_t inst;  // product instance: index into the launch's arena tables (0 for one product)
   int32_t trows;  // SF_TILE: rows of the tile (a multiple of 8)
 };

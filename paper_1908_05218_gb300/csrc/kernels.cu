@@ -290,20 +290,34 @@ __global__ void __launch_bounds__(GNT, 12) seg_gemm32_kernel(const Seg* __restri
     }
     return;
   }
+  // a diagonal block of a symmetric matrix: its lower tiles and, in a tile on the
+  // diagonal, its lower 4 x 4 blocks only; every off-diagonal value is also written to
+  // the transposed position
+  const bool sym = s.flags2 & SF2_SYM;
   for (int n0 = blockIdx.y * TILE; n0 < N; n0 += gridDim.y * TILE) {
     const int nc = min(TILE, N - n0);
     for (int m0 = 0; m0 < M; m0 += TILE) {
+      if (sym && n0 > m0) continue;
       const int mc = min(TILE, M - m0);
-      // the tile's live 4 x 4 blocks go to threads 0 .. nthr-1 (row-major); idle
-      // threads read block 0.  A tile of at most 32 live blocks (e.g. 20 x 24) is
-      // computed by both warps on the same blocks, each over every other k-chunk of
-      // four, and the two partial sums are added in a fixed order at the end;
-      // otherwise a warp whose threads all lie beyond the blocks skips the arithmetic
-      const int ncq = (nc + 3) >> 2, nthr = ((mc + 3) >> 2) * ncq;
+      const bool tri = sym && m0 == n0;  // (then mc == nc)
+      // the tile's live 4 x 4 blocks go to threads 0 .. nthr-1 (row-major; a triangle on
+      // a symmetric diagonal tile); idle threads read block 0.  A tile of at most 32 live
+      // blocks (e.g. 20 x 24) is computed by both warps on the same blocks, each over
+      // every other k-chunk of four, and the two partial sums are added in a fixed order
+      // at the end; otherwise a warp whose threads all lie beyond the blocks skips the
+      // arithmetic
+      const int ncq = (nc + 3) >> 2, nthr = tri ? ncq * (ncq + 1) / 2 : ((mc + 3) >> 2) * ncq;
       const bool split = nthr <= 32;
       const int me = split ? lane : tid;
       const bool mine = me < nthr;
-      const int qy = mine ? me / ncq : 0, qx = mine ? me - qy * ncq : 0;
+      int qy = 0, qx = 0;
+      if (mine && tri) {
+        while ((qy + 1) * (qy + 2) / 2 <= me) ++qy;
+        qx = me - qy * (qy + 1) / 2;
+      } else if (mine) {
+        qy = me / ncq;
+        qx = me - qy * ncq;
+      }
       const bool live = split || (tid & ~31) < nthr;
       const int k0 = split ? 4 * (tid >> 5) : 0, kstep = split ? 8 : 4;
       float acc[4][4];
@@ -472,12 +486,16 @@ __global__ void __launch_bounds__(GNT, 12) seg_gemm32_kernel(const Seg* __restri
               if (r - m0 < mc && c - n0 < nc) tile_store(out.base, s.trows, s.ldc, tt ? c : r, tt ? r : c, acc[i][j]);
             }
         } else {
+          const bool mirror = sym && !(tri && qx == qy);  // (a diagonal block holds both halves)
 #pragma unroll
           for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
               const int r = 4 * qy + i, c = 4 * qx + j;
-              if (r < mc && c < nc) st<float>(out, (int64_t)(m0 + r) * s.ldc + n0 + c, acc[i][j], accum);
+              if (r < mc && c < nc) {
+                st<float>(out, (int64_t)(m0 + r) * s.ldc + n0 + c, acc[i][j], accum);
+                if (mirror) st<float>(out, (int64_t)(n0 + c) * s.ldc + m0 + r, acc[i][j], accum);
+              }
             }
         }
       }

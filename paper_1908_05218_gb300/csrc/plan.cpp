@@ -363,6 +363,12 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
     sg.ldc = (int16_t)kp;
     sg.trows = tr;
   };
+  // the segment just emitted for output `out`, if any, is a diagonal block of a symmetric
+  // Gram matrix: the float32 kernel computes its lower half (SF2_SYM)
+  const bool symok = !cplx && (prm.precision == H2_MIXED_FP32 || prm.precision == H2_MIXED_BF16X3);
+  auto sym_at = [&](int64_t out) {
+    if (symok && !P.segs.empty() && P.segs.back().out == out) P.segs.back().flags2 |= SF2_SYM;
+  };
   // the sum segment just emitted, if any, reads operand tiles
   auto tile_in = [&](size_t nseg, int tr, int kp, bool transposed) {
     if (P.segs.size() == nseg) return;
@@ -569,7 +575,9 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       }
       for (int64_t t = 0; t < nc && !formatted; ++t) {
         pb.gemm1(G3r[t], LS, LS, rA(l), rA(l), rA(l), LS, SF_TB | SF_CB, tA(A.Vr(t)), tA(A.Vr(t)), -1, -1, AR(l, t));
+        sym_at(G3r[t]);
         pb.gemm1(G3c[t], LS, LS, cB(l), cB(l), cB(l), LS, SF_TB | SF_CB, tB(B.Vc(t)), tB(B.Vc(t)), -1, -1, BC(l, t));
+        sym_at(G3c[t]);
       }
       pb.end("leaf_blockprod", l);
       // L2: dense targets (Sec. III-A) and Gram pieces
@@ -598,10 +606,12 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         if (!r2.empty()) {
           G2r[t] = pb.alloc(AR_S, LS2);
           pb.gemm(G2r[t], LS, LS, rB(l), rB(l), rB(l), LS, SF_TB | SF_CB, r2);  // Eq. Gr2L
+          sym_at(G2r[t]);
         }
         if (!c2.empty()) {
           G2c[t] = pb.alloc(AR_S, LS2);
           pb.gemm(G2c[t], LS, LS, cA(l), LS, LS, LS, SF_TA | SF_CB, c2);  // Eq. case2-ch
+          sym_at(G2c[t]);
         }
       }
       pb.end("leaf_dense_gram", l);
@@ -637,10 +647,12 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         if (!r1.empty()) {
           G1r[t] = pb.alloc(AR_S, LS2);
           pb.gemm(G1r[t], LS, LS, LS, LS, LS, LS, SF_TB | SF_CB, r1);
+          sym_at(G1r[t]);
         }
         if (!c1.empty()) {
           G1c[t] = pb.alloc(AR_S, LS2);
           pb.gemm(G1c[t], LS, LS, LS, LS, LS, LS, SF_TA, c1);
+          sym_at(G1c[t]);
         }
       }
       pb.end("leaf_dense_gram", l);
@@ -776,6 +788,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
                                 CC(c, 2 * lt.tg[tq.first].k + b)});
               pb.gemm(G1r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr, hr, hr, hc, hc, hc, gr, SF_TB | SF_CB, it,
                       CR(c, 2 * t + a), CR(c, 2 * t + a2));
+              if (a == a2) sym_at(G1r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr);
             }
         }
         if (!tcol[t].empty()) {
@@ -791,6 +804,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
                                 CR(c, 2 * lt.tg[tq.first].i + a)});
               pb.gemm(G1c[t] + (int64_t)b * hc * gc + (int64_t)b2 * hc, hc, hc, hr, hc, hc, gc, SF_TA | SF_CB, it,
                       CC(c, 2 * t + b), CC(c, 2 * t + b2));
+              if (b == b2) sym_at(G1c[t] + (int64_t)b * hc * gc + (int64_t)b2 * hc);
             }
         }
       }
@@ -816,6 +830,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
                 it.push_back(Item(y.a + (int64_t)a * hr * rB(l), y.b + (int64_t)a2 * hr * rB(l), y.kref));
               pb.gemm(G2r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr, hr, hr, rB(l), rB(l), rB(l), gr,
                       SF_TB | SF_CB, it, CR(c, 2 * t + a), CR(c, 2 * t + a2));
+              if (a == a2) sym_at(G2r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr);
             }
         }
         if (!c2.empty()) {
@@ -828,6 +843,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
               for (const Item& y : c2) it.push_back(Item(y.a + (int64_t)b * hc, y.b + (int64_t)b2 * hc, y.kref));
               pb.gemm(G2c[t] + (int64_t)b * hc * gc + (int64_t)b2 * hc, hc, hc, cA(l), gc, gc, gc, SF_TA | SF_CB, it,
                       CC(c, 2 * t + b), CC(c, 2 * t + b2));
+              if (b == b2) sym_at(G2c[t] + (int64_t)b * hc * gc + (int64_t)b2 * hc);
             }
         }
         if (!cplx) {
@@ -840,9 +856,11 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
             pb.gemm1(G3r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr, hr, hr, rA(l), rA(l), rA(l), gr, SF_TB | SF_CB,
                      Wr[t] + (int64_t)a * hr * rA(l), Wr[t] + (int64_t)a2 * hr * rA(l), CR(c, 2 * t + a),
                      CR(c, 2 * t + a2), AR(l, t));
+            if (a == a2) sym_at(G3r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr);
             pb.gemm1(G3c[t] + (int64_t)a * hc * gc + (int64_t)a2 * hc, hc, hc, cB(l), cB(l), cB(l), gc, SF_TB | SF_CB,
                      Wc[t] + (int64_t)a * hc * cB(l), Wc[t] + (int64_t)a2 * hc * cB(l), CC(c, 2 * t + a),
                      CC(c, 2 * t + a2), BC(l, t));
+            if (a == a2) sym_at(G3c[t] + (int64_t)a * hc * gc + (int64_t)a2 * hc);
           }
       }
       pb.end("nl_gram", l);
