@@ -241,10 +241,11 @@ def batched_main(args):
         "metric": "H2-MMP throughput, 48 independent products (bytes of A+A+C at actual ranks / batch time)",
         "value": nbytes / (tot_ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic",
         "config": {"workload": "48 products A_i x A_i, N_i log-uniform in [4096, 131072] (total %d), points "
                                "uniform in boxes with sides (1, s2, s3), s log-uniform in [1, 8]; 1/(4 pi r), "
                                "leaf 32, eta 1, eps %g (%s rule)" % (sum(ns), eps, args.trunc),
+                   "precision": args.precision,
                    "parallelism": "6 chunks of 8; per chunk one CUDA graph, one concurrent branch per product"},
         "ms_one_call_per_product": tot_single, "speedup_vs_one_call_per_product": tot_single / tot_ms,
         "gpu_launches_per_step": nk // args.steps, "max_rel_err_vs_exact_h2_matvecs": max(errs),
