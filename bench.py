@@ -45,13 +45,14 @@ WORKLOADS = {
     "sample_ref": (2, 2, 2048, 1e-4, "N=8,192 panel centroids on a 2x2 array of unit cubes"),
 }
 # DRAM traffic of the float32 GEMM kernel (dram__bytes_read.sum + dram__bytes_write.sum)
-# from one ncu capture of three of its launches -- the leaf-level projections, R images
-# and couplings of the N=65,536 cube-array product, 4.610 GB over 1.2807e11 padded flops
-# (2 m n k at the padded dims of their segments) -- valid only for the kernel source it
-# was taken on (the hash of seg_gemm32_kernel's text).  A run's traffic per GEMM launch
-# is that ratio times its own padded flops per GEMM launch.
-TRAFFIC = {"kernel": "seg_gemm32_kernel", "src_sha256": "fcaf5b47a52cf177a2dd6d4fd6dc897efa6427657cc844ef960069a869ccec44",
-           "bytes": 4610484992.0, "padded_flops": 1.28074e11}
+# from one ncu capture of four of its launches -- the leaf level's dense targets, Gram
+# pieces and case-1 Gram matrices of the N=65,536 cube-array product (BF16 split
+# precision, the float32 kernel's share of it), 6.653 GB over 6.916e10 padded flops (2 m n
+# k at the padded dims of their segments) -- valid only for the kernel source it was
+# taken on (the hash of seg_gemm32_kernel's text).  A run's traffic per GEMM launch is
+# that ratio times its own padded flops per GEMM launch.
+TRAFFIC = {"kernel": "seg_gemm32_kernel", "src_sha256": "a6ae0b2f18ff361cf72fa4d4b5ee7b690290b40676dde85f96c615a0dbee48a5",
+           "bytes": 6652807680.0, "padded_flops": 6.9159639040e10}
 LEAF, ETA, EPS_H2 = 32, 1.0, 1e-4
 # the variable-rank complex case: Fibonacci-sphere points, radius 4 wavelengths, Helmholtz
 # kernel exp(-j k r) / (4 pi r) with k = 2 pi, leaf 64, eta 1, eps_trunc = eps_H2 = 1e-3,
@@ -303,7 +304,7 @@ def roofline(tr, precision):
     achieved = fl / (gemm_ms * 1e-3) / 1e12 if gemm_ms else 0.0
     dom = max(tot, key=lambda k: tot[k][0])
     traffic = None
-    if precision == "mixed" and tot.get("gemm", [0, 0, 0])[2]:
+    if precision in ("mixed", "bf16x3") and tot.get("gemm", [0, 0, 0])[2]:
         import hashlib
         src = open(os.path.join(ROOT, "paper_1908_05218_gb300", "csrc", "kernels.cu")).read()
         a = src.find("// ------------------------------------------------------------ segmented GEMM, float32")
@@ -332,7 +333,7 @@ def roofline(tr, precision):
               "note": "coupling sums: 2 m n k per item at the plan's padded dims / CUDA-event time"}
     return {"bound": bound, "kernel": KERNELS[precision], "dominant": dom, "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": traffic,
-            "traffic_note": ("DRAM bytes per GEMM launch: bytes per padded flop of three captured launches "
+            "traffic_note": ("DRAM bytes per GEMM launch: bytes per padded flop of four captured launches "
                              "(N=65,536) x this run's padded flops per GEMM launch"
                              if traffic else "no DRAM capture of this kernel source at this precision"),
             "peak_note": peak_note, "launches_per_step": tot.get("gemm", [0, 0, 0])[2], "ms_per_step": gemm_ms,
