@@ -322,6 +322,7 @@ void launch_gemm_mma(const Seg* d_segs, const Item* d_items, int64_t first, int6
 // coupling sums from operand tiles on the tensor cores (tc.cu): groups of up to two
 // targets with their steps (A tiles rp x kpad, B tile np x kpad), rp, np the launch's tile
 // rows, kpmax its largest k
+void init_coup_tc_attributes();  // once per process, before launches or captures (kernel attributes)
 void launch_coup_tc(const TcGroup* d_groups, const TcStep* d_steps, int64_t first, int64_t count,
                     const Arenas* d_ars, int rp, int np, int kpmax, unsigned int* err, int variant, void* stream);
 void launch_eig(const EigTask* d_eigs, int64_t first, int64_t count, const Arenas* d_ars, double eps, int trunc,

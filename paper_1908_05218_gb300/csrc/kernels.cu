@@ -1457,6 +1457,7 @@ void init_kernel_attributes() {
     cudaFuncSetAttribute(eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(2 * kEigSmemMax * (kEigSmemMax + 1) * sizeof(double)));
   });
+  init_coup_tc_attributes();
 }
 
 // auxiliary streams of the concurrent eigen tiers, one set per (device, calling stream);

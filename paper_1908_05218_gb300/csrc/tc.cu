@@ -477,27 +477,31 @@ __global__ void __launch_bounds__(kThreads, 6) coup_tc_kernel(const TcGroup* __r
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(lay.tmem_cols));
 }
 
+// registers per thread of the kernel (allocation granularity 8), read once
+int g_tc_regs = 0;
+
 }  // namespace
+
+void init_coup_tc_attributes() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(coup_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    cudaFuncAttributes fa{};
+    g_tc_regs = cudaFuncGetAttributes(&fa, coup_tc_kernel) == cudaSuccess ? std::max(8, (fa.numRegs + 7) & ~7) : 64;
+  });
+}
 
 void launch_coup_tc(const TcGroup* d_groups, const TcStep* d_steps, int64_t first, int64_t count,
                     const Arenas* d_ars, int rp, int np, int kpmax, unsigned int* err, int variant, void* stream) {
   if (count <= 0) return;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    cudaFuncSetAttribute(coup_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-  });
+  init_coup_tc_attributes();
   const TcLayout lay = tc_layout(rp, np, kpmax, variant % kTcVariants);
   if (rp > 64 || rp % 8 || np > 64 || np % 8 || np == 0 || kpmax % 16 || kpmax > 64 || lay.total > kMaxSmem)
     throw Error(H2_EINTERNAL, "tensor-core coupling launch outside its tile limits");
   // resident CTAs per SM: shared memory (227 KB, ~1 KB static and 1 KB reserved per CTA),
   // registers, threads, and tensor memory (512 columns: every resident CTA must get its
   // columns)
-  static int regs = 0;
-  if (!regs) {
-    cudaFuncAttributes fa{};
-    cuda_check(cudaFuncGetAttributes(&fa, coup_tc_kernel), "kernel attributes");
-    regs = std::max(1, (fa.numRegs + 7) & ~7);
-  }
+  const int regs = g_tc_regs;
   const int sm_cap = (227 * 1024) / (lay.total + 2048);
   const int reg_cap = 65536 / (kThreads * regs), thr_cap = 2048 / kThreads;
   const int per_sm = std::max(1, std::min(std::min(sm_cap, reg_cap), std::min(thr_cap, 512 / lay.tmem_cols)));

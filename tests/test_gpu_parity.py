@@ -312,14 +312,15 @@ def test_mixed_product_is_deterministic_with_odd_leaf_sizes(lib, n):
             np.testing.assert_array_equal(getattr(e, f), getattr(ex[0], f))
 
 
-@pytest.mark.parametrize("precision,trunc", [("mixed", "paper"), ("fp64", "paper"), ("mixed", "formatted")])
+@pytest.mark.parametrize("precision,trunc", [("mixed", "paper"), ("fp64", "paper"), ("mixed", "formatted"),
+                                             ("bf16x3", "paper")])
 def test_batched_graph_and_replay_equal_single(lib, precision, trunc):
     # instances of uneven size in one captured graph, one branch per product (the
     # repeated instance shares its plan with the first and gets its own slice of the
     # work space); the second call replays the graph.  Every result equals its single
-    # product bit for bit.
+    # product bit for bit (the tensor-core coupling pass included).
     import torch
-    prec = lib.MIXED_FP32 if precision == "mixed" else lib.FP64
+    prec = {"mixed": lib.MIXED_FP32, "fp64": lib.FP64, "bf16x3": lib.MIXED_BF16X3}[precision]
     specs = [(900, 11, "box"), (1700, 12, "box"), (900, 11, "box"), (1200, 13, "uniform")]
     hs = []
     for n, seed, kind in specs:
