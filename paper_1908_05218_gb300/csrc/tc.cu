@@ -12,7 +12,9 @@
 // Targets are summed in pairs (TcGroup): the targets (i, k) and (i', k) of two sibling row
 // clusters share the B operand of every term with a common middle cluster, so one step
 // multiplies the two stacked A tiles (slot 0 in rows 0 .. sr-1, slot 1 in rows sr ..
-// 2 sr - 1; sr = 32 or 64) by one B tile with an MMA of M = 2 sr rows.  A slot without a
+// 2 sr - 1) by one B tile with an MMA of M = 2 sr rows: sr = 32 when both targets' ranks
+// fit 32 rows (decided per pair from the ranks on the device), else 64, and such a step
+// takes two consecutive stages of the ring (which is sized for M = 64).  A slot without a
 // term in a step gets zero rows (copied from a zero block).  The MMA reads operands from
 // shared memory, and this stacking halves the operand traffic of a term.
 //
@@ -24,10 +26,10 @@
 //     (the rank of the middle cluster, rounded up to 16: the tiles hold zeros beyond it)
 //     and whether it starts or ends the group;
 //   * warp 5 (one thread) issues, per k-step of 16, the three products hi*hi, hi*lo and
-//     lo*hi (tcgen05.mma kind::f16 with BF16 A and B, M = 2 sr, N = np, float32 accumulation
-//     in tensor memory; the dropped lo*lo term is below 2^-16 of the product) into one of
-//     nacc accumulators, commits each stage to its "empty" mbarrier and the group's last
-//     product to the accumulator's "full" mbarrier;
+//     lo*hi (tcgen05.mma kind::f16 with BF16 A and B, M = 2 sr, N = np rounded up to 16
+//     for M = 128, float32 accumulation in tensor memory; the dropped lo*lo term is below
+//     2^-16 of the product) into one of nacc accumulators, commits each stage to its
+//     "empty" mbarrier and the group's last product to the accumulator's "full" mbarrier;
 //   * warps 0-3 read the finished accumulator (tcgen05.ld) and store or add each slot's
 //     rows to its target's coupling (warps 0, 1: slot 0; warps 2, 3: slot 1: with M = 64
 //     row r sits in lane 32 (r / 16) + r % 16, with M = 128 in lane r), then release the
