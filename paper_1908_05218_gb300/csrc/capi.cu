@@ -881,8 +881,8 @@ h2_status h2_plan_selfcheck(const double* points, int64_t n, int32_t leaf_size, 
           try {
             build_mmp_plan(m, m, C, prm, P);
             const int64_t csz = mat_elems(C);
-            int64_t sizes[kArenas] = {asz, asz, csz, P.region[AR_P], P.region[AR_G0], P.region[AR_G1], P.region[AR_S],
-                                      is_mixed(prec) ? C.off_S[0] : 0};
+            int64_t sizes[kArenas] = {asz + P.fext, asz + P.fext, csz, P.region[AR_P], P.region[AR_G0],
+                                      P.region[AR_G1], P.region[AR_S], is_mixed(prec) ? C.off_S[0] : 0};
             validate_plan(P, sizes);
           } catch (Error& e) {
             throw Error(e.code, "product plan (trunc " + std::to_string(trunc) + ", precision " +
@@ -1070,7 +1070,8 @@ Prepared prepare_product(h2_handle A, h2_handle B, double eps, const h2_opts& o,
       probe.Kr = Ccaps.Kr;
       probe.Kc = Ccaps.Kc;
       int64_t csize = mat_elems(probe);
-      int64_t sizes[kArenas] = {A->m.arena_elems, B->m.arena_elems, csize, ent->plan.region[AR_P],
+      int64_t sizes[kArenas] = {A->m.arena_elems + ent->plan.fext, B->m.arena_elems + ent->plan.fext, csize,
+                                ent->plan.region[AR_P],
                                 ent->plan.region[AR_G0], ent->plan.region[AR_G1], ent->plan.region[AR_S],
                                 is_mixed(o.precision) ? probe.off_S[0] : 0};
       validate_plan(ent->plan, sizes);
@@ -1117,14 +1118,32 @@ Prepared prepare_product(h2_handle A, h2_handle B, double eps, const h2_opts& o,
   const bool mixed = is_mixed(o.precision);
   if (mixed) {
     const int w = A->m.cplx ? 2 : 1;  // floats per element
+    const int64_t fext = ent->plan.fext;  // the dense blocks' operand tiles after the copy
     for (h2_matrix* h : {A, B}) {
       // the float copy of the whole arena: made on first use, made again when a product
-      // has rewritten the arena since (a product's output used as an input)
-      if (!h->m.arena32 || h->m.arena32_stale) {
-        if (!h->m.arena32) h->m.arena32 = (float*)dmalloc(h->m.arena_elems * w * sizeof(float));
+      // has rewritten the arena since (a product's output used as an input); with the
+      // operand tiles of its dense blocks after it where the program reads them
+      const int64_t need = h->m.arena_elems * w + fext;
+      if (h->m.arena32 && h->m.arena32_cap < need) {
+        cuda_check(cudaStreamSynchronize((cudaStream_t)o.stream), "synchronise");
+        cudaFree(h->m.arena32);
+        h->m.arena32 = nullptr;
+      }
+      if (!h->m.arena32) {
+        h->m.arena32 = (float*)dmalloc(need * sizeof(float));
+        h->m.arena32_cap = need;
+        h->m.arena32_stale = true;
+      }
+      if (h->m.arena32_stale) {
         launch_to_f32(h->m.arena, h->m.arena32, h->m.arena_elems * w, o.stream);
         cuda_check(cudaGetLastError(), "convert to float");
         h->m.arena32_stale = false;
+        h->m.ftiles = false;
+      }
+      if (fext && !h->m.ftiles) {
+        launch_f_tiles(h->m.arena, h->m.off_F, h->m.st->nF, h->m.st->LS, h->m.arena32 + h->m.arena_elems, o.stream);
+        cuda_check(cudaGetLastError(), "dense block tiles");
+        h->m.ftiles = true;
       }
     }
     ar.p[AR_A] = A->m.arena32;

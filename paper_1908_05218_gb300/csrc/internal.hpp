@@ -74,7 +74,9 @@ struct Mat {
   int32_t* d_kr = nullptr;  // device ranks, indexed by Structure::node
   int32_t* d_kc = nullptr;
   float* arena32 = nullptr;  // float copy of the arena (mixed precision), made on first use
+  int64_t arena32_cap = 0;     // floats allocated for arena32 (the copy, then the F tiles)
   bool arena32_stale = false;  // the arena was rewritten (by a product) since arena32 was made
+  bool ftiles = false;         // arena32 also holds the operand tiles of the dense blocks
   float* bases32 = nullptr;  // float copy of the bases written by a mixed product into this matrix
   std::vector<int32_t> h_kr, h_kc;  // host copies
   bool ranks_on_host = false;
@@ -226,6 +228,9 @@ struct Plan {
   int64_t scratch_elems = 0;    // float64 eigen work space for Gram matrices above 112 (taken
                                 // with the work regions, so that concurrent products never share it)
   int64_t flops = 0;     // counted 2mnk over GEMM segments (padded dims)
+  // elements after A's and B's float copies that the program reads: the operand tiles of
+  // their dense blocks (H2_MIXED_BF16X3, ftile_elems), 0 if none
+  int64_t fext = 0;
   std::vector<int> ckr, ckc;  // caps of the product
   // allocations and resets of the work regions in program order (launch = index of
   // the first launch group emitted after the event); validate_plan replays them to
@@ -248,6 +253,12 @@ struct MmpParams {
 };
 // float32 operands and work regions (every precision but H2_FP64)
 inline bool is_mixed(int precision) { return precision != H2_FP64; }
+// Operand tiles of the dense leaf blocks for the tensor-core dense products
+// (H2_MIXED_BF16X3): after a matrix's float copy (arena_elems floats), the tile of dense
+// block f as an A operand (rows x k) at arena_elems + f T, and as a B operand (transposed)
+// at arena_elems + (nF + f) T; T = pad8(LS) x pad16(LS) floats (BF16 hi and lo parts)
+inline int64_t ftile_elems(int LS) { return (int64_t)((LS + 7) & ~7) * ((LS + 15) & ~15); }
+void launch_f_tiles(const double* arena, int64_t off_F, int64_t nF, int LS, float* dst, void* stream);
 // the eigen launches of the mixed product that take the kept-columns kernel (launch_eig_mixed)
 inline bool eig_kept_path(const MmpParams& p, const Launch& L) {
   return is_mixed(p.precision) && L.aux <= 96 && p.norm == H2_NORM_FROBENIUS;

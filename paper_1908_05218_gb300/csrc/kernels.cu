@@ -588,6 +588,34 @@ void launch_sum(const Seg* d_segs, const Item* d_items, int64_t first, int64_t c
   }
 }
 
+// The operand tiles of a matrix's dense leaf blocks (LS x LS, float64 in the arena) for the
+// tensor-core dense products: block f as an A operand (tile position (r, c) = F[r][c]) at
+// dst + f T and as a B operand (position (r, c) = F[c][r]) at dst + (nF + f) T, BF16 hi / lo
+// parts of the float32 value; every position of the tiles is written (zeros past LS).
+__global__ void f_tiles_kernel(const double* __restrict__ arena, int64_t off_F, int64_t nF, int LS, int tr, int kp,
+                               char* __restrict__ dst) {
+  const int64_t f = blockIdx.x;
+  const double* F = arena + off_F + f * (int64_t)LS * LS;
+  const int64_t T = (int64_t)tr * kp;  // floats per tile
+  char* ta = dst + (size_t)(f * T) * 4;
+  char* tb = dst + (size_t)((nF + f) * T) * 4;
+  for (int e = threadIdx.x; e < tr * kp; e += blockDim.x) {
+    const int r = e / kp, c = e - r * kp;
+    const float xa = (r < LS && c < LS) ? (float)F[(int64_t)r * LS + c] : 0.f;
+    const float xb = (r < LS && c < LS) ? (float)F[(int64_t)c * LS + r] : 0.f;
+    tile_store(ta, tr, kp, r, c, xa);
+    tile_store(tb, tr, kp, r, c, xb);
+  }
+}
+
+void launch_f_tiles(const double* arena, int64_t off_F, int64_t nF, int LS, float* dst, void* stream) {
+  if (nF <= 0) return;
+  if (nF > 2147483647LL) throw Error(H2_EUNSUPPORTED, "more dense blocks than one launch covers");
+  const int tr = (LS + 7) & ~7, kp = (LS + 15) & ~15;
+  f_tiles_kernel<<<(unsigned)nF, 256, 0, (cudaStream_t)stream>>>(arena, off_F, nF, LS, tr, kp, (char*)dst);
+  g_launches += 1;
+}
+
 __global__ void set_arenas_kernel(Arenas* dst, Arenas a) { *dst = a; }
 
 void upload_arenas(Arenas* dst, const Arenas& a, void* stream) {

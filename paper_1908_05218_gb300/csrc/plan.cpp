@@ -580,12 +580,14 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         sym_at(G3c[t]);
       }
       pb.end("leaf_blockprod", l);
-      // L2: dense targets (Sec. III-A) and Gram pieces
+      // L2: dense targets (Sec. III-A) and Gram pieces (the dense products F F of the
+      // dense targets on the tensor cores instead, tcF below)
+      const bool tcF = tcmode && ((LS + 7) & ~7) <= 64;
       pb.begin();
       for (size_t q = 0; q < lt.tg.size(); ++q) {
         const Target& T = lt.tg[q];
         if (T.cls != TC_F) continue;
-        pb.gemm(tC(C.F(bl[T.cpos].idx)), LS, LS, LS, LS, LS, LS, SF_ACC, gF.ptr(q), gF.size(q));
+        if (!tcF) pb.gemm(tC(C.F(bl[T.cpos].idx)), LS, LS, LS, LS, LS, LS, SF_ACC, gF.ptr(q), gF.size(q));
         pb.gemm(Z[q], LS, cB(l), rB(l), rB(l), cB(l), cB(l), 0, gZ.ptr(q), gZ.size(q), -1, BC(l, T.k));
         pb.gemm(Zp[q], rA(l), LS, cA(l), cA(l), LS, LS, 0, gZp.ptr(q), gZp.size(q), AR(l, T.i));
         pb.gemm(Zpp[q], rA(l), cB(l), rB(l), rB(l), cB(l), cB(l), 0, gZpp.ptr(q), gZpp.size(q), AR(l, T.i),
@@ -615,6 +617,118 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         }
       }
       pb.end("leaf_dense_gram", l);
+      if (tcF) {
+        // ---- the dense products F^A_ij F^B_jk of the dense targets (i, k) on the tensor
+        // cores (tc.cu): the operand tiles of A's and B's dense blocks follow their float
+        // copies; targets in sibling pairs (i, i') sharing the B tile of each common j,
+        // the terms of a pair merged by B tile.  Each target's F^C block is stored here
+        // (its first contribution); the later passes add to it.
+        const int TP = (LS + 7) & ~7, KPF = (LS + 15) & ~15;
+        const int64_t Tn = ftile_elems(LS), nF = st.nF;
+        P.fext = 2 * nF * Tn;
+        auto fterms = [&](int64_t q, std::vector<Item>& out) {
+          out.clear();
+          if (q < 0) return;
+          for (size_t x = 0; x < gF.size(q); ++x) {
+            const Item& it = gF.ptr(q)[x];
+            const int64_t fa = (offset_of(it.a) - A.off_F) / LS2, fb = (offset_of(it.b) - B.off_F) / LS2;
+            out.push_back(Item(tA(A.arena_elems + fa * Tn), tB(B.arena_elems + (nF + fb) * Tn), -1, 0, 0, KPF));
+          }
+          std::sort(out.begin(), out.end(), [](const Item& x, const Item& y) { return x.b < y.b; });
+        };
+        auto fhas = [&](int64_t q) { return lt.tg[q].cls == TC_F && gF.size(q) > 0; };
+        std::vector<std::array<int32_t, 2>> grp;
+        for (int64_t q = 0; q < (int64_t)lt.tg.size(); ++q) {
+          if (!fhas(q)) continue;
+          const Target& T = lt.tg[q];
+          const int32_t sib = lt.find(T.i ^ 1, T.k);
+          const bool paired = sib >= 0 && fhas(sib);
+          if (!(T.i & 1)) grp.push_back({(int32_t)q, paired ? sib : -1});
+          else if (!paired) grp.push_back({-1, (int32_t)q});
+        }
+        const int64_t ng = (int64_t)grp.size();
+        auto merge = [&](const std::vector<Item>& t0, const std::vector<Item>& t1, TcStep* out) {
+          size_t i0 = 0, i1 = 0;
+          int64_t n = 0;
+          while (i0 < t0.size() || i1 < t1.size()) {
+            const bool take0 = i0 < t0.size() && (i1 >= t1.size() || t0[i0].b <= t1[i1].b);
+            const bool take1 = i1 < t1.size() && (i0 >= t0.size() || t1[i1].b <= t0[i0].b);
+            const Item& x = take0 ? t0[i0] : t1[i1];
+            if (out) {
+              TcStep& sp = out[n];
+              sp.a[0] = take0 ? t0[i0].a : -1;
+              sp.a[1] = take1 ? t1[i1].a : -1;
+              sp.b = x.b;
+              sp.kref = -1;
+              sp.kpad = (int16_t)KPF;
+              sp.pad0 = 0;
+            }
+            ++n;
+            if (take0) ++i0;
+            if (take1) ++i1;
+          }
+          return n;
+        };
+        std::vector<int64_t> goff(ng + 1, 0);
+#pragma omp parallel
+        {
+          std::vector<Item> t0, t1;
+#pragma omp for schedule(dynamic, 1024)
+          for (int64_t gq = 0; gq < ng; ++gq) {
+            fterms(grp[gq][0], t0);
+            fterms(grp[gq][1], t1);
+            goff[gq + 1] = merge(t0, t1, nullptr);
+          }
+        }
+        for (int64_t gq = 0; gq < ng; ++gq) goff[gq + 1] += goff[gq];
+        const size_t st0 = P.tsteps.size(), gr0 = P.tgroups.size();
+        if ((int64_t)st0 + goff[ng] > INT32_MAX) throw Error(H2_ENOMEM, "plan too large");
+        P.tsteps.resize(st0 + (size_t)goff[ng]);
+        P.tgroups.resize(gr0 + (size_t)ng);
+        int64_t fl = 0;
+#pragma omp parallel reduction(+ : fl)
+        {
+          std::vector<Item> t0, t1;
+#pragma omp for schedule(dynamic, 1024)
+          for (int64_t gq = 0; gq < ng; ++gq) {
+            fterms(grp[gq][0], t0);
+            fterms(grp[gq][1], t1);
+            TcStep* stp = P.tsteps.data() + st0 + goff[gq];
+            const int64_t n = merge(t0, t1, stp);
+            TcGroup G{};
+            for (int sl = 0; sl < 2; ++sl) {
+              const int32_t q = grp[gq][sl];
+              G.out[sl] = q >= 0 ? tC(C.F(bl[lt.tg[q].cpos].idx)) : -1;
+              G.mref[sl] = -1;
+            }
+            G.nref = -1;
+            G.first = (int32_t)(st0 + goff[gq]);
+            G.count = (int32_t)n;
+            G.m = (int16_t)LS;
+            G.n = (int16_t)LS;
+            G.ldc = (int16_t)LS;
+            P.tgroups[gr0 + gq] = G;
+            for (int64_t x = 0; x < n; ++x)
+              fl += 2LL * LS * LS * KPF * ((stp[x].a[0] >= 0) + (stp[x].a[1] >= 0));
+          }
+        }
+        P.flops += fl;
+        if (ng > 0) {
+          Launch Lc;
+          Lc.kind = Launch::GEMM;
+          Lc.tc = true;
+          Lc.first = (int64_t)gr0;
+          Lc.count = ng;
+          Lc.level = l;
+          Lc.phase = "leaf_dense";
+          Lc.aux = TP;   // B tile rows
+          Lc.aux2 = TP;  // A tile rows
+          Lc.aux3 = KPF;
+          Lc.flops = (double)fl;
+          P.launches.push_back(Lc);
+        }
+      }
+
       // L3: Z += V^A_i Z''; F W and W F (into the storage of F F^T, F^T F)
       pb.begin();
       for (size_t q = 0; q < lt.tg.size(); ++q) {

@@ -461,9 +461,9 @@ def test_tensor_core_product_is_deterministic_and_tracks_float32(lib, n, prec):
 
 
 def test_bf16_split_couplings_run_on_the_tensor_cores(lib):
-    # H2_MIXED_BF16X3: the coupling pass of every level whose tiles fit runs on the
-    # tensor-core kernel (trace kind "tc"), the leaf level's included; the executed-flop
-    # counter covers it
+    # H2_MIXED_BF16X3: the coupling pass of every level whose tiles fit, and the dense
+    # leaf products F F, run on the tensor-core kernel (trace kind "tc"); the
+    # executed-flop counter covers the CUDA-core rest
     w, leaf, eta, A = oracle_case("cubes_2048_invr2")
     ga = lib.h2_import(w.points, leaf, eta, pack(A))
     ga.trace_enable(True)
@@ -472,7 +472,8 @@ def test_bf16_split_couplings_run_on_the_tensor_cores(lib):
     ga.trace_enable(False)
     tc_levels = {int(lv) for k, lv, nm in zip(kinds, levels, names) if k == "tc" and nm == "coup"}
     assert A.L in tc_levels and len(tc_levels) >= 3
-    assert all(nm == "coup" for k, nm in zip(kinds, names) if k == "tc")
+    assert [int(lv) for k, lv, nm in zip(kinds, levels, names) if k == "tc" and nm == "leaf_dense"] == [A.L]
+    assert all(nm in ("coup", "leaf_dense") for k, nm in zip(kinds, names) if k == "tc")
     assert c.trace_flops() > 0 and c.info()["cap_hits"] == 0
 
 
