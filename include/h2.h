@@ -76,12 +76,14 @@ typedef enum {
                            (tcgen05): each float32 operand split into two TF32 parts,
                            three TF32 products per pair, float32 accumulation */
   H2_MIXED_BF16X3 = 3   /* as H2_MIXED_FP32, with the main coupling pass of every level
-                           (Eq. leafcoup_simple / nonleafcoup_simple) on the tensor cores
-                           (tcgen05 kind::f16): each float32 operand split into two BF16
-                           parts, x = hi + lo, three BF16 products per pair (hi hi, hi lo,
-                           lo hi), float32 accumulation; about 2^-16 relative error per
-                           coupling product.  Levels whose tiles exceed 64 rows, columns or
-                           k take the float32 path.  Real matrices only. */
+                           (Eq. leafcoup_simple / nonleafcoup_simple) and the dense leaf
+                           products F F of the dense targets (Sec. III-A) on the tensor
+                           cores (tcgen05 kind::f16): each float32 operand split into two
+                           BF16 parts, x = hi + lo, three BF16 products per pair (hi hi,
+                           hi lo, lo hi), float32 accumulation; about 2^-16 relative error
+                           per product.  Levels whose tiles exceed 64 rows, columns or k
+                           take the float32 path.  Each operand keeps BF16 tiles of its
+                           dense blocks beside its float copy.  Real matrices only. */
 } h2_precision;
 
 /* Norm that scales each Gram matrix before the sum (Sec. III-C, "normalized"). */

@@ -1,9 +1,12 @@
-// Coupling sums on the fifth-generation tensor cores (tcgen05) for H2_MIXED_BF16X3: the
-// main coupling pass of every level (Eq. leafcoup_simple / nonleafcoup_simple: leaf case 1,
-// cases 2/4 and case 3, summed per target), S_ik (=|+=) sum over the terms of A_t B_t.
+// Sums of small products on the fifth-generation tensor cores (tcgen05) for
+// H2_MIXED_BF16X3: the main coupling pass of every level (Eq. leafcoup_simple /
+// nonleafcoup_simple: leaf case 1, cases 2/4 and case 3, summed per target), S_ik (=|+=)
+// sum over the terms of A_t B_t, and the dense leaf products of the dense targets (Sec.
+// III-A), F^C_ik = sum over j of F^A_ij F^B_jk (the tiles of the input matrices' dense
+// blocks follow their float copies).
 //
-// The operands were written by their producers (the projections and R images of the
-// level) as BF16 split tiles (device.cuh): an A operand (rows of the target, k) as an
+// The coupling operands were written by their producers (the projections and R images of
+// the level) as BF16 split tiles (device.cuh): an A operand (rows of the target, k) as an
 // rp x kp tile, a B operand transposed (columns of the target, k) as an np x kp tile, each
 // in the K-major core-matrix layout of tcgen05 without swizzle, high parts then low parts.
 // So a term's operands reach shared memory by bulk copies (cp.async.bulk, completing on
