@@ -288,7 +288,9 @@ h2_status h2_matvec(h2_handle h, const double* x, double* y, int64_t nrhs);
  * that loads the library holds the array until the process exits.  All calls share
  * it: calls that overlap on the GPU (different streams or threads) race and return
  * wrong results.  The first call on a device looks the array's address up
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress).  Every call copies the block lists from pageable host
+ * memory into the array (cudaMemcpyAsync), which stream capture does not support:
+ * do not capture the call into a CUDA graph.
  * Enqueued on the stream of the handle's last call. */
 h2_status h2_matvec_noalloc(h2_handle h, const double* x, double* y, int64_t nrhs);
 
