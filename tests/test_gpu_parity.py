@@ -137,6 +137,15 @@ def test_import_export_roundtrip_and_matvec(lib, name):
     e = g.export()
     for f in ("kr", "kc", "vr", "vc", "er", "ec", "s", "f"):
         np.testing.assert_array_equal(getattr(e, f), getattr(p, f))
+    # in place: arrays of the right size are written, not replaced; a wrong one is replaced
+    sz = g.export_sizes()
+    o = lib.Packed(np.full(sz[0], -7, np.int32), np.full(sz[0], -7, np.int32),
+                   *[np.full(sz[i], np.nan) for i in range(1, 6)], np.zeros(3))
+    keep = [o.kr, o.vr, o.s]
+    o2 = g.export(out=o)
+    assert o2 is o and o.kr is keep[0] and o.vr is keep[1] and o.s is keep[2]
+    for f in ("kr", "kc", "vr", "vc", "er", "ec", "s", "f"):
+        np.testing.assert_array_equal(getattr(o, f), getattr(p, f))
     x = inputs.standard_normal((w.points.shape[0], 3), seed=2)
     y = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
     assert_entries_close(y, oh2.matvec(A, x), 1e-13)
