@@ -5,7 +5,9 @@
 #include <memory>
 #include <stdexcept>
 #include <string>
+#include <type_traits>
 #include <unordered_map>
+#include <utility>
 #include <vector>
 
 #include "../../include/h2.h"
@@ -206,12 +208,37 @@ struct Launch {
   double flops = 0;              // GEMM: counted 2 m n k over the group
 };
 
+// Allocator of the program's large arrays: resize() leaves new elements of trivially
+// copyable types unconstructed instead of value-initialising them, so that growing an
+// array by hundreds of millions of entries costs no serial fill; the loops that follow
+// every such resize write each new element (in parallel, touching the pages first).
+template <class T>
+struct UninitAlloc : std::allocator<T> {
+  template <class U>
+  struct rebind {
+    using other = UninitAlloc<U>;
+  };
+  UninitAlloc() = default;
+  template <class U>
+  UninitAlloc(const UninitAlloc<U>&) noexcept {}
+  template <class U>
+  void construct(U* p) noexcept(std::is_nothrow_default_constructible<U>::value) {
+    if constexpr (!std::is_trivially_copyable<U>::value) ::new (static_cast<void*>(p)) U;
+  }
+  template <class U, class... Args>
+  void construct(U* p, Args&&... args) {
+    ::new (static_cast<void*>(p)) U(std::forward<Args>(args)...);
+  }
+};
+template <class T>
+using PlanArray = std::vector<T, UninitAlloc<T>>;
+
 struct Plan {
-  std::vector<Seg> segs;
-  std::vector<Item> items;
+  PlanArray<Seg> segs;
+  PlanArray<Item> items;
   std::vector<EigTask> eigs;
-  std::vector<TcGroup> tgroups;
-  std::vector<TcStep> tsteps;
+  PlanArray<TcGroup> tgroups;
+  PlanArray<TcStep> tsteps;
   std::vector<Launch> launches;
   int64_t region[kArenas] = {0, 0, 0, 0, 0, 0, 0, 0};  // sizes of P, G0, G1, S (others 0)
   // device copies

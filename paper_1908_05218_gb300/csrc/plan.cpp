@@ -72,7 +72,8 @@ struct PlanBuilder {
     if (n < 2) return;
     std::vector<int> cls(n);
     int cmin = INT32_MAX, cmax = INT32_MIN;
-    for (size_t i = 0; i < n; ++i) {
+#pragma omp parallel for schedule(static, 4096) reduction(min : cmin) reduction(max : cmax) if (n > 65536)
+    for (int64_t i = 0; i < (int64_t)n; ++i) {
       const Seg& sg = P.segs[g0 + i];
       double k = 0;
       for (int32_t q = sg.first; q < sg.first + sg.count; ++q) k += P.items[q].kpad ? P.items[q].kpad : sg.k;
@@ -86,7 +87,7 @@ struct PlanBuilder {
     std::vector<size_t> start((size_t)(cmax - cmin) + 2, 0);
     for (size_t i = 0; i < n; ++i) ++start[(size_t)(cls[i] - cmin) + 1];
     for (size_t c = 1; c < start.size(); ++c) start[c] += start[c - 1];
-    std::vector<Seg> sorted(n);
+    PlanArray<Seg> sorted(n);
     for (size_t i = 0; i < n; ++i) sorted[start[(size_t)(cls[i] - cmin)]++] = P.segs[g0 + i];
     std::copy(sorted.begin(), sorted.end(), P.segs.begin() + g0);
   }
@@ -185,7 +186,7 @@ struct Target {
 template <typename V>
 struct Lists {
   std::vector<int64_t> off, cur;
-  std::vector<V> val;
+  PlanArray<V> val;  // every entry written by put after finish_count
   explicit Lists(size_t nkeys = 0) : off(nkeys + 1, 0) {}
   void count(size_t key) { ++off[key + 1]; }
   void finish_count() {
@@ -323,6 +324,8 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
     }
     P.items.reserve(P.items.size() + (size_t)(trip + trip / 2 + 16 * nblk));
     P.segs.reserve(P.segs.size() + (size_t)(20 * nblk));
+    // the tensor-core passes' steps: at most one per coupling term and dense product
+    if (prm.precision == H2_MIXED_BF16X3 && !A.cplx) P.tsteps.reserve(P.tsteps.size() + (size_t)(trip + trip / 2));
   }
   // caps of C: leaf LS, non-leaf min(2 K[l+1], cap) (no cap in full mode), 0 above l_min;
   // each rounded up to a multiple of four for storage
