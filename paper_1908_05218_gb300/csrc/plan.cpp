@@ -20,10 +20,13 @@
 //           coupling at the leaf level is regrouped as sum_j (V^C_i^T F_ij)(F_jk V^C_k)
 //   merge   2 x 2 assembly of children couplings (Eq. nonleafA, first form)
 //   split   top-down split of couplings held by NL targets (Sec. IV-E)
+#include <omp.h>
+
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
-#include <array>
+#include <exception>
 #include <map>
 
 #include "internal.hpp"
@@ -33,6 +36,84 @@ namespace h2 {
 namespace {
 
 enum TClass : int8_t { TC_R = 0, TC_F = 1, TC_NL = 2, TC_SUB = 3 };
+
+// Segments and items emitted by one thread of a parallel loop (PlanBuilder::par); item
+// indices in its segments are local until the buffer is appended to the program.
+struct SegBuf {
+  PlanArray<Seg> segs;
+  PlanArray<Item> items;
+  int64_t flops = 0;
+};
+
+// Emission of one segment into a sink (the program itself, or a SegBuf): out[m x n]
+// (=|+=) sum over the items of op(A) op(B), or a plain sum of matrices.
+template <class S>
+void emit_gemm(S& d, int64_t out, int m, int n, int k, int lda, int ldb, int ldc, uint8_t fl, const Item* it,
+               size_t nit, int32_t mref, int32_t nref) {
+  if (m <= 0 || n <= 0 || nit == 0) return;
+  if (k <= 0) return;  // zero contribution; outputs start at zero
+  Seg s{};
+  s.out = out;
+  s.first = (int32_t)d.items.size();
+  s.count = (int32_t)nit;
+  s.m = (int16_t)m;
+  s.n = (int16_t)n;
+  s.k = (int16_t)k;
+  s.lda = (int16_t)lda;
+  s.ldb = (int16_t)ldb;
+  s.ldc = (int16_t)ldc;
+  s.mref = mref;
+  s.nref = nref;
+  s.flags = fl;
+  if ((int64_t)d.items.size() + (int64_t)nit > INT32_MAX) throw Error(H2_ENOMEM, "plan too large");
+  d.items.insert(d.items.end(), it, it + nit);
+  d.segs.push_back(s);
+  for (size_t q = 0; q < nit; ++q) d.flops += 2LL * m * n * (it[q].kpad ? it[q].kpad : k);
+}
+template <class S>
+void emit_sum(S& d, int64_t out, int m, int n, int lda, int ldc, bool acc, const int64_t* mats, size_t nm) {
+  if (m <= 0 || n <= 0 || nm == 0) return;
+  Seg s{};
+  s.out = out;
+  s.first = (int32_t)d.items.size();
+  s.count = (int32_t)nm;
+  s.m = (int16_t)m;
+  s.n = (int16_t)n;
+  s.k = 0;
+  s.lda = (int16_t)lda;
+  s.ldb = 0;
+  s.ldc = (int16_t)ldc;
+  s.mref = -1;
+  s.nref = -1;
+  s.flags = SF_SUM | (acc ? SF_ACC : 0);
+  for (size_t q = 0; q < nm; ++q) d.items.push_back(Item{mats[q], 0});
+  d.segs.push_back(s);
+}
+
+// The emission calls on a sink, with the argument conventions of PlanBuilder's
+template <class S>
+struct Emit {
+  S& d;
+  void gemm(int64_t out, int m, int n, int k, int lda, int ldb, int ldc, uint8_t fl, const std::vector<Item>& it,
+            int32_t mref = -1, int32_t nref = -1) {
+    emit_gemm(d, out, m, n, k, lda, ldb, ldc, fl, it.data(), it.size(), mref, nref);
+  }
+  void gemm(int64_t out, int m, int n, int k, int lda, int ldb, int ldc, uint8_t fl, const Item* it, size_t nit,
+            int32_t mref = -1, int32_t nref = -1) {
+    emit_gemm(d, out, m, n, k, lda, ldb, ldc, fl, it, nit, mref, nref);
+  }
+  void gemm1(int64_t out, int m, int n, int k, int lda, int ldb, int ldc, uint8_t fl, int64_t a, int64_t b,
+             int32_t mref = -1, int32_t nref = -1, int32_t kref = -1) {
+    const Item x{a, b, kref};
+    emit_gemm(d, out, m, n, k, lda, ldb, ldc, fl, &x, 1, mref, nref);
+  }
+  void sum(int64_t out, int m, int n, int lda, int ldc, bool acc, const std::vector<int64_t>& mats) {
+    emit_sum(d, out, m, n, lda, ldc, acc, mats.data(), mats.size());
+  }
+  void sum(int64_t out, int m, int n, int lda, int ldc, bool acc, const int64_t* mats, size_t nm) {
+    emit_sum(d, out, m, n, lda, ldc, acc, mats, nm);
+  }
+};
 
 struct PlanBuilder {
   Plan& P;
@@ -116,55 +197,79 @@ struct PlanBuilder {
   }
   void gemm(int64_t out, int m, int n, int k, int lda, int ldb, int ldc, uint8_t fl,
             const std::vector<Item>& it, int32_t mref = -1, int32_t nref = -1) {
-    gemm(out, m, n, k, lda, ldb, ldc, fl, it.data(), it.size(), mref, nref);
+    emit_gemm(P, out, m, n, k, lda, ldb, ldc, fl, it.data(), it.size(), mref, nref);
   }
   void gemm(int64_t out, int m, int n, int k, int lda, int ldb, int ldc, uint8_t fl, const Item* it, size_t nit,
             int32_t mref = -1, int32_t nref = -1) {
-    if (m <= 0 || n <= 0 || nit == 0) return;
-    if (k <= 0) return;  // zero contribution; outputs start at zero
-    Seg s{};
-    s.out = out;
-    s.first = (int32_t)P.items.size();
-    s.count = (int32_t)nit;
-    s.m = (int16_t)m;
-    s.n = (int16_t)n;
-    s.k = (int16_t)k;
-    s.lda = (int16_t)lda;
-    s.ldb = (int16_t)ldb;
-    s.ldc = (int16_t)ldc;
-    s.mref = mref;
-    s.nref = nref;
-    s.flags = fl;
-    if ((int64_t)P.items.size() + (int64_t)nit > INT32_MAX) throw Error(H2_ENOMEM, "plan too large");
-    P.items.insert(P.items.end(), it, it + nit);
-    P.segs.push_back(s);
-    for (size_t q = 0; q < nit; ++q) P.flops += 2LL * m * n * (it[q].kpad ? it[q].kpad : k);
+    emit_gemm(P, out, m, n, k, lda, ldb, ldc, fl, it, nit, mref, nref);
   }
   void gemm1(int64_t out, int m, int n, int k, int lda, int ldb, int ldc, uint8_t fl, int64_t a, int64_t b,
              int32_t mref = -1, int32_t nref = -1, int32_t kref = -1) {
     const Item x{a, b, kref};
-    gemm(out, m, n, k, lda, ldb, ldc, fl, &x, 1, mref, nref);
+    emit_gemm(P, out, m, n, k, lda, ldb, ldc, fl, &x, 1, mref, nref);
   }
   void sum(int64_t out, int m, int n, int lda, int ldc, bool acc, const std::vector<int64_t>& mats) {
-    sum(out, m, n, lda, ldc, acc, mats.data(), mats.size());
+    emit_sum(P, out, m, n, lda, ldc, acc, mats.data(), mats.size());
   }
   void sum(int64_t out, int m, int n, int lda, int ldc, bool acc, const int64_t* mats, size_t nm) {
-    if (m <= 0 || n <= 0 || nm == 0) return;
-    Seg s{};
-    s.out = out;
-    s.first = (int32_t)P.items.size();
-    s.count = (int32_t)nm;
-    s.m = (int16_t)m;
-    s.n = (int16_t)n;
-    s.k = 0;
-    s.lda = (int16_t)lda;
-    s.ldb = 0;
-    s.ldc = (int16_t)ldc;
-    s.mref = -1;
-    s.nref = -1;
-    s.flags = SF_SUM | (acc ? SF_ACC : 0);
-    for (size_t q = 0; q < nm; ++q) P.items.push_back(Item{mats[q], 0});
-    P.segs.push_back(s);
+    emit_sum(P, out, m, n, lda, ldc, acc, mats, nm);
+  }
+  // The loop `for x in [0, n): body(x, e)` with the segments emitted through e (an
+  // Emit<SegBuf>) in parallel: each thread takes a contiguous range of x into its own
+  // buffer, and the buffers are appended in thread order with their item indices
+  // rebased, so the program is the one the serial loop writes.  The body must not
+  // allocate (alloc / reset) or touch the program directly.
+  template <class F>
+  void par(int64_t n, F&& body) {
+    if (n <= 0) return;
+    std::vector<SegBuf> buf;
+    std::vector<std::exception_ptr> err;
+    int used = 1;
+    if (n < 4096) {
+      buf.resize(1);
+      Emit<SegBuf> e{buf[0]};
+      for (int64_t x = 0; x < n; ++x) body(x, e);
+    } else {
+#pragma omp parallel
+      {
+#pragma omp single
+        {
+          used = omp_get_num_threads();
+          buf.resize((size_t)used);
+          err.resize((size_t)used);
+        }
+        const int id = omp_get_thread_num();
+        const int64_t lo = n * id / used, hi = n * (id + 1) / used;
+        try {
+          Emit<SegBuf> e{buf[(size_t)id]};
+          for (int64_t x = lo; x < hi; ++x) body(x, e);
+        } catch (...) {
+          err[(size_t)id] = std::current_exception();
+        }
+      }
+      for (auto& e : err)
+        if (e) std::rethrow_exception(e);
+    }
+    std::vector<size_t> so((size_t)used + 1, 0), io((size_t)used + 1, 0);
+    for (int t = 0; t < used; ++t) {
+      so[t + 1] = so[t] + buf[t].segs.size();
+      io[t + 1] = io[t] + buf[t].items.size();
+      P.flops += buf[t].flops;
+    }
+    const size_t s0 = P.segs.size(), i0 = P.items.size();
+    if ((int64_t)(i0 + io[used]) > INT32_MAX) throw Error(H2_ENOMEM, "plan too large");
+    P.segs.resize(s0 + so[used]);
+    P.items.resize(i0 + io[used]);
+#pragma omp parallel for schedule(static, 1) if (used > 1)
+    for (int t = 0; t < used; ++t) {
+      const int32_t base = (int32_t)(i0 + io[t]);
+      Seg* ds = P.segs.data() + s0 + so[t];
+      for (size_t q = 0; q < buf[t].segs.size(); ++q) {
+        ds[q] = buf[t].segs[q];
+        ds[q].first += base;
+      }
+      std::copy(buf[t].items.begin(), buf[t].items.end(), P.items.begin() + (i0 + io[t]));
+    }
   }
 };
 
@@ -359,9 +464,10 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
              A.Kc[l] > 0 && pad16(B.Kr[l]) <= 64 && pad16(A.Kc[l]) <= 64 && (l < L || pad16(LS) <= 64);
   // the segment just emitted, if any, writes an operand tile of tr rows and kp columns
   // (transposed: matrix element (r, c) at tile position (c, r))
-  auto tile_out = [&](size_t nseg, int tr, int kp, bool transposed) {
-    if (P.segs.size() == nseg) return;
-    Seg& sg = P.segs.back();
+  // (d: the sink the segment went to, the program or a thread's buffer)
+  auto tile_out = [](auto& d, size_t nseg, int tr, int kp, bool transposed) {
+    if (d.segs.size() == nseg) return;
+    Seg& sg = d.segs.back();
     sg.flags |= SF_TILE | (transposed ? SF_TILE_T : 0);
     sg.ldc = (int16_t)kp;
     sg.trows = tr;
@@ -369,13 +475,13 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
   // the segment just emitted for output `out`, if any, is a diagonal block of a symmetric
   // Gram matrix: the float32 kernel computes its lower half (SF2_SYM)
   const bool symok = !cplx && (prm.precision == H2_MIXED_FP32 || prm.precision == H2_MIXED_BF16X3);
-  auto sym_at = [&](int64_t out) {
-    if (symok && !P.segs.empty() && P.segs.back().out == out) P.segs.back().flags2 |= SF2_SYM;
+  auto sym_at = [symok](auto& d, int64_t out) {
+    if (symok && !d.segs.empty() && d.segs.back().out == out) d.segs.back().flags2 |= SF2_SYM;
   };
   // the sum segment just emitted, if any, reads operand tiles
-  auto tile_in = [&](size_t nseg, int tr, int kp, bool transposed) {
-    if (P.segs.size() == nseg) return;
-    Seg& sg = P.segs.back();
+  auto tile_in = [](auto& d, size_t nseg, int tr, int kp, bool transposed) {
+    if (d.segs.size() == nseg) return;
+    Seg& sg = d.segs.back();
     sg.flags |= SF_TILE | (transposed ? SF_TILE_T : 0);
     sg.lda = (int16_t)kp;
     sg.trows = tr;
@@ -478,14 +584,14 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       }
     }
     pb.begin();
-    for (int64_t p = 0; p < nb; ++p) {
+    pb.par(nb, [&](int64_t p, auto& e) {
       const Block& b = bl[p];
-      if (b.kind != KR) continue;
-      pb.gemm1(T1[p], rA(l), rB(l), cA(l), cA(l), rB(l), rB(l), 0, tA(A.S(l, b.idx)), Bj[l][b.s], AR(l, b.t),
-               BR(l, b.s), AC(l, b.s));
-      pb.gemm1(T2[p], cA(l), cB(l), rB(l), rB(l), cB(l), cB(l), 0, Bj[l][b.t], tB(B.S(l, b.idx)), AC(l, b.t),
-               BC(l, b.s), BR(l, b.t));
-    }
+      if (b.kind != KR) return;
+      e.gemm1(T1[p], rA(l), rB(l), cA(l), cA(l), rB(l), rB(l), 0, tA(A.S(l, b.idx)), Bj[l][b.s], AR(l, b.t),
+              BR(l, b.s), AC(l, b.s));
+      e.gemm1(T2[p], cA(l), cB(l), rB(l), rB(l), cB(l), cB(l), 0, Bj[l][b.t], tB(B.S(l, b.idx)), AC(l, b.t),
+              BC(l, b.s), BR(l, b.t));
+    });
     pb.end("rprod", l);
 
     // Gram matrices of the new bases (row: gr x gr, column: gc x gc)
@@ -567,57 +673,67 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       }
       // L1: per-block products
       pb.begin();
-      for (int64_t p = 0; p < nb; ++p) {
+      pb.par(nb, [&](int64_t p, auto& e) {
         const Block& b = bl[p];
-        if (b.kind != KF) continue;
-        pb.gemm1(Y[p], LS, rB(l), LS, LS, rB(l), rB(l), 0, tA(A.F(b.idx)), tB(B.Vr(b.s)), -1, BR(l, b.s));
-        pb.gemm1(Yb[p], cA(l), LS, LS, cA(l), LS, LS, SF_TA, tA(A.Vc(b.t)), tB(B.F(b.idx)), AC(l, b.t));
-        if (formatted) continue;
-        pb.gemm1(Q[p], LS, LS, LS, LS, LS, LS, SF_TB | SF_CB, tB(B.F(b.idx)), tB(B.F(b.idx)));
-        pb.gemm1(Rr[p], LS, LS, LS, LS, LS, LS, SF_TA | SF_CB, tA(A.F(b.idx)), tA(A.F(b.idx)));
-      }
-      for (int64_t t = 0; t < nc && !formatted; ++t) {
-        pb.gemm1(G3r[t], LS, LS, rA(l), rA(l), rA(l), LS, SF_TB | SF_CB, tA(A.Vr(t)), tA(A.Vr(t)), -1, -1, AR(l, t));
-        sym_at(G3r[t]);
-        pb.gemm1(G3c[t], LS, LS, cB(l), cB(l), cB(l), LS, SF_TB | SF_CB, tB(B.Vc(t)), tB(B.Vc(t)), -1, -1, BC(l, t));
-        sym_at(G3c[t]);
-      }
+        if (b.kind != KF) return;
+        e.gemm1(Y[p], LS, rB(l), LS, LS, rB(l), rB(l), 0, tA(A.F(b.idx)), tB(B.Vr(b.s)), -1, BR(l, b.s));
+        e.gemm1(Yb[p], cA(l), LS, LS, cA(l), LS, LS, SF_TA, tA(A.Vc(b.t)), tB(B.F(b.idx)), AC(l, b.t));
+        if (formatted) return;
+        e.gemm1(Q[p], LS, LS, LS, LS, LS, LS, SF_TB | SF_CB, tB(B.F(b.idx)), tB(B.F(b.idx)));
+        e.gemm1(Rr[p], LS, LS, LS, LS, LS, LS, SF_TA | SF_CB, tA(A.F(b.idx)), tA(A.F(b.idx)));
+      });
+      if (!formatted)
+        pb.par(nc, [&](int64_t t, auto& e) {
+          e.gemm1(G3r[t], LS, LS, rA(l), rA(l), rA(l), LS, SF_TB | SF_CB, tA(A.Vr(t)), tA(A.Vr(t)), -1, -1, AR(l, t));
+          sym_at(e.d, G3r[t]);
+          e.gemm1(G3c[t], LS, LS, cB(l), cB(l), cB(l), LS, SF_TB | SF_CB, tB(B.Vc(t)), tB(B.Vc(t)), -1, -1, BC(l, t));
+          sym_at(e.d, G3c[t]);
+        });
       pb.end("leaf_blockprod", l);
       // L2: dense targets (Sec. III-A) and Gram pieces (the dense products F F of the
       // dense targets on the tensor cores instead, tcF below)
       const bool tcF = tcmode && ((LS + 7) & ~7) <= 64;
       pb.begin();
-      for (size_t q = 0; q < lt.tg.size(); ++q) {
+      pb.par((int64_t)lt.tg.size(), [&](int64_t q, auto& e) {
         const Target& T = lt.tg[q];
-        if (T.cls != TC_F) continue;
-        if (!tcF) pb.gemm(tC(C.F(bl[T.cpos].idx)), LS, LS, LS, LS, LS, LS, SF_ACC, gF.ptr(q), gF.size(q));
-        pb.gemm(Z[q], LS, cB(l), rB(l), rB(l), cB(l), cB(l), 0, gZ.ptr(q), gZ.size(q), -1, BC(l, T.k));
-        pb.gemm(Zp[q], rA(l), LS, cA(l), cA(l), LS, LS, 0, gZp.ptr(q), gZp.size(q), AR(l, T.i));
-        pb.gemm(Zpp[q], rA(l), cB(l), rB(l), rB(l), cB(l), cB(l), 0, gZpp.ptr(q), gZpp.size(q), AR(l, T.i),
-                BC(l, T.k));
-      }
-      for (int64_t p = 0; p < nb && !formatted; ++p) {
-        pb.sum(Wsum[p], LS, LS, LS, LS, false, Ksets.ptr(p), Ksets.size(p));
-        pb.sum(Wsc[p], LS, LS, LS, LS, false, Isets.ptr(p), Isets.size(p));
-      }
-      for (int64_t t = 0; t < nc && !formatted; ++t) {
-        std::vector<Item> r2, c2;
-        for (int32_t p = st.row_ptr[l][t]; p < st.row_ptr[l][t + 1]; ++p)
-          if (bl[p].kind == KF) r2.push_back({Y[p], Y[p], BR(l, bl[p].s)});
-        for (int32_t q = st.col_ptr[l][t]; q < st.col_ptr[l][t + 1]; ++q) {
-          int32_t p = st.col_list[l][q];
-          if (bl[p].kind == KF) c2.push_back({Yb[p], Yb[p], AC(l, bl[p].t)});
+        if (T.cls != TC_F) return;
+        if (!tcF) e.gemm(tC(C.F(bl[T.cpos].idx)), LS, LS, LS, LS, LS, LS, SF_ACC, gF.ptr(q), gF.size(q));
+        e.gemm(Z[q], LS, cB(l), rB(l), rB(l), cB(l), cB(l), 0, gZ.ptr(q), gZ.size(q), -1, BC(l, T.k));
+        e.gemm(Zp[q], rA(l), LS, cA(l), cA(l), LS, LS, 0, gZp.ptr(q), gZp.size(q), AR(l, T.i));
+        e.gemm(Zpp[q], rA(l), cB(l), rB(l), rB(l), cB(l), cB(l), 0, gZpp.ptr(q), gZpp.size(q), AR(l, T.i),
+               BC(l, T.k));
+      });
+      if (!formatted) {
+        pb.par(nb, [&](int64_t p, auto& e) {
+          e.sum(Wsum[p], LS, LS, LS, LS, false, Ksets.ptr(p), Ksets.size(p));
+          e.sum(Wsc[p], LS, LS, LS, LS, false, Isets.ptr(p), Isets.size(p));
+        });
+        // Eq. Gr2L / case2-ch over the dense blocks of row t / column t: the Gram
+        // matrices allocated first (in cluster order), then the products emitted
+        for (int64_t t = 0; t < nc; ++t) {
+          bool rf = false, cf = false;
+          for (int32_t p = st.row_ptr[l][t]; p < st.row_ptr[l][t + 1] && !rf; ++p) rf = bl[p].kind == KF;
+          for (int32_t q = st.col_ptr[l][t]; q < st.col_ptr[l][t + 1] && !cf; ++q) cf = bl[st.col_list[l][q]].kind == KF;
+          if (rf) G2r[t] = pb.alloc(AR_S, LS2);
+          if (cf) G2c[t] = pb.alloc(AR_S, LS2);
         }
-        if (!r2.empty()) {
-          G2r[t] = pb.alloc(AR_S, LS2);
-          pb.gemm(G2r[t], LS, LS, rB(l), rB(l), rB(l), LS, SF_TB | SF_CB, r2);  // Eq. Gr2L
-          sym_at(G2r[t]);
-        }
-        if (!c2.empty()) {
-          G2c[t] = pb.alloc(AR_S, LS2);
-          pb.gemm(G2c[t], LS, LS, cA(l), LS, LS, LS, SF_TA | SF_CB, c2);  // Eq. case2-ch
-          sym_at(G2c[t]);
-        }
+        pb.par(nc, [&](int64_t t, auto& e) {
+          std::vector<Item> r2, c2;
+          for (int32_t p = st.row_ptr[l][t]; p < st.row_ptr[l][t + 1]; ++p)
+            if (bl[p].kind == KF) r2.push_back({Y[p], Y[p], BR(l, bl[p].s)});
+          for (int32_t q = st.col_ptr[l][t]; q < st.col_ptr[l][t + 1]; ++q) {
+            int32_t p = st.col_list[l][q];
+            if (bl[p].kind == KF) c2.push_back({Yb[p], Yb[p], AC(l, bl[p].t)});
+          }
+          if (!r2.empty()) {
+            e.gemm(G2r[t], LS, LS, rB(l), rB(l), rB(l), LS, SF_TB | SF_CB, r2);  // Eq. Gr2L
+            sym_at(e.d, G2r[t]);
+          }
+          if (!c2.empty()) {
+            e.gemm(G2c[t], LS, LS, cA(l), LS, LS, LS, SF_TA | SF_CB, c2);  // Eq. case2-ch
+            sym_at(e.d, G2c[t]);
+          }
+        });
       }
       pb.end("leaf_dense_gram", l);
       if (tcF) {
@@ -764,12 +880,12 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
         if (!r1.empty()) {
           G1r[t] = pb.alloc(AR_S, LS2);
           pb.gemm(G1r[t], LS, LS, LS, LS, LS, LS, SF_TB | SF_CB, r1);
-          sym_at(G1r[t]);
+          sym_at(P, G1r[t]);
         }
         if (!c1.empty()) {
           G1c[t] = pb.alloc(AR_S, LS2);
           pb.gemm(G1c[t], LS, LS, LS, LS, LS, LS, SF_TA, c1);
-          sym_at(G1c[t]);
+          sym_at(P, G1c[t]);
         }
       }
       pb.end("leaf_dense_gram", l);
@@ -812,10 +928,10 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
             size_t ns = P.segs.size();
             pb.sum(Ac[p] + (int64_t)a * hr * 2 * rB(c) + (int64_t)bb * rB(c), hr, rB(c), rB(c), 2 * rB(c), false,
                    &Ahat[c][cp], 1);
-            if (tcl[c]) tile_in(ns, pad8(rC(c)), pad16(rB(c)), false);  // the children's tiles
+            if (tcl[c]) tile_in(P, ns, pad8(rC(c)), pad16(rB(c)), false);  // the children's tiles
             ns = P.segs.size();
             pb.sum(Bc[p] + (int64_t)a * cA(c) * gc + (int64_t)bb * hc, cA(c), hc, hc, gc, false, &Bhat[c][cp], 1);
-            if (tcl[c]) tile_in(ns, pad8(cC(c)), pad16(cA(c)), true);
+            if (tcl[c]) tile_in(P, ns, pad8(cC(c)), pad16(cA(c)), true);
           }
       }
       pb.end("collect", l);
@@ -905,7 +1021,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
                                 CC(c, 2 * lt.tg[tq.first].k + b)});
               pb.gemm(G1r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr, hr, hr, hc, hc, hc, gr, SF_TB | SF_CB, it,
                       CR(c, 2 * t + a), CR(c, 2 * t + a2));
-              if (a == a2) sym_at(G1r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr);
+              if (a == a2) sym_at(P, G1r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr);
             }
         }
         if (!tcol[t].empty()) {
@@ -921,7 +1037,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
                                 CR(c, 2 * lt.tg[tq.first].i + a)});
               pb.gemm(G1c[t] + (int64_t)b * hc * gc + (int64_t)b2 * hc, hc, hc, hr, hc, hc, gc, SF_TA | SF_CB, it,
                       CC(c, 2 * t + b), CC(c, 2 * t + b2));
-              if (b == b2) sym_at(G1c[t] + (int64_t)b * hc * gc + (int64_t)b2 * hc);
+              if (b == b2) sym_at(P, G1c[t] + (int64_t)b * hc * gc + (int64_t)b2 * hc);
             }
         }
       }
@@ -947,7 +1063,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
                 it.push_back(Item(y.a + (int64_t)a * hr * rB(l), y.b + (int64_t)a2 * hr * rB(l), y.kref));
               pb.gemm(G2r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr, hr, hr, rB(l), rB(l), rB(l), gr,
                       SF_TB | SF_CB, it, CR(c, 2 * t + a), CR(c, 2 * t + a2));
-              if (a == a2) sym_at(G2r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr);
+              if (a == a2) sym_at(P, G2r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr);
             }
         }
         if (!c2.empty()) {
@@ -960,7 +1076,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
               for (const Item& y : c2) it.push_back(Item(y.a + (int64_t)b * hc, y.b + (int64_t)b2 * hc, y.kref));
               pb.gemm(G2c[t] + (int64_t)b * hc * gc + (int64_t)b2 * hc, hc, hc, cA(l), gc, gc, gc, SF_TA | SF_CB, it,
                       CC(c, 2 * t + b), CC(c, 2 * t + b2));
-              if (b == b2) sym_at(G2c[t] + (int64_t)b * hc * gc + (int64_t)b2 * hc);
+              if (b == b2) sym_at(P, G2c[t] + (int64_t)b * hc * gc + (int64_t)b2 * hc);
             }
         }
         if (!cplx) {
@@ -973,11 +1089,11 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
             pb.gemm1(G3r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr, hr, hr, rA(l), rA(l), rA(l), gr, SF_TB | SF_CB,
                      Wr[t] + (int64_t)a * hr * rA(l), Wr[t] + (int64_t)a2 * hr * rA(l), CR(c, 2 * t + a),
                      CR(c, 2 * t + a2), AR(l, t));
-            if (a == a2) sym_at(G3r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr);
+            if (a == a2) sym_at(P, G3r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr);
             pb.gemm1(G3c[t] + (int64_t)a * hc * gc + (int64_t)a2 * hc, hc, hc, cB(l), cB(l), cB(l), gc, SF_TB | SF_CB,
                      Wc[t] + (int64_t)a * hc * cB(l), Wc[t] + (int64_t)a2 * hc * cB(l), CC(c, 2 * t + a),
                      CC(c, 2 * t + a2), BC(l, t));
-            if (a == a2) sym_at(G3c[t] + (int64_t)a * hc * gc + (int64_t)a2 * hc);
+            if (a == a2) sym_at(P, G3c[t] + (int64_t)a * hc * gc + (int64_t)a2 * hc);
           }
       }
       pb.end("nl_gram", l);
@@ -1042,11 +1158,11 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       PB[l][t] = pb.alloc(g, (int64_t)cB(l) * cC(l));
     }
     pb.begin();
-    for (int64_t t = 0; t < nc; ++t) {
+    pb.par(nc, [&](int64_t t, auto& e) {
       if (leaf) {
-        pb.gemm1(PA[l][t], rC(l), rA(l), LS, rC(l), rA(l), rA(l), SF_TA | SF_CA, tCb(C.Vr(t)), tA(A.Vr(t)), CR(l, t),
+        e.gemm1(PA[l][t], rC(l), rA(l), LS, rC(l), rA(l), rA(l), SF_TA | SF_CA, tCb(C.Vr(t)), tA(A.Vr(t)), CR(l, t),
                  AR(l, t));
-        pb.gemm1(PB[l][t], cB(l), cC(l), LS, cB(l), cC(l), cC(l), SF_TA | SF_CB, tB(B.Vc(t)), tCb(C.Vc(t)), BC(l, t),
+        e.gemm1(PB[l][t], cB(l), cC(l), LS, cB(l), cC(l), cC(l), SF_TA | SF_CB, tB(B.Vc(t)), tCb(C.Vc(t)), BC(l, t),
                  CC(l, t));
       } else {  // (k over the children, each bounded by its rank)
         const int hr = rC(c), hc = cC(c);
@@ -1056,29 +1172,29 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
           ib.push_back(Item((cplx ? Wcp[t] : Wc[t]) + (int64_t)a * hc * cB(l), tCb(C.Ec(l, t) + (int64_t)a * hc * cC(l)),
                             CC(c, 2 * t + a)));
         }
-        pb.gemm(PA[l][t], rC(l), rA(l), hr, rC(l), rA(l), rA(l), SF_TA | SF_CA, ia, CR(l, t), AR(l, t));
-        pb.gemm(PB[l][t], cB(l), cC(l), hc, cB(l), cC(l), cC(l), SF_TA | SF_CB, ib, BC(l, t), CC(l, t));
+        e.gemm(PA[l][t], rC(l), rA(l), hr, rC(l), rA(l), rA(l), SF_TA | SF_CA, ia, CR(l, t), AR(l, t));
+        e.gemm(PB[l][t], cB(l), cC(l), hc, cB(l), cC(l), cC(l), SF_TA | SF_CB, ib, BC(l, t), CC(l, t));
       }
-    }
+    });
     // (with the tensor-core coupling pass the coupling operands go out as tiles: A
     // operands rows x k, B operands transposed)
     const bool tl = tcl[l];
-    for (int64_t p = 0; p < nb; ++p) {
+    pb.par(nb, [&](int64_t p, auto& e) {
       const Block& b = bl[p];
-      size_t ns = P.segs.size();
+      size_t ns = e.d.segs.size();
       if (leaf && b.kind == KF) {
-        pb.gemm1(Ahat[l][p], rC(l), rB(l), LS, rC(l), rB(l), rB(l), SF_TA | SF_CA, tCb(C.Vr(b.t)), Y[p], CR(l, b.t),
+        e.gemm1(Ahat[l][p], rC(l), rB(l), LS, rC(l), rB(l), rB(l), SF_TA | SF_CA, tCb(C.Vr(b.t)), Y[p], CR(l, b.t),
                  BR(l, b.s));
-        if (tl) tile_out(ns, RP, KP2, false);
-        ns = P.segs.size();
-        pb.gemm1(Bhat[l][p], cA(l), cC(l), LS, LS, cC(l), cC(l), SF_CB, Yb[p], tCb(C.Vc(b.s)), AC(l, b.t), CC(l, b.s));
-        if (tl) tile_out(ns, NP, KP3, true);
-        ns = P.segs.size();
-        pb.gemm1(Ach[p], rC(l), LS, LS, rC(l), LS, LS, SF_TA | SF_CA, tCb(C.Vr(b.t)), tA(A.F(b.idx)), CR(l, b.t));
-        if (tl) tile_out(ns, RP, KP1, false);
-        ns = P.segs.size();
-        pb.gemm1(Bch[p], LS, cC(l), LS, LS, cC(l), cC(l), SF_CB, tB(B.F(b.idx)), tCb(C.Vc(b.s)), -1, CC(l, b.s));
-        if (tl) tile_out(ns, NP, KP1, true);
+        if (tl) tile_out(e.d, ns, RP, KP2, false);
+        ns = e.d.segs.size();
+        e.gemm1(Bhat[l][p], cA(l), cC(l), LS, LS, cC(l), cC(l), SF_CB, Yb[p], tCb(C.Vc(b.s)), AC(l, b.t), CC(l, b.s));
+        if (tl) tile_out(e.d, ns, NP, KP3, true);
+        ns = e.d.segs.size();
+        e.gemm1(Ach[p], rC(l), LS, LS, rC(l), LS, LS, SF_TA | SF_CA, tCb(C.Vr(b.t)), tA(A.F(b.idx)), CR(l, b.t));
+        if (tl) tile_out(e.d, ns, RP, KP1, false);
+        ns = e.d.segs.size();
+        e.gemm1(Bch[p], LS, cC(l), LS, LS, cC(l), cC(l), SF_CB, tB(B.F(b.idx)), tCb(C.Vc(b.s)), -1, CC(l, b.s));
+        if (tl) tile_out(e.d, ns, NP, KP1, true);
       } else if (!leaf && b.kind == KNL) {  // (k over the children, each bounded by its rank)
         const int hr = rC(c), hc = cC(c);
         std::vector<Item> ia, ib;
@@ -1087,18 +1203,18 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
                             CR(c, 2 * b.t + a)));
           ib.push_back(Item(Yb[p] + (int64_t)a * hc, tCb(C.Ec(l, b.s) + (int64_t)a * hc * cC(l)), CC(c, 2 * b.s + a)));
         }
-        pb.gemm(Ahat[l][p], rC(l), rB(l), hr, rC(l), rB(l), rB(l), SF_TA | SF_CA, ia, CR(l, b.t), BR(l, b.s));
-        if (tl) tile_out(ns, RP, KP2, false);
-        ns = P.segs.size();
-        pb.gemm(Bhat[l][p], cA(l), cC(l), hc, gc, cC(l), cC(l), SF_CB, ib, AC(l, b.t), CC(l, b.s));
-        if (tl) tile_out(ns, NP, KP3, true);
+        e.gemm(Ahat[l][p], rC(l), rB(l), hr, rC(l), rB(l), rB(l), SF_TA | SF_CA, ia, CR(l, b.t), BR(l, b.s));
+        if (tl) tile_out(e.d, ns, RP, KP2, false);
+        ns = e.d.segs.size();
+        e.gemm(Bhat[l][p], cA(l), cC(l), hc, gc, cC(l), cC(l), SF_CB, ib, AC(l, b.t), CC(l, b.s));
+        if (tl) tile_out(e.d, ns, NP, KP3, true);
       }
-    }
+    });
     if (!leaf) {
       // M E^C_k from the children's sums: half a = sum_b S_{ia,kb} T^C_{kb}
       const int hr = rC(c), hc = cC(c);
-      for (size_t q = 0; q < lt.tg.size(); ++q) {
-        if (Mt[q] < 0) continue;
+      pb.par((int64_t)lt.tg.size(), [&](int64_t q, auto& e) {
+        if (Mt[q] < 0) return;
         const Target& T = lt.tg[q];
         for (int a = 0; a < 2; ++a) {
           std::vector<Item> it;
@@ -1107,34 +1223,34 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
             if (f < 0) throw Error(H2_EINTERNAL, "missing child target");
             it.push_back({LT[c].tg[f].ssum, tCb(C.Ec(l, T.k) + (int64_t)b * hc * cC(l)), CC(c, 2 * T.k + b)});
           }
-          pb.gemm(Mt[q] + (int64_t)a * hr * cC(l), hr, cC(l), hc, hc, cC(l), cC(l), SF_CB, it, CR(c, 2 * T.i + a),
-                  CC(l, T.k));
+          e.gemm(Mt[q] + (int64_t)a * hr * cC(l), hr, cC(l), hc, hc, cC(l), cC(l), SF_CB, it, CR(c, 2 * T.i + a),
+                 CC(l, T.k));
         }
-      }
+      });
     }
     pb.end("proj", l);
     // R images (Eq. nonleafA / nonleafB) and the case-2/3/4 factors
     pb.begin();
-    for (int64_t p = 0; p < nb; ++p) {
+    pb.par(nb, [&](int64_t p, auto& e) {
       const Block& b = bl[p];
-      if (b.kind != KR) continue;
-      size_t ns = P.segs.size();
-      pb.gemm1(Ahat[l][p], rC(l), rB(l), rA(l), rA(l), rB(l), rB(l), 0, PA[l][b.t], T1[p], CR(l, b.t), BR(l, b.s),
+      if (b.kind != KR) return;
+      size_t ns = e.d.segs.size();
+      e.gemm1(Ahat[l][p], rC(l), rB(l), rA(l), rA(l), rB(l), rB(l), 0, PA[l][b.t], T1[p], CR(l, b.t), BR(l, b.s),
                AR(l, b.t));
-      if (tcl[l]) tile_out(ns, RP, KP2, false);
-      ns = P.segs.size();
-      pb.gemm1(Bhat[l][p], cA(l), cC(l), cB(l), cB(l), cC(l), cC(l), 0, T2[p], PB[l][b.s], AC(l, b.t), CC(l, b.s),
+      if (tcl[l]) tile_out(e.d, ns, RP, KP2, false);
+      ns = e.d.segs.size();
+      e.gemm1(Bhat[l][p], cA(l), cC(l), cB(l), cB(l), cC(l), cC(l), 0, T2[p], PB[l][b.s], AC(l, b.t), CC(l, b.s),
                BC(l, b.s));
-      if (tcl[l]) tile_out(ns, NP, KP3, true);
-      ns = P.segs.size();
-      pb.gemm1(PAS[p], rC(l), cA(l), rA(l), rA(l), cA(l), cA(l), 0, PA[l][b.t], tA(A.S(l, b.idx)), CR(l, b.t),
+      if (tcl[l]) tile_out(e.d, ns, NP, KP3, true);
+      ns = e.d.segs.size();
+      e.gemm1(PAS[p], rC(l), cA(l), rA(l), rA(l), cA(l), cA(l), 0, PA[l][b.t], tA(A.S(l, b.idx)), CR(l, b.t),
                AC(l, b.s), AR(l, b.t));
-      if (tcl[l]) tile_out(ns, RP, KP3, false);
-      ns = P.segs.size();
-      pb.gemm1(SBP[p], rB(l), cC(l), cB(l), cB(l), cC(l), cC(l), 0, tB(B.S(l, b.idx)), PB[l][b.s], BR(l, b.t),
+      if (tcl[l]) tile_out(e.d, ns, RP, KP3, false);
+      ns = e.d.segs.size();
+      e.gemm1(SBP[p], rB(l), cC(l), cB(l), cB(l), cC(l), cC(l), 0, tB(B.S(l, b.idx)), PB[l][b.s], BR(l, b.t),
                CC(l, b.s), BC(l, b.s));
-      if (tcl[l]) tile_out(ns, NP, KP2, true);
-    }
+      if (tcl[l]) tile_out(e.d, ns, NP, KP2, true);
+    });
     pb.end("rimage", l);
 
     // ---- couplings (Eq. leafcoup_simple / nonleafcoup_simple), summed per target in
