@@ -918,22 +918,22 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       // steps 1-2: collected NL blocks of A and B (Eq. nonleafA / nonleafB)
       pb.begin();
       const int hr = rC(c), hc = cC(c);
-      for (int64_t p = 0; p < nb; ++p) {
+      pb.par(nb, [&](int64_t p, auto& e) {
         const Block& b = bl[p];
-        if (b.kind != KNL) continue;
+        if (b.kind != KNL) return;
         for (int a = 0; a < 2; ++a)
           for (int bb = 0; bb < 2; ++bb) {
             int32_t cp = st.find(c, 2 * b.t + a, 2 * b.s + bb);
             if (cp < 0) throw Error(H2_EINTERNAL, "missing child block");
-            size_t ns = P.segs.size();
-            pb.sum(Ac[p] + (int64_t)a * hr * 2 * rB(c) + (int64_t)bb * rB(c), hr, rB(c), rB(c), 2 * rB(c), false,
-                   &Ahat[c][cp], 1);
-            if (tcl[c]) tile_in(P, ns, pad8(rC(c)), pad16(rB(c)), false);  // the children's tiles
-            ns = P.segs.size();
-            pb.sum(Bc[p] + (int64_t)a * cA(c) * gc + (int64_t)bb * hc, cA(c), hc, hc, gc, false, &Bhat[c][cp], 1);
-            if (tcl[c]) tile_in(P, ns, pad8(cC(c)), pad16(cA(c)), true);
+            size_t ns = e.d.segs.size();
+            e.sum(Ac[p] + (int64_t)a * hr * 2 * rB(c) + (int64_t)bb * rB(c), hr, rB(c), rB(c), 2 * rB(c), false,
+                  &Ahat[c][cp], 1);
+            if (tcl[c]) tile_in(e.d, ns, pad8(rC(c)), pad16(rB(c)), false);  // the children's tiles
+            ns = e.d.segs.size();
+            e.sum(Bc[p] + (int64_t)a * cA(c) * gc + (int64_t)bb * hc, cA(c), hc, hc, gc, false, &Bhat[c][cp], 1);
+            if (tcl[c]) tile_in(e.d, ns, pad8(cC(c)), pad16(cA(c)), true);
           }
-      }
+      });
       pb.end("collect", l);
       // Gram factors: Y = (NL^A)_coll E^B_j, Yb = (E^A_j)^T (NL^B)_coll, W = P_ch E
       for (int64_t t = 0; t < nc; ++t) {
@@ -946,36 +946,37 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       // (every stacked operand is taken per child half, each bounded by the child's rank:
       // the rows / columns and k past a child's rank are zero padding)
       pb.begin();
-      for (int64_t p = 0; p < nb; ++p) {
+      pb.par(nb, [&](int64_t p, auto& e) {
         const Block& b = bl[p];
-        if (b.kind != KNL) continue;
+        if (b.kind != KNL) return;
         for (int a = 0; a < 2; ++a) {  // rows of C's row child a; k over B's row children
           std::vector<Item> it;
           for (int bb = 0; bb < 2; ++bb)
             it.push_back(Item(Ac[p] + (int64_t)a * hr * 2 * rB(c) + (int64_t)bb * rB(c),
                               tB(B.Er(l, b.s) + (int64_t)bb * rB(c) * rB(l)), BR(c, 2 * b.s + bb)));
-          pb.gemm(Y[p] + (int64_t)a * hr * rB(l), hr, rB(l), rB(c), 2 * rB(c), rB(l), rB(l), 0, it,
-                  CR(c, 2 * b.t + a), BR(l, b.s));
+          e.gemm(Y[p] + (int64_t)a * hr * rB(l), hr, rB(l), rB(c), 2 * rB(c), rB(l), rB(l), 0, it,
+                 CR(c, 2 * b.t + a), BR(l, b.s));
         }
         for (int bc = 0; bc < 2; ++bc) {  // columns of C's column child bc; k over A's column children
           std::vector<Item> it;
           for (int aa = 0; aa < 2; ++aa)
             it.push_back(Item(tA(A.Ec(l, b.t) + (int64_t)aa * cA(c) * cA(l)),
                               Bc[p] + (int64_t)aa * cA(c) * gc + (int64_t)bc * hc, AC(c, 2 * b.t + aa)));
-          pb.gemm(Yb[p] + (int64_t)bc * hc, cA(l), hc, cA(c), cA(l), gc, gc, SF_TA, it, AC(l, b.t),
-                  CC(c, 2 * b.s + bc));
+          e.gemm(Yb[p] + (int64_t)bc * hc, cA(l), hc, cA(c), cA(l), gc, gc, SF_TA, it, AC(l, b.t),
+                 CC(c, 2 * b.s + bc));
         }
-      }
-      for (int64_t t = 0; t < nc; ++t)
+      });
+      pb.par(nc, [&](int64_t t, auto& e) {
         for (int a = 0; a < 2; ++a) {
-          pb.gemm1(Wr[t] + (int64_t)a * hr * rA(l), hr, rA(l), rA(c), rA(c), rA(l), rA(l), 0, PA[c][2 * t + a],
-                   tA(A.Er(l, t) + (int64_t)a * rA(c) * rA(l)), CR(c, 2 * t + a), AR(l, t), AR(c, 2 * t + a));
-          pb.gemm1(Wc[t] + (int64_t)a * hc * cB(l), hc, cB(l), cB(c), hc, cB(l), cB(l), SF_TA | SF_CB, PB[c][2 * t + a],
-                   tB(B.Ec(l, t) + (int64_t)a * cB(c) * cB(l)), CC(c, 2 * t + a), BC(l, t), BC(c, 2 * t + a));
+          e.gemm1(Wr[t] + (int64_t)a * hr * rA(l), hr, rA(l), rA(c), rA(c), rA(l), rA(l), 0, PA[c][2 * t + a],
+                  tA(A.Er(l, t) + (int64_t)a * rA(c) * rA(l)), CR(c, 2 * t + a), AR(l, t), AR(c, 2 * t + a));
+          e.gemm1(Wc[t] + (int64_t)a * hc * cB(l), hc, cB(l), cB(c), hc, cB(l), cB(l), SF_TA | SF_CB, PB[c][2 * t + a],
+                  tB(B.Ec(l, t) + (int64_t)a * cB(c) * cB(l)), CC(c, 2 * t + a), BC(l, t), BC(c, 2 * t + a));
           if (cplx)  // P^B_ch^T E^B without conjugation, for the nested projection (Eq. nonleafproj)
-            pb.gemm1(Wcp[t] + (int64_t)a * hc * cB(l), hc, cB(l), cB(c), hc, cB(l), cB(l), SF_TA, PB[c][2 * t + a],
-                     tB(B.Ec(l, t) + (int64_t)a * cB(c) * cB(l)), CC(c, 2 * t + a), BC(l, t), BC(c, 2 * t + a));
+            e.gemm1(Wcp[t] + (int64_t)a * hc * cB(l), hc, cB(l), cB(c), hc, cB(l), cB(l), SF_TA, PB[c][2 * t + a],
+                    tB(B.Ec(l, t) + (int64_t)a * cB(c) * cB(l)), CC(c, 2 * t + a), BC(l, t), BC(c, 2 * t + a));
         }
+      });
       // Eq. case1-ch-nl from the children's summed couplings, without assembling M:
       // block (a, a') of G1r_i = sum over targets (i, k), b of S_{ia,kb} S_{ia',kb}^T
       std::vector<std::vector<std::pair<int32_t, int32_t>>> trow(nc), tcol(nc);  // (target, -) per i / per k
@@ -1007,103 +1008,120 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       // the transposed values)
       std::vector<std::array<int64_t, 3>> mirror;  // (Gram matrix, half, leading dim)
       auto skip_10 = [&](int a, int a2) { return !cplx && a == 1 && a2 == 0; };
-      for (int64_t t = 0; t < nc && !formatted; ++t) {
-        if (!trow[t].empty()) {
-          G1r[t] = pb.alloc(AR_S, (int64_t)gr * gr);
-          if (!cplx) mirror.push_back({G1r[t], hr, gr});
-          for (int a = 0; a < 2; ++a)
-            for (int a2 = 0; a2 < 2; ++a2) {
-              if (skip_10(a, a2)) continue;
-              std::vector<Item> it;
-              for (auto& tq : trow[t])
-                for (int b = 0; b < 2; ++b)
-                  it.push_back({child_ssum(tq.first, a, b), child_ssum(tq.first, a2, b),
-                                CC(c, 2 * lt.tg[tq.first].k + b)});
-              pb.gemm(G1r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr, hr, hr, hc, hc, hc, gr, SF_TB | SF_CB, it,
-                      CR(c, 2 * t + a), CR(c, 2 * t + a2));
-              if (a == a2) sym_at(P, G1r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr);
-            }
+      if (!formatted) {
+        // the Gram matrices allocated first (in cluster order), then the products emitted
+        for (int64_t t = 0; t < nc; ++t) {
+          if (!trow[t].empty()) {
+            G1r[t] = pb.alloc(AR_S, (int64_t)gr * gr);
+            if (!cplx) mirror.push_back({G1r[t], hr, gr});
+          }
+          if (!tcol[t].empty()) {
+            G1c[t] = pb.alloc(AR_S, (int64_t)gc * gc);
+            if (!cplx) mirror.push_back({G1c[t], hc, gc});
+          }
         }
-        if (!tcol[t].empty()) {
-          G1c[t] = pb.alloc(AR_S, (int64_t)gc * gc);
-          if (!cplx) mirror.push_back({G1c[t], hc, gc});
-          for (int b = 0; b < 2; ++b)
-            for (int b2 = 0; b2 < 2; ++b2) {
-              if (skip_10(b, b2)) continue;
-              std::vector<Item> it;
-              for (auto& tq : tcol[t])
-                for (int a = 0; a < 2; ++a)
-                  it.push_back({child_ssum(tq.first, a, b), child_ssum(tq.first, a, b2),
-                                CR(c, 2 * lt.tg[tq.first].i + a)});
-              pb.gemm(G1c[t] + (int64_t)b * hc * gc + (int64_t)b2 * hc, hc, hc, hr, hc, hc, gc, SF_TA | SF_CB, it,
-                      CC(c, 2 * t + b), CC(c, 2 * t + b2));
-              if (b == b2) sym_at(P, G1c[t] + (int64_t)b * hc * gc + (int64_t)b2 * hc);
-            }
-        }
+        pb.par(nc, [&](int64_t t, auto& e) {
+          if (!trow[t].empty())
+            for (int a = 0; a < 2; ++a)
+              for (int a2 = 0; a2 < 2; ++a2) {
+                if (skip_10(a, a2)) continue;
+                std::vector<Item> it;
+                for (auto& tq : trow[t])
+                  for (int b = 0; b < 2; ++b)
+                    it.push_back({child_ssum(tq.first, a, b), child_ssum(tq.first, a2, b),
+                                  CC(c, 2 * lt.tg[tq.first].k + b)});
+                e.gemm(G1r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr, hr, hr, hc, hc, hc, gr, SF_TB | SF_CB, it,
+                       CR(c, 2 * t + a), CR(c, 2 * t + a2));
+                if (a == a2) sym_at(e.d, G1r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr);
+              }
+          if (!tcol[t].empty())
+            for (int b = 0; b < 2; ++b)
+              for (int b2 = 0; b2 < 2; ++b2) {
+                if (skip_10(b, b2)) continue;
+                std::vector<Item> it;
+                for (auto& tq : tcol[t])
+                  for (int a = 0; a < 2; ++a)
+                    it.push_back({child_ssum(tq.first, a, b), child_ssum(tq.first, a, b2),
+                                  CR(c, 2 * lt.tg[tq.first].i + a)});
+                e.gemm(G1c[t] + (int64_t)b * hc * gc + (int64_t)b2 * hc, hc, hc, hr, hc, hc, gc, SF_TA | SF_CB, it,
+                       CC(c, 2 * t + b), CC(c, 2 * t + b2));
+                if (b == b2) sym_at(e.d, G1c[t] + (int64_t)b * hc * gc + (int64_t)b2 * hc);
+              }
+        });
       }
       pb.end("nl_gram", l);
       pb.begin();
-      for (int64_t t = 0; t < nc && !formatted; ++t) {
-        std::vector<Item> r2, c2;
-        for (int32_t p = st.row_ptr[l][t]; p < st.row_ptr[l][t + 1]; ++p)
-          if (bl[p].kind == KNL) r2.push_back({Y[p], Y[p], BR(l, bl[p].s)});
-        for (int32_t q = st.col_ptr[l][t]; q < st.col_ptr[l][t + 1]; ++q) {
-          int32_t p = st.col_list[l][q];
-          if (bl[p].kind == KNL) c2.push_back({Yb[p], Yb[p], AC(l, bl[p].t)});
+      if (!formatted) {
+        for (int64_t t = 0; t < nc; ++t) {
+          bool rn = false, cn = false;
+          for (int32_t p = st.row_ptr[l][t]; p < st.row_ptr[l][t + 1] && !rn; ++p) rn = bl[p].kind == KNL;
+          for (int32_t q = st.col_ptr[l][t]; q < st.col_ptr[l][t + 1] && !cn; ++q) cn = bl[st.col_list[l][q]].kind == KNL;
+          if (rn) {
+            G2r[t] = pb.alloc(AR_S, (int64_t)gr * gr);
+            if (!cplx) mirror.push_back({G2r[t], hr, gr});
+          }
+          if (cn) {
+            G2c[t] = pb.alloc(AR_S, (int64_t)gc * gc);
+            if (!cplx) mirror.push_back({G2c[t], hc, gc});
+          }
+          if (!cplx) {
+            mirror.push_back({G3r[t], hr, gr});
+            mirror.push_back({G3c[t], hc, gc});
+          }
         }
-        // (each Gram matrix in its 2 x 2 blocks of children, bounded by the children's ranks)
-        if (!r2.empty()) {  // Eq. case2-ch-nl
-          G2r[t] = pb.alloc(AR_S, (int64_t)gr * gr);
-          if (!cplx) mirror.push_back({G2r[t], hr, gr});
-          for (int a = 0; a < 2; ++a)
+        pb.par(nc, [&](int64_t t, auto& e) {
+          std::vector<Item> r2, c2;
+          for (int32_t p = st.row_ptr[l][t]; p < st.row_ptr[l][t + 1]; ++p)
+            if (bl[p].kind == KNL) r2.push_back({Y[p], Y[p], BR(l, bl[p].s)});
+          for (int32_t q = st.col_ptr[l][t]; q < st.col_ptr[l][t + 1]; ++q) {
+            int32_t p = st.col_list[l][q];
+            if (bl[p].kind == KNL) c2.push_back({Yb[p], Yb[p], AC(l, bl[p].t)});
+          }
+          // (each Gram matrix in its 2 x 2 blocks of children, bounded by the children's ranks)
+          if (!r2.empty())  // Eq. case2-ch-nl
+            for (int a = 0; a < 2; ++a)
+              for (int a2 = 0; a2 < 2; ++a2) {
+                if (skip_10(a, a2)) continue;
+                std::vector<Item> it;
+                for (const Item& y : r2)
+                  it.push_back(Item(y.a + (int64_t)a * hr * rB(l), y.b + (int64_t)a2 * hr * rB(l), y.kref));
+                e.gemm(G2r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr, hr, hr, rB(l), rB(l), rB(l), gr,
+                       SF_TB | SF_CB, it, CR(c, 2 * t + a), CR(c, 2 * t + a2));
+                if (a == a2) sym_at(e.d, G2r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr);
+              }
+          if (!c2.empty())
+            for (int b = 0; b < 2; ++b)
+              for (int b2 = 0; b2 < 2; ++b2) {
+                if (skip_10(b, b2)) continue;
+                std::vector<Item> it;
+                for (const Item& y : c2) it.push_back(Item(y.a + (int64_t)b * hc, y.b + (int64_t)b2 * hc, y.kref));
+                e.gemm(G2c[t] + (int64_t)b * hc * gc + (int64_t)b2 * hc, hc, hc, cA(l), gc, gc, gc, SF_TA | SF_CB, it,
+                       CC(c, 2 * t + b), CC(c, 2 * t + b2));
+                if (b == b2) sym_at(e.d, G2c[t] + (int64_t)b * hc * gc + (int64_t)b2 * hc);
+              }
+          for (int a = 0; a < 2; ++a)  // Eq. case3-ch-nl
             for (int a2 = 0; a2 < 2; ++a2) {
               if (skip_10(a, a2)) continue;
-              std::vector<Item> it;
-              for (const Item& y : r2)
-                it.push_back(Item(y.a + (int64_t)a * hr * rB(l), y.b + (int64_t)a2 * hr * rB(l), y.kref));
-              pb.gemm(G2r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr, hr, hr, rB(l), rB(l), rB(l), gr,
-                      SF_TB | SF_CB, it, CR(c, 2 * t + a), CR(c, 2 * t + a2));
-              if (a == a2) sym_at(P, G2r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr);
+              e.gemm1(G3r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr, hr, hr, rA(l), rA(l), rA(l), gr, SF_TB | SF_CB,
+                      Wr[t] + (int64_t)a * hr * rA(l), Wr[t] + (int64_t)a2 * hr * rA(l), CR(c, 2 * t + a),
+                      CR(c, 2 * t + a2), AR(l, t));
+              if (a == a2) sym_at(e.d, G3r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr);
+              e.gemm1(G3c[t] + (int64_t)a * hc * gc + (int64_t)a2 * hc, hc, hc, cB(l), cB(l), cB(l), gc, SF_TB | SF_CB,
+                      Wc[t] + (int64_t)a * hc * cB(l), Wc[t] + (int64_t)a2 * hc * cB(l), CC(c, 2 * t + a),
+                      CC(c, 2 * t + a2), BC(l, t));
+              if (a == a2) sym_at(e.d, G3c[t] + (int64_t)a * hc * gc + (int64_t)a2 * hc);
             }
-        }
-        if (!c2.empty()) {
-          G2c[t] = pb.alloc(AR_S, (int64_t)gc * gc);
-          if (!cplx) mirror.push_back({G2c[t], hc, gc});
-          for (int b = 0; b < 2; ++b)
-            for (int b2 = 0; b2 < 2; ++b2) {
-              if (skip_10(b, b2)) continue;
-              std::vector<Item> it;
-              for (const Item& y : c2) it.push_back(Item(y.a + (int64_t)b * hc, y.b + (int64_t)b2 * hc, y.kref));
-              pb.gemm(G2c[t] + (int64_t)b * hc * gc + (int64_t)b2 * hc, hc, hc, cA(l), gc, gc, gc, SF_TA | SF_CB, it,
-                      CC(c, 2 * t + b), CC(c, 2 * t + b2));
-              if (b == b2) sym_at(P, G2c[t] + (int64_t)b * hc * gc + (int64_t)b2 * hc);
-            }
-        }
-        if (!cplx) {
-          mirror.push_back({G3r[t], hr, gr});
-          mirror.push_back({G3c[t], hc, gc});
-        }
-        for (int a = 0; a < 2; ++a)  // Eq. case3-ch-nl
-          for (int a2 = 0; a2 < 2; ++a2) {
-            if (skip_10(a, a2)) continue;
-            pb.gemm1(G3r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr, hr, hr, rA(l), rA(l), rA(l), gr, SF_TB | SF_CB,
-                     Wr[t] + (int64_t)a * hr * rA(l), Wr[t] + (int64_t)a2 * hr * rA(l), CR(c, 2 * t + a),
-                     CR(c, 2 * t + a2), AR(l, t));
-            if (a == a2) sym_at(P, G3r[t] + (int64_t)a * hr * gr + (int64_t)a2 * hr);
-            pb.gemm1(G3c[t] + (int64_t)a * hc * gc + (int64_t)a2 * hc, hc, hc, cB(l), cB(l), cB(l), gc, SF_TB | SF_CB,
-                     Wc[t] + (int64_t)a * hc * cB(l), Wc[t] + (int64_t)a2 * hc * cB(l), CC(c, 2 * t + a),
-                     CC(c, 2 * t + a2), BC(l, t));
-            if (a == a2) sym_at(P, G3c[t] + (int64_t)a * hc * gc + (int64_t)a2 * hc);
-          }
+        });
       }
       pb.end("nl_gram", l);
       pb.begin();  // the (1, 0) blocks: transposes of the (0, 1) blocks (plain sums)
-      for (const auto& mm : mirror) {
-        if (mm[1] <= 0) continue;
+      pb.par((int64_t)mirror.size(), [&](int64_t x, auto& e) {
+        const auto& mm = mirror[x];
+        if (mm[1] <= 0) return;
         const int64_t src = mm[0] + mm[1];
-        pb.sum(mm[0] + mm[1] * mm[2], (int)mm[1], (int)mm[1], (int)mm[2], (int)mm[2], false, &src, 1);
-        P.segs.back().flags |= SF_TA;
-      }
+        e.sum(mm[0] + mm[1] * mm[2], (int)mm[1], (int)mm[1], (int)mm[2], (int)mm[2], false, &src, 1);
+        e.d.segs.back().flags |= SF_TA;
+      });
       pb.end("nl_gram", l);
       for (size_t q = 0; q < lt.tg.size(); ++q)
         if (lt.tg[q].has_nlnl && lt.tg[q].cls != TC_NL) Mt[q] = pb.alloc(AR_S, (int64_t)gr * cC(l));
