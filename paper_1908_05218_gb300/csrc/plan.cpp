@@ -308,6 +308,7 @@ struct Lists {
 struct LevelTargets {
   std::vector<Target> tg;       // by row cluster i, then in order of first appearance
   std::vector<int64_t> first;   // targets of row cluster i: [first[i], first[i + 1])
+  std::vector<int64_t> tfirst;  // triples of row cluster i: [tfirst[i], tfirst[i + 1])
   std::vector<int32_t> byk;     // the same ranges, ids sorted by column cluster k
   std::vector<Triple> trip;
   Lists<Item> g1;               // leaf case-1 items by target (V^C_i^T F_ij, F_jk V^C_k)
@@ -399,6 +400,7 @@ void enumerate(const Structure& st, int l, LevelTargets& lt) {
       lt.trip.resize((size_t)ntr[nc]);
       lt.byk.resize((size_t)ntg[nc]);
       lt.first = ntg;
+      lt.tfirst = ntr;
     }
   }
 }
@@ -1285,30 +1287,36 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       if (ba.kind == KF && bb.kind == KF) return false;  // case-1 (leaf), above
       return true;
     };
+    // (per row cluster in parallel: the triples of row i only name targets of row i)
+    const int64_t nrow = (int64_t)lt.first.size() - 1;
     std::vector<int64_t> toff(ntg + 1, 0);  // counted triples per target
-    for (auto& tr : lt.trip)
-      if (counted(tr)) ++toff[tr.tgt + 1];
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t i = 0; i < nrow; ++i)
+      for (int64_t x = lt.tfirst[i]; x < lt.tfirst[i + 1]; ++x)
+        if (counted(lt.trip[x])) ++toff[lt.trip[x].tgt + 1];
     for (size_t q = 0; q < ntg; ++q) toff[q + 1] += toff[q];
     std::vector<int32_t> tord((size_t)toff[ntg]);
     {
       std::vector<int64_t> cur(toff.begin(), toff.end() - 1);
-      for (int32_t x = 0; x < (int32_t)lt.trip.size(); ++x)
-        if (counted(lt.trip[x])) tord[cur[lt.trip[x].tgt]++] = x;
+#pragma omp parallel for schedule(dynamic, 256)
+      for (int64_t i = 0; i < nrow; ++i)
+        for (int64_t x = lt.tfirst[i]; x < lt.tfirst[i + 1]; ++x)
+          if (counted(lt.trip[x])) tord[cur[lt.trip[x].tgt]++] = (int32_t)x;
     }
     const int kmax = std::max(std::max(leaf ? LS : 0, rB(l)), cA(l));
     if (!leaf) {
       pb.begin();
-      for (size_t q = 0; q < lt.tg.size(); ++q) {
-        Target& T = lt.tg[q];
+      pb.par((int64_t)lt.tg.size(), [&](int64_t q, auto& e) {
+        const Target& T = lt.tg[q];
         if (Mt[q] >= 0) {  // (k over the children of i, each bounded by its rank)
           const int hr = rC(c);
           std::vector<Item> it;
           for (int a = 0; a < 2; ++a)
             it.push_back(Item(tCb(C.Er(l, T.i) + (int64_t)a * hr * rC(l)), Mt[q] + (int64_t)a * hr * cC(l),
                               CR(c, 2 * T.i + a)));
-          pb.gemm(T.ssum, rC(l), cC(l), hr, rC(l), cC(l), cC(l), SF_TA | SF_CA | SF_ACC, it, CR(l, T.i), CC(l, T.k));
+          e.gemm(T.ssum, rC(l), cC(l), hr, rC(l), cC(l), cC(l), SF_TA | SF_CA | SF_ACC, it, CR(l, T.i), CC(l, T.k));
         }
-      }
+      });
       pb.end("coup", l);
     }
     if (tcl[l]) {
@@ -1524,22 +1532,25 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
           if (pp >= 0 && X[pp] >= 0) H[c][p] = pb.alloc(AR_P, (int64_t)rC(c) * cC(c));
         }
     // (the children's halves of Xt and X, each bounded by the children's ranks)
+    const int64_t nbl = (int64_t)bl.size();
     pb.begin();
-    for (size_t p = 0; p < bl.size(); ++p)
+    pb.par(nbl, [&](int64_t p, auto& e) {
       if (Xt[p] >= 0)
         for (int b = 0; b < 2; ++b)
-          pb.gemm1(Xt[p] + (int64_t)b * hc, rC(l), hc, cC(l), cC(l), cC(l), 2 * hc, SF_TB, H[l][p],
-                   tCb(C.Ec(l, bl[p].s) + (int64_t)b * hc * cC(l)), CR(l, bl[p].t), CC(c, 2 * bl[p].s + b),
-                   CC(l, bl[p].s));
+          e.gemm1(Xt[p] + (int64_t)b * hc, rC(l), hc, cC(l), cC(l), cC(l), 2 * hc, SF_TB, H[l][p],
+                  tCb(C.Ec(l, bl[p].s) + (int64_t)b * hc * cC(l)), CR(l, bl[p].t), CC(c, 2 * bl[p].s + b),
+                  CC(l, bl[p].s));
+    });
     pb.end("split", l);
     pb.begin();
-    for (size_t p = 0; p < bl.size(); ++p)
+    pb.par(nbl, [&](int64_t p, auto& e) {
       if (X[p] >= 0)
         for (int a = 0; a < 2; ++a)
           for (int b = 0; b < 2; ++b)
-            pb.gemm1(X[p] + (int64_t)a * hr * 2 * hc + (int64_t)b * hc, hr, hc, rC(l), rC(l), 2 * hc, 2 * hc, 0,
-                     tCb(C.Er(l, bl[p].t) + (int64_t)a * hr * rC(l)), Xt[p] + (int64_t)b * hc, CR(c, 2 * bl[p].t + a),
-                     CC(c, 2 * bl[p].s + b), CR(l, bl[p].t));
+            e.gemm1(X[p] + (int64_t)a * hr * 2 * hc + (int64_t)b * hc, hr, hc, rC(l), rC(l), 2 * hc, 2 * hc, 0,
+                    tCb(C.Er(l, bl[p].t) + (int64_t)a * hr * rC(l)), Xt[p] + (int64_t)b * hc, CR(c, 2 * bl[p].t + a),
+                    CC(c, 2 * bl[p].s + b), CR(l, bl[p].t));
+    });
     pb.end("split", l);
     std::vector<std::pair<int64_t, int64_t>> Fupd;
     std::vector<int32_t> Frow;
@@ -1548,17 +1559,24 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
     // launch) into F += V^C (X E^C) (a third)
     std::vector<std::pair<int64_t, int32_t>> fpart;  // (part of X, child block)
     pb.begin();
-    for (size_t p = 0; p < bl.size(); ++p) {
-      if (X[p] < 0) continue;
-      for (int a = 0; a < 2; ++a)
-        for (int bb = 0; bb < 2; ++bb) {
-          int32_t cp = st.find(c, 2 * bl[p].t + a, 2 * bl[p].s + bb);
-          const Block& cb = st.blocks[c][cp];
-          int64_t xab = X[p] + (int64_t)a * hr * 2 * hc + (int64_t)bb * hc;
-          if (cb.kind == KR) pb.sum(tC(C.S(c, cb.idx)), hr, hc, 2 * hc, cC(c), true, {xab});
-          else if (cb.kind == KNL) pb.sum(H[c][cp], hr, hc, 2 * hc, cC(c), true, {xab});
-          else fpart.push_back({xab, cp});
-        }
+    {
+      // (the F children's parts collected per block, then listed in block order)
+      std::vector<std::array<std::pair<int64_t, int32_t>, 4>> fp((size_t)nbl);
+      std::vector<int8_t> nfp((size_t)nbl, 0);
+      pb.par(nbl, [&](int64_t p, auto& e) {
+        if (X[p] < 0) return;
+        for (int a = 0; a < 2; ++a)
+          for (int bb = 0; bb < 2; ++bb) {
+            int32_t cp = st.find(c, 2 * bl[p].t + a, 2 * bl[p].s + bb);
+            const Block& cb = st.blocks[c][cp];
+            int64_t xab = X[p] + (int64_t)a * hr * 2 * hc + (int64_t)bb * hc;
+            if (cb.kind == KR) e.sum(tC(C.S(c, cb.idx)), hr, hc, 2 * hc, cC(c), true, {xab});
+            else if (cb.kind == KNL) e.sum(H[c][cp], hr, hc, 2 * hc, cC(c), true, {xab});
+            else fp[p][nfp[p]++] = {xab, cp};
+          }
+      });
+      for (int64_t p = 0; p < nbl; ++p)
+        for (int x = 0; x < nfp[p]; ++x) fpart.push_back(fp[p][x]);
     }
     pb.end("split", l);
     pb.begin();
@@ -1572,9 +1590,10 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
     }
     pb.end("split", l);
     pb.begin();
-    for (size_t q = 0; q < Fupd.size(); ++q)
-      pb.gemm1(Fupd[q].second, LS, LS, rC(c), rC(c), LS, LS, SF_ACC, tCb(C.Vr(Frow[q])), Fupd[q].first, -1, -1,
-               CR(c, Frow[q]));
+    pb.par((int64_t)Fupd.size(), [&](int64_t q, auto& e) {
+      e.gemm1(Fupd[q].second, LS, LS, rC(c), rC(c), LS, LS, SF_ACC, tCb(C.Vr(Frow[q])), Fupd[q].first, -1, -1,
+              CR(c, Frow[q]));
+    });
     pb.end("split", c);
     pb.close_memset(zS, AR_S);
   }
