@@ -618,36 +618,64 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       Lists<int64_t> Ksets(nb), Isets(nb);
       const size_t ntg = lt.tg.size();
       Lists<Item> gF(ntg), gZ(ntg), gZp(ntg), gZpp(ntg), g1(ntg);
+      // The lists keyed by target or by the block (i, j) hold entries of one row cluster
+      // i only, so the rows are processed in parallel, each in triple order.  The lists
+      // keyed by the block (j, k) (Isets) collect over the rows i of column j: they are
+      // built per block from column j's blocks (i, j), which come in the order of i, the
+      // order of the triples.
+      auto iset_terms = [&](int64_t q, auto&& f) {
+        const Block& bb = bl[q];
+        if (bb.kind != KF) return;
+        for (int32_t x = st.col_ptr[l][bb.t]; x < st.col_ptr[l][bb.t + 1]; ++x) {
+          const int32_t pa = st.col_list[l][x];
+          if (bl[pa].kind != KF) continue;
+          const int32_t id = lt.find(bl[pa].t, bb.s);
+          if (id < 0) throw Error(H2_EINTERNAL, "missing target");
+          if (lt.tg[id].cls != TC_F) f(pa);
+        }
+      };
       for (int pass = 0; pass < 2; ++pass) {
-        for (auto& tr : lt.trip) {
-          const Block &ba = bl[tr.pa], &bb = bl[tr.pb];
-          const Target& T = lt.tg[tr.tgt];
-          if (T.cls == TC_F) {
-            if (ba.kind == KF && bb.kind == KF) {
-              if (pass) gF.put(tr.tgt, {tA(A.F(ba.idx)), tB(B.F(bb.idx))});
-              else gF.count(tr.tgt);
-            } else if (ba.kind == KF) {
-              if (pass) gZ.put(tr.tgt, {Y[tr.pa], tB(B.S(l, bb.idx)), BR(l, ba.s)});
-              else gZ.count(tr.tgt);
-            } else if (bb.kind == KF) {
-              if (pass) gZp.put(tr.tgt, {tA(A.S(l, ba.idx)), Yb[tr.pb], AC(l, ba.s)});
-              else gZp.count(tr.tgt);
-            } else {
-              if (pass) gZpp.put(tr.tgt, {T1[tr.pa], tB(B.S(l, bb.idx)), BR(l, ba.s)});
-              else gZpp.count(tr.tgt);
-            }
-          } else if (ba.kind == KF && bb.kind == KF) {
-            if (pass) {
-              Ksets.put(tr.pa, Q[tr.pb]);
-              Isets.put(tr.pb, Rr[tr.pa]);
-              g1.put(tr.tgt, {tr.pa, tr.pb});  // (V^C_i^T F_ij)(F_jk V^C_k) after the eig (blocks)
-            } else {
-              Ksets.count(tr.pa);
-              Isets.count(tr.pb);
-              g1.count(tr.tgt);
+        int missing = 0;
+#pragma omp parallel for schedule(dynamic, 64)
+        for (int64_t i = 0; i < nc; ++i)
+          for (int64_t x = lt.tfirst[i]; x < lt.tfirst[i + 1]; ++x) {
+            const Triple& tr = lt.trip[x];
+            const Block &ba = bl[tr.pa], &bb = bl[tr.pb];
+            const Target& T = lt.tg[tr.tgt];
+            if (T.cls == TC_F) {
+              if (ba.kind == KF && bb.kind == KF) {
+                if (pass) gF.put(tr.tgt, {tA(A.F(ba.idx)), tB(B.F(bb.idx))});
+                else gF.count(tr.tgt);
+              } else if (ba.kind == KF) {
+                if (pass) gZ.put(tr.tgt, {Y[tr.pa], tB(B.S(l, bb.idx)), BR(l, ba.s)});
+                else gZ.count(tr.tgt);
+              } else if (bb.kind == KF) {
+                if (pass) gZp.put(tr.tgt, {tA(A.S(l, ba.idx)), Yb[tr.pb], AC(l, ba.s)});
+                else gZp.count(tr.tgt);
+              } else {
+                if (pass) gZpp.put(tr.tgt, {T1[tr.pa], tB(B.S(l, bb.idx)), BR(l, ba.s)});
+                else gZpp.count(tr.tgt);
+              }
+            } else if (ba.kind == KF && bb.kind == KF) {
+              if (pass) {
+                Ksets.put(tr.pa, Q[tr.pb]);
+                g1.put(tr.tgt, {tr.pa, tr.pb});  // (V^C_i^T F_ij)(F_jk V^C_k) after the eig (blocks)
+              } else {
+                Ksets.count(tr.pa);
+                g1.count(tr.tgt);
+              }
             }
           }
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : missing)
+        for (int64_t q = 0; q < nb; ++q) {
+          try {
+            if (pass) iset_terms(q, [&](int32_t pa) { Isets.put(q, Rr[pa]); });
+            else iset_terms(q, [&](int32_t) { Isets.count(q); });
+          } catch (const Error&) {
+            ++missing;
+          }
         }
+        if (missing) throw Error(H2_EINTERNAL, "missing target");
         if (pass == 0) {
           gF.finish_count();
           gZ.finish_count();
