@@ -431,6 +431,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
     }
     P.items.reserve(P.items.size() + (size_t)(trip + trip / 2 + 16 * nblk));
     P.segs.reserve(P.segs.size() + (size_t)(20 * nblk));
+    P.aev.reserve(P.aev.size() + (size_t)(20 * nblk));  // about 15 allocations per block
     // the tensor-core passes' steps: at most one per coupling term and dense product
     if (prm.precision == H2_MIXED_BF16X3 && !A.cplx) P.tsteps.reserve(P.tsteps.size() + (size_t)(trip + trip / 2));
   }
