@@ -164,13 +164,30 @@ struct PlanBuilder {
       cmax = std::max(cmax, cls[i]);
     }
     if (cmin == cmax) return;
-    // stable counting sort on the class (largest cost first)
-    std::vector<size_t> start((size_t)(cmax - cmin) + 2, 0);
-    for (size_t i = 0; i < n; ++i) ++start[(size_t)(cls[i] - cmin) + 1];
-    for (size_t c = 1; c < start.size(); ++c) start[c] += start[c - 1];
+    // stable counting sort on the class (largest cost first): the segments in nch
+    // contiguous chunks, each chunk's share of every class placed after the shares of
+    // the classes before it and of the earlier chunks of its class
+    const size_t ncls = (size_t)(cmax - cmin) + 1;
+    const int64_t nch = n > 65536 ? 64 : 1;
+    std::vector<size_t> cnt((size_t)nch * ncls, 0);
+#pragma omp parallel for schedule(static, 1) if (nch > 1)
+    for (int64_t h = 0; h < nch; ++h)
+      for (size_t i = n * h / nch; i < n * (h + 1) / nch; ++i) ++cnt[(size_t)h * ncls + (size_t)(cls[i] - cmin)];
+    size_t run = 0;
+    for (size_t c = 0; c < ncls; ++c)
+      for (int64_t h = 0; h < nch; ++h) {
+        const size_t x = cnt[(size_t)h * ncls + c];
+        cnt[(size_t)h * ncls + c] = run;
+        run += x;
+      }
     PlanArray<Seg> sorted(n);
-    for (size_t i = 0; i < n; ++i) sorted[start[(size_t)(cls[i] - cmin)]++] = P.segs[g0 + i];
-    std::copy(sorted.begin(), sorted.end(), P.segs.begin() + g0);
+#pragma omp parallel for schedule(static, 1) if (nch > 1)
+    for (int64_t h = 0; h < nch; ++h) {
+      size_t* at = cnt.data() + (size_t)h * ncls;
+      for (size_t i = n * h / nch; i < n * (h + 1) / nch; ++i) sorted[at[(size_t)(cls[i] - cmin)]++] = P.segs[g0 + i];
+    }
+#pragma omp parallel for schedule(static) if (nch > 1)
+    for (int64_t i = 0; i < (int64_t)n; ++i) P.segs[g0 + i] = sorted[i];
   }
   void end(const char* phase, int level) {
     if (P.segs.size() > g0) {
