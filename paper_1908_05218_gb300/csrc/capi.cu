@@ -468,6 +468,12 @@ void validate_plan(const Plan& P, const int64_t sizes[kArenas]) {
   // live allocations of the work regions, replayed in program order; a region is
   // bump-allocated between resets, so its live list stays sorted by start
   std::vector<std::pair<int64_t, int64_t>> live[kArenas];
+  // the search's first level: the start of every kStride-th live allocation, rebuilt
+  // when the list has changed (small enough to stay in cache while millions of
+  // accesses are looked up)
+  constexpr size_t kStride = 64;
+  std::vector<int64_t> top[kArenas];
+  bool stale[kArenas] = {};
   size_t ev = 0;
   auto is_work = [](int64_t a) { return a == AR_P || a == AR_G0 || a == AR_G1 || a == AR_S; };
   auto check = [&](int64_t tagged, int64_t extent, const char* what) {
@@ -476,9 +482,15 @@ void validate_plan(const Plan& P, const int64_t sizes[kArenas]) {
     if (tagged < 0 || off + extent > sizes[a])
       throw Error(H2_EINTERNAL, std::string("plan access out of bounds: ") + what);
     if (!is_work(a)) return;
+    // the last allocation starting at or before off: its block of kStride from the
+    // first level, then within the block
     const auto& v = live[a];
-    auto it = std::upper_bound(v.begin(), v.end(), std::make_pair(off, INT64_MAX));
-    if (it == v.begin() || std::prev(it)->first + std::prev(it)->second < off + extent)
+    const auto& t = top[a];
+    const size_t blk = (size_t)(std::upper_bound(t.begin(), t.end(), off) - t.begin());
+    if (blk == 0) throw Error(H2_EINTERNAL, std::string("plan access outside its allocation: ") + what);
+    const auto lo = v.begin() + (blk - 1) * kStride, hi = v.begin() + std::min(v.size(), blk * kStride);
+    const auto it = std::upper_bound(lo, hi, std::make_pair(off, INT64_MAX));
+    if (std::prev(it)->first + std::prev(it)->second < off + extent)
       throw Error(H2_EINTERNAL, std::string("plan access outside its allocation: ") + what);
   };
   // an operand tile of tr rows and kp columns holding an m x n matrix (transposed: n x m)
@@ -562,12 +574,20 @@ void validate_plan(const Plan& P, const int64_t sizes[kArenas]) {
       const Plan::AllocEv& x = P.aev[ev];
       if (x.reset) {
         live[x.arena].clear();
+        stale[x.arena] = true;
       } else if (x.size > 0) {  // (an empty allocation shares the next one's start)
         if (!live[x.arena].empty() && live[x.arena].back().first + live[x.arena].back().second > x.start)
           throw Error(H2_EINTERNAL, "plan allocations overlap");
         live[x.arena].push_back({x.start, x.size});
+        stale[x.arena] = true;
       }
     }
+    for (int a = 0; a < kArenas; ++a)
+      if (stale[a]) {
+        top[a].clear();
+        for (size_t q = 0; q < live[a].size(); q += kStride) top[a].push_back(live[a][q].first);
+        stale[a] = false;
+      }
     const Launch& L = P.launches[li];
     if (L.kind == Launch::GEMM) {
       // segments of one launch are checked in parallel (the live lists are read only)
