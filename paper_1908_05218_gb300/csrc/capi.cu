@@ -468,12 +468,12 @@ void validate_plan(const Plan& P, const int64_t sizes[kArenas]) {
   // live allocations of the work regions, replayed in program order; a region is
   // bump-allocated between resets, so its live list stays sorted by start
   std::vector<std::pair<int64_t, int64_t>> live[kArenas];
-  // the search's first level: the start of every kStride-th live allocation, rebuilt
-  // when the list has changed (small enough to stay in cache while millions of
-  // accesses are looked up)
-  constexpr size_t kStride = 64;
-  std::vector<int64_t> top[kArenas];
-  bool stale[kArenas] = {};
+  // lookup table of each region: entry b = the last live allocation starting at or
+  // before offset b * kBucket (-1: none), extended as allocations are appended (their
+  // starts increase) and cleared with the region
+  constexpr int64_t kBucket = 512;
+  std::vector<int32_t> bucket[kArenas];
+  size_t done[kArenas] = {};
   size_t ev = 0;
   auto is_work = [](int64_t a) { return a == AR_P || a == AR_G0 || a == AR_G1 || a == AR_S; };
   auto check = [&](int64_t tagged, int64_t extent, const char* what) {
@@ -482,15 +482,14 @@ void validate_plan(const Plan& P, const int64_t sizes[kArenas]) {
     if (tagged < 0 || off + extent > sizes[a])
       throw Error(H2_EINTERNAL, std::string("plan access out of bounds: ") + what);
     if (!is_work(a)) return;
-    // the last allocation starting at or before off: its block of kStride from the
-    // first level, then within the block
+    // the last allocation starting at or before off: from the table's entry for off's
+    // bucket, forward over the allocations that start inside the bucket
     const auto& v = live[a];
-    const auto& t = top[a];
-    const size_t blk = (size_t)(std::upper_bound(t.begin(), t.end(), off) - t.begin());
-    if (blk == 0) throw Error(H2_EINTERNAL, std::string("plan access outside its allocation: ") + what);
-    const auto lo = v.begin() + (blk - 1) * kStride, hi = v.begin() + std::min(v.size(), blk * kStride);
-    const auto it = std::upper_bound(lo, hi, std::make_pair(off, INT64_MAX));
-    if (std::prev(it)->first + std::prev(it)->second < off + extent)
+    const auto& bt = bucket[a];
+    const size_t b = (size_t)(off / kBucket);
+    int64_t h = bt.empty() ? -1 : bt[std::min(b, bt.size() - 1)];
+    while (h + 1 < (int64_t)v.size() && v[(size_t)h + 1].first <= off) ++h;
+    if (h < 0 || v[(size_t)h].first + v[(size_t)h].second < off + extent)
       throw Error(H2_EINTERNAL, std::string("plan access outside its allocation: ") + what);
   };
   // an operand tile of tr rows and kp columns holding an m x n matrix (transposed: n x m)
@@ -574,20 +573,30 @@ void validate_plan(const Plan& P, const int64_t sizes[kArenas]) {
       const Plan::AllocEv& x = P.aev[ev];
       if (x.reset) {
         live[x.arena].clear();
-        stale[x.arena] = true;
+        bucket[x.arena].clear();
+        done[x.arena] = 0;
       } else if (x.size > 0) {  // (an empty allocation shares the next one's start)
         if (!live[x.arena].empty() && live[x.arena].back().first + live[x.arena].back().second > x.start)
           throw Error(H2_EINTERNAL, "plan allocations overlap");
         live[x.arena].push_back({x.start, x.size});
-        stale[x.arena] = true;
       }
     }
-    for (int a = 0; a < kArenas; ++a)
-      if (stale[a]) {
-        top[a].clear();
-        for (size_t q = 0; q < live[a].size(); q += kStride) top[a].push_back(live[a][q].first);
-        stale[a] = false;
+    // extend each table over the allocations appended since: bucket b gets the last
+    // allocation with start <= b * kBucket, up to the bucket of the last one's start
+    for (int a = 0; a < kArenas; ++a) {
+      const auto& v = live[a];
+      auto& bt = bucket[a];
+      for (size_t q = done[a]; q < v.size(); ++q) {
+        const size_t upto = (size_t)(v[q].first / kBucket) + 1;  // buckets whose start is < next bucket
+        while (bt.size() < upto) {
+          // bucket bt.size() starts at bt.size() * kBucket; allocation q starts at or
+          // before it only if bt.size() * kBucket >= v[q].first
+          const int64_t bs = (int64_t)bt.size() * kBucket;
+          bt.push_back(bs >= v[q].first ? (int32_t)q : (int32_t)q - 1);
+        }
       }
+      done[a] = v.size();
+    }
     const Launch& L = P.launches[li];
     if (L.kind == Launch::GEMM) {
       // segments of one launch are checked in parallel (the live lists are read only)
