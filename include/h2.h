@@ -198,14 +198,26 @@ h2_status h2_plan_stats(const double* points, int64_t n, int32_t leaf_size, doub
 /* Host-only self-check of the product program (no device memory, no GPU needed):
  * builds the tree, partition and H^2 ranks of the Laplace kernel (as h2_build_packed, at
  * ε = eps) for the points, then the program of C = A A for every truncation mode
- * (paper, sv, full, formatted), both precisions and rank caps 24 and 48, and the
- * matvec programs for 1 and 3 right-hand sides.  Each is validated: every operand and
- * output of every segment and eigen task lies inside one live allocation of its
- * region (replayed in program order) or inside its matrix.  *checked gets the number of
- * programs checked (18).  H2_EINTERNAL names the first program and access that fails.
+ * (paper, sv, full, formatted), the precisions H2_FP64, H2_MIXED_FP32 and
+ * H2_MIXED_BF16X3 and rank caps 24 and 48, and the matvec programs for 1 and 3
+ * right-hand sides.  Each is validated: every operand and output of every segment,
+ * tensor-core step and eigen task lies inside one live allocation of its region
+ * (replayed in program order) or inside its matrix.  *checked gets the number of
+ * programs checked (26).  H2_EINTERNAL names the first program and access that fails.
  * The paper has no counterpart: this checks the library's own memory layout. */
 h2_status h2_plan_selfcheck(const double* points, int64_t n, int32_t leaf_size, double eta, double eps,
                             int32_t* checked);
+
+/* Host-only digest of the product program (no device memory, no GPU needed): the
+ * program of C = A A for the points, built as h2_plan_stats builds it (Laplace ranks
+ * at ε = eps, rank cap 48) for `precision` (h2_precision) and `trunc` (h2_trunc),
+ * hashed (64-bit FNV-1a) over every field of every segment, item, tensor-core group
+ * and step, eigen task, launch and allocation of the work regions.  Equal digests mean
+ * equal programs.  The program is built with every host thread; its content does not
+ * depend on their number.  Errors: H2_EINVAL for bad arguments.  The paper has no
+ * counterpart. */
+h2_status h2_plan_digest(const double* points, int64_t n, int32_t leaf_size, double eta, double eps,
+                         int32_t precision, int32_t trunc, uint64_t* digest);
 
 /* Create a handle from host arrays that describe an H^2 matrix on the same tree
  * and partition that h2_build(points, n, kernel, leaf_size, eta, ...) makes.  Used

@@ -873,6 +873,72 @@ h2_status h2_plan_stats(const double* points, int64_t n, int32_t leaf_size, doub
   });
 }
 
+h2_status h2_plan_digest(const double* points, int64_t n, int32_t leaf_size, double eta, double eps,
+                         int32_t precision, int32_t trunc, uint64_t* digest) {
+  if (!points || !digest) return fail(H2_EINVAL, "null argument");
+  return guarded([&] {
+    if (!(eps > 0) || !(eps < 1)) throw Error(H2_EINVAL, "eps must lie in (0, 1)");
+    if (trunc < H2_TRUNC_PAPER || trunc > H2_TRUNC_FORMATTED) throw Error(H2_EINVAL, "unknown truncation rule");
+    if (precision < H2_FP64 || precision > H2_MIXED_BF16X3) throw Error(H2_EINVAL, "unknown precision");
+    auto st = build_structure(points, n, leaf_size, eta);
+    const double h = std::cbrt(1.0 / (double)n);
+    h2_kernel k{H2_K_LAPLACE, 0.0, 1.0 / (2.0 * M_PI * h), 0.0};
+    Packed p;
+    build_h2_host(*st, k, eps, p);
+    Mat m;
+    m.st = st;
+    m.Kr.assign(st->L + 1, 0);
+    m.Kc.assign(st->L + 1, 0);
+    for (int l = 0; l <= st->L; ++l)
+      for (int64_t t = 0; t < (1LL << l); ++t) {
+        m.Kr[l] = std::max(m.Kr[l], p.kr[Structure::node(l, t)]);
+        m.Kc[l] = std::max(m.Kc[l], p.kc[Structure::node(l, t)]);
+      }
+    for (int l = 0; l <= st->L; ++l) {
+      m.Kr[l] = cap_round(m.Kr[l]);
+      m.Kc[l] = cap_round(m.Kc[l]);
+    }
+    mat_elems(m);
+    Plan P;
+    Mat C;
+    C.st = st;
+    MmpParams prm{1e-4, trunc, 48, precision};
+    build_mmp_plan(m, m, C, prm, P);
+    // FNV-1a over the fields (not the raw structs: their padding bytes are unset)
+    uint64_t hsh = 1469598103934665603ull;
+    auto mix = [&](auto v) {
+      const unsigned char* c = reinterpret_cast<const unsigned char*>(&v);
+      for (size_t i = 0; i < sizeof(v); ++i) {
+        hsh ^= c[i];
+        hsh *= 1099511628211ull;
+      }
+    };
+    for (const Seg& x : P.segs) {
+      mix(x.out), mix(x.first), mix(x.count), mix(x.m), mix(x.n), mix(x.k), mix(x.lda), mix(x.ldb), mix(x.ldc);
+      mix(x.mref), mix(x.nref), mix(x.flags), mix(x.flags2), mix(x.inst), mix(x.trows);
+    }
+    for (const Item& x : P.items) mix(x.a), mix(x.b), mix(x.kref), mix(x.lda), mix(x.ldb), mix(x.kpad);
+    for (const TcGroup& x : P.tgroups) {
+      mix(x.out[0]), mix(x.out[1]), mix(x.mref[0]), mix(x.mref[1]), mix(x.nref), mix(x.first), mix(x.count);
+      mix(x.m), mix(x.n), mix(x.ldc), mix(x.acc), mix(x.inst);
+    }
+    for (const TcStep& x : P.tsteps) mix(x.a[0]), mix(x.a[1]), mix(x.b), mix(x.kref), mix(x.kpad);
+    for (const EigTask& x : P.eigs) {
+      mix(x.g[0]), mix(x.g[1]), mix(x.g[2]), mix(x.out), mix(x.rank_out), mix(x.child1), mix(x.child2);
+      mix(x.nleaf), mix(x.n_pad), mix(x.half), mix(x.kcap), mix(x.col), mix(x.klim), mix(x.inst);
+    }
+    for (const Launch& x : P.launches) {
+      mix((int)x.kind), mix(x.first), mix(x.count), mix(x.off), mix(x.elems), mix(x.level), mix(x.tc);
+      mix(x.sums), mix(x.aux), mix(x.aux2), mix(x.aux3), mix(x.flops);
+      for (const char* c = x.phase; *c; ++c) mix(*c);
+    }
+    for (const auto& x : P.aev) mix(x.launch), mix(x.arena), mix(x.reset), mix(x.start), mix(x.size);
+    for (int a = 0; a < kArenas; ++a) mix(P.region[a]);
+    mix(P.fext), mix(P.flops), mix(P.scratch_elems), mix(P.region_esize);
+    *digest = hsh;
+  });
+}
+
 h2_status h2_plan_selfcheck(const double* points, int64_t n, int32_t leaf_size, double eta, double eps,
                             int32_t* checked) {
   if (!points || !checked) return fail(H2_EINVAL, "null argument");

@@ -27,7 +27,7 @@ _TRUNC = {"paper": TRUNC_PAPER, "sv": TRUNC_SV, "full": TRUNC_FULL, "formatted":
 SYMBOLS = ["h2_build", "h2_import", "h2_import_complex", "h2_export", "h2_mmp", "h2_mmp_batched", "h2_matvec", "h2_matvec_noalloc", "h2_to_dense", "h2_info",
            "h2_tree_perm", "h2_level_blocks", "h2_trace_enable", "h2_trace_read", "h2_trace_flops", "h2_trace_phase", "h2_destroy",
            "h2_last_error", "h2_kernel_launches", "h2_plan_selfcheck", "h2_set_alloc_limit", "h2_plan_stats",
-           "h2_build_packed"]
+           "h2_plan_digest", "h2_build_packed"]
 
 
 class H2Error(RuntimeError):
@@ -84,6 +84,7 @@ def load(path: str = LIB_PATH):
     lib.h2_plan_selfcheck.argtypes = [P, I64, I32, C.c_double, C.c_double, P]
     lib.h2_set_alloc_limit.argtypes = [I64]
     lib.h2_plan_stats.argtypes = [P, I64, I32, D, D, I32, P, P, P]
+    lib.h2_plan_digest.argtypes = [P, I64, I32, D, D, I32, I32, P]
     lib.h2_build_packed.argtypes = [P, I64, C.POINTER(Kernel), I32, D, D, P, P, P, P, P, P, P, P, P]
     lib.h2_trace_phase.argtypes = [P, I32]
     lib.h2_trace_phase.restype = C.c_char_p
@@ -327,6 +328,16 @@ def plan_stats(points: np.ndarray, leaf_size: int = 32, eta: float = 1.0, eps: f
     _check(load().h2_plan_stats(_ptr(pts), pts.shape[0], leaf_size, float(eta), float(eps), _TRUNC[trunc],
                                 C.byref(fl), C.byref(sg), C.byref(it)))
     return fl.value, int(sg.value), int(it.value)
+
+
+def plan_digest(points: np.ndarray, leaf_size: int = 32, eta: float = 1.0, eps: float = 1e-4,
+                precision: int = FP64, trunc: str = "paper") -> int:
+    """64-bit digest of the program of C = A A for these points (h2_plan_digest), on the host."""
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    d = C.c_uint64(0)
+    _check(load().h2_plan_digest(_ptr(pts), pts.shape[0], leaf_size, float(eta), float(eps), int(precision),
+                                 _TRUNC[trunc], C.byref(d)))
+    return int(d.value)
 
 
 def kernel_launches() -> int:

@@ -5,8 +5,13 @@ mode, three precisions (float64, float32, BF16 split with the tensor-core coupli
 and its operand tiles) and two rank caps, plus the matvec programs, and validates every
 access of every segment and eigen task against the live allocations of its region.
 The geometries cover leaf sizes that are not multiples of four (storage caps round
-up), ragged trees and η ≠ 1.
+up), ragged trees and η ≠ 1.  h2_plan_digest hashes a program: the host builds it
+with all its threads, and the program must not depend on their number.
 """
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 
@@ -74,3 +79,35 @@ def test_program_size_follows_the_truncation_rule(lib):
     assert st["paper"] == st["sv"]
     assert st["full"][0] > st["paper"][0]
     assert st["formatted"][0] < st["paper"][0] and st["formatted"][1] < st["paper"][1]
+
+
+_DIGEST_CHILD = """
+import sys
+sys.path.insert(0, {root!r})
+from paper_1908_05218_gb300 import h2, inputs
+pts = inputs.workload_cube_array(4, 4, 1024).points
+print(" ".join(str(h2.plan_digest(pts, 32, 1.0, 1e-4, p, t)) for p in (0, 1, 3) for t in ("paper", "formatted")))
+"""
+
+
+def test_program_does_not_depend_on_the_host_thread_count(lib):
+    # N = 16,384: the launch groups are large enough for the parallel emission (each
+    # thread writes a contiguous range of its loop, appended in index order)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = []
+    for nt in ("1", "3", "8"):
+        env = dict(os.environ, OMP_NUM_THREADS=nt)
+        r = subprocess.run([sys.executable, "-c", _DIGEST_CHILD.format(root=root)], env=env, capture_output=True,
+                           text=True, timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        out.append(r.stdout.split())
+    assert out[0] == out[1] == out[2]
+    assert len(set(out[0])) == len(out[0])  # the precisions and truncation modes differ
+
+
+def test_digest_rejects_bad_arguments(lib):
+    pts = inputs.uniform_cube(300, 9)
+    with pytest.raises(lib.H2Error):
+        lib.plan_digest(pts, 7, 0.7, 1e-4, precision=9)
+    with pytest.raises(lib.H2Error):
+        lib.plan_digest(pts, 7, 0.7, 1.5)
