@@ -115,6 +115,31 @@ struct Emit {
   }
 };
 
+// The loop `for x in [0, n): body(x, out)` (body appends to out) in parallel: each
+// thread collects a contiguous range of x in its own vector, and the vectors are joined
+// in order, so the result is the serial loop's.
+template <class T, class F>
+std::vector<T> ordered_collect(int64_t n, F&& body) {
+  std::vector<std::vector<T>> part;
+  int used = 1;
+#pragma omp parallel if (n >= 256)
+  {
+#pragma omp single
+    {
+      used = omp_get_num_threads();
+      part.resize((size_t)used);
+    }
+    const int id = omp_get_thread_num();
+    for (int64_t x = n * id / used; x < n * (id + 1) / used; ++x) body(x, part[(size_t)id]);
+  }
+  std::vector<T> out;
+  size_t tot = 0;
+  for (auto& v : part) tot += v.size();
+  out.reserve(tot);
+  for (auto& v : part) out.insert(out.end(), v.begin(), v.end());
+  return out;
+}
+
 struct PlanBuilder {
   Plan& P;
   int64_t top[kArenas] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -287,6 +312,63 @@ struct PlanBuilder {
       }
       std::copy(buf[t].items.begin(), buf[t].items.end(), P.items.begin() + (i0 + io[t]));
     }
+  }
+  // Tensor-core groups written in parallel: body(g, steps, flops) appends the steps of
+  // group g (0 <= g < ng) to `steps` (its thread's buffer), adds their flops and returns
+  // the group with `first` = the position of its first step in that buffer; each thread
+  // takes a contiguous range of g, and the buffers are appended to the program in group
+  // order with `first` rebased.  Returns the flops of all groups.
+  template <class F>
+  int64_t tc_par(int64_t ng, F&& body) {
+    if (ng <= 0) return 0;
+    struct Buf {
+      PlanArray<TcStep> steps;
+      PlanArray<TcGroup> groups;
+      int64_t fl = 0;
+    };
+    std::vector<Buf> buf;
+    std::vector<std::exception_ptr> err;
+    int used = 1;
+#pragma omp parallel if (ng >= 4096)
+    {
+#pragma omp single
+      {
+        used = omp_get_num_threads();
+        buf.resize((size_t)used);
+        err.resize((size_t)used);
+      }
+      const int id = omp_get_thread_num();
+      const int64_t lo = ng * id / used, hi = ng * (id + 1) / used;
+      try {
+        Buf& b = buf[(size_t)id];
+        for (int64_t g = lo; g < hi; ++g) b.groups.push_back(body(g, b.steps, b.fl));
+      } catch (...) {
+        err[(size_t)id] = std::current_exception();
+      }
+    }
+    for (auto& e : err)
+      if (e) std::rethrow_exception(e);
+    std::vector<size_t> so((size_t)used + 1, 0), go((size_t)used + 1, 0);
+    int64_t fl = 0;
+    for (int t = 0; t < used; ++t) {
+      so[t + 1] = so[t] + buf[t].steps.size();
+      go[t + 1] = go[t] + buf[t].groups.size();
+      fl += buf[t].fl;
+    }
+    const size_t st0 = P.tsteps.size(), gr0 = P.tgroups.size();
+    if ((int64_t)(st0 + so[used]) > INT32_MAX) throw Error(H2_ENOMEM, "plan too large");
+    P.tsteps.resize(st0 + so[used]);
+    P.tgroups.resize(gr0 + go[used]);
+#pragma omp parallel for schedule(static, 1) if (used > 1)
+    for (int t = 0; t < used; ++t) {
+      std::copy(buf[t].steps.begin(), buf[t].steps.end(), P.tsteps.begin() + (st0 + so[t]));
+      TcGroup* dg = P.tgroups.data() + gr0 + go[t];
+      for (size_t q = 0; q < buf[t].groups.size(); ++q) {
+        dg[q] = buf[t].groups[q];
+        dg[q].first += (int32_t)(st0 + so[t]);
+      }
+    }
+    return fl;
   }
 };
 
@@ -804,81 +886,63 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
           std::sort(out.begin(), out.end(), [](const Item& x, const Item& y) { return x.b < y.b; });
         };
         auto fhas = [&](int64_t q) { return lt.tg[q].cls == TC_F && gF.size(q) > 0; };
-        std::vector<std::array<int32_t, 2>> grp;
-        for (int64_t q = 0; q < (int64_t)lt.tg.size(); ++q) {
-          if (!fhas(q)) continue;
-          const Target& T = lt.tg[q];
-          const int32_t sib = lt.find(T.i ^ 1, T.k);
-          const bool paired = sib >= 0 && fhas(sib);
-          if (!(T.i & 1)) grp.push_back({(int32_t)q, paired ? sib : -1});
-          else if (!paired) grp.push_back({-1, (int32_t)q});
-        }
+        // (the targets of row cluster i are [first[i], first[i + 1]), in target order)
+        const std::vector<std::array<int32_t, 2>> grp = ordered_collect<std::array<int32_t, 2>>(
+            (int64_t)lt.first.size() - 1, [&](int64_t i, std::vector<std::array<int32_t, 2>>& out) {
+              for (int64_t q = lt.first[i]; q < lt.first[i + 1]; ++q) {
+                if (!fhas(q)) continue;
+                const Target& T = lt.tg[q];
+                const int32_t sib = lt.find(T.i ^ 1, T.k);
+                const bool paired = sib >= 0 && fhas(sib);
+                if (!(T.i & 1)) out.push_back({(int32_t)q, paired ? sib : -1});
+                else if (!paired) out.push_back({-1, (int32_t)q});
+              }
+            });
         const int64_t ng = (int64_t)grp.size();
-        auto merge = [&](const std::vector<Item>& t0, const std::vector<Item>& t1, TcStep* out) {
+        auto merge = [&](const std::vector<Item>& t0, const std::vector<Item>& t1, PlanArray<TcStep>& out) {
           size_t i0 = 0, i1 = 0;
           int64_t n = 0;
           while (i0 < t0.size() || i1 < t1.size()) {
             const bool take0 = i0 < t0.size() && (i1 >= t1.size() || t0[i0].b <= t1[i1].b);
             const bool take1 = i1 < t1.size() && (i0 >= t0.size() || t1[i1].b <= t0[i0].b);
             const Item& x = take0 ? t0[i0] : t1[i1];
-            if (out) {
-              TcStep& sp = out[n];
-              sp.a[0] = take0 ? t0[i0].a : -1;
-              sp.a[1] = take1 ? t1[i1].a : -1;
-              sp.b = x.b;
-              sp.kref = -1;
-              sp.kpad = (int16_t)KPF;
-              sp.pad0 = 0;
-            }
+            TcStep sp;
+            sp.a[0] = take0 ? t0[i0].a : -1;
+            sp.a[1] = take1 ? t1[i1].a : -1;
+            sp.b = x.b;
+            sp.kref = -1;
+            sp.kpad = (int16_t)KPF;
+            sp.pad0 = 0;
+            out.push_back(sp);
             ++n;
             if (take0) ++i0;
             if (take1) ++i1;
           }
           return n;
         };
-        std::vector<int64_t> goff(ng + 1, 0);
-#pragma omp parallel
-        {
-          std::vector<Item> t0, t1;
-#pragma omp for schedule(dynamic, 1024)
-          for (int64_t gq = 0; gq < ng; ++gq) {
-            fterms(grp[gq][0], t0);
-            fterms(grp[gq][1], t1);
-            goff[gq + 1] = merge(t0, t1, nullptr);
+        const size_t gr0 = P.tgroups.size();
+        const int64_t fl = pb.tc_par(ng, [&](int64_t gq, PlanArray<TcStep>& steps, int64_t& flg) {
+          thread_local std::vector<Item> t0, t1;
+          fterms(grp[gq][0], t0);
+          fterms(grp[gq][1], t1);
+          const size_t f0 = steps.size();
+          const int64_t n = merge(t0, t1, steps);
+          TcGroup G{};
+          for (int sl = 0; sl < 2; ++sl) {
+            const int32_t q = grp[gq][sl];
+            G.out[sl] = q >= 0 ? tC(C.F(bl[lt.tg[q].cpos].idx)) : -1;
+            G.mref[sl] = -1;
           }
-        }
-        for (int64_t gq = 0; gq < ng; ++gq) goff[gq + 1] += goff[gq];
-        const size_t st0 = P.tsteps.size(), gr0 = P.tgroups.size();
-        if ((int64_t)st0 + goff[ng] > INT32_MAX) throw Error(H2_ENOMEM, "plan too large");
-        P.tsteps.resize(st0 + (size_t)goff[ng]);
-        P.tgroups.resize(gr0 + (size_t)ng);
-        int64_t fl = 0;
-#pragma omp parallel reduction(+ : fl)
-        {
-          std::vector<Item> t0, t1;
-#pragma omp for schedule(dynamic, 1024)
-          for (int64_t gq = 0; gq < ng; ++gq) {
-            fterms(grp[gq][0], t0);
-            fterms(grp[gq][1], t1);
-            TcStep* stp = P.tsteps.data() + st0 + goff[gq];
-            const int64_t n = merge(t0, t1, stp);
-            TcGroup G{};
-            for (int sl = 0; sl < 2; ++sl) {
-              const int32_t q = grp[gq][sl];
-              G.out[sl] = q >= 0 ? tC(C.F(bl[lt.tg[q].cpos].idx)) : -1;
-              G.mref[sl] = -1;
-            }
-            G.nref = -1;
-            G.first = (int32_t)(st0 + goff[gq]);
-            G.count = (int32_t)n;
-            G.m = (int16_t)LS;
-            G.n = (int16_t)LS;
-            G.ldc = (int16_t)LS;
-            P.tgroups[gr0 + gq] = G;
-            for (int64_t x = 0; x < n; ++x)
-              fl += 2LL * LS * LS * KPF * ((stp[x].a[0] >= 0) + (stp[x].a[1] >= 0));
-          }
-        }
+          G.nref = -1;
+          G.first = (int32_t)f0;
+          G.count = (int32_t)n;
+          G.m = (int16_t)LS;
+          G.n = (int16_t)LS;
+          G.ldc = (int16_t)LS;
+          for (size_t x = f0; x < steps.size(); ++x)
+            flg += 2LL * LS * LS * KPF * ((steps[x].a[0] >= 0) + (steps[x].a[1] >= 0));
+          return G;
+        });
         P.flops += fl;
         if (ng > 0) {
           Launch Lc;
@@ -1391,84 +1455,66 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       };
       // groups: a target of an even row cluster with the target of the next cluster and
       // the same column cluster, if that one has terms; an odd-row target alone otherwise
-      std::vector<std::array<int32_t, 2>> grp;
-      for (int64_t q = 0; q < (int64_t)ntg; ++q) {
-        if (!has_terms(q)) continue;
-        const Target& T = lt.tg[q];
-        const int32_t sib = lt.find(T.i ^ 1, T.k);
-        const bool paired = sib >= 0 && has_terms(sib);
-        if (!(T.i & 1)) grp.push_back({(int32_t)q, paired ? sib : -1});
-        else if (!paired) grp.push_back({-1, (int32_t)q});
-      }
+      // (the targets of row cluster i are [first[i], first[i + 1]), in target order)
+      const std::vector<std::array<int32_t, 2>> grp = ordered_collect<std::array<int32_t, 2>>(
+          nrow, [&](int64_t i, std::vector<std::array<int32_t, 2>>& out) {
+            for (int64_t q = lt.first[i]; q < lt.first[i + 1]; ++q) {
+              if (!has_terms(q)) continue;
+              const Target& T = lt.tg[q];
+              const int32_t sib = lt.find(T.i ^ 1, T.k);
+              const bool paired = sib >= 0 && has_terms(sib);
+              if (!(T.i & 1)) out.push_back({(int32_t)q, paired ? sib : -1});
+              else if (!paired) out.push_back({-1, (int32_t)q});
+            }
+          });
       const int64_t ng = (int64_t)grp.size();
-      // the union of the two targets' B tiles: steps counted, then written
-      auto merge = [&](const std::vector<Item>& t0, const std::vector<Item>& t1, TcStep* out) {
+      // the union of the two targets' B tiles, in order, one step per B tile
+      auto merge = [&](const std::vector<Item>& t0, const std::vector<Item>& t1, PlanArray<TcStep>& out) {
         size_t i0 = 0, i1 = 0;
         int64_t n = 0;
         while (i0 < t0.size() || i1 < t1.size()) {
           const bool take0 = i0 < t0.size() && (i1 >= t1.size() || t0[i0].b <= t1[i1].b);
           const bool take1 = i1 < t1.size() && (i0 >= t0.size() || t1[i1].b <= t0[i0].b);
           const Item& x = take0 ? t0[i0] : t1[i1];
-          if (out) {
-            TcStep& st = out[n];
-            st.a[0] = take0 ? t0[i0].a : -1;
-            st.a[1] = take1 ? t1[i1].a : -1;
-            st.b = x.b;
-            st.kref = x.kref;
-            st.kpad = x.kpad;
-            st.pad0 = 0;
-          }
+          TcStep st;
+          st.a[0] = take0 ? t0[i0].a : -1;
+          st.a[1] = take1 ? t1[i1].a : -1;
+          st.b = x.b;
+          st.kref = x.kref;
+          st.kpad = x.kpad;
+          st.pad0 = 0;
+          out.push_back(st);
           ++n;
           if (take0) ++i0;
           if (take1) ++i1;
         }
         return n;
       };
-      std::vector<int64_t> goff(ng + 1, 0);
-#pragma omp parallel
-      {
-        std::vector<Item> t0, t1;
-#pragma omp for schedule(dynamic, 1024)
-        for (int64_t gq = 0; gq < ng; ++gq) {
-          terms(grp[gq][0], t0);
-          terms(grp[gq][1], t1);
-          goff[gq + 1] = merge(t0, t1, nullptr);
+      const size_t gr0 = P.tgroups.size();
+      const int64_t fl = pb.tc_par(ng, [&](int64_t gq, PlanArray<TcStep>& steps, int64_t& flg) {
+        thread_local std::vector<Item> t0, t1;
+        terms(grp[gq][0], t0);
+        terms(grp[gq][1], t1);
+        const size_t f0 = steps.size();
+        const int64_t n = merge(t0, t1, steps);
+        TcGroup G{};
+        for (int sl = 0; sl < 2; ++sl) {
+          const int32_t q = grp[gq][sl];
+          G.out[sl] = q >= 0 ? lt.tg[q].ssum : -1;
+          G.mref[sl] = q >= 0 ? CR(l, lt.tg[q].i) : -1;
+          // the first contribution is stored, unless the case-1 pass above has written
+          if (q >= 0 && Mt[q] >= 0) G.acc |= (uint8_t)(1u << sl);
         }
-      }
-      for (int64_t gq = 0; gq < ng; ++gq) goff[gq + 1] += goff[gq];
-      const size_t st0 = P.tsteps.size(), gr0 = P.tgroups.size();
-      if ((int64_t)st0 + goff[ng] > INT32_MAX) throw Error(H2_ENOMEM, "plan too large");
-      P.tsteps.resize(st0 + (size_t)goff[ng]);
-      P.tgroups.resize(gr0 + (size_t)ng);
-      int64_t fl = 0;
-#pragma omp parallel reduction(+ : fl)
-      {
-        std::vector<Item> t0, t1;
-#pragma omp for schedule(dynamic, 1024)
-        for (int64_t gq = 0; gq < ng; ++gq) {
-          terms(grp[gq][0], t0);
-          terms(grp[gq][1], t1);
-          TcStep* stp = P.tsteps.data() + st0 + goff[gq];
-          const int64_t n = merge(t0, t1, stp);
-          TcGroup G{};
-          for (int sl = 0; sl < 2; ++sl) {
-            const int32_t q = grp[gq][sl];
-            G.out[sl] = q >= 0 ? lt.tg[q].ssum : -1;
-            G.mref[sl] = q >= 0 ? CR(l, lt.tg[q].i) : -1;
-            // the first contribution is stored, unless the case-1 pass above has written
-            if (q >= 0 && Mt[q] >= 0) G.acc |= (uint8_t)(1u << sl);
-          }
-          G.nref = CC(l, lt.tg[grp[gq][0] >= 0 ? grp[gq][0] : grp[gq][1]].k);
-          G.first = (int32_t)(st0 + goff[gq]);
-          G.count = (int32_t)n;
-          G.m = (int16_t)cm;
-          G.n = (int16_t)cn;
-          G.ldc = (int16_t)cn;
-          P.tgroups[gr0 + gq] = G;
-          for (int64_t x = 0; x < n; ++x)
-            fl += 2LL * cm * cn * stp[x].kpad * ((stp[x].a[0] >= 0) + (stp[x].a[1] >= 0));
-        }
-      }
+        G.nref = CC(l, lt.tg[grp[gq][0] >= 0 ? grp[gq][0] : grp[gq][1]].k);
+        G.first = (int32_t)f0;
+        G.count = (int32_t)n;
+        G.m = (int16_t)cm;
+        G.n = (int16_t)cn;
+        G.ldc = (int16_t)cn;
+        for (size_t x = f0; x < steps.size(); ++x)
+          flg += 2LL * cm * cn * steps[x].kpad * ((steps[x].a[0] >= 0) + (steps[x].a[1] >= 0));
+        return G;
+      });
       P.flops += fl;
       if (ng > 0) {
         Launch Lc;
