@@ -5,6 +5,9 @@
 // over its items), an eigen batch (new bases), or a memset.  Segments of one group
 // never share an output, so every sum has a fixed order: reruns are bitwise equal.
 // All dims are the padded caps of the level; padded entries are exactly zero.
+// The host threads emit a group's segments over contiguous ranges of its loop into
+// their own buffers, joined in loop order (PlanBuilder::par, tc_par): the program does
+// not depend on their number.
 //
 // The product's phases (names as in the paper):
 //   bprod   B_j = (V^A_{j,c})^T V^B_{j,r} and its nested form (Sec. III-D, Eq.
@@ -90,7 +93,8 @@ void emit_sum(S& d, int64_t out, int m, int n, int lda, int ldc, bool acc, const
   d.segs.push_back(s);
 }
 
-// The emission calls on a sink, with the argument conventions of PlanBuilder's
+// The emission calls (gemm, gemm1, sum) on a sink: PlanBuilder has them for the program
+// itself, PlanBuilder::par hands each thread a set over its own buffer
 template <class S>
 struct Emit {
   S& d;
@@ -140,11 +144,11 @@ std::vector<T> ordered_collect(int64_t n, F&& body) {
   return out;
 }
 
-struct PlanBuilder {
+struct PlanBuilder : Emit<Plan> {
   Plan& P;
   int64_t top[kArenas] = {0, 0, 0, 0, 0, 0, 0, 0};
   size_t g0 = 0;
-  explicit PlanBuilder(Plan& p) : P(p) {}
+  explicit PlanBuilder(Plan& p) : Emit<Plan>{p}, P(p) {}
 
   // bump allocation in one region, 256-byte aligned
   int64_t alloc(Arena a, int64_t elems) {
@@ -236,25 +240,6 @@ struct PlanBuilder {
       L.phase = phase;
       P.launches.push_back(L);
     }
-  }
-  void gemm(int64_t out, int m, int n, int k, int lda, int ldb, int ldc, uint8_t fl,
-            const std::vector<Item>& it, int32_t mref = -1, int32_t nref = -1) {
-    emit_gemm(P, out, m, n, k, lda, ldb, ldc, fl, it.data(), it.size(), mref, nref);
-  }
-  void gemm(int64_t out, int m, int n, int k, int lda, int ldb, int ldc, uint8_t fl, const Item* it, size_t nit,
-            int32_t mref = -1, int32_t nref = -1) {
-    emit_gemm(P, out, m, n, k, lda, ldb, ldc, fl, it, nit, mref, nref);
-  }
-  void gemm1(int64_t out, int m, int n, int k, int lda, int ldb, int ldc, uint8_t fl, int64_t a, int64_t b,
-             int32_t mref = -1, int32_t nref = -1, int32_t kref = -1) {
-    const Item x{a, b, kref};
-    emit_gemm(P, out, m, n, k, lda, ldb, ldc, fl, &x, 1, mref, nref);
-  }
-  void sum(int64_t out, int m, int n, int lda, int ldc, bool acc, const std::vector<int64_t>& mats) {
-    emit_sum(P, out, m, n, lda, ldc, acc, mats.data(), mats.size());
-  }
-  void sum(int64_t out, int m, int n, int lda, int ldc, bool acc, const int64_t* mats, size_t nm) {
-    emit_sum(P, out, m, n, lda, ldc, acc, mats, nm);
   }
   // The loop `for x in [0, n): body(x, e)` with the segments emitted through e (an
   // Emit<SegBuf>) in parallel: each thread takes a contiguous range of x into its own
@@ -1291,9 +1276,9 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
     pb.par(nc, [&](int64_t t, auto& e) {
       if (leaf) {
         e.gemm1(PA[l][t], rC(l), rA(l), LS, rC(l), rA(l), rA(l), SF_TA | SF_CA, tCb(C.Vr(t)), tA(A.Vr(t)), CR(l, t),
-                 AR(l, t));
+                AR(l, t));
         e.gemm1(PB[l][t], cB(l), cC(l), LS, cB(l), cC(l), cC(l), SF_TA | SF_CB, tB(B.Vc(t)), tCb(C.Vc(t)), BC(l, t),
-                 CC(l, t));
+                CC(l, t));
       } else {  // (k over the children, each bounded by its rank)
         const int hr = rC(c), hc = cC(c);
         std::vector<Item> ia, ib;
@@ -1314,7 +1299,7 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       size_t ns = e.d.segs.size();
       if (leaf && b.kind == KF) {
         e.gemm1(Ahat[l][p], rC(l), rB(l), LS, rC(l), rB(l), rB(l), SF_TA | SF_CA, tCb(C.Vr(b.t)), Y[p], CR(l, b.t),
-                 BR(l, b.s));
+                BR(l, b.s));
         if (tl) tile_out(e.d, ns, RP, KP2, false);
         ns = e.d.segs.size();
         e.gemm1(Bhat[l][p], cA(l), cC(l), LS, LS, cC(l), cC(l), SF_CB, Yb[p], tCb(C.Vc(b.s)), AC(l, b.t), CC(l, b.s));
@@ -1366,19 +1351,19 @@ void build_mmp_plan(const Mat& A, const Mat& B, Mat& C, const MmpParams& prm, Pl
       if (b.kind != KR) return;
       size_t ns = e.d.segs.size();
       e.gemm1(Ahat[l][p], rC(l), rB(l), rA(l), rA(l), rB(l), rB(l), 0, PA[l][b.t], T1[p], CR(l, b.t), BR(l, b.s),
-               AR(l, b.t));
+              AR(l, b.t));
       if (tcl[l]) tile_out(e.d, ns, RP, KP2, false);
       ns = e.d.segs.size();
       e.gemm1(Bhat[l][p], cA(l), cC(l), cB(l), cB(l), cC(l), cC(l), 0, T2[p], PB[l][b.s], AC(l, b.t), CC(l, b.s),
-               BC(l, b.s));
+              BC(l, b.s));
       if (tcl[l]) tile_out(e.d, ns, NP, KP3, true);
       ns = e.d.segs.size();
       e.gemm1(PAS[p], rC(l), cA(l), rA(l), rA(l), cA(l), cA(l), 0, PA[l][b.t], tA(A.S(l, b.idx)), CR(l, b.t),
-               AC(l, b.s), AR(l, b.t));
+              AC(l, b.s), AR(l, b.t));
       if (tcl[l]) tile_out(e.d, ns, RP, KP3, false);
       ns = e.d.segs.size();
       e.gemm1(SBP[p], rB(l), cC(l), cB(l), cB(l), cC(l), cC(l), 0, tB(B.S(l, b.idx)), PB[l][b.s], BR(l, b.t),
-               CC(l, b.s), BC(l, b.s));
+              CC(l, b.s), BC(l, b.s));
       if (tcl[l]) tile_out(e.d, ns, NP, KP2, true);
     });
     pb.end("rimage", l);
