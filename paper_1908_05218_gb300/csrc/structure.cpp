@@ -7,9 +7,12 @@
 // A block (t, s) is admissible when max(diam_t, diam_s) <= eta * dist(t, s) with
 // box diagonals and box distance, compared squared, and dist > 0.  Non-admissible
 // blocks are dense (F) on the leaf level and subdivided (NL) above it.
+#include <omp.h>
+
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <parallel/algorithm>
 
 #include "internal.hpp"
 
@@ -50,11 +53,17 @@ std::shared_ptr<Structure> build_structure(const double* up, int64_t n, int leaf
   st->size.assign(L + 1, {});
   st->start[0] = {0};
   st->size[0] = {n};
+  // The clusters of a level are split in parallel; on the top levels, which have fewer
+  // clusters than threads, each sort runs on all threads instead.  The order (coordinate,
+  // then user index) is total, so every sort has one result whatever the threads.
+  const int nthr = omp_get_max_threads();
   for (int l = 0; l < L; ++l) {
     auto& ns = st->start[l + 1];
     auto& nz = st->size[l + 1];
     ns.resize(2LL << l);
     nz.resize(2LL << l);
+    const bool wide = (1LL << l) < nthr;
+#pragma omp parallel for schedule(dynamic, 1) if (!wide)
     for (int64_t t = 0; t < (1LL << l); ++t) {
       int64_t s0 = st->start[l][t], m = st->size[l][t];
       std::array<double, 3> lo{INFINITY, INFINITY, INFINITY}, hi{-INFINITY, -INFINITY, -INFINITY};
@@ -67,11 +76,15 @@ std::shared_ptr<Structure> build_structure(const double* up, int64_t n, int leaf
       int axis = 0;
       for (int d = 1; d < 3; ++d)
         if (hi[d] - lo[d] > hi[axis] - lo[axis]) axis = d;
-      std::sort(perm.begin() + s0, perm.begin() + s0 + m, [&](int64_t a, int64_t b) {
+      auto before = [&](int64_t a, int64_t b) {
         double va = up[3 * a + axis], vb = up[3 * b + axis];
         if (va != vb) return va < vb;
         return a < b;
-      });
+      };
+      if (wide && m >= (1 << 16))
+        __gnu_parallel::sort(perm.begin() + s0, perm.begin() + s0 + m, before);
+      else
+        std::sort(perm.begin() + s0, perm.begin() + s0 + m, before);
       int64_t m1 = (m + 1) / 2;
       ns[2 * t] = s0;
       nz[2 * t] = m1;
