@@ -756,6 +756,36 @@ void run_plan(const Plan& P, const ArenaSet& ar, const Arenas* d_ars, const MmpP
 
 }  // namespace h2
 
+namespace {
+
+// The matrix that the host-only program checks (h2_plan_stats, h2_plan_digest,
+// h2_plan_selfcheck) multiply: the structure of the points and the storage caps that an
+// import of their Laplace H^2 matrix (host construction at eps) would set, with the
+// arena offsets computed; no device memory.  Returns the arena size.
+int64_t laplace_host_mat(const double* points, int64_t n, int32_t leaf_size, double eta, double eps, h2::Mat& m) {
+  using namespace h2;
+  auto st = build_structure(points, n, leaf_size, eta);
+  const double h = std::cbrt(1.0 / (double)n);
+  h2_kernel k{H2_K_LAPLACE, 0.0, 1.0 / (2.0 * M_PI * h), 0.0};
+  Packed p;
+  build_h2_host(*st, k, eps, p);
+  m.st = st;
+  m.Kr.assign(st->L + 1, 0);
+  m.Kc.assign(st->L + 1, 0);
+  for (int l = 0; l <= st->L; ++l)
+    for (int64_t t = 0; t < (1LL << l); ++t) {
+      m.Kr[l] = std::max(m.Kr[l], p.kr[Structure::node(l, t)]);
+      m.Kc[l] = std::max(m.Kc[l], p.kc[Structure::node(l, t)]);
+    }
+  for (int l = 0; l <= st->L; ++l) {
+    m.Kr[l] = cap_round(m.Kr[l]);
+    m.Kc[l] = cap_round(m.Kc[l]);
+  }
+  return mat_elems(m);
+}
+
+}  // namespace
+
 using namespace h2;
 
 extern "C" {
@@ -843,25 +873,9 @@ h2_status h2_plan_stats(const double* points, int64_t n, int32_t leaf_size, doub
   return guarded([&] {
     if (!(eps > 0) || !(eps < 1)) throw Error(H2_EINVAL, "eps must lie in (0, 1)");
     if (trunc < H2_TRUNC_PAPER || trunc > H2_TRUNC_FORMATTED) throw Error(H2_EINVAL, "unknown truncation rule");
-    auto st = build_structure(points, n, leaf_size, eta);
-    const double h = std::cbrt(1.0 / (double)n);
-    h2_kernel k{H2_K_LAPLACE, 0.0, 1.0 / (2.0 * M_PI * h), 0.0};
-    Packed p;
-    build_h2_host(*st, k, eps, p);
     Mat m;
-    m.st = st;
-    m.Kr.assign(st->L + 1, 0);
-    m.Kc.assign(st->L + 1, 0);
-    for (int l = 0; l <= st->L; ++l)
-      for (int64_t t = 0; t < (1LL << l); ++t) {
-        m.Kr[l] = std::max(m.Kr[l], p.kr[Structure::node(l, t)]);
-        m.Kc[l] = std::max(m.Kc[l], p.kc[Structure::node(l, t)]);
-      }
-    for (int l = 0; l <= st->L; ++l) {
-      m.Kr[l] = cap_round(m.Kr[l]);
-      m.Kc[l] = cap_round(m.Kc[l]);
-    }
-    mat_elems(m);
+    laplace_host_mat(points, n, leaf_size, eta, eps, m);
+    const std::shared_ptr<Structure>& st = m.st;
     Plan P;
     Mat C;
     C.st = st;
@@ -880,25 +894,9 @@ h2_status h2_plan_digest(const double* points, int64_t n, int32_t leaf_size, dou
     if (!(eps > 0) || !(eps < 1)) throw Error(H2_EINVAL, "eps must lie in (0, 1)");
     if (trunc < H2_TRUNC_PAPER || trunc > H2_TRUNC_FORMATTED) throw Error(H2_EINVAL, "unknown truncation rule");
     if (precision < H2_FP64 || precision > H2_MIXED_BF16X3) throw Error(H2_EINVAL, "unknown precision");
-    auto st = build_structure(points, n, leaf_size, eta);
-    const double h = std::cbrt(1.0 / (double)n);
-    h2_kernel k{H2_K_LAPLACE, 0.0, 1.0 / (2.0 * M_PI * h), 0.0};
-    Packed p;
-    build_h2_host(*st, k, eps, p);
     Mat m;
-    m.st = st;
-    m.Kr.assign(st->L + 1, 0);
-    m.Kc.assign(st->L + 1, 0);
-    for (int l = 0; l <= st->L; ++l)
-      for (int64_t t = 0; t < (1LL << l); ++t) {
-        m.Kr[l] = std::max(m.Kr[l], p.kr[Structure::node(l, t)]);
-        m.Kc[l] = std::max(m.Kc[l], p.kc[Structure::node(l, t)]);
-      }
-    for (int l = 0; l <= st->L; ++l) {
-      m.Kr[l] = cap_round(m.Kr[l]);
-      m.Kc[l] = cap_round(m.Kc[l]);
-    }
-    mat_elems(m);
+    laplace_host_mat(points, n, leaf_size, eta, eps, m);
+    const std::shared_ptr<Structure>& st = m.st;
     Plan P;
     Mat C;
     C.st = st;
@@ -947,25 +945,9 @@ h2_status h2_plan_selfcheck(const double* points, int64_t n, int32_t leaf_size, 
     if (!(eps > 0) || !(eps < 1)) throw Error(H2_EINVAL, "eps must lie in (0, 1)");
     // host only: structure, H^2 ranks of the Laplace kernel, storage caps as an import
     // would set them, then every program built and validated (no device memory)
-    auto st = build_structure(points, n, leaf_size, eta);
-    const double h = std::cbrt(1.0 / (double)n);
-    h2_kernel k{H2_K_LAPLACE, 0.0, 1.0 / (2.0 * M_PI * h), 0.0};
-    Packed p;
-    build_h2_host(*st, k, eps, p);
     Mat m;
-    m.st = st;
-    m.Kr.assign(st->L + 1, 0);
-    m.Kc.assign(st->L + 1, 0);
-    for (int l = 0; l <= st->L; ++l)
-      for (int64_t t = 0; t < (1LL << l); ++t) {
-        m.Kr[l] = std::max(m.Kr[l], p.kr[Structure::node(l, t)]);
-        m.Kc[l] = std::max(m.Kc[l], p.kc[Structure::node(l, t)]);
-      }
-    for (int l = 0; l <= st->L; ++l) {
-      m.Kr[l] = cap_round(m.Kr[l]);
-      m.Kc[l] = cap_round(m.Kc[l]);
-    }
-    const int64_t asz = mat_elems(m);
+    const int64_t asz = laplace_host_mat(points, n, leaf_size, eta, eps, m);
+    const std::shared_ptr<Structure>& st = m.st;
     for (int trunc : {H2_TRUNC_PAPER, H2_TRUNC_SV, H2_TRUNC_FULL, H2_TRUNC_FORMATTED})
       for (int prec : {H2_FP64, H2_MIXED_FP32, H2_MIXED_BF16X3})
         for (int cap : {24, 48}) {
