@@ -41,7 +41,6 @@ struct Structure {
   std::vector<std::vector<int64_t>> start, size;  // per level, per cluster
   std::vector<std::vector<std::array<double, 3>>> lo, hi;
   std::vector<std::vector<Block>> blocks;  // per level, sorted by (t, s)
-  std::vector<std::unordered_map<int64_t, int32_t>> where;  // (t<<32|s) -> position
   std::vector<std::vector<int32_t>> row_ptr;  // CSR over blocks[l] by row cluster
   std::vector<std::vector<int32_t>> col_ptr, col_list;  // CSC: positions by column
   std::vector<int64_t> nR;  // admissible blocks per level
@@ -49,10 +48,19 @@ struct Structure {
   int lmin = 0;
   int csp = 0;
 
-  static int64_t key(int64_t t, int64_t s) { return (t << 32) | s; }
+  // position of block (t, s) in blocks[l], -1 if absent: a binary search over row t's
+  // blocks, which are sorted by s
   int32_t find(int l, int64_t t, int64_t s) const {
-    auto it = where[l].find(key(t, s));
-    return it == where[l].end() ? -1 : it->second;
+    const std::vector<int32_t>& rp = row_ptr[l];
+    if (t < 0 || t + 1 >= (int64_t)rp.size()) return -1;
+    const std::vector<Block>& bl = blocks[l];
+    int32_t lo = rp[t], hi = rp[t + 1];
+    while (lo < hi) {
+      const int32_t mid = lo + (hi - lo) / 2;
+      if (bl[mid].s < s) lo = mid + 1;
+      else hi = mid;
+    }
+    return (lo < rp[t + 1] && bl[lo].s == s) ? lo : -1;
   }
   static int node(int l, int64_t t) { return (int)((1LL << l) - 1 + t); }
   int nnodes() const { return (int)((1LL << (L + 1)) - 1); }

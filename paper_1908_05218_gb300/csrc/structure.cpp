@@ -126,7 +126,6 @@ std::shared_ptr<Structure> build_structure(const double* up, int64_t n, int leaf
 
   // block partition, level by level, candidates sorted by (t, s)
   st->blocks.assign(L + 1, {});
-  st->where.assign(L + 1, {});
   st->nR.assign(L + 1, 0);
   std::vector<std::pair<int64_t, int64_t>> cand{{0, 0}};
   const double eta2 = eta * eta;
@@ -169,11 +168,9 @@ std::shared_ptr<Structure> build_structure(const double* up, int64_t n, int leaf
     auto& rp = st->row_ptr[l];
     rp.assign(nc + 1, 0);
     std::vector<int32_t> ccount(nc + 1, 0);
-    st->where[l].reserve(bl.size() * 2);
     for (size_t p = 0; p < bl.size(); ++p) {
       rp[bl[p].t + 1]++;
       ccount[bl[p].s + 1]++;
-      st->where[l][Structure::key(bl[p].t, bl[p].s)] = (int32_t)p;
       if (bl[p].kind == KR) st->lmin = std::min(st->lmin, l);
     }
     for (int64_t t = 0; t < nc; ++t) {
